@@ -1,0 +1,61 @@
+/*
+ * opta_debug.h -- verification hooks of libopta.so.
+ *
+ * Each hook runs one preparation kernel of the library in isolation on
+ * caller-owned DEVICE buffers so that tests can compare it with a CPU
+ * statement of the same step.  They are not needed to search.  All
+ * pointers named *_dev are device pointers; the caller owns every buffer.
+ * Images are row-major uint8 with stride == cols.  Each hook synchronises
+ * `stream` (a cudaStream_t) and returns an opta_status.
+ */
+#ifndef OPTA_DEBUG_H
+#define OPTA_DEBUG_H
+
+#include "opta.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Local statistics (Algorithm 3's Run-Sum S, Q and Omega) of every m x n
+ * window of I: inv_sigma_dev[y*(q-n+1)+x] = 1/Omega (0 for a flat window),
+ * Omega = sqrt(Q - S^2/mn), from FP64 integral images. */
+opta_status opta_dbg_window_stats(const uint8_t *I_dev, int32_t p, int32_t q,
+                                  int32_t m, int32_t n, float *inv_sigma_dev,
+                                  void *stream);
+
+/* Spatially varying Gaussian blur (Eq. defblur, Eq. Gauss) rounded to the
+ * nearest integer: sigma_map_host is ceil(p/block) x ceil(q/block) floats,
+ * each 0 or one of the values allowed by opta_params (radius ceil(3 sigma)
+ * <= 9, sigma <= 3).  P_dev receives p x q bytes. */
+opta_status opta_dbg_blur(const uint8_t *I_dev, int32_t p, int32_t q,
+                          const float *sigma_map_host, int32_t block,
+                          uint8_t *P_dev, void *stream);
+
+/* Blur correlation R_oo(x) = rho(P window at x, I window at x)
+ * (Algorithm 3); R_dev receives (p-m+1)(q-n+1) floats. */
+opta_status opta_dbg_blur_corr(const uint8_t *P_dev, const uint8_t *I_dev,
+                               int32_t p, int32_t q, int32_t m, int32_t n,
+                               float *R_dev, void *stream);
+
+/* Pivot auto-correlation (Algorithm 1 with the pivot block read from P):
+ * rco_dev[x] = rho(P window at the centre of x's group, I window at x) for
+ * odd group side h in {1,3,5,7,9}.  rco_dev may be NULL; n_retained_host
+ * (nullable) receives #{x : rho_co(x) < rho_cut} (Algorithm 2's count). */
+opta_status opta_dbg_rho_co(const uint8_t *P_dev, const uint8_t *I_dev,
+                            int32_t p, int32_t q, int32_t m, int32_t n, int32_t h,
+                            float *rco_dev, double rho_cut, int64_t *n_retained_host,
+                            void *stream);
+
+/* The prepared state of size (m, n) of a handle: pivot_dev (p x q bytes),
+ * rho_co_dev (L floats), sigma_map_host (blocks_y x blocks_x floats).
+ * Any pointer may be NULL. */
+opta_status optA_debug_maps(opta_handle *h, int32_t m, int32_t n,
+                            uint8_t *pivot_dev, float *rho_co_dev,
+                            float *sigma_map_host, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OPTA_DEBUG_H */

@@ -1,0 +1,263 @@
+"""GB300 OptA template search: Python binding of libopta.so.
+
+Thin marshalling layer over the C ABI declared in include/opta.h (same
+names).  Images and templates may be numpy arrays (host) or torch tensors
+(host or CUDA); streams are torch.cuda.Stream objects, raw cudaStream_t
+integers or None (the current torch stream when torch has CUDA, else the
+legacy default stream).  Nothing here computes any part of the search.
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import byref, c_double, c_float, c_int32, c_int64, c_size_t, c_void_p
+
+from . import _lib
+from ._lib import OptaImage, OptaParams, OptaResult, OptaSizeInfo, OptaTemplate, STATUS
+
+__all__ = [
+    "OptaError", "opta_params_default", "optA_prepare", "optA_search", "zncc_full",
+    "optA_debug_bounds", "optA_size_info", "optA_memory_bytes", "optA_destroy",
+    "optA_debug_maps", "opta_dbg_window_stats", "opta_dbg_blur", "opta_dbg_blur_corr",
+    "opta_dbg_rho_co", "Handle", "lib",
+]
+
+lib = _lib.lib
+
+
+class OptaError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = int(code)
+        name = STATUS.get(self.code, str(code))
+        super().__init__(f"{what}: {name}" if what else name)
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise OptaError(code, what)
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return c_void_p(0)
+    if isinstance(stream, int):
+        return c_void_p(stream)
+    return c_void_p(stream.cuda_stream)
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _array_desc(a, kind):
+    """(rows, cols, stride_elems, dtype_code, on_device, ptr, keepalive)."""
+    if _is_torch(a):
+        import torch
+        if a.dim() != 2 or a.stride(1) != 1:
+            raise ValueError(f"{kind} must be a 2-D tensor with unit column stride")
+        if a.dtype == torch.uint8:
+            code = _lib.OPTA_U8
+        elif a.dtype == torch.float32:
+            code = _lib.OPTA_F32
+        else:
+            raise TypeError(f"{kind} dtype must be uint8 or float32")
+        return a.shape[0], a.shape[1], a.stride(0), code, int(a.is_cuda), a.data_ptr(), a
+    import numpy as np
+    a = np.asarray(a)
+    if a.ndim != 2:
+        raise ValueError(f"{kind} must be 2-D")
+    if a.dtype not in (np.uint8, np.float32) or a.strides[1] != a.itemsize:
+        a = np.ascontiguousarray(a, dtype=np.float32 if a.dtype != np.uint8 else np.uint8)
+    code = _lib.OPTA_U8 if a.dtype == np.uint8 else _lib.OPTA_F32
+    return a.shape[0], a.shape[1], a.strides[0] // a.itemsize, code, 0, a.ctypes.data, a
+
+
+def _image(a):
+    r, c, s, code, dev, ptr, keep = _array_desc(a, "image")
+    return OptaImage(r, c, s, code, dev, ptr), keep
+
+
+def _template(a):
+    r, c, s, code, dev, ptr, keep = _array_desc(a, "template")
+    if code != _lib.OPTA_F32:
+        if _is_torch(keep):
+            keep = keep.float()
+            s = keep.stride(0); ptr = keep.data_ptr()
+        else:
+            import numpy as np
+            keep = np.ascontiguousarray(keep, dtype=np.float32)
+            s = keep.strides[0] // 4; ptr = keep.ctypes.data
+    return OptaTemplate(r, c, s, dev, 0, ptr), keep
+
+
+def opta_params_default(**overrides) -> OptaParams:
+    """Section 7 defaults, with keyword overrides (sigma_levels as a sequence)."""
+    p = OptaParams()
+    lib().opta_params_default(byref(p))
+    for k, v in overrides.items():
+        if k == "sigma_levels":
+            v = list(v)
+            p.n_levels = len(v)
+            for i in range(8):
+                p.sigma_levels[i] = float(v[i]) if i < len(v) else 0.0
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class Handle:
+    """Owns an opta_handle*; released by close() or garbage collection."""
+
+    def __init__(self, ptr: int, rows: int, cols: int):
+        self._ptr = c_void_p(ptr)
+        self.rows, self.cols = rows, cols
+
+    @property
+    def ptr(self):
+        if not self._ptr:
+            raise ValueError("handle closed")
+        return self._ptr
+
+    def close(self):
+        if self._ptr:
+            lib().optA_destroy(self._ptr)
+            self._ptr = c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def optA_prepare(image, params: OptaParams | None = None, sizes=None, stream=None) -> Handle:
+    img, keep = _image(image)
+    sz = list(sizes or [])
+    arr = (c_int32 * (2 * len(sz) or 1))()
+    for i, s in enumerate(sz):
+        m, n = (s, s) if isinstance(s, int) else s
+        arr[2 * i], arr[2 * i + 1] = int(m), int(n)
+    out = c_void_p(0)
+    code = lib().optA_prepare(byref(img), byref(params) if params is not None else None,
+                              arr if sz else None, len(sz), _stream(stream), byref(out))
+    del keep
+    _check(code, "optA_prepare")
+    return Handle(out.value, img.rows, img.cols)
+
+
+def optA_search(handle: Handle, templates, stream=None, check: bool = True):
+    """Best match per template: list of OptaResult (status per template)."""
+    if not isinstance(templates, (list, tuple)):
+        templates = [templates]
+    n = len(templates)
+    descs = (OptaTemplate * max(n, 1))()
+    keep = []
+    for i, t in enumerate(templates):
+        d, k = _template(t)
+        descs[i] = d
+        keep.append(k)
+    out = (OptaResult * max(n, 1))()
+    code = lib().optA_search(handle.ptr, descs, n, out, _stream(stream))
+    if check and code not in (0, 2):
+        raise OptaError(code, "optA_search")
+    return [out[i] for i in range(n)]
+
+
+def zncc_full(image, template, rho_map=None, stream=None, check: bool = True) -> OptaResult:
+    """Exhaustive search; rho_map (optional) is a CUDA float32 tensor of L elements."""
+    img, k1 = _image(image)
+    t, k2 = _template(template)
+    res = OptaResult()
+    ptr = c_void_p(rho_map.data_ptr()) if rho_map is not None else c_void_p(0)
+    code = lib().zncc_full(byref(img), byref(t), ptr, byref(res), _stream(stream))
+    del k1, k2
+    if check and code not in (0, 2):
+        raise OptaError(code, "zncc_full")
+    return res
+
+
+def optA_debug_bounds(handle: Handle, template, ub_map=None, survived=None, stream=None) -> int:
+    t, k = _template(template)
+    code = lib().optA_debug_bounds(handle.ptr, byref(t),
+                                   c_void_p(ub_map.data_ptr() if ub_map is not None else 0),
+                                   c_void_p(survived.data_ptr() if survived is not None else 0),
+                                   _stream(stream))
+    del k
+    if code not in (0, 2):
+        raise OptaError(code, "optA_debug_bounds")
+    return code
+
+
+def optA_size_info(handle: Handle, m: int, n: int) -> dict:
+    info = OptaSizeInfo()
+    _check(lib().optA_size_info(handle.ptr, m, n, byref(info)), "optA_size_info")
+    return info.as_dict()
+
+
+def optA_memory_bytes(handle: Handle) -> int:
+    b = c_size_t(0)
+    _check(lib().optA_memory_bytes(handle.ptr, byref(b)), "optA_memory_bytes")
+    return int(b.value)
+
+
+def optA_destroy(handle: Handle) -> None:
+    handle.close()
+
+
+def optA_debug_maps(handle: Handle, m: int, n: int, pivot=None, rho_co=None, stream=None):
+    """Copies the prepared pivot image / rho_co map into CUDA tensors; returns the sigma map."""
+    import numpy as np
+    by = (handle.rows + 63) // 64
+    info = optA_size_info(handle, m, n)
+    smap = np.zeros((info["blocks_y"], info["blocks_x"]), dtype=np.float32)
+    _check(lib().optA_debug_maps(handle.ptr, m, n,
+                                 c_void_p(pivot.data_ptr() if pivot is not None else 0),
+                                 c_void_p(rho_co.data_ptr() if rho_co is not None else 0),
+                                 smap.ctypes.data_as(ctypes.POINTER(c_float)), _stream(stream)),
+           "optA_debug_maps")
+    del by
+    return smap
+
+
+def opta_dbg_window_stats(I_dev, m: int, n: int, inv_sigma_dev, stream=None):
+    p, q = I_dev.shape
+    _check(lib().opta_dbg_window_stats(c_void_p(I_dev.data_ptr()), p, q, m, n,
+                                       c_void_p(inv_sigma_dev.data_ptr()), _stream(stream)),
+           "opta_dbg_window_stats")
+
+
+def opta_dbg_blur(I_dev, sigma_map, block: int, P_dev, stream=None):
+    import numpy as np
+    p, q = I_dev.shape
+    sm = np.ascontiguousarray(sigma_map, dtype=np.float32)
+    _check(lib().opta_dbg_blur(c_void_p(I_dev.data_ptr()), p, q,
+                               sm.ctypes.data_as(ctypes.POINTER(c_float)), block,
+                               c_void_p(P_dev.data_ptr()), _stream(stream)), "opta_dbg_blur")
+
+
+def opta_dbg_blur_corr(P_dev, I_dev, m: int, n: int, R_dev, stream=None):
+    p, q = I_dev.shape
+    _check(lib().opta_dbg_blur_corr(c_void_p(P_dev.data_ptr()), c_void_p(I_dev.data_ptr()),
+                                    p, q, m, n, c_void_p(R_dev.data_ptr()), _stream(stream)),
+           "opta_dbg_blur_corr")
+
+
+def opta_dbg_rho_co(P_dev, I_dev, m: int, n: int, h: int, rco_dev=None, rho_cut: float = 0.6,
+                    stream=None) -> int:
+    p, q = I_dev.shape
+    cnt = c_int64(0)
+    _check(lib().opta_dbg_rho_co(c_void_p(P_dev.data_ptr()), c_void_p(I_dev.data_ptr()), p, q,
+                                 m, n, h, c_void_p(rco_dev.data_ptr() if rco_dev is not None else 0),
+                                 c_double(rho_cut), byref(cnt), _stream(stream)), "opta_dbg_rho_co")
+    return int(cnt.value)

@@ -1,0 +1,101 @@
+"""ctypes declarations of libopta.so's C ABI (include/opta.h, include/opta_debug.h).
+
+Argument marshalling only: every step of the search runs in the library's
+CUDA kernels.  Loading fails loudly when the shared library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_float, c_int32, c_int64, c_size_t, c_uint8, c_void_p
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.environ.get("OPTA_LIB", os.path.join(PKG, "_build", "libopta.so"))
+
+OPTA_U8, OPTA_F32 = 0, 1
+
+STATUS = {
+    0: "OPTA_OK", 1: "OPTA_ERR_INVALID_ARG", 2: "OPTA_ERR_FLAT_TEMPLATE", 3: "OPTA_ERR_OOM",
+    4: "OPTA_ERR_CUDA", 5: "OPTA_ERR_TIMEOUT", 6: "OPTA_ERR_BUSY", 7: "OPTA_ERR_UNSUPPORTED",
+}
+
+
+class OptaImage(ctypes.Structure):
+    _fields_ = [("rows", c_int32), ("cols", c_int32), ("stride_elems", c_int64),
+                ("dtype", c_int32), ("on_device", c_int32), ("data", c_void_p)]
+
+
+class OptaTemplate(ctypes.Structure):
+    _fields_ = [("rows", c_int32), ("cols", c_int32), ("stride_elems", c_int64),
+                ("on_device", c_int32), ("reserved", c_int32), ("data", c_void_p)]
+
+
+class OptaResult(ctypes.Structure):
+    _fields_ = [("y", c_int32), ("x", c_int32), ("rho", c_double),
+                ("n_locations", c_int64), ("n_centres", c_int64), ("n_survivors", c_int64),
+                ("n_candidates", c_int64), ("group_h", c_int32), ("status", c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class OptaParams(ctypes.Structure):
+    _fields_ = [("rho_th", c_double), ("rho_max", c_double), ("xi", c_double),
+                ("block", c_int32), ("n_levels", c_int32), ("sigma_levels", c_float * 8),
+                ("h_max", c_int32), ("fixed_h", c_int32), ("blur", c_int32), ("topk", c_int32),
+                ("precision", c_int32), ("reserved", c_int32 * 7)]
+
+
+class OptaSizeInfo(ctypes.Structure):
+    _fields_ = [("m", c_int32), ("n", c_int32), ("group_h", c_int32), ("level", c_int32),
+                ("cost", c_int64), ("n_groups", c_int64), ("blocks_y", c_int32),
+                ("blocks_x", c_int32), ("n_egs_evals", c_int32), ("reserved", c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+# name -> (restype, argtypes); every symbol declared in include/*.h
+SIGNATURES = {
+    "opta_params_default": (None, [POINTER(OptaParams)]),
+    "opta_status_str": (c_char_p, [c_int32]),
+    "optA_prepare": (c_int32, [POINTER(OptaImage), POINTER(OptaParams), POINTER(c_int32), c_int32,
+                               c_void_p, POINTER(c_void_p)]),
+    "optA_search": (c_int32, [c_void_p, POINTER(OptaTemplate), c_int32, POINTER(OptaResult),
+                              c_void_p]),
+    "zncc_full": (c_int32, [POINTER(OptaImage), POINTER(OptaTemplate), c_void_p,
+                            POINTER(OptaResult), c_void_p]),
+    "optA_debug_bounds": (c_int32, [c_void_p, POINTER(OptaTemplate), c_void_p, c_void_p, c_void_p]),
+    "optA_size_info": (c_int32, [c_void_p, c_int32, c_int32, POINTER(OptaSizeInfo)]),
+    "optA_memory_bytes": (c_int32, [c_void_p, POINTER(c_size_t)]),
+    "optA_destroy": (c_int32, [c_void_p]),
+    "opta_dbg_window_stats": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32, c_void_p,
+                                        c_void_p]),
+    "opta_dbg_blur": (c_int32, [c_void_p, c_int32, c_int32, POINTER(c_float), c_int32, c_void_p,
+                                c_void_p]),
+    "opta_dbg_blur_corr": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32,
+                                     c_void_p, c_void_p]),
+    "opta_dbg_rho_co": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32,
+                                  c_void_p, c_double, POINTER(c_int64), c_void_p]),
+    "optA_debug_maps": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p,
+                                  POINTER(c_float), c_void_p]),
+}
+
+_LIB = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"libopta.so not found at {LIB_PATH}; build it with "
+                "`python -m paper_1407_3535_gb300.build` (no CPU fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB

@@ -1,0 +1,878 @@
+// C ABI of libopta.so: handle lifecycle, OptA preparation driver
+// (Algorithms 2 and 3), per-template search sequencing (Sections 2 and 6)
+// and the exhaustive search.  All device work is enqueued on the caller's
+// stream; host decisions of the preparation loop read back a few scalars.
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+#include "opta_debug.h"
+
+using namespace opta;
+
+namespace {
+
+opta_status map_err(cudaError_t e) {
+    if (e == cudaSuccess) return OPTA_OK;
+    cudaGetLastError();   // clear the non-sticky error state
+    return e == cudaErrorMemoryAllocation ? OPTA_ERR_OOM : OPTA_ERR_CUDA;
+}
+
+#define CK(x)                                                    \
+    do {                                                         \
+        cudaError_t e__ = (x);                                   \
+        if (e__ != cudaSuccess) return map_err(e__);             \
+    } while (0)
+#define TRY(x)                                                   \
+    do {                                                         \
+        opta_status s__ = (x);                                   \
+        if (s__ != OPTA_OK) return s__;                          \
+    } while (0)
+
+constexpr int kMaxRadius = 9;
+
+// Device allocation that keeps a running byte count.
+struct DevMem {
+    size_t bytes = 0;
+    template <class T>
+    opta_status alloc(T **p, size_t count) {
+        *p = nullptr;
+        if (count == 0) count = 1;
+        void *v = nullptr;
+        cudaError_t e = cudaMalloc(&v, count * sizeof(T));
+        if (e != cudaSuccess) { cudaGetLastError(); return OPTA_ERR_OOM; }
+        bytes += count * sizeof(T);
+        *p = static_cast<T *>(v);
+        return OPTA_OK;
+    }
+    template <class T>
+    void release(T *&p, size_t count) {
+        if (p) { cudaFree(p); bytes -= (count ? count : 1) * sizeof(T); p = nullptr; }
+    }
+};
+
+struct SizeState {
+    int m = 0, n = 0, Ly = 0, Lx = 0, Gy = 0, Gx = 0;
+    int h = 1, level = 0, n_evals = 0;
+    long long cost = 0;
+    uint8_t *P = nullptr;          // pivot image (owned unless it aliases the image)
+    bool P_owned = false;
+    float *inv_sigma = nullptr;    // L
+    float *rho_co = nullptr;       // L
+    float *c_inv_sigma = nullptr;  // G
+    float *c_efac = nullptr;       // G
+    std::vector<float> sigma_map;
+};
+
+}  // namespace
+
+struct opta_handle {
+    int p = 0, q = 0, device = 0;
+    opta_params prm;
+    DevMem mem;
+    uint8_t *I8 = nullptr;
+    double *IIS = nullptr, *IIQ = nullptr;
+    std::map<std::pair<int, int>, SizeState *> sizes;
+    // search scratch (grown on demand)
+    size_t capL = 0, capG = 0, capT = 0, capN = 0;
+    float *rho_tc = nullptr, *e_tc = nullptr;
+    int *surv = nullptr;
+    float *surv_rho = nullptr, *surv_eps = nullptr;
+    int *cand = nullptr;
+    double *cand_rho = nullptr;
+    float *topk_v = nullptr;
+    int *topk_i = nullptr;
+    float *tf = nullptr, *tstage = nullptr;
+    double *td = nullptr;
+    TmplState *states = nullptr;
+    // blur tables
+    float *weights = nullptr;
+    int *radius = nullptr;
+    bool busy = false;
+};
+
+namespace {
+
+bool valid_params(const opta_params &p) {
+    if (!(p.rho_th > -1.0 && p.rho_th < 1.0)) return false;
+    if (!(p.rho_max >= -1.0 && p.rho_max <= 1.0)) return false;
+    if (!(p.xi >= 0.0)) return false;
+    if (p.block < 8 || p.block > 128) return false;
+    if (p.n_levels < 0 || p.n_levels > 8) return false;
+    for (int i = 0; i < p.n_levels; ++i)
+        if (!(p.sigma_levels[i] > 0.f && p.sigma_levels[i] <= 3.0f)) return false;
+    if (p.h_max < 1 || p.h_max > 9 || (p.h_max % 2) == 0) return false;
+    if (p.fixed_h < 0 || p.fixed_h > 9 || (p.fixed_h > 0 && p.fixed_h % 2 == 0)) return false;
+    if (p.topk < 1 || p.topk > kTopkMax) return false;
+    if (p.precision != 0) return false;
+    return true;
+}
+
+double lambda_of(double rth, double rmax) {   // Eq. misDec
+    const double r = 1.0 + rth * rth * rmax * rmax - (rth * rth + rmax * rmax);
+    return rth * rmax + std::sqrt(r > 0.0 ? r : 0.0);
+}
+
+// 1-D normalised Gaussian weights for the level table (radius ceil(3 sigma)).
+void gauss_table(const opta_params &prm, std::vector<float> &w, std::vector<int> &rad) {
+    const int L = prm.n_levels + 1;
+    w.assign((size_t)L * (kMaxRadius + 1), 0.f);
+    rad.assign(L, 0);
+    for (int l = 1; l < L; ++l) {
+        const double s = prm.sigma_levels[l - 1];
+        const int R = (int)std::ceil(3.0 * s);
+        rad[l] = R;
+        double tot = 0.0;
+        std::vector<double> g(R + 1);
+        for (int i = 0; i <= R; ++i) g[i] = std::exp(-(double)(i * i) / (2.0 * s * s));
+        for (int i = -R; i <= R; ++i) tot += g[i < 0 ? -i : i];
+        for (int i = 0; i <= R; ++i) w[(size_t)l * (kMaxRadius + 1) + i] = (float)(g[i] / tot);
+    }
+}
+
+opta_status ingest(const opta_image *img, uint8_t *dst, cudaStream_t s) {
+    const int p = img->rows, q = img->cols;
+    const int64_t ld = img->stride_elems;
+    if (img->dtype == OPTA_U8) {
+        if (img->on_device) {
+            CK(launch_ingest_u8(static_cast<const uint8_t *>(img->data), ld, p, q, dst, s));
+        } else {
+            CK(cudaMemcpy2DAsync(dst, q, img->data, ld, q, p, cudaMemcpyHostToDevice, s));
+        }
+        return OPTA_OK;
+    }
+    // float32: must hold integers in [0, 255]
+    const float *src = static_cast<const float *>(img->data);
+    float *staging = nullptr;
+    int *bad = nullptr;
+    CK(cudaMallocAsync(&bad, sizeof(int), s));
+    CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    int64_t sld = ld;
+    if (!img->on_device) {
+        CK(cudaMallocAsync(&staging, (size_t)p * q * sizeof(float), s));
+        CK(cudaMemcpy2DAsync(staging, (size_t)q * sizeof(float), src, ld * sizeof(float),
+                             (size_t)q * sizeof(float), p, cudaMemcpyHostToDevice, s));
+        src = staging;
+        sld = q;
+    }
+    CK(launch_ingest_f32(src, sld, p, q, dst, bad, s));
+    int hbad = 0;
+    CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (staging) CK(cudaFreeAsync(staging, s));
+    CK(cudaFreeAsync(bad, s));
+    CK(cudaStreamSynchronize(s));
+    return hbad ? OPTA_ERR_UNSUPPORTED : OPTA_OK;
+}
+
+bool valid_image(const opta_image *img) {
+    return img && img->data && img->rows > 0 && img->cols > 0 &&
+           img->stride_elems >= img->cols && (img->dtype == OPTA_U8 || img->dtype == OPTA_F32) &&
+           (int64_t)img->rows * img->cols < (int64_t)1 << 31;
+}
+
+bool valid_template(const opta_template *t, int p, int q) {
+    return t && t->data && t->rows > 0 && t->cols > 0 && t->stride_elems >= t->cols &&
+           t->rows <= p && t->cols <= q && t->cols <= 1024;
+}
+
+// ---------------------------------------------------------------------------
+// Preparation of one template size: Algorithm 3 (OptA) driving Algorithm 2
+// (EGS) under the readings documented with the oracle.
+// ---------------------------------------------------------------------------
+struct PrepScratch {
+    uint8_t *Pcur = nullptr, *Pacc = nullptr;
+    double *PS = nullptr, *PQ = nullptr, *PX = nullptr;
+    int *fail = nullptr;
+    uint8_t *lvl = nullptr;
+    unsigned long long *count = nullptr;
+    size_t nII = 0;
+};
+
+opta_status egs_cost(opta_handle *H, SizeState *S, const uint8_t *P, const double *PS,
+                     const double *PQ, int h, unsigned long long *dcount, long long *cost,
+                     cudaStream_t s) {
+    const float cut = (float)std::sqrt(1.0 - H->prm.rho_th * H->prm.rho_th);
+    CK(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), s));
+    CK(launch_rho_co(P, H->I8, H->p, H->q, S->m, S->n, h, H->IIS, H->IIQ, PS, PQ, cut, nullptr,
+                     dcount, s));
+    unsigned long long c = 0;
+    CK(cudaMemcpyAsync(&c, dcount, sizeof(c), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *cost = (long long)groups_along(S->Ly, h) * groups_along(S->Lx, h) + (long long)c;
+    S->n_evals++;
+    return OPTA_OK;
+}
+
+// Largest group side the auto-correlation kernel supports for width n.
+int h_limit(int n, int hmax) {
+    int h = hmax;
+    while (h > 1) {
+        const int maxt = h >= 9 ? 512 : (h >= 7 ? 640 : 1024);
+        if (n + h <= maxt) break;
+        h -= 2;
+    }
+    return h;
+}
+
+// Algorithm 2: grow h by 2 while the cost drops by more than xi of the last.
+opta_status egs(opta_handle *H, SizeState *S, const uint8_t *P, const double *PS,
+                const double *PQ, int h_start, unsigned long long *dcount, int *h_out,
+                long long *c_out, cudaStream_t s) {
+    const int hmax = h_limit(S->n, H->prm.h_max);
+    int h = std::min(h_start, hmax);
+    long long c = 0;
+    TRY(egs_cost(H, S, P, PS, PQ, h, dcount, &c, s));
+    while (h + 2 <= hmax) {
+        long long c2 = 0;
+        TRY(egs_cost(H, S, P, PS, PQ, h + 2, dcount, &c2, s));
+        if ((double)(c - c2) > H->prm.xi * (double)c) { h += 2; c = c2; }
+        else break;
+    }
+    *h_out = h;
+    *c_out = c;
+    return OPTA_OK;
+}
+
+opta_status blur_to(opta_handle *H, PrepScratch &W, const std::vector<uint8_t> &levels,
+                    uint8_t *P, cudaStream_t s) {
+    CK(cudaMemcpyAsync(W.lvl, levels.data(), levels.size(), cudaMemcpyHostToDevice, s));
+    CK(launch_blur(H->I8, H->p, H->q, W.lvl, H->prm.block, H->weights, H->radius, P, s));
+    // levels is a host vector: keep the copy ordered before it can change
+    CK(cudaStreamSynchronize(s));
+    return OPTA_OK;
+}
+
+opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
+    auto key = std::make_pair(m, n);
+    if (H->sizes.count(key)) return OPTA_OK;
+    const int p = H->p, q = H->q;
+    SizeState *S = new (std::nothrow) SizeState();
+    if (!S) return OPTA_ERR_OOM;
+    S->m = m; S->n = n; S->Ly = p - m + 1; S->Lx = q - n + 1;
+    const int64_t L = (int64_t)S->Ly * S->Lx;
+    const opta_params &prm = H->prm;
+    const int block = prm.block;
+    const int bp = (p + block - 1) / block, bq = (q + block - 1) / block;
+    S->sigma_map.assign((size_t)bp * bq, 0.f);
+
+    PrepScratch W;
+    auto cleanup = [&](opta_status st) {
+        if (W.Pcur) cudaFree(W.Pcur);
+        if (W.Pacc && W.Pacc != S->P) cudaFree(W.Pacc);
+        if (W.PS) cudaFree(W.PS);
+        if (W.PQ) cudaFree(W.PQ);
+        if (W.PX) cudaFree(W.PX);
+        if (W.fail) cudaFree(W.fail);
+        if (W.lvl) cudaFree(W.lvl);
+        if (W.count) cudaFree(W.count);
+        if (st != OPTA_OK) {
+            H->mem.release(S->inv_sigma, L);
+            H->mem.release(S->rho_co, L);
+            H->mem.release(S->c_inv_sigma, (size_t)S->Gy * S->Gx);
+            H->mem.release(S->c_efac, (size_t)S->Gy * S->Gx);
+            if (S->P_owned) H->mem.release(S->P, (size_t)p * q);
+            delete S;
+        }
+        return st;
+    };
+#define PTRY(x) do { opta_status s__ = (x); if (s__ != OPTA_OK) return cleanup(s__); } while (0)
+#define PCK(x) do { cudaError_t e__ = (x); if (e__ != cudaSuccess) return cleanup(map_err(e__)); } while (0)
+
+    PTRY(H->mem.alloc(&S->inv_sigma, L));
+    PCK(launch_window_stats(H->IIS, H->IIQ, p, q, m, n, S->inv_sigma, nullptr, s));
+    PCK(cudaMalloc(&W.count, sizeof(unsigned long long)));
+
+    // Level 0: unblurred pivots (P = I).
+    int h_best = 1;
+    long long c_best = 0;
+    bool best_is_image = true;
+    if (prm.fixed_h > 0) {
+        h_best = std::min(prm.fixed_h, h_limit(n, 9));
+    } else {
+        PTRY(egs(H, S, H->I8, H->IIS, H->IIQ, 1, W.count, &h_best, &c_best, s));
+    }
+    int level_best = 0;
+    if (prm.blur && prm.n_levels > 0 && prm.fixed_h == 0) {
+        const size_t nII = (size_t)(p + 1) * (q + 1);
+        PCK(cudaMalloc(&W.Pcur, (size_t)p * q));
+        PCK(cudaMalloc(&W.Pacc, (size_t)p * q));
+        PCK(cudaMalloc(&W.PS, nII * sizeof(double)));
+        PCK(cudaMalloc(&W.PQ, nII * sizeof(double)));
+        PCK(cudaMalloc(&W.PX, nII * sizeof(double)));
+        PCK(cudaMalloc(&W.fail, (size_t)bp * bq * sizeof(int)));
+        PCK(cudaMalloc(&W.lvl, (size_t)bp * bq));
+        const float lam = (float)lambda_of(prm.rho_th, prm.rho_max);
+        std::vector<uint8_t> cur_level((size_t)bp * bq, 0);   // accepted level index per block
+        std::vector<char> frozen((size_t)bp * bq, 0);
+        std::vector<int> fail((size_t)bp * bq);
+        for (int k = 1; k <= prm.n_levels; ++k) {
+            bool all_frozen = true;
+            for (char f : frozen) all_frozen = all_frozen && f;
+            if (all_frozen) break;
+            std::vector<uint8_t> cand(cur_level);
+            for (size_t b = 0; b < cand.size(); ++b) if (!frozen[b]) cand[b] = (uint8_t)k;
+            PTRY(blur_to(H, W, cand, W.Pcur, s));
+            PCK(launch_integrals(W.Pcur, H->I8, p, q, W.PS, W.PQ, W.PX, s));
+            PCK(cudaMemsetAsync(W.fail, 0, (size_t)bp * bq * sizeof(int), s));
+            PCK(launch_blur_corr(H->IIS, H->IIQ, W.PS, W.PQ, W.PX, p, q, m, n, lam, block,
+                                 W.fail, nullptr, s));
+            PCK(cudaMemcpyAsync(fail.data(), W.fail, fail.size() * sizeof(int),
+                                cudaMemcpyDeviceToHost, s));
+            PCK(cudaStreamSynchronize(s));
+            bool any = false;
+            std::vector<char> new_frozen(frozen);
+            for (size_t b = 0; b < cand.size(); ++b) {
+                if (!frozen[b] && fail[b]) { cand[b] = cur_level[b]; new_frozen[b] = 1; any = true; }
+            }
+            if (any) {
+                PTRY(blur_to(H, W, cand, W.Pcur, s));
+                PCK(launch_integrals(W.Pcur, nullptr, p, q, W.PS, W.PQ, nullptr, s));
+            }
+            int hk = 0;
+            long long ck = 0;
+            PTRY(egs(H, S, W.Pcur, W.PS, W.PQ, h_best, W.count, &hk, &ck, s));
+            if ((double)(c_best - ck) > prm.xi * (double)c_best) {
+                cur_level = cand;
+                frozen = new_frozen;
+                h_best = hk;
+                c_best = ck;
+                level_best = k;
+                std::swap(W.Pcur, W.Pacc);
+                best_is_image = false;
+            } else {
+                break;
+            }
+        }
+        for (size_t b = 0; b < cur_level.size(); ++b)
+            S->sigma_map[b] = cur_level[b] ? prm.sigma_levels[cur_level[b] - 1] : 0.f;
+    }
+    S->h = h_best;
+    S->level = level_best;
+    S->cost = c_best;
+    S->Gy = groups_along(S->Ly, S->h);
+    S->Gx = groups_along(S->Lx, S->h);
+    const int64_t G = (int64_t)S->Gy * S->Gx;
+    const double *PS = H->IIS, *PQ = H->IIQ;
+    if (best_is_image) {
+        S->P = H->I8;
+        S->P_owned = false;
+    } else {
+        // the accepted pivot moves into the size state; its integrals are recomputed
+        H->mem.bytes += (size_t)p * q;
+        S->P = W.Pacc;
+        S->P_owned = true;
+        W.Pacc = nullptr;
+        PCK(launch_integrals(S->P, nullptr, p, q, W.PS, W.PQ, nullptr, s));
+        PS = W.PS;
+        PQ = W.PQ;
+    }
+    PTRY(H->mem.alloc(&S->rho_co, L));
+    PTRY(H->mem.alloc(&S->c_inv_sigma, G));
+    PTRY(H->mem.alloc(&S->c_efac, G));
+    PCK(launch_rho_co(S->P, H->I8, p, q, m, n, S->h, H->IIS, H->IIQ, PS, PQ, 0.f, S->rho_co,
+                      nullptr, s));
+    PCK(launch_centre_stats(PS, PQ, p, q, m, n, S->h, S->Ly, S->Lx, S->c_inv_sigma, S->c_efac, s));
+    PCK(cudaStreamSynchronize(s));
+    H->sizes[key] = S;
+    return cleanup(OPTA_OK);
+#undef PTRY
+#undef PCK
+}
+
+template <class T>
+opta_status grow(opta_handle *H, T *&p, size_t &cap_field_unused, size_t old_n, size_t new_n) {
+    (void)cap_field_unused;
+    H->mem.release(p, old_n);
+    return H->mem.alloc(&p, new_n);
+}
+
+// Make the search scratch large enough for L locations, G groups, a template
+// of T = m * npad elements and N templates in one call.
+opta_status ensure_scratch(opta_handle *H, size_t L, size_t G, size_t T, size_t N) {
+    size_t dummy = 0;
+    if (L > H->capL) {
+        TRY(grow(H, H->surv, dummy, H->capL, L));
+        TRY(grow(H, H->surv_rho, dummy, H->capL, L));
+        TRY(grow(H, H->surv_eps, dummy, H->capL, L));
+        TRY(grow(H, H->cand, dummy, H->capL + kTopkMax, L + kTopkMax));
+        TRY(grow(H, H->cand_rho, dummy, H->capL + kTopkMax, L + kTopkMax));
+        H->capL = L;
+    }
+    if (G > H->capG) {
+        TRY(grow(H, H->rho_tc, dummy, H->capG, G));
+        TRY(grow(H, H->e_tc, dummy, H->capG, G));
+        H->capG = G;
+    }
+    if (!H->topk_v) {
+        TRY(H->mem.alloc(&H->topk_v, 256 * kTopkMax));
+        TRY(H->mem.alloc(&H->topk_i, 256 * kTopkMax));
+    }
+    if (T > H->capT) {
+        TRY(grow(H, H->tf, dummy, H->capT, T));
+        TRY(grow(H, H->td, dummy, H->capT, T));
+        TRY(grow(H, H->tstage, dummy, H->capT, T));
+        H->capT = T;
+    }
+    if (N > H->capN) {
+        TRY(grow(H, H->states, dummy, H->capN, N));
+        H->capN = N;
+    }
+    return OPTA_OK;
+}
+
+// Device pointer to template data (copies host data into the staging buffer).
+opta_status template_device(opta_handle *H, const opta_template *t, const float **dptr,
+                            int64_t *ld, cudaStream_t s) {
+    if (t->on_device) { *dptr = t->data; *ld = t->stride_elems; return OPTA_OK; }
+    CK(cudaMemcpy2DAsync(H->tstage, (size_t)t->cols * sizeof(float), t->data,
+                         (size_t)t->stride_elems * sizeof(float), (size_t)t->cols * sizeof(float),
+                         t->rows, cudaMemcpyHostToDevice, s));
+    *dptr = H->tstage;
+    *ld = t->cols;
+    return OPTA_OK;
+}
+
+// Enqueue the whole pruned search of one template (no host synchronisation).
+opta_status enqueue_search(opta_handle *H, const opta_template *t, TmplState *st, float *ub_map,
+                           uint8_t *surv_map, cudaStream_t s) {
+    SizeState *S = H->sizes[std::make_pair(t->rows, t->cols)];
+    const int m = t->rows, n = t->cols, npad = (n + 7) & ~7;
+    const int capL = (int)H->capL;
+    const float *td_in = nullptr;
+    int64_t ld = 0;
+    TRY(template_device(H, t, &td_in, &ld, s));
+    CK(launch_tmpl_prep(td_in, ld, m, n, npad, H->tf, H->td, st, H->prm.topk, s));
+    CK(launch_centre_rho(S->P, H->p, H->q, H->tf, m, n, npad, S->h, S->Ly, S->Lx,
+                         S->c_inv_sigma, S->c_efac, st, H->rho_tc, H->e_tc, s));
+    CK(launch_topk(H->rho_tc, S->Gy, S->Gx, S->h, S->Ly, S->Lx, H->prm.topk, st, H->topk_v,
+                   H->topk_i, H->cand, s));
+    CK(launch_refine64(H->I8, H->q, S->Lx, H->td, m, n, st, H->cand, H->cand_rho,
+                       capL + kTopkMax, true, s));
+    CK(launch_threshold(st, H->cand_rho, s));
+    CK(launch_bound_compact(H->rho_tc, H->e_tc, S->rho_co, S->Ly, S->Lx, S->h, st, H->surv,
+                            capL, ub_map, surv_map, s));
+    CK(launch_survivors(H->I8, H->q, S->Lx, H->IIS, H->IIQ, H->tf, m, n, npad, S->inv_sigma, st,
+                        H->surv, H->surv_rho, H->surv_eps, capL, s));
+    CK(launch_surv_candidates(st, H->surv, H->surv_rho, H->surv_eps, H->cand,
+                              capL + kTopkMax, s));
+    CK(launch_refine64(H->I8, H->q, S->Lx, H->td, m, n, st, H->cand, H->cand_rho,
+                       capL + kTopkMax, false, s));
+    CK(launch_final_argmax(st, H->cand, H->cand_rho, capL + kTopkMax, s));
+    return OPTA_OK;
+}
+
+void fill_result(const TmplState &st, const SizeState *S, int Lx, int64_t L, int h,
+                 int64_t n_centres, opta_result *r) {
+    std::memset(r, 0, sizeof(*r));
+    r->n_locations = L;
+    r->group_h = h;
+    r->n_centres = n_centres;
+    r->n_survivors = st.n_surv;
+    r->n_candidates = st.n_cand;
+    if (st.flat) {
+        r->y = 0; r->x = 0; r->rho = 0.0;
+        r->status = OPTA_ERR_FLAT_TEMPLATE;
+        return;
+    }
+    r->y = st.best_idx / Lx;
+    r->x = st.best_idx % Lx;
+    r->rho = st.best_rho;
+    r->status = st.overflow ? OPTA_ERR_CUDA : OPTA_OK;
+    (void)S;
+}
+
+struct BusyGuard {
+    opta_handle *h;
+    explicit BusyGuard(opta_handle *hh) : h(hh) { h->busy = true; }
+    ~BusyGuard() { h->busy = false; }
+};
+
+opta_status setup_tables(opta_handle *H) {
+    std::vector<float> w;
+    std::vector<int> rad;
+    gauss_table(H->prm, w, rad);
+    TRY(H->mem.alloc(&H->weights, w.size()));
+    TRY(H->mem.alloc(&H->radius, rad.size()));
+    CK(cudaMemcpy(H->weights, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(H->radius, rad.data(), rad.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return OPTA_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// Public ABI
+// ===========================================================================
+extern "C" {
+
+void opta_params_default(opta_params *prm) {
+    if (!prm) return;
+    std::memset(prm, 0, sizeof(*prm));
+    prm->rho_th = 0.80;
+    prm->rho_max = 0.95;
+    prm->xi = 0.005;
+    prm->block = 64;
+    prm->n_levels = 4;
+    prm->sigma_levels[0] = 0.5f;
+    prm->sigma_levels[1] = 1.0f;
+    prm->sigma_levels[2] = 2.0f;
+    prm->sigma_levels[3] = 3.0f;
+    prm->h_max = 9;
+    prm->fixed_h = 0;
+    prm->blur = 1;
+    prm->topk = 8;
+    prm->precision = 0;
+}
+
+const char *opta_status_str(opta_status s) {
+    switch (s) {
+        case OPTA_OK: return "ok";
+        case OPTA_ERR_INVALID_ARG: return "invalid argument";
+        case OPTA_ERR_FLAT_TEMPLATE: return "flat template (sigma_t == 0)";
+        case OPTA_ERR_OOM: return "out of device memory";
+        case OPTA_ERR_CUDA: return "CUDA error";
+        case OPTA_ERR_TIMEOUT: return "timeout";
+        case OPTA_ERR_BUSY: return "handle busy";
+        case OPTA_ERR_UNSUPPORTED: return "unsupported input";
+    }
+    return "unknown status";
+}
+
+opta_status optA_destroy(opta_handle *h) {
+    if (!h) return OPTA_OK;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(h->device);
+    for (auto &kv : h->sizes) {
+        SizeState *S = kv.second;
+        cudaFree(S->inv_sigma); cudaFree(S->rho_co); cudaFree(S->c_inv_sigma); cudaFree(S->c_efac);
+        if (S->P_owned) cudaFree(S->P);
+        delete S;
+    }
+    void *ptrs[] = {h->I8, h->IIS, h->IIQ, h->rho_tc, h->e_tc, h->surv, h->surv_rho, h->surv_eps,
+                    h->cand, h->cand_rho, h->topk_v, h->topk_i, h->tf, h->tstage, h->td,
+                    h->states, h->weights, h->radius};
+    for (void *p : ptrs) if (p) cudaFree(p);
+    cudaSetDevice(cur);
+    delete h;
+    return OPTA_OK;
+}
+
+opta_status optA_prepare(const opta_image *img, const opta_params *prm, const int32_t *sizes_mn,
+                         int32_t n_sizes, void *stream, opta_handle **out) {
+    if (!out) return OPTA_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!valid_image(img) || n_sizes < 0 || (n_sizes > 0 && !sizes_mn)) return OPTA_ERR_INVALID_ARG;
+    opta_params P;
+    if (prm) P = *prm; else opta_params_default(&P);
+    if (!valid_params(P)) return OPTA_ERR_INVALID_ARG;
+    for (int i = 0; i < n_sizes; ++i) {
+        const int m = sizes_mn[2 * i], n = sizes_mn[2 * i + 1];
+        if (m < 1 || n < 1 || m > img->rows || n > img->cols || n > 1024) return OPTA_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    opta_handle *H = new (std::nothrow) opta_handle();
+    if (!H) return OPTA_ERR_OOM;
+    cudaGetDevice(&H->device);
+    H->prm = P;
+    H->p = img->rows;
+    H->q = img->cols;
+    const int p = H->p, q = H->q;
+    auto fail = [&](opta_status st) { optA_destroy(H); return st; };
+    opta_status st;
+    if ((st = H->mem.alloc(&H->I8, (size_t)p * q)) != OPTA_OK) return fail(st);
+    if ((st = ingest(img, H->I8, s)) != OPTA_OK) return fail(st);
+    const size_t nII = (size_t)(p + 1) * (q + 1);
+    if ((st = H->mem.alloc(&H->IIS, nII)) != OPTA_OK) return fail(st);
+    if ((st = H->mem.alloc(&H->IIQ, nII)) != OPTA_OK) return fail(st);
+    cudaError_t e = launch_integrals(H->I8, nullptr, p, q, H->IIS, H->IIQ, nullptr, s);
+    if (e != cudaSuccess) return fail(map_err(e));
+    if ((st = setup_tables(H)) != OPTA_OK) return fail(st);
+    for (int i = 0; i < n_sizes; ++i)
+        if ((st = prepare_size(H, sizes_mn[2 * i], sizes_mn[2 * i + 1], s)) != OPTA_OK) return fail(st);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(map_err(e));
+    *out = H;
+    return OPTA_OK;
+}
+
+opta_status optA_search(opta_handle *h, const opta_template *t, int32_t n_t, opta_result *out,
+                        void *stream) {
+    if (!h || n_t < 0 || (n_t > 0 && (!t || !out))) return OPTA_ERR_INVALID_ARG;
+    if (h->busy) return OPTA_ERR_BUSY;
+    BusyGuard guard(h);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    size_t maxL = 0, maxG = 0, maxT = 0;
+    for (int i = 0; i < n_t; ++i) {
+        if (!valid_template(&t[i], h->p, h->q)) return OPTA_ERR_INVALID_ARG;
+        TRY(prepare_size(h, t[i].rows, t[i].cols, s));
+        SizeState *S = h->sizes[std::make_pair(t[i].rows, t[i].cols)];
+        maxL = std::max(maxL, (size_t)S->Ly * S->Lx);
+        maxG = std::max(maxG, (size_t)S->Gy * S->Gx);
+        maxT = std::max(maxT, (size_t)t[i].rows * ((t[i].cols + 7) & ~7));
+    }
+    if (n_t == 0) return OPTA_OK;
+    TRY(ensure_scratch(h, maxL, maxG, maxT, (size_t)n_t));
+    for (int i = 0; i < n_t; ++i) TRY(enqueue_search(h, &t[i], h->states + i, nullptr, nullptr, s));
+    std::vector<TmplState> hs(n_t);
+    CK(cudaMemcpyAsync(hs.data(), h->states, sizeof(TmplState) * n_t, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    opta_status first = OPTA_OK;
+    for (int i = 0; i < n_t; ++i) {
+        SizeState *S = h->sizes[std::make_pair(t[i].rows, t[i].cols)];
+        fill_result(hs[i], S, S->Lx, (int64_t)S->Ly * S->Lx, S->h, (int64_t)S->Gy * S->Gx, &out[i]);
+        if (first == OPTA_OK && out[i].status != OPTA_OK) first = (opta_status)out[i].status;
+    }
+    return first;
+}
+
+opta_status optA_debug_bounds(opta_handle *h, const opta_template *t, float *ub_map,
+                              uint8_t *survived, void *stream) {
+    if (!h || !t) return OPTA_ERR_INVALID_ARG;
+    if (!valid_template(t, h->p, h->q)) return OPTA_ERR_INVALID_ARG;
+    if (h->busy) return OPTA_ERR_BUSY;
+    BusyGuard guard(h);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TRY(prepare_size(h, t->rows, t->cols, s));
+    SizeState *S = h->sizes[std::make_pair(t->rows, t->cols)];
+    TRY(ensure_scratch(h, (size_t)S->Ly * S->Lx, (size_t)S->Gy * S->Gx,
+                       (size_t)t->rows * ((t->cols + 7) & ~7), 1));
+    TRY(enqueue_search(h, t, h->states, ub_map, survived, s));
+    TmplState st;
+    CK(cudaMemcpyAsync(&st, h->states, sizeof(st), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return st.flat ? OPTA_ERR_FLAT_TEMPLATE : OPTA_OK;
+}
+
+opta_status optA_size_info(opta_handle *h, int32_t m, int32_t n, opta_size_info *info) {
+    if (!h || !info || m < 1 || n < 1 || m > h->p || n > h->q || n > 1024) return OPTA_ERR_INVALID_ARG;
+    if (h->busy) return OPTA_ERR_BUSY;
+    BusyGuard guard(h);
+    TRY(prepare_size(h, m, n, nullptr));
+    SizeState *S = h->sizes[std::make_pair(m, n)];
+    std::memset(info, 0, sizeof(*info));
+    info->m = m; info->n = n;
+    info->group_h = S->h;
+    info->level = S->level;
+    info->cost = S->cost;
+    info->n_groups = (int64_t)S->Gy * S->Gx;
+    info->blocks_y = (h->p + h->prm.block - 1) / h->prm.block;
+    info->blocks_x = (h->q + h->prm.block - 1) / h->prm.block;
+    info->n_egs_evals = S->n_evals;
+    return OPTA_OK;
+}
+
+opta_status optA_debug_maps(opta_handle *h, int32_t m, int32_t n, uint8_t *pivot_dev,
+                            float *rho_co_dev, float *sigma_map_host, void *stream) {
+    if (!h || m < 1 || n < 1 || m > h->p || n > h->q || n > 1024) return OPTA_ERR_INVALID_ARG;
+    if (h->busy) return OPTA_ERR_BUSY;
+    BusyGuard guard(h);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TRY(prepare_size(h, m, n, s));
+    SizeState *S = h->sizes[std::make_pair(m, n)];
+    if (pivot_dev)
+        CK(cudaMemcpyAsync(pivot_dev, S->P, (size_t)h->p * h->q, cudaMemcpyDeviceToDevice, s));
+    if (rho_co_dev)
+        CK(cudaMemcpyAsync(rho_co_dev, S->rho_co, (size_t)S->Ly * S->Lx * sizeof(float),
+                           cudaMemcpyDeviceToDevice, s));
+    if (sigma_map_host)
+        std::memcpy(sigma_map_host, S->sigma_map.data(), S->sigma_map.size() * sizeof(float));
+    CK(cudaStreamSynchronize(s));
+    return OPTA_OK;
+}
+
+opta_status optA_memory_bytes(const opta_handle *h, size_t *bytes) {
+    if (!h || !bytes) return OPTA_ERR_INVALID_ARG;
+    *bytes = h->mem.bytes;
+    return OPTA_OK;
+}
+
+opta_status zncc_full(const opta_image *img, const opta_template *t, float *rho_map,
+                      opta_result *best, void *stream) {
+    if (!valid_image(img) || !best) return OPTA_ERR_INVALID_ARG;
+    if (!valid_template(t, img->rows, img->cols)) return OPTA_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int p = img->rows, q = img->cols, m = t->rows, n = t->cols, npad = (n + 7) & ~7;
+    const int Ly = p - m + 1, Lx = q - n + 1;
+    const int64_t L = (int64_t)Ly * Lx;
+    const size_t nII = (size_t)(p + 1) * (q + 1);
+    uint8_t *I8 = nullptr;
+    double *IIS = nullptr, *IIQ = nullptr, *td = nullptr;
+    float *inv = nullptr, *ef = nullptr, *map = rho_map, *tf = nullptr, *tst = nullptr;
+    int *cand = nullptr;
+    double *cand_rho = nullptr;
+    TmplState *st = nullptr;
+    std::vector<void *> owned;
+    auto A = [&](auto **ptr, size_t bytes) -> cudaError_t {
+        cudaError_t e = cudaMallocAsync((void **)ptr, bytes ? bytes : 1, s);
+        if (e == cudaSuccess) owned.push_back(*ptr);
+        return e;
+    };
+    auto finish = [&](opta_status stt) {
+        for (void *p2 : owned) cudaFreeAsync(p2, s);
+        cudaStreamSynchronize(s);
+        return stt;
+    };
+#define ZCK(x) do { cudaError_t e__ = (x); if (e__ != cudaSuccess) return finish(map_err(e__)); } while (0)
+    ZCK(A(&I8, (size_t)p * q));
+    {
+        opta_status stt = ingest(img, I8, s);
+        if (stt != OPTA_OK) return finish(stt);
+    }
+    ZCK(A(&IIS, nII * sizeof(double)));
+    ZCK(A(&IIQ, nII * sizeof(double)));
+    ZCK(A(&inv, L * sizeof(float)));
+    ZCK(A(&ef, L * sizeof(float)));
+    if (!map) ZCK(A(&map, L * sizeof(float)));
+    ZCK(A(&tf, (size_t)m * npad * sizeof(float)));
+    ZCK(A(&td, (size_t)m * n * sizeof(double)));
+    ZCK(A(&cand, L * sizeof(int)));
+    ZCK(A(&cand_rho, L * sizeof(double)));
+    ZCK(A(&st, sizeof(TmplState)));
+    const float *tdev = t->data;
+    int64_t ld = t->stride_elems;
+    if (!t->on_device) {
+        ZCK(A(&tst, (size_t)m * n * sizeof(float)));
+        ZCK(cudaMemcpy2DAsync(tst, (size_t)n * sizeof(float), t->data,
+                              (size_t)t->stride_elems * sizeof(float), (size_t)n * sizeof(float), m,
+                              cudaMemcpyHostToDevice, s));
+        tdev = tst;
+        ld = n;
+    }
+    ZCK(launch_integrals(I8, nullptr, p, q, IIS, IIQ, nullptr, s));
+    ZCK(launch_window_stats(IIS, IIQ, p, q, m, n, inv, ef, s));
+    ZCK(launch_tmpl_prep(tdev, ld, m, n, npad, tf, td, st, 0, s));
+    ZCK(launch_zncc_map(I8, p, q, tf, m, n, npad, inv, ef, st, map, s));
+    ZCK(launch_map_candidates(map, ef, L, m, n, st, cand, (int)L, s));
+    ZCK(launch_refine64(I8, q, Lx, td, m, n, st, cand, cand_rho, (int)L, false, s));
+    ZCK(launch_final_argmax(st, cand, cand_rho, (int)L, s));
+    TmplState hs;
+    ZCK(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    ZCK(cudaStreamSynchronize(s));
+    fill_result(hs, nullptr, Lx, L, 1, L, best);
+    best->n_survivors = L;
+    return finish((opta_status)best->status);
+#undef ZCK
+}
+
+// ---------------------------------------------------------------------------
+// Verification hooks (opta_debug.h)
+// ---------------------------------------------------------------------------
+opta_status opta_dbg_window_stats(const uint8_t *I_dev, int32_t p, int32_t q, int32_t m,
+                                  int32_t n, float *inv_sigma_dev, void *stream) {
+    if (!I_dev || !inv_sigma_dev || p < 1 || q < 1 || m < 1 || n < 1 || m > p || n > q)
+        return OPTA_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t nII = (size_t)(p + 1) * (q + 1);
+    double *S = nullptr, *Q = nullptr;
+    CK(cudaMallocAsync(&S, nII * sizeof(double), s));
+    CK(cudaMallocAsync(&Q, nII * sizeof(double), s));
+    cudaError_t e = launch_integrals(I_dev, nullptr, p, q, S, Q, nullptr, s);
+    if (e == cudaSuccess) e = launch_window_stats(S, Q, p, q, m, n, inv_sigma_dev, nullptr, s);
+    cudaFreeAsync(S, s);
+    cudaFreeAsync(Q, s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    CK(e);
+    CK(e2);
+    return OPTA_OK;
+}
+
+opta_status opta_dbg_blur(const uint8_t *I_dev, int32_t p, int32_t q, const float *sigma_map_host,
+                          int32_t block, uint8_t *P_dev, void *stream) {
+    if (!I_dev || !P_dev || !sigma_map_host || p < 1 || q < 1 || block < 8 || block > 128)
+        return OPTA_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int bp = (p + block - 1) / block, bq = (q + block - 1) / block;
+    // distinct sigma values -> level table
+    opta_params prm;
+    opta_params_default(&prm);
+    prm.n_levels = 0;
+    std::vector<uint8_t> lv((size_t)bp * bq, 0);
+    for (int b = 0; b < bp * bq; ++b) {
+        const float sg = sigma_map_host[b];
+        if (!(sg >= 0.f && sg <= 3.0f)) return OPTA_ERR_INVALID_ARG;
+        if (sg == 0.f) continue;
+        int l = -1;
+        for (int k = 0; k < prm.n_levels; ++k) if (prm.sigma_levels[k] == sg) l = k;
+        if (l < 0) {
+            if (prm.n_levels == 8) return OPTA_ERR_INVALID_ARG;
+            prm.sigma_levels[prm.n_levels] = sg;
+            l = prm.n_levels++;
+        }
+        lv[b] = (uint8_t)(l + 1);
+    }
+    std::vector<float> w;
+    std::vector<int> rad;
+    gauss_table(prm, w, rad);
+    float *dw = nullptr;
+    int *dr = nullptr;
+    uint8_t *dl = nullptr;
+    CK(cudaMallocAsync(&dw, w.size() * sizeof(float), s));
+    CK(cudaMallocAsync(&dr, rad.size() * sizeof(int), s));
+    CK(cudaMallocAsync(&dl, lv.size(), s));
+    CK(cudaMemcpyAsync(dw, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dr, rad.data(), rad.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dl, lv.data(), lv.size(), cudaMemcpyHostToDevice, s));
+    cudaError_t e = launch_blur(I_dev, p, q, dl, block, dw, dr, P_dev, s);
+    cudaFreeAsync(dw, s);
+    cudaFreeAsync(dr, s);
+    cudaFreeAsync(dl, s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    CK(e);
+    CK(e2);
+    return OPTA_OK;
+}
+
+opta_status opta_dbg_blur_corr(const uint8_t *P_dev, const uint8_t *I_dev, int32_t p, int32_t q,
+                               int32_t m, int32_t n, float *R_dev, void *stream) {
+    if (!P_dev || !I_dev || !R_dev || p < 1 || q < 1 || m < 1 || n < 1 || m > p || n > q)
+        return OPTA_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t nII = (size_t)(p + 1) * (q + 1);
+    double *b[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    for (auto &x : b) CK(cudaMallocAsync(&x, nII * sizeof(double), s));
+    cudaError_t e = launch_integrals(I_dev, nullptr, p, q, b[0], b[1], nullptr, s);
+    if (e == cudaSuccess) e = launch_integrals(P_dev, I_dev, p, q, b[2], b[3], b[4], s);
+    if (e == cudaSuccess)
+        e = launch_blur_corr(b[0], b[1], b[2], b[3], b[4], p, q, m, n, 0.f, 64, nullptr, R_dev, s);
+    for (auto &x : b) cudaFreeAsync(x, s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    CK(e);
+    CK(e2);
+    return OPTA_OK;
+}
+
+opta_status opta_dbg_rho_co(const uint8_t *P_dev, const uint8_t *I_dev, int32_t p, int32_t q,
+                            int32_t m, int32_t n, int32_t h, float *rco_dev, double rho_cut,
+                            int64_t *n_retained_host, void *stream) {
+    if (!P_dev || !I_dev || p < 1 || q < 1 || m < 1 || n < 1 || m > p || n > q)
+        return OPTA_ERR_INVALID_ARG;
+    if (h < 1 || h > 9 || h % 2 == 0 || h_limit(n, 9) < h) return OPTA_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t nII = (size_t)(p + 1) * (q + 1);
+    double *b[4] = {nullptr, nullptr, nullptr, nullptr};
+    unsigned long long *cnt = nullptr;
+    for (auto &x : b) CK(cudaMallocAsync(&x, nII * sizeof(double), s));
+    CK(cudaMallocAsync(&cnt, sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+    cudaError_t e = launch_integrals(I_dev, nullptr, p, q, b[0], b[1], nullptr, s);
+    if (e == cudaSuccess) e = launch_integrals(P_dev, nullptr, p, q, b[2], b[3], nullptr, s);
+    if (e == cudaSuccess)
+        e = launch_rho_co(P_dev, I_dev, p, q, m, n, h, b[0], b[1], b[2], b[3], (float)rho_cut,
+                          rco_dev, cnt, s);
+    unsigned long long hc = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s);
+    for (auto &x : b) cudaFreeAsync(x, s);
+    cudaFreeAsync(cnt, s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    CK(e);
+    CK(e2);
+    if (n_retained_host) *n_retained_host = (int64_t)hc;
+    return OPTA_OK;
+}
+
+}  // extern "C"

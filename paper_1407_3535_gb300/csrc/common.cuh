@@ -1,0 +1,138 @@
+// Internal declarations shared by the CUDA translation units of libopta.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "opta.h"
+
+namespace opta {
+
+// Unit roundoff of binary32.
+constexpr float kU32 = 5.9604644775390625e-8f;  // 2^-24
+
+// ---------------------------------------------------------------------------
+// Group layout (Section 2, Fig. 1): groups of h x h locations tile the
+// location grid from (0, 0); the last group along an axis may be cut short;
+// its centre is start + (size - 1) / 2.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int group_centre_of(int g, int len, int h) {
+    const int start = g * h;
+    int size = len - start;
+    if (size > h) size = h;
+    return start + (size - 1) / 2;
+}
+__host__ __device__ inline int groups_along(int len, int h) { return (len + h - 1) / h; }
+
+// Order-preserving map of a float to uint32 (larger float -> larger key).
+__device__ inline uint32_t float_key(float f) {
+    uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ inline float key_float(uint32_t k) {
+    uint32_t b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+    return __uint_as_float(b);
+}
+
+// Per-template device state, one per template in flight.
+struct TmplState {
+    double mu;          // template mean (FP64)
+    double sigma;       // sqrt(sum (t - mu)^2) (FP64)
+    float inv_sigma;    // 1 / sigma (0 if flat)
+    int flat;           // sigma == 0
+    // search pipeline
+    unsigned int lo_key;      // float_key of the best certain lower bound on max rho
+    int n_surv;               // survivors written
+    int n_cand;               // candidates written (the first `topk` are threshold centres)
+    int n_topk;               // number of threshold centres
+    double thr;               // threshold: max exact rho over the threshold centres
+    float thr_lo;             // thr rounded down, minus margin (compare in FP32)
+    int best_idx;             // final argmax (linear location index)
+    double best_rho;          // final rho (FP64)
+    int overflow;             // candidate buffer overflowed (status)
+    int pad_;
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (stream-ordered, return cudaError_t of the launch).
+// ---------------------------------------------------------------------------
+// Integral images (FP64, (p+1) x (q+1), zero first row/col) of A, A*A and,
+// if B != null and o2 != null, A*B.
+cudaError_t launch_integrals(const uint8_t *A, const uint8_t *B, int p, int q,
+                             double *o0, double *o1, double *o2, cudaStream_t s);
+
+// inv_sigma[y*Lx+x] = 1/Omega and efac[y*Lx+x] = ||I-128|| / Omega (0 when flat).
+cudaError_t launch_window_stats(const double *IIS, const double *IIQ, int p, int q,
+                                int m, int n, float *inv_sigma, float *efac128,
+                                cudaStream_t s);
+
+// Convert a float32 image holding integers in [0,255] into uint8; bad = 1 otherwise.
+cudaError_t launch_ingest_f32(const float *src, int64_t ld, int p, int q, uint8_t *dst,
+                              int *bad, cudaStream_t s);
+cudaError_t launch_ingest_u8(const uint8_t *src, int64_t ld, int p, int q, uint8_t *dst,
+                             cudaStream_t s);
+
+// Template statistics: tf (m x npad, FP32, zero padded) and td (m x n, FP64) hold t - mu.
+cudaError_t launch_tmpl_prep(const float *t, int64_t ld, int m, int n, int npad,
+                             float *tf, double *td, TmplState *st, int topk, cudaStream_t s);
+
+// Exhaustive FP32 map (Eq. rho1 with v = I - 128), plus the certain lower bound key.
+cudaError_t launch_zncc_map(const uint8_t *I, int p, int q, const float *tf, int m, int n,
+                            int npad, const float *inv_sigma, const float *efac128,
+                            TmplState *st, float *map, cudaStream_t s);
+// Candidates from a full FP32 map: map + eps >= lower bound.
+cudaError_t launch_map_candidates(const float *map, const float *efac128, int64_t L, int m,
+                                  int n, TmplState *st, int *cand, int cap, cudaStream_t s);
+
+// FP64 recomputation of rho at the candidate locations [from, n_cand).
+cudaError_t launch_refine64(const uint8_t *I, int q, int Lx, const double *td, int m, int n,
+                            TmplState *st, const int *cand, double *cand_rho, int cap,
+                            bool topk_range, cudaStream_t s);
+// Final argmax over candidates -> st->best_idx / best_rho.
+cudaError_t launch_final_argmax(TmplState *st, const int *cand, const double *cand_rho, int cap,
+                                cudaStream_t s);
+
+// --- pruned search ---
+cudaError_t launch_centre_rho(const uint8_t *P, int p, int q, const float *tf, int m, int n,
+                              int npad, int h, int Ly, int Lx, const float *c_inv_sigma,
+                              const float *c_efac, TmplState *st, float *rho_tc,
+                              float *e_tc, cudaStream_t s);
+cudaError_t launch_topk(const float *rho_tc, int Gy, int Gx, int h, int Ly, int Lx, int k,
+                        TmplState *st, float *tmp_val, int *tmp_idx, int *cand,
+                        cudaStream_t s);
+cudaError_t launch_threshold(TmplState *st, const double *cand_rho, cudaStream_t s);
+cudaError_t launch_bound_compact(const float *rho_tc, const float *e_tc, const float *rho_co,
+                                 int Ly, int Lx, int h, TmplState *st, int *surv, int cap,
+                                 float *ub_map, uint8_t *surv_map, cudaStream_t s);
+cudaError_t launch_survivors(const uint8_t *I, int q, int Lx, const double *IIS,
+                             const double *IIQ, const float *tf, int m, int n, int npad,
+                             const float *inv_sigma, TmplState *st, const int *surv,
+                             float *surv_rho, float *surv_eps, int cap, cudaStream_t s);
+cudaError_t launch_surv_candidates(TmplState *st, const int *surv, const float *surv_rho,
+                                   const float *surv_eps, int *cand, int cap,
+                                   cudaStream_t s);
+
+// --- preparation ---
+// Blur with per-block sigma-level index (uint8 map; level 0 = copy) and weight table.
+cudaError_t launch_blur(const uint8_t *I, int p, int q, const uint8_t *level_map, int block,
+                        const float *weights /* [levels][10] */, const int *radius,
+                        uint8_t *P, cudaStream_t s);
+// Blur correlation per location; block fail flags where a non-flat window has R < lambda.
+cudaError_t launch_blur_corr(const double *IIS, const double *IIQ, const double *PS,
+                             const double *PQ, const double *PX, int p, int q, int m, int n,
+                             float lambda, int block, int *fail, float *R, cudaStream_t s);
+// Pivot auto-correlation map / retained count for odd group side h.
+cudaError_t launch_rho_co(const uint8_t *P, const uint8_t *I, int p, int q, int m, int n,
+                          int h, const double *IIS, const double *IIQ, const double *PS,
+                          const double *PQ, float cut, float *rco,
+                          unsigned long long *count, cudaStream_t s);
+// Per-centre pivot statistics: inv_sigma_hat and ||P-128||/sigma_hat.
+cudaError_t launch_centre_stats(const double *PS, const double *PQ, int p, int q, int m,
+                                int n, int h, int Ly, int Lx, float *c_inv_sigma,
+                                float *c_efac, cudaStream_t s);
+
+int num_sms();
+int topk_blocks(int G);
+constexpr int kTopkMax = 16;   // largest supported params.topk
+
+}  // namespace opta

@@ -1,0 +1,730 @@
+// Per-template search kernels: template statistics, the exhaustive FP32 map,
+// the pruned path of Sections 2 and 6 (centre rho, threshold, transitive
+// bound + compaction, survivors) and the FP64 final argmax.
+//
+// Error bounds.  Every FP32 correlation produced here carries a certain
+// bound eps on |rho_fp32 - rho_exact|: for a dot product accumulated with
+// at most k roundings per term (Higham, Accuracy and Stability of
+// Numerical Algorithms, Section 3.1) and template values rounded once,
+//   |num_fp32 - num| <= (k+2) u ||t'||_2 ||v||_2     (Cauchy-Schwarz),
+// so eps = (k+2) u (1.01) ||v||/sigma_v + 8u (the 8u covers the final
+// products with 1/sigma).  ||v||/sigma_v ("efac") comes from exact integer
+// window sums.  These bounds make the elimination test and the choice of
+// FP64 candidates safe.
+#include "common.cuh"
+
+namespace opta {
+
+namespace {
+
+__device__ inline float eps_bound(int k, float efac) {
+    return (float)(k + 2) * kU32 * 1.01f * efac + 8.f * kU32;
+}
+
+__device__ inline double warp_sum_d(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ inline float warp_sum_f(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ inline float warp_max_f(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide sum of a double (blockDim.x multiple of 32, <= 1024).
+__device__ double block_sum_d(double v, double *sh) {
+    v = warp_sum_d(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = lane < nw ? sh[lane] : 0.0;
+        r = warp_sum_d(r);
+        if (lane == 0) sh[0] = r;
+    }
+    __syncthreads();
+    r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Template statistics (Eq. rho1's mu_t and sigma_t), two FP64 passes.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024)
+tmpl_prep_kernel(const float *__restrict__ t, int64_t ld, int m, int n, int npad,
+                 float *tf, double *td, TmplState *st, int topk) {
+    __shared__ double sh[32];
+    const int mn = m * n;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < mn; i += blockDim.x) s += (double)t[(int64_t)(i / n) * ld + (i % n)];
+    s = block_sum_d(s, sh);
+    const double mu = s / (double)mn;
+    double ss = 0.0;
+    for (int i = threadIdx.x; i < mn; i += blockDim.x) {
+        const double d = (double)t[(int64_t)(i / n) * ld + (i % n)] - mu;
+        td[i] = d;
+        ss += d * d;
+    }
+    for (int i = threadIdx.x; i < m * npad; i += blockDim.x) {
+        const int u = i / npad, v = i % npad;
+        tf[i] = v < n ? (float)((double)t[(int64_t)u * ld + v] - mu) : 0.f;
+    }
+    ss = block_sum_d(ss, sh);
+    if (threadIdx.x == 0) {
+        const double sg = sqrt(ss);
+        st->mu = mu;
+        st->sigma = sg;
+        st->inv_sigma = sg > 0.0 ? (float)(1.0 / sg) : 0.f;
+        st->flat = sg > 0.0 ? 0 : 1;
+        st->lo_key = float_key(-4.f);   // below every correlation
+        st->n_surv = 0;
+        st->n_cand = 0;
+        st->n_topk = topk;
+        st->thr = -2.0;
+        st->thr_lo = -2.f;
+        st->best_idx = -1;
+        st->best_rho = 0.0;
+        st->overflow = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Exhaustive FP32 correlation map (brute force, Eq. rho1).
+// Tile: 16 output rows x 128 output columns, 256 threads, each thread 8
+// consecutive columns.  Template streamed in chunks of MT rows x NT columns.
+// ---------------------------------------------------------------------------
+constexpr int ZT_Y = 16, ZT_X = 128, ZT_MT = 32, ZT_NT = 128;
+constexpr int ZT_W = ZT_X + ZT_NT + 8;           // image tile row length (floats)
+constexpr int ZT_ROWS = ZT_Y + ZT_MT - 1;
+constexpr size_t ZT_SMEM = (size_t)(ZT_ROWS * ZT_W + ZT_MT * ZT_NT) * sizeof(float);
+
+__device__ inline int zncc_kacc(int m, int npad) {
+    return ZT_NT + m * ((npad + ZT_NT - 1) / ZT_NT) + 1;
+}
+
+__global__ void __launch_bounds__(256)
+zncc_map_kernel(const uint8_t *__restrict__ I, int p, int q, const float *__restrict__ tf,
+                int m, int n, int npad, const float *__restrict__ inv_sigma,
+                const float *__restrict__ efac, TmplState *st, float *map) {
+    extern __shared__ float4 zsm4[];
+    float *img = reinterpret_cast<float *>(zsm4);
+    float *tm = img + ZT_ROWS * ZT_W;
+    const int Ly = p - m + 1, Lx = q - n + 1;
+    const int y0 = blockIdx.y * ZT_Y, x0 = blockIdx.x * ZT_X;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    if (st->flat) return;
+    float acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+    for (int u0 = 0; u0 < m; u0 += ZT_MT) {
+        const int mt = min(ZT_MT, m - u0);
+        for (int v0 = 0; v0 < npad; v0 += ZT_NT) {
+            const int nt = min(ZT_NT, npad - v0);
+            __syncthreads();
+            for (int i = tid; i < ZT_MT * ZT_NT; i += 256) {
+                const int u = i / ZT_NT, v = i % ZT_NT;
+                tm[i] = (u < mt && v < nt) ? tf[(int64_t)(u0 + u) * npad + v0 + v] : 0.f;
+            }
+            const int rows = ZT_Y + mt - 1;
+            for (int i = tid; i < rows * ZT_W; i += 256) {
+                const int r = i / ZT_W, c = i % ZT_W;
+                const int gy = y0 + u0 + r, gx = x0 + v0 + c;
+                float v = 0.f;
+                if (gy < p && gx < q) v = (float)I[(int64_t)gy * q + gx] - 128.f;
+                img[i] = v;
+            }
+            __syncthreads();
+            for (int u = 0; u < mt; ++u) {
+                const float *row = img + (ty + u) * ZT_W + tx * 8;
+                const float *trow = tm + u * ZT_NT;
+                float racc[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) racc[k] = 0.f;
+                for (int v = 0; v < nt; v += 8) {
+                    float w[16], tv[8];
+                    const float4 *r4 = reinterpret_cast<const float4 *>(row + v);
+                    const float4 *t4 = reinterpret_cast<const float4 *>(trow + v);
+                    float4 a = r4[0], b = r4[1], c = r4[2], d = r4[3];
+                    float4 e = t4[0], f = t4[1];
+                    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+                    w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+                    w[8] = c.x; w[9] = c.y; w[10] = c.z; w[11] = c.w;
+                    w[12] = d.x; w[13] = d.y; w[14] = d.z; w[15] = d.w;
+                    tv[0] = e.x; tv[1] = e.y; tv[2] = e.z; tv[3] = e.w;
+                    tv[4] = f.x; tv[5] = f.y; tv[6] = f.z; tv[7] = f.w;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) racc[k] = fmaf(tv[j], w[k + j], racc[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) acc[k] += racc[k];
+            }
+        }
+    }
+    const int y = y0 + ty;
+    const int kacc = zncc_kacc(m, npad);
+    float lo = -3.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int x = x0 + tx * 8 + k;
+        if (y < Ly && x < Lx) {
+            const int64_t i = (int64_t)y * Lx + x;
+            const float is = inv_sigma[i];
+            const float rho = (acc[k] * st->inv_sigma) * is;
+            map[i] = rho;
+            const float eps = is > 0.f ? eps_bound(kacc, efac[i]) : 0.f;
+            lo = fmaxf(lo, rho - eps);
+        }
+    }
+    lo = warp_max_f(lo);
+    if ((tid & 31) == 0 && lo > -2.5f) atomicMax(&st->lo_key, float_key(lo));
+}
+
+// Warp-aggregated append of flagged items to list[base...]; returns nothing.
+__device__ inline void warp_append(bool flag, int value, int *counter, int *list, int cap,
+                                   int *overflow) {
+    const unsigned mask = __ballot_sync(0xffffffffu, flag);
+    if (mask == 0) return;
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(counter, __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (flag) {
+        const int pos = base + __popc(mask & ((1u << lane) - 1u));
+        if (pos < cap) list[pos] = value;
+        else atomicOr(overflow, 1);
+    }
+}
+
+__global__ void map_candidates_kernel(const float *__restrict__ map, const float *__restrict__ efac,
+                                      int64_t L, int kacc, TmplState *st, int *cand, int cap) {
+    if (st->flat) return;
+    const float lstar = key_float(st->lo_key);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < L; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        bool f = false;
+        if (i < L) {
+            const float ef = efac[i];
+            const float eps = ef > 0.f ? eps_bound(kacc, ef) : 0.f;
+            f = map[i] + eps >= lstar;
+        }
+        warp_append(f, (int)i, &st->n_cand, cand, cap, &st->overflow);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 recomputation of Eq. rho1 at candidate locations (two passes, as the
+// definition reads).  One block per candidate.
+// mode 0: candidates [0, n_topk)   mode 1: [n_topk, n_cand)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+refine64_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__restrict__ td,
+                int m, int n, TmplState *st, const int *__restrict__ cand, double *cand_rho,
+                int mode, int cap) {
+    __shared__ double sh[32];
+    if (st->flat) return;
+    int from, to;
+    if (mode == 0) { from = 0; to = min(st->n_topk, cap); }
+    else { from = st->n_topk; to = min(st->n_cand, cap); }
+    const int mn = m * n;
+    for (int c = from + blockIdx.x; c < to; c += gridDim.x) {
+        const int idx = cand[c];
+        const int y = idx / Lx, x = idx % Lx;
+        long long si = 0;
+        for (int i = threadIdx.x; i < mn; i += blockDim.x)
+            si += I[(int64_t)(y + i / n) * q + x + (i % n)];
+        const double S = block_sum_d((double)si, sh);
+        const double mu = S / (double)mn;
+        double num = 0.0, vv = 0.0;
+        for (int i = threadIdx.x; i < mn; i += blockDim.x) {
+            const double d = (double)I[(int64_t)(y + i / n) * q + x + (i % n)] - mu;
+            num += td[i] * d;
+            vv += d * d;
+        }
+        num = block_sum_d(num, sh);
+        vv = block_sum_d(vv, sh);
+        if (threadIdx.x == 0)
+            cand_rho[c] = (vv == 0.0 || st->sigma == 0.0) ? 0.0 : num / (sqrt(vv) * st->sigma);
+    }
+}
+
+// Argmax of (rho64, -index) over all candidates; one block.
+__global__ void __launch_bounds__(256)
+final_argmax_kernel(TmplState *st, const int *__restrict__ cand,
+                    const double *__restrict__ cand_rho, int cap) {
+    __shared__ double sv[256];
+    __shared__ int si[256];
+    const int nc = min(st->n_cand, cap);
+    double bv = -3.0;
+    int bi = 0x7fffffff;
+    if (!st->flat) {
+        for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+            const double v = cand_rho[c];
+            const int i = cand[c];
+            if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+        }
+    }
+    sv[threadIdx.x] = bv; si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            const double v = sv[threadIdx.x + o];
+            const int i = si[threadIdx.x + o];
+            if (v > sv[threadIdx.x] || (v == sv[threadIdx.x] && i < si[threadIdx.x])) {
+                sv[threadIdx.x] = v; si[threadIdx.x] = i;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (st->flat || nc == 0) { st->best_idx = 0; st->best_rho = 0.0; }
+        else { st->best_idx = si[0]; st->best_rho = sv[0]; }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Scan 1 (Section 6): rho(t, pivot block) at every group centre, FP32.
+// Tile of 4 x 32 centres, one thread per centre; template in chunks of
+// 16 x 64; pivot tile (P - 128) in shared memory.
+// ---------------------------------------------------------------------------
+constexpr int CT_Y = 4, CT_X = 32, CT_MT = 16, CT_NT = 64;
+
+__device__ inline int centre_kacc(int m, int npad) {
+    return CT_NT + m * ((npad + CT_NT - 1) / CT_NT) + 1;
+}
+
+__global__ void __launch_bounds__(128)
+centre_rho_kernel(const uint8_t *__restrict__ P, int p, int q, const float *__restrict__ tf,
+                  int m, int n, int npad, int h, int Ly, int Lx,
+                  const float *__restrict__ c_inv_sigma, const float *__restrict__ c_efac,
+                  TmplState *st, float *rho_tc, float *e_tc, int tile_w) {
+    extern __shared__ float4 csm4[];
+    float *tile = reinterpret_cast<float *>(csm4);
+    const int tile_rows = (CT_Y - 1) * h + CT_MT;
+    float *tm = tile + tile_rows * tile_w;
+    const int Gy = groups_along(Ly, h), Gx = groups_along(Lx, h);
+    const int gy0 = blockIdx.y * CT_Y, gx0 = blockIdx.x * CT_X;
+    const int ty = threadIdx.x / CT_X, tx = threadIdx.x % CT_X;
+    if (st->flat) return;
+    const int cy0 = group_centre_of(gy0, Ly, h), cx0 = group_centre_of(gx0, Lx, h);
+    const int gy = gy0 + ty, gx = gx0 + tx;
+    const bool valid = gy < Gy && gx < Gx;
+    const int oy = valid ? group_centre_of(gy, Ly, h) - cy0 : 0;
+    const int ox = valid ? group_centre_of(gx, Lx, h) - cx0 : 0;
+    float acc = 0.f;
+    for (int u0 = 0; u0 < m; u0 += CT_MT) {
+        const int mt = min(CT_MT, m - u0);
+        for (int v0 = 0; v0 < npad; v0 += CT_NT) {
+            const int nt = min(CT_NT, npad - v0);
+            __syncthreads();
+            for (int i = threadIdx.x; i < CT_MT * CT_NT; i += blockDim.x) {
+                const int u = i / CT_NT, v = i % CT_NT;
+                tm[i] = (u < mt && v < nt) ? tf[(int64_t)(u0 + u) * npad + v0 + v] : 0.f;
+            }
+            for (int i = threadIdx.x; i < tile_rows * tile_w; i += blockDim.x) {
+                const int r = i / tile_w, c = i % tile_w;
+                const int yy = cy0 + u0 + r, xx = cx0 + v0 + c;
+                tile[i] = (yy < p && xx < q) ? (float)P[(int64_t)yy * q + xx] - 128.f : 0.f;
+            }
+            __syncthreads();
+            if (valid) {
+                for (int u = 0; u < mt; ++u) {
+                    const float *row = tile + (oy + u) * tile_w + ox;
+                    const float *trow = tm + u * CT_NT;
+                    float racc = 0.f;
+                    for (int v = 0; v < nt; v += 4) {
+                        const float4 tv = *reinterpret_cast<const float4 *>(trow + v);
+                        racc = fmaf(tv.x, row[v], racc);
+                        racc = fmaf(tv.y, row[v + 1], racc);
+                        racc = fmaf(tv.z, row[v + 2], racc);
+                        racc = fmaf(tv.w, row[v + 3], racc);
+                    }
+                    acc += racc;
+                }
+            }
+        }
+    }
+    if (valid) {
+        const int g = gy * Gx + gx;
+        const float is = c_inv_sigma[g];
+        const float r = (acc * st->inv_sigma) * is;
+        rho_tc[g] = r;
+        e_tc[g] = is > 0.f ? eps_bound(centre_kacc(m, npad), c_efac[g]) : 0.f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Threshold centres: approximate top-k of rho_tc (any k achieved values give a
+// valid threshold; Section 6 uses the single best centre).
+// ---------------------------------------------------------------------------
+constexpr int TOPK_PER_THREAD = 4;
+constexpr int TOPK_MAX = kTopkMax;
+
+__device__ inline void block_topk(float *sv, int *si, int n, int k, float *out_v, int *out_i) {
+    // k rounds of block argmax over sv[0..n); chosen entries are set to -inf.
+    __shared__ float rv[32];
+    __shared__ int rp[32];
+    for (int r = 0; r < k; ++r) {
+        float bv = -INFINITY; int bp = -1;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            if (sv[j] > bv || (sv[j] == bv && bp >= 0 && si[j] < si[bp])) { bv = sv[j]; bp = j; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+            if (ov > bv || (ov == bv && op >= 0 && (bp < 0 || si[op] < si[bp]))) { bv = ov; bp = op; }
+        }
+        if ((threadIdx.x & 31) == 0) { rv[threadIdx.x >> 5] = bv; rp[threadIdx.x >> 5] = bp; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float b = -INFINITY; int pp = -1;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                if (rp[w] >= 0 && (rv[w] > b || (rv[w] == b && (pp < 0 || si[rp[w]] < si[pp])))) { b = rv[w]; pp = rp[w]; }
+            out_v[r] = b;
+            out_i[r] = pp >= 0 ? si[pp] : -1;
+            if (pp >= 0) sv[pp] = -INFINITY;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256)
+topk_stage1_kernel(const float *__restrict__ rho_tc, int G, int k, float *tmp_v, int *tmp_i,
+                   TmplState *st) {
+    __shared__ float sv[256 * TOPK_PER_THREAD];
+    __shared__ int si[256 * TOPK_PER_THREAD];
+    if (st->flat) return;
+    float v[TOPK_PER_THREAD];
+    int ix[TOPK_PER_THREAD];
+#pragma unroll
+    for (int j = 0; j < TOPK_PER_THREAD; ++j) { v[j] = -INFINITY; ix[j] = -1; }
+    const int chunk = (G + gridDim.x - 1) / gridDim.x;
+    const int g0 = blockIdx.x * chunk, g1 = min(G, g0 + chunk);
+    for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+        float x = rho_tc[g];
+        int xi = g;
+        if (x > v[TOPK_PER_THREAD - 1]) {
+#pragma unroll
+            for (int j = 0; j < TOPK_PER_THREAD; ++j) {
+                if (x > v[j]) { float tv = v[j]; int ti = ix[j]; v[j] = x; ix[j] = xi; x = tv; xi = ti; }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < TOPK_PER_THREAD; ++j) {
+        sv[threadIdx.x * TOPK_PER_THREAD + j] = ix[j] >= 0 ? v[j] : -INFINITY;
+        si[threadIdx.x * TOPK_PER_THREAD + j] = ix[j] >= 0 ? ix[j] : 0x7fffffff;
+    }
+    __syncthreads();
+    __shared__ float ov[TOPK_MAX];
+    __shared__ int oi[TOPK_MAX];
+    block_topk(sv, si, 256 * TOPK_PER_THREAD, k, ov, oi);
+    if (threadIdx.x < k) {
+        tmp_v[blockIdx.x * TOPK_MAX + threadIdx.x] = ov[threadIdx.x];
+        tmp_i[blockIdx.x * TOPK_MAX + threadIdx.x] = oi[threadIdx.x];
+    }
+}
+
+__global__ void __launch_bounds__(256)
+topk_stage2_kernel(const float *__restrict__ tmp_v, const int *__restrict__ tmp_i, int nb, int k,
+                   int Gx, int h, int Ly, int Lx, TmplState *st, int *cand) {
+    extern __shared__ float t2sm[];
+    float *sv = t2sm;
+    int *si = reinterpret_cast<int *>(t2sm + nb * k);
+    if (st->flat) return;
+    for (int j = threadIdx.x; j < nb * k; j += blockDim.x) {
+        const int b = j / k, r = j % k;
+        const int gi = tmp_i[b * TOPK_MAX + r];
+        sv[j] = gi >= 0 ? tmp_v[b * TOPK_MAX + r] : -INFINITY;
+        si[j] = gi >= 0 ? gi : 0x7fffffff;
+    }
+    __syncthreads();
+    __shared__ float ov[TOPK_MAX];
+    __shared__ int oi[TOPK_MAX];
+    block_topk(sv, si, nb * k, k, ov, oi);
+    if (threadIdx.x == 0) {
+        int cnt = 0;
+        for (int r = 0; r < k; ++r) {
+            const int g = oi[r];
+            if (g < 0 || g == 0x7fffffff) continue;
+            const int gy = g / Gx, gx = g % Gx;
+            const int cy = group_centre_of(gy, Ly, h), cx = group_centre_of(gx, Lx, h);
+            cand[cnt++] = cy * Lx + cx;
+        }
+        st->n_topk = cnt;
+        st->n_cand = cnt;
+    }
+}
+
+// thr = max exact rho over the threshold centres; thr_lo = float below thr - 1e-9.
+__global__ void threshold_kernel(TmplState *st, const double *__restrict__ cand_rho) {
+    if (threadIdx.x != 0 || st->flat) return;
+    double thr = -2.0;
+    for (int c = 0; c < st->n_topk; ++c) thr = fmax(thr, cand_rho[c]);
+    st->thr = thr;
+    const float lo = __double2float_rd(thr - 1e-9);
+    st->thr_lo = lo;
+    st->lo_key = max(st->lo_key, float_key(lo));
+}
+
+// ---------------------------------------------------------------------------
+// Scan 2: interval-safe transitive bound (Eq. tranEqq in angle form) and
+// warp-ballot compaction of the locations that fail Eq. SEC.
+// ---------------------------------------------------------------------------
+constexpr float kEcoBound = 1e-6f;    // |rho_co fp32 - exact| (exact integer sums, FP32 finish)
+constexpr float kAngMargin = 2e-6f;   // acosf / subtraction rounding, radians
+constexpr float kCosMargin = 2e-6f;   // cosf rounding
+
+__device__ inline float safe_upper_bound(float r_tc, float e_tc, float r_co) {
+    const float tlo = acosf(fminf(1.f, r_tc + e_tc)) - kAngMargin;
+    const float thi = acosf(fmaxf(-1.f, r_tc - e_tc)) + kAngMargin;
+    const float clo = acosf(fminf(1.f, r_co + kEcoBound)) - kAngMargin;
+    const float chi = acosf(fmaxf(-1.f, r_co - kEcoBound)) + kAngMargin;
+    const float gap = fmaxf(0.f, fmaxf(tlo - chi, clo - thi));
+    return cosf(gap) + kCosMargin;
+}
+
+__global__ void __launch_bounds__(256)
+bound_compact_kernel(const float *__restrict__ rho_tc, const float *__restrict__ e_tc,
+                     const float *__restrict__ rho_co, int Ly, int Lx, int h, TmplState *st,
+                     int *surv, float *ub_map, uint8_t *surv_map, int cap) {
+    if (st->flat) return;
+    const int Gx = groups_along(Lx, h);
+    const float thr = st->thr_lo;
+    const int64_t L = (int64_t)Ly * Lx;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < L; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        bool f = false;
+        if (i < L) {
+            const int y = (int)(i / Lx), x = (int)(i % Lx);
+            const int g = (y / h) * Gx + (x / h);
+            const float ub = safe_upper_bound(rho_tc[g], e_tc[g], rho_co[i]);
+            f = ub >= thr;
+            if (ub_map) ub_map[i] = ub;
+            if (surv_map) surv_map[i] = f ? 1 : 0;
+        }
+        warp_append(f, (int)i, &st->n_surv, surv, cap, &st->overflow);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Exact-ish rho (FP32, per-window centring v = I - rint(mu_o)) at the survivors;
+// one warp per survivor, template in shared memory when it fits.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+survivors_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__restrict__ IIS,
+                 const double *__restrict__ IIQ, const float *__restrict__ tf, int m, int n,
+                 int npad, const float *__restrict__ inv_sigma, TmplState *st,
+                 const int *__restrict__ surv, float *surv_rho, float *surv_eps, int cap,
+                 int tmpl_in_smem) {
+    extern __shared__ float4 ssm4[];
+    float *tsm = reinterpret_cast<float *>(ssm4);
+    if (st->flat) return;
+    const float *tm = tf;
+    if (tmpl_in_smem) {
+        for (int i = threadIdx.x; i < m * npad; i += blockDim.x) tsm[i] = tf[i];
+        __syncthreads();
+        tm = tsm;
+    }
+    const int ns = min(st->n_surv, cap);
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int64_t q1 = q + 1;
+    const double mn = (double)m * n;
+    const float ist = st->inv_sigma;
+    const int kacc = (n + 31) / 32 + m + 6;
+    for (int s = warp; s < ns; s += nwarps) {
+        const int idx = surv[s];
+        const int y = idx / Lx, x = idx % Lx;
+        const double S = IIS[(int64_t)(y + m) * q1 + x + n] - IIS[(int64_t)y * q1 + x + n]
+                       - IIS[(int64_t)(y + m) * q1 + x] + IIS[(int64_t)y * q1 + x];
+        const double Q = IIQ[(int64_t)(y + m) * q1 + x + n] - IIQ[(int64_t)y * q1 + x + n]
+                       - IIQ[(int64_t)(y + m) * q1 + x] + IIQ[(int64_t)y * q1 + x];
+        const float a = (float)rint(S / mn);
+        float acc = 0.f;
+        const uint8_t *base = I + (int64_t)y * q + x;
+        for (int u = 0; u < m; ++u) {
+            const uint8_t *row = base + (int64_t)u * q;
+            const float *trow = tm + u * npad;
+            float racc = 0.f;
+            for (int v = lane; v < n; v += 32) racc = fmaf(trow[v], (float)row[v] - a, racc);
+            acc += racc;
+        }
+        acc = warp_sum_f(acc);
+        if (lane == 0) {
+            const float is = inv_sigma[idx];
+            const float rho = (acc * ist) * is;
+            float eps = 0.f;
+            if (is > 0.f) {
+                const double var = mn * Q - S * S;
+                const double da = (double)a;
+                const double c2 = Q - 2.0 * da * S + mn * da * da;   // sum (I - a)^2
+                eps = eps_bound(kacc, (float)sqrt(mn * c2 / var));
+            }
+            surv_rho[s] = rho;
+            surv_eps[s] = eps;
+            atomicMax(&st->lo_key, float_key(rho - eps));
+        }
+    }
+}
+
+__global__ void surv_candidates_kernel(TmplState *st, const int *__restrict__ surv,
+                                       const float *__restrict__ surv_rho,
+                                       const float *__restrict__ surv_eps, int *cand, int cap) {
+    if (st->flat) return;
+    const float lstar = key_float(st->lo_key);
+    const int ns = min(st->n_surv, cap);
+    for (int base = blockIdx.x * blockDim.x; base < ns; base += gridDim.x * blockDim.x) {
+        const int s = base + threadIdx.x;
+        bool f = false;
+        if (s < ns) f = surv_rho[s] + surv_eps[s] >= lstar;
+        warp_append(f, s < ns ? surv[s] : 0, &st->n_cand, cand, cap, &st->overflow);
+    }
+}
+
+}  // namespace
+
+static int grid_cap(int64_t n, int threads, int per_sm) {
+    int64_t b = (n + threads - 1) / threads;
+    const int64_t cap = (int64_t)num_sms() * per_sm;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+cudaError_t launch_tmpl_prep(const float *t, int64_t ld, int m, int n, int npad, float *tf,
+                             double *td, TmplState *st, int topk, cudaStream_t s) {
+    tmpl_prep_kernel<<<1, 1024, 0, s>>>(t, ld, m, n, npad, tf, td, st, topk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zncc_map(const uint8_t *I, int p, int q, const float *tf, int m, int n,
+                            int npad, const float *inv_sigma, const float *efac128,
+                            TmplState *st, float *map, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(zncc_map_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZT_SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int Ly = p - m + 1, Lx = q - n + 1;
+    dim3 grid((Lx + ZT_X - 1) / ZT_X, (Ly + ZT_Y - 1) / ZT_Y);
+    zncc_map_kernel<<<grid, 256, ZT_SMEM, s>>>(I, p, q, tf, m, n, npad, inv_sigma, efac128, st, map);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_map_candidates(const float *map, const float *efac128, int64_t L, int m,
+                                  int n, TmplState *st, int *cand, int cap, cudaStream_t s) {
+    const int npad = (n + 7) & ~7;
+    const int kacc = ZT_NT + m * ((npad + ZT_NT - 1) / ZT_NT) + 1;
+    map_candidates_kernel<<<grid_cap(L, 256, 8), 256, 0, s>>>(map, efac128, L, kacc, st, cand, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine64(const uint8_t *I, int q, int Lx, const double *td, int m, int n,
+                            TmplState *st, const int *cand, double *cand_rho, int cap,
+                            bool topk_range, cudaStream_t s) {
+    refine64_kernel<<<num_sms() * 2, 256, 0, s>>>(I, q, Lx, td, m, n, st, cand, cand_rho,
+                                                   topk_range ? 0 : 1, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_final_argmax(TmplState *st, const int *cand, const double *cand_rho, int cap,
+                                cudaStream_t s) {
+    final_argmax_kernel<<<1, 256, 0, s>>>(st, cand, cand_rho, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_centre_rho(const uint8_t *P, int p, int q, const float *tf, int m, int n,
+                              int npad, int h, int Ly, int Lx, const float *c_inv_sigma,
+                              const float *c_efac, TmplState *st, float *rho_tc, float *e_tc,
+                              cudaStream_t s) {
+    const int Gy = groups_along(Ly, h), Gx = groups_along(Lx, h);
+    const int tile_w = ((CT_X - 1) * h + CT_NT + 3) & ~3;
+    const int tile_rows = (CT_Y - 1) * h + CT_MT;
+    const size_t smem = (size_t)(tile_rows * tile_w + CT_MT * CT_NT) * sizeof(float);
+    static size_t attr = 0;
+    if (smem > attr) {
+        cudaError_t e = cudaFuncSetAttribute(centre_rho_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = smem;
+    }
+    dim3 grid((Gx + CT_X - 1) / CT_X, (Gy + CT_Y - 1) / CT_Y);
+    centre_rho_kernel<<<grid, CT_Y * CT_X, smem, s>>>(P, p, q, tf, m, n, npad, h, Ly, Lx,
+                                                     c_inv_sigma, c_efac, st, rho_tc, e_tc, tile_w);
+    return cudaGetLastError();
+}
+
+int topk_blocks(int G) {
+    int nb = (G + 4095) / 4096;
+    if (nb > 256) nb = 256;
+    if (nb < 1) nb = 1;
+    return nb;
+}
+
+cudaError_t launch_topk(const float *rho_tc, int Gy, int Gx, int h, int Ly, int Lx, int k,
+                        TmplState *st, float *tmp_val, int *tmp_idx, int *cand, cudaStream_t s) {
+    const int G = Gy * Gx;
+    if (k > TOPK_MAX) k = TOPK_MAX;
+    if (k < 1) k = 1;
+    const int nb = topk_blocks(G);
+    topk_stage1_kernel<<<nb, 256, 0, s>>>(rho_tc, G, k, tmp_val, tmp_idx, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)nb * k * (sizeof(float) + sizeof(int));
+    topk_stage2_kernel<<<1, 256, smem, s>>>(tmp_val, tmp_idx, nb, k, Gx, h, Ly, Lx, st, cand);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_threshold(TmplState *st, const double *cand_rho, cudaStream_t s) {
+    threshold_kernel<<<1, 32, 0, s>>>(st, cand_rho);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bound_compact(const float *rho_tc, const float *e_tc, const float *rho_co,
+                                 int Ly, int Lx, int h, TmplState *st, int *surv, int cap,
+                                 float *ub_map, uint8_t *surv_map, cudaStream_t s) {
+    bound_compact_kernel<<<grid_cap((int64_t)Ly * Lx, 256, 8), 256, 0, s>>>(
+        rho_tc, e_tc, rho_co, Ly, Lx, h, st, surv, ub_map, surv_map, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_survivors(const uint8_t *I, int q, int Lx, const double *IIS,
+                             const double *IIQ, const float *tf, int m, int n, int npad,
+                             const float *inv_sigma, TmplState *st, const int *surv,
+                             float *surv_rho, float *surv_eps, int cap, cudaStream_t s) {
+    size_t smem = (size_t)m * npad * sizeof(float);
+    int in_smem = smem <= 200 * 1024;
+    if (!in_smem) smem = 0;
+    static size_t attr = 0;
+    if (smem > attr) {
+        cudaError_t e = cudaFuncSetAttribute(survivors_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = smem;
+    }
+    survivors_kernel<<<num_sms() * 4, 256, smem, s>>>(I, q, Lx, IIS, IIQ, tf, m, n, npad,
+                                                      inv_sigma, st, surv, surv_rho, surv_eps,
+                                                      cap, in_smem);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_surv_candidates(TmplState *st, const int *surv, const float *surv_rho,
+                                   const float *surv_eps, int *cand, int cap, cudaStream_t s) {
+    surv_candidates_kernel<<<num_sms() * 4, 256, 0, s>>>(st, surv, surv_rho, surv_eps, cand, cap);
+    return cudaGetLastError();
+}
+
+}  // namespace opta

@@ -1,0 +1,205 @@
+// Local statistics: FP64 integral images and per-window sum / sum of squares
+// (Algorithm 3's Run-Sum S, Q and Omega = sqrt(Q - S^2/mn); the "four
+// operations" per window of Section 3.1).
+//
+// The integral images hold integer values (pixels are integers in [0,255]),
+// so every entry is exact in FP64 up to 2^53; window sums taken from them are
+// exact, and mn*Q - S^2 is exact for mn <= 2^18.
+#include "common.cuh"
+
+namespace opta {
+
+namespace {
+
+constexpr int kRowThreads = 256;
+
+// Row pass: o_k[(y+1)*(q+1) + x+1] = sum_{j<=x} f_k(A[y][j], B[y][j]).
+__global__ void __launch_bounds__(kRowThreads)
+ii_rows_kernel(const uint8_t *__restrict__ A, const uint8_t *__restrict__ B, int p, int q,
+               double *o0, double *o1, double *o2) {
+    const int y = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int chunk = (q + kRowThreads - 1) / kRowThreads;
+    const int x0 = min(q, tid * chunk), x1 = min(q, x0 + chunk);
+    const uint8_t *a = A + (int64_t)y * q;
+    const uint8_t *b = B ? B + (int64_t)y * q : nullptr;
+    long long s0 = 0, s1 = 0, s2 = 0;
+    for (int x = x0; x < x1; ++x) {
+        const int v = a[x];
+        s0 += v;
+        s1 += v * v;
+        if (b) s2 += v * (int)b[x];
+    }
+    // exclusive block scan of (s0, s1, s2)
+    __shared__ long long sh[3][kRowThreads];
+    sh[0][tid] = s0; sh[1][tid] = s1; sh[2][tid] = s2;
+    __syncthreads();
+    for (int off = 1; off < kRowThreads; off <<= 1) {
+        long long v0 = 0, v1 = 0, v2 = 0;
+        if (tid >= off) { v0 = sh[0][tid - off]; v1 = sh[1][tid - off]; v2 = sh[2][tid - off]; }
+        __syncthreads();
+        sh[0][tid] += v0; sh[1][tid] += v1; sh[2][tid] += v2;
+        __syncthreads();
+    }
+    long long r0 = sh[0][tid] - s0, r1 = sh[1][tid] - s1, r2 = sh[2][tid] - s2;
+    const int64_t q1 = q + 1;
+    double *d0 = o0 + (int64_t)(y + 1) * q1;
+    double *d1 = o1 + (int64_t)(y + 1) * q1;
+    double *d2 = (b && o2) ? o2 + (int64_t)(y + 1) * q1 : nullptr;
+    if (tid == 0) { d0[0] = 0.0; d1[0] = 0.0; if (d2) d2[0] = 0.0; }
+    for (int x = x0; x < x1; ++x) {
+        const int v = a[x];
+        r0 += v; r1 += v * v;
+        d0[x + 1] = (double)r0;
+        d1[x + 1] = (double)r1;
+        if (d2) { r2 += v * (int)b[x]; d2[x + 1] = (double)r2; }
+    }
+}
+
+// Column pass over rows 1..p of up to three arrays, 32 columns x 32 row segments.
+__global__ void __launch_bounds__(1024)
+ii_cols_kernel(int p, int q, double *o0, double *o1, double *o2) {
+    const int64_t q1 = q + 1;
+    const int x = blockIdx.x * 32 + threadIdx.x;
+    const int seg = threadIdx.y;
+    const int seglen = (p + 31) / 32;
+    const int r0 = 1 + seg * seglen, r1 = min(p + 1, r0 + seglen);
+    double a0 = 0, a1 = 0, a2 = 0;
+    if (x < q1) {
+        for (int r = r0; r < r1; ++r) {
+            a0 += o0[r * q1 + x];
+            a1 += o1[r * q1 + x];
+            if (o2) a2 += o2[r * q1 + x];
+        }
+    }
+    __shared__ double sh[3][32][33];
+    sh[0][seg][threadIdx.x] = a0; sh[1][seg][threadIdx.x] = a1; sh[2][seg][threadIdx.x] = a2;
+    __syncthreads();
+    if (seg == 0) {
+        double c0 = 0, c1 = 0, c2 = 0;
+        for (int k = 0; k < 32; ++k) {
+            const double t0 = sh[0][k][threadIdx.x], t1 = sh[1][k][threadIdx.x], t2 = sh[2][k][threadIdx.x];
+            sh[0][k][threadIdx.x] = c0; sh[1][k][threadIdx.x] = c1; sh[2][k][threadIdx.x] = c2;
+            c0 += t0; c1 += t1; c2 += t2;
+        }
+    }
+    __syncthreads();
+    if (x >= q1) return;
+    double c0 = sh[0][seg][threadIdx.x], c1 = sh[1][seg][threadIdx.x], c2 = sh[2][seg][threadIdx.x];
+    for (int r = r0; r < r1; ++r) {
+        c0 += o0[r * q1 + x]; o0[r * q1 + x] = c0;
+        c1 += o1[r * q1 + x]; o1[r * q1 + x] = c1;
+        if (o2) { c2 += o2[r * q1 + x]; o2[r * q1 + x] = c2; }
+    }
+}
+
+__device__ inline double box(const double *II, int64_t q1, int y, int x, int m, int n) {
+    return II[(int64_t)(y + m) * q1 + x + n] - II[(int64_t)y * q1 + x + n]
+         - II[(int64_t)(y + m) * q1 + x] + II[(int64_t)y * q1 + x];
+}
+
+__global__ void window_stats_kernel(const double *__restrict__ IIS, const double *__restrict__ IIQ,
+                                    int q, int Ly, int Lx, int m, int n,
+                                    float *inv_sigma, float *efac128) {
+    const int64_t L = (int64_t)Ly * Lx;
+    const int64_t q1 = q + 1;
+    const double mn = (double)m * n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / Lx), x = (int)(i % Lx);
+        const double S = box(IIS, q1, y, x, m, n);
+        const double Q = box(IIQ, q1, y, x, m, n);
+        const double var = mn * Q - S * S;          // exact: mn * Omega^2
+        float inv = 0.f, ef = 0.f;
+        if (var > 0.0) {
+            inv = (float)sqrt(mn / var);
+            const double c2 = Q - 256.0 * S + 16384.0 * mn;   // sum (I - 128)^2
+            ef = (float)sqrt(mn * c2 / var);
+        }
+        inv_sigma[i] = inv;
+        if (efac128) efac128[i] = ef;
+    }
+}
+
+__global__ void ingest_f32_kernel(const float *__restrict__ src, int64_t ld, int p, int q,
+                                  uint8_t *dst, int *bad) {
+    const int64_t N = (int64_t)p * q;
+    int any = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / q), x = (int)(i % q);
+        const float v = src[(int64_t)y * ld + x];
+        if (!(v >= 0.f && v <= 255.f && v == rintf(v))) any = 1;
+        dst[i] = (uint8_t)fminf(fmaxf(rintf(v), 0.f), 255.f);
+    }
+    if (any) atomicOr(bad, 1);
+}
+
+__global__ void ingest_u8_kernel(const uint8_t *__restrict__ src, int64_t ld, int p, int q,
+                                 uint8_t *dst) {
+    const int64_t N = (int64_t)p * q;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / q), x = (int)(i % q);
+        dst[i] = src[(int64_t)y * ld + x];
+    }
+}
+
+}  // namespace
+
+int num_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 132;
+    }
+    return sms;
+}
+
+static int grid_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    const int64_t cap = (int64_t)num_sms() * 16;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+cudaError_t launch_integrals(const uint8_t *A, const uint8_t *B, int p, int q,
+                             double *o0, double *o1, double *o2, cudaStream_t s) {
+    const int64_t q1 = q + 1;
+    cudaError_t e;
+    // first row zero
+    if ((e = cudaMemsetAsync(o0, 0, q1 * sizeof(double), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(o1, 0, q1 * sizeof(double), s)) != cudaSuccess) return e;
+    if (B && o2 && (e = cudaMemsetAsync(o2, 0, q1 * sizeof(double), s)) != cudaSuccess) return e;
+    ii_rows_kernel<<<p, kRowThreads, 0, s>>>(A, B, p, q, o0, o1, (B ? o2 : nullptr));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    dim3 blk(32, 32);
+    ii_cols_kernel<<<(int)((q1 + 31) / 32), blk, 0, s>>>(p, q, o0, o1, (B ? o2 : nullptr));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_window_stats(const double *IIS, const double *IIQ, int p, int q,
+                                int m, int n, float *inv_sigma, float *efac128,
+                                cudaStream_t s) {
+    const int Ly = p - m + 1, Lx = q - n + 1;
+    window_stats_kernel<<<grid_for((int64_t)Ly * Lx, 256), 256, 0, s>>>(
+        IIS, IIQ, q, Ly, Lx, m, n, inv_sigma, efac128);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ingest_f32(const float *src, int64_t ld, int p, int q, uint8_t *dst,
+                              int *bad, cudaStream_t s) {
+    ingest_f32_kernel<<<grid_for((int64_t)p * q, 256), 256, 0, s>>>(src, ld, p, q, dst, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ingest_u8(const uint8_t *src, int64_t ld, int p, int q, uint8_t *dst,
+                             cudaStream_t s) {
+    ingest_u8_kernel<<<grid_for((int64_t)p * q, 256), 256, 0, s>>>(src, ld, p, q, dst);
+    return cudaGetLastError();
+}
+
+}  // namespace opta

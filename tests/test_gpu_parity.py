@@ -1,0 +1,205 @@
+"""GPU path vs the CPU FP64 oracle, through the C ABI (ctypes binding).
+
+Bar (from the method's statement): the returned location equals the oracle's
+argmax or has oracle rho within 1e-6 of the oracle maximum, and
+|rho_gpu - rho_oracle| <= 1e-5; the elimination test never drops a
+location whose oracle rho is at or above the maximum (full-map check).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import synth
+from oracle import ref
+
+RHO_TOL = 1e-5
+TIE_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def opta():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1407_3535_gb300 as m
+    m.lib()
+    return m
+
+
+def _check_best(res, rho_map, label=""):
+    """res: OptaResult; rho_map: oracle FP64 map."""
+    assert res.status == 0, (label, res.as_dict())
+    y, x, best = ref.argmax_first(rho_map)
+    got = rho_map[res.y, res.x]
+    assert (res.y, res.x) == (y, x) or got >= best - TIE_TOL, (label, res.as_dict(), (y, x, best))
+    assert abs(res.rho - got) <= RHO_TOL, (label, res.rho, got)
+    assert abs(res.rho - best) <= RHO_TOL + TIE_TOL, (label, res.rho, best)
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+# ---------------------------------------------------------------------------
+# Exhaustive search (zncc_full)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape,tshape,seed", [
+    ((256, 256), (16, 16), 1),      # the 256^2 / 16^2 workload
+    ((300, 257), (17, 23), 2),      # ragged tiles, n not a multiple of 8
+    ((150, 400), (33, 150), 3),     # template wider than one 128-column chunk
+    ((64, 64), (64, 64), 4),        # single location
+    ((40, 300), (1, 9), 5),         # one-row template
+])
+def test_zncc_full_map_and_best(opta, shape, tshape, seed):
+    img = synth.aerial_image(max(shape), n_octaves=6, n_prims=10, seed=seed)[:shape[0], :shape[1]].copy()
+    t = synth.make_templates(img, [tshape], seed=seed + 100, noise=4.0)[0].data
+    rho = ref.zncc_map(img, t)
+    L = rho.size
+    dmap = torch.empty(L, dtype=torch.float32, device="cuda")
+    res = opta.zncc_full(_cuda(img), _cuda(t), rho_map=dmap)
+    _check_best(res, rho, f"zncc {shape} {tshape}")
+    got = dmap.cpu().numpy().reshape(rho.shape).astype(np.float64)
+    assert np.max(np.abs(got - rho)) <= 1e-4
+
+
+def test_zncc_full_host_buffers_and_float_image(opta):
+    img = synth.white_blur_image(256, seed=1001)           # float32 holding integers
+    t = synth.make_templates(img, [16], seed=1101, noise=5.0)[0].data
+    rho = ref.zncc_map(img, t)
+    res = opta.zncc_full(img, t)                           # host numpy inputs
+    _check_best(res, rho, "zncc host")
+    res2 = opta.zncc_full(_cuda(img.astype(np.uint8)), _cuda(t))
+    assert (res2.y, res2.x, res2.rho) == (res.y, res.x, res.rho)
+
+
+def test_zncc_full_rejects_non_integer_float_image(opta):
+    img = synth.white_blur_image(64, seed=3) + 0.25
+    t = img[:8, :8].copy()
+    with pytest.raises(opta.OptaError) as e:
+        opta.zncc_full(img.astype(np.float32), t)
+    assert e.value.code == 7
+    with pytest.raises(opta.OptaError) as e:
+        opta.optA_prepare(img.astype(np.float32))
+    assert e.value.code == 7
+
+
+def test_flat_template_status(opta):
+    img = synth.white_blur_image(64, seed=3)
+    t = np.full((8, 8), 7.0, dtype=np.float32)
+    res = opta.zncc_full(img, t, check=False)
+    assert res.status == 2
+    h = opta.optA_prepare(img, opta.opta_params_default(fixed_h=3, blur=0))
+    (r,) = opta.optA_search(h, [t], check=False)
+    assert r.status == 2
+    h.close()
+
+
+def test_negative_affine_template(opta):
+    img = synth.aerial_image(200, n_octaves=6, n_prims=8, seed=9)
+    t = synth.make_templates(img, [24], seed=77, noise=2.0, gain=(-1.2, -0.8))[0].data
+    rho = ref.zncc_map(img, t)
+    _check_best(opta.zncc_full(_cuda(img), _cuda(t)), rho, "zncc negative")
+    h = opta.optA_prepare(_cuda(img), opta.opta_params_default(fixed_h=5, blur=0))
+    _check_best(opta.optA_search(h, [_cuda(t)])[0], rho, "opta negative")
+    h.close()
+
+
+# ---------------------------------------------------------------------------
+# Pruned search (optA_search): plain groups, no blur
+# ---------------------------------------------------------------------------
+def test_config1_plain_groups(opta):
+    img = synth.white_blur_image(256, seed=1001)
+    t = synth.make_templates(img, [16], seed=1101, noise=5.0)[0].data
+    rho = ref.zncc_map(img, t)
+    h = opta.optA_prepare(_cuda(img), opta.opta_params_default(fixed_h=3, blur=0), sizes=[(16, 16)])
+    (r,) = opta.optA_search(h, [_cuda(t)])
+    _check_best(r, rho, "config1")
+    assert r.group_h == 3 and r.n_survivors < r.n_locations
+    # full-map safety of the elimination test
+    L = rho.size
+    ub = torch.empty(L, dtype=torch.float32, device="cuda")
+    sv = torch.empty(L, dtype=torch.uint8, device="cuda")
+    opta.optA_debug_bounds(h, _cuda(t), ub, sv)
+    ub = ub.cpu().numpy().reshape(rho.shape)
+    sv = sv.cpu().numpy().reshape(rho.shape)
+    assert np.all(ub >= rho - 1e-6), float((rho - ub).max())
+    assert np.all(sv[rho >= rho.max() - TIE_TOL] == 1)
+    h.close()
+
+
+@pytest.mark.parametrize("hsz", [1, 3, 5, 7, 9])
+def test_fixed_group_sizes_many_templates(opta, hsz):
+    img = synth.aerial_image(320, n_octaves=7, n_prims=20, seed=31)
+    ts = synth.make_templates(img, [16, 24, (19, 29)], seed=500 + hsz, noise=3.0)
+    h = opta.optA_prepare(_cuda(img), opta.opta_params_default(fixed_h=hsz, blur=0))
+    res = opta.optA_search(h, [_cuda(t.data) for t in ts])
+    for t, r in zip(ts, res):
+        _check_best(r, ref.zncc_map(img, t.data), f"h={hsz} {t.data.shape}")
+        assert r.group_h == hsz
+    h.close()
+
+
+def test_flat_regions_and_truncated_groups(opta):
+    """Constant rectangles make flat windows and flat pivots; odd image sizes
+    make truncated edge groups."""
+    img = synth.aerial_image(203, n_octaves=6, n_prims=6, seed=41).astype(np.uint8)
+    img[20:90, 30:120] = 100
+    img[150:203, 0:60] = 7
+    ts = synth.make_templates(img, [(12, 12), (9, 14)], seed=42, noise=1.0)
+    ts.append(synth.Template(np.ascontiguousarray(img[25:37, 40:52].astype(np.float32) + np.float32(
+        np.random.default_rng(1).normal(0, 1.0, (12, 12)))), 25, 40, 1.0, 0.0, 1.0))
+    h = opta.optA_prepare(_cuda(img), opta.opta_params_default(fixed_h=7, blur=0))
+    for t in ts:
+        rho = ref.zncc_map(img, t.data)
+        (r,) = opta.optA_search(h, [_cuda(t.data)])
+        _check_best(r, rho, f"flat {t.data.shape}")
+        L = rho.size
+        ub = torch.empty(L, dtype=torch.float32, device="cuda")
+        opta.optA_debug_bounds(h, _cuda(t.data), ub, None)
+        assert np.all(ub.cpu().numpy().reshape(rho.shape) >= rho - 1e-6)
+    h.close()
+
+
+def test_template_equals_image(opta):
+    img = synth.white_blur_image(48, seed=5)
+    t = (img * 1.5 + 3).astype(np.float32)
+    h = opta.optA_prepare(img, opta.opta_params_default())
+    (r,) = opta.optA_search(h, [t])
+    assert (r.y, r.x) == (0, 0) and abs(r.rho - 1.0) <= 1e-9
+    h.close()
+
+
+# ---------------------------------------------------------------------------
+# Pruned search with the OptA preparation (blur levels + EGS)
+# ---------------------------------------------------------------------------
+def test_opta_blur_egs_many_sizes(opta):
+    img = synth.aerial_image(512, n_octaves=7, n_prims=40, seed=2002)
+    ts = synth.make_templates(img, [16, 32, 32, 48, (24, 40)], seed=2102, noise=3.0)
+    h = opta.optA_prepare(_cuda(img), opta.opta_params_default())
+    res = opta.optA_search(h, [_cuda(t.data) for t in ts])
+    for t, r in zip(ts, res):
+        rho = ref.zncc_map(img, t.data)
+        _check_best(r, rho, f"opta {t.data.shape}")
+        L = rho.size
+        ub = torch.empty(L, dtype=torch.float32, device="cuda")
+        sv = torch.empty(L, dtype=torch.uint8, device="cuda")
+        opta.optA_debug_bounds(h, _cuda(t.data), ub, sv)
+        ub = ub.cpu().numpy().reshape(rho.shape)
+        assert np.all(ub >= rho - 1e-6), float((rho - ub).max())
+        assert np.all(sv.cpu().numpy().reshape(rho.shape)[rho >= rho.max() - TIE_TOL] == 1)
+    info = opta.optA_size_info(h, 32, 32)
+    assert info["group_h"] in (1, 3, 5, 7, 9) and info["n_egs_evals"] >= 1
+    h.close()
+
+
+def test_search_is_deterministic(opta):
+    img = synth.aerial_image(384, n_octaves=7, n_prims=30, seed=7)
+    ts = synth.make_templates(img, [24, 32], seed=8, noise=3.0)
+    h = opta.optA_prepare(_cuda(img), opta.opta_params_default())
+    first = [r.as_dict() for r in opta.optA_search(h, [_cuda(t.data) for t in ts])]
+    for _ in range(4):
+        again = [r.as_dict() for r in opta.optA_search(h, [_cuda(t.data) for t in ts])]
+        for a, b in zip(first, again):
+            assert (a["y"], a["x"], a["rho"], a["n_survivors"]) == (b["y"], b["x"], b["rho"], b["n_survivors"])
+    h.close()
