@@ -1,0 +1,448 @@
+"""Benchmark of the OptA search on GB300 (one JSON line on stdout).
+
+Workload: the batched form -- one 4096 x 4096 uint8 remote-sensing-like
+image (1/f noise + 800 rectangles/lines, seed 2004) and 256 templates whose
+sizes are drawn uniformly from {16, 24, 32, 48, 64, 96, 128} (crops +
+affine intensity + N(0, 3^2) noise, seed 2104).
+
+One step = the whole hot path over that batch: optA_prepare (local
+statistics, blur levels, blur correlation, auto-correlation, EGS, for all
+seven template sizes) followed by optA_search of the 256 templates.
+metric: effective rho-locations/s = sum over templates of (p-m+1)(q-n+1)
+divided by the step time (device time, CUDA events, inputs resident in HBM,
+L2 flushed before every timed step).
+
+Beside it: e2e (the same metric through the C ABI with host buffers, the
+host->device copy of image and templates and the device->host read of the
+results inside the timed region), the exhaustive GPU search (zncc_full) on
+the same GPU, p50/p99 per-template query latency, the roofline of the
+dominant kernel, and the CPU FP64 oracle timed on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "batched-4096sq-256tmpl-uneven16to128"
+METRIC = "effective rho-locations/s per template at 4096^2 (whole batch)"
+UNIT = "locations/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--templates", type=int, default=256)
+    ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-brute", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(size: int, count: int):
+    if size == 4096:
+        img = synth.config_image(4)
+        ts = synth.config_templates(4, img, count=count)
+    else:
+        img = synth.aerial_image(size, n_octaves=max(3, int(np.log2(size)) - 3),
+                                 n_prims=max(4, 800 * size * size // 4096 ** 2), seed=2004)
+        ts = synth.make_templates(img, synth.batch_sizes(count, 2104), seed=2104, noise=3.0)
+    return img, ts
+
+
+def shard(items, rank, world):
+    """Templates are independent problems: rank r takes every world-th one."""
+    return items[rank::world]
+
+
+def n_locations(shape, ts):
+    p, q = shape
+    return int(sum((p - t.data.shape[0] + 1) * (q - t.data.shape[1] + 1) for t in ts))
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm / CPU baseline: the FP64 oracle on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_sample_rate(img, ts, seconds: float = 12.0, rows: int = 2):
+    """Time the oracle (as it stands) on bands of `rows` location rows of
+    successive templates until ~`seconds` of CPU work; returns (loc/s, cores, desc)."""
+    from oracle import ref
+    cores = ref.max_threads()
+    done_loc, t0, k = 0, time.perf_counter(), 0
+    used = []
+    while True:
+        t = ts[k % len(ts)].data
+        m, n = t.shape
+        y0 = (k * 37) % (img.shape[0] - m + 1 - rows)
+        band = img[y0:y0 + rows + m - 1, :]
+        ref.zncc_map(band, t)
+        done_loc += rows * (img.shape[1] - n + 1)
+        used.append(m)
+        k += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    desc = (f"FP64 oracle (direct Eq. rho1, C + OpenMP) on {k} bands of {rows} location rows "
+            f"x {img.shape[1]} columns, template sizes {sorted(set(used))}, {dt:.1f} s")
+    return done_loc / dt, cores, desc
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    img, ts = workload(args.size, args.templates)
+    for _ in range(args.warmup):
+        oracle_sample_rate(img, ts, seconds=2.0)
+    vals, cores, desc = [], 1, ""
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        v, cores, desc = oracle_sample_rate(img, ts, seconds=6.0)
+        vals.append(v)
+    wall = time.perf_counter() - t_all
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * wall / max(1, args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "bands of location rows"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GB300 arm
+# ---------------------------------------------------------------------------
+ALGO = {}   # kernel -> (kind, per-launch work function) filled in main
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_1407_3535_gb300 as opta
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    img, ts_all = workload(args.size, args.templates)
+    ts = shard(ts_all, rank, world)
+    sizes = sorted({t.data.shape for t in ts})
+    p, q = img.shape
+    L_step = n_locations(img.shape, ts)
+
+    stream = torch.cuda.current_stream()
+    dimg = torch.from_numpy(img).cuda()
+    dts = [torch.from_numpy(t.data).cuda() for t in ts]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    prm = opta.opta_params_default()
+
+    def step_device():
+        h = opta.optA_prepare(dimg, prm, sizes=sizes, stream=stream)
+        res = opta.optA_search(h, dts, stream=stream)
+        h.close()
+        return res
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (also checks every result)
+    results = None
+    for _ in range(args.warmup):
+        results = step_device()
+    assert all(r.status == 0 for r in results), [r.as_dict() for r in results if r.status]
+
+    # timed region: K steps, each bracketed by events; L2 flushed before each
+    launches0 = opta.opta_dbg_launch_count()
+    sampler = ClockSampler(torch.cuda.current_device())
+    barrier()
+    sampler.start()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step_device()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    barrier()
+    clocks = sampler.stop()
+    launches = (opta.opta_dbg_launch_count() - launches0) // max(1, args.steps)
+    ms = float(np.mean(times))
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        tot = torch.tensor([L_step], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tot)
+        L_all = float(tot.item())
+    else:
+        L_all = float(L_step)
+    value = L_all / (ms / 1000.0)
+
+    # search-only and prepare-only split (one extra step, not part of `value`)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e2 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h = opta.optA_prepare(dimg, prm, sizes=sizes, stream=stream)
+    e1.record(stream)
+    opta.optA_search(h, dts, stream=stream)
+    e2.record(stream)
+    e2.synchronize()
+    prep_ms, search_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    size_info = {f"{m}x{n}": opta.optA_size_info(h, m, n) for (m, n) in sizes}
+
+    # per-template query latency on the prepared handle (one template per call)
+    lat = []
+    for t in dts:
+        a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        opta.optA_search(h, [t], stream=stream)
+        b.record(stream)
+        b.synchronize()
+        lat.append(a.elapsed_time(b))
+    lat = np.array(lat)
+
+    # per-kernel device time of one search pass (CUDA events on the launch stream)
+    opta.opta_dbg_profile_read()
+    opta.opta_dbg_profile_enable(True)
+    res_prof = opta.optA_search(h, dts, stream=stream)
+    torch.cuda.synchronize()
+    opta.opta_dbg_profile_enable(False)
+    prof = opta.opta_dbg_profile_read()
+    h.close()
+
+    # end to end through the C ABI with host buffers
+    host_img = np.ascontiguousarray(img)
+    host_ts = [np.ascontiguousarray(t.data) for t in ts]
+    h2d = host_img.nbytes + sum(t.nbytes for t in host_ts)
+    d2h = 56 * len(host_ts)
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.zero_()
+        barrier()
+        t0 = time.perf_counter()
+        hh = opta.optA_prepare(host_img, prm, sizes=sizes, stream=stream)
+        opta.optA_search(hh, host_ts, stream=stream)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        hh.close()
+    e2e_value = L_all / float(np.mean(e2e_times)) if world == 1 else L_step / float(np.mean(e2e_times)) * world
+
+    # exhaustive GPU search on the same GPU (a sample of templates, one per size)
+    brute = None
+    if not args.no_brute:
+        by_size = {}
+        for t, d in zip(ts, dts):
+            by_size.setdefault(t.data.shape, d)
+        bt = []
+        bl = 0
+        for shp, d in by_size.items():
+            opta.zncc_full(dimg, d, stream=stream)           # warm
+            a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            a.record(stream)
+            opta.zncc_full(dimg, d, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            bt.append(a.elapsed_time(b))
+            bl += (p - shp[0] + 1) * (q - shp[1] + 1)
+        # same size mix as the batch: weight per-size rates by the batch composition
+        per_size = {shp: ((p - shp[0] + 1) * (q - shp[1] + 1)) / (ms_ / 1000.0)
+                    for shp, ms_ in zip(by_size.keys(), bt)}
+        tot_t = sum(((p - t.data.shape[0] + 1) * (q - t.data.shape[1] + 1)) / per_size[t.data.shape]
+                    for t in ts)
+        brute_rate = L_step / tot_t
+        brute = {"value": brute_rate, "unit": UNIT,
+                 "per_size_ms": {f"{s[0]}x{s[1]}": round(v, 3) for s, v in zip(by_size.keys(), bt)},
+                 "speedup_of_opta_search": (L_step / (search_ms / 1000.0)) / brute_rate,
+                 "speedup_of_opta_step": value / brute_rate if world == 1 else None}
+
+    roof = roofline(prof, ts, res_prof, size_info, img.shape, clocks)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, desc = oracle_sample_rate(img, ts_all, seconds=12.0)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    surv = [r.n_survivors / r.n_locations for r in res_prof]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "image": f"{p}x{q} uint8", "templates": len(ts_all),
+                   "template_sizes": "uniform over {16,24,32,48,64,96,128}",
+                   "step": "optA_prepare(7 sizes) + optA_search(256 templates)",
+                   "l2": "512 MiB buffer written before every timed step",
+                   "parallelism": f"templates sharded over {world} GPU(s)"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "roofline": roof,
+        "split_ms": {"prepare": prep_ms, "search": search_ms},
+        "search_only_value": L_step / (search_ms / 1000.0),
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "mean": float(lat.mean())},
+        "survivor_fraction": {"mean": float(np.mean(surv)), "max": float(np.max(surv))},
+        "brute_force": brute,
+        "kernels_ms": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
+        "group_sizes": {k: v["group_h"] for k, v in size_info.items()},
+        "blur_levels": {k: v["level"] for k, v in size_info.items()},
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def roofline(prof, ts, results, size_info, shape, clocks):
+    """Roofline of the kernel with the largest share of the search pass."""
+    if not prof:
+        return None
+    pk, src = peaks()
+    p, q = shape
+    name, (tot_ms, nl) = max(prof.items(), key=lambda kv: kv[1][0])
+    # algorithmic work per launch
+    flops = 0.0
+    bytes_ = 0.0
+    kind = "alu"
+    for t, r in zip(ts, results):
+        m, n = t.data.shape
+        Ly, Lx = p - m + 1, q - n + 1
+        h = r.group_h
+        G = ((Ly + h - 1) // h) * ((Lx + h - 1) // h)
+        if name == "survivors_kernel":
+            flops += 2.0 * m * n * r.n_survivors
+        elif name == "centre_rho_kernel":
+            flops += 2.0 * m * n * G
+        elif name == "bound_compact_kernel":
+            kind = "hbm"
+            bytes_ += 4.0 * Ly * Lx + 8.0 * G + 4.0 * r.n_survivors
+        elif name == "zncc_map_kernel":
+            flops += 2.0 * m * n * Ly * Lx
+    avg_s = (tot_ms / nl) / 1000.0
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    if kind == "hbm":
+        achieved = bytes_ / nl / avg_s / 1e9
+        peak = pk.get("hbm_gbs", 6800.0)
+        unit = "GB/s"
+        note = f"HBM copy bandwidth ({src})"
+    else:
+        achieved = flops / nl / avg_s / 1e12
+        # FP32 FMA pipe: 152 SMs x 128 lanes x 2 flops x max SM clock
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        unit = "TFLOP/s"
+        note = f"FP32 FMA peak from 152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz ({src} clock)"
+    return {"kernel": name, "bound": kind, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak if peak else None, "traffic": None,
+            "launches": nl, "avg_launch_ms": tot_ms / nl, "peak_source": note}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

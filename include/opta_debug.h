@@ -54,6 +54,20 @@ opta_status optA_debug_maps(opta_handle *h, int32_t m, int32_t n,
                             uint8_t *pivot_dev, float *rho_co_dev,
                             float *sigma_map_host, void *stream);
 
+/* Number of kernel launches the library has issued in this process. */
+uint64_t opta_dbg_launch_count(void);
+
+/* Enable (1) or disable (0) per-kernel timing: every later launch is
+ * bracketed by a CUDA event pair recorded on its stream. */
+void opta_dbg_profile_enable(int32_t on);
+
+/* Read and clear the timings recorded so far (waits for their events).
+ * Writes up to `capacity` entries: kernel name (NUL-terminated, at most
+ * name_stride bytes each, into `names`), total milliseconds and launch
+ * count.  Returns the number of distinct kernels recorded. */
+int32_t opta_dbg_profile_read(char *names, int32_t name_stride, double *total_ms,
+                              int64_t *launches, int32_t capacity);
+
 #ifdef __cplusplus
 }
 #endif

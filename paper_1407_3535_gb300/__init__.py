@@ -18,7 +18,8 @@ __all__ = [
     "OptaError", "opta_params_default", "optA_prepare", "optA_search", "zncc_full",
     "optA_debug_bounds", "optA_size_info", "optA_memory_bytes", "optA_destroy",
     "optA_debug_maps", "opta_dbg_window_stats", "opta_dbg_blur", "opta_dbg_blur_corr",
-    "opta_dbg_rho_co", "Handle", "lib",
+    "opta_dbg_rho_co", "opta_dbg_launch_count", "opta_dbg_profile_enable",
+    "opta_dbg_profile_read", "Handle", "lib",
 ]
 
 lib = _lib.lib
@@ -261,3 +262,26 @@ def opta_dbg_rho_co(P_dev, I_dev, m: int, n: int, h: int, rco_dev=None, rho_cut:
                                  m, n, h, c_void_p(rco_dev.data_ptr() if rco_dev is not None else 0),
                                  c_double(rho_cut), byref(cnt), _stream(stream)), "opta_dbg_rho_co")
     return int(cnt.value)
+
+
+def opta_dbg_launch_count() -> int:
+    """Kernel launches issued by the library so far in this process."""
+    return int(lib().opta_dbg_launch_count())
+
+
+def opta_dbg_profile_enable(on: bool = True) -> None:
+    lib().opta_dbg_profile_enable(1 if on else 0)
+
+
+def opta_dbg_profile_read(capacity: int = 64) -> dict:
+    """{kernel_name: (total_ms, launches)} recorded since the last read."""
+    stride = 64
+    names = ctypes.create_string_buffer(stride * capacity)
+    tot = (c_double * capacity)()
+    cnt = (c_int64 * capacity)()
+    n = lib().opta_dbg_profile_read(names, stride, tot, cnt, capacity)
+    out = {}
+    for i in range(min(n, capacity)):
+        nm = names.raw[i * stride:(i + 1) * stride].split(b"\0", 1)[0].decode()
+        out[nm] = (float(tot[i]), int(cnt[i]))
+    return out

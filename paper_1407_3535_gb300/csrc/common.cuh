@@ -133,6 +133,21 @@ cudaError_t launch_centre_stats(const double *PS, const double *PQ, int p, int q
 
 int num_sms();
 int topk_blocks(int G);
+
+// Counts every kernel launch of the library and, when per-kernel timing is
+// enabled (opta_dbg_profile_enable), brackets it with CUDA events on its stream.
+class LaunchScope {
+  public:
+    LaunchScope(const char *name, cudaStream_t s);
+    ~LaunchScope();
+    LaunchScope(const LaunchScope &) = delete;
+    LaunchScope &operator=(const LaunchScope &) = delete;
+
+  private:
+    const char *name_;
+    cudaStream_t s_;
+    void *a_ = nullptr;
+};
 constexpr int kTopkMax = 16;   // largest supported params.topk
 
 }  // namespace opta

@@ -288,6 +288,7 @@ cudaError_t launch_rho_co_h(const uint8_t *P, const uint8_t *I, int p, int q, in
         attr = smem;
     }
     dim3 grid(strips, bands);
+    LaunchScope ls_rho_co_kernel("rho_co_kernel", s);
     rho_co_kernel<H><<<grid, threads, smem, s>>>(P, I, p, q, m, n, Ly, Lx, IIS, IIQ, PS, PQ,
                                                  GXS, GYB, ring_w, cut, rco, count);
     return cudaGetLastError();
@@ -315,6 +316,7 @@ cudaError_t launch_blur(const uint8_t *I, int p, int q, const uint8_t *level_map
         if (e != cudaSuccess) return e;
         attr = smem;
     }
+    LaunchScope ls_blur_kernel("blur_kernel", s);
     blur_kernel<<<dim3(bq, bp), 256, smem, s>>>(I, p, q, level_map, block, weights, radius, P);
     return cudaGetLastError();
 }
@@ -323,6 +325,7 @@ cudaError_t launch_blur_corr(const double *IIS, const double *IIQ, const double 
                              const double *PQ, const double *PX, int p, int q, int m, int n,
                              float lambda, int block, int *fail, float *R, cudaStream_t s) {
     const int Ly = p - m + 1, Lx = q - n + 1;
+    LaunchScope ls_blur_corr_kernel("blur_corr_kernel", s);
     blur_corr_kernel<<<grid_for((int64_t)Ly * Lx, 256), 256, 0, s>>>(
         IIS, IIQ, PS, PQ, PX, q, Ly, Lx, m, n, lambda, block, fail, R);
     return cudaGetLastError();
@@ -346,6 +349,7 @@ cudaError_t launch_centre_stats(const double *PS, const double *PQ, int p, int q
                                 int h, int Ly, int Lx, float *c_inv_sigma, float *c_efac,
                                 cudaStream_t s) {
     const int64_t G = (int64_t)groups_along(Ly, h) * groups_along(Lx, h);
+    LaunchScope ls_centre_stats_kernel("centre_stats_kernel", s);
     centre_stats_kernel<<<grid_for(G, 256), 256, 0, s>>>(PS, PQ, q, m, n, h, Ly, Lx,
                                                          c_inv_sigma, c_efac);
     return cudaGetLastError();

@@ -604,6 +604,7 @@ static int grid_cap(int64_t n, int threads, int per_sm) {
 
 cudaError_t launch_tmpl_prep(const float *t, int64_t ld, int m, int n, int npad, float *tf,
                              double *td, TmplState *st, int topk, cudaStream_t s) {
+    LaunchScope ls_tmpl_prep_kernel("tmpl_prep_kernel", s);
     tmpl_prep_kernel<<<1, 1024, 0, s>>>(t, ld, m, n, npad, tf, td, st, topk);
     return cudaGetLastError();
 }
@@ -620,6 +621,7 @@ cudaError_t launch_zncc_map(const uint8_t *I, int p, int q, const float *tf, int
     }
     const int Ly = p - m + 1, Lx = q - n + 1;
     dim3 grid((Lx + ZT_X - 1) / ZT_X, (Ly + ZT_Y - 1) / ZT_Y);
+    LaunchScope ls_zncc_map_kernel("zncc_map_kernel", s);
     zncc_map_kernel<<<grid, 256, ZT_SMEM, s>>>(I, p, q, tf, m, n, npad, inv_sigma, efac128, st, map);
     return cudaGetLastError();
 }
@@ -628,6 +630,7 @@ cudaError_t launch_map_candidates(const float *map, const float *efac128, int64_
                                   int n, TmplState *st, int *cand, int cap, cudaStream_t s) {
     const int npad = (n + 7) & ~7;
     const int kacc = ZT_NT + m * ((npad + ZT_NT - 1) / ZT_NT) + 1;
+    LaunchScope ls_map_candidates_kernel("map_candidates_kernel", s);
     map_candidates_kernel<<<grid_cap(L, 256, 8), 256, 0, s>>>(map, efac128, L, kacc, st, cand, cap);
     return cudaGetLastError();
 }
@@ -635,6 +638,7 @@ cudaError_t launch_map_candidates(const float *map, const float *efac128, int64_
 cudaError_t launch_refine64(const uint8_t *I, int q, int Lx, const double *td, int m, int n,
                             TmplState *st, const int *cand, double *cand_rho, int cap,
                             bool topk_range, cudaStream_t s) {
+    LaunchScope ls_refine64_kernel("refine64_kernel", s);
     refine64_kernel<<<num_sms() * 2, 256, 0, s>>>(I, q, Lx, td, m, n, st, cand, cand_rho,
                                                    topk_range ? 0 : 1, cap);
     return cudaGetLastError();
@@ -642,6 +646,7 @@ cudaError_t launch_refine64(const uint8_t *I, int q, int Lx, const double *td, i
 
 cudaError_t launch_final_argmax(TmplState *st, const int *cand, const double *cand_rho, int cap,
                                 cudaStream_t s) {
+    LaunchScope ls_final_argmax_kernel("final_argmax_kernel", s);
     final_argmax_kernel<<<1, 256, 0, s>>>(st, cand, cand_rho, cap);
     return cudaGetLastError();
 }
@@ -662,6 +667,7 @@ cudaError_t launch_centre_rho(const uint8_t *P, int p, int q, const float *tf, i
         attr = smem;
     }
     dim3 grid((Gx + CT_X - 1) / CT_X, (Gy + CT_Y - 1) / CT_Y);
+    LaunchScope ls_centre_rho_kernel("centre_rho_kernel", s);
     centre_rho_kernel<<<grid, CT_Y * CT_X, smem, s>>>(P, p, q, tf, m, n, npad, h, Ly, Lx,
                                                      c_inv_sigma, c_efac, st, rho_tc, e_tc, tile_w);
     return cudaGetLastError();
@@ -680,15 +686,22 @@ cudaError_t launch_topk(const float *rho_tc, int Gy, int Gx, int h, int Ly, int 
     if (k > TOPK_MAX) k = TOPK_MAX;
     if (k < 1) k = 1;
     const int nb = topk_blocks(G);
-    topk_stage1_kernel<<<nb, 256, 0, s>>>(rho_tc, G, k, tmp_val, tmp_idx, st);
+    {
+        LaunchScope ls("topk_stage1_kernel", s);
+        topk_stage1_kernel<<<nb, 256, 0, s>>>(rho_tc, G, k, tmp_val, tmp_idx, st);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = (size_t)nb * k * (sizeof(float) + sizeof(int));
-    topk_stage2_kernel<<<1, 256, smem, s>>>(tmp_val, tmp_idx, nb, k, Gx, h, Ly, Lx, st, cand);
+    {
+        LaunchScope ls("topk_stage2_kernel", s);
+        topk_stage2_kernel<<<1, 256, smem, s>>>(tmp_val, tmp_idx, nb, k, Gx, h, Ly, Lx, st, cand);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_threshold(TmplState *st, const double *cand_rho, cudaStream_t s) {
+    LaunchScope ls_threshold_kernel("threshold_kernel", s);
     threshold_kernel<<<1, 32, 0, s>>>(st, cand_rho);
     return cudaGetLastError();
 }
@@ -696,6 +709,7 @@ cudaError_t launch_threshold(TmplState *st, const double *cand_rho, cudaStream_t
 cudaError_t launch_bound_compact(const float *rho_tc, const float *e_tc, const float *rho_co,
                                  int Ly, int Lx, int h, TmplState *st, int *surv, int cap,
                                  float *ub_map, uint8_t *surv_map, cudaStream_t s) {
+    LaunchScope ls_bound_compact_kernel("bound_compact_kernel", s);
     bound_compact_kernel<<<grid_cap((int64_t)Ly * Lx, 256, 8), 256, 0, s>>>(
         rho_tc, e_tc, rho_co, Ly, Lx, h, st, surv, ub_map, surv_map, cap);
     return cudaGetLastError();
@@ -715,6 +729,7 @@ cudaError_t launch_survivors(const uint8_t *I, int q, int Lx, const double *IIS,
         if (e != cudaSuccess) return e;
         attr = smem;
     }
+    LaunchScope ls_survivors_kernel("survivors_kernel", s);
     survivors_kernel<<<num_sms() * 4, 256, smem, s>>>(I, q, Lx, IIS, IIQ, tf, m, n, npad,
                                                       inv_sigma, st, surv, surv_rho, surv_eps,
                                                       cap, in_smem);
@@ -723,6 +738,7 @@ cudaError_t launch_survivors(const uint8_t *I, int q, int Lx, const double *IIS,
 
 cudaError_t launch_surv_candidates(TmplState *st, const int *surv, const float *surv_rho,
                                    const float *surv_eps, int *cand, int cap, cudaStream_t s) {
+    LaunchScope ls_surv_candidates_kernel("surv_candidates_kernel", s);
     surv_candidates_kernel<<<num_sms() * 4, 256, 0, s>>>(st, surv, surv_rho, surv_eps, cand, cap);
     return cudaGetLastError();
 }

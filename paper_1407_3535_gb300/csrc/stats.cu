@@ -174,10 +174,15 @@ cudaError_t launch_integrals(const uint8_t *A, const uint8_t *B, int p, int q,
     if ((e = cudaMemsetAsync(o0, 0, q1 * sizeof(double), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(o1, 0, q1 * sizeof(double), s)) != cudaSuccess) return e;
     if (B && o2 && (e = cudaMemsetAsync(o2, 0, q1 * sizeof(double), s)) != cudaSuccess) return e;
-    ii_rows_kernel<<<p, kRowThreads, 0, s>>>(A, B, p, q, o0, o1, (B ? o2 : nullptr));
+    {
+        LaunchScope ls("ii_rows_kernel", s);
+        ii_rows_kernel<<<p, kRowThreads, 0, s>>>(A, B, p, q, o0, o1, (B ? o2 : nullptr));
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    dim3 blk(32, 32);
-    ii_cols_kernel<<<(int)((q1 + 31) / 32), blk, 0, s>>>(p, q, o0, o1, (B ? o2 : nullptr));
+    {
+        LaunchScope ls("ii_cols_kernel", s);
+        ii_cols_kernel<<<(int)((q1 + 31) / 32), dim3(32, 32), 0, s>>>(p, q, o0, o1, (B ? o2 : nullptr));
+    }
     return cudaGetLastError();
 }
 
@@ -185,6 +190,7 @@ cudaError_t launch_window_stats(const double *IIS, const double *IIQ, int p, int
                                 int m, int n, float *inv_sigma, float *efac128,
                                 cudaStream_t s) {
     const int Ly = p - m + 1, Lx = q - n + 1;
+    LaunchScope ls_window_stats_kernel("window_stats_kernel", s);
     window_stats_kernel<<<grid_for((int64_t)Ly * Lx, 256), 256, 0, s>>>(
         IIS, IIQ, q, Ly, Lx, m, n, inv_sigma, efac128);
     return cudaGetLastError();
@@ -192,12 +198,14 @@ cudaError_t launch_window_stats(const double *IIS, const double *IIQ, int p, int
 
 cudaError_t launch_ingest_f32(const float *src, int64_t ld, int p, int q, uint8_t *dst,
                               int *bad, cudaStream_t s) {
+    LaunchScope ls_ingest_f32_kernel("ingest_f32_kernel", s);
     ingest_f32_kernel<<<grid_for((int64_t)p * q, 256), 256, 0, s>>>(src, ld, p, q, dst, bad);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ingest_u8(const uint8_t *src, int64_t ld, int p, int q, uint8_t *dst,
                              cudaStream_t s) {
+    LaunchScope ls_ingest_u8_kernel("ingest_u8_kernel", s);
     ingest_u8_kernel<<<grid_for((int64_t)p * q, 256), 256, 0, s>>>(src, ld, p, q, dst);
     return cudaGetLastError();
 }
