@@ -23,6 +23,7 @@ dominant kernel, and the CPU FP64 oracle timed on a bounded sample.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import subprocess
@@ -308,7 +309,7 @@ def main():
     host_img = np.ascontiguousarray(img)
     host_ts = [np.ascontiguousarray(t.data) for t in ts]
     h2d = host_img.nbytes + sum(t.nbytes for t in host_ts)
-    d2h = 56 * len(host_ts)
+    d2h = ctypes.sizeof(opta.OptaResult) * len(host_ts)
     e2e_times = []
     for _ in range(max(1, min(args.steps, 3))):
         flush.zero_()
@@ -358,6 +359,7 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
 
     surv = [r.n_survivors / r.n_locations for r in res_prof]
+    evald = [r.n_evaluated / r.n_locations for r in res_prof]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -378,6 +380,10 @@ def main():
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "mean": float(lat.mean())},
         "survivor_fraction": {"mean": float(np.mean(surv)), "max": float(np.max(surv))},
+        "evaluated_fraction": {"mean": float(np.mean(evald)), "max": float(np.max(evald))},
+        "threshold_vs_best": {"mean_thr": float(np.mean([r.rho_threshold for r in res_prof])),
+                              "mean_best": float(np.mean([r.rho for r in res_prof])),
+                              "min_best": float(np.min([r.rho for r in res_prof]))},
         "brute_force": brute,
         "kernels_ms": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
         "group_sizes": {k: v["group_h"] for k, v in size_info.items()},

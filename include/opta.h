@@ -86,6 +86,9 @@ typedef struct opta_result {
     int64_t n_centres;     /* group centres matched (scan 1, Section 6) */
     int64_t n_survivors;   /* locations that failed the elimination test */
     int64_t n_candidates;  /* locations recomputed in FP64 for the final argmax */
+    int64_t n_evaluated;   /* survivors whose rho was computed; the others were
+                              skipped once the running threshold passed their bound */
+    double rho_threshold;  /* scan-1 threshold (max exact rho over the threshold centres) */
     int32_t group_h;       /* group side h (1 for zncc_full) */
     int32_t status;        /* opta_status of this template */
 } opta_result;
@@ -101,7 +104,7 @@ typedef struct opta_params {
     int32_t h_max;          /* 9: largest group side tried by EGS (odd) */
     int32_t fixed_h;        /* 0: EGS chooses h; odd h > 0: fixed group side */
     int32_t blur;           /* 1: run the OptA level loop; 0: unblurred pivots */
-    int32_t topk;           /* 8: centres re-evaluated on I for the threshold (1..32) */
+    int32_t topk;           /* 8: centres re-evaluated on I for the threshold (1..16) */
     int32_t precision;      /* 0: FP32 CUDA-core products (only mode implemented) */
     int32_t reserved[7];
 } opta_params;
@@ -155,8 +158,9 @@ opta_status optA_search(opta_handle *h, const opta_template *t, int32_t n_t,
                         opta_result *out, void *stream);
 
 /*
- * Exhaustive search: rho at all locations and its argmax (Eq. rho1).  Any
- * float32 or uint8 image.  `rho_map` (nullable) is a DEVICE buffer of
+ * Exhaustive search: rho at all locations and its argmax (Eq. rho1).  Same
+ * image domain as optA_prepare (integers in [0, 255]; OPTA_ERR_UNSUPPORTED
+ * otherwise).  `rho_map` (nullable) is a DEVICE buffer of
  * (p-m+1)(q-n+1) floats that receives the FP32 rho map; `best` (host)
  * receives the FP64-refined best match.  Allocates its scratch with
  * stream-ordered allocation and frees it before returning.  Synchronises.

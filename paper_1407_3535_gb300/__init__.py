@@ -19,7 +19,7 @@ __all__ = [
     "optA_debug_bounds", "optA_size_info", "optA_memory_bytes", "optA_destroy",
     "optA_debug_maps", "opta_dbg_window_stats", "opta_dbg_blur", "opta_dbg_blur_corr",
     "opta_dbg_rho_co", "opta_dbg_launch_count", "opta_dbg_profile_enable",
-    "opta_dbg_profile_read", "Handle", "lib",
+    "opta_dbg_profile_read", "Handle", "lib", "OptaResult",
 ]
 
 lib = _lib.lib

@@ -33,7 +33,8 @@ class OptaTemplate(ctypes.Structure):
 class OptaResult(ctypes.Structure):
     _fields_ = [("y", c_int32), ("x", c_int32), ("rho", c_double),
                 ("n_locations", c_int64), ("n_centres", c_int64), ("n_survivors", c_int64),
-                ("n_candidates", c_int64), ("group_h", c_int32), ("status", c_int32)]
+                ("n_candidates", c_int64), ("n_evaluated", c_int64), ("rho_threshold", c_double),
+                ("group_h", c_int32), ("status", c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

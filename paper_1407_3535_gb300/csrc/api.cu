@@ -81,7 +81,8 @@ struct opta_handle {
     size_t capL = 0, capG = 0, capT = 0, capN = 0;
     float *rho_tc = nullptr, *e_tc = nullptr;
     int *surv = nullptr;
-    float *surv_rho = nullptr, *surv_eps = nullptr;
+    float *surv_rho = nullptr, *surv_eps = nullptr, *surv_ub = nullptr, *ubbuf = nullptr;
+    int *bucket_cnt = nullptr, *bucket_cur = nullptr;
     int *cand = nullptr;
     double *cand_rho = nullptr;
     float *topk_v = nullptr;
@@ -398,6 +399,8 @@ opta_status ensure_scratch(opta_handle *H, size_t L, size_t G, size_t T, size_t 
         TRY(grow(H, H->surv, dummy, H->capL, L));
         TRY(grow(H, H->surv_rho, dummy, H->capL, L));
         TRY(grow(H, H->surv_eps, dummy, H->capL, L));
+        TRY(grow(H, H->surv_ub, dummy, H->capL, L));
+        TRY(grow(H, H->ubbuf, dummy, H->capL, L));
         TRY(grow(H, H->cand, dummy, H->capL + kTopkMax, L + kTopkMax));
         TRY(grow(H, H->cand_rho, dummy, H->capL + kTopkMax, L + kTopkMax));
         H->capL = L;
@@ -410,6 +413,8 @@ opta_status ensure_scratch(opta_handle *H, size_t L, size_t G, size_t T, size_t 
     if (!H->topk_v) {
         TRY(H->mem.alloc(&H->topk_v, 256 * kTopkMax));
         TRY(H->mem.alloc(&H->topk_i, 256 * kTopkMax));
+        TRY(H->mem.alloc(&H->bucket_cnt, kUbBuckets));
+        TRY(H->mem.alloc(&H->bucket_cur, kUbBuckets));
     }
     if (T > H->capT) {
         TRY(grow(H, H->tf, dummy, H->capT, T));
@@ -454,9 +459,10 @@ opta_status enqueue_search(opta_handle *H, const opta_template *t, TmplState *st
                        capL + kTopkMax, true, s));
     CK(launch_threshold(st, H->cand_rho, s));
     CK(launch_bound_compact(H->rho_tc, H->e_tc, S->rho_co, S->Ly, S->Lx, S->h, st, H->surv,
-                            capL, ub_map, surv_map, s));
+                            H->surv_ub, capL, ub_map ? ub_map : H->ubbuf, surv_map,
+                            H->bucket_cnt, H->bucket_cur, s));
     CK(launch_survivors(H->I8, H->q, S->Lx, H->IIS, H->IIQ, H->tf, m, n, npad, S->inv_sigma, st,
-                        H->surv, H->surv_rho, H->surv_eps, capL, s));
+                        H->surv, H->surv_ub, H->surv_rho, H->surv_eps, capL, s));
     CK(launch_surv_candidates(st, H->surv, H->surv_rho, H->surv_eps, H->cand,
                               capL + kTopkMax, s));
     CK(launch_refine64(H->I8, H->q, S->Lx, H->td, m, n, st, H->cand, H->cand_rho,
@@ -473,6 +479,8 @@ void fill_result(const TmplState &st, const SizeState *S, int Lx, int64_t L, int
     r->n_centres = n_centres;
     r->n_survivors = st.n_surv;
     r->n_candidates = st.n_cand;
+    r->n_evaluated = st.n_eval;
+    r->rho_threshold = st.thr;
     if (st.flat) {
         r->y = 0; r->x = 0; r->rho = 0.0;
         r->status = OPTA_ERR_FLAT_TEMPLATE;
@@ -554,6 +562,7 @@ opta_status optA_destroy(opta_handle *h) {
         delete S;
     }
     void *ptrs[] = {h->I8, h->IIS, h->IIQ, h->rho_tc, h->e_tc, h->surv, h->surv_rho, h->surv_eps,
+                    h->surv_ub, h->ubbuf, h->bucket_cnt, h->bucket_cur,
                     h->cand, h->cand_rho, h->topk_v, h->topk_i, h->tf, h->tstage, h->td,
                     h->states, h->weights, h->radius};
     for (void *p : ptrs) if (p) cudaFree(p);
@@ -755,6 +764,7 @@ opta_status zncc_full(const opta_image *img, const opta_template *t, float *rho_
     ZCK(cudaStreamSynchronize(s));
     fill_result(hs, nullptr, Lx, L, 1, L, best);
     best->n_survivors = L;
+    best->n_evaluated = L;
     return finish((opta_status)best->status);
 #undef ZCK
 }

@@ -50,8 +50,12 @@ struct TmplState {
     int best_idx;             // final argmax (linear location index)
     double best_rho;          // final rho (FP64)
     int overflow;             // candidate buffer overflowed (status)
-    int pad_;
+    int n_eval;               // survivors evaluated (not skipped by the running threshold)
 };
+
+// Survivors are bucketed by their upper bound (bucket 0 = highest) so that
+// they are evaluated roughly in decreasing bound order.
+constexpr int kUbBuckets = 32;
 
 // ---------------------------------------------------------------------------
 // Launchers (stream-ordered, return cudaError_t of the launch).
@@ -101,13 +105,17 @@ cudaError_t launch_topk(const float *rho_tc, int Gy, int Gx, int h, int Ly, int 
                         TmplState *st, float *tmp_val, int *tmp_idx, int *cand,
                         cudaStream_t s);
 cudaError_t launch_threshold(TmplState *st, const double *cand_rho, cudaStream_t s);
+// Scan 2: upper bound of every location into ub (L floats), bucket histogram of
+// the survivors, then compaction of the survivors in bucket order.
 cudaError_t launch_bound_compact(const float *rho_tc, const float *e_tc, const float *rho_co,
-                                 int Ly, int Lx, int h, TmplState *st, int *surv, int cap,
-                                 float *ub_map, uint8_t *surv_map, cudaStream_t s);
+                                 int Ly, int Lx, int h, TmplState *st, int *surv, float *surv_ub,
+                                 int cap, float *ub, uint8_t *surv_map, int *bucket_cnt,
+                                 int *bucket_cur, cudaStream_t s);
 cudaError_t launch_survivors(const uint8_t *I, int q, int Lx, const double *IIS,
                              const double *IIQ, const float *tf, int m, int n, int npad,
                              const float *inv_sigma, TmplState *st, const int *surv,
-                             float *surv_rho, float *surv_eps, int cap, cudaStream_t s);
+                             const float *surv_ub, float *surv_rho, float *surv_eps, int cap,
+                             cudaStream_t s);
 cudaError_t launch_surv_candidates(TmplState *st, const int *surv, const float *surv_rho,
                                    const float *surv_eps, int *cand, int cap,
                                    cudaStream_t s);

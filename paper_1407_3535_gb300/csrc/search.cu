@@ -91,6 +91,7 @@ tmpl_prep_kernel(const float *__restrict__ t, int64_t ld, int m, int n, int npad
         st->best_idx = -1;
         st->best_rho = 0.0;
         st->overflow = 0;
+        st->n_eval = 0;
     }
 }
 
@@ -492,27 +493,74 @@ __device__ inline float safe_upper_bound(float r_tc, float e_tc, float r_co) {
     return cosf(gap) + kCosMargin;
 }
 
+__device__ inline int ub_bucket(float ub, float thr) {
+    const float span = 1.f - thr;
+    if (ub >= 1.f || span <= 0.f) return 0;
+    int b = (int)((1.f - ub) / span * (float)kUbBuckets);
+    return b < 0 ? 0 : (b >= kUbBuckets ? kUbBuckets - 1 : b);
+}
+
+// Pass 1: bound of every location (stored), survivor histogram by bucket.
 __global__ void __launch_bounds__(256)
-bound_compact_kernel(const float *__restrict__ rho_tc, const float *__restrict__ e_tc,
-                     const float *__restrict__ rho_co, int Ly, int Lx, int h, TmplState *st,
-                     int *surv, float *ub_map, uint8_t *surv_map, int cap) {
+bound_hist_kernel(const float *__restrict__ rho_tc, const float *__restrict__ e_tc,
+                  const float *__restrict__ rho_co, int Ly, int Lx, int h, TmplState *st,
+                  float *ub_out, uint8_t *surv_map, int *bucket_cnt) {
+    __shared__ int hist[kUbBuckets];
     if (st->flat) return;
+    for (int i = threadIdx.x; i < kUbBuckets; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
     const int Gx = groups_along(Lx, h);
     const float thr = st->thr_lo;
     const int64_t L = (int64_t)Ly * Lx;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / Lx), x = (int)(i % Lx);
+        const int g = (y / h) * Gx + (x / h);
+        const float ub = safe_upper_bound(rho_tc[g], e_tc[g], rho_co[i]);
+        ub_out[i] = ub;
+        const bool f = ub >= thr;
+        if (surv_map) surv_map[i] = f ? 1 : 0;
+        if (f) atomicAdd(&hist[ub_bucket(ub, thr)], 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kUbBuckets; i += blockDim.x)
+        if (hist[i]) atomicAdd(&bucket_cnt[i], hist[i]);
+}
+
+// Exclusive scan of the bucket counts into write cursors; total survivors.
+__global__ void bucket_scan_kernel(TmplState *st, const int *__restrict__ bucket_cnt,
+                                   int *bucket_cur) {
+    if (threadIdx.x != 0 || st->flat) return;
+    int acc = 0;
+    for (int b = 0; b < kUbBuckets; ++b) { bucket_cur[b] = acc; acc += bucket_cnt[b]; }
+    st->n_surv = acc;
+}
+
+// Pass 2: scatter the survivors into their bucket ranges (bucket 0 first).
+__global__ void __launch_bounds__(256)
+bound_scatter_kernel(const float *__restrict__ ub_in, int64_t L, TmplState *st, int *surv,
+                     float *surv_ub, int cap, int *bucket_cur) {
+    if (st->flat) return;
+    const float thr = st->thr_lo;
+    const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < L; base += stride) {
         const int64_t i = base + threadIdx.x;
-        bool f = false;
-        if (i < L) {
-            const int y = (int)(i / Lx), x = (int)(i % Lx);
-            const int g = (y / h) * Gx + (x / h);
-            const float ub = safe_upper_bound(rho_tc[g], e_tc[g], rho_co[i]);
-            f = ub >= thr;
-            if (ub_map) ub_map[i] = ub;
-            if (surv_map) surv_map[i] = f ? 1 : 0;
+        const float ub = i < L ? ub_in[i] : -4.f;
+        const bool f = ub >= thr;
+        const int b = f ? ub_bucket(ub, thr) : -1;
+        const unsigned act = __ballot_sync(0xffffffffu, f);
+        if (!act) continue;
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        if (f) {
+            const int leader = __ffs(peers) - 1;
+            int pos = 0;
+            if (lane == leader) pos = atomicAdd(&bucket_cur[b], __popc(peers));
+            pos = __shfl_sync(peers, pos, leader);
+            pos += __popc(peers & ((1u << lane) - 1u));
+            if (pos < cap) { surv[pos] = (int)i; surv_ub[pos] = ub; }
+            else atomicOr(&st->overflow, 1);
         }
-        warp_append(f, (int)i, &st->n_surv, surv, cap, &st->overflow);
     }
 }
 
@@ -524,8 +572,8 @@ __global__ void __launch_bounds__(256)
 survivors_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__restrict__ IIS,
                  const double *__restrict__ IIQ, const float *__restrict__ tf, int m, int n,
                  int npad, const float *__restrict__ inv_sigma, TmplState *st,
-                 const int *__restrict__ surv, float *surv_rho, float *surv_eps, int cap,
-                 int tmpl_in_smem) {
+                 const int *__restrict__ surv, const float *__restrict__ surv_ub, float *surv_rho,
+                 float *surv_eps, int cap, int tmpl_in_smem) {
     extern __shared__ float4 ssm4[];
     float *tsm = reinterpret_cast<float *>(ssm4);
     if (st->flat) return;
@@ -541,9 +589,23 @@ survivors_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__r
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int64_t q1 = q + 1;
     const double mn = (double)m * n;
+    const int mnI = m * n;
     const float ist = st->inv_sigma;
-    const int kacc = (n + 31) / 32 + m + 6;
+    const int kacc = (mnI + 31) / 32 + 6;
+    // lane start (u, v) in the flattened window and the per-step advance of 32 elements
+    const int du = 32 / n, dv = 32 % n;
+    const int u0 = lane / n, v0 = lane % n;
+    volatile unsigned int *lo_key = &st->lo_key;
+    int evaluated = 0;
     for (int s = warp; s < ns; s += nwarps) {
+        // running threshold: a location whose bound is below a certain lower bound
+        // of the maximum cannot be the best match
+        float lim = key_float(*lo_key);
+        lim = __shfl_sync(0xffffffffu, lim, 0);
+        if (surv_ub[s] < lim) {
+            if (lane == 0) { surv_rho[s] = -3.f; surv_eps[s] = 0.f; }
+            continue;
+        }
         const int idx = surv[s];
         const int y = idx / Lx, x = idx % Lx;
         const double S = IIS[(int64_t)(y + m) * q1 + x + n] - IIS[(int64_t)y * q1 + x + n]
@@ -551,16 +613,23 @@ survivors_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__r
         const double Q = IIQ[(int64_t)(y + m) * q1 + x + n] - IIQ[(int64_t)y * q1 + x + n]
                        - IIQ[(int64_t)(y + m) * q1 + x] + IIQ[(int64_t)y * q1 + x];
         const float a = (float)rint(S / mn);
-        float acc = 0.f;
         const uint8_t *base = I + (int64_t)y * q + x;
-        for (int u = 0; u < m; ++u) {
-            const uint8_t *row = base + (int64_t)u * q;
-            const float *trow = tm + u * npad;
-            float racc = 0.f;
-            for (int v = lane; v < n; v += 32) racc = fmaf(trow[v], (float)row[v] - a, racc);
-            acc += racc;
+        float acc0 = 0.f, acc1 = 0.f;
+        int u = u0, v = v0;
+        int e = lane;
+        // two independent chains over the flattened window, 32 lanes wide
+        for (; e + 32 < mnI; e += 64) {
+            const float t0 = tm[u * npad + v];
+            const float i0 = (float)base[(int64_t)u * q + v];
+            u += du; v += dv; if (v >= n) { v -= n; ++u; }
+            const float t1 = tm[u * npad + v];
+            const float i1 = (float)base[(int64_t)u * q + v];
+            u += du; v += dv; if (v >= n) { v -= n; ++u; }
+            acc0 = fmaf(t0, i0 - a, acc0);
+            acc1 = fmaf(t1, i1 - a, acc1);
         }
-        acc = warp_sum_f(acc);
+        if (e < mnI) acc0 = fmaf(tm[u * npad + v], (float)base[(int64_t)u * q + v] - a, acc0);
+        float acc = warp_sum_f(acc0 + acc1);
         if (lane == 0) {
             const float is = inv_sigma[idx];
             const float rho = (acc * ist) * is;
@@ -574,8 +643,10 @@ survivors_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__r
             surv_rho[s] = rho;
             surv_eps[s] = eps;
             atomicMax(&st->lo_key, float_key(rho - eps));
+            ++evaluated;
         }
     }
+    if (lane == 0 && evaluated) atomicAdd(&st->n_eval, evaluated);
 }
 
 __global__ void surv_candidates_kernel(TmplState *st, const int *__restrict__ surv,
@@ -707,18 +778,36 @@ cudaError_t launch_threshold(TmplState *st, const double *cand_rho, cudaStream_t
 }
 
 cudaError_t launch_bound_compact(const float *rho_tc, const float *e_tc, const float *rho_co,
-                                 int Ly, int Lx, int h, TmplState *st, int *surv, int cap,
-                                 float *ub_map, uint8_t *surv_map, cudaStream_t s) {
-    LaunchScope ls_bound_compact_kernel("bound_compact_kernel", s);
-    bound_compact_kernel<<<grid_cap((int64_t)Ly * Lx, 256, 8), 256, 0, s>>>(
-        rho_tc, e_tc, rho_co, Ly, Lx, h, st, surv, ub_map, surv_map, cap);
+                                 int Ly, int Lx, int h, TmplState *st, int *surv, float *surv_ub,
+                                 int cap, float *ub, uint8_t *surv_map, int *bucket_cnt,
+                                 int *bucket_cur, cudaStream_t s) {
+    const int64_t L = (int64_t)Ly * Lx;
+    cudaError_t e = cudaMemsetAsync(bucket_cnt, 0, kUbBuckets * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    {
+        LaunchScope ls("bound_hist_kernel", s);
+        bound_hist_kernel<<<grid_cap(L, 256, 8), 256, 0, s>>>(rho_tc, e_tc, rho_co, Ly, Lx, h, st,
+                                                             ub, surv_map, bucket_cnt);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    {
+        LaunchScope ls("bucket_scan_kernel", s);
+        bucket_scan_kernel<<<1, 32, 0, s>>>(st, bucket_cnt, bucket_cur);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    {
+        LaunchScope ls("bound_scatter_kernel", s);
+        bound_scatter_kernel<<<grid_cap(L, 256, 8), 256, 0, s>>>(ub, L, st, surv, surv_ub, cap,
+                                                                bucket_cur);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_survivors(const uint8_t *I, int q, int Lx, const double *IIS,
                              const double *IIQ, const float *tf, int m, int n, int npad,
                              const float *inv_sigma, TmplState *st, const int *surv,
-                             float *surv_rho, float *surv_eps, int cap, cudaStream_t s) {
+                             const float *surv_ub, float *surv_rho, float *surv_eps, int cap,
+                             cudaStream_t s) {
     size_t smem = (size_t)m * npad * sizeof(float);
     int in_smem = smem <= 200 * 1024;
     if (!in_smem) smem = 0;
@@ -731,8 +820,8 @@ cudaError_t launch_survivors(const uint8_t *I, int q, int Lx, const double *IIS,
     }
     LaunchScope ls_survivors_kernel("survivors_kernel", s);
     survivors_kernel<<<num_sms() * 4, 256, smem, s>>>(I, q, Lx, IIS, IIQ, tf, m, n, npad,
-                                                      inv_sigma, st, surv, surv_rho, surv_eps,
-                                                      cap, in_smem);
+                                                      inv_sigma, st, surv, surv_ub, surv_rho,
+                                                      surv_eps, cap, in_smem);
     return cudaGetLastError();
 }
 

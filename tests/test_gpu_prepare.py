@@ -1,0 +1,113 @@
+"""Preparation kernels vs the CPU oracle (diagnostic parity: these steps only
+decide how much work the search skips, never its answer).  Each hook runs
+one kernel through the C ABI on inputs the oracle also sees."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import synth
+from oracle import ref
+
+
+@pytest.fixture(scope="module")
+def opta():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1407_3535_gb300 as m
+    m.lib()
+    return m
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _window_inv_sigma(img, m, n):
+    from numpy.lib.stride_tricks import sliding_window_view
+    w = sliding_window_view(img.astype(np.float64), (m, n))
+    d = w - w.mean(axis=(2, 3), keepdims=True)
+    var = (d * d).sum(axis=(2, 3))
+    out = np.zeros_like(var)
+    nz = var > 0
+    out[nz] = 1.0 / np.sqrt(var[nz])
+    return out
+
+
+@pytest.mark.parametrize("shape,m,n", [((130, 141), 16, 16), ((97, 300), 9, 31), ((64, 64), 64, 64)])
+def test_window_stats(opta, shape, m, n):
+    img = synth.aerial_image(max(shape), 6, 6, seed=3)[:shape[0], :shape[1]].copy()
+    img[10:50, 10:60] = 42                       # flat windows
+    L = (shape[0] - m + 1) * (shape[1] - n + 1)
+    out = torch.empty(L, dtype=torch.float32, device="cuda")
+    opta.opta_dbg_window_stats(_cuda(img), m, n, out)
+    got = out.cpu().numpy().reshape(shape[0] - m + 1, shape[1] - n + 1)
+    exp = _window_inv_sigma(img, m, n)
+    assert np.array_equal(got == 0, exp == 0)
+    nz = exp > 0
+    assert np.allclose(got[nz], exp[nz], rtol=2e-7, atol=0)
+
+
+def test_blur_matches_definition(opta):
+    img = synth.aerial_image(200, 7, 12, seed=5)
+    smap = np.array([[0.0, 0.5, 1.0, 2.0], [3.0, 2.0, 0.0, 1.0], [0.5, 3.0, 3.0, 0.0], [1.0, 0.0, 2.0, 0.5]])
+    P = torch.empty(img.shape, dtype=torch.uint8, device="cuda")
+    opta.opta_dbg_blur(_cuda(img), smap, 64, P)
+    got = P.cpu().numpy().astype(int)
+    exp_f = ref.blur(img, smap, 64)
+    exp = ref.quantise_pivot(exp_f).astype(int)
+    diff = np.abs(got - exp)
+    assert diff.max() <= 1
+    # a one-step difference only where the FP64 value sits at a rounding tie
+    frac = np.abs(exp_f - np.floor(exp_f) - 0.5)
+    assert np.all(frac[diff == 1] < 1e-4)
+    # unblurred blocks are copies
+    assert np.array_equal(got[:64, :64], img[:64, :64].astype(int))
+
+
+@pytest.mark.parametrize("m,n", [(16, 16), (11, 27)])
+def test_blur_correlation(opta, m, n):
+    img = synth.aerial_image(180, 7, 10, seed=6)
+    P = ref.quantise_pivot(ref.blur(img, np.full((3, 3), 1.0), 64))
+    L = (180 - m + 1) * (180 - n + 1)
+    R = torch.empty(L, dtype=torch.float32, device="cuda")
+    opta.opta_dbg_blur_corr(_cuda(P), _cuda(img), m, n, R)
+    got = R.cpu().numpy().reshape(180 - m + 1, 180 - n + 1)
+    exp = ref.blur_corr_map(P, img, m, n)
+    assert np.max(np.abs(got - exp)) <= 2e-6
+
+
+@pytest.mark.parametrize("h", [1, 3, 5, 7, 9])
+def test_rho_co_map_and_retained_count(opta, h):
+    img = synth.aerial_image(150, 7, 10, seed=7)
+    img[40:80, 0:30] = 99                        # flat windows and pivots
+    m, n = 16, 20
+    P = ref.quantise_pivot(ref.blur(img, np.array([[2.0, 0.0, 1.0]] * 3), 64))
+    Ly, Lx = 150 - m + 1, 150 - n + 1
+    R = torch.empty(Ly * Lx, dtype=torch.float32, device="cuda")
+    cnt = opta.opta_dbg_rho_co(_cuda(P), _cuda(img), m, n, h, R, rho_cut=0.6)
+    got = R.cpu().numpy().reshape(Ly, Lx)
+    exp = ref.rho_co_map(P, img, m, n, h)
+    assert np.max(np.abs(got - exp)) <= 2e-6
+    exp_cnt = int(np.count_nonzero(exp < 0.6))
+    near = int(np.count_nonzero(np.abs(exp - 0.6) < 2e-6))
+    assert abs(cnt - exp_cnt) <= near
+
+
+def test_opta_decisions_match_oracle(opta):
+    """The OptA level loop's choices (group side, per-block sigma) equal the
+    oracle's on a case without decisions within rounding of a threshold."""
+    img = synth.aerial_image(320, 7, 20, seed=77)
+    m = n = 24
+    res = ref.opta(img, m, n)
+    h = opta.optA_prepare(_cuda(img), opta.opta_params_default(), sizes=[(m, n)])
+    info = opta.optA_size_info(h, m, n)
+    pivot = torch.empty(img.shape, dtype=torch.uint8, device="cuda")
+    smap = opta.optA_debug_maps(h, m, n, pivot=pivot)
+    assert info["group_h"] == res["h"]
+    assert info["cost"] == res["cost"]
+    assert np.array_equal(smap, res["sigma_map"].astype(np.float32))
+    diff = np.abs(pivot.cpu().numpy().astype(int) - res["pivot"].astype(int))
+    assert diff.max() <= 1 and np.count_nonzero(diff) <= 1e-3 * diff.size
+    h.close()
