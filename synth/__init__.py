@@ -12,9 +12,11 @@ not available; the paper's experiments, Section 7, use real 962x622 and
 * ``white_blur_image``  -- white Gaussian noise smoothed with a Gaussian of
   sigma 2, rescaled to [0, 255] and rounded to integers (float32).
 * ``aerial_image``      -- "remote-sensing-like" uint8 image: 1/f multi-octave
-  value noise (bilinearly upsampled random grids, amplitude halving per
-  octave) plus axis-aligned rectangles and line segments of random
-  intensity, rescaled to [0, 255] and rounded.
+  value noise (bilinearly upsampled random grids, one per octave, all with
+  the same amplitude: a 1/f amplitude spectrum puts equal variance in every
+  octave of a 2-D image, the statistic of natural and aerial images) plus
+  axis-aligned rectangles and line segments of random intensity, rescaled
+  to [0, 255] and rounded.
 * ``make_templates``    -- square crops of the search image at seeded
   locations, transformed by an affine intensity map a*x+b and perturbed by
   additive Gaussian noise (float32, not clipped).
@@ -96,12 +98,14 @@ def _draw_segment(img: np.ndarray, y0, x0, y1, x1, width, amp):
 
 
 def aerial_image(size: int, n_octaves: int, n_prims: int, seed: int,
-                 as_float32: bool = False) -> np.ndarray:
+                 as_float32: bool = False, decay: float = 1.0) -> np.ndarray:
     """Remote-sensing-like image, uint8 (or float32 holding the same integers).
 
     1/f noise: octave o = 0..n_octaves-1 is an N(0,1) grid of
     (size / 2**(n_octaves-o))**2 cells -- the finest octave has 2-pixel cells --
-    bilinearly upsampled to size x size and scaled by 2**-o.  Then n_prims
+    bilinearly upsampled to size x size and scaled by decay**o (decay = 1:
+    equal variance per octave, a 1/f amplitude spectrum; decay = 0.5 gives
+    the much smoother "persistence 1/2" fractal sum).  Then n_prims
     primitives, half axis-aligned rectangles (sides U{8..256}) and half line
     segments (length U{32..512}, width U{1..3}, uniform angle), each added
     with amplitude U[-3,3] * std(noise).  Rescaled to [0,255], rounded.
@@ -111,7 +115,7 @@ def aerial_image(size: int, n_octaves: int, n_prims: int, seed: int,
     for o in range(n_octaves):
         cells = max(2, size >> (n_octaves - o))
         grid = rng.standard_normal((cells, cells))
-        acc += _upsample_bilinear(grid, size, size) * np.float32(2.0 ** (-o))
+        acc += _upsample_bilinear(grid, size, size) * np.float32(decay ** o)
     sd = float(acc.std())
     n_rect = n_prims // 2
     for _ in range(n_rect):

@@ -173,8 +173,9 @@ def test_template_equals_image(opta):
 # ---------------------------------------------------------------------------
 # Pruned search with the OptA preparation (blur levels + EGS)
 # ---------------------------------------------------------------------------
-def test_opta_blur_egs_many_sizes(opta):
-    img = synth.aerial_image(512, n_octaves=7, n_prims=40, seed=2002)
+@pytest.mark.parametrize("decay", [1.0, 0.5])
+def test_opta_blur_egs_many_sizes(opta, decay):
+    img = synth.aerial_image(512, n_octaves=7, n_prims=40, seed=2002, decay=decay)
     ts = synth.make_templates(img, [16, 32, 32, 48, (24, 40)], seed=2102, noise=3.0)
     h = opta.optA_prepare(_cuda(img), opta.opta_params_default())
     res = opta.optA_search(h, [_cuda(t.data) for t in ts])
