@@ -63,6 +63,7 @@ struct SizeState {
     bool P_owned = false;
     float *inv_sigma = nullptr;    // L
     float *rho_co = nullptr;       // L
+    float2 *theta_co = nullptr;    // L angle intervals of rho_co
     float *c_inv_sigma = nullptr;  // G
     float *c_efac = nullptr;       // G
     std::vector<float> sigma_map;
@@ -79,7 +80,8 @@ struct opta_handle {
     std::map<std::pair<int, int>, SizeState *> sizes;
     // search scratch (grown on demand)
     size_t capL = 0, capG = 0, capT = 0, capN = 0;
-    float *rho_tc = nullptr, *e_tc = nullptr;
+    float *rho_tc = nullptr;
+    float2 *tc = nullptr;
     int *surv = nullptr;
     float *surv_rho = nullptr, *surv_eps = nullptr, *surv_ub = nullptr, *ubbuf = nullptr;
     int *bucket_cnt = nullptr, *bucket_cur = nullptr;
@@ -273,6 +275,7 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
         if (st != OPTA_OK) {
             H->mem.release(S->inv_sigma, L);
             H->mem.release(S->rho_co, L);
+            H->mem.release(S->theta_co, L);
             H->mem.release(S->c_inv_sigma, (size_t)S->Gy * S->Gx);
             H->mem.release(S->c_efac, (size_t)S->Gy * S->Gx);
             if (S->P_owned) H->mem.release(S->P, (size_t)p * q);
@@ -372,10 +375,12 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
         PQ = W.PQ;
     }
     PTRY(H->mem.alloc(&S->rho_co, L));
+    PTRY(H->mem.alloc(&S->theta_co, L));
     PTRY(H->mem.alloc(&S->c_inv_sigma, G));
     PTRY(H->mem.alloc(&S->c_efac, G));
     PCK(launch_rho_co(S->P, H->I8, p, q, m, n, S->h, H->IIS, H->IIQ, PS, PQ, 0.f, S->rho_co,
                       nullptr, s));
+    PCK(launch_theta_co(S->rho_co, L, S->theta_co, s));
     PCK(launch_centre_stats(PS, PQ, p, q, m, n, S->h, S->Ly, S->Lx, S->c_inv_sigma, S->c_efac, s));
     PCK(cudaStreamSynchronize(s));
     H->sizes[key] = S;
@@ -407,7 +412,7 @@ opta_status ensure_scratch(opta_handle *H, size_t L, size_t G, size_t T, size_t 
     }
     if (G > H->capG) {
         TRY(grow(H, H->rho_tc, dummy, H->capG, G));
-        TRY(grow(H, H->e_tc, dummy, H->capG, G));
+        TRY(grow(H, H->tc, dummy, H->capG, G));
         H->capG = G;
     }
     if (!H->topk_v) {
@@ -452,18 +457,17 @@ opta_status enqueue_search(opta_handle *H, const opta_template *t, TmplState *st
     TRY(template_device(H, t, &td_in, &ld, s));
     CK(launch_tmpl_prep(td_in, ld, m, n, npad, H->tf, H->td, st, H->prm.topk, s));
     CK(launch_centre_rho(S->P, H->p, H->q, H->tf, m, n, npad, S->h, S->Ly, S->Lx,
-                         S->c_inv_sigma, S->c_efac, st, H->rho_tc, H->e_tc, s));
+                         S->c_inv_sigma, S->c_efac, st, H->rho_tc, H->tc, s));
     CK(launch_topk(H->rho_tc, S->Gy, S->Gx, S->h, S->Ly, S->Lx, H->prm.topk, st, H->topk_v,
                    H->topk_i, H->cand, s));
     CK(launch_refine64(H->I8, H->q, S->Lx, H->td, m, n, st, H->cand, H->cand_rho,
                        capL + kTopkMax, true, s));
     CK(launch_threshold(st, H->cand_rho, s));
-    CK(launch_bound_compact(H->rho_tc, H->e_tc, S->rho_co, S->Ly, S->Lx, S->h, st, H->surv,
-                            H->surv_ub, capL, ub_map ? ub_map : H->ubbuf, surv_map,
-                            H->bucket_cnt, H->bucket_cur, s));
+    CK(launch_bound_compact(H->tc, S->theta_co, S->Ly, S->Lx, S->h, st, H->surv, H->surv_ub,
+                            capL, H->ubbuf, ub_map, surv_map, H->bucket_cnt, H->bucket_cur, s));
     CK(launch_survivors(H->I8, H->q, S->Lx, H->IIS, H->IIQ, H->tf, m, n, npad, S->inv_sigma, st,
                         H->surv, H->surv_ub, H->surv_rho, H->surv_eps, capL, s));
-    CK(launch_surv_candidates(st, H->surv, H->surv_rho, H->surv_eps, H->cand,
+    CK(launch_surv_candidates(st, H->surv, H->surv_ub, H->surv_rho, H->surv_eps, H->cand,
                               capL + kTopkMax, s));
     CK(launch_refine64(H->I8, H->q, S->Lx, H->td, m, n, st, H->cand, H->cand_rho,
                        capL + kTopkMax, false, s));
@@ -557,11 +561,12 @@ opta_status optA_destroy(opta_handle *h) {
     cudaSetDevice(h->device);
     for (auto &kv : h->sizes) {
         SizeState *S = kv.second;
-        cudaFree(S->inv_sigma); cudaFree(S->rho_co); cudaFree(S->c_inv_sigma); cudaFree(S->c_efac);
+        cudaFree(S->inv_sigma); cudaFree(S->rho_co); cudaFree(S->theta_co);
+        cudaFree(S->c_inv_sigma); cudaFree(S->c_efac);
         if (S->P_owned) cudaFree(S->P);
         delete S;
     }
-    void *ptrs[] = {h->I8, h->IIS, h->IIQ, h->rho_tc, h->e_tc, h->surv, h->surv_rho, h->surv_eps,
+    void *ptrs[] = {h->I8, h->IIS, h->IIQ, h->rho_tc, h->tc, h->surv, h->surv_rho, h->surv_eps,
                     h->surv_ub, h->ubbuf, h->bucket_cnt, h->bucket_cur,
                     h->cand, h->cand_rho, h->topk_v, h->topk_i, h->tf, h->tstage, h->td,
                     h->states, h->weights, h->radius};

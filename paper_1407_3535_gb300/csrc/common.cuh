@@ -34,6 +34,20 @@ __device__ inline float key_float(uint32_t k) {
     return __uint_as_float(b);
 }
 
+// Safety margins of the elimination test (Section 2, Eq. tranEqq in angle form):
+// |rho_co(fp32) - rho_co| <= kEcoBound (exact integer sums, FP32 quotient);
+// kAngMargin covers acosf and the subtraction of two angles; kCosMargin cosf.
+constexpr float kEcoBound = 1e-6f;
+constexpr float kAngMargin = 2e-6f;
+constexpr float kCosMargin = 2e-6f;
+
+// Angle interval [lo, hi] that certainly contains acos(rho_true) when
+// |rho - rho_true| <= e.
+__device__ inline float2 angle_interval(float r, float e) {
+    return make_float2(acosf(fminf(1.f, r + e)) - kAngMargin,
+                       acosf(fmaxf(-1.f, r - e)) + kAngMargin);
+}
+
 // Per-template device state, one per template in flight.
 struct TmplState {
     double mu;          // template mean (FP64)
@@ -51,6 +65,8 @@ struct TmplState {
     double best_rho;          // final rho (FP64)
     int overflow;             // candidate buffer overflowed (status)
     int n_eval;               // survivors evaluated (not skipped by the running threshold)
+    float theta_lim;          // survive iff angular gap <= theta_lim (from thr_lo)
+    int pad_;
 };
 
 // Survivors are bucketed by their upper bound (bucket 0 = highest) so that
@@ -97,28 +113,30 @@ cudaError_t launch_final_argmax(TmplState *st, const int *cand, const double *ca
                                 cudaStream_t s);
 
 // --- pruned search ---
+// rho_tc per group and the angle interval of its true value (tc).
 cudaError_t launch_centre_rho(const uint8_t *P, int p, int q, const float *tf, int m, int n,
                               int npad, int h, int Ly, int Lx, const float *c_inv_sigma,
                               const float *c_efac, TmplState *st, float *rho_tc,
-                              float *e_tc, cudaStream_t s);
+                              float2 *tc, cudaStream_t s);
 cudaError_t launch_topk(const float *rho_tc, int Gy, int Gx, int h, int Ly, int Lx, int k,
                         TmplState *st, float *tmp_val, int *tmp_idx, int *cand,
                         cudaStream_t s);
 cudaError_t launch_threshold(TmplState *st, const double *cand_rho, cudaStream_t s);
-// Scan 2: upper bound of every location into ub (L floats), bucket histogram of
-// the survivors, then compaction of the survivors in bucket order.
-cudaError_t launch_bound_compact(const float *rho_tc, const float *e_tc, const float *rho_co,
-                                 int Ly, int Lx, int h, TmplState *st, int *surv, float *surv_ub,
-                                 int cap, float *ub, uint8_t *surv_map, int *bucket_cnt,
+// Scan 2: angular gap of every location into gap (L floats), bucket histogram
+// of the survivors, then compaction of the survivors in bucket order with
+// their upper bound; ub_map / surv_map (nullable) receive the full maps.
+cudaError_t launch_bound_compact(const float2 *tc, const float2 *theta_co, int Ly, int Lx, int h,
+                                 TmplState *st, int *surv, float *surv_ub, int cap, float *gap,
+                                 float *ub_map, uint8_t *surv_map, int *bucket_cnt,
                                  int *bucket_cur, cudaStream_t s);
 cudaError_t launch_survivors(const uint8_t *I, int q, int Lx, const double *IIS,
                              const double *IIQ, const float *tf, int m, int n, int npad,
                              const float *inv_sigma, TmplState *st, const int *surv,
                              const float *surv_ub, float *surv_rho, float *surv_eps, int cap,
                              cudaStream_t s);
-cudaError_t launch_surv_candidates(TmplState *st, const int *surv, const float *surv_rho,
-                                   const float *surv_eps, int *cand, int cap,
-                                   cudaStream_t s);
+cudaError_t launch_surv_candidates(TmplState *st, const int *surv, const float *surv_ub,
+                                   const float *surv_rho, const float *surv_eps, int *cand,
+                                   int cap, cudaStream_t s);
 
 // --- preparation ---
 // Blur with per-block sigma-level index (uint8 map; level 0 = copy) and weight table.
@@ -134,6 +152,8 @@ cudaError_t launch_rho_co(const uint8_t *P, const uint8_t *I, int p, int q, int 
                           int h, const double *IIS, const double *IIQ, const double *PS,
                           const double *PQ, float cut, float *rco,
                           unsigned long long *count, cudaStream_t s);
+// Angle intervals of the pivot auto-correlation map (kEcoBound wide).
+cudaError_t launch_theta_co(const float *rho_co, int64_t L, float2 *theta_co, cudaStream_t s);
 // Per-centre pivot statistics: inv_sigma_hat and ||P-128||/sigma_hat.
 cudaError_t launch_centre_stats(const double *PS, const double *PQ, int p, int q, int m,
                                 int n, int h, int Ly, int Lx, float *c_inv_sigma,

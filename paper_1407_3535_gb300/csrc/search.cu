@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(128)
 centre_rho_kernel(const uint8_t *__restrict__ P, int p, int q, const float *__restrict__ tf,
                   int m, int n, int npad, int h, int Ly, int Lx,
                   const float *__restrict__ c_inv_sigma, const float *__restrict__ c_efac,
-                  TmplState *st, float *rho_tc, float *e_tc, int tile_w) {
+                  TmplState *st, float *rho_tc, float2 *tc, int tile_w) {
     extern __shared__ float4 csm4[];
     float *tile = reinterpret_cast<float *>(csm4);
     const int tile_rows = (CT_Y - 1) * h + CT_MT;
@@ -358,7 +358,7 @@ centre_rho_kernel(const uint8_t *__restrict__ P, int p, int q, const float *__re
         const float is = c_inv_sigma[g];
         const float r = (acc * st->inv_sigma) * is;
         rho_tc[g] = r;
-        e_tc[g] = is > 0.f ? eps_bound(centre_kacc(m, npad), c_efac[g]) : 0.f;
+        tc[g] = angle_interval(r, is > 0.f ? eps_bound(centre_kacc(m, npad), c_efac[g]) : 0.f);
     }
 }
 
@@ -474,53 +474,52 @@ __global__ void threshold_kernel(TmplState *st, const double *__restrict__ cand_
     const float lo = __double2float_rd(thr - 1e-9);
     st->thr_lo = lo;
     st->lo_key = max(st->lo_key, float_key(lo));
+    // cos(gap) + kCosMargin >= thr_lo  <=>  gap <= acos(thr_lo - kCosMargin)
+    st->theta_lim = acosf(fminf(1.f, fmaxf(-1.f, lo - kCosMargin))) + kAngMargin;
 }
 
 // ---------------------------------------------------------------------------
 // Scan 2: interval-safe transitive bound (Eq. tranEqq in angle form) and
 // warp-ballot compaction of the locations that fail Eq. SEC.
 // ---------------------------------------------------------------------------
-constexpr float kEcoBound = 1e-6f;    // |rho_co fp32 - exact| (exact integer sums, FP32 finish)
-constexpr float kAngMargin = 2e-6f;   // acosf / subtraction rounding, radians
-constexpr float kCosMargin = 2e-6f;   // cosf rounding
-
-__device__ inline float safe_upper_bound(float r_tc, float e_tc, float r_co) {
-    const float tlo = acosf(fminf(1.f, r_tc + e_tc)) - kAngMargin;
-    const float thi = acosf(fmaxf(-1.f, r_tc - e_tc)) + kAngMargin;
-    const float clo = acosf(fminf(1.f, r_co + kEcoBound)) - kAngMargin;
-    const float chi = acosf(fmaxf(-1.f, r_co - kEcoBound)) + kAngMargin;
-    const float gap = fmaxf(0.f, fmaxf(tlo - chi, clo - thi));
-    return cosf(gap) + kCosMargin;
-}
-
-__device__ inline int ub_bucket(float ub, float thr) {
-    const float span = 1.f - thr;
-    if (ub >= 1.f || span <= 0.f) return 0;
-    int b = (int)((1.f - ub) / span * (float)kUbBuckets);
+__device__ inline int gap_bucket(float gap, float lim) {
+    if (!(lim > 0.f)) return 0;
+    int b = (int)((gap / lim) * (float)kUbBuckets);
     return b < 0 ? 0 : (b >= kUbBuckets ? kUbBuckets - 1 : b);
 }
 
-// Pass 1: bound of every location (stored), survivor histogram by bucket.
+// Pass 1: angular gap of every location (stored), survivor histogram by bucket.
+// gap = max(0, tc.lo - co.hi, co.lo - tc.hi) is the smallest angle between
+// t and the location allowed by the two intervals; rho <= cos(gap).
 __global__ void __launch_bounds__(256)
-bound_hist_kernel(const float *__restrict__ rho_tc, const float *__restrict__ e_tc,
-                  const float *__restrict__ rho_co, int Ly, int Lx, int h, TmplState *st,
-                  float *ub_out, uint8_t *surv_map, int *bucket_cnt) {
+bound_hist_kernel(const float2 *__restrict__ tc, const float2 *__restrict__ theta_co, int Ly,
+                  int Lx, int h, TmplState *st, float *gap_out, float *ub_map,
+                  uint8_t *surv_map, int *bucket_cnt) {
     __shared__ int hist[kUbBuckets];
     if (st->flat) return;
     for (int i = threadIdx.x; i < kUbBuckets; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     const int Gx = groups_along(Lx, h);
-    const float thr = st->thr_lo;
+    const float lim = st->theta_lim;
     const int64_t L = (int64_t)Ly * Lx;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int y = (int)(i / Lx), x = (int)(i % Lx);
-        const int g = (y / h) * Gx + (x / h);
-        const float ub = safe_upper_bound(rho_tc[g], e_tc[g], rho_co[i]);
-        ub_out[i] = ub;
-        const bool f = ub >= thr;
-        if (surv_map) surv_map[i] = f ? 1 : 0;
-        if (f) atomicAdd(&hist[ub_bucket(ub, thr)], 1);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < L; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        bool f = false;
+        int b = -1;
+        if (i < L) {
+            const int y = (int)(i / Lx), x = (int)(i % Lx);
+            const float2 t = tc[(y / h) * Gx + (x / h)];
+            const float2 c = theta_co[i];
+            const float gap = fmaxf(0.f, fmaxf(t.x - c.y, c.x - t.y));
+            gap_out[i] = gap;
+            f = gap <= lim;
+            if (ub_map) ub_map[i] = cosf(gap) + kCosMargin;
+            if (surv_map) surv_map[i] = f ? 1 : 0;
+            if (f) b = gap_bucket(gap, lim);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        if (f && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[b], __popc(peers));
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kUbBuckets; i += blockDim.x)
@@ -536,19 +535,20 @@ __global__ void bucket_scan_kernel(TmplState *st, const int *__restrict__ bucket
     st->n_surv = acc;
 }
 
-// Pass 2: scatter the survivors into their bucket ranges (bucket 0 first).
+// Pass 2: scatter the survivors into their bucket ranges (bucket 0 = smallest
+// gap first) together with their upper bound cos(gap) + margin.
 __global__ void __launch_bounds__(256)
-bound_scatter_kernel(const float *__restrict__ ub_in, int64_t L, TmplState *st, int *surv,
+bound_scatter_kernel(const float *__restrict__ gap_in, int64_t L, TmplState *st, int *surv,
                      float *surv_ub, int cap, int *bucket_cur) {
     if (st->flat) return;
-    const float thr = st->thr_lo;
+    const float lim = st->theta_lim;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < L; base += stride) {
         const int64_t i = base + threadIdx.x;
-        const float ub = i < L ? ub_in[i] : -4.f;
-        const bool f = ub >= thr;
-        const int b = f ? ub_bucket(ub, thr) : -1;
+        const float gap = i < L ? gap_in[i] : 4.f;
+        const bool f = gap <= lim;
+        const int b = f ? gap_bucket(gap, lim) : -1;
         const unsigned act = __ballot_sync(0xffffffffu, f);
         if (!act) continue;
         const unsigned peers = __match_any_sync(0xffffffffu, b);
@@ -558,10 +558,17 @@ bound_scatter_kernel(const float *__restrict__ ub_in, int64_t L, TmplState *st, 
             if (lane == leader) pos = atomicAdd(&bucket_cur[b], __popc(peers));
             pos = __shfl_sync(peers, pos, leader);
             pos += __popc(peers & ((1u << lane) - 1u));
-            if (pos < cap) { surv[pos] = (int)i; surv_ub[pos] = ub; }
+            if (pos < cap) { surv[pos] = (int)i; surv_ub[pos] = cosf(gap) + kCosMargin; }
             else atomicOr(&st->overflow, 1);
         }
     }
+}
+
+// Angle intervals of the auto-correlation map.
+__global__ void theta_co_kernel(const float *__restrict__ rho_co, int64_t L, float2 *theta_co) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L;
+         i += (int64_t)gridDim.x * blockDim.x)
+        theta_co[i] = angle_interval(rho_co[i], kEcoBound);
 }
 
 // ---------------------------------------------------------------------------
@@ -597,59 +604,66 @@ survivors_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__r
     const int u0 = lane / n, v0 = lane % n;
     volatile unsigned int *lo_key = &st->lo_key;
     int evaluated = 0;
-    for (int s = warp; s < ns; s += nwarps) {
-        // running threshold: a location whose bound is below a certain lower bound
-        // of the maximum cannot be the best match
+    for (int base = warp * 32; base < ns; base += nwarps * 32) {
+        // running threshold: a location whose bound is below a certain lower
+        // bound of the maximum cannot be the best match (Eq. SEC with the best
+        // rho_tb found so far); check 32 survivors at once
         float lim = key_float(*lo_key);
         lim = __shfl_sync(0xffffffffu, lim, 0);
-        if (surv_ub[s] < lim) {
-            if (lane == 0) { surv_rho[s] = -3.f; surv_eps[s] = 0.f; }
-            continue;
-        }
-        const int idx = surv[s];
-        const int y = idx / Lx, x = idx % Lx;
-        const double S = IIS[(int64_t)(y + m) * q1 + x + n] - IIS[(int64_t)y * q1 + x + n]
-                       - IIS[(int64_t)(y + m) * q1 + x] + IIS[(int64_t)y * q1 + x];
-        const double Q = IIQ[(int64_t)(y + m) * q1 + x + n] - IIQ[(int64_t)y * q1 + x + n]
-                       - IIQ[(int64_t)(y + m) * q1 + x] + IIQ[(int64_t)y * q1 + x];
-        const float a = (float)rint(S / mn);
-        const uint8_t *base = I + (int64_t)y * q + x;
-        float acc0 = 0.f, acc1 = 0.f;
-        int u = u0, v = v0;
-        int e = lane;
-        // two independent chains over the flattened window, 32 lanes wide
-        for (; e + 32 < mnI; e += 64) {
-            const float t0 = tm[u * npad + v];
-            const float i0 = (float)base[(int64_t)u * q + v];
-            u += du; v += dv; if (v >= n) { v -= n; ++u; }
-            const float t1 = tm[u * npad + v];
-            const float i1 = (float)base[(int64_t)u * q + v];
-            u += du; v += dv; if (v >= n) { v -= n; ++u; }
-            acc0 = fmaf(t0, i0 - a, acc0);
-            acc1 = fmaf(t1, i1 - a, acc1);
-        }
-        if (e < mnI) acc0 = fmaf(tm[u * npad + v], (float)base[(int64_t)u * q + v] - a, acc0);
-        float acc = warp_sum_f(acc0 + acc1);
-        if (lane == 0) {
-            const float is = inv_sigma[idx];
-            const float rho = (acc * ist) * is;
-            float eps = 0.f;
-            if (is > 0.f) {
-                const double var = mn * Q - S * S;
-                const double da = (double)a;
-                const double c2 = Q - 2.0 * da * S + mn * da * da;   // sum (I - a)^2
-                eps = eps_bound(kacc, (float)sqrt(mn * c2 / var));
+        const int sl = base + lane;
+        unsigned todo = __ballot_sync(0xffffffffu, sl < ns && surv_ub[sl] >= lim);
+        while (todo) {
+            const int j = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int s = base + j;
+            lim = __shfl_sync(0xffffffffu, key_float(*lo_key), 0);
+            if (surv_ub[s] < lim) continue;
+            const int idx = surv[s];
+            const int y = idx / Lx, x = idx % Lx;
+            const double S = IIS[(int64_t)(y + m) * q1 + x + n] - IIS[(int64_t)y * q1 + x + n]
+                           - IIS[(int64_t)(y + m) * q1 + x] + IIS[(int64_t)y * q1 + x];
+            const double Q = IIQ[(int64_t)(y + m) * q1 + x + n] - IIQ[(int64_t)y * q1 + x + n]
+                           - IIQ[(int64_t)(y + m) * q1 + x] + IIQ[(int64_t)y * q1 + x];
+            const float a = (float)rint(S / mn);
+            const uint8_t *bp = I + (int64_t)y * q + x;
+            float acc0 = 0.f, acc1 = 0.f;
+            int u = u0, v = v0;
+            int e = lane;
+            // two independent chains over the flattened window, 32 lanes wide
+            for (; e + 32 < mnI; e += 64) {
+                const float t0 = tm[u * npad + v];
+                const float i0 = (float)bp[(int64_t)u * q + v];
+                u += du; v += dv; if (v >= n) { v -= n; ++u; }
+                const float t1 = tm[u * npad + v];
+                const float i1 = (float)bp[(int64_t)u * q + v];
+                u += du; v += dv; if (v >= n) { v -= n; ++u; }
+                acc0 = fmaf(t0, i0 - a, acc0);
+                acc1 = fmaf(t1, i1 - a, acc1);
             }
-            surv_rho[s] = rho;
-            surv_eps[s] = eps;
-            atomicMax(&st->lo_key, float_key(rho - eps));
-            ++evaluated;
+            if (e < mnI) acc0 = fmaf(tm[u * npad + v], (float)bp[(int64_t)u * q + v] - a, acc0);
+            const float acc = warp_sum_f(acc0 + acc1);
+            if (lane == 0) {
+                const float is = inv_sigma[idx];
+                const float rho = (acc * ist) * is;
+                float eps = 0.f;
+                if (is > 0.f) {
+                    const double var = mn * Q - S * S;
+                    const double da = (double)a;
+                    const double c2 = Q - 2.0 * da * S + mn * da * da;   // sum (I - a)^2
+                    eps = eps_bound(kacc, (float)sqrt(mn * c2 / var));
+                }
+                surv_rho[s] = rho;
+                surv_eps[s] = eps;
+                atomicMax(&st->lo_key, float_key(rho - eps));
+                ++evaluated;
+            }
         }
     }
     if (lane == 0 && evaluated) atomicAdd(&st->n_eval, evaluated);
 }
 
 __global__ void surv_candidates_kernel(TmplState *st, const int *__restrict__ surv,
+                                       const float *__restrict__ surv_ub,
                                        const float *__restrict__ surv_rho,
                                        const float *__restrict__ surv_eps, int *cand, int cap) {
     if (st->flat) return;
@@ -658,7 +672,9 @@ __global__ void surv_candidates_kernel(TmplState *st, const int *__restrict__ su
     for (int base = blockIdx.x * blockDim.x; base < ns; base += gridDim.x * blockDim.x) {
         const int s = base + threadIdx.x;
         bool f = false;
-        if (s < ns) f = surv_rho[s] + surv_eps[s] >= lstar;
+        // entries whose bound is below the final lower bound were skipped (never
+        // written) and cannot be the maximum
+        if (s < ns && surv_ub[s] >= lstar) f = surv_rho[s] + surv_eps[s] >= lstar;
         warp_append(f, s < ns ? surv[s] : 0, &st->n_cand, cand, cap, &st->overflow);
     }
 }
@@ -724,7 +740,7 @@ cudaError_t launch_final_argmax(TmplState *st, const int *cand, const double *ca
 
 cudaError_t launch_centre_rho(const uint8_t *P, int p, int q, const float *tf, int m, int n,
                               int npad, int h, int Ly, int Lx, const float *c_inv_sigma,
-                              const float *c_efac, TmplState *st, float *rho_tc, float *e_tc,
+                              const float *c_efac, TmplState *st, float *rho_tc, float2 *tc,
                               cudaStream_t s) {
     const int Gy = groups_along(Ly, h), Gx = groups_along(Lx, h);
     const int tile_w = ((CT_X - 1) * h + CT_NT + 3) & ~3;
@@ -740,7 +756,7 @@ cudaError_t launch_centre_rho(const uint8_t *P, int p, int q, const float *tf, i
     dim3 grid((Gx + CT_X - 1) / CT_X, (Gy + CT_Y - 1) / CT_Y);
     LaunchScope ls_centre_rho_kernel("centre_rho_kernel", s);
     centre_rho_kernel<<<grid, CT_Y * CT_X, smem, s>>>(P, p, q, tf, m, n, npad, h, Ly, Lx,
-                                                     c_inv_sigma, c_efac, st, rho_tc, e_tc, tile_w);
+                                                     c_inv_sigma, c_efac, st, rho_tc, tc, tile_w);
     return cudaGetLastError();
 }
 
@@ -777,17 +793,17 @@ cudaError_t launch_threshold(TmplState *st, const double *cand_rho, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_bound_compact(const float *rho_tc, const float *e_tc, const float *rho_co,
-                                 int Ly, int Lx, int h, TmplState *st, int *surv, float *surv_ub,
-                                 int cap, float *ub, uint8_t *surv_map, int *bucket_cnt,
+cudaError_t launch_bound_compact(const float2 *tc, const float2 *theta_co, int Ly, int Lx, int h,
+                                 TmplState *st, int *surv, float *surv_ub, int cap, float *gap,
+                                 float *ub_map, uint8_t *surv_map, int *bucket_cnt,
                                  int *bucket_cur, cudaStream_t s) {
     const int64_t L = (int64_t)Ly * Lx;
     cudaError_t e = cudaMemsetAsync(bucket_cnt, 0, kUbBuckets * sizeof(int), s);
     if (e != cudaSuccess) return e;
     {
         LaunchScope ls("bound_hist_kernel", s);
-        bound_hist_kernel<<<grid_cap(L, 256, 8), 256, 0, s>>>(rho_tc, e_tc, rho_co, Ly, Lx, h, st,
-                                                             ub, surv_map, bucket_cnt);
+        bound_hist_kernel<<<grid_cap(L, 256, 8), 256, 0, s>>>(tc, theta_co, Ly, Lx, h, st, gap,
+                                                             ub_map, surv_map, bucket_cnt);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
@@ -797,9 +813,15 @@ cudaError_t launch_bound_compact(const float *rho_tc, const float *e_tc, const f
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
         LaunchScope ls("bound_scatter_kernel", s);
-        bound_scatter_kernel<<<grid_cap(L, 256, 8), 256, 0, s>>>(ub, L, st, surv, surv_ub, cap,
+        bound_scatter_kernel<<<grid_cap(L, 256, 8), 256, 0, s>>>(gap, L, st, surv, surv_ub, cap,
                                                                 bucket_cur);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_theta_co(const float *rho_co, int64_t L, float2 *theta_co, cudaStream_t s) {
+    LaunchScope ls("theta_co_kernel", s);
+    theta_co_kernel<<<grid_cap(L, 256, 16), 256, 0, s>>>(rho_co, L, theta_co);
     return cudaGetLastError();
 }
 
@@ -825,10 +847,12 @@ cudaError_t launch_survivors(const uint8_t *I, int q, int Lx, const double *IIS,
     return cudaGetLastError();
 }
 
-cudaError_t launch_surv_candidates(TmplState *st, const int *surv, const float *surv_rho,
-                                   const float *surv_eps, int *cand, int cap, cudaStream_t s) {
+cudaError_t launch_surv_candidates(TmplState *st, const int *surv, const float *surv_ub,
+                                   const float *surv_rho, const float *surv_eps, int *cand,
+                                   int cap, cudaStream_t s) {
     LaunchScope ls_surv_candidates_kernel("surv_candidates_kernel", s);
-    surv_candidates_kernel<<<num_sms() * 4, 256, 0, s>>>(st, surv, surv_rho, surv_eps, cand, cap);
+    surv_candidates_kernel<<<num_sms() * 4, 256, 0, s>>>(st, surv, surv_ub, surv_rho, surv_eps,
+                                                         cand, cap);
     return cudaGetLastError();
 }
 
