@@ -54,6 +54,14 @@ opta_status optA_debug_maps(opta_handle *h, int32_t m, int32_t n,
                             uint8_t *pivot_dev, float *rho_co_dev,
                             float *sigma_map_host, void *stream);
 
+/* Scan 1 alone (Section 6) for n_t (1..128) templates of one size with the
+ * handle's precision: rho_dev receives n_t x G floats (template-major;
+ * G = groups of that size, row-major over the group grid) holding rho(t,
+ * pivot block at each centre); theta_dev (nullable) n_t x G x 2 floats, the
+ * angle interval [lo, hi] certain to contain acos of the exact value. */
+opta_status optA_debug_scan1(opta_handle *h, const opta_template *t, int32_t n_t,
+                             float *rho_dev, float *theta_dev, void *stream);
+
 /* Number of kernel launches the library has issued in this process. */
 uint64_t opta_dbg_launch_count(void);
 

@@ -19,7 +19,7 @@ __all__ = [
     "optA_debug_bounds", "optA_size_info", "optA_memory_bytes", "optA_destroy",
     "optA_debug_maps", "opta_dbg_window_stats", "opta_dbg_blur", "opta_dbg_blur_corr",
     "opta_dbg_rho_co", "opta_dbg_launch_count", "opta_dbg_profile_enable",
-    "opta_dbg_profile_read", "Handle", "lib", "OptaResult",
+    "opta_dbg_profile_read", "optA_debug_scan1", "Handle", "lib", "OptaResult",
 ]
 
 lib = _lib.lib
@@ -285,3 +285,17 @@ def opta_dbg_profile_read(capacity: int = 64) -> dict:
         nm = names.raw[i * stride:(i + 1) * stride].split(b"\0", 1)[0].decode()
         out[nm] = (float(tot[i]), int(cnt[i]))
     return out
+
+
+def optA_debug_scan1(handle: Handle, templates, rho_out, theta_out=None, stream=None) -> None:
+    """Scan 1 of same-size templates: rho(t, pivot) per centre into CUDA tensors."""
+    n = len(templates)
+    descs = (OptaTemplate * n)()
+    keep = []
+    for i, t in enumerate(templates):
+        d, k = _template(t)
+        descs[i] = d
+        keep.append(k)
+    _check(lib().optA_debug_scan1(handle.ptr, descs, n, c_void_p(rho_out.data_ptr()),
+                                  c_void_p(theta_out.data_ptr() if theta_out is not None else 0),
+                                  _stream(stream)), "optA_debug_scan1")

@@ -4,6 +4,7 @@
 // stream; host decisions of the preparation loop read back a few scalars.
 #include <cmath>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <new>
 #include <utility>
@@ -89,9 +90,12 @@ struct opta_handle {
     double *cand_rho = nullptr;
     float *topk_v = nullptr;
     int *topk_i = nullptr;
-    float *tf = nullptr, *tstage = nullptr;
-    double *td = nullptr;
+    float *tf = nullptr, *tstage = nullptr;   // tf: chunk of templates, m x npad each
+    double *td = nullptr;                     // chunk of templates, m x n each
     TmplState *states = nullptr;
+    size_t capTS = 0, capB = 0, capRT = 0;    // template-slot, B-buffer, rho_tc capacities
+    void *Bmma = nullptr;                     // bf16 hi/lo planes of a chunk (core-matrix layout)
+    int *dev_err = nullptr;                   // set by a kernel whose bounded wait gave up
     // blur tables
     float *weights = nullptr;
     int *radius = nullptr;
@@ -111,7 +115,7 @@ bool valid_params(const opta_params &p) {
     if (p.h_max < 1 || p.h_max > 9 || (p.h_max % 2) == 0) return false;
     if (p.fixed_h < 0 || p.fixed_h > 9 || (p.fixed_h > 0 && p.fixed_h % 2 == 0)) return false;
     if (p.topk < 1 || p.topk > kTopkMax) return false;
-    if (p.precision != 0) return false;
+    if (p.precision != 0 && p.precision != 1) return false;
     return true;
 }
 
@@ -396,10 +400,13 @@ opta_status grow(opta_handle *H, T *&p, size_t &cap_field_unused, size_t old_n, 
     return H->mem.alloc(&p, new_n);
 }
 
-// Make the search scratch large enough for L locations, G groups, a template
-// of T = m * npad elements and N templates in one call.
-opta_status ensure_scratch(opta_handle *H, size_t L, size_t G, size_t T, size_t N) {
+// Make the search scratch large enough for L locations, G groups (times the
+// templates of one chunk: RT = chunk * G), chunk template slots of T = m*npad
+// elements each (TS = chunk * T), a B buffer of `Bbytes` and N templates.
+opta_status ensure_scratch(opta_handle *H, size_t L, size_t RT, size_t T, size_t TS,
+                           size_t Bbytes, size_t N) {
     size_t dummy = 0;
+    const size_t G = RT;
     if (L > H->capL) {
         TRY(grow(H, H->surv, dummy, H->capL, L));
         TRY(grow(H, H->surv_rho, dummy, H->capL, L));
@@ -422,10 +429,23 @@ opta_status ensure_scratch(opta_handle *H, size_t L, size_t G, size_t T, size_t 
         TRY(H->mem.alloc(&H->bucket_cur, kUbBuckets));
     }
     if (T > H->capT) {
-        TRY(grow(H, H->tf, dummy, H->capT, T));
-        TRY(grow(H, H->td, dummy, H->capT, T));
         TRY(grow(H, H->tstage, dummy, H->capT, T));
         H->capT = T;
+    }
+    if (TS > H->capTS) {
+        TRY(grow(H, H->tf, dummy, H->capTS, TS));
+        TRY(grow(H, H->td, dummy, H->capTS, TS));
+        H->capTS = TS;
+    }
+    if (Bbytes > H->capB) {
+        uint8_t *b = static_cast<uint8_t *>(H->Bmma);
+        TRY(grow(H, b, dummy, H->capB, Bbytes));
+        H->Bmma = b;
+        H->capB = Bbytes;
+    }
+    if (!H->dev_err) {
+        TRY(H->mem.alloc(&H->dev_err, 1));
+        CK(cudaMemset(H->dev_err, 0, sizeof(int)));
     }
     if (N > H->capN) {
         TRY(grow(H, H->states, dummy, H->capN, N));
@@ -446,32 +466,126 @@ opta_status template_device(opta_handle *H, const opta_template *t, const float 
     return OPTA_OK;
 }
 
-// Enqueue the whole pruned search of one template (no host synchronisation).
-opta_status enqueue_search(opta_handle *H, const opta_template *t, TmplState *st, float *ub_map,
-                           uint8_t *surv_map, cudaStream_t s) {
-    SizeState *S = H->sizes[std::make_pair(t->rows, t->cols)];
-    const int m = t->rows, n = t->cols, npad = (n + 7) & ~7;
+constexpr int kChunk = 128;   // templates per tensor-core batch (N = 2 * chunk <= 256)
+
+bool use_mma(const opta_handle *H) { return H->prm.precision == 1; }
+
+// Scratch needed by a batch of templates (sizes already prepared).
+opta_status size_scratch(opta_handle *H, const opta_template *t, int n_t) {
+    size_t maxL = 0, maxRT = 0, maxT = 0, maxTS = 0, maxB = 0;
+    std::map<std::pair<int, int>, int> count;
+    for (int i = 0; i < n_t; ++i) count[std::make_pair(t[i].rows, t[i].cols)]++;
+    for (auto &kv : count) {
+        SizeState *S = H->sizes[kv.first];
+        const int m = kv.first.first, n = kv.first.second, npad = (n + 7) & ~7, Kp = (n + 15) & ~15;
+        const size_t chunk = (size_t)std::min(kv.second, kChunk);
+        const size_t G = (size_t)S->Gy * S->Gx;
+        maxL = std::max(maxL, (size_t)S->Ly * S->Lx);
+        maxRT = std::max(maxRT, chunk * G);
+        maxT = std::max(maxT, (size_t)m * npad);
+        maxTS = std::max(maxTS, chunk * (size_t)m * npad);
+        const size_t N = ((2 * chunk + 15) / 16) * 16;
+        if (use_mma(H)) maxB = std::max(maxB, (size_t)m * Kp * N * 2);
+    }
+    return ensure_scratch(H, maxL, maxRT, maxT, maxTS, maxB, (size_t)n_t);
+}
+
+// Template statistics and scan 1 (Section 6: rho(t, pivot) at every centre)
+// of templates t[0..n) -- all of one size -- into the chunk slots; states
+// st[0..n).  No host synchronisation.
+opta_status enqueue_scan1(opta_handle *H, const opta_template *const *t, int n, TmplState *st,
+                          cudaStream_t s) {
+    const int m = t[0]->rows, nn = t[0]->cols, npad = (nn + 7) & ~7, Kp = (nn + 15) & ~15;
+    SizeState *S = H->sizes[std::make_pair(m, nn)];
+    const int64_t G = (int64_t)S->Gy * S->Gx;
+    const size_t tsz = (size_t)m * npad, dsz = (size_t)m * nn;
+    // template statistics (Eq. rho1's mu_t, sigma_t) into per-template slots
+    for (int k = 0; k < n; ++k) {
+        const float *tin = nullptr;
+        int64_t ld = 0;
+        TRY(template_device(H, t[k], &tin, &ld, s));
+        CK(launch_tmpl_prep(tin, ld, m, nn, npad, H->tf + k * tsz, H->td + k * dsz, st + k,
+                            H->prm.topk, s));
+    }
+    // scan 1: rho(t, pivot) at every centre
+    if (use_mma(H)) {
+        const int N = ((2 * n + 15) / 16) * 16;
+        CK(cudaMemsetAsync(H->Bmma, 0, (size_t)m * Kp * N * 2, s));
+        for (int k = 0; k < n; ++k)
+            CK(launch_tmpl_split(H->tf + k * tsz, m, nn, npad, Kp, N, k, H->Bmma, s));
+        int Gx_u = S->Gx;
+        CK(launch_corr_mma(S->P, H->p, H->q, H->Bmma, m, nn, Kp, N, S->h, S->Ly, S->Lx, n,
+                           S->c_inv_sigma, S->c_efac, st, H->rho_tc, H->tc, G, H->dev_err,
+                           &Gx_u, s));
+        if (Gx_u < S->Gx)
+            for (int k = 0; k < n; ++k)
+                CK(launch_centre_rho(S->P, H->p, H->q, H->tf + k * tsz, m, nn, npad, S->h, S->Ly,
+                                     S->Lx, S->c_inv_sigma, S->c_efac, st + k, H->rho_tc + k * G,
+                                     H->tc + k * G, Gx_u, s));
+    } else {
+        for (int k = 0; k < n; ++k)
+            CK(launch_centre_rho(S->P, H->p, H->q, H->tf + k * tsz, m, nn, npad, S->h, S->Ly,
+                                 S->Lx, S->c_inv_sigma, S->c_efac, st + k, H->rho_tc + k * G,
+                                 H->tc + k * G, 0, s));
+    }
+    return OPTA_OK;
+}
+
+// Threshold (Section 6), scan 2 (Eq. SEC), survivors and FP64 argmax of the
+// templates whose scan 1 is in the chunk slots.
+opta_status enqueue_scan2(opta_handle *H, const opta_template *const *t, int n, TmplState *st,
+                          float *ub_map, uint8_t *surv_map, cudaStream_t s) {
+    const int m = t[0]->rows, nn = t[0]->cols, npad = (nn + 7) & ~7;
+    SizeState *S = H->sizes[std::make_pair(m, nn)];
     const int capL = (int)H->capL;
-    const float *td_in = nullptr;
-    int64_t ld = 0;
-    TRY(template_device(H, t, &td_in, &ld, s));
-    CK(launch_tmpl_prep(td_in, ld, m, n, npad, H->tf, H->td, st, H->prm.topk, s));
-    CK(launch_centre_rho(S->P, H->p, H->q, H->tf, m, n, npad, S->h, S->Ly, S->Lx,
-                         S->c_inv_sigma, S->c_efac, st, H->rho_tc, H->tc, s));
-    CK(launch_topk(H->rho_tc, S->Gy, S->Gx, S->h, S->Ly, S->Lx, H->prm.topk, st, H->topk_v,
-                   H->topk_i, H->cand, s));
-    CK(launch_refine64(H->I8, H->q, S->Lx, H->td, m, n, st, H->cand, H->cand_rho,
-                       capL + kTopkMax, true, s));
-    CK(launch_threshold(st, H->cand_rho, s));
-    CK(launch_bound_compact(H->tc, S->theta_co, S->Ly, S->Lx, S->h, st, H->surv, H->surv_ub,
-                            capL, H->ubbuf, ub_map, surv_map, H->bucket_cnt, H->bucket_cur, s));
-    CK(launch_survivors(H->I8, H->q, S->Lx, H->IIS, H->IIQ, H->tf, m, n, npad, S->inv_sigma, st,
-                        H->surv, H->surv_ub, H->surv_rho, H->surv_eps, capL, s));
-    CK(launch_surv_candidates(st, H->surv, H->surv_ub, H->surv_rho, H->surv_eps, H->cand,
-                              capL + kTopkMax, s));
-    CK(launch_refine64(H->I8, H->q, S->Lx, H->td, m, n, st, H->cand, H->cand_rho,
-                       capL + kTopkMax, false, s));
-    CK(launch_final_argmax(st, H->cand, H->cand_rho, capL + kTopkMax, s));
+    const int64_t G = (int64_t)S->Gy * S->Gx;
+    const size_t tsz = (size_t)m * npad, dsz = (size_t)m * nn;
+    for (int k = 0; k < n; ++k) {
+        const float *tf = H->tf + k * tsz;
+        const double *td = H->td + k * dsz;
+        TmplState *sk = st + k;
+        CK(launch_topk(H->rho_tc + k * G, S->Gy, S->Gx, S->h, S->Ly, S->Lx, H->prm.topk, sk,
+                       H->topk_v, H->topk_i, H->cand, s));
+        CK(launch_refine64(H->I8, H->q, S->Lx, td, m, nn, sk, H->cand, H->cand_rho,
+                           capL + kTopkMax, true, s));
+        CK(launch_threshold(sk, H->cand_rho, s));
+        CK(launch_bound_compact(H->tc + k * G, S->theta_co, S->Ly, S->Lx, S->h, sk, H->surv,
+                                H->surv_ub, capL, H->ubbuf, ub_map, surv_map, H->bucket_cnt,
+                                H->bucket_cur, s));
+        CK(launch_survivors(H->I8, H->q, S->Lx, H->IIS, H->IIQ, tf, m, nn, npad, S->inv_sigma, sk,
+                            H->surv, H->surv_ub, H->surv_rho, H->surv_eps, capL, s));
+        CK(launch_surv_candidates(sk, H->surv, H->surv_ub, H->surv_rho, H->surv_eps, H->cand,
+                                  capL + kTopkMax, s));
+        CK(launch_refine64(H->I8, H->q, S->Lx, td, m, nn, sk, H->cand, H->cand_rho,
+                           capL + kTopkMax, false, s));
+        CK(launch_final_argmax(sk, H->cand, H->cand_rho, capL + kTopkMax, s));
+    }
+    return OPTA_OK;
+}
+
+// Group templates by size (stable) and enqueue them chunk by chunk; order[i]
+// is the input index of the template whose state is states[i].
+opta_status enqueue_all(opta_handle *H, const opta_template *t, int n_t, std::vector<int> &order,
+                        cudaStream_t s) {
+    order.resize(n_t);
+    for (int i = 0; i < n_t; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return std::make_pair(t[a].rows, t[a].cols) < std::make_pair(t[b].rows, t[b].cols);
+    });
+    int i = 0;
+    std::vector<const opta_template *> chunk;
+    while (i < n_t) {
+        int j = i;
+        chunk.clear();
+        while (j < n_t && (int)chunk.size() < kChunk && t[order[j]].rows == t[order[i]].rows &&
+               t[order[j]].cols == t[order[i]].cols) {
+            chunk.push_back(&t[order[j]]);
+            ++j;
+        }
+        TRY(enqueue_scan1(H, chunk.data(), (int)chunk.size(), H->states + i, s));
+        TRY(enqueue_scan2(H, chunk.data(), (int)chunk.size(), H->states + i, nullptr, nullptr, s));
+        i = j;
+    }
     return OPTA_OK;
 }
 
@@ -567,7 +681,7 @@ opta_status optA_destroy(opta_handle *h) {
         delete S;
     }
     void *ptrs[] = {h->I8, h->IIS, h->IIQ, h->rho_tc, h->tc, h->surv, h->surv_rho, h->surv_eps,
-                    h->surv_ub, h->ubbuf, h->bucket_cnt, h->bucket_cur,
+                    h->surv_ub, h->ubbuf, h->bucket_cnt, h->bucket_cur, h->Bmma, h->dev_err,
                     h->cand, h->cand_rho, h->topk_v, h->topk_i, h->tf, h->tstage, h->td,
                     h->states, h->weights, h->radius};
     for (void *p : ptrs) if (p) cudaFree(p);
@@ -630,17 +744,25 @@ opta_status optA_search(opta_handle *h, const opta_template *t, int32_t n_t, opt
         maxT = std::max(maxT, (size_t)t[i].rows * ((t[i].cols + 7) & ~7));
     }
     if (n_t == 0) return OPTA_OK;
-    TRY(ensure_scratch(h, maxL, maxG, maxT, (size_t)n_t));
-    for (int i = 0; i < n_t; ++i) TRY(enqueue_search(h, &t[i], h->states + i, nullptr, nullptr, s));
+    (void)maxL; (void)maxG; (void)maxT;
+    TRY(size_scratch(h, t, n_t));
+    std::vector<int> order;
+    TRY(enqueue_all(h, t, n_t, order, s));
     std::vector<TmplState> hs(n_t);
+    int herr = 0;
     CK(cudaMemcpyAsync(hs.data(), h->states, sizeof(TmplState) * n_t, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&herr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     opta_status first = OPTA_OK;
-    for (int i = 0; i < n_t; ++i) {
+    for (int k = 0; k < n_t; ++k) {
+        const int i = order[k];
         SizeState *S = h->sizes[std::make_pair(t[i].rows, t[i].cols)];
-        fill_result(hs[i], S, S->Lx, (int64_t)S->Ly * S->Lx, S->h, (int64_t)S->Gy * S->Gx, &out[i]);
-        if (first == OPTA_OK && out[i].status != OPTA_OK) first = (opta_status)out[i].status;
+        fill_result(hs[k], S, S->Lx, (int64_t)S->Ly * S->Lx, S->h, (int64_t)S->Gy * S->Gx, &out[i]);
+        if (herr) out[i].status = OPTA_ERR_TIMEOUT;
     }
+    for (int i = 0; i < n_t; ++i)
+        if (first == OPTA_OK && out[i].status != OPTA_OK) first = (opta_status)out[i].status;
+    if (herr) CK(cudaMemsetAsync(h->dev_err, 0, sizeof(int), s));
     return first;
 }
 
@@ -653,13 +775,46 @@ opta_status optA_debug_bounds(opta_handle *h, const opta_template *t, float *ub_
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     TRY(prepare_size(h, t->rows, t->cols, s));
     SizeState *S = h->sizes[std::make_pair(t->rows, t->cols)];
-    TRY(ensure_scratch(h, (size_t)S->Ly * S->Lx, (size_t)S->Gy * S->Gx,
-                       (size_t)t->rows * ((t->cols + 7) & ~7), 1));
-    TRY(enqueue_search(h, t, h->states, ub_map, survived, s));
+    (void)S;
+    TRY(size_scratch(h, t, 1));
+    const opta_template *one = t;
+    TRY(enqueue_scan1(h, &one, 1, h->states, s));
+    TRY(enqueue_scan2(h, &one, 1, h->states, ub_map, survived, s));
     TmplState st;
     CK(cudaMemcpyAsync(&st, h->states, sizeof(st), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return st.flat ? OPTA_ERR_FLAT_TEMPLATE : OPTA_OK;
+}
+
+opta_status optA_debug_scan1(opta_handle *h, const opta_template *t, int32_t n_t,
+                             float *rho_dev, float *theta_dev, void *stream) {
+    if (!h || !t || n_t < 1 || n_t > kChunk) return OPTA_ERR_INVALID_ARG;
+    for (int i = 0; i < n_t; ++i) {
+        if (!valid_template(&t[i], h->p, h->q)) return OPTA_ERR_INVALID_ARG;
+        if (t[i].rows != t[0].rows || t[i].cols != t[0].cols) return OPTA_ERR_INVALID_ARG;
+    }
+    if (h->busy) return OPTA_ERR_BUSY;
+    BusyGuard guard(h);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TRY(prepare_size(h, t[0].rows, t[0].cols, s));
+    SizeState *S = h->sizes[std::make_pair(t[0].rows, t[0].cols)];
+    TRY(size_scratch(h, t, n_t));
+    std::vector<const opta_template *> ptrs(n_t);
+    for (int i = 0; i < n_t; ++i) ptrs[i] = &t[i];
+    TRY(enqueue_scan1(h, ptrs.data(), n_t, h->states, s));
+    const size_t G = (size_t)S->Gy * S->Gx;
+    if (rho_dev)
+        CK(cudaMemcpyAsync(rho_dev, h->rho_tc, n_t * G * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (theta_dev)
+        CK(cudaMemcpyAsync(theta_dev, h->tc, n_t * G * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (herr) {
+        CK(cudaMemset(h->dev_err, 0, sizeof(int)));
+        return OPTA_ERR_TIMEOUT;
+    }
+    return OPTA_OK;
 }
 
 opta_status optA_size_info(opta_handle *h, int32_t m, int32_t n, opta_size_info *info) {

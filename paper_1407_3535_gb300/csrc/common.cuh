@@ -113,11 +113,19 @@ cudaError_t launch_final_argmax(TmplState *st, const int *cand, const double *ca
                                 cudaStream_t s);
 
 // --- pruned search ---
-// rho_tc per group and the angle interval of its true value (tc).
+// rho_tc per group and the angle interval of its true value (tc), for the
+// group columns gx >= gx_begin (FP32 CUDA cores).
 cudaError_t launch_centre_rho(const uint8_t *P, int p, int q, const float *tf, int m, int n,
                               int npad, int h, int Ly, int Lx, const float *c_inv_sigma,
                               const float *c_efac, TmplState *st, float *rho_tc,
-                              float2 *tc, cudaStream_t s);
+                              float2 *tc, int gx_begin, cudaStream_t s);
+// Tensor-core scan 1 for T same-size templates (planes of B), see corr_mma.cu.
+cudaError_t launch_corr_mma(const uint8_t *V, int p, int q, const void *B, int m, int n, int Kp,
+                            int N, int h, int Ly, int Lx, int T, const float *c_inv_sigma,
+                            const float *c_efac, const TmplState *st, float *rho_tc, float2 *tc,
+                            int64_t gstride, int *err, int *Gx_u_out, cudaStream_t s);
+cudaError_t launch_tmpl_split(const float *tf, int m, int n, int npad, int Kp, int N, int t,
+                              void *B, cudaStream_t s);
 cudaError_t launch_topk(const float *rho_tc, int Gy, int Gx, int h, int Ly, int Lx, int k,
                         TmplState *st, float *tmp_val, int *tmp_idx, int *cand,
                         cudaStream_t s);

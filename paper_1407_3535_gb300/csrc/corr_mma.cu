@@ -1,0 +1,269 @@
+// Scan 1 (Section 6) on the 5th-generation tensor cores: rho(t, pivot block)
+// at every group centre for a batch of same-size templates at once.
+//
+// For one centre row cy and 128 consecutive centres along x (spacing h):
+//
+//   D[i][j] = sum_{u<m} sum_{v<Kp} A_u[i][v] * B_u[j][v]
+//   A_u[i][v] = P(cy + u, cx0 + h*i + v) - 128            (bf16, exact)
+//   B_u[j][v] = template plane j, row u                     (bf16 hi/lo split)
+//
+// with j = 2t (hi part of template t) and 2t+1 (lo part), so each template's
+// numerator is D[i][2t] + D[i][2t+1].  D lives in TMEM; the contraction over
+// (u, v) is m * Kp/16 tcgen05.mma instructions of shape 128 x N x 16.
+//
+// A_u is a Hankel operand: row i is the pivot row shifted by h*i.  It is
+// stored once per template row in the K-major "core matrix" layout without
+// swizzle: segment w (128 bytes) holds 8 copies b = 0..7 of the 8 pixels
+// starting at column cx0 + h*b + 8*w.  Element (i = 8a + b, k = 8c + d) then
+// sits at byte (h*a + c)*128 + 16*b + 2*d, i.e. a descriptor with leading
+// (K) byte offset 128 and stride (M) byte offset 128*h; core matrices
+// overlap, which costs nothing.  B_u arrives by one bulk copy from a buffer
+// already laid out as core matrices.  Two stages (A and B) overlap the build
+// of the next template row with the MMAs of the current one.
+//
+// Error bound of the numerator: the hi/lo split represents each template
+// value to within 2^-16 relative; FP32 accumulation in TMEM is bounded by
+// 4u per accumulation step (one step per MMA) -- see eps_mma below.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "tc5.cuh"
+
+namespace opta {
+
+namespace {
+
+constexpr int kMmaM = 128;
+constexpr uint64_t kWaitNs = 2000000000ull;   // every wait gives up after 2 s
+
+__host__ __device__ inline uint32_t round_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+
+struct CorrMmaArgs {
+    const uint8_t *V;          // pivot image, p x q
+    int p, q;
+    const __nv_bfloat16 *B;    // [m][Kp/8][N/8][8][8]
+    int m, n, Kp, N;
+    int h, Ly, Lx, Gx, Gx_u;   // Gx_u: leading groups whose centres are uniform (cx0 + h*i)
+    int T;                     // templates (planes 2t, 2t+1)
+    const float *c_inv_sigma;  // per group
+    const float *c_efac;       // per group: ||P - 128|| / sigma_hat
+    const TmplState *st;       // T states
+    float *rho_tc;             // [T][gstride]
+    float2 *tc;                // [T][gstride]
+    int64_t gstride;
+    int *err;
+};
+
+__device__ inline float eps_mma(int steps, float efac) {
+    // 2^-16 split error + 4u per TMEM accumulation step + final products
+    return ((float)(4 * steps + 16) * kU32 + 1.55e-5f) * 1.01f * efac + 8.f * kU32;
+}
+
+__global__ void __launch_bounds__(128, 1) corr_mma_kernel(const CorrMmaArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t *b_full = reinterpret_cast<uint64_t *>(smem);   // [2]
+    uint64_t *mma_done = b_full + 2;                         // [2]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_done + 2);
+    const int WA = 15 * a.h + a.Kp / 8;
+    const uint32_t abytes = (uint32_t)WA * 128u;
+    const uint32_t bbytes = (uint32_t)a.N * a.Kp * 2u;
+    uint8_t *Abuf[2], *Bbuf[2];
+    Abuf[0] = smem + 1024;
+    Abuf[1] = Abuf[0] + round_up(abytes, 1024);
+    Bbuf[0] = Abuf[1] + round_up(abytes, 1024);
+    Bbuf[1] = Bbuf[0] + round_up(bbytes, 1024);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int gy = blockIdx.y;
+    const int gx0 = blockIdx.x * kMmaM;
+    const int cy = group_centre_of(gy, a.Ly, a.h);
+    const int cx0 = group_centre_of(gx0, a.Lx, a.h);
+
+    uint32_t ncols = 32;
+    while ((int)ncols < a.N) ncols <<= 1;
+    if (tid == 0) {
+        tc5::mbar_init(&b_full[0], 1);
+        tc5::mbar_init(&b_full[1], 1);
+        tc5::mbar_init(&mma_done[0], 1);
+        tc5::mbar_init(&mma_done[1], 1);
+        tc5::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc5::tmem_alloc(tmem_slot, ncols);
+        tc5::tmem_relinquish();
+    }
+    tc5::tc_fence_before();
+    __syncthreads();
+    tc5::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t idesc = tc5::idesc_bf16_f32(kMmaM, a.N);
+
+    bool ok = true;
+    int last_issue = -1;          // last template row whose copy/MMAs thread 0 issued
+    bool last_committed = false;
+    for (int u = 0; u < a.m; ++u) {
+        const int s = u & 1;
+        if (u >= 2 && !tc5::mbar_wait(&mma_done[s], ((u - 2) >> 1) & 1, kWaitNs)) ok = false;
+        if (!__syncthreads_and(ok)) { ok = false; break; }
+        if (tid == 0) {
+            tc5::mbar_arrive_expect_tx(&b_full[s], bbytes);
+            tc5::bulk_g2s(Bbuf[s], a.B + (size_t)u * a.N * a.Kp, bbytes, &b_full[s]);
+            last_issue = u;
+            last_committed = false;
+        }
+        // build A_u: segment w, copy b = pixels cx0 + h*b + 8w .. +7 of row cy + u
+        const uint8_t *row = a.V + (size_t)(cy + u) * a.q;
+        uint8_t *Ab = Abuf[s];
+        for (int j = tid; j < WA * 8; j += blockDim.x) {
+            const int w = j >> 3, b = j & 7;
+            const int x = cx0 + a.h * b + 8 * w;
+            uint32_t pk[4];
+#pragma unroll
+            for (int d = 0; d < 8; d += 2) {
+                const int xa = min(x + d, a.q - 1), xb = min(x + d + 1, a.q - 1);
+                const __nv_bfloat162 v2 =
+                    __floats2bfloat162_rn((float)row[xa] - 128.f, (float)row[xb] - 128.f);
+                pk[d >> 1] = *reinterpret_cast<const uint32_t *>(&v2);
+            }
+            *reinterpret_cast<uint4 *>(Ab + w * 128 + b * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+        tc5::fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            if (!tc5::mbar_wait(&b_full[s], (u >> 1) & 1, kWaitNs)) {
+                ok = false;
+            } else {
+                tc5::tc_fence_after();
+                const uint32_t abase = tc5::smem_u32(Ab), bbase = tc5::smem_u32(Bbuf[s]);
+                const uint32_t blbo = (uint32_t)(a.N / 8) * 128u;
+                for (int kk = 0; kk < a.Kp / 16; ++kk) {
+                    const uint64_t ad = tc5::smem_desc(abase + kk * 256, 128, 128u * a.h);
+                    const uint64_t bd = tc5::smem_desc(bbase + kk * 2 * blbo, blbo, 128);
+                    tc5::mma_bf16(tmem, ad, bd, idesc, (u > 0 || kk > 0));
+                }
+                tc5::mma_commit(&mma_done[s]);
+                last_committed = true;
+            }
+        }
+    }
+    // drain: thread 0 waits (bounded) for its last copy and last MMA batch
+    if (tid == 0 && last_issue >= 0) {
+        const int s = last_issue & 1;
+        const uint32_t ph = (last_issue >> 1) & 1;
+        if (last_committed) {
+            if (!tc5::mbar_wait(&mma_done[s], ph, kWaitNs)) ok = false;
+        } else {
+            tc5::mbar_wait(&b_full[s], ph, kWaitNs);
+            ok = false;
+        }
+    }
+    tc5::tc_fence_before();
+    ok = __syncthreads_and(ok) != 0;
+    tc5::tc_fence_after();
+
+    if (ok) {
+        const int i = warp * 32 + lane;                 // TMEM lane = accumulator row
+        const int gx = gx0 + i;
+        const bool valid = gx < a.Gx_u;
+        const int64_t g = (int64_t)gy * a.Gx + gx;
+        float cis = 0.f, cef = 0.f;
+        if (valid) { cis = a.c_inv_sigma[g]; cef = a.c_efac[g]; }
+        const int steps = a.m * (a.Kp / 16);
+        for (int c0 = 0; c0 < a.N; c0 += 8) {
+            float v[8];
+            tc5::tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+            for (int k = 0; k < 8; k += 2) {
+                const int t = (c0 + k) >> 1;
+                if (valid && t < a.T) {
+                    const float num = v[k] + v[k + 1];
+                    const float r = (num * a.st[t].inv_sigma) * cis;
+                    const float e = cis > 0.f ? eps_mma(steps, cef) : 0.f;
+                    a.rho_tc[t * a.gstride + g] = r;
+                    a.tc[t * a.gstride + g] = angle_interval(r, e);
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(a.err, 1);
+    }
+    tc5::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc5::tmem_dealloc(tmem, ncols);
+}
+
+// Template t' (FP32, m x npad) -> hi/lo bf16 planes 2t, 2t+1 of the B buffer.
+__global__ void tmpl_split_kernel(const float *__restrict__ tf, int m, int n, int npad, int Kp,
+                                  int N, int t, __nv_bfloat16 *B) {
+    const int total = m * Kp;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += gridDim.x * blockDim.x) {
+        const int u = idx / Kp, v = idx % Kp;
+        const float x = v < n ? tf[u * npad + v] : 0.f;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+        const int64_t base = (((int64_t)u * (Kp / 8) + v / 8) * (N / 8)) * 64 + (v % 8);
+        const int j0 = 2 * t, j1 = 2 * t + 1;
+        B[base + (int64_t)(j0 / 8) * 64 + (j0 % 8) * 8] = hi;
+        B[base + (int64_t)(j1 / 8) * 64 + (j1 % 8) * 8] = lo;
+    }
+}
+
+}  // namespace
+
+size_t corr_mma_smem(int h, int Kp, int N) {
+    const uint32_t WA = 15u * h + Kp / 8;
+    return 1024 + 2 * round_up(WA * 128u, 1024) + 2 * round_up((uint32_t)N * Kp * 2u, 1024);
+}
+
+cudaError_t launch_tmpl_split(const float *tf, int m, int n, int npad, int Kp, int N, int t,
+                              void *B, cudaStream_t s) {
+    LaunchScope ls("tmpl_split_kernel", s);
+    const int total = m * Kp;
+    tmpl_split_kernel<<<(total + 255) / 256, 256, 0, s>>>(tf, m, n, npad, Kp, N, t,
+                                                          static_cast<__nv_bfloat16 *>(B));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_corr_mma(const uint8_t *V, int p, int q, const void *B, int m, int n, int Kp,
+                            int N, int h, int Ly, int Lx, int T, const float *c_inv_sigma,
+                            const float *c_efac, const TmplState *st, float *rho_tc, float2 *tc,
+                            int64_t gstride, int *err, int *Gx_u_out, cudaStream_t s) {
+    const int Gy = groups_along(Ly, h), Gx = groups_along(Lx, h);
+    // centres along x are uniform (g*h + (h-1)/2) except possibly the last group
+    int Gx_u = Gx;
+    if (group_centre_of(Gx - 1, Lx, h) != (Gx - 1) * h + (h - 1) / 2) Gx_u = Gx - 1;
+    *Gx_u_out = Gx_u;
+    if (Gx_u <= 0) return cudaSuccess;
+    if (N % 16 != 0 || N < 16 || N > 256 || Kp % 16 != 0) return cudaErrorInvalidValue;
+    size_t smem = corr_mma_smem(h, Kp, N);
+    // never more resident CTAs per SM than TMEM can hold (512 columns): pad the
+    // shared-memory request so that 228 KB / (request + 1 KB) <= 512 / ncols
+    int ncols = 32;
+    while (ncols < N) ncols <<= 1;
+    const int max_ctas = 512 / ncols;
+    const size_t floor_req = (size_t)(228 * 1024) / (size_t)(max_ctas + 1) + 1;
+    if (smem + 1024 < floor_req) smem = floor_req - 1024 + 16;
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    static size_t attr = 0;
+    if (smem > attr) {
+        cudaError_t e = cudaFuncSetAttribute(corr_mma_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = smem;
+    }
+    CorrMmaArgs a;
+    a.V = V; a.p = p; a.q = q;
+    a.B = static_cast<const __nv_bfloat16 *>(B);
+    a.m = m; a.n = n; a.Kp = Kp; a.N = N;
+    a.h = h; a.Ly = Ly; a.Lx = Lx; a.Gx = Gx; a.Gx_u = Gx_u;
+    a.T = T;
+    a.c_inv_sigma = c_inv_sigma; a.c_efac = c_efac;
+    a.st = st; a.rho_tc = rho_tc; a.tc = tc; a.gstride = gstride; a.err = err;
+    dim3 grid((Gx_u + kMmaM - 1) / kMmaM, Gy);
+    LaunchScope ls("corr_mma_kernel", s);
+    corr_mma_kernel<<<grid, 128, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace opta

@@ -306,13 +306,13 @@ __global__ void __launch_bounds__(128)
 centre_rho_kernel(const uint8_t *__restrict__ P, int p, int q, const float *__restrict__ tf,
                   int m, int n, int npad, int h, int Ly, int Lx,
                   const float *__restrict__ c_inv_sigma, const float *__restrict__ c_efac,
-                  TmplState *st, float *rho_tc, float2 *tc, int tile_w) {
+                  TmplState *st, float *rho_tc, float2 *tc, int tile_w, int gx_begin) {
     extern __shared__ float4 csm4[];
     float *tile = reinterpret_cast<float *>(csm4);
     const int tile_rows = (CT_Y - 1) * h + CT_MT;
     float *tm = tile + tile_rows * tile_w;
     const int Gy = groups_along(Ly, h), Gx = groups_along(Lx, h);
-    const int gy0 = blockIdx.y * CT_Y, gx0 = blockIdx.x * CT_X;
+    const int gy0 = blockIdx.y * CT_Y, gx0 = gx_begin + blockIdx.x * CT_X;
     const int ty = threadIdx.x / CT_X, tx = threadIdx.x % CT_X;
     if (st->flat) return;
     const int cy0 = group_centre_of(gy0, Ly, h), cx0 = group_centre_of(gx0, Lx, h);
@@ -741,7 +741,7 @@ cudaError_t launch_final_argmax(TmplState *st, const int *cand, const double *ca
 cudaError_t launch_centre_rho(const uint8_t *P, int p, int q, const float *tf, int m, int n,
                               int npad, int h, int Ly, int Lx, const float *c_inv_sigma,
                               const float *c_efac, TmplState *st, float *rho_tc, float2 *tc,
-                              cudaStream_t s) {
+                              int gx_begin, cudaStream_t s) {
     const int Gy = groups_along(Ly, h), Gx = groups_along(Lx, h);
     const int tile_w = ((CT_X - 1) * h + CT_NT + 3) & ~3;
     const int tile_rows = (CT_Y - 1) * h + CT_MT;
@@ -753,10 +753,12 @@ cudaError_t launch_centre_rho(const uint8_t *P, int p, int q, const float *tf, i
         if (e != cudaSuccess) return e;
         attr = smem;
     }
-    dim3 grid((Gx + CT_X - 1) / CT_X, (Gy + CT_Y - 1) / CT_Y);
+    if (gx_begin >= Gx) return cudaSuccess;
+    dim3 grid((Gx - gx_begin + CT_X - 1) / CT_X, (Gy + CT_Y - 1) / CT_Y);
     LaunchScope ls_centre_rho_kernel("centre_rho_kernel", s);
     centre_rho_kernel<<<grid, CT_Y * CT_X, smem, s>>>(P, p, q, tf, m, n, npad, h, Ly, Lx,
-                                                     c_inv_sigma, c_efac, st, rho_tc, tc, tile_w);
+                                                     c_inv_sigma, c_efac, st, rho_tc, tc, tile_w,
+                                                     gx_begin);
     return cudaGetLastError();
 }
 
