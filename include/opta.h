@@ -105,7 +105,8 @@ typedef struct opta_params {
     int32_t fixed_h;        /* 0: EGS chooses h; odd h > 0: fixed group side */
     int32_t blur;           /* 1: run the OptA level loop; 0: unblurred pivots */
     int32_t topk;           /* 8: centres re-evaluated on I for the threshold (1..16) */
-    int32_t precision;      /* 0: FP32 CUDA-core products (only mode implemented) */
+    int32_t precision;      /* scan 1 (centre rho): 1 = bf16 hi/lo split products on the
+                               tensor cores, FP32 accumulation (default); 0 = FP32 CUDA cores */
     int32_t reserved[7];
 } opta_params;
 
@@ -125,7 +126,7 @@ typedef struct opta_size_info {
 
 /* Fill `prm` with the Section 7 defaults: rho_th 0.80, rho_max 0.95,
  * xi 0.005, 64-pixel blur blocks, sigma levels {0.5,1,2,3}, h_max 9, EGS
- * group sizes, blur on, top-8 threshold centres. */
+ * group sizes, blur on, top-8 threshold centres, tensor-core scan 1. */
 void opta_params_default(opta_params *prm);
 
 /* Static string for a status code (never NULL). */

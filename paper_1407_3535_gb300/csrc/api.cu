@@ -651,7 +651,7 @@ void opta_params_default(opta_params *prm) {
     prm->fixed_h = 0;
     prm->blur = 1;
     prm->topk = 8;
-    prm->precision = 0;
+    prm->precision = 1;
 }
 
 const char *opta_status_str(opta_status s) {

@@ -71,7 +71,7 @@ struct TmplState {
 
 // Survivors are bucketed by their upper bound (bucket 0 = highest) so that
 // they are evaluated roughly in decreasing bound order.
-constexpr int kUbBuckets = 32;
+constexpr int kUbBuckets = 256;
 
 // ---------------------------------------------------------------------------
 // Launchers (stream-ordered, return cudaError_t of the launch).

@@ -482,9 +482,13 @@ __global__ void threshold_kernel(TmplState *st, const double *__restrict__ cand_
 // Scan 2: interval-safe transitive bound (Eq. tranEqq in angle form) and
 // warp-ballot compaction of the locations that fail Eq. SEC.
 // ---------------------------------------------------------------------------
+// Buckets are uniform in the bound cos(gap): bucket 0 holds the largest bounds.
+// Any monotone map is valid; pass 2 recomputes it from the stored gap with the
+// same code, so both passes agree.
 __device__ inline int gap_bucket(float gap, float lim) {
     if (!(lim > 0.f)) return 0;
-    int b = (int)((gap / lim) * (float)kUbBuckets);
+    const float x = gap / lim;                 // in [0, 1]
+    int b = (int)(x * x * (float)kUbBuckets);  // ~ (1 - cos gap) / (1 - cos lim)
     return b < 0 ? 0 : (b >= kUbBuckets ? kUbBuckets - 1 : b);
 }
 
@@ -529,10 +533,23 @@ bound_hist_kernel(const float2 *__restrict__ tc, const float2 *__restrict__ thet
 // Exclusive scan of the bucket counts into write cursors; total survivors.
 __global__ void bucket_scan_kernel(TmplState *st, const int *__restrict__ bucket_cnt,
                                    int *bucket_cur) {
-    if (threadIdx.x != 0 || st->flat) return;
-    int acc = 0;
-    for (int b = 0; b < kUbBuckets; ++b) { bucket_cur[b] = acc; acc += bucket_cnt[b]; }
-    st->n_surv = acc;
+    if (st->flat) return;
+    // one warp: each lane owns kUbBuckets/32 consecutive buckets
+    constexpr int PER = kUbBuckets / 32;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x >= 32) return;
+    int loc[PER], sum = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) { loc[k] = bucket_cnt[lane * PER + k]; sum += loc[k]; }
+    int incl = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    int acc = incl - sum;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) { bucket_cur[lane * PER + k] = acc; acc += loc[k]; }
+    if (lane == 31) st->n_surv = incl;
 }
 
 // Pass 2: scatter the survivors into their bucket ranges (bucket 0 = smallest
@@ -598,10 +615,10 @@ survivors_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__r
     const double mn = (double)m * n;
     const int mnI = m * n;
     const float ist = st->inv_sigma;
-    const int kacc = (mnI + 31) / 32 + 6;
-    // lane start (u, v) in the flattened window and the per-step advance of 32 elements
-    const int du = 32 / n, dv = 32 % n;
-    const int u0 = lane / n, v0 = lane % n;
+    // accumulation depth per lane: ceil(m/4) rows x ceil(n/32) columns per chain,
+    // + 2 chain merges + 5 shuffle levels
+    const int kacc = ((m + 3) / 4) * ((n + 31) / 32) + 8 + (m % 4) * ((n + 31) / 32);
+    (void)mnI;
     volatile unsigned int *lo_key = &st->lo_key;
     int evaluated = 0;
     for (int base = warp * 32; base < ns; base += nwarps * 32) {
@@ -626,21 +643,26 @@ survivors_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__r
                            - IIQ[(int64_t)(y + m) * q1 + x] + IIQ[(int64_t)y * q1 + x];
             const float a = (float)rint(S / mn);
             const uint8_t *bp = I + (int64_t)y * q + x;
-            float acc0 = 0.f, acc1 = 0.f;
-            int u = u0, v = v0;
-            int e = lane;
-            // two independent chains over the flattened window, 32 lanes wide
-            for (; e + 32 < mnI; e += 64) {
-                const float t0 = tm[u * npad + v];
-                const float i0 = (float)bp[(int64_t)u * q + v];
-                u += du; v += dv; if (v >= n) { v -= n; ++u; }
-                const float t1 = tm[u * npad + v];
-                const float i1 = (float)bp[(int64_t)u * q + v];
-                u += du; v += dv; if (v >= n) { v -= n; ++u; }
-                acc0 = fmaf(t0, i0 - a, acc0);
-                acc1 = fmaf(t1, i1 - a, acc1);
+            float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+            // lanes over columns, four independent row chains
+            int u = 0;
+            for (; u + 4 <= m; u += 4) {
+                const uint8_t *r0 = bp + (int64_t)u * q;
+                const float *t0 = tm + u * npad;
+                for (int v = lane; v < n; v += 32) {
+                    const float i0 = (float)r0[v], i1 = (float)r0[q + v];
+                    const float i2 = (float)r0[2 * (int64_t)q + v], i3 = (float)r0[3 * (int64_t)q + v];
+                    acc0 = fmaf(t0[v], i0 - a, acc0);
+                    acc1 = fmaf(t0[npad + v], i1 - a, acc1);
+                    acc2 = fmaf(t0[2 * npad + v], i2 - a, acc2);
+                    acc3 = fmaf(t0[3 * npad + v], i3 - a, acc3);
+                }
             }
-            if (e < mnI) acc0 = fmaf(tm[u * npad + v], (float)bp[(int64_t)u * q + v] - a, acc0);
+            for (; u < m; ++u)
+                for (int v = lane; v < n; v += 32)
+                    acc0 = fmaf(tm[u * npad + v], (float)bp[(int64_t)u * q + v] - a, acc0);
+            acc0 += acc2;
+            acc1 += acc3;
             const float acc = warp_sum_f(acc0 + acc1);
             if (lane == 0) {
                 const float is = inv_sigma[idx];
