@@ -407,47 +407,73 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def roofline(prof, ts, results, size_info, shape, clocks):
-    """Roofline of the kernel with the largest share of the search pass."""
-    if not prof:
-        return None
-    pk, src = peaks()
+def kernel_roofline(name, tot_ms, nl, ts, results, shape, pk, src):
+    """Algorithmic work of one launch of `name`, divided by its average time."""
     p, q = shape
-    name, (tot_ms, nl) = max(prof.items(), key=lambda kv: kv[1][0])
-    # algorithmic work per launch
     flops = 0.0
     bytes_ = 0.0
-    kind = "alu"
+    kind = None
     for t, r in zip(ts, results):
         m, n = t.data.shape
         Ly, Lx = p - m + 1, q - n + 1
         h = r.group_h
         G = ((Ly + h - 1) // h) * ((Lx + h - 1) // h)
         if name == "survivors_kernel":
-            flops += 2.0 * m * n * r.n_survivors
+            kind = "alu"; flops += 2.0 * m * n * r.n_evaluated
         elif name == "centre_rho_kernel":
-            flops += 2.0 * m * n * G
-        elif name == "bound_compact_kernel":
+            kind = "alu"; flops += 2.0 * m * n * G
+        elif name == "corr_mma_kernel":
+            kind = "tensor"; flops += 2.0 * 2.0 * m * n * G       # hi and lo products
+        elif name in ("bound_hist_kernel", "bound_scatter_kernel"):
             kind = "hbm"
-            bytes_ += 4.0 * Ly * Lx + 8.0 * G + 4.0 * r.n_survivors
+            if name == "bound_hist_kernel":
+                bytes_ += 8.0 * Ly * Lx + 4.0 * Ly * Lx + 8.0 * G
+            else:
+                bytes_ += 4.0 * Ly * Lx + 8.0 * r.n_survivors
         elif name == "zncc_map_kernel":
-            flops += 2.0 * m * n * Ly * Lx
+            kind = "alu"; flops += 2.0 * m * n * Ly * Lx
+    if kind is None:
+        return None
     avg_s = (tot_ms / nl) / 1000.0
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
     if kind == "hbm":
         achieved = bytes_ / nl / avg_s / 1e9
         peak = pk.get("hbm_gbs", 6800.0)
-        unit = "GB/s"
-        note = f"HBM copy bandwidth ({src})"
+        unit, note = "GB/s", f"HBM copy bandwidth ({src})"
+    elif kind == "tensor":
+        achieved = flops / nl / avg_s / 1e12
+        peak = pk.get("bf16_tflops", 1900.0)
+        unit, note = "TFLOP/s", f"dense bf16 cuBLAS burst ({src})"
     else:
         achieved = flops / nl / avg_s / 1e12
-        # FP32 FMA pipe: 152 SMs x 128 lanes x 2 flops x max SM clock
         peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
         unit = "TFLOP/s"
         note = f"FP32 FMA peak from 152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz ({src} clock)"
     return {"kernel": name, "bound": kind, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak if peak else None, "traffic": None,
             "launches": nl, "avg_launch_ms": tot_ms / nl, "peak_source": note}
+
+
+def roofline(prof, ts, results, size_info, shape, clocks):
+    """Roofline of the kernel with the largest share of the search pass, plus
+    the other main kernels under `others`."""
+    if not prof:
+        return None
+    pk, src = peaks()
+    order = sorted(prof.items(), key=lambda kv: -kv[1][0])
+    main = None
+    others = []
+    for name, (tot_ms, nl) in order:
+        r = kernel_roofline(name, tot_ms, nl, ts, results, shape, pk, src)
+        if r is None:
+            continue
+        if main is None:
+            main = r
+        else:
+            others.append(r)
+    if main is not None:
+        main["others"] = others
+    return main
 
 
 if __name__ == "__main__":

@@ -517,11 +517,9 @@ opta_status enqueue_scan1(opta_handle *H, const opta_template *const *t, int n, 
         CK(launch_corr_mma(S->P, H->p, H->q, H->Bmma, m, nn, Kp, N, S->h, S->Ly, S->Lx, n,
                            S->c_inv_sigma, S->c_efac, st, H->rho_tc, H->tc, G, H->dev_err,
                            &Gx_u, s));
-        if (Gx_u < S->Gx)
-            for (int k = 0; k < n; ++k)
-                CK(launch_centre_rho(S->P, H->p, H->q, H->tf + k * tsz, m, nn, npad, S->h, S->Ly,
-                                     S->Lx, S->c_inv_sigma, S->c_efac, st + k, H->rho_tc + k * G,
-                                     H->tc + k * G, Gx_u, s));
+        for (int gx = Gx_u; gx < S->Gx; ++gx)
+            CK(launch_centre_column(S->P, H->q, H->tf, m, nn, npad, tsz, S->h, S->Ly, S->Lx, gx, n,
+                                    S->c_inv_sigma, S->c_efac, st, H->rho_tc, H->tc, G, s));
     } else {
         for (int k = 0; k < n; ++k)
             CK(launch_centre_rho(S->P, H->p, H->q, H->tf + k * tsz, m, nn, npad, S->h, S->Ly,

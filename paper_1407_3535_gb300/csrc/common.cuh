@@ -124,6 +124,11 @@ cudaError_t launch_corr_mma(const uint8_t *V, int p, int q, const void *B, int m
                             int N, int h, int Ly, int Lx, int T, const float *c_inv_sigma,
                             const float *c_efac, const TmplState *st, float *rho_tc, float2 *tc,
                             int64_t gstride, int *err, int *Gx_u_out, cudaStream_t s);
+// rho_tc of one group column for a chunk of templates (warp per centre).
+cudaError_t launch_centre_column(const uint8_t *P, int q, const float *tf, int m, int n, int npad,
+                                 size_t tsz, int h, int Ly, int Lx, int gx, int T,
+                                 const float *c_inv_sigma, const float *c_efac, const TmplState *st,
+                                 float *rho_tc, float2 *tc, int64_t gstride, cudaStream_t s);
 cudaError_t launch_tmpl_split(const float *tf, int m, int n, int npad, int Kp, int N, int t,
                               void *B, cudaStream_t s);
 cudaError_t launch_topk(const float *rho_tc, int Gy, int Gx, int h, int Ly, int Lx, int k,

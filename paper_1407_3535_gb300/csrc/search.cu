@@ -362,6 +362,40 @@ centre_rho_kernel(const uint8_t *__restrict__ P, int p, int q, const float *__re
     }
 }
 
+// rho(t_k, pivot) at the centres of one group column gx (all group rows) for a
+// chunk of templates: one warp per (template, centre).  Used for the last
+// column when its centre is off the uniform grid the tensor-core path covers.
+__global__ void __launch_bounds__(256)
+centre_column_kernel(const uint8_t *__restrict__ P, int q, const float *__restrict__ tf, int m,
+                     int n, int npad, size_t tsz, int h, int Ly, int Lx, int gx, int T,
+                     const float *__restrict__ c_inv_sigma, const float *__restrict__ c_efac,
+                     const TmplState *__restrict__ st, float *rho_tc, float2 *tc, int64_t gstride) {
+    const int Gy = groups_along(Ly, h), Gx = groups_along(Lx, h);
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int cx = group_centre_of(gx, Lx, h);
+    const int kacc = m * ((n + 31) / 32) + 6;
+    for (int w = warp; w < T * Gy; w += nwarps) {
+        const int k = w / Gy, gy = w % Gy;
+        const int cy = group_centre_of(gy, Ly, h);
+        const float *tm = tf + (size_t)k * tsz;
+        const uint8_t *bp = P + (int64_t)cy * q + cx;
+        float acc = 0.f;
+        for (int u = 0; u < m; ++u)
+            for (int v = lane; v < n; v += 32)
+                acc = fmaf(tm[u * npad + v], (float)bp[(int64_t)u * q + v] - 128.f, acc);
+        acc = warp_sum_f(acc);
+        if (lane == 0) {
+            const int64_t g = (int64_t)gy * Gx + gx;
+            const float is = c_inv_sigma[g];
+            const float r = (acc * st[k].inv_sigma) * is;
+            rho_tc[k * gstride + g] = r;
+            tc[k * gstride + g] = angle_interval(r, is > 0.f ? eps_bound(kacc, c_efac[g]) : 0.f);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Threshold centres: approximate top-k of rho_tc (any k achieved values give a
 // valid threshold; Section 6 uses the single best centre).
@@ -552,32 +586,50 @@ __global__ void bucket_scan_kernel(TmplState *st, const int *__restrict__ bucket
     if (lane == 31) st->n_surv = incl;
 }
 
-// Pass 2: scatter the survivors into their bucket ranges (bucket 0 = smallest
-// gap first) together with their upper bound cos(gap) + margin.
+// Pass 2: scatter the survivors into their bucket ranges (bucket 0 = largest
+// bound first) together with their upper bound cos(gap) + margin.  Each block
+// takes chunks of 256 x SC_PER locations, counts them per bucket in shared
+// memory, reserves every bucket's slice with one global atomic, then writes.
+constexpr int SC_PER = 16;
 __global__ void __launch_bounds__(256)
 bound_scatter_kernel(const float *__restrict__ gap_in, int64_t L, TmplState *st, int *surv,
                      float *surv_ub, int cap, int *bucket_cur) {
+    __shared__ int cnt[kUbBuckets];
+    __shared__ int basep[kUbBuckets];
     if (st->flat) return;
     const float lim = st->theta_lim;
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < L; base += stride) {
-        const int64_t i = base + threadIdx.x;
-        const float gap = i < L ? gap_in[i] : 4.f;
-        const bool f = gap <= lim;
-        const int b = f ? gap_bucket(gap, lim) : -1;
-        const unsigned act = __ballot_sync(0xffffffffu, f);
-        if (!act) continue;
-        const unsigned peers = __match_any_sync(0xffffffffu, b);
-        if (f) {
-            const int leader = __ffs(peers) - 1;
-            int pos = 0;
-            if (lane == leader) pos = atomicAdd(&bucket_cur[b], __popc(peers));
-            pos = __shfl_sync(peers, pos, leader);
-            pos += __popc(peers & ((1u << lane) - 1u));
-            if (pos < cap) { surv[pos] = (int)i; surv_ub[pos] = cosf(gap) + kCosMargin; }
-            else atomicOr(&st->overflow, 1);
+    const int64_t chunk = 256 * SC_PER;
+    for (int64_t c0 = (int64_t)blockIdx.x * chunk; c0 < L; c0 += (int64_t)gridDim.x * chunk) {
+        for (int b = threadIdx.x; b < kUbBuckets; b += blockDim.x) cnt[b] = 0;
+        __syncthreads();
+        float g[SC_PER];
+        int bk[SC_PER];
+#pragma unroll
+        for (int k = 0; k < SC_PER; ++k) {
+            const int64_t i = c0 + k * 256 + threadIdx.x;
+            g[k] = i < L ? gap_in[i] : 4.f;
+            bk[k] = g[k] <= lim ? gap_bucket(g[k], lim) : -1;
+            if (bk[k] >= 0) atomicAdd(&cnt[bk[k]], 1);
         }
+        __syncthreads();
+        for (int b = threadIdx.x; b < kUbBuckets; b += blockDim.x) {
+            const int c = cnt[b];
+            basep[b] = c ? atomicAdd(&bucket_cur[b], c) : 0;
+            cnt[b] = 0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < SC_PER; ++k) {
+            if (bk[k] < 0) continue;
+            const int pos = basep[bk[k]] + atomicAdd(&cnt[bk[k]], 1);
+            if (pos < cap) {
+                surv[pos] = (int)(c0 + k * 256 + threadIdx.x);
+                surv_ub[pos] = cosf(g[k]) + kCosMargin;
+            } else {
+                atomicOr(&st->overflow, 1);
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -791,6 +843,17 @@ int topk_blocks(int G) {
     return nb;
 }
 
+cudaError_t launch_centre_column(const uint8_t *P, int q, const float *tf, int m, int n, int npad,
+                                 size_t tsz, int h, int Ly, int Lx, int gx, int T,
+                                 const float *c_inv_sigma, const float *c_efac, const TmplState *st,
+                                 float *rho_tc, float2 *tc, int64_t gstride, cudaStream_t s) {
+    const int Gy = groups_along(Ly, h);
+    LaunchScope ls("centre_column_kernel", s);
+    centre_column_kernel<<<grid_cap((int64_t)T * Gy * 32, 256, 8), 256, 0, s>>>(
+        P, q, tf, m, n, npad, tsz, h, Ly, Lx, gx, T, c_inv_sigma, c_efac, st, rho_tc, tc, gstride);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_topk(const float *rho_tc, int Gy, int Gx, int h, int Ly, int Lx, int k,
                         TmplState *st, float *tmp_val, int *tmp_idx, int *cand, cudaStream_t s) {
     const int G = Gy * Gx;
@@ -837,8 +900,8 @@ cudaError_t launch_bound_compact(const float2 *tc, const float2 *theta_co, int L
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
         LaunchScope ls("bound_scatter_kernel", s);
-        bound_scatter_kernel<<<grid_cap(L, 256, 8), 256, 0, s>>>(gap, L, st, surv, surv_ub, cap,
-                                                                bucket_cur);
+        bound_scatter_kernel<<<grid_cap((L + SC_PER - 1) / SC_PER, 256, 4), 256, 0, s>>>(
+            gap, L, st, surv, surv_ub, cap, bucket_cur);
     }
     return cudaGetLastError();
 }
