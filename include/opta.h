@@ -50,7 +50,8 @@ typedef enum opta_status {
     OPTA_ERR_CUDA = 4,          /* any other CUDA runtime error */
     OPTA_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
     OPTA_ERR_BUSY = 6,          /* handle in use */
-    OPTA_ERR_UNSUPPORTED = 7    /* input outside the supported domain (see optA_prepare) */
+    OPTA_ERR_UNSUPPORTED = 7,   /* input outside the supported domain (see optA_prepare) */
+    OPTA_ERR_TOO_LARGE = 8      /* problem larger than zncc_full_noalloc's fixed scratch */
 } opta_status;
 
 typedef enum opta_dtype {
@@ -168,6 +169,27 @@ opta_status optA_search(opta_handle *h, const opta_template *t, int32_t n_t,
  */
 opta_status zncc_full(const opta_image *img, const opta_template *t,
                       float *rho_map, opta_result *best, void *stream);
+
+/*
+ * zncc_full without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * while they search (a framework allocator owns the device heap, a
+ * real-time loop must not call cudaMalloc/cudaFree, which may synchronise
+ * the device, or a fixed memory budget).  Same arguments, results and
+ * image domain as zncc_full.
+ *
+ * Scratch: one ~12 MB array in the library's device memory, held by every
+ * GPU that loads the library until the process exits.  Limits: p, q <= 4096
+ * with p*q <= 262144 pixels, and m * round_up(n, 8) <= 4096 template
+ * elements; larger problems return OPTA_ERR_TOO_LARGE before touching the
+ * GPU.  The first call on each device looks up the array's device address
+ * (on that device, which must be current); make that first call before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * (e.g. from two streams or threads) race and must be serialised by the
+ * caller.  Calls no cudaMalloc/cudaFree.  Synchronises `stream`.
+ */
+opta_status zncc_full_noalloc(const opta_image *img, const opta_template *t,
+                              float *rho_map, opta_result *best, void *stream);
 
 /*
  * Elimination test of one template over the full location map, for

@@ -16,6 +16,7 @@ from ._lib import OptaImage, OptaParams, OptaResult, OptaSizeInfo, OptaTemplate,
 
 __all__ = [
     "OptaError", "opta_params_default", "optA_prepare", "optA_search", "zncc_full",
+    "zncc_full_noalloc",
     "optA_debug_bounds", "optA_size_info", "optA_memory_bytes", "optA_destroy",
     "optA_debug_maps", "opta_dbg_window_stats", "opta_dbg_blur", "opta_dbg_blur_corr",
     "opta_dbg_rho_co", "opta_dbg_launch_count", "opta_dbg_profile_enable",
@@ -185,6 +186,22 @@ def zncc_full(image, template, rho_map=None, stream=None, check: bool = True) ->
     del k1, k2
     if check and code not in (0, 2):
         raise OptaError(code, "zncc_full")
+    return res
+
+
+def zncc_full_noalloc(image, template, rho_map=None, stream=None, check: bool = True) -> OptaResult:
+    """zncc_full on the library's fixed device scratch: no device allocation.
+
+    For callers that must not allocate device memory during a search (see
+    include/opta.h for the limits and the one-time set-up per device)."""
+    img, k1 = _image(image)
+    t, k2 = _template(template)
+    res = OptaResult()
+    ptr = c_void_p(rho_map.data_ptr()) if rho_map is not None else c_void_p(0)
+    code = lib().zncc_full_noalloc(byref(img), byref(t), ptr, byref(res), _stream(stream))
+    del k1, k2
+    if check and code not in (0, 2):
+        raise OptaError(code, "zncc_full_noalloc")
     return res
 
 

@@ -17,6 +17,7 @@ OPTA_U8, OPTA_F32 = 0, 1
 STATUS = {
     0: "OPTA_OK", 1: "OPTA_ERR_INVALID_ARG", 2: "OPTA_ERR_FLAT_TEMPLATE", 3: "OPTA_ERR_OOM",
     4: "OPTA_ERR_CUDA", 5: "OPTA_ERR_TIMEOUT", 6: "OPTA_ERR_BUSY", 7: "OPTA_ERR_UNSUPPORTED",
+    8: "OPTA_ERR_TOO_LARGE",
 }
 
 
@@ -66,6 +67,8 @@ SIGNATURES = {
                               c_void_p]),
     "zncc_full": (c_int32, [POINTER(OptaImage), POINTER(OptaTemplate), c_void_p,
                             POINTER(OptaResult), c_void_p]),
+    "zncc_full_noalloc": (c_int32, [POINTER(OptaImage), POINTER(OptaTemplate), c_void_p,
+                                    POINTER(OptaResult), c_void_p]),
     "optA_debug_bounds": (c_int32, [c_void_p, POINTER(OptaTemplate), c_void_p, c_void_p, c_void_p]),
     "optA_size_info": (c_int32, [c_void_p, c_int32, c_int32, POINTER(OptaSizeInfo)]),
     "optA_memory_bytes": (c_int32, [c_void_p, POINTER(c_size_t)]),

@@ -662,6 +662,7 @@ const char *opta_status_str(opta_status s) {
         case OPTA_ERR_TIMEOUT: return "timeout";
         case OPTA_ERR_BUSY: return "handle busy";
         case OPTA_ERR_UNSUPPORTED: return "unsupported input";
+        case OPTA_ERR_TOO_LARGE: return "problem exceeds the fixed scratch of the no-alloc entry point";
     }
     return "unknown status";
 }
