@@ -546,6 +546,8 @@ opta_status enqueue_scan2(opta_handle *H, const opta_template *const *t, int n, 
                        H->topk_v, H->topk_i, H->cand, s));
         CK(launch_refine64(H->I8, H->q, S->Lx, td, m, nn, sk, H->cand, H->cand_rho,
                            capL + kTopkMax, true, s));
+        CK(launch_group_members(H->I8, H->q, S->Ly, S->Lx, S->h, H->IIS, H->IIQ, tf, m, nn, npad,
+                                S->inv_sigma, sk, H->cand, H->prm.topk, s));
         CK(launch_threshold(sk, H->cand_rho, s));
         CK(launch_bound_compact(H->tc + k * G, S->theta_co, S->Ly, S->Lx, S->h, sk, H->surv,
                                 H->surv_ub, capL, H->ubbuf, ub_map, surv_map, H->bucket_cnt,

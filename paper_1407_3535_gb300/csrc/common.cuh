@@ -135,6 +135,11 @@ cudaError_t launch_topk(const float *rho_tc, int Gy, int Gx, int h, int Ly, int 
                         TmplState *st, float *tmp_val, int *tmp_idx, int *cand,
                         cudaStream_t s);
 cudaError_t launch_threshold(TmplState *st, const double *cand_rho, cudaStream_t s);
+// FP32 rho at the members of the threshold centres' groups (raises lo_key).
+cudaError_t launch_group_members(const uint8_t *I, int q, int Ly, int Lx, int h, const double *IIS,
+                                 const double *IIQ, const float *tf, int m, int n, int npad,
+                                 const float *inv_sigma, TmplState *st, const int *cand, int topk,
+                                 cudaStream_t s);
 // Scan 2: angular gap of every location into gap (L floats), bucket histogram
 // of the survivors, then compaction of the survivors in bucket order with
 // their upper bound; ub_map / surv_map (nullable) receive the full maps.

@@ -505,7 +505,9 @@ __global__ void threshold_kernel(TmplState *st, const double *__restrict__ cand_
     double thr = -2.0;
     for (int c = 0; c < st->n_topk; ++c) thr = fmax(thr, cand_rho[c]);
     st->thr = thr;
-    const float lo = __double2float_rd(thr - 1e-9);
+    // certain lower bound of the maximum: the exact threshold centres, or any
+    // FP32 rho minus its error bound evaluated so far (group members)
+    const float lo = fmaxf(__double2float_rd(thr - 1e-9), key_float(st->lo_key));
     st->thr_lo = lo;
     st->lo_key = max(st->lo_key, float_key(lo));
     // cos(gap) + kCosMargin >= thr_lo  <=>  gap <= acos(thr_lo - kCosMargin)
@@ -644,39 +646,87 @@ __global__ void theta_co_kernel(const float *__restrict__ rho_co, int64_t L, flo
 // Exact-ish rho (FP32, per-window centring v = I - rint(mu_o)) at the survivors;
 // one warp per survivor, template in shared memory when it fits.
 // ---------------------------------------------------------------------------
+// rho at location idx in FP32 with per-window centring v = I - rint(mu_o), by
+// the whole warp (lanes over columns, four row chains), and its error bound.
+// Results are valid in lane 0.
+__device__ inline void warp_rho32(const uint8_t *__restrict__ I, int q, int Lx,
+                                  const double *__restrict__ IIS, const double *__restrict__ IIQ,
+                                  const float *__restrict__ tm, int m, int n, int npad,
+                                  const float *__restrict__ inv_sigma, float ist, int idx,
+                                  float &rho, float &eps) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q1 = q + 1;
+    const double mn = (double)m * n;
+    const int y = idx / Lx, x = idx % Lx;
+    const double S = IIS[(int64_t)(y + m) * q1 + x + n] - IIS[(int64_t)y * q1 + x + n]
+                   - IIS[(int64_t)(y + m) * q1 + x] + IIS[(int64_t)y * q1 + x];
+    const double Q = IIQ[(int64_t)(y + m) * q1 + x + n] - IIQ[(int64_t)y * q1 + x + n]
+                   - IIQ[(int64_t)(y + m) * q1 + x] + IIQ[(int64_t)y * q1 + x];
+    const float a = (float)rint(S / mn);
+    const uint8_t *bp = I + (int64_t)y * q + x;
+    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+    int u = 0;
+    for (; u + 4 <= m; u += 4) {
+        const uint8_t *r0 = bp + (int64_t)u * q;
+        const float *t0 = tm + u * npad;
+        for (int v = lane; v < n; v += 32) {
+            const float i0 = (float)r0[v], i1 = (float)r0[q + v];
+            const float i2 = (float)r0[2 * (int64_t)q + v], i3 = (float)r0[3 * (int64_t)q + v];
+            acc0 = fmaf(t0[v], i0 - a, acc0);
+            acc1 = fmaf(t0[npad + v], i1 - a, acc1);
+            acc2 = fmaf(t0[2 * npad + v], i2 - a, acc2);
+            acc3 = fmaf(t0[3 * npad + v], i3 - a, acc3);
+        }
+    }
+    for (; u < m; ++u)
+        for (int v = lane; v < n; v += 32)
+            acc0 = fmaf(tm[u * npad + v], (float)bp[(int64_t)u * q + v] - a, acc0);
+    const float acc = warp_sum_f((acc0 + acc2) + (acc1 + acc3));
+    rho = 0.f;
+    eps = 0.f;
+    if (lane == 0) {
+        // accumulation depth per lane: ceil(m/4) rows x ceil(n/32) columns per
+        // chain (+ the remainder rows), 2 chain merges, 5 shuffle levels
+        const int kacc = ((m + 3) / 4 + (m % 4)) * ((n + 31) / 32) + 8;
+        const float is = inv_sigma[idx];
+        rho = (acc * ist) * is;
+        if (is > 0.f) {
+            const double var = mn * Q - S * S;
+            const double da = (double)a;
+            const double c2 = Q - 2.0 * da * S + mn * da * da;   // sum (I - a)^2
+            eps = eps_bound(kacc, (float)sqrt(mn * c2 / var));
+        }
+    }
+}
+
+__device__ inline const float *stage_template(const float *tf, int m, int npad, int in_smem,
+                                              float *tsm) {
+    if (!in_smem) return tf;
+    for (int i = threadIdx.x; i < m * npad; i += blockDim.x) tsm[i] = tf[i];
+    __syncthreads();
+    return tsm;
+}
+
+// Survivors [s_begin, min(n_surv, s_end)) in bucket order, skipping those whose
+// bound has fallen below the running certain lower bound of the maximum.
 __global__ void __launch_bounds__(256)
 survivors_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__restrict__ IIS,
                  const double *__restrict__ IIQ, const float *__restrict__ tf, int m, int n,
                  int npad, const float *__restrict__ inv_sigma, TmplState *st,
                  const int *__restrict__ surv, const float *__restrict__ surv_ub, float *surv_rho,
-                 float *surv_eps, int cap, int tmpl_in_smem) {
+                 float *surv_eps, int cap, int tmpl_in_smem, int s_begin, int s_end) {
     extern __shared__ float4 ssm4[];
-    float *tsm = reinterpret_cast<float *>(ssm4);
     if (st->flat) return;
-    const float *tm = tf;
-    if (tmpl_in_smem) {
-        for (int i = threadIdx.x; i < m * npad; i += blockDim.x) tsm[i] = tf[i];
-        __syncthreads();
-        tm = tsm;
-    }
-    const int ns = min(st->n_surv, cap);
+    const float *tm = stage_template(tf, m, npad, tmpl_in_smem, reinterpret_cast<float *>(ssm4));
+    const int ns = min(min(st->n_surv, cap), s_end);
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int64_t q1 = q + 1;
-    const double mn = (double)m * n;
-    const int mnI = m * n;
     const float ist = st->inv_sigma;
-    // accumulation depth per lane: ceil(m/4) rows x ceil(n/32) columns per chain,
-    // + 2 chain merges + 5 shuffle levels
-    const int kacc = ((m + 3) / 4) * ((n + 31) / 32) + 8 + (m % 4) * ((n + 31) / 32);
-    (void)mnI;
     volatile unsigned int *lo_key = &st->lo_key;
     int evaluated = 0;
-    for (int base = warp * 32; base < ns; base += nwarps * 32) {
-        // running threshold: a location whose bound is below a certain lower
-        // bound of the maximum cannot be the best match (Eq. SEC with the best
-        // rho_tb found so far); check 32 survivors at once
+    for (int base = s_begin + warp * 32; base < ns; base += nwarps * 32) {
+        // running threshold (Eq. SEC with the best rho_tb found so far); 32 at a time
         float lim = key_float(*lo_key);
         lim = __shfl_sync(0xffffffffu, lim, 0);
         const int sl = base + lane;
@@ -687,45 +737,9 @@ survivors_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__r
             const int s = base + j;
             lim = __shfl_sync(0xffffffffu, key_float(*lo_key), 0);
             if (surv_ub[s] < lim) continue;
-            const int idx = surv[s];
-            const int y = idx / Lx, x = idx % Lx;
-            const double S = IIS[(int64_t)(y + m) * q1 + x + n] - IIS[(int64_t)y * q1 + x + n]
-                           - IIS[(int64_t)(y + m) * q1 + x] + IIS[(int64_t)y * q1 + x];
-            const double Q = IIQ[(int64_t)(y + m) * q1 + x + n] - IIQ[(int64_t)y * q1 + x + n]
-                           - IIQ[(int64_t)(y + m) * q1 + x] + IIQ[(int64_t)y * q1 + x];
-            const float a = (float)rint(S / mn);
-            const uint8_t *bp = I + (int64_t)y * q + x;
-            float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
-            // lanes over columns, four independent row chains
-            int u = 0;
-            for (; u + 4 <= m; u += 4) {
-                const uint8_t *r0 = bp + (int64_t)u * q;
-                const float *t0 = tm + u * npad;
-                for (int v = lane; v < n; v += 32) {
-                    const float i0 = (float)r0[v], i1 = (float)r0[q + v];
-                    const float i2 = (float)r0[2 * (int64_t)q + v], i3 = (float)r0[3 * (int64_t)q + v];
-                    acc0 = fmaf(t0[v], i0 - a, acc0);
-                    acc1 = fmaf(t0[npad + v], i1 - a, acc1);
-                    acc2 = fmaf(t0[2 * npad + v], i2 - a, acc2);
-                    acc3 = fmaf(t0[3 * npad + v], i3 - a, acc3);
-                }
-            }
-            for (; u < m; ++u)
-                for (int v = lane; v < n; v += 32)
-                    acc0 = fmaf(tm[u * npad + v], (float)bp[(int64_t)u * q + v] - a, acc0);
-            acc0 += acc2;
-            acc1 += acc3;
-            const float acc = warp_sum_f(acc0 + acc1);
+            float rho, eps;
+            warp_rho32(I, q, Lx, IIS, IIQ, tm, m, n, npad, inv_sigma, ist, surv[s], rho, eps);
             if (lane == 0) {
-                const float is = inv_sigma[idx];
-                const float rho = (acc * ist) * is;
-                float eps = 0.f;
-                if (is > 0.f) {
-                    const double var = mn * Q - S * S;
-                    const double da = (double)a;
-                    const double c2 = Q - 2.0 * da * S + mn * da * da;   // sum (I - a)^2
-                    eps = eps_bound(kacc, (float)sqrt(mn * c2 / var));
-                }
                 surv_rho[s] = rho;
                 surv_eps[s] = eps;
                 atomicMax(&st->lo_key, float_key(rho - eps));
@@ -734,6 +748,34 @@ survivors_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__r
         }
     }
     if (lane == 0 && evaluated) atomicAdd(&st->n_eval, evaluated);
+}
+
+// Threshold refinement: FP32 rho at every member of the groups of the
+// threshold centres (the best match usually lies in the group of one of
+// them); raises the certain lower bound of the maximum before scan 2.
+__global__ void __launch_bounds__(256)
+group_members_kernel(const uint8_t *__restrict__ I, int q, int Ly, int Lx, int h,
+                     const double *__restrict__ IIS, const double *__restrict__ IIQ,
+                     const float *__restrict__ tf, int m, int n, int npad,
+                     const float *__restrict__ inv_sigma, TmplState *st,
+                     const int *__restrict__ cand, int tmpl_in_smem) {
+    extern __shared__ float4 gsm4[];
+    if (st->flat) return;
+    const float *tm = stage_template(tf, m, npad, tmpl_in_smem, reinterpret_cast<float *>(gsm4));
+    const int k = blockIdx.x;
+    if (k >= st->n_topk) return;
+    const int c = cand[k];
+    const int gy = (c / Lx) / h, gx = (c % Lx) / h;
+    const int y0 = gy * h, x0 = gx * h;
+    const int hy = min(h, Ly - y0), hx = min(h, Lx - x0);
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const float ist = st->inv_sigma;
+    for (int j = warp; j < hy * hx; j += nw) {
+        const int idx = (y0 + j / hx) * Lx + x0 + j % hx;
+        float rho, eps;
+        warp_rho32(I, q, Lx, IIS, IIQ, tm, m, n, npad, inv_sigma, ist, idx, rho, eps);
+        if ((threadIdx.x & 31) == 0) atomicMax(&st->lo_key, float_key(rho - eps));
+    }
 }
 
 __global__ void surv_candidates_kernel(TmplState *st, const int *__restrict__ surv,
@@ -912,14 +954,19 @@ cudaError_t launch_theta_co(const float *rho_co, int64_t L, float2 *theta_co, cu
     return cudaGetLastError();
 }
 
+static size_t tmpl_smem(int m, int npad, int *in_smem) {
+    size_t smem = (size_t)m * npad * sizeof(float);
+    *in_smem = smem <= 200 * 1024;
+    return *in_smem ? smem : 0;
+}
+
 cudaError_t launch_survivors(const uint8_t *I, int q, int Lx, const double *IIS,
                              const double *IIQ, const float *tf, int m, int n, int npad,
                              const float *inv_sigma, TmplState *st, const int *surv,
                              const float *surv_ub, float *surv_rho, float *surv_eps, int cap,
                              cudaStream_t s) {
-    size_t smem = (size_t)m * npad * sizeof(float);
-    int in_smem = smem <= 200 * 1024;
-    if (!in_smem) smem = 0;
+    int in_smem = 0;
+    const size_t smem = tmpl_smem(m, npad, &in_smem);
     static size_t attr = 0;
     if (smem > attr) {
         cudaError_t e = cudaFuncSetAttribute(survivors_kernel,
@@ -927,10 +974,43 @@ cudaError_t launch_survivors(const uint8_t *I, int q, int Lx, const double *IIS,
         if (e != cudaSuccess) return e;
         attr = smem;
     }
-    LaunchScope ls_survivors_kernel("survivors_kernel", s);
-    survivors_kernel<<<num_sms() * 4, 256, smem, s>>>(I, q, Lx, IIS, IIQ, tf, m, n, npad,
-                                                      inv_sigma, st, surv, surv_ub, surv_rho,
-                                                      surv_eps, cap, in_smem);
+    // priority phase: the first (largest-bound) survivors with few warps, so
+    // the running threshold rises before the whole GPU sweeps the rest
+    constexpr int kPriority = 2048;
+    {
+        LaunchScope ls("survivors_kernel", s);
+        survivors_kernel<<<16, 256, smem, s>>>(I, q, Lx, IIS, IIQ, tf, m, n, npad, inv_sigma, st,
+                                               surv, surv_ub, surv_rho, surv_eps, cap, in_smem, 0,
+                                               kPriority);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    {
+        LaunchScope ls("survivors_kernel", s);
+        survivors_kernel<<<num_sms() * 4, 256, smem, s>>>(I, q, Lx, IIS, IIQ, tf, m, n, npad,
+                                                          inv_sigma, st, surv, surv_ub, surv_rho,
+                                                          surv_eps, cap, in_smem, kPriority,
+                                                          0x7fffffff);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_members(const uint8_t *I, int q, int Ly, int Lx, int h, const double *IIS,
+                                 const double *IIQ, const float *tf, int m, int n, int npad,
+                                 const float *inv_sigma, TmplState *st, const int *cand, int topk,
+                                 cudaStream_t s) {
+    int in_smem = 0;
+    const size_t smem = tmpl_smem(m, npad, &in_smem);
+    static size_t attr = 0;
+    if (smem > attr) {
+        cudaError_t e = cudaFuncSetAttribute(group_members_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = smem;
+    }
+    LaunchScope ls("group_members_kernel", s);
+    group_members_kernel<<<topk, 256, smem, s>>>(I, q, Ly, Lx, h, IIS, IIQ, tf, m, n, npad,
+                                                 inv_sigma, st, cand, in_smem);
     return cudaGetLastError();
 }
 
