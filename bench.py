@@ -358,6 +358,16 @@ def main():
         v, cores, desc = oracle_sample_rate(img, ts_all, seconds=12.0)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
 
+    per_size = {}
+    for t, r in zip(ts, res_prof):
+        k = f"{t.data.shape[0]}x{t.data.shape[1]}"
+        d = per_size.setdefault(k, {"templates": 0, "survivor_frac": 0.0, "evaluated_frac": 0.0})
+        d["templates"] += 1
+        d["survivor_frac"] += r.n_survivors / r.n_locations
+        d["evaluated_frac"] += r.n_evaluated / r.n_locations
+    for d in per_size.values():
+        d["survivor_frac"] /= d["templates"]
+        d["evaluated_frac"] /= d["templates"]
     surv = [r.n_survivors / r.n_locations for r in res_prof]
     evald = [r.n_evaluated / r.n_locations for r in res_prof]
     line = {
@@ -387,6 +397,7 @@ def main():
         "brute_force": brute,
         "kernels_ms": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
         "group_sizes": {k: v["group_h"] for k, v in size_info.items()},
+        "per_size": per_size,
         "blur_levels": {k: v["level"] for k, v in size_info.items()},
     }
     if cpu is not None:

@@ -552,7 +552,7 @@ opta_status enqueue_scan2(opta_handle *H, const opta_template *const *t, int n, 
         CK(launch_bound_compact(H->tc + k * G, S->theta_co, S->Ly, S->Lx, S->h, sk, H->surv,
                                 H->surv_ub, capL, H->ubbuf, ub_map, surv_map, H->bucket_cnt,
                                 H->bucket_cur, s));
-        CK(launch_survivors(H->I8, H->q, S->Lx, H->IIS, H->IIQ, tf, m, nn, npad, S->inv_sigma, sk,
+        CK(launch_survivors(H->I8, H->p, H->q, S->Lx, H->IIS, H->IIQ, tf, m, nn, npad, S->inv_sigma, sk,
                             H->surv, H->surv_ub, H->surv_rho, H->surv_eps, capL, s));
         CK(launch_surv_candidates(sk, H->surv, H->surv_ub, H->surv_rho, H->surv_eps, H->cand,
                                   capL + kTopkMax, s));

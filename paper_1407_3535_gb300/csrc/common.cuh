@@ -147,7 +147,7 @@ cudaError_t launch_bound_compact(const float2 *tc, const float2 *theta_co, int L
                                  TmplState *st, int *surv, float *surv_ub, int cap, float *gap,
                                  float *ub_map, uint8_t *surv_map, int *bucket_cnt,
                                  int *bucket_cur, cudaStream_t s);
-cudaError_t launch_survivors(const uint8_t *I, int q, int Lx, const double *IIS,
+cudaError_t launch_survivors(const uint8_t *I, int pimg, int q, int Lx, const double *IIS,
                              const double *IIQ, const float *tf, int m, int n, int npad,
                              const float *inv_sigma, TmplState *st, const int *surv,
                              const float *surv_ub, float *surv_rho, float *surv_eps, int cap,

@@ -156,8 +156,12 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
     const int cx0 = group_centre_of(gx0, Lx, H);
     const int W = group_centre_of(gx1 - 1, Lx, H) + n - cx0;   // pivot columns
     const int RING = m + 2 * R + 1;
-    int *hs = rsm;                                              // H x W ints
-    uint8_t *ring = reinterpret_cast<uint8_t *>(rsm + H * W);   // RING x ring_w bytes
+    // per shift column sx: prefix sums of the column sums over the W pivot
+    // columns (H x (W+1), unsigned: differences of wrapped prefixes are exact
+    // because every window sum is < 2^32), warp totals, then the image ring
+    unsigned *hs = reinterpret_cast<unsigned *>(rsm);
+    unsigned *wtot = hs + H * (W + 1);
+    uint8_t *ring = reinterpret_cast<uint8_t *>(wtot + H * 32);   // RING x ring_w bytes
     const int j = threadIdx.x;
     const bool active = j < W;
     const int jc = cx0 + j;
@@ -193,6 +197,8 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
         }
     }
     unsigned long long local = 0;
+    // ring slots of rows r - R (oldest used) and r + m - R, kept incrementally
+    int so = r % RING, sn = (r + m) % RING;
     for (int gy = gy0; gy < gy1; ++gy) {
         const int cy = group_centre_of(gy, Ly, H);
         while (r < cy) {
@@ -201,8 +207,9 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
                 const int pnew = P[(int64_t)(r + m) * q + jc];
 #pragma unroll
                 for (int sy = 0; sy < H; ++sy) {
-                    const uint8_t *ro = ring + ((r + sy) % RING) * ring_w + j;          // row r + sy - R
-                    const uint8_t *rn = ring + ((r + m + sy) % RING) * ring_w + j;      // row r + m + sy - R
+                    const int a = so + sy, b = sn + sy;
+                    const uint8_t *ro = ring + (a >= RING ? a - RING : a) * ring_w + j;   // row r + sy - R
+                    const uint8_t *rn = ring + (b >= RING ? b - RING : b) * ring_w + j;   // row r + m + sy - R
 #pragma unroll
                     for (int sx = 0; sx < H; ++sx)
                         cs[sy * H + sx] += pnew * (int)rn[sx] - pold * (int)ro[sx];
@@ -210,21 +217,57 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
             }
             __syncthreads();
             ++r;
+            so = (so + 1 == RING) ? 0 : so + 1;
+            sn = (sn + 1 == RING) ? 0 : sn + 1;
             load_row(r + m + R);
             __syncthreads();
         }
-        // emit centre row cy: one shift row (sy) at a time through shared memory
+        // emit centre row cy, one shift row (sy) at a time: block-wide prefix
+        // sums of the column sums turn each n-column window sum into one
+        // difference
         const int gys = gy * H, gye = min(gys + H, Ly);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 #pragma unroll
         for (int syi = 0; syi < H; ++syi) {
+            const int my = cy + syi - R;
+            if (my < gys || my >= gye) continue;   // uniform over the block
+            unsigned v[H];
+#pragma unroll
+            for (int sxi = 0; sxi < H; ++sxi) v[sxi] = active ? (unsigned)cs[syi * H + sxi] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+                for (int sxi = 0; sxi < H; ++sxi) {
+                    const unsigned t = __shfl_up_sync(0xffffffffu, v[sxi], o);
+                    if (lane >= o) v[sxi] += t;
+                }
+            }
+            __syncthreads();   // previous readers of hs / wtot are done
+            if (lane == 31) {
+#pragma unroll
+                for (int sxi = 0; sxi < H; ++sxi) wtot[sxi * 32 + warp] = v[sxi];
+            }
+            __syncthreads();
+            if (warp == 0) {
+#pragma unroll
+                for (int sxi = 0; sxi < H; ++sxi) {
+                    const unsigned t = lane < nwarps ? wtot[sxi * 32 + lane] : 0u;
+                    unsigned inc = t;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const unsigned u2 = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += u2;
+                    }
+                    wtot[sxi * 32 + lane] = inc - t;
+                }
+            }
             __syncthreads();
             if (active) {
 #pragma unroll
-                for (int sxi = 0; sxi < H; ++sxi) hs[sxi * W + j] = cs[syi * H + sxi];
+                for (int sxi = 0; sxi < H; ++sxi)
+                    hs[sxi * (W + 1) + j + 1] = v[sxi] + wtot[sxi * 32 + warp];
             }
+            if (threadIdx.x < H) hs[threadIdx.x * (W + 1)] = 0u;
             __syncthreads();
-            const int my = cy + syi - R;
-            if (my < gys || my >= gye) continue;
             const int ntask = (gx1 - gx0) * H;
             for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
                 const int gxi = task / H, sxi = task % H;
@@ -233,9 +276,8 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
                 const int mx = cx + sxi - R;
                 const int gxs = gx * H, gxe = min(gxs + H, Lx);
                 if (mx < gxs || mx >= gxe) continue;
-                const int *src = hs + sxi * W + (cx - cx0);
-                long long X = 0;
-                for (int v = 0; v < n; ++v) X += src[v];
+                const unsigned *pre = hs + sxi * (W + 1) + (cx - cx0);
+                const long long X = (long long)(unsigned)(pre[n] - pre[0]);
                 const double S = box(IIS, q1, my, mx, m, n), Q = box(IIQ, q1, my, mx, m, n);
                 const double Sp = box(PS, q1, cy, cx, m, n), Qp = box(PQ, q1, cy, cx, m, n);
                 const long long Si = (long long)S, Qi = (long long)Q;
@@ -278,7 +320,7 @@ cudaError_t launch_rho_co_h(const uint8_t *P, const uint8_t *I, int p, int q, in
     int GYB = (Gy + bands - 1) / bands;
     bands = (Gy + GYB - 1) / GYB;
     const int ring_w = ((Wmax + 2 * R) + 15) & ~15;
-    const size_t smem = (size_t)H * Wmax * sizeof(int) + (size_t)(m + 2 * R + 1) * ring_w;
+    const size_t smem = (size_t)H * (Wmax + 1 + 32) * sizeof(unsigned) + (size_t)(m + 2 * R + 1) * ring_w;
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     static size_t attr = 0;
     if (smem > attr) {

@@ -646,14 +646,49 @@ __global__ void theta_co_kernel(const float *__restrict__ rho_co, int64_t L, flo
 // Exact-ish rho (FP32, per-window centring v = I - rint(mu_o)) at the survivors;
 // one warp per survivor, template in shared memory when it fits.
 // ---------------------------------------------------------------------------
+// Per-warp staging of a survivor's window in shared memory: rows are copied
+// with 16-byte cp.async (aligned down; zero-filled past the image end) in
+// chunks of kStageRows rows, double-buffered, so that each warp keeps many
+// loads in flight instead of waiting on one byte load per row.
+constexpr int kStageRows = 16;
+
+__device__ inline int stage_width(int n) { return 16 * ((n + 30) / 16); }
+
+__device__ inline void cp_async16(void *dst, const void *src, int bytes) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes)
+                 : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ inline void stage_rows(const uint8_t *I, const uint8_t *img_end, int q, int y, int x,
+                                  int u0, int rows, int n, uint8_t *buf, int WB) {
+    const int lane = threadIdx.x & 31;
+    const int CW = WB / 16;
+    for (int t = lane; t < rows * CW; t += 32) {
+        const int r = t / CW, k = t % CW;
+        const uint8_t *row = I + (int64_t)(y + u0 + r) * q + x;
+        const uint8_t *ga = reinterpret_cast<const uint8_t *>(
+            reinterpret_cast<uintptr_t>(row) & ~static_cast<uintptr_t>(15));
+        const uint8_t *src = ga + 16 * k;
+        const int64_t avail = img_end - src;
+        const int bytes = avail >= 16 ? 16 : (avail > 0 ? (int)avail : 0);
+        cp_async16(buf + r * WB + 16 * k, bytes > 0 ? src : I, bytes);
+    }
+    cp_async_commit();
+}
+
 // rho at location idx in FP32 with per-window centring v = I - rint(mu_o), by
-// the whole warp (lanes over columns, four row chains), and its error bound.
-// Results are valid in lane 0.
+// the whole warp, and its error bound; results valid in lane 0.  With a
+// staging buffer (wbuf: 2 x kStageRows x WB bytes) the window goes through
+// shared memory; without, it is read straight from global memory.
 __device__ inline void warp_rho32(const uint8_t *__restrict__ I, int q, int Lx,
                                   const double *__restrict__ IIS, const double *__restrict__ IIQ,
                                   const float *__restrict__ tm, int m, int n, int npad,
                                   const float *__restrict__ inv_sigma, float ist, int idx,
-                                  float &rho, float &eps) {
+                                  uint8_t *wbuf, const uint8_t *img_end, float &rho, float &eps) {
     const int lane = threadIdx.x & 31;
     const int64_t q1 = q + 1;
     const double mn = (double)m * n;
@@ -665,29 +700,56 @@ __device__ inline void warp_rho32(const uint8_t *__restrict__ I, int q, int Lx,
     const float a = (float)rint(S / mn);
     const uint8_t *bp = I + (int64_t)y * q + x;
     float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
-    int u = 0;
-    for (; u + 4 <= m; u += 4) {
-        const uint8_t *r0 = bp + (int64_t)u * q;
-        const float *t0 = tm + u * npad;
-        for (int v = lane; v < n; v += 32) {
-            const float i0 = (float)r0[v], i1 = (float)r0[q + v];
-            const float i2 = (float)r0[2 * (int64_t)q + v], i3 = (float)r0[3 * (int64_t)q + v];
-            acc0 = fmaf(t0[v], i0 - a, acc0);
-            acc1 = fmaf(t0[npad + v], i1 - a, acc1);
-            acc2 = fmaf(t0[2 * npad + v], i2 - a, acc2);
-            acc3 = fmaf(t0[3 * npad + v], i3 - a, acc3);
+    if (wbuf) {
+        const int WB = stage_width(n);
+        const int nch = (m + kStageRows - 1) / kStageRows;
+        stage_rows(I, img_end, q, y, x, 0, min(kStageRows, m), n, wbuf, WB);
+        for (int c = 0; c < nch; ++c) {
+            const int u0 = c * kStageRows, rows = min(kStageRows, m - u0);
+            uint8_t *buf = wbuf + (c & 1) * kStageRows * WB;
+            if (c + 1 < nch) {
+                stage_rows(I, img_end, q, y, x, u0 + kStageRows, min(kStageRows, m - u0 - kStageRows),
+                           n, wbuf + ((c + 1) & 1) * kStageRows * WB, WB);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncwarp();
+            for (int r = 0; r < rows; ++r) {
+                const uint8_t *row = I + (int64_t)(y + u0 + r) * q + x;
+                const uint8_t *sb = buf + r * WB + (int)(reinterpret_cast<uintptr_t>(row) & 15);
+                const float *tr = tm + (u0 + r) * npad;
+                float racc = 0.f;
+                for (int v = lane; v < n; v += 32) racc = fmaf(tr[v], (float)sb[v] - a, racc);
+                if (r & 1) acc1 += racc; else acc0 += racc;
+            }
+            __syncwarp();   // the buffer is refilled two chunks later
         }
+    } else {
+        int u = 0;
+        for (; u + 4 <= m; u += 4) {
+            const uint8_t *r0 = bp + (int64_t)u * q;
+            const float *t0 = tm + u * npad;
+            for (int v = lane; v < n; v += 32) {
+                const float i0 = (float)r0[v], i1 = (float)r0[q + v];
+                const float i2 = (float)r0[2 * (int64_t)q + v], i3 = (float)r0[3 * (int64_t)q + v];
+                acc0 = fmaf(t0[v], i0 - a, acc0);
+                acc1 = fmaf(t0[npad + v], i1 - a, acc1);
+                acc2 = fmaf(t0[2 * npad + v], i2 - a, acc2);
+                acc3 = fmaf(t0[3 * npad + v], i3 - a, acc3);
+            }
+        }
+        for (; u < m; ++u)
+            for (int v = lane; v < n; v += 32)
+                acc0 = fmaf(tm[u * npad + v], (float)bp[(int64_t)u * q + v] - a, acc0);
     }
-    for (; u < m; ++u)
-        for (int v = lane; v < n; v += 32)
-            acc0 = fmaf(tm[u * npad + v], (float)bp[(int64_t)u * q + v] - a, acc0);
     const float acc = warp_sum_f((acc0 + acc2) + (acc1 + acc3));
     rho = 0.f;
     eps = 0.f;
     if (lane == 0) {
-        // accumulation depth per lane: ceil(m/4) rows x ceil(n/32) columns per
-        // chain (+ the remainder rows), 2 chain merges, 5 shuffle levels
-        const int kacc = ((m + 3) / 4 + (m % 4)) * ((n + 31) / 32) + 8;
+        // accumulation depth per lane: ceil(n/32) per row, then at most m row
+        // partial sums into one chain, the chain merges and 5 shuffle levels
+        const int kacc = ((n + 31) / 32) + m + 8;
         const float is = inv_sigma[idx];
         rho = (acc * ist) * is;
         if (is > 0.f) {
@@ -714,10 +776,17 @@ survivors_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__r
                  const double *__restrict__ IIQ, const float *__restrict__ tf, int m, int n,
                  int npad, const float *__restrict__ inv_sigma, TmplState *st,
                  const int *__restrict__ surv, const float *__restrict__ surv_ub, float *surv_rho,
-                 float *surv_eps, int cap, int tmpl_in_smem, int s_begin, int s_end) {
+                 float *surv_eps, int cap, int tmpl_in_smem, int s_begin, int s_end,
+                 int stage, const uint8_t *img_end) {
     extern __shared__ float4 ssm4[];
     if (st->flat) return;
     const float *tm = stage_template(tf, m, npad, tmpl_in_smem, reinterpret_cast<float *>(ssm4));
+    uint8_t *wbuf = nullptr;
+    if (stage) {
+        const size_t tb = tmpl_in_smem ? (((size_t)m * npad * sizeof(float) + 15) & ~(size_t)15) : 0;
+        wbuf = reinterpret_cast<uint8_t *>(ssm4) + tb +
+               (size_t)(threadIdx.x >> 5) * 2 * kStageRows * stage_width(n);
+    }
     const int ns = min(min(st->n_surv, cap), s_end);
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -738,7 +807,8 @@ survivors_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__r
             lim = __shfl_sync(0xffffffffu, key_float(*lo_key), 0);
             if (surv_ub[s] < lim) continue;
             float rho, eps;
-            warp_rho32(I, q, Lx, IIS, IIQ, tm, m, n, npad, inv_sigma, ist, surv[s], rho, eps);
+            warp_rho32(I, q, Lx, IIS, IIQ, tm, m, n, npad, inv_sigma, ist, surv[s], wbuf, img_end,
+                       rho, eps);
             if (lane == 0) {
                 surv_rho[s] = rho;
                 surv_eps[s] = eps;
@@ -773,7 +843,8 @@ group_members_kernel(const uint8_t *__restrict__ I, int q, int Ly, int Lx, int h
     for (int j = warp; j < hy * hx; j += nw) {
         const int idx = (y0 + j / hx) * Lx + x0 + j % hx;
         float rho, eps;
-        warp_rho32(I, q, Lx, IIS, IIQ, tm, m, n, npad, inv_sigma, ist, idx, rho, eps);
+        warp_rho32(I, q, Lx, IIS, IIQ, tm, m, n, npad, inv_sigma, ist, idx, nullptr, nullptr, rho,
+                   eps);
         if ((threadIdx.x & 31) == 0) atomicMax(&st->lo_key, float_key(rho - eps));
     }
 }
@@ -960,13 +1031,19 @@ static size_t tmpl_smem(int m, int npad, int *in_smem) {
     return *in_smem ? smem : 0;
 }
 
-cudaError_t launch_survivors(const uint8_t *I, int q, int Lx, const double *IIS,
+cudaError_t launch_survivors(const uint8_t *I, int pimg, int q, int Lx, const double *IIS,
                              const double *IIQ, const float *tf, int m, int n, int npad,
                              const float *inv_sigma, TmplState *st, const int *surv,
                              const float *surv_ub, float *surv_rho, float *surv_eps, int cap,
                              cudaStream_t s) {
     int in_smem = 0;
-    const size_t smem = tmpl_smem(m, npad, &in_smem);
+    size_t smem = tmpl_smem(m, npad, &in_smem);
+    smem = (smem + 15) & ~(size_t)15;
+    // stage windows through shared memory when the template is there and the
+    // rows are narrow enough
+    const int WB = 16 * ((n + 30) / 16);
+    const int stage = in_smem && n <= 256 ? 1 : 0;
+    if (stage) smem += (size_t)8 * 2 * kStageRows * WB;
     static size_t attr = 0;
     if (smem > attr) {
         cudaError_t e = cudaFuncSetAttribute(survivors_kernel,
@@ -974,14 +1051,15 @@ cudaError_t launch_survivors(const uint8_t *I, int q, int Lx, const double *IIS,
         if (e != cudaSuccess) return e;
         attr = smem;
     }
-    // priority phase: the first (largest-bound) survivors with few warps, so
-    // the running threshold rises before the whole GPU sweeps the rest
+    const uint8_t *iend = I + (int64_t)q * pimg;
+    // priority phase: the first (largest-bound) survivors on part of the GPU,
+    // so the running threshold rises before the full sweep of the rest
     constexpr int kPriority = 2048;
     {
         LaunchScope ls("survivors_kernel", s);
-        survivors_kernel<<<16, 256, smem, s>>>(I, q, Lx, IIS, IIQ, tf, m, n, npad, inv_sigma, st,
+        survivors_kernel<<<64, 256, smem, s>>>(I, q, Lx, IIS, IIQ, tf, m, n, npad, inv_sigma, st,
                                                surv, surv_ub, surv_rho, surv_eps, cap, in_smem, 0,
-                                               kPriority);
+                                               kPriority, stage, iend);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -990,7 +1068,7 @@ cudaError_t launch_survivors(const uint8_t *I, int q, int Lx, const double *IIS,
         survivors_kernel<<<num_sms() * 4, 256, smem, s>>>(I, q, Lx, IIS, IIQ, tf, m, n, npad,
                                                           inv_sigma, st, surv, surv_ub, surv_rho,
                                                           surv_eps, cap, in_smem, kPriority,
-                                                          0x7fffffff);
+                                                          0x7fffffff, stage, iend);
     }
     return cudaGetLastError();
 }

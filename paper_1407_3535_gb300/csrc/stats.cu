@@ -14,45 +14,67 @@ namespace {
 constexpr int kRowThreads = 256;
 
 // Row pass: o_k[(y+1)*(q+1) + x+1] = sum_{j<=x} f_k(A[y][j], B[y][j]).
+// One block per row; tiles of 4 * 256 pixels: each thread takes 4 consecutive
+// pixels, the block scans the thread totals, and consecutive threads write
+// consecutive 32-byte runs (coalesced).  Sums are exact in int64.
 __global__ void __launch_bounds__(kRowThreads)
 ii_rows_kernel(const uint8_t *__restrict__ A, const uint8_t *__restrict__ B, int p, int q,
                double *o0, double *o1, double *o2) {
+    __shared__ long long wsum[3][kRowThreads / 32];
+    __shared__ long long carry[3];
     const int y = blockIdx.x;
-    const int tid = threadIdx.x;
-    const int chunk = (q + kRowThreads - 1) / kRowThreads;
-    const int x0 = min(q, tid * chunk), x1 = min(q, x0 + chunk);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint8_t *a = A + (int64_t)y * q;
     const uint8_t *b = B ? B + (int64_t)y * q : nullptr;
-    long long s0 = 0, s1 = 0, s2 = 0;
-    for (int x = x0; x < x1; ++x) {
-        const int v = a[x];
-        s0 += v;
-        s1 += v * v;
-        if (b) s2 += v * (int)b[x];
-    }
-    // exclusive block scan of (s0, s1, s2)
-    __shared__ long long sh[3][kRowThreads];
-    sh[0][tid] = s0; sh[1][tid] = s1; sh[2][tid] = s2;
-    __syncthreads();
-    for (int off = 1; off < kRowThreads; off <<= 1) {
-        long long v0 = 0, v1 = 0, v2 = 0;
-        if (tid >= off) { v0 = sh[0][tid - off]; v1 = sh[1][tid - off]; v2 = sh[2][tid - off]; }
-        __syncthreads();
-        sh[0][tid] += v0; sh[1][tid] += v1; sh[2][tid] += v2;
-        __syncthreads();
-    }
-    long long r0 = sh[0][tid] - s0, r1 = sh[1][tid] - s1, r2 = sh[2][tid] - s2;
     const int64_t q1 = q + 1;
     double *d0 = o0 + (int64_t)(y + 1) * q1;
     double *d1 = o1 + (int64_t)(y + 1) * q1;
     double *d2 = (b && o2) ? o2 + (int64_t)(y + 1) * q1 : nullptr;
-    if (tid == 0) { d0[0] = 0.0; d1[0] = 0.0; if (d2) d2[0] = 0.0; }
-    for (int x = x0; x < x1; ++x) {
-        const int v = a[x];
-        r0 += v; r1 += v * v;
-        d0[x + 1] = (double)r0;
-        d1[x + 1] = (double)r1;
-        if (d2) { r2 += v * (int)b[x]; d2[x + 1] = (double)r2; }
+    if (tid == 0) {
+        d0[0] = 0.0; d1[0] = 0.0; if (d2) d2[0] = 0.0;
+        carry[0] = carry[1] = carry[2] = 0;
+    }
+    __syncthreads();
+    for (int x0 = 0; x0 < q; x0 += 4 * kRowThreads) {
+        const int xs = x0 + 4 * tid;
+        int va[4], vb[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            va[k] = xs + k < q ? a[xs + k] : 0;
+            vb[k] = (b && xs + k < q) ? b[xs + k] : 0;
+        }
+        long long p0[4], p1[4], p2[4];
+        long long r0 = 0, r1 = 0, r2 = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            r0 += va[k]; r1 += va[k] * va[k]; r2 += va[k] * vb[k];
+            p0[k] = r0; p1[k] = r1; p2[k] = r2;
+        }
+        // inclusive warp scan of the thread totals
+        long long i0 = r0, i1 = r1, i2 = r2;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t0 = __shfl_up_sync(0xffffffffu, i0, o);
+            const long long t1 = __shfl_up_sync(0xffffffffu, i1, o);
+            const long long t2 = __shfl_up_sync(0xffffffffu, i2, o);
+            if (lane >= o) { i0 += t0; i1 += t1; i2 += t2; }
+        }
+        if (lane == 31) { wsum[0][warp] = i0; wsum[1][warp] = i1; wsum[2][warp] = i2; }
+        __syncthreads();
+        long long e0 = carry[0] + i0 - r0, e1 = carry[1] + i1 - r1, e2 = carry[2] + i2 - r2;
+        for (int w = 0; w < warp; ++w) { e0 += wsum[0][w]; e1 += wsum[1][w]; e2 += wsum[2][w]; }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (xs + k < q) {
+                d0[xs + k + 1] = (double)(e0 + p0[k]);
+                d1[xs + k + 1] = (double)(e1 + p1[k]);
+                if (d2) d2[xs + k + 1] = (double)(e2 + p2[k]);
+            }
+        }
+        __syncthreads();
+        if (tid == kRowThreads - 1) {
+            carry[0] = e0 + r0; carry[1] = e1 + r1; carry[2] = e2 + r2;
+        }
+        __syncthreads();
     }
 }
 
