@@ -550,7 +550,8 @@ opta_status enqueue_scan2(opta_handle *H, const opta_template *const *t, int n, 
                                 S->inv_sigma, sk, H->cand, H->prm.topk, s));
         CK(launch_threshold(sk, H->cand_rho, s));
         CK(launch_bound_compact(H->tc + k * G, S->theta_co, S->Ly, S->Lx, S->h, sk, H->surv,
-                                H->surv_ub, capL, H->ubbuf, ub_map, surv_map, H->bucket_cnt,
+                                H->surv_ub, capL, reinterpret_cast<int *>(H->ubbuf), ub_map, surv_map,
+                                H->bucket_cnt,
                                 H->bucket_cur, s));
         CK(launch_survivors(H->I8, H->p, H->q, S->Lx, H->IIS, H->IIQ, tf, m, nn, npad, S->inv_sigma, sk,
                             H->surv, H->surv_ub, H->surv_rho, H->surv_eps, capL, s));

@@ -140,11 +140,12 @@ cudaError_t launch_group_members(const uint8_t *I, int q, int Ly, int Lx, int h,
                                  const double *IIQ, const float *tf, int m, int n, int npad,
                                  const float *inv_sigma, TmplState *st, const int *cand, int topk,
                                  cudaStream_t s);
-// Scan 2: angular gap of every location into gap (L floats), bucket histogram
-// of the survivors, then compaction of the survivors in bucket order with
-// their upper bound; ub_map / surv_map (nullable) receive the full maps.
+// Scan 2: bound of every location, bucket histogram of the survivors and
+// survivor count per chunk of 4096 locations (chunk_cnt: ceil(L/4096) ints),
+// then compaction of the survivors in bucket order with their upper bound;
+// ub_map / surv_map (nullable) receive the full maps.
 cudaError_t launch_bound_compact(const float2 *tc, const float2 *theta_co, int Ly, int Lx, int h,
-                                 TmplState *st, int *surv, float *surv_ub, int cap, float *gap,
+                                 TmplState *st, int *surv, float *surv_ub, int cap, int *chunk_cnt,
                                  float *ub_map, uint8_t *surv_map, int *bucket_cnt,
                                  int *bucket_cur, cudaStream_t s);
 cudaError_t launch_survivors(const uint8_t *I, int pimg, int q, int Lx, const double *IIS,

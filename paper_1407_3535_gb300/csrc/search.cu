@@ -11,6 +11,8 @@
 // products with 1/sigma).  ||v||/sigma_v ("efac") comes from exact integer
 // window sums.  These bounds make the elimination test and the choice of
 // FP64 candidates safe.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace opta {
@@ -528,38 +530,61 @@ __device__ inline int gap_bucket(float gap, float lim) {
     return b < 0 ? 0 : (b >= kUbBuckets ? kUbBuckets - 1 : b);
 }
 
-// Pass 1: angular gap of every location (stored), survivor histogram by bucket.
-// gap = max(0, tc.lo - co.hi, co.lo - tc.hi) is the smallest angle between
-// t and the location allowed by the two intervals; rho <= cos(gap).
+// Scan 2 works on chunks of kChunkLoc consecutive locations (256 threads x
+// SC_PER each).  gap = max(0, tc.lo - co.hi, co.lo - tc.hi) is the smallest
+// angle between t and the location allowed by the two intervals, so
+// rho <= cos(gap).  It is computed with subtractions and maxima only, so the
+// two passes below obtain bit-identical values.
+constexpr int SC_PER = 16;
+constexpr int kChunkLoc = 256 * SC_PER;
+
+__device__ inline float loc_gap(const float2 *__restrict__ tc, const float2 *__restrict__ theta_co,
+                                int Lx, int h, int Gx, int64_t i) {
+    const int y = (int)(i / Lx), x = (int)(i % Lx);
+    const float2 t = tc[(y / h) * Gx + (x / h)];
+    const float2 c = theta_co[i];
+    return fmaxf(0.f, fmaxf(t.x - c.y, c.x - t.y));
+}
+
+// Pass 1: survivor histogram by bucket, and the survivor count of every chunk.
 __global__ void __launch_bounds__(256)
 bound_hist_kernel(const float2 *__restrict__ tc, const float2 *__restrict__ theta_co, int Ly,
-                  int Lx, int h, TmplState *st, float *gap_out, float *ub_map,
+                  int Lx, int h, TmplState *st, int *chunk_cnt, float *ub_map,
                   uint8_t *surv_map, int *bucket_cnt) {
     __shared__ int hist[kUbBuckets];
+    __shared__ int ccount;
     if (st->flat) return;
     for (int i = threadIdx.x; i < kUbBuckets; i += blockDim.x) hist[i] = 0;
-    __syncthreads();
     const int Gx = groups_along(Lx, h);
     const float lim = st->theta_lim;
     const int64_t L = (int64_t)Ly * Lx;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < L; base += stride) {
-        const int64_t i = base + threadIdx.x;
-        bool f = false;
-        int b = -1;
-        if (i < L) {
-            const int y = (int)(i / Lx), x = (int)(i % Lx);
-            const float2 t = tc[(y / h) * Gx + (x / h)];
-            const float2 c = theta_co[i];
-            const float gap = fmaxf(0.f, fmaxf(t.x - c.y, c.x - t.y));
-            gap_out[i] = gap;
-            f = gap <= lim;
-            if (ub_map) ub_map[i] = cosf(gap) + kCosMargin;
-            if (surv_map) surv_map[i] = f ? 1 : 0;
-            if (f) b = gap_bucket(gap, lim);
+    const int64_t nchunks = (L + kChunkLoc - 1) / kChunkLoc;
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        if (threadIdx.x == 0) ccount = 0;
+        __syncthreads();
+        int mine = 0;
+#pragma unroll 4
+        for (int k = 0; k < SC_PER; ++k) {
+            const int64_t i = c * kChunkLoc + k * 256 + threadIdx.x;
+            bool f = false;
+            int b = -1;
+            if (i < L) {
+                const float gap = loc_gap(tc, theta_co, Lx, h, Gx, i);
+                f = gap <= lim;
+                if (ub_map) ub_map[i] = cosf(gap) + kCosMargin;
+                if (surv_map) surv_map[i] = f ? 1 : 0;
+                if (f) b = gap_bucket(gap, lim);
+            }
+            if (__any_sync(0xffffffffu, f)) {
+                const unsigned peers = __match_any_sync(0xffffffffu, b);
+                if (f && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[b], __popc(peers));
+            }
+            mine += f ? 1 : 0;
         }
-        const unsigned peers = __match_any_sync(0xffffffffu, b);
-        if (f && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[b], __popc(peers));
+        for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+        if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&ccount, mine);
+        __syncthreads();
+        if (threadIdx.x == 0) chunk_cnt[c] = ccount;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kUbBuckets; i += blockDim.x)
@@ -589,34 +614,38 @@ __global__ void bucket_scan_kernel(TmplState *st, const int *__restrict__ bucket
 }
 
 // Pass 2: scatter the survivors into their bucket ranges (bucket 0 = largest
-// bound first) together with their upper bound cos(gap) + margin.  Each block
-// takes chunks of 256 x SC_PER locations, counts them per bucket in shared
-// memory, reserves every bucket's slice with one global atomic, then writes.
-constexpr int SC_PER = 16;
+// bound first) together with their bound cos(gap) + margin.  Only chunks with
+// survivors are revisited; their gaps are recomputed bit-identically.  Each
+// block counts a chunk per bucket in shared memory and reserves every bucket's
+// slice with one global atomic.
 __global__ void __launch_bounds__(256)
-bound_scatter_kernel(const float *__restrict__ gap_in, int64_t L, TmplState *st, int *surv,
+bound_scatter_kernel(const float2 *__restrict__ tc, const float2 *__restrict__ theta_co, int Ly,
+                     int Lx, int h, const int *__restrict__ chunk_cnt, TmplState *st, int *surv,
                      float *surv_ub, int cap, int *bucket_cur) {
     __shared__ int cnt[kUbBuckets];
     __shared__ int basep[kUbBuckets];
     if (st->flat) return;
+    const int Gx = groups_along(Lx, h);
     const float lim = st->theta_lim;
-    const int64_t chunk = 256 * SC_PER;
-    for (int64_t c0 = (int64_t)blockIdx.x * chunk; c0 < L; c0 += (int64_t)gridDim.x * chunk) {
+    const int64_t L = (int64_t)Ly * Lx;
+    const int64_t nchunks = (L + kChunkLoc - 1) / kChunkLoc;
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        if (chunk_cnt[c] == 0) continue;   // uniform over the block
         for (int b = threadIdx.x; b < kUbBuckets; b += blockDim.x) cnt[b] = 0;
         __syncthreads();
         float g[SC_PER];
         int bk[SC_PER];
 #pragma unroll
         for (int k = 0; k < SC_PER; ++k) {
-            const int64_t i = c0 + k * 256 + threadIdx.x;
-            g[k] = i < L ? gap_in[i] : 4.f;
+            const int64_t i = c * kChunkLoc + k * 256 + threadIdx.x;
+            g[k] = i < L ? loc_gap(tc, theta_co, Lx, h, Gx, i) : 4.f;
             bk[k] = g[k] <= lim ? gap_bucket(g[k], lim) : -1;
             if (bk[k] >= 0) atomicAdd(&cnt[bk[k]], 1);
         }
         __syncthreads();
         for (int b = threadIdx.x; b < kUbBuckets; b += blockDim.x) {
-            const int c = cnt[b];
-            basep[b] = c ? atomicAdd(&bucket_cur[b], c) : 0;
+            const int n = cnt[b];
+            basep[b] = n ? atomicAdd(&bucket_cur[b], n) : 0;
             cnt[b] = 0;
         }
         __syncthreads();
@@ -625,7 +654,7 @@ bound_scatter_kernel(const float *__restrict__ gap_in, int64_t L, TmplState *st,
             if (bk[k] < 0) continue;
             const int pos = basep[bk[k]] + atomicAdd(&cnt[bk[k]], 1);
             if (pos < cap) {
-                surv[pos] = (int)(c0 + k * 256 + threadIdx.x);
+                surv[pos] = (int)(c * kChunkLoc + k * 256 + threadIdx.x);
                 surv_ub[pos] = cosf(g[k]) + kCosMargin;
             } else {
                 atomicOr(&st->overflow, 1);
@@ -761,10 +790,21 @@ __device__ inline void warp_rho32(const uint8_t *__restrict__ I, int q, int Lx,
     }
 }
 
+// Copy the template (m x npad floats, npad a multiple of 8) into shared
+// memory with 16-byte loads, several in flight per thread.
 __device__ inline const float *stage_template(const float *tf, int m, int npad, int in_smem,
                                               float *tsm) {
     if (!in_smem) return tf;
-    for (int i = threadIdx.x; i < m * npad; i += blockDim.x) tsm[i] = tf[i];
+    const float4 *src = reinterpret_cast<const float4 *>(tf);
+    float4 *dst = reinterpret_cast<float4 *>(tsm);
+    const int n4 = m * npad / 4;
+    int i = threadIdx.x;
+    for (; i + 3 * (int)blockDim.x < n4; i += 4 * blockDim.x) {
+        const float4 a = src[i], b = src[i + blockDim.x], c = src[i + 2 * blockDim.x],
+                     d = src[i + 3 * blockDim.x];
+        dst[i] = a; dst[i + blockDim.x] = b; dst[i + 2 * blockDim.x] = c; dst[i + 3 * blockDim.x] = d;
+    }
+    for (; i < n4; i += blockDim.x) dst[i] = src[i];
     __syncthreads();
     return tsm;
 }
@@ -780,6 +820,8 @@ survivors_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__r
                  int stage, const uint8_t *img_end) {
     extern __shared__ float4 ssm4[];
     if (st->flat) return;
+    // blocks whose first chunk lies beyond the survivor list have nothing to do
+    if (s_begin + blockIdx.x * (int)blockDim.x >= min(min(st->n_surv, cap), s_end)) return;
     const float *tm = stage_template(tf, m, npad, tmpl_in_smem, reinterpret_cast<float *>(ssm4));
     uint8_t *wbuf = nullptr;
     if (stage) {
@@ -994,16 +1036,19 @@ cudaError_t launch_threshold(TmplState *st, const double *cand_rho, cudaStream_t
 }
 
 cudaError_t launch_bound_compact(const float2 *tc, const float2 *theta_co, int Ly, int Lx, int h,
-                                 TmplState *st, int *surv, float *surv_ub, int cap, float *gap,
+                                 TmplState *st, int *surv, float *surv_ub, int cap, int *chunk_cnt,
                                  float *ub_map, uint8_t *surv_map, int *bucket_cnt,
                                  int *bucket_cur, cudaStream_t s) {
     const int64_t L = (int64_t)Ly * Lx;
+    const int64_t nchunks = (L + kChunkLoc - 1) / kChunkLoc;
+    int grid = (int)std::min<int64_t>(nchunks, (int64_t)num_sms() * 8);
+    if (grid < 1) grid = 1;
     cudaError_t e = cudaMemsetAsync(bucket_cnt, 0, kUbBuckets * sizeof(int), s);
     if (e != cudaSuccess) return e;
     {
         LaunchScope ls("bound_hist_kernel", s);
-        bound_hist_kernel<<<grid_cap(L, 256, 8), 256, 0, s>>>(tc, theta_co, Ly, Lx, h, st, gap,
-                                                             ub_map, surv_map, bucket_cnt);
+        bound_hist_kernel<<<grid, 256, 0, s>>>(tc, theta_co, Ly, Lx, h, st, chunk_cnt, ub_map,
+                                               surv_map, bucket_cnt);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
@@ -1013,8 +1058,8 @@ cudaError_t launch_bound_compact(const float2 *tc, const float2 *theta_co, int L
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
         LaunchScope ls("bound_scatter_kernel", s);
-        bound_scatter_kernel<<<grid_cap((L + SC_PER - 1) / SC_PER, 256, 4), 256, 0, s>>>(
-            gap, L, st, surv, surv_ub, cap, bucket_cur);
+        bound_scatter_kernel<<<grid, 256, 0, s>>>(tc, theta_co, Ly, Lx, h, chunk_cnt, st, surv,
+                                                  surv_ub, cap, bucket_cur);
     }
     return cudaGetLastError();
 }

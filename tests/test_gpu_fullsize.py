@@ -1,0 +1,85 @@
+"""Full-size parity in the bench's launch configuration (the 2048^2, 4096^2
+and 8192^2 workloads), on outputs the oracle computes one by one:
+
+* rho returned at the GPU location equals the oracle's rho there (1e-5);
+* no sampled location -- the template's true crop location, the whole
+  neighbourhood of the GPU optimum and random locations -- has an oracle rho
+  above the returned value (+1e-6), a property of the true maximum;
+* the pruned search and the exhaustive GPU search agree on the location
+  (or on a location within 1e-6 in oracle rho)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import synth
+from oracle import ref
+
+
+@pytest.fixture(scope="module")
+def opta():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1407_3535_gb300 as m
+    m.lib()
+    return m
+
+
+def _check_full(opta, img, templates, h, res, zres, seed):
+    rng = np.random.default_rng(seed)
+    p, q = img.shape
+    for t, r, z in zip(templates, res, zres):
+        m, n = t.data.shape
+        Ly, Lx = p - m + 1, q - n + 1
+        assert r.status == 0 and z.status == 0, (r.as_dict(), z.as_dict())
+        got = ref.rho_at(img, t.data, [r.y], [r.x])[0]
+        assert abs(got - r.rho) <= 1e-5
+        zgot = ref.rho_at(img, t.data, [z.y], [z.x])[0]
+        assert abs(zgot - z.rho) <= 1e-5
+        assert (r.y, r.x) == (z.y, z.x) or abs(got - zgot) <= 1e-6
+        ys = [t.y] + list(rng.integers(0, Ly, 48))
+        xs = [t.x] + list(rng.integers(0, Lx, 48))
+        for dy in range(-3, 4):
+            for dx in range(-3, 4):
+                yy, xx = r.y + dy, r.x + dx
+                if 0 <= yy < Ly and 0 <= xx < Lx:
+                    ys.append(yy); xs.append(xx)
+        vals = ref.rho_at(img, t.data, ys, xs)
+        assert np.all(vals <= r.rho + 1e-6), float(vals.max() - r.rho)
+
+
+def _run(opta, img, ts):
+    dimg = torch.from_numpy(img).cuda()
+    dts = [torch.from_numpy(t.data).cuda() for t in ts]
+    h = opta.optA_prepare(dimg, opta.opta_params_default(), sizes=sorted({t.data.shape for t in ts}))
+    res = opta.optA_search(h, dts)
+    zres = [opta.zncc_full(dimg, d) for d in dts]
+    h.close()
+    return res, zres
+
+
+def test_batched_4096_one_template_per_size(opta):
+    img = synth.config_image(4)
+    ts = synth.config_templates(4, img)
+    seen, pick = set(), []
+    for t in ts:
+        if t.data.shape not in seen:
+            seen.add(t.data.shape)
+            pick.append(t)
+    res, zres = _run(opta, img, pick)
+    _check_full(opta, img, pick, None, res, zres, seed=4)
+
+
+def test_aerial_2048_sixteen_templates(opta):
+    img = synth.config_image(2)
+    ts = synth.config_templates(2, img)
+    res, zres = _run(opta, img, ts)
+    _check_full(opta, img, ts, None, res, zres, seed=2)
+
+
+def test_precision_8192_four_templates(opta):
+    img = synth.config_image(3)
+    ts = synth.config_templates(3, img, count=4)
+    res, zres = _run(opta, img, ts)
+    _check_full(opta, img, ts, None, res, zres, seed=3)
