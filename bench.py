@@ -304,6 +304,13 @@ def main():
     opta.opta_dbg_profile_enable(False)
     prof = opta.opta_dbg_profile_read()
     h.close()
+    # and of one preparation
+    opta.opta_dbg_profile_enable(True)
+    hp = opta.optA_prepare(dimg, prm, sizes=sizes, stream=stream)
+    torch.cuda.synchronize()
+    opta.opta_dbg_profile_enable(False)
+    prof_prep = opta.opta_dbg_profile_read()
+    hp.close()
 
     # end to end through the C ABI with host buffers
     host_img = np.ascontiguousarray(img)
@@ -396,6 +403,8 @@ def main():
                               "min_best": float(np.min([r.rho for r in res_prof]))},
         "brute_force": brute,
         "kernels_ms": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
+        "prepare_kernels_ms": {k: [round(v[0], 3), v[1]] for k, v in
+                               sorted(prof_prep.items(), key=lambda kv: -kv[1][0])},
         "group_sizes": {k: v["group_h"] for k, v in size_info.items()},
         "per_size": per_size,
         "blur_levels": {k: v["level"] for k, v in size_info.items()},

@@ -554,7 +554,8 @@ opta_status enqueue_scan2(opta_handle *H, const opta_template *const *t, int n, 
                                 H->bucket_cnt,
                                 H->bucket_cur, s));
         CK(launch_survivors(H->I8, H->p, H->q, S->Lx, H->IIS, H->IIQ, tf, m, nn, npad, S->inv_sigma, sk,
-                            H->surv, H->surv_ub, H->surv_rho, H->surv_eps, capL, s));
+                            H->surv, H->surv_ub, H->surv_rho, H->surv_eps, capL, H->bucket_cur,
+                            s));
         CK(launch_surv_candidates(sk, H->surv, H->surv_ub, H->surv_rho, H->surv_eps, H->cand,
                                   capL + kTopkMax, s));
         CK(launch_refine64(H->I8, H->q, S->Lx, td, m, nn, sk, H->cand, H->cand_rho,

@@ -66,7 +66,7 @@ struct TmplState {
     int overflow;             // candidate buffer overflowed (status)
     int n_eval;               // survivors evaluated (not skipped by the running threshold)
     float theta_lim;          // survive iff angular gap <= theta_lim (from thr_lo)
-    int pad_;
+    int n_surv_eff;           // survivors past this index are known to be skippable
 };
 
 // Survivors are bucketed by their upper bound (bucket 0 = highest) so that
@@ -152,7 +152,7 @@ cudaError_t launch_survivors(const uint8_t *I, int pimg, int q, int Lx, const do
                              const double *IIQ, const float *tf, int m, int n, int npad,
                              const float *inv_sigma, TmplState *st, const int *surv,
                              const float *surv_ub, float *surv_rho, float *surv_eps, int cap,
-                             cudaStream_t s);
+                             const int *bucket_end, cudaStream_t s);
 cudaError_t launch_surv_candidates(TmplState *st, const int *surv, const float *surv_ub,
                                    const float *surv_rho, const float *surv_eps, int *cand,
                                    int cap, cudaStream_t s);

@@ -94,6 +94,7 @@ tmpl_prep_kernel(const float *__restrict__ t, int64_t ld, int m, int n, int npad
         st->best_rho = 0.0;
         st->overflow = 0;
         st->n_eval = 0;
+        st->n_surv_eff = 0x7fffffff;
     }
 }
 
@@ -610,7 +611,7 @@ __global__ void bucket_scan_kernel(TmplState *st, const int *__restrict__ bucket
     int acc = incl - sum;
 #pragma unroll
     for (int k = 0; k < PER; ++k) { bucket_cur[lane * PER + k] = acc; acc += loc[k]; }
-    if (lane == 31) st->n_surv = incl;
+    if (lane == 31) { st->n_surv = incl; st->n_surv_eff = incl; }
 }
 
 // Pass 2: scatter the survivors into their bucket ranges (bucket 0 = largest
@@ -820,8 +821,9 @@ survivors_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__r
                  int stage, const uint8_t *img_end) {
     extern __shared__ float4 ssm4[];
     if (st->flat) return;
-    // blocks whose first chunk lies beyond the survivor list have nothing to do
-    if (s_begin + blockIdx.x * (int)blockDim.x >= min(min(st->n_surv, cap), s_end)) return;
+    // blocks whose first entry lies beyond the survivor list have nothing to do
+    const int ns0 = min(min(min(st->n_surv, cap), s_end), st->n_surv_eff);
+    if (s_begin + blockIdx.x * (int)(blockDim.x >> 5) >= ns0) return;
     const float *tm = stage_template(tf, m, npad, tmpl_in_smem, reinterpret_cast<float *>(ssm4));
     uint8_t *wbuf = nullptr;
     if (stage) {
@@ -829,37 +831,50 @@ survivors_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__r
         wbuf = reinterpret_cast<uint8_t *>(ssm4) + tb +
                (size_t)(threadIdx.x >> 5) * 2 * kStageRows * stage_width(n);
     }
-    const int ns = min(min(st->n_surv, cap), s_end);
+    const int ns = ns0;
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const float ist = st->inv_sigma;
     volatile unsigned int *lo_key = &st->lo_key;
     int evaluated = 0;
-    for (int base = s_begin + warp * 32; base < ns; base += nwarps * 32) {
-        // running threshold (Eq. SEC with the best rho_tb found so far); 32 at a time
-        float lim = key_float(*lo_key);
-        lim = __shfl_sync(0xffffffffu, lim, 0);
-        const int sl = base + lane;
-        unsigned todo = __ballot_sync(0xffffffffu, sl < ns && surv_ub[sl] >= lim);
-        while (todo) {
-            const int j = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int s = base + j;
-            lim = __shfl_sync(0xffffffffu, key_float(*lo_key), 0);
-            if (surv_ub[s] < lim) continue;
-            float rho, eps;
-            warp_rho32(I, q, Lx, IIS, IIQ, tm, m, n, npad, inv_sigma, ist, surv[s], wbuf, img_end,
-                       rho, eps);
-            if (lane == 0) {
-                surv_rho[s] = rho;
-                surv_eps[s] = eps;
-                atomicMax(&st->lo_key, float_key(rho - eps));
-                ++evaluated;
-            }
+    // one survivor per warp, interleaved so that all warps advance through
+    // the bound-ordered list together; a survivor whose bound has fallen below
+    // the running certain lower bound of the maximum is skipped (Eq. SEC with
+    // the best rho_tb found so far)
+    for (int s = s_begin + warp; s < ns; s += nwarps) {
+        const float lim = __shfl_sync(0xffffffffu, key_float(*lo_key), 0);
+        const float ub = __shfl_sync(0xffffffffu, surv_ub[s], 0);
+        if (ub < lim) continue;
+        float rho, eps;
+        warp_rho32(I, q, Lx, IIS, IIQ, tm, m, n, npad, inv_sigma, ist, surv[s], wbuf, img_end,
+                   rho, eps);
+        if (lane == 0) {
+            surv_rho[s] = rho;
+            surv_eps[s] = eps;
+            atomicMax(&st->lo_key, float_key(rho - eps));
+            ++evaluated;
         }
+        __syncwarp();
     }
     if (lane == 0 && evaluated) atomicAdd(&st->n_eval, evaluated);
+}
+
+// After the priority pass: the survivors from the first bucket whose largest
+// bound is already below the running lower bound onward can all be skipped.
+// bucket_end[b] = end of bucket b in the list; bucket b holds gaps with
+// (gap/lim)^2 in [b/NB, (b+1)/NB), i.e. bounds <= cos(lim sqrt(b/NB)) + margin
+// (evaluated with a relative slack on the angle and a doubled margin).
+__global__ void survivor_cut_kernel(TmplState *st, const int *__restrict__ bucket_end) {
+    if (threadIdx.x != 0 || st->flat) return;
+    const float lstar = key_float(st->lo_key);
+    const float lim = st->theta_lim;
+    int cut = st->n_surv;
+    for (int b = 1; b < kUbBuckets; ++b) {
+        const float gmin = lim * sqrtf((float)b / (float)kUbBuckets) * 0.9999f;
+        if (cosf(gmin) + 2.f * kCosMargin < lstar) { cut = bucket_end[b - 1]; break; }
+    }
+    st->n_surv_eff = cut;
 }
 
 // Threshold refinement: FP32 rho at every member of the groups of the
@@ -1080,7 +1095,7 @@ cudaError_t launch_survivors(const uint8_t *I, int pimg, int q, int Lx, const do
                              const double *IIQ, const float *tf, int m, int n, int npad,
                              const float *inv_sigma, TmplState *st, const int *surv,
                              const float *surv_ub, float *surv_rho, float *surv_eps, int cap,
-                             cudaStream_t s) {
+                             const int *bucket_end, cudaStream_t s) {
     int in_smem = 0;
     size_t smem = tmpl_smem(m, npad, &in_smem);
     smem = (smem + 15) & ~(size_t)15;
@@ -1108,6 +1123,11 @@ cudaError_t launch_survivors(const uint8_t *I, int pimg, int q, int Lx, const do
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    {
+        LaunchScope ls("survivor_cut_kernel", s);
+        survivor_cut_kernel<<<1, 32, 0, s>>>(st, bucket_end);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
         LaunchScope ls("survivors_kernel", s);
         survivors_kernel<<<num_sms() * 4, 256, smem, s>>>(I, q, Lx, IIS, IIQ, tf, m, n, npad,
