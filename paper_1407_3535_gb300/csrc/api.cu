@@ -35,6 +35,7 @@ opta_status map_err(cudaError_t e) {
     } while (0)
 
 constexpr int kMaxRadius = 9;
+constexpr int kChunk = 128;   // templates per batch (tensor-core N = 2 * chunk <= 256)
 
 // Device allocation that keeps a running byte count.
 struct DevMem {
@@ -88,8 +89,11 @@ struct opta_handle {
     int *bucket_cnt = nullptr, *bucket_cur = nullptr;
     int *cand = nullptr;
     double *cand_rho = nullptr;
-    float *topk_v = nullptr;
+    float *topk_v = nullptr;                  // chunk x 256 x kTopkMax
     int *topk_i = nullptr;
+    int *cand_topk = nullptr;                 // chunk x kTopkMax threshold centres
+    double *cand_rho_topk = nullptr;
+    TmplIn *tin = nullptr;                    // chunk template descriptors
     float *tf = nullptr, *tstage = nullptr;   // tf: chunk of templates, m x npad each
     double *td = nullptr;                     // chunk of templates, m x n each
     TmplState *states = nullptr;
@@ -423,8 +427,11 @@ opta_status ensure_scratch(opta_handle *H, size_t L, size_t RT, size_t T, size_t
         H->capG = G;
     }
     if (!H->topk_v) {
-        TRY(H->mem.alloc(&H->topk_v, 256 * kTopkMax));
-        TRY(H->mem.alloc(&H->topk_i, 256 * kTopkMax));
+        TRY(H->mem.alloc(&H->topk_v, (size_t)kChunk * 256 * kTopkMax));
+        TRY(H->mem.alloc(&H->topk_i, (size_t)kChunk * 256 * kTopkMax));
+        TRY(H->mem.alloc(&H->cand_topk, (size_t)kChunk * kTopkMax));
+        TRY(H->mem.alloc(&H->cand_rho_topk, (size_t)kChunk * kTopkMax));
+        TRY(H->mem.alloc(&H->tin, (size_t)kChunk));
         TRY(H->mem.alloc(&H->bucket_cnt, kUbBuckets));
         TRY(H->mem.alloc(&H->bucket_cur, kUbBuckets));
     }
@@ -454,20 +461,6 @@ opta_status ensure_scratch(opta_handle *H, size_t L, size_t RT, size_t T, size_t
     return OPTA_OK;
 }
 
-// Device pointer to template data (copies host data into the staging buffer).
-opta_status template_device(opta_handle *H, const opta_template *t, const float **dptr,
-                            int64_t *ld, cudaStream_t s) {
-    if (t->on_device) { *dptr = t->data; *ld = t->stride_elems; return OPTA_OK; }
-    CK(cudaMemcpy2DAsync(H->tstage, (size_t)t->cols * sizeof(float), t->data,
-                         (size_t)t->stride_elems * sizeof(float), (size_t)t->cols * sizeof(float),
-                         t->rows, cudaMemcpyHostToDevice, s));
-    *dptr = H->tstage;
-    *ld = t->cols;
-    return OPTA_OK;
-}
-
-constexpr int kChunk = 128;   // templates per tensor-core batch (N = 2 * chunk <= 256)
-
 bool use_mma(const opta_handle *H) { return H->prm.precision == 1; }
 
 // Scratch needed by a batch of templates (sizes already prepared).
@@ -482,7 +475,7 @@ opta_status size_scratch(opta_handle *H, const opta_template *t, int n_t) {
         const size_t G = (size_t)S->Gy * S->Gx;
         maxL = std::max(maxL, (size_t)S->Ly * S->Lx);
         maxRT = std::max(maxRT, chunk * G);
-        maxT = std::max(maxT, (size_t)m * npad);
+        maxT = std::max(maxT, chunk * (size_t)m * n);
         maxTS = std::max(maxTS, chunk * (size_t)m * npad);
         const size_t N = ((2 * chunk + 15) / 16) * 16;
         if (use_mma(H)) maxB = std::max(maxB, (size_t)m * Kp * N * 2);
@@ -499,20 +492,28 @@ opta_status enqueue_scan1(opta_handle *H, const opta_template *const *t, int n, 
     SizeState *S = H->sizes[std::make_pair(m, nn)];
     const int64_t G = (int64_t)S->Gy * S->Gx;
     const size_t tsz = (size_t)m * npad, dsz = (size_t)m * nn;
-    // template statistics (Eq. rho1's mu_t, sigma_t) into per-template slots
+    // template statistics (Eq. rho1's mu_t, sigma_t) of the whole chunk in one launch
+    std::vector<TmplIn> tin(n);
     for (int k = 0; k < n; ++k) {
-        const float *tin = nullptr;
-        int64_t ld = 0;
-        TRY(template_device(H, t[k], &tin, &ld, s));
-        CK(launch_tmpl_prep(tin, ld, m, nn, npad, H->tf + k * tsz, H->td + k * dsz, st + k,
-                            H->prm.topk, s));
+        if (t[k]->on_device) {
+            tin[k].data = t[k]->data;
+            tin[k].ld = t[k]->stride_elems;
+        } else {
+            float *slot = H->tstage + (size_t)k * m * nn;
+            CK(cudaMemcpy2DAsync(slot, (size_t)nn * sizeof(float), t[k]->data,
+                                 (size_t)t[k]->stride_elems * sizeof(float),
+                                 (size_t)nn * sizeof(float), m, cudaMemcpyHostToDevice, s));
+            tin[k].data = slot;
+            tin[k].ld = nn;
+        }
     }
+    CK(cudaMemcpyAsync(H->tin, tin.data(), n * sizeof(TmplIn), cudaMemcpyHostToDevice, s));
+    CK(launch_tmpl_prep_batch(H->tin, n, m, nn, npad, H->tf, tsz, H->td, dsz, st, H->prm.topk, s));
     // scan 1: rho(t, pivot) at every centre
     if (use_mma(H)) {
         const int N = ((2 * n + 15) / 16) * 16;
         CK(cudaMemsetAsync(H->Bmma, 0, (size_t)m * Kp * N * 2, s));
-        for (int k = 0; k < n; ++k)
-            CK(launch_tmpl_split(H->tf + k * tsz, m, nn, npad, Kp, N, k, H->Bmma, s));
+        CK(launch_tmpl_split(H->tf, tsz, n, m, nn, npad, Kp, N, H->Bmma, s));
         int Gx_u = S->Gx;
         CK(launch_corr_mma(S->P, H->p, H->q, H->Bmma, m, nn, Kp, N, S->h, S->Ly, S->Lx, n,
                            S->c_inv_sigma, S->c_efac, st, H->rho_tc, H->tc, G, H->dev_err,
@@ -526,11 +527,20 @@ opta_status enqueue_scan1(opta_handle *H, const opta_template *const *t, int n, 
                                  S->Lx, S->c_inv_sigma, S->c_efac, st + k, H->rho_tc + k * G,
                                  H->tc + k * G, 0, s));
     }
+    // threshold (Section 6): top-k centres, their exact rho, the members of
+    // their groups -- batched over the chunk
+    CK(launch_topk(H->rho_tc, G, S->Gy, S->Gx, S->h, S->Ly, S->Lx, H->prm.topk, n, st, H->topk_v,
+                   H->topk_i, H->cand_topk, s));
+    CK(launch_refine64_topk(H->I8, H->q, S->Lx, H->td, dsz, m, nn, n, st, H->cand_topk,
+                            H->cand_rho_topk, s));
+    CK(launch_group_members(H->I8, H->q, S->Ly, S->Lx, S->h, H->IIS, H->IIQ, H->tf, tsz, m, nn,
+                            npad, S->inv_sigma, n, st, H->cand_topk, H->prm.topk, s));
+    CK(launch_threshold(st, H->cand_rho_topk, n, s));
     return OPTA_OK;
 }
 
-// Threshold (Section 6), scan 2 (Eq. SEC), survivors and FP64 argmax of the
-// templates whose scan 1 is in the chunk slots.
+// Scan 2 (Eq. SEC), survivors and FP64 argmax, template by template, of the
+// chunk whose scan 1 and threshold are done.
 opta_status enqueue_scan2(opta_handle *H, const opta_template *const *t, int n, TmplState *st,
                           float *ub_map, uint8_t *surv_map, cudaStream_t s) {
     const int m = t[0]->rows, nn = t[0]->cols, npad = (nn + 7) & ~7;
@@ -542,25 +552,17 @@ opta_status enqueue_scan2(opta_handle *H, const opta_template *const *t, int n, 
         const float *tf = H->tf + k * tsz;
         const double *td = H->td + k * dsz;
         TmplState *sk = st + k;
-        CK(launch_topk(H->rho_tc + k * G, S->Gy, S->Gx, S->h, S->Ly, S->Lx, H->prm.topk, sk,
-                       H->topk_v, H->topk_i, H->cand, s));
-        CK(launch_refine64(H->I8, H->q, S->Lx, td, m, nn, sk, H->cand, H->cand_rho,
-                           capL + kTopkMax, true, s));
-        CK(launch_group_members(H->I8, H->q, S->Ly, S->Lx, S->h, H->IIS, H->IIQ, tf, m, nn, npad,
-                                S->inv_sigma, sk, H->cand, H->prm.topk, s));
-        CK(launch_threshold(sk, H->cand_rho, s));
         CK(launch_bound_compact(H->tc + k * G, S->theta_co, S->Ly, S->Lx, S->h, sk, H->surv,
                                 H->surv_ub, capL, reinterpret_cast<int *>(H->ubbuf), ub_map, surv_map,
-                                H->bucket_cnt,
-                                H->bucket_cur, s));
+                                H->bucket_cnt, H->bucket_cur, s));
         CK(launch_survivors(H->I8, H->p, H->q, S->Lx, H->IIS, H->IIQ, tf, m, nn, npad, S->inv_sigma, sk,
                             H->surv, H->surv_ub, H->surv_rho, H->surv_eps, capL, H->bucket_cur,
                             s));
         CK(launch_surv_candidates(sk, H->surv, H->surv_ub, H->surv_rho, H->surv_eps, H->cand,
-                                  capL + kTopkMax, s));
-        CK(launch_refine64(H->I8, H->q, S->Lx, td, m, nn, sk, H->cand, H->cand_rho,
-                           capL + kTopkMax, false, s));
-        CK(launch_final_argmax(sk, H->cand, H->cand_rho, capL + kTopkMax, s));
+                                  capL, s));
+        CK(launch_refine64(H->I8, H->q, S->Lx, td, m, nn, sk, H->cand, H->cand_rho, capL, false, s));
+        CK(launch_final_argmax(sk, H->cand, H->cand_rho, capL, H->cand_topk + k * kTopkMax,
+                               H->cand_rho_topk + k * kTopkMax, s));
     }
     return OPTA_OK;
 }
@@ -685,6 +687,7 @@ opta_status optA_destroy(opta_handle *h) {
     }
     void *ptrs[] = {h->I8, h->IIS, h->IIQ, h->rho_tc, h->tc, h->surv, h->surv_rho, h->surv_eps,
                     h->surv_ub, h->ubbuf, h->bucket_cnt, h->bucket_cur, h->Bmma, h->dev_err,
+                    h->cand_topk, h->cand_rho_topk, h->tin,
                     h->cand, h->cand_rho, h->topk_v, h->topk_i, h->tf, h->tstage, h->td,
                     h->states, h->weights, h->radius};
     for (void *p : ptrs) if (p) cudaFree(p);
@@ -921,7 +924,7 @@ opta_status zncc_full(const opta_image *img, const opta_template *t, float *rho_
     ZCK(launch_zncc_map(I8, p, q, tf, m, n, npad, inv, ef, st, map, s));
     ZCK(launch_map_candidates(map, ef, L, m, n, st, cand, (int)L, s));
     ZCK(launch_refine64(I8, q, Lx, td, m, n, st, cand, cand_rho, (int)L, false, s));
-    ZCK(launch_final_argmax(st, cand, cand_rho, (int)L, s));
+    ZCK(launch_final_argmax(st, cand, cand_rho, (int)L, nullptr, nullptr, s));
     TmplState hs;
     ZCK(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
     ZCK(cudaStreamSynchronize(s));

@@ -73,6 +73,12 @@ struct TmplState {
 // they are evaluated roughly in decreasing bound order.
 constexpr int kUbBuckets = 256;
 
+// Device pointer and row stride of one template of a batch.
+struct TmplIn {
+    const float *data;
+    int64_t ld;
+};
+
 // ---------------------------------------------------------------------------
 // Launchers (stream-ordered, return cudaError_t of the launch).
 // ---------------------------------------------------------------------------
@@ -95,6 +101,10 @@ cudaError_t launch_ingest_u8(const uint8_t *src, int64_t ld, int p, int q, uint8
 // Template statistics: tf (m x npad, FP32, zero padded) and td (m x n, FP64) hold t - mu.
 cudaError_t launch_tmpl_prep(const float *t, int64_t ld, int m, int n, int npad,
                              float *tf, double *td, TmplState *st, int topk, cudaStream_t s);
+// The same for T templates (tin: T device descriptors), outputs at k * tsz / k * dsz / st + k.
+cudaError_t launch_tmpl_prep_batch(const TmplIn *tin, int T, int m, int n, int npad, float *tf,
+                                   size_t tsz, double *td, size_t dsz, TmplState *st, int topk,
+                                   cudaStream_t s);
 
 // Exhaustive FP32 map (Eq. rho1 with v = I - 128), plus the certain lower bound key.
 cudaError_t launch_zncc_map(const uint8_t *I, int p, int q, const float *tf, int m, int n,
@@ -104,13 +114,17 @@ cudaError_t launch_zncc_map(const uint8_t *I, int p, int q, const float *tf, int
 cudaError_t launch_map_candidates(const float *map, const float *efac128, int64_t L, int m,
                                   int n, TmplState *st, int *cand, int cap, cudaStream_t s);
 
-// FP64 recomputation of rho at the candidate locations [from, n_cand).
+// FP64 recomputation of rho at the candidate locations [0, n_cand).
 cudaError_t launch_refine64(const uint8_t *I, int q, int Lx, const double *td, int m, int n,
                             TmplState *st, const int *cand, double *cand_rho, int cap,
                             bool topk_range, cudaStream_t s);
-// Final argmax over candidates -> st->best_idx / best_rho.
+// Final argmax over candidates and threshold centres (nullable) -> st->best_idx / best_rho.
 cudaError_t launch_final_argmax(TmplState *st, const int *cand, const double *cand_rho, int cap,
-                                cudaStream_t s);
+                                const int *cand_topk, const double *cand_rho_topk, cudaStream_t s);
+// FP64 rho at the threshold centres of T templates (kTopkMax slots each).
+cudaError_t launch_refine64_topk(const uint8_t *I, int q, int Lx, const double *td, size_t dsz,
+                                 int m, int n, int T, TmplState *st, const int *cand_topk,
+                                 double *cand_rho_topk, cudaStream_t s);
 
 // --- pruned search ---
 // rho_tc per group and the angle interval of its true value (tc), for the
@@ -129,17 +143,19 @@ cudaError_t launch_centre_column(const uint8_t *P, int q, const float *tf, int m
                                  size_t tsz, int h, int Ly, int Lx, int gx, int T,
                                  const float *c_inv_sigma, const float *c_efac, const TmplState *st,
                                  float *rho_tc, float2 *tc, int64_t gstride, cudaStream_t s);
-cudaError_t launch_tmpl_split(const float *tf, int m, int n, int npad, int Kp, int N, int t,
-                              void *B, cudaStream_t s);
-cudaError_t launch_topk(const float *rho_tc, int Gy, int Gx, int h, int Ly, int Lx, int k,
-                        TmplState *st, float *tmp_val, int *tmp_idx, int *cand,
+cudaError_t launch_tmpl_split(const float *tf, size_t tsz, int T, int m, int n, int npad, int Kp,
+                              int N, void *B, cudaStream_t s);
+// Threshold centres of T templates: rho_tc of template k at k * gstride;
+// tmp_val/tmp_idx: T x 256 x kTopkMax; cand_topk: T x kTopkMax.
+cudaError_t launch_topk(const float *rho_tc, int64_t gstride, int Gy, int Gx, int h, int Ly, int Lx,
+                        int k, int T, TmplState *st, float *tmp_val, int *tmp_idx, int *cand_topk,
                         cudaStream_t s);
-cudaError_t launch_threshold(TmplState *st, const double *cand_rho, cudaStream_t s);
+cudaError_t launch_threshold(TmplState *st, const double *cand_rho_topk, int T, cudaStream_t s);
 // FP32 rho at the members of the threshold centres' groups (raises lo_key).
 cudaError_t launch_group_members(const uint8_t *I, int q, int Ly, int Lx, int h, const double *IIS,
-                                 const double *IIQ, const float *tf, int m, int n, int npad,
-                                 const float *inv_sigma, TmplState *st, const int *cand, int topk,
-                                 cudaStream_t s);
+                                 const double *IIQ, const float *tf, size_t tsz, int m, int n,
+                                 int npad, const float *inv_sigma, int T, TmplState *st,
+                                 const int *cand_topk, int topk, cudaStream_t s);
 // Scan 2: bound of every location, bucket histogram of the survivors and
 // survivor count per chunk of 4096 locations (chunk_cnt: ceil(L/4096) ints),
 // then compaction of the survivors in bucket order with their upper bound;

@@ -192,9 +192,12 @@ __global__ void __launch_bounds__(128, 1) corr_mma_kernel(const CorrMmaArgs a) {
     if (warp == 0) tc5::tmem_dealloc(tmem, ncols);
 }
 
-// Template t' (FP32, m x npad) -> hi/lo bf16 planes 2t, 2t+1 of the B buffer.
-__global__ void tmpl_split_kernel(const float *__restrict__ tf, int m, int n, int npad, int Kp,
-                                  int N, int t, __nv_bfloat16 *B) {
+// Template t' (FP32, m x npad) -> hi/lo bf16 planes 2t, 2t+1 of the B buffer;
+// template t = t0 + blockIdx.y, whose t' is at tf + blockIdx.y * tsz.
+__global__ void tmpl_split_kernel(const float *__restrict__ tf, size_t tsz, int m, int n, int npad,
+                                  int Kp, int N, int t0, __nv_bfloat16 *B) {
+    const int t = t0 + blockIdx.y;
+    tf += blockIdx.y * tsz;
     const int total = m * Kp;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += gridDim.x * blockDim.x) {
@@ -216,12 +219,12 @@ size_t corr_mma_smem(int h, int Kp, int N) {
     return 1024 + 2 * round_up(WA * 128u, 1024) + 2 * round_up((uint32_t)N * Kp * 2u, 1024);
 }
 
-cudaError_t launch_tmpl_split(const float *tf, int m, int n, int npad, int Kp, int N, int t,
-                              void *B, cudaStream_t s) {
+cudaError_t launch_tmpl_split(const float *tf, size_t tsz, int T, int m, int n, int npad, int Kp,
+                              int N, void *B, cudaStream_t s) {
     LaunchScope ls("tmpl_split_kernel", s);
     const int total = m * Kp;
-    tmpl_split_kernel<<<(total + 255) / 256, 256, 0, s>>>(tf, m, n, npad, Kp, N, t,
-                                                          static_cast<__nv_bfloat16 *>(B));
+    tmpl_split_kernel<<<dim3((total + 255) / 256, T), 256, 0, s>>>(
+        tf, tsz, m, n, npad, Kp, N, 0, static_cast<__nv_bfloat16 *>(B));
     return cudaGetLastError();
 }
 

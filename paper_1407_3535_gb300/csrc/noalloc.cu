@@ -170,7 +170,7 @@ extern "C" opta_status zncc_full_noalloc(const opta_image *img, const opta_templ
     NA(launch_zncc_map(I8, p, q, tf, m, n, npad, inv, ef, st, map, s));
     NA(launch_map_candidates(map, ef, L, m, n, st, cand, (int)L, s));
     NA(launch_refine64(I8, q, Lx, td, m, n, st, cand, crho, (int)L, false, s));
-    NA(launch_final_argmax(st, cand, crho, (int)L, s));
+    NA(launch_final_argmax(st, cand, crho, (int)L, nullptr, nullptr, s));
     TmplState hs;
     NA(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
     NA(cudaStreamSynchronize(s));

@@ -59,10 +59,17 @@ __device__ double block_sum_d(double v, double *sh) {
 // Template statistics (Eq. rho1's mu_t and sigma_t), two FP64 passes.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024)
-tmpl_prep_kernel(const float *__restrict__ t, int64_t ld, int m, int n, int npad,
-                 float *tf, double *td, TmplState *st, int topk) {
+tmpl_prep_kernel(const float *__restrict__ t, int64_t ld, const TmplIn *__restrict__ tin, int m,
+                 int n, int npad, float *tf, size_t tsz, double *td, size_t dsz, TmplState *st,
+                 int topk) {
     __shared__ double sh[32];
     const int mn = m * n;
+    // block k prepares template k of the batch
+    const int k = blockIdx.x;
+    if (tin) { t = tin[k].data; ld = tin[k].ld; }
+    tf += k * tsz;
+    td += k * dsz;
+    st += k;
     double s = 0.0;
     for (int i = threadIdx.x; i < mn; i += blockDim.x) s += (double)t[(int64_t)(i / n) * ld + (i % n)];
     s = block_sum_d(s, sh);
@@ -227,7 +234,7 @@ __global__ void map_candidates_kernel(const float *__restrict__ map, const float
 // ---------------------------------------------------------------------------
 // FP64 recomputation of Eq. rho1 at candidate locations (two passes, as the
 // definition reads).  One block per candidate.
-// mode 0: candidates [0, n_topk)   mode 1: [n_topk, n_cand)
+// Candidates [0, n_cand) of one template.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 refine64_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__restrict__ td,
@@ -235,9 +242,8 @@ refine64_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__re
                 int mode, int cap) {
     __shared__ double sh[32];
     if (st->flat) return;
-    int from, to;
-    if (mode == 0) { from = 0; to = min(st->n_topk, cap); }
-    else { from = st->n_topk; to = min(st->n_cand, cap); }
+    (void)mode;
+    const int from = 0, to = min(st->n_cand, cap);
     const int mn = m * n;
     for (int c = from + blockIdx.x; c < to; c += gridDim.x) {
         const int idx = cand[c];
@@ -260,10 +266,44 @@ refine64_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__re
     }
 }
 
-// Argmax of (rho64, -index) over all candidates; one block.
+// FP64 rho at the threshold centres of a batch: block (j, k) takes centre j
+// of template k.
+__global__ void __launch_bounds__(256)
+refine64_topk_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__restrict__ td,
+                     size_t dsz, int m, int n, TmplState *st, const int *__restrict__ cand_topk,
+                     double *cand_rho_topk) {
+    __shared__ double sh[32];
+    const int j = blockIdx.x, k = blockIdx.y;
+    st += k;
+    if (st->flat || j >= st->n_topk) return;
+    td += k * dsz;
+    const int mn = m * n;
+    const int idx = cand_topk[k * kTopkMax + j];
+    const int y = idx / Lx, x = idx % Lx;
+    long long si = 0;
+    for (int i = threadIdx.x; i < mn; i += blockDim.x)
+        si += I[(int64_t)(y + i / n) * q + x + (i % n)];
+    const double S = block_sum_d((double)si, sh);
+    const double mu = S / (double)mn;
+    double num = 0.0, vv = 0.0;
+    for (int i = threadIdx.x; i < mn; i += blockDim.x) {
+        const double d = (double)I[(int64_t)(y + i / n) * q + x + (i % n)] - mu;
+        num += td[i] * d;
+        vv += d * d;
+    }
+    num = block_sum_d(num, sh);
+    vv = block_sum_d(vv, sh);
+    if (threadIdx.x == 0)
+        cand_rho_topk[k * kTopkMax + j] =
+            (vv == 0.0 || st->sigma == 0.0) ? 0.0 : num / (sqrt(vv) * st->sigma);
+}
+
+// Argmax of (rho64, -index) over the survivor candidates and the threshold
+// centres of one template; one block.
 __global__ void __launch_bounds__(256)
 final_argmax_kernel(TmplState *st, const int *__restrict__ cand,
-                    const double *__restrict__ cand_rho, int cap) {
+                    const double *__restrict__ cand_rho, int cap, const int *__restrict__ ctk,
+                    const double *__restrict__ crtk) {
     __shared__ double sv[256];
     __shared__ int si[256];
     const int nc = min(st->n_cand, cap);
@@ -273,6 +313,11 @@ final_argmax_kernel(TmplState *st, const int *__restrict__ cand,
         for (int c = threadIdx.x; c < nc; c += blockDim.x) {
             const double v = cand_rho[c];
             const int i = cand[c];
+            if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+        }
+        if (ctk && (int)threadIdx.x < st->n_topk) {
+            const double v = crtk[threadIdx.x];
+            const int i = ctk[threadIdx.x];
             if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
         }
     }
@@ -289,7 +334,7 @@ final_argmax_kernel(TmplState *st, const int *__restrict__ cand,
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        if (st->flat || nc == 0) { st->best_idx = 0; st->best_rho = 0.0; }
+        if (st->flat || si[0] == 0x7fffffff) { st->best_idx = 0; st->best_rho = 0.0; }
         else { st->best_idx = si[0]; st->best_rho = sv[0]; }
     }
 }
@@ -435,10 +480,15 @@ __device__ inline void block_topk(float *sv, int *si, int n, int k, float *out_v
 }
 
 __global__ void __launch_bounds__(256)
-topk_stage1_kernel(const float *__restrict__ rho_tc, int G, int k, float *tmp_v, int *tmp_i,
-                   TmplState *st) {
+topk_stage1_kernel(const float *__restrict__ rho_tc, int G, int64_t gstride, int k, float *tmp_v,
+                   int *tmp_i, TmplState *st) {
     __shared__ float sv[256 * TOPK_PER_THREAD];
     __shared__ int si[256 * TOPK_PER_THREAD];
+    // blockIdx.y: template of the batch
+    st += blockIdx.y;
+    rho_tc += blockIdx.y * gstride;
+    tmp_v += (size_t)blockIdx.y * 256 * TOPK_MAX;
+    tmp_i += (size_t)blockIdx.y * 256 * TOPK_MAX;
     if (st->flat) return;
     float v[TOPK_PER_THREAD];
     int ix[TOPK_PER_THREAD];
@@ -477,6 +527,11 @@ topk_stage2_kernel(const float *__restrict__ tmp_v, const int *__restrict__ tmp_
     extern __shared__ float t2sm[];
     float *sv = t2sm;
     int *si = reinterpret_cast<int *>(t2sm + nb * k);
+    // blockIdx.x: template of the batch; cand: its kTopkMax threshold slots
+    st += blockIdx.x;
+    tmp_v += (size_t)blockIdx.x * 256 * TOPK_MAX;
+    tmp_i += (size_t)blockIdx.x * 256 * TOPK_MAX;
+    cand += blockIdx.x * TOPK_MAX;
     if (st->flat) return;
     for (int j = threadIdx.x; j < nb * k; j += blockDim.x) {
         const int b = j / k, r = j % k;
@@ -498,12 +553,13 @@ topk_stage2_kernel(const float *__restrict__ tmp_v, const int *__restrict__ tmp_
             cand[cnt++] = cy * Lx + cx;
         }
         st->n_topk = cnt;
-        st->n_cand = cnt;
     }
 }
 
 // thr = max exact rho over the threshold centres; thr_lo = float below thr - 1e-9.
 __global__ void threshold_kernel(TmplState *st, const double *__restrict__ cand_rho) {
+    st += blockIdx.x;
+    cand_rho += blockIdx.x * kTopkMax;
     if (threadIdx.x != 0 || st->flat) return;
     double thr = -2.0;
     for (int c = 0; c < st->n_topk; ++c) thr = fmax(thr, cand_rho[c]);
@@ -540,12 +596,28 @@ constexpr int SC_PER = 16;
 constexpr int kChunkLoc = 256 * SC_PER;
 
 __device__ inline float loc_gap(const float2 *__restrict__ tc, const float2 *__restrict__ theta_co,
-                                int Lx, int h, int Gx, int64_t i) {
-    const int y = (int)(i / Lx), x = (int)(i % Lx);
-    const float2 t = tc[(y / h) * Gx + (x / h)];
+                                int Gx, int64_t i, int y, int x, int gyrow, float inv_h) {
+    // x / h by a rounded reciprocal: exact for x < 2^20 and h <= 9
+    const int gx = (int)(((float)x + 0.5f) * inv_h);
+    const float2 t = tc[gyrow * Gx + gx];
     const float2 c = theta_co[i];
+    (void)y;
     return fmaxf(0.f, fmaxf(t.x - c.y, c.x - t.y));
 }
+
+// Row/column of location i, advanced incrementally by `step` locations.
+struct LocCursor {
+    int y, x;
+    __device__ LocCursor(int64_t i, int Lx) {
+        const int ii = (int)i;
+        y = ii / Lx;
+        x = ii - y * Lx;
+    }
+    __device__ void advance(int step, int Lx) {
+        x += step;
+        while (x >= Lx) { x -= Lx; ++y; }
+    }
+};
 
 // Pass 1: survivor histogram by bucket, and the survivor count of every chunk.
 __global__ void __launch_bounds__(256)
@@ -558,19 +630,23 @@ bound_hist_kernel(const float2 *__restrict__ tc, const float2 *__restrict__ thet
     for (int i = threadIdx.x; i < kUbBuckets; i += blockDim.x) hist[i] = 0;
     const int Gx = groups_along(Lx, h);
     const float lim = st->theta_lim;
+    const float inv_h = 1.f / (float)h;
     const int64_t L = (int64_t)Ly * Lx;
     const int64_t nchunks = (L + kChunkLoc - 1) / kChunkLoc;
     for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
         if (threadIdx.x == 0) ccount = 0;
         __syncthreads();
         int mine = 0;
+        LocCursor cur(c * kChunkLoc + threadIdx.x, Lx);
 #pragma unroll 4
         for (int k = 0; k < SC_PER; ++k) {
             const int64_t i = c * kChunkLoc + k * 256 + threadIdx.x;
             bool f = false;
             int b = -1;
+            if (k) cur.advance(256, Lx);
             if (i < L) {
-                const float gap = loc_gap(tc, theta_co, Lx, h, Gx, i);
+                const int gyrow = (int)(((float)cur.y + 0.5f) * inv_h);
+                const float gap = loc_gap(tc, theta_co, Gx, i, cur.y, cur.x, gyrow, inv_h);
                 f = gap <= lim;
                 if (ub_map) ub_map[i] = cosf(gap) + kCosMargin;
                 if (surv_map) surv_map[i] = f ? 1 : 0;
@@ -628,6 +704,7 @@ bound_scatter_kernel(const float2 *__restrict__ tc, const float2 *__restrict__ t
     if (st->flat) return;
     const int Gx = groups_along(Lx, h);
     const float lim = st->theta_lim;
+    const float inv_h = 1.f / (float)h;
     const int64_t L = (int64_t)Ly * Lx;
     const int64_t nchunks = (L + kChunkLoc - 1) / kChunkLoc;
     for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
@@ -636,10 +713,14 @@ bound_scatter_kernel(const float2 *__restrict__ tc, const float2 *__restrict__ t
         __syncthreads();
         float g[SC_PER];
         int bk[SC_PER];
+        LocCursor cur(c * kChunkLoc + threadIdx.x, Lx);
 #pragma unroll
         for (int k = 0; k < SC_PER; ++k) {
             const int64_t i = c * kChunkLoc + k * 256 + threadIdx.x;
-            g[k] = i < L ? loc_gap(tc, theta_co, Lx, h, Gx, i) : 4.f;
+            if (k) cur.advance(256, Lx);
+            g[k] = i < L ? loc_gap(tc, theta_co, Gx, i, cur.y, cur.x,
+                                   (int)(((float)cur.y + 0.5f) * inv_h), inv_h)
+                         : 4.f;
             bk[k] = g[k] <= lim ? gap_bucket(g[k], lim) : -1;
             if (bk[k] >= 0) atomicAdd(&cnt[bk[k]], 1);
         }
@@ -883,11 +964,15 @@ __global__ void survivor_cut_kernel(TmplState *st, const int *__restrict__ bucke
 __global__ void __launch_bounds__(256)
 group_members_kernel(const uint8_t *__restrict__ I, int q, int Ly, int Lx, int h,
                      const double *__restrict__ IIS, const double *__restrict__ IIQ,
-                     const float *__restrict__ tf, int m, int n, int npad,
+                     const float *__restrict__ tf, size_t tsz, int m, int n, int npad,
                      const float *__restrict__ inv_sigma, TmplState *st,
                      const int *__restrict__ cand, int tmpl_in_smem) {
     extern __shared__ float4 gsm4[];
-    if (st->flat) return;
+    // blockIdx.y: template of the batch; blockIdx.x: its threshold centre
+    st += blockIdx.y;
+    tf += blockIdx.y * tsz;
+    cand += blockIdx.y * kTopkMax;
+    if (st->flat || (int)blockIdx.x >= st->n_topk) return;
     const float *tm = stage_template(tf, m, npad, tmpl_in_smem, reinterpret_cast<float *>(gsm4));
     const int k = blockIdx.x;
     if (k >= st->n_topk) return;
@@ -936,7 +1021,15 @@ static int grid_cap(int64_t n, int threads, int per_sm) {
 cudaError_t launch_tmpl_prep(const float *t, int64_t ld, int m, int n, int npad, float *tf,
                              double *td, TmplState *st, int topk, cudaStream_t s) {
     LaunchScope ls_tmpl_prep_kernel("tmpl_prep_kernel", s);
-    tmpl_prep_kernel<<<1, 1024, 0, s>>>(t, ld, m, n, npad, tf, td, st, topk);
+    tmpl_prep_kernel<<<1, 1024, 0, s>>>(t, ld, nullptr, m, n, npad, tf, 0, td, 0, st, topk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tmpl_prep_batch(const TmplIn *tin, int T, int m, int n, int npad, float *tf,
+                                   size_t tsz, double *td, size_t dsz, TmplState *st, int topk,
+                                   cudaStream_t s) {
+    LaunchScope ls("tmpl_prep_kernel", s);
+    tmpl_prep_kernel<<<T, 1024, 0, s>>>(nullptr, 0, tin, m, n, npad, tf, tsz, td, dsz, st, topk);
     return cudaGetLastError();
 }
 
@@ -976,9 +1069,18 @@ cudaError_t launch_refine64(const uint8_t *I, int q, int Lx, const double *td, i
 }
 
 cudaError_t launch_final_argmax(TmplState *st, const int *cand, const double *cand_rho, int cap,
-                                cudaStream_t s) {
+                                const int *cand_topk, const double *cand_rho_topk, cudaStream_t s) {
     LaunchScope ls_final_argmax_kernel("final_argmax_kernel", s);
-    final_argmax_kernel<<<1, 256, 0, s>>>(st, cand, cand_rho, cap);
+    final_argmax_kernel<<<1, 256, 0, s>>>(st, cand, cand_rho, cap, cand_topk, cand_rho_topk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine64_topk(const uint8_t *I, int q, int Lx, const double *td, size_t dsz,
+                                 int m, int n, int T, TmplState *st, const int *cand_topk,
+                                 double *cand_rho_topk, cudaStream_t s) {
+    LaunchScope ls("refine64_topk_kernel", s);
+    refine64_topk_kernel<<<dim3(kTopkMax, T), 256, 0, s>>>(I, q, Lx, td, dsz, m, n, st, cand_topk,
+                                                           cand_rho_topk);
     return cudaGetLastError();
 }
 
@@ -1024,29 +1126,30 @@ cudaError_t launch_centre_column(const uint8_t *P, int q, const float *tf, int m
     return cudaGetLastError();
 }
 
-cudaError_t launch_topk(const float *rho_tc, int Gy, int Gx, int h, int Ly, int Lx, int k,
-                        TmplState *st, float *tmp_val, int *tmp_idx, int *cand, cudaStream_t s) {
+cudaError_t launch_topk(const float *rho_tc, int64_t gstride, int Gy, int Gx, int h, int Ly, int Lx,
+                        int k, int T, TmplState *st, float *tmp_val, int *tmp_idx, int *cand_topk,
+                        cudaStream_t s) {
     const int G = Gy * Gx;
     if (k > TOPK_MAX) k = TOPK_MAX;
     if (k < 1) k = 1;
     const int nb = topk_blocks(G);
     {
         LaunchScope ls("topk_stage1_kernel", s);
-        topk_stage1_kernel<<<nb, 256, 0, s>>>(rho_tc, G, k, tmp_val, tmp_idx, st);
+        topk_stage1_kernel<<<dim3(nb, T), 256, 0, s>>>(rho_tc, G, gstride, k, tmp_val, tmp_idx, st);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = (size_t)nb * k * (sizeof(float) + sizeof(int));
     {
         LaunchScope ls("topk_stage2_kernel", s);
-        topk_stage2_kernel<<<1, 256, smem, s>>>(tmp_val, tmp_idx, nb, k, Gx, h, Ly, Lx, st, cand);
+        topk_stage2_kernel<<<T, 256, smem, s>>>(tmp_val, tmp_idx, nb, k, Gx, h, Ly, Lx, st, cand_topk);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_threshold(TmplState *st, const double *cand_rho, cudaStream_t s) {
+cudaError_t launch_threshold(TmplState *st, const double *cand_rho_topk, int T, cudaStream_t s) {
     LaunchScope ls_threshold_kernel("threshold_kernel", s);
-    threshold_kernel<<<1, 32, 0, s>>>(st, cand_rho);
+    threshold_kernel<<<T, 32, 0, s>>>(st, cand_rho_topk);
     return cudaGetLastError();
 }
 
@@ -1139,9 +1242,9 @@ cudaError_t launch_survivors(const uint8_t *I, int pimg, int q, int Lx, const do
 }
 
 cudaError_t launch_group_members(const uint8_t *I, int q, int Ly, int Lx, int h, const double *IIS,
-                                 const double *IIQ, const float *tf, int m, int n, int npad,
-                                 const float *inv_sigma, TmplState *st, const int *cand, int topk,
-                                 cudaStream_t s) {
+                                 const double *IIQ, const float *tf, size_t tsz, int m, int n,
+                                 int npad, const float *inv_sigma, int T, TmplState *st,
+                                 const int *cand_topk, int topk, cudaStream_t s) {
     int in_smem = 0;
     const size_t smem = tmpl_smem(m, npad, &in_smem);
     static size_t attr = 0;
@@ -1152,8 +1255,8 @@ cudaError_t launch_group_members(const uint8_t *I, int q, int Ly, int Lx, int h,
         attr = smem;
     }
     LaunchScope ls("group_members_kernel", s);
-    group_members_kernel<<<topk, 256, smem, s>>>(I, q, Ly, Lx, h, IIS, IIQ, tf, m, n, npad,
-                                                 inv_sigma, st, cand, in_smem);
+    group_members_kernel<<<dim3(topk, T), 256, smem, s>>>(I, q, Ly, Lx, h, IIS, IIQ, tf, tsz, m, n,
+                                                          npad, inv_sigma, st, cand_topk, in_smem);
     return cudaGetLastError();
 }
 
