@@ -83,10 +83,12 @@ __global__ void blur_corr_kernel(const double *__restrict__ IIS, const double *_
         const double S = box(IIS, q1, y, x, m, n), Q = box(IIQ, q1, y, x, m, n);
         const double Sp = box(PS, q1, y, x, m, n), Qp = box(PQ, q1, y, x, m, n);
         const double X = box(PX, q1, y, x, m, n);
+        // numerator and variances are exact in FP64 (integers < 2^53); the
+        // quotient only drives the lambda decision and is finished in FP32
         const double dB = mn * Q - S * S, dA = mn * Qp - Sp * Sp;
         const double num = mn * X - Sp * S;
         float r = 0.f;
-        if (dA > 0.0 && dB > 0.0) r = (float)(num / sqrt(dA * dB));
+        if (dA > 0.0 && dB > 0.0) r = (float)num / sqrtf((float)dA * (float)dB);
         if (R) R[i] = r;
         if (fail && dB > 0.0 && r < lambda) {
             int *f = fail + (y / block) * bq + (x / block);
@@ -108,11 +110,12 @@ __global__ void centre_stats_kernel(const double *__restrict__ PS, const double 
         const int cy = group_centre_of((int)(g / Gx), Ly, h);
         const int cx = group_centre_of((int)(g % Gx), Lx, h);
         const double S = box(PS, q1, cy, cx, m, n), Q = box(PQ, q1, cy, cx, m, n);
-        const double var = mn * Q - S * S;
+        const double var = mn * Q - S * S;   // exact
         float is = 0.f, ef = 0.f;
         if (var > 0.0) {
-            is = (float)sqrt(mn / var);
-            ef = (float)sqrt(mn * (Q - 256.0 * S + 16384.0 * mn) / var);
+            const float fv = (float)var, fmn = (float)mn;
+            is = sqrtf(fmn / fv);
+            ef = sqrtf(fmn * (float)(Q - 256.0 * S + 16384.0 * mn) / fv);
         }
         c_inv_sigma[g] = is;
         c_efac[g] = ef;

@@ -946,16 +946,21 @@ survivors_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__r
 // bucket_end[b] = end of bucket b in the list; bucket b holds gaps with
 // (gap/lim)^2 in [b/NB, (b+1)/NB), i.e. bounds <= cos(lim sqrt(b/NB)) + margin
 // (evaluated with a relative slack on the angle and a doubled margin).
-__global__ void survivor_cut_kernel(TmplState *st, const int *__restrict__ bucket_end) {
-    if (threadIdx.x != 0 || st->flat) return;
+__global__ void __launch_bounds__(kUbBuckets)
+survivor_cut_kernel(TmplState *st, const int *__restrict__ bucket_end) {
+    __shared__ int first;
+    if (st->flat) return;
+    if (threadIdx.x == 0) first = kUbBuckets;
+    __syncthreads();
     const float lstar = key_float(st->lo_key);
     const float lim = st->theta_lim;
-    int cut = st->n_surv;
-    for (int b = 1; b < kUbBuckets; ++b) {
+    const int b = threadIdx.x;
+    if (b >= 1) {
         const float gmin = lim * sqrtf((float)b / (float)kUbBuckets) * 0.9999f;
-        if (cosf(gmin) + 2.f * kCosMargin < lstar) { cut = bucket_end[b - 1]; break; }
+        if (cosf(gmin) + 2.f * kCosMargin < lstar) atomicMin(&first, b);
     }
-    st->n_surv_eff = cut;
+    __syncthreads();
+    if (threadIdx.x == 0) st->n_surv_eff = first < kUbBuckets ? bucket_end[first - 1] : st->n_surv;
 }
 
 // Threshold refinement: FP32 rho at every member of the groups of the
@@ -1215,28 +1220,20 @@ cudaError_t launch_survivors(const uint8_t *I, int pimg, int q, int Lx, const do
         attr = smem;
     }
     const uint8_t *iend = I + (int64_t)q * pimg;
-    // priority phase: the first (largest-bound) survivors on part of the GPU,
-    // so the running threshold rises before the full sweep of the rest
-    constexpr int kPriority = 2048;
+    // buckets whose largest bound is below the certain lower bound already
+    // reached (threshold centres and their groups) are cut off, then one sweep
     {
-        LaunchScope ls("survivors_kernel", s);
-        survivors_kernel<<<64, 256, smem, s>>>(I, q, Lx, IIS, IIQ, tf, m, n, npad, inv_sigma, st,
-                                               surv, surv_ub, surv_rho, surv_eps, cap, in_smem, 0,
-                                               kPriority, stage, iend);
+        LaunchScope ls("survivor_cut_kernel", s);
+        survivor_cut_kernel<<<1, kUbBuckets, 0, s>>>(st, bucket_end);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     {
-        LaunchScope ls("survivor_cut_kernel", s);
-        survivor_cut_kernel<<<1, 32, 0, s>>>(st, bucket_end);
-    }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    {
         LaunchScope ls("survivors_kernel", s);
         survivors_kernel<<<num_sms() * 4, 256, smem, s>>>(I, q, Lx, IIS, IIQ, tf, m, n, npad,
                                                           inv_sigma, st, surv, surv_ub, surv_rho,
-                                                          surv_eps, cap, in_smem, kPriority,
-                                                          0x7fffffff, stage, iend);
+                                                          surv_eps, cap, in_smem, 0, 0x7fffffff,
+                                                          stage, iend);
     }
     return cudaGetLastError();
 }

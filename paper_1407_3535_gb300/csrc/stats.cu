@@ -134,9 +134,11 @@ __global__ void window_stats_kernel(const double *__restrict__ IIS, const double
         const double var = mn * Q - S * S;          // exact: mn * Omega^2
         float inv = 0.f, ef = 0.f;
         if (var > 0.0) {
-            inv = (float)sqrt(mn / var);
-            const double c2 = Q - 256.0 * S + 16384.0 * mn;   // sum (I - 128)^2
-            ef = (float)sqrt(mn * c2 / var);
+            // FP32 finish (a few ulp; the error bounds that use 1/Omega allow 8u)
+            const float fv = (float)var, fmn = (float)mn;
+            inv = sqrtf(fmn / fv);
+            const double c2 = Q - 256.0 * S + 16384.0 * mn;   // sum (I - 128)^2, exact
+            ef = sqrtf(fmn * (float)c2 / fv);
         }
         inv_sigma[i] = inv;
         if (efac128) efac128[i] = ef;

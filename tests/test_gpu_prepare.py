@@ -46,7 +46,7 @@ def test_window_stats(opta, shape, m, n):
     exp = _window_inv_sigma(img, m, n)
     assert np.array_equal(got == 0, exp == 0)
     nz = exp > 0
-    assert np.allclose(got[nz], exp[nz], rtol=2e-7, atol=0)
+    assert np.allclose(got[nz], exp[nz], rtol=1e-6, atol=0)   # FP32 finish: a few ulp
 
 
 def test_blur_matches_definition(opta):
