@@ -64,6 +64,7 @@ struct SizeState {
     uint8_t *P = nullptr;          // pivot image (owned unless it aliases the image)
     bool P_owned = false;
     float *inv_sigma = nullptr;    // L
+    float *wsum = nullptr;         // L window sums of I (exact in FP32)
     float *rho_co = nullptr;       // L
     float2 *theta_co = nullptr;    // L angle intervals of rho_co
     float *c_inv_sigma = nullptr;  // G
@@ -208,7 +209,7 @@ opta_status egs_cost(opta_handle *H, SizeState *S, const uint8_t *P, const doubl
                      cudaStream_t s) {
     const float cut = (float)std::sqrt(1.0 - H->prm.rho_th * H->prm.rho_th);
     CK(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), s));
-    CK(launch_rho_co(P, H->I8, H->p, H->q, S->m, S->n, h, H->IIS, H->IIQ, PS, PQ, cut, nullptr,
+    CK(launch_rho_co(P, H->I8, H->p, H->q, S->m, S->n, h, S->wsum, S->inv_sigma, PS, PQ, cut, nullptr,
                      dcount, s));
     unsigned long long c = 0;
     CK(cudaMemcpyAsync(&c, dcount, sizeof(c), cudaMemcpyDeviceToHost, s));
@@ -282,6 +283,7 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
         if (W.count) cudaFree(W.count);
         if (st != OPTA_OK) {
             H->mem.release(S->inv_sigma, L);
+            H->mem.release(S->wsum, L);
             H->mem.release(S->rho_co, L);
             H->mem.release(S->theta_co, L);
             H->mem.release(S->c_inv_sigma, (size_t)S->Gy * S->Gx);
@@ -295,7 +297,8 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
 #define PCK(x) do { cudaError_t e__ = (x); if (e__ != cudaSuccess) return cleanup(map_err(e__)); } while (0)
 
     PTRY(H->mem.alloc(&S->inv_sigma, L));
-    PCK(launch_window_stats(H->IIS, H->IIQ, p, q, m, n, S->inv_sigma, nullptr, s));
+    PTRY(H->mem.alloc(&S->wsum, L));
+    PCK(launch_window_stats(H->IIS, H->IIQ, p, q, m, n, S->inv_sigma, nullptr, s, S->wsum));
     PCK(cudaMalloc(&W.count, sizeof(unsigned long long)));
 
     // Level 0: unblurred pivots (P = I).
@@ -386,7 +389,7 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     PTRY(H->mem.alloc(&S->theta_co, L));
     PTRY(H->mem.alloc(&S->c_inv_sigma, G));
     PTRY(H->mem.alloc(&S->c_efac, G));
-    PCK(launch_rho_co(S->P, H->I8, p, q, m, n, S->h, H->IIS, H->IIQ, PS, PQ, 0.f, S->rho_co,
+    PCK(launch_rho_co(S->P, H->I8, p, q, m, n, S->h, S->wsum, S->inv_sigma, PS, PQ, 0.f, S->rho_co,
                       nullptr, s));
     PCK(launch_theta_co(S->rho_co, L, S->theta_co, s));
     PCK(launch_centre_stats(PS, PQ, p, q, m, n, S->h, S->Ly, S->Lx, S->c_inv_sigma, S->c_efac, s));
@@ -680,7 +683,7 @@ opta_status optA_destroy(opta_handle *h) {
     cudaSetDevice(h->device);
     for (auto &kv : h->sizes) {
         SizeState *S = kv.second;
-        cudaFree(S->inv_sigma); cudaFree(S->rho_co); cudaFree(S->theta_co);
+        cudaFree(S->inv_sigma); cudaFree(S->wsum); cudaFree(S->rho_co); cudaFree(S->theta_co);
         cudaFree(S->c_inv_sigma); cudaFree(S->c_efac);
         if (S->P_owned) cudaFree(S->P);
         delete S;
@@ -1031,18 +1034,25 @@ opta_status opta_dbg_rho_co(const uint8_t *P_dev, const uint8_t *I_dev, int32_t 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t nII = (size_t)(p + 1) * (q + 1);
     double *b[4] = {nullptr, nullptr, nullptr, nullptr};
+    float *inv = nullptr, *ws = nullptr;
     unsigned long long *cnt = nullptr;
+    const size_t L = (size_t)(p - m + 1) * (q - n + 1);
     for (auto &x : b) CK(cudaMallocAsync(&x, nII * sizeof(double), s));
+    CK(cudaMallocAsync(&inv, L * sizeof(float), s));
+    CK(cudaMallocAsync(&ws, L * sizeof(float), s));
     CK(cudaMallocAsync(&cnt, sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
     cudaError_t e = launch_integrals(I_dev, nullptr, p, q, b[0], b[1], nullptr, s);
+    if (e == cudaSuccess) e = launch_window_stats(b[0], b[1], p, q, m, n, inv, nullptr, s, ws);
     if (e == cudaSuccess) e = launch_integrals(P_dev, nullptr, p, q, b[2], b[3], nullptr, s);
     if (e == cudaSuccess)
-        e = launch_rho_co(P_dev, I_dev, p, q, m, n, h, b[0], b[1], b[2], b[3], (float)rho_cut,
+        e = launch_rho_co(P_dev, I_dev, p, q, m, n, h, ws, inv, b[2], b[3], (float)rho_cut,
                           rco_dev, cnt, s);
     unsigned long long hc = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s);
     for (auto &x : b) cudaFreeAsync(x, s);
+    cudaFreeAsync(inv, s);
+    cudaFreeAsync(ws, s);
     cudaFreeAsync(cnt, s);
     cudaError_t e2 = cudaStreamSynchronize(s);
     CK(e);

@@ -35,9 +35,10 @@ __device__ inline float key_float(uint32_t k) {
 }
 
 // Safety margins of the elimination test (Section 2, Eq. tranEqq in angle form):
-// |rho_co(fp32) - rho_co| <= kEcoBound (exact integer sums, FP32 quotient);
+// |rho_co(fp32) - rho_co| <= kEcoBound (exact integer numerator, FP32 finish with
+// 1/Omega factors of a few ulp each);
 // kAngMargin covers acosf and the subtraction of two angles; kCosMargin cosf.
-constexpr float kEcoBound = 1e-6f;
+constexpr float kEcoBound = 2e-6f;
 constexpr float kAngMargin = 2e-6f;
 constexpr float kCosMargin = 2e-6f;
 
@@ -87,10 +88,11 @@ struct TmplIn {
 cudaError_t launch_integrals(const uint8_t *A, const uint8_t *B, int p, int q,
                              double *o0, double *o1, double *o2, cudaStream_t s);
 
-// inv_sigma[y*Lx+x] = 1/Omega and efac[y*Lx+x] = ||I-128|| / Omega (0 when flat).
+// inv_sigma[y*Lx+x] = 1/Omega and efac[y*Lx+x] = ||I-128|| / Omega (0 when flat);
+// wsum (nullable) = the window sum S (exact in FP32 for windows below 2^24 / 255 pixels).
 cudaError_t launch_window_stats(const double *IIS, const double *IIQ, int p, int q,
                                 int m, int n, float *inv_sigma, float *efac128,
-                                cudaStream_t s);
+                                cudaStream_t s, float *wsum = nullptr);
 
 // Convert a float32 image holding integers in [0,255] into uint8; bad = 1 otherwise.
 cudaError_t launch_ingest_f32(const float *src, int64_t ld, int p, int q, uint8_t *dst,
@@ -182,9 +184,10 @@ cudaError_t launch_blur(const uint8_t *I, int p, int q, const uint8_t *level_map
 cudaError_t launch_blur_corr(const double *IIS, const double *IIQ, const double *PS,
                              const double *PQ, const double *PX, int p, int q, int m, int n,
                              float lambda, int block, int *fail, float *R, cudaStream_t s);
-// Pivot auto-correlation map / retained count for odd group side h.
+// Pivot auto-correlation map / retained count for odd group side h; the
+// member windows' statistics come from the window-sum and 1/Omega maps of I.
 cudaError_t launch_rho_co(const uint8_t *P, const uint8_t *I, int p, int q, int m, int n,
-                          int h, const double *IIS, const double *IIQ, const double *PS,
+                          int h, const float *wsum, const float *inv_sigma, const double *PS,
                           const double *PQ, float cut, float *rco,
                           unsigned long long *count, cudaStream_t s);
 // Angle intervals of the pivot auto-correlation map (kEcoBound wide).

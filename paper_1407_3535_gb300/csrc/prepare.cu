@@ -143,10 +143,10 @@ struct RcoCfg {
 };
 
 template <int H>
-__global__ void __launch_bounds__(RcoCfg<H>::MAXT)
+__global__ void __launch_bounds__(RcoCfg<H>::MAXT, 1)
 rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int p, int q,
-              int m, int n, int Ly, int Lx, const double *__restrict__ IIS,
-              const double *__restrict__ IIQ, const double *__restrict__ PS,
+              int m, int n, int Ly, int Lx, const float *__restrict__ wsum,
+              const float *__restrict__ inv_sigma, const double *__restrict__ PS,
               const double *__restrict__ PQ, int GXS, int GYB, int ring_w, float cut,
               float *rco, unsigned long long *count) {
     constexpr int R = RcoCfg<H>::R;
@@ -158,31 +158,37 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
     const int gx1 = min(Gx, gx0 + GXS), gy1 = min(Gy, gy0 + GYB);
     const int cx0 = group_centre_of(gx0, Lx, H);
     const int W = group_centre_of(gx1 - 1, Lx, H) + n - cx0;   // pivot columns
-    const int RING = m + 2 * R + 1;
+    // ring of image rows: the m + 2R + 1 rows one slide step needs, plus the
+    // H rows that the next batch of steps (one group row) loads ahead
+    const int RING = m + 2 * R + 1 + H;
     // per shift column sx: prefix sums of the column sums over the W pivot
     // columns (H x (W+1), unsigned: differences of wrapped prefixes are exact
     // because every window sum is < 2^32), warp totals, then the image ring
     unsigned *hs = reinterpret_cast<unsigned *>(rsm);
     unsigned *wtot = hs + H * (W + 1);
-    uint8_t *ring = reinterpret_cast<uint8_t *>(wtot + H * 32);   // RING x ring_w bytes
+    float *cst = reinterpret_cast<float *>(wtot + H * 32);        // per centre: S_hat, 1/Omega_hat
+    uint8_t *ring = reinterpret_cast<uint8_t *>(cst + 2 * GXS);   // RING x ring_w bytes
     const int j = threadIdx.x;
     const bool active = j < W;
     const int jc = cx0 + j;
     const int64_t q1 = q + 1;
     const long long mn = (long long)m * n;
+    const int RW = W + 2 * R;                                     // ring row width used
 
-    auto load_row = [&](int r) {
-        const int slot = (r + R) % RING;
-        const int rr = min(max(r, 0), p - 1);
-        const uint8_t *src = I + (int64_t)rr * q;
-        for (int c = threadIdx.x; c < W + 2 * R; c += blockDim.x) {
-            const int xx = min(max(cx0 - R + c, 0), q - 1);
-            ring[slot * ring_w + c] = src[xx];
+    // rows [r0, r0 + cnt) into their ring slots, all loads of all rows in flight
+    auto load_rows = [&](int r0, int cnt) {
+        for (int c = threadIdx.x; c < cnt * RW; c += blockDim.x) {
+            const int k = c / RW, col = c - k * RW;
+            const int rr = r0 + k;
+            const int slot = (rr + R) % RING;
+            const int ry = min(max(rr, 0), p - 1);
+            const int xx = min(max(cx0 - R + col, 0), q - 1);
+            ring[slot * ring_w + col] = I[(int64_t)ry * q + xx];
         }
     };
 
     int r = group_centre_of(gy0, Ly, H);
-    for (int rr = r - R; rr <= r + m + R; ++rr) load_row(rr);
+    load_rows(r - R, m + 2 * R + 1);
     __syncthreads();
 
     int cs[NS];
@@ -193,37 +199,56 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
             const int pv = P[(int64_t)(r + i) * q + jc];
 #pragma unroll
             for (int sy = 0; sy < H; ++sy) {
-                const uint8_t *row = ring + ((r + i + sy - R + R) % RING) * ring_w + j;
+                const uint8_t *row = ring + ((r + i + sy) % RING) * ring_w + j;   // row r+i+sy-R
 #pragma unroll
                 for (int sx = 0; sx < H; ++sx) cs[sy * H + sx] += pv * (int)row[sx];
             }
         }
     }
     unsigned long long local = 0;
-    // ring slots of rows r - R (oldest used) and r + m - R, kept incrementally
-    int so = r % RING, sn = (r + m) % RING;
     for (int gy = gy0; gy < gy1; ++gy) {
         const int cy = group_centre_of(gy, Ly, H);
-        while (r < cy) {
-            if (active) {
-                const int pold = P[(int64_t)r * q + jc];
-                const int pnew = P[(int64_t)(r + m) * q + jc];
+        const int steps = cy - r;            // 0 for the first row, <= H after
+        if (steps > 0) {
+            // the batch needs rows up to r + steps - 1 + m + R; load the new ones
+            load_rows(r + m + R + 1, steps);
+            int pold[H], pnew[H];
 #pragma unroll
-                for (int sy = 0; sy < H; ++sy) {
-                    const int a = so + sy, b = sn + sy;
-                    const uint8_t *ro = ring + (a >= RING ? a - RING : a) * ring_w + j;   // row r + sy - R
-                    const uint8_t *rn = ring + (b >= RING ? b - RING : b) * ring_w + j;   // row r + m + sy - R
-#pragma unroll
-                    for (int sx = 0; sx < H; ++sx)
-                        cs[sy * H + sx] += pnew * (int)rn[sx] - pold * (int)ro[sx];
-                }
+            for (int k = 0; k < H; ++k) {
+                const bool ok = active && k < steps;
+                pold[k] = ok ? P[(int64_t)(r + k) * q + jc] : 0;
+                pnew[k] = ok ? P[(int64_t)(r + k + m) * q + jc] : 0;
             }
             __syncthreads();
-            ++r;
-            so = (so + 1 == RING) ? 0 : so + 1;
-            sn = (sn + 1 == RING) ? 0 : sn + 1;
-            load_row(r + m + R);
-            __syncthreads();
+            if (active) {
+                int so = r % RING, sn = (r + m) % RING;     // slots of rows r - R and r + m - R
+#pragma unroll
+                for (int k = 0; k < H; ++k) {
+                    if (k < steps) {
+#pragma unroll
+                        for (int sy = 0; sy < H; ++sy) {
+                            const int a = so + sy, b = sn + sy;
+                            const uint8_t *ro = ring + (a >= RING ? a - RING : a) * ring_w + j;
+                            const uint8_t *rn = ring + (b >= RING ? b - RING : b) * ring_w + j;
+#pragma unroll
+                            for (int sx = 0; sx < H; ++sx)
+                                cs[sy * H + sx] += pnew[k] * (int)rn[sx] - pold[k] * (int)ro[sx];
+                        }
+                        so = (so + 1 == RING) ? 0 : so + 1;
+                        sn = (sn + 1 == RING) ? 0 : sn + 1;
+                    }
+                }
+            }
+            r += steps;
+            __syncthreads();   // nobody reads the dead rows the next batch overwrites
+        }
+        // pivot statistics of this row's centres (exact sums, FP32 1/Omega_hat)
+        for (int i = threadIdx.x; i < gx1 - gx0; i += blockDim.x) {
+            const int cx = group_centre_of(gx0 + i, Lx, H);
+            const double Sp = box(PS, q1, cy, cx, m, n), Qp = box(PQ, q1, cy, cx, m, n);
+            const double var = (double)mn * Qp - Sp * Sp;
+            cst[2 * i] = (float)Sp;
+            cst[2 * i + 1] = var > 0.0 ? sqrtf((float)mn / (float)var) : 0.f;
         }
         // emit centre row cy, one shift row (sy) at a time: block-wide prefix
         // sums of the column sums turn each n-column window sum into one
@@ -281,15 +306,11 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
                 if (mx < gxs || mx >= gxe) continue;
                 const unsigned *pre = hs + sxi * (W + 1) + (cx - cx0);
                 const long long X = (long long)(unsigned)(pre[n] - pre[0]);
-                const double S = box(IIS, q1, my, mx, m, n), Q = box(IIQ, q1, my, mx, m, n);
-                const double Sp = box(PS, q1, cy, cx, m, n), Qp = box(PQ, q1, cy, cx, m, n);
-                const long long Si = (long long)S, Qi = (long long)Q;
-                const long long Spi = (long long)Sp, Qpi = (long long)Qp;
-                const long long num = mn * X - Spi * Si;
-                const long long dA = mn * Qpi - Spi * Spi;
-                const long long dB = mn * Qi - Si * Si;
-                float rho = 0.f;
-                if (dA > 0 && dB > 0) rho = (float)num / sqrtf((float)dA * (float)dB);
+                const int64_t li = (int64_t)my * Lx + mx;
+                // rho = (mn X - S_hat S) / (mn Omega_hat Omega): exact integer
+                // numerator, FP32 finish (flat windows have 1/Omega = 0 -> 0)
+                const long long num = mn * X - (long long)cst[2 * gxi] * (long long)wsum[li];
+                const float rho = ((float)num * inv_sigma[li]) * (cst[2 * gxi + 1] / (float)mn);
                 if (rco) rco[(int64_t)my * Lx + mx] = rho;
                 if (rho < cut) ++local;
             }
@@ -303,7 +324,7 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
 
 template <int H>
 cudaError_t launch_rho_co_h(const uint8_t *P, const uint8_t *I, int p, int q, int m, int n,
-                            const double *IIS, const double *IIQ, const double *PS,
+                            const float *wsum, const float *inv_sigma, const double *PS,
                             const double *PQ, float cut, float *rco,
                             unsigned long long *count, cudaStream_t s) {
     constexpr int R = RcoCfg<H>::R;
@@ -323,7 +344,8 @@ cudaError_t launch_rho_co_h(const uint8_t *P, const uint8_t *I, int p, int q, in
     int GYB = (Gy + bands - 1) / bands;
     bands = (Gy + GYB - 1) / GYB;
     const int ring_w = ((Wmax + 2 * R) + 15) & ~15;
-    const size_t smem = (size_t)H * (Wmax + 1 + 32) * sizeof(unsigned) + (size_t)(m + 2 * R + 1) * ring_w;
+    const size_t smem = (size_t)H * (Wmax + 1 + 32) * sizeof(unsigned) + 2 * (size_t)GXS * sizeof(float) +
+                        (size_t)(m + 2 * R + 1 + H) * ring_w;
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     static size_t attr = 0;
     if (smem > attr) {
@@ -334,7 +356,7 @@ cudaError_t launch_rho_co_h(const uint8_t *P, const uint8_t *I, int p, int q, in
     }
     dim3 grid(strips, bands);
     LaunchScope ls_rho_co_kernel("rho_co_kernel", s);
-    rho_co_kernel<H><<<grid, threads, smem, s>>>(P, I, p, q, m, n, Ly, Lx, IIS, IIQ, PS, PQ,
+    rho_co_kernel<H><<<grid, threads, smem, s>>>(P, I, p, q, m, n, Ly, Lx, wsum, inv_sigma, PS, PQ,
                                                  GXS, GYB, ring_w, cut, rco, count);
     return cudaGetLastError();
 }
@@ -377,15 +399,15 @@ cudaError_t launch_blur_corr(const double *IIS, const double *IIQ, const double 
 }
 
 cudaError_t launch_rho_co(const uint8_t *P, const uint8_t *I, int p, int q, int m, int n,
-                          int h, const double *IIS, const double *IIQ, const double *PS,
+                          int h, const float *wsum, const float *inv_sigma, const double *PS,
                           const double *PQ, float cut, float *rco,
                           unsigned long long *count, cudaStream_t s) {
     switch (h) {
-        case 1: return launch_rho_co_h<1>(P, I, p, q, m, n, IIS, IIQ, PS, PQ, cut, rco, count, s);
-        case 3: return launch_rho_co_h<3>(P, I, p, q, m, n, IIS, IIQ, PS, PQ, cut, rco, count, s);
-        case 5: return launch_rho_co_h<5>(P, I, p, q, m, n, IIS, IIQ, PS, PQ, cut, rco, count, s);
-        case 7: return launch_rho_co_h<7>(P, I, p, q, m, n, IIS, IIQ, PS, PQ, cut, rco, count, s);
-        case 9: return launch_rho_co_h<9>(P, I, p, q, m, n, IIS, IIQ, PS, PQ, cut, rco, count, s);
+        case 1: return launch_rho_co_h<1>(P, I, p, q, m, n, wsum, inv_sigma, PS, PQ, cut, rco, count, s);
+        case 3: return launch_rho_co_h<3>(P, I, p, q, m, n, wsum, inv_sigma, PS, PQ, cut, rco, count, s);
+        case 5: return launch_rho_co_h<5>(P, I, p, q, m, n, wsum, inv_sigma, PS, PQ, cut, rco, count, s);
+        case 7: return launch_rho_co_h<7>(P, I, p, q, m, n, wsum, inv_sigma, PS, PQ, cut, rco, count, s);
+        case 9: return launch_rho_co_h<9>(P, I, p, q, m, n, wsum, inv_sigma, PS, PQ, cut, rco, count, s);
         default: return cudaErrorInvalidValue;
     }
 }

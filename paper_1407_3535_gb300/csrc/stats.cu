@@ -122,7 +122,7 @@ __device__ inline double box(const double *II, int64_t q1, int y, int x, int m, 
 
 __global__ void window_stats_kernel(const double *__restrict__ IIS, const double *__restrict__ IIQ,
                                     int q, int Ly, int Lx, int m, int n,
-                                    float *inv_sigma, float *efac128) {
+                                    float *inv_sigma, float *efac128, float *wsum) {
     const int64_t L = (int64_t)Ly * Lx;
     const int64_t q1 = q + 1;
     const double mn = (double)m * n;
@@ -142,6 +142,7 @@ __global__ void window_stats_kernel(const double *__restrict__ IIS, const double
         }
         inv_sigma[i] = inv;
         if (efac128) efac128[i] = ef;
+        if (wsum) wsum[i] = (float)S;   // exact: window sums of 8-bit pixels < 2^24
     }
 }
 
@@ -212,11 +213,11 @@ cudaError_t launch_integrals(const uint8_t *A, const uint8_t *B, int p, int q,
 
 cudaError_t launch_window_stats(const double *IIS, const double *IIQ, int p, int q,
                                 int m, int n, float *inv_sigma, float *efac128,
-                                cudaStream_t s) {
+                                cudaStream_t s, float *wsum) {
     const int Ly = p - m + 1, Lx = q - n + 1;
     LaunchScope ls_window_stats_kernel("window_stats_kernel", s);
     window_stats_kernel<<<grid_for((int64_t)Ly * Lx, 256), 256, 0, s>>>(
-        IIS, IIQ, q, Ly, Lx, m, n, inv_sigma, efac128);
+        IIS, IIQ, q, Ly, Lx, m, n, inv_sigma, efac128, wsum);
     return cudaGetLastError();
 }
 
