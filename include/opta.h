@@ -51,7 +51,8 @@ typedef enum opta_status {
     OPTA_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
     OPTA_ERR_BUSY = 6,          /* handle in use */
     OPTA_ERR_UNSUPPORTED = 7,   /* input outside the supported domain (see optA_prepare) */
-    OPTA_ERR_TOO_LARGE = 8      /* problem larger than zncc_full_noalloc's fixed scratch */
+    OPTA_ERR_TOO_LARGE = 8      /* template size outside optA's limits, or a problem larger
+                                   than zncc_full_noalloc's fixed scratch */
 } opta_status;
 
 typedef enum opta_dtype {
@@ -140,7 +141,11 @@ const char *opta_status_str(opta_status s);
  * float32 holding such integers); other float images give
  * OPTA_ERR_UNSUPPORTED (use zncc_full for them).  `sizes_mn` lists n_sizes
  * (m, n) pairs to prepare now (may be NULL / 0); other sizes are prepared
- * on first use by optA_search.  The handle owns all device memory it
+ * on first use by optA_search.  Template sizes: n <= 1023 and m * n <=
+ * 66051 pixels (e.g. 256 x 256; the group auto-correlation sums are 32-bit),
+ * and the rows of one window must fit the kernel's shared-memory ring;
+ * larger sizes give OPTA_ERR_TOO_LARGE (zncc_full has no pixel-count limit).
+ * The handle owns all device memory it
  * allocates (integral images, blur maps, pivot images, auto-correlation
  * maps, group statistics, search scratch).  `prm` may be NULL (defaults).
  * Synchronises `stream`.

@@ -64,7 +64,7 @@ struct SizeState {
     uint8_t *P = nullptr;          // pivot image (owned unless it aliases the image)
     bool P_owned = false;
     float *inv_sigma = nullptr;    // L
-    float *wsum = nullptr;         // L window sums of I (exact in FP32)
+    int *wsum = nullptr;           // L window sums of I
     float *rho_co = nullptr;       // L
     float2 *theta_co = nullptr;    // L angle intervals of rho_co
     float *c_inv_sigma = nullptr;  // G
@@ -79,7 +79,7 @@ struct opta_handle {
     opta_params prm;
     DevMem mem;
     uint8_t *I8 = nullptr;
-    double *IIS = nullptr, *IIQ = nullptr;
+    long long *IIS = nullptr, *IIQ = nullptr;
     std::map<std::pair<int, int>, SizeState *> sizes;
     // search scratch (grown on demand)
     size_t capL = 0, capG = 0, capT = 0, capN = 0;
@@ -197,15 +197,15 @@ bool valid_template(const opta_template *t, int p, int q) {
 // ---------------------------------------------------------------------------
 struct PrepScratch {
     uint8_t *Pcur = nullptr, *Pacc = nullptr;
-    double *PS = nullptr, *PQ = nullptr, *PX = nullptr;
+    long long *PS = nullptr, *PQ = nullptr, *PX = nullptr;
     int *fail = nullptr;
     uint8_t *lvl = nullptr;
     unsigned long long *count = nullptr;
     size_t nII = 0;
 };
 
-opta_status egs_cost(opta_handle *H, SizeState *S, const uint8_t *P, const double *PS,
-                     const double *PQ, int h, unsigned long long *dcount, long long *cost,
+opta_status egs_cost(opta_handle *H, SizeState *S, const uint8_t *P, const long long *PS,
+                     const long long *PQ, int h, unsigned long long *dcount, long long *cost,
                      cudaStream_t s) {
     const float cut = (float)std::sqrt(1.0 - H->prm.rho_th * H->prm.rho_th);
     CK(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), s));
@@ -219,22 +219,19 @@ opta_status egs_cost(opta_handle *H, SizeState *S, const uint8_t *P, const doubl
     return OPTA_OK;
 }
 
-// Largest group side the auto-correlation kernel supports for width n.
-int h_limit(int n, int hmax) {
+// Largest odd group side <= hmax the auto-correlation kernel supports for
+// m x n windows of a p x q image (0: none).
+int h_limit(int p, int q, int m, int n, int hmax) {
     int h = hmax;
-    while (h > 1) {
-        const int maxt = h >= 9 ? 512 : (h >= 7 ? 640 : 1024);
-        if (n + h <= maxt) break;
-        h -= 2;
-    }
+    while (h >= 1 && !rho_co_supported(p, q, m, n, h)) h -= 2;
     return h;
 }
 
 // Algorithm 2: grow h by 2 while the cost drops by more than xi of the last.
-opta_status egs(opta_handle *H, SizeState *S, const uint8_t *P, const double *PS,
-                const double *PQ, int h_start, unsigned long long *dcount, int *h_out,
+opta_status egs(opta_handle *H, SizeState *S, const uint8_t *P, const long long *PS,
+                const long long *PQ, int h_start, unsigned long long *dcount, int *h_out,
                 long long *c_out, cudaStream_t s) {
-    const int hmax = h_limit(S->n, H->prm.h_max);
+    const int hmax = h_limit(H->p, H->q, S->m, S->n, H->prm.h_max);
     int h = std::min(h_start, hmax);
     long long c = 0;
     TRY(egs_cost(H, S, P, PS, PQ, h, dcount, &c, s));
@@ -262,6 +259,7 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     auto key = std::make_pair(m, n);
     if (H->sizes.count(key)) return OPTA_OK;
     const int p = H->p, q = H->q;
+    if (h_limit(p, q, m, n, 1) < 1) return OPTA_ERR_TOO_LARGE;
     SizeState *S = new (std::nothrow) SizeState();
     if (!S) return OPTA_ERR_OOM;
     S->m = m; S->n = n; S->Ly = p - m + 1; S->Lx = q - n + 1;
@@ -306,7 +304,7 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     long long c_best = 0;
     bool best_is_image = true;
     if (prm.fixed_h > 0) {
-        h_best = std::min(prm.fixed_h, h_limit(n, 9));
+        h_best = std::min(prm.fixed_h, h_limit(p, q, m, n, 9));
     } else {
         PTRY(egs(H, S, H->I8, H->IIS, H->IIQ, 1, W.count, &h_best, &c_best, s));
     }
@@ -315,9 +313,9 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
         const size_t nII = (size_t)(p + 1) * (q + 1);
         PCK(cudaMalloc(&W.Pcur, (size_t)p * q));
         PCK(cudaMalloc(&W.Pacc, (size_t)p * q));
-        PCK(cudaMalloc(&W.PS, nII * sizeof(double)));
-        PCK(cudaMalloc(&W.PQ, nII * sizeof(double)));
-        PCK(cudaMalloc(&W.PX, nII * sizeof(double)));
+        PCK(cudaMalloc(&W.PS, nII * sizeof(long long)));
+        PCK(cudaMalloc(&W.PQ, nII * sizeof(long long)));
+        PCK(cudaMalloc(&W.PX, nII * sizeof(long long)));
         PCK(cudaMalloc(&W.fail, (size_t)bp * bq * sizeof(int)));
         PCK(cudaMalloc(&W.lvl, (size_t)bp * bq));
         const float lam = (float)lambda_of(prm.rho_th, prm.rho_max);
@@ -333,7 +331,7 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
             PTRY(blur_to(H, W, cand, W.Pcur, s));
             PCK(launch_integrals(W.Pcur, H->I8, p, q, W.PS, W.PQ, W.PX, s));
             PCK(cudaMemsetAsync(W.fail, 0, (size_t)bp * bq * sizeof(int), s));
-            PCK(launch_blur_corr(H->IIS, H->IIQ, W.PS, W.PQ, W.PX, p, q, m, n, lam, block,
+            PCK(launch_blur_corr(S->wsum, S->inv_sigma, W.PS, W.PQ, W.PX, p, q, m, n, lam, block,
                                  W.fail, nullptr, s));
             PCK(cudaMemcpyAsync(fail.data(), W.fail, fail.size() * sizeof(int),
                                 cudaMemcpyDeviceToHost, s));
@@ -371,7 +369,7 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     S->Gy = groups_along(S->Ly, S->h);
     S->Gx = groups_along(S->Lx, S->h);
     const int64_t G = (int64_t)S->Gy * S->Gx;
-    const double *PS = H->IIS, *PQ = H->IIQ;
+    const long long *PS = H->IIS, *PQ = H->IIQ;
     if (best_is_image) {
         S->P = H->I8;
         S->P_owned = false;
@@ -879,7 +877,8 @@ opta_status zncc_full(const opta_image *img, const opta_template *t, float *rho_
     const int64_t L = (int64_t)Ly * Lx;
     const size_t nII = (size_t)(p + 1) * (q + 1);
     uint8_t *I8 = nullptr;
-    double *IIS = nullptr, *IIQ = nullptr, *td = nullptr;
+    long long *IIS = nullptr, *IIQ = nullptr;
+    double *td = nullptr;
     float *inv = nullptr, *ef = nullptr, *map = rho_map, *tf = nullptr, *tst = nullptr;
     int *cand = nullptr;
     double *cand_rho = nullptr;
@@ -901,8 +900,8 @@ opta_status zncc_full(const opta_image *img, const opta_template *t, float *rho_
         opta_status stt = ingest(img, I8, s);
         if (stt != OPTA_OK) return finish(stt);
     }
-    ZCK(A(&IIS, nII * sizeof(double)));
-    ZCK(A(&IIQ, nII * sizeof(double)));
+    ZCK(A(&IIS, nII * sizeof(long long)));
+    ZCK(A(&IIQ, nII * sizeof(long long)));
     ZCK(A(&inv, L * sizeof(float)));
     ZCK(A(&ef, L * sizeof(float)));
     if (!map) ZCK(A(&map, L * sizeof(float)));
@@ -947,9 +946,9 @@ opta_status opta_dbg_window_stats(const uint8_t *I_dev, int32_t p, int32_t q, in
         return OPTA_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t nII = (size_t)(p + 1) * (q + 1);
-    double *S = nullptr, *Q = nullptr;
-    CK(cudaMallocAsync(&S, nII * sizeof(double), s));
-    CK(cudaMallocAsync(&Q, nII * sizeof(double), s));
+    long long *S = nullptr, *Q = nullptr;
+    CK(cudaMallocAsync(&S, nII * sizeof(long long), s));
+    CK(cudaMallocAsync(&Q, nII * sizeof(long long), s));
     cudaError_t e = launch_integrals(I_dev, nullptr, p, q, S, Q, nullptr, s);
     if (e == cudaSuccess) e = launch_window_stats(S, Q, p, q, m, n, inv_sigma_dev, nullptr, s);
     cudaFreeAsync(S, s);
@@ -1012,13 +1011,21 @@ opta_status opta_dbg_blur_corr(const uint8_t *P_dev, const uint8_t *I_dev, int32
         return OPTA_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t nII = (size_t)(p + 1) * (q + 1);
-    double *b[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    for (auto &x : b) CK(cudaMallocAsync(&x, nII * sizeof(double), s));
+    const size_t L = (size_t)(p - m + 1) * (q - n + 1);
+    long long *b[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    float *inv = nullptr;
+    int *ws = nullptr;
+    for (auto &x : b) CK(cudaMallocAsync(&x, nII * sizeof(long long), s));
+    CK(cudaMallocAsync(&inv, L * sizeof(float), s));
+    CK(cudaMallocAsync(&ws, L * sizeof(int), s));
     cudaError_t e = launch_integrals(I_dev, nullptr, p, q, b[0], b[1], nullptr, s);
+    if (e == cudaSuccess) e = launch_window_stats(b[0], b[1], p, q, m, n, inv, nullptr, s, ws);
     if (e == cudaSuccess) e = launch_integrals(P_dev, I_dev, p, q, b[2], b[3], b[4], s);
     if (e == cudaSuccess)
-        e = launch_blur_corr(b[0], b[1], b[2], b[3], b[4], p, q, m, n, 0.f, 64, nullptr, R_dev, s);
+        e = launch_blur_corr(ws, inv, b[2], b[3], b[4], p, q, m, n, 0.f, 64, nullptr, R_dev, s);
     for (auto &x : b) cudaFreeAsync(x, s);
+    cudaFreeAsync(inv, s);
+    cudaFreeAsync(ws, s);
     cudaError_t e2 = cudaStreamSynchronize(s);
     CK(e);
     CK(e2);
@@ -1030,16 +1037,17 @@ opta_status opta_dbg_rho_co(const uint8_t *P_dev, const uint8_t *I_dev, int32_t 
                             int64_t *n_retained_host, void *stream) {
     if (!P_dev || !I_dev || p < 1 || q < 1 || m < 1 || n < 1 || m > p || n > q)
         return OPTA_ERR_INVALID_ARG;
-    if (h < 1 || h > 9 || h % 2 == 0 || h_limit(n, 9) < h) return OPTA_ERR_INVALID_ARG;
+    if (h < 1 || h > 9 || h % 2 == 0 || h_limit(p, q, m, n, h) != h) return OPTA_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t nII = (size_t)(p + 1) * (q + 1);
-    double *b[4] = {nullptr, nullptr, nullptr, nullptr};
-    float *inv = nullptr, *ws = nullptr;
+    long long *b[4] = {nullptr, nullptr, nullptr, nullptr};
+    float *inv = nullptr;
+    int *ws = nullptr;
     unsigned long long *cnt = nullptr;
     const size_t L = (size_t)(p - m + 1) * (q - n + 1);
-    for (auto &x : b) CK(cudaMallocAsync(&x, nII * sizeof(double), s));
+    for (auto &x : b) CK(cudaMallocAsync(&x, nII * sizeof(long long), s));
     CK(cudaMallocAsync(&inv, L * sizeof(float), s));
-    CK(cudaMallocAsync(&ws, L * sizeof(float), s));
+    CK(cudaMallocAsync(&ws, L * sizeof(int), s));
     CK(cudaMallocAsync(&cnt, sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
     cudaError_t e = launch_integrals(I_dev, nullptr, p, q, b[0], b[1], nullptr, s);

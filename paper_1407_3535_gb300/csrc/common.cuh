@@ -24,6 +24,23 @@ __host__ __device__ inline int group_centre_of(int g, int len, int h) {
 }
 __host__ __device__ inline int groups_along(int len, int h) { return (len + h - 1) / h; }
 
+// Sum over the m x n window at (y, x) from an inclusive-prefix integral image
+// with row pitch q1 = q + 1 (entry (0, *) and (*, 0) zero).  Integer adds:
+// exact, and off the GPU's narrow FP64 pipe.
+__device__ inline long long ii_box(const long long *__restrict__ II, int64_t q1, int y, int x,
+                                   int m, int n) {
+    return II[(int64_t)(y + m) * q1 + x + n] - II[(int64_t)y * q1 + x + n]
+         - II[(int64_t)(y + m) * q1 + x] + II[(int64_t)y * q1 + x];
+}
+
+// mn * Q - S * S (= mn^2 * variance) of a window of mn 8-bit pixels with sum S
+// and square sum Q, as FP32.  Exact in int64 up to 2^23 pixels (the product
+// stays below 2^62); larger windows take it from FP64 products.
+__device__ inline float win_var(long long mn, long long S, long long Q) {
+    if (mn <= (1ll << 23)) return (float)(mn * Q - S * S);
+    return (float)((double)mn * (double)Q - (double)S * (double)S);
+}
+
 // Order-preserving map of a float to uint32 (larger float -> larger key).
 __device__ inline uint32_t float_key(float f) {
     uint32_t b = __float_as_uint(f);
@@ -83,16 +100,16 @@ struct TmplIn {
 // ---------------------------------------------------------------------------
 // Launchers (stream-ordered, return cudaError_t of the launch).
 // ---------------------------------------------------------------------------
-// Integral images (FP64, (p+1) x (q+1), zero first row/col) of A, A*A and,
-// if B != null and o2 != null, A*B.
-cudaError_t launch_integrals(const uint8_t *A, const uint8_t *B, int p, int q,
-                             double *o0, double *o1, double *o2, cudaStream_t s);
+// Integral images (int64, exact; (p+1) x (q+1), zero first row/col) of A, A*A
+// and, if B != null and o2 != null, A*B.
+cudaError_t launch_integrals(const uint8_t *A, const uint8_t *B, int p, int q, long long *o0,
+                             long long *o1, long long *o2, cudaStream_t s);
 
 // inv_sigma[y*Lx+x] = 1/Omega and efac[y*Lx+x] = ||I-128|| / Omega (0 when flat);
-// wsum (nullable) = the window sum S (exact in FP32 for windows below 2^24 / 255 pixels).
-cudaError_t launch_window_stats(const double *IIS, const double *IIQ, int p, int q,
+// wsum (nullable) = the window sum S (int32: asked for windows of at most 2^23 pixels).
+cudaError_t launch_window_stats(const long long *IIS, const long long *IIQ, int p, int q,
                                 int m, int n, float *inv_sigma, float *efac128,
-                                cudaStream_t s, float *wsum = nullptr);
+                                cudaStream_t s, int *wsum = nullptr);
 
 // Convert a float32 image holding integers in [0,255] into uint8; bad = 1 otherwise.
 cudaError_t launch_ingest_f32(const float *src, int64_t ld, int p, int q, uint8_t *dst,
@@ -154,8 +171,8 @@ cudaError_t launch_topk(const float *rho_tc, int64_t gstride, int Gy, int Gx, in
                         cudaStream_t s);
 cudaError_t launch_threshold(TmplState *st, const double *cand_rho_topk, int T, cudaStream_t s);
 // FP32 rho at the members of the threshold centres' groups (raises lo_key).
-cudaError_t launch_group_members(const uint8_t *I, int q, int Ly, int Lx, int h, const double *IIS,
-                                 const double *IIQ, const float *tf, size_t tsz, int m, int n,
+cudaError_t launch_group_members(const uint8_t *I, int q, int Ly, int Lx, int h, const long long *IIS,
+                                 const long long *IIQ, const float *tf, size_t tsz, int m, int n,
                                  int npad, const float *inv_sigma, int T, TmplState *st,
                                  const int *cand_topk, int topk, cudaStream_t s);
 // Scan 2: bound of every location, bucket histogram of the survivors and
@@ -166,8 +183,8 @@ cudaError_t launch_bound_compact(const float2 *tc, const float2 *theta_co, int L
                                  TmplState *st, int *surv, float *surv_ub, int cap, int *chunk_cnt,
                                  float *ub_map, uint8_t *surv_map, int *bucket_cnt,
                                  int *bucket_cur, cudaStream_t s);
-cudaError_t launch_survivors(const uint8_t *I, int pimg, int q, int Lx, const double *IIS,
-                             const double *IIQ, const float *tf, int m, int n, int npad,
+cudaError_t launch_survivors(const uint8_t *I, int pimg, int q, int Lx, const long long *IIS,
+                             const long long *IIQ, const float *tf, int m, int n, int npad,
                              const float *inv_sigma, TmplState *st, const int *surv,
                              const float *surv_ub, float *surv_rho, float *surv_eps, int cap,
                              const int *bucket_end, cudaStream_t s);
@@ -180,20 +197,26 @@ cudaError_t launch_surv_candidates(TmplState *st, const int *surv, const float *
 cudaError_t launch_blur(const uint8_t *I, int p, int q, const uint8_t *level_map, int block,
                         const float *weights /* [levels][10] */, const int *radius,
                         uint8_t *P, cudaStream_t s);
-// Blur correlation per location; block fail flags where a non-flat window has R < lambda.
-cudaError_t launch_blur_corr(const double *IIS, const double *IIQ, const double *PS,
-                             const double *PQ, const double *PX, int p, int q, int m, int n,
+// Blur correlation per location (I's windows from the window-sum and 1/Omega
+// maps, the pivot's from int64 integrals); block fail flags where a non-flat
+// window has R < lambda.
+cudaError_t launch_blur_corr(const int *wsum, const float *inv_sigma, const long long *PS,
+                             const long long *PQ, const long long *PX, int p, int q, int m, int n,
                              float lambda, int block, int *fail, float *R, cudaStream_t s);
 // Pivot auto-correlation map / retained count for odd group side h; the
 // member windows' statistics come from the window-sum and 1/Omega maps of I.
+// Whether the auto-correlation kernel can run group side h for m x n windows
+// of a p x q image (its strip of window columns and ring of image rows must
+// fit the thread and shared-memory limits).
+bool rho_co_supported(int p, int q, int m, int n, int h);
 cudaError_t launch_rho_co(const uint8_t *P, const uint8_t *I, int p, int q, int m, int n,
-                          int h, const float *wsum, const float *inv_sigma, const double *PS,
-                          const double *PQ, float cut, float *rco,
+                          int h, const int *wsum, const float *inv_sigma, const long long *PS,
+                          const long long *PQ, float cut, float *rco,
                           unsigned long long *count, cudaStream_t s);
 // Angle intervals of the pivot auto-correlation map (kEcoBound wide).
 cudaError_t launch_theta_co(const float *rho_co, int64_t L, float2 *theta_co, cudaStream_t s);
 // Per-centre pivot statistics: inv_sigma_hat and ||P-128||/sigma_hat.
-cudaError_t launch_centre_stats(const double *PS, const double *PQ, int p, int q, int m,
+cudaError_t launch_centre_stats(const long long *PS, const long long *PQ, int p, int q, int m,
                                 int n, int h, int Ly, int Lx, float *c_inv_sigma,
                                 float *c_efac, cudaStream_t s);
 

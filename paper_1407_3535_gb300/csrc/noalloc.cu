@@ -119,8 +119,8 @@ extern "C" opta_status zncc_full_noalloc(const opta_image *img, const opta_templ
     const int64_t L = (int64_t)Ly * Lx;
     uint8_t *I8 = base + kLay.i8;
     float *stage = reinterpret_cast<float *>(base + kLay.stage);
-    double *IIS = reinterpret_cast<double *>(base + kLay.iis);
-    double *IIQ = reinterpret_cast<double *>(base + kLay.iiq);
+    long long *IIS = reinterpret_cast<long long *>(base + kLay.iis);
+    long long *IIQ = reinterpret_cast<long long *>(base + kLay.iiq);
     float *inv = reinterpret_cast<float *>(base + kLay.inv);
     float *ef = reinterpret_cast<float *>(base + kLay.ef);
     float *map = rho_map ? rho_map : reinterpret_cast<float *>(base + kLay.map);

@@ -5,8 +5,10 @@
 // statistics.
 //
 // All correlation sums here are exact integer sums (uint8 x uint8 products
-// in int32/int64; FP64 integral images holding integers); only the final
-// quotient is rounded, so |rho_co(fp32) - rho_co| <= ~5 u.
+// in int32/int64, int64 integral images); only the final quotient is
+// rounded, so |rho_co(fp32) - rho_co| <= ~5 u.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace opta {
@@ -63,34 +65,30 @@ __global__ void blur_kernel(const uint8_t *__restrict__ I, int p, int q,
     }
 }
 
-__device__ inline double box(const double *II, int64_t q1, int y, int x, int m, int n) {
-    return II[(int64_t)(y + m) * q1 + x + n] - II[(int64_t)y * q1 + x + n]
-         - II[(int64_t)(y + m) * q1 + x] + II[(int64_t)y * q1 + x];
-}
 
 // R_oo(x) = rho(P window, I window) (Algorithm 3) and the lambda test.
-__global__ void blur_corr_kernel(const double *__restrict__ IIS, const double *__restrict__ IIQ,
-                                 const double *__restrict__ PS, const double *__restrict__ PQ,
-                                 const double *__restrict__ PX, int q, int Ly, int Lx, int m,
+__global__ void blur_corr_kernel(const int *__restrict__ wsum, const float *__restrict__ inv_sigma,
+                                 const long long *__restrict__ PS, const long long *__restrict__ PQ,
+                                 const long long *__restrict__ PX, int q, int Ly, int Lx, int m,
                                  int n, float lambda, int block, int *fail, float *R) {
     const int64_t L = (int64_t)Ly * Lx;
     const int64_t q1 = q + 1;
-    const double mn = (double)m * n;
+    const long long mn = (long long)m * n;
     const int bq = (q + block - 1) / block;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int y = (int)(i / Lx), x = (int)(i % Lx);
-        const double S = box(IIS, q1, y, x, m, n), Q = box(IIQ, q1, y, x, m, n);
-        const double Sp = box(PS, q1, y, x, m, n), Qp = box(PQ, q1, y, x, m, n);
-        const double X = box(PX, q1, y, x, m, n);
-        // numerator and variances are exact in FP64 (integers < 2^53); the
-        // quotient only drives the lambda decision and is finished in FP32
-        const double dB = mn * Q - S * S, dA = mn * Qp - Sp * Sp;
-        const double num = mn * X - Sp * S;
+        const int ii = (int)i;
+        const int y = ii / Lx, x = ii - y * Lx;
+        const long long Sp = ii_box(PS, q1, y, x, m, n), Qp = ii_box(PQ, q1, y, x, m, n);
+        const long long X = ii_box(PX, q1, y, x, m, n);
+        const long long dA = mn * Qp - Sp * Sp;                        // exact
+        const long long num = mn * X - Sp * (long long)wsum[i];        // exact
+        const float iw = inv_sigma[i];                                 // 0: flat I window
         float r = 0.f;
-        if (dA > 0.0 && dB > 0.0) r = (float)num / sqrtf((float)dA * (float)dB);
+        if (dA > 0 && iw > 0.f)
+            r = ((float)num * iw) * (sqrtf((float)mn / (float)dA) / (float)mn);
         if (R) R[i] = r;
-        if (fail && dB > 0.0 && r < lambda) {
+        if (fail && iw > 0.f && r < lambda) {
             int *f = fail + (y / block) * bq + (x / block);
             if (*f == 0) atomicOr(f, 1);
         }
@@ -98,7 +96,7 @@ __global__ void blur_corr_kernel(const double *__restrict__ IIS, const double *_
 }
 
 // Per-centre pivot statistics.
-__global__ void centre_stats_kernel(const double *__restrict__ PS, const double *__restrict__ PQ,
+__global__ void centre_stats_kernel(const long long *__restrict__ PS, const long long *__restrict__ PQ,
                                     int q, int m, int n, int h, int Ly, int Lx,
                                     float *c_inv_sigma, float *c_efac) {
     const int Gy = groups_along(Ly, h), Gx = groups_along(Lx, h);
@@ -109,13 +107,14 @@ __global__ void centre_stats_kernel(const double *__restrict__ PS, const double 
          g += (int64_t)gridDim.x * blockDim.x) {
         const int cy = group_centre_of((int)(g / Gx), Ly, h);
         const int cx = group_centre_of((int)(g % Gx), Lx, h);
-        const double S = box(PS, q1, cy, cx, m, n), Q = box(PQ, q1, cy, cx, m, n);
-        const double var = mn * Q - S * S;   // exact
+        const long long S = ii_box(PS, q1, cy, cx, m, n), Q = ii_box(PQ, q1, cy, cx, m, n);
+        const long long imn = (long long)m * n;
+        const long long var = imn * Q - S * S;   // exact
         float is = 0.f, ef = 0.f;
-        if (var > 0.0) {
+        if (var > 0) {
             const float fv = (float)var, fmn = (float)mn;
             is = sqrtf(fmn / fv);
-            ef = sqrtf(fmn * (float)(Q - 256.0 * S + 16384.0 * mn) / fv);
+            ef = sqrtf(fmn * (float)(Q - 256 * S + 16384 * imn) / fv);
         }
         c_inv_sigma[g] = is;
         c_efac[g] = ef;
@@ -129,28 +128,98 @@ __global__ void centre_stats_kernel(const double *__restrict__ PS, const double 
 // (vertically).  Thread j owns pivot column cx0 + j and keeps, for every
 // shift s = (sy, sx) of the group, the column sum
 //     colsum_s(r) = sum_{i<m} P(r+i, j) * I(r+i+sy, j+sx)
-// which slides down one row at a time (add the new bottom product, subtract
-// the old top one).  At each centre row the column sums are summed over the
-// n pivot columns of each centre, giving the exact cross sum of the pivot
-// block and the member block x = c + s.  A ring buffer in shared memory holds
-// the m + 2R + 1 image rows the slide needs.
+// which slides down H rows per group row (add the new bottom products,
+// subtract the old top ones).  At each centre row the column sums are summed
+// over the n pivot columns of each centre, giving the exact cross sum of the
+// pivot block and the member block x = c + s.
+//
+// The slide works on 4-row words: the image rows sit column-major in a
+// shared-memory ring (each column's ring slots packed 4 per 32-bit word), the
+// pivot rows of one slide batch are packed 4 per word, and one dp4a (four
+// uint8 x uint8 products summed into a 32-bit accumulator) takes four rows
+// of one shift at once.  A funnel shift realigns the image words to the
+// batch's first row and to each sy.
 // ---------------------------------------------------------------------------
 template <int H>
 struct RcoCfg {
     static constexpr int R = (H - 1) / 2;
     static constexpr int NS = H * H;
     static constexpr int MAXT = H >= 9 ? 512 : (H >= 7 ? 640 : 1024);
+    static constexpr int KW = (H + 3) / 4;           // pivot words per batch
+    static constexpr int BATCH = 4 * KW;             // rows per batch (>= H)
+    static constexpr int NA = (H + BATCH + 2) / 4;   // aligned image words per column and batch
 };
+
+// Ring geometry shared by host and device: RING slots (a multiple of 4, at
+// least the m + 2R + 1 rows one slide step needs plus the H rows loaded
+// ahead), RW4 words per column, column stride CSW words (odd: conflict-free
+// column-parallel reads).
+__host__ __device__ inline int rco_ring(int m, int H) { return (m + (H - 1) + 1 + H + 3) & ~3; }
+__host__ __device__ inline int rco_csw(int ring) { return (ring >> 2) | 1; }
+
+// cs[sy][sx] += (or -=) sum_{k<cnt} P(prow+k, jc) * I(prow+k+sy-R, cx0+j+sx-R)
+// for cnt <= BATCH rows; image row rr lives in ring slot (rr + R) % RING.
+template <int H, bool SUB>
+__device__ __forceinline__ void rco_batch(int (&cs)[H * H], const uint8_t *__restrict__ P, int q,
+                                          int jc, int prow, int cnt, const unsigned *ringw, int j,
+                                          int CSW, int RW4, int RING) {
+    constexpr int KW = RcoCfg<H>::KW, NA = RcoCfg<H>::NA;
+    unsigned pw[KW];
+#pragma unroll
+    for (int w = 0; w < KW; ++w) {
+        pw[w] = 0u;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int k = 4 * w + b;
+            if (k < cnt) pw[w] |= (unsigned)P[(int64_t)(prow + k) * q + jc] << (8 * b);
+        }
+    }
+    const int slot0 = prow % RING;                  // slot of image row prow - R
+    const unsigned sh = (unsigned)(slot0 & 3) * 8u;
+    int woff[NA + 1];
+    {
+        int w = slot0 >> 2;
+#pragma unroll
+        for (int i = 0; i <= NA; ++i) {
+            woff[i] = w;
+            w = (w + 1 == RW4) ? 0 : w + 1;
+        }
+    }
+#pragma unroll
+    for (int sx = 0; sx < H; ++sx) {
+        const unsigned *col = ringw + (j + sx) * CSW;
+        unsigned wd[NA + 1];
+#pragma unroll
+        for (int i = 0; i <= NA; ++i) wd[i] = col[woff[i]];
+        unsigned al[NA];                             // byte t = image row prow - R + t
+#pragma unroll
+        for (int i = 0; i < NA; ++i) al[i] = __funnelshift_r(wd[i], wd[i + 1], sh);
+#pragma unroll
+        for (int sy = 0; sy < H; ++sy) {
+            unsigned acc = 0u;
+#pragma unroll
+            for (int w = 0; w < KW; ++w) {
+                const int t = sy + 4 * w;
+                const unsigned x = (t & 3) ? __funnelshift_r(al[t >> 2], al[(t >> 2) + 1], 8 * (t & 3))
+                                           : al[t >> 2];
+                acc = __dp4a(x, pw[w], acc);
+            }
+            if (SUB) cs[sy * H + sx] -= (int)acc;
+            else cs[sy * H + sx] += (int)acc;
+        }
+    }
+}
 
 template <int H>
 __global__ void __launch_bounds__(RcoCfg<H>::MAXT, 1)
 rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int p, int q,
-              int m, int n, int Ly, int Lx, const float *__restrict__ wsum,
-              const float *__restrict__ inv_sigma, const double *__restrict__ PS,
-              const double *__restrict__ PQ, int GXS, int GYB, int ring_w, float cut,
+              int m, int n, int Ly, int Lx, const int *__restrict__ wsum,
+              const float *__restrict__ inv_sigma, const long long *__restrict__ PS,
+              const long long *__restrict__ PQ, int GXS, int GYB, float cut,
               float *rco, unsigned long long *count) {
     constexpr int R = RcoCfg<H>::R;
     constexpr int NS = RcoCfg<H>::NS;
+    constexpr int BATCH = RcoCfg<H>::BATCH;
     extern __shared__ int rsm[];
     const int Gy = groups_along(Ly, H), Gx = groups_along(Lx, H);
     const int gx0 = blockIdx.x * GXS, gy0 = blockIdx.y * GYB;
@@ -158,22 +227,23 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
     const int gx1 = min(Gx, gx0 + GXS), gy1 = min(Gy, gy0 + GYB);
     const int cx0 = group_centre_of(gx0, Lx, H);
     const int W = group_centre_of(gx1 - 1, Lx, H) + n - cx0;   // pivot columns
-    // ring of image rows: the m + 2R + 1 rows one slide step needs, plus the
-    // H rows that the next batch of steps (one group row) loads ahead
-    const int RING = m + 2 * R + 1 + H;
+    const int RING = rco_ring(m, H), RW4 = RING >> 2, CSW = rco_csw(RING);
     // per shift column sx: prefix sums of the column sums over the W pivot
     // columns (H x (W+1), unsigned: differences of wrapped prefixes are exact
-    // because every window sum is < 2^32), warp totals, then the image ring
+    // because every window sum is < 2^32), warp totals, per-centre pivot
+    // statistics, then the image ring
     unsigned *hs = reinterpret_cast<unsigned *>(rsm);
     unsigned *wtot = hs + H * (W + 1);
-    float *cst = reinterpret_cast<float *>(wtot + H * 32);        // per centre: S_hat, 1/Omega_hat
-    uint8_t *ring = reinterpret_cast<uint8_t *>(cst + 2 * GXS);   // RING x ring_w bytes
+    int *cS = reinterpret_cast<int *>(wtot + H * 32);             // per centre: S_hat
+    float *cI = reinterpret_cast<float *>(cS + GXS);              // per centre: 1/Omega_hat
+    unsigned *ringw = reinterpret_cast<unsigned *>(cI + GXS);     // (W + 2R) columns x CSW words
+    uint8_t *ring8 = reinterpret_cast<uint8_t *>(ringw);
     const int j = threadIdx.x;
     const bool active = j < W;
     const int jc = cx0 + j;
     const int64_t q1 = q + 1;
     const long long mn = (long long)m * n;
-    const int RW = W + 2 * R;                                     // ring row width used
+    const int RW = W + 2 * R;                                     // ring columns used
 
     // rows [r0, r0 + cnt) into their ring slots, all loads of all rows in flight
     auto load_rows = [&](int r0, int cnt) {
@@ -183,7 +253,7 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
             const int slot = (rr + R) % RING;
             const int ry = min(max(rr, 0), p - 1);
             const int xx = min(max(cx0 - R + col, 0), q - 1);
-            ring[slot * ring_w + col] = I[(int64_t)ry * q + xx];
+            ring8[(col * CSW + (slot >> 2)) * 4 + (slot & 3)] = I[(int64_t)ry * q + xx];
         }
     };
 
@@ -195,15 +265,8 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
 #pragma unroll
     for (int s = 0; s < NS; ++s) cs[s] = 0;
     if (active) {
-        for (int i = 0; i < m; ++i) {
-            const int pv = P[(int64_t)(r + i) * q + jc];
-#pragma unroll
-            for (int sy = 0; sy < H; ++sy) {
-                const uint8_t *row = ring + ((r + i + sy) % RING) * ring_w + j;   // row r+i+sy-R
-#pragma unroll
-                for (int sx = 0; sx < H; ++sx) cs[sy * H + sx] += pv * (int)row[sx];
-            }
-        }
+        for (int b0 = 0; b0 < m; b0 += BATCH)
+            rco_batch<H, false>(cs, P, q, jc, r + b0, min(BATCH, m - b0), ringw, j, CSW, RW4, RING);
     }
     unsigned long long local = 0;
     for (int gy = gy0; gy < gy1; ++gy) {
@@ -212,32 +275,10 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
         if (steps > 0) {
             // the batch needs rows up to r + steps - 1 + m + R; load the new ones
             load_rows(r + m + R + 1, steps);
-            int pold[H], pnew[H];
-#pragma unroll
-            for (int k = 0; k < H; ++k) {
-                const bool ok = active && k < steps;
-                pold[k] = ok ? P[(int64_t)(r + k) * q + jc] : 0;
-                pnew[k] = ok ? P[(int64_t)(r + k + m) * q + jc] : 0;
-            }
             __syncthreads();
             if (active) {
-                int so = r % RING, sn = (r + m) % RING;     // slots of rows r - R and r + m - R
-#pragma unroll
-                for (int k = 0; k < H; ++k) {
-                    if (k < steps) {
-#pragma unroll
-                        for (int sy = 0; sy < H; ++sy) {
-                            const int a = so + sy, b = sn + sy;
-                            const uint8_t *ro = ring + (a >= RING ? a - RING : a) * ring_w + j;
-                            const uint8_t *rn = ring + (b >= RING ? b - RING : b) * ring_w + j;
-#pragma unroll
-                            for (int sx = 0; sx < H; ++sx)
-                                cs[sy * H + sx] += pnew[k] * (int)rn[sx] - pold[k] * (int)ro[sx];
-                        }
-                        so = (so + 1 == RING) ? 0 : so + 1;
-                        sn = (sn + 1 == RING) ? 0 : sn + 1;
-                    }
-                }
+                rco_batch<H, false>(cs, P, q, jc, r + m, steps, ringw, j, CSW, RW4, RING);
+                rco_batch<H, true>(cs, P, q, jc, r, steps, ringw, j, CSW, RW4, RING);
             }
             r += steps;
             __syncthreads();   // nobody reads the dead rows the next batch overwrites
@@ -245,10 +286,10 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
         // pivot statistics of this row's centres (exact sums, FP32 1/Omega_hat)
         for (int i = threadIdx.x; i < gx1 - gx0; i += blockDim.x) {
             const int cx = group_centre_of(gx0 + i, Lx, H);
-            const double Sp = box(PS, q1, cy, cx, m, n), Qp = box(PQ, q1, cy, cx, m, n);
-            const double var = (double)mn * Qp - Sp * Sp;
-            cst[2 * i] = (float)Sp;
-            cst[2 * i + 1] = var > 0.0 ? sqrtf((float)mn / (float)var) : 0.f;
+            const long long Sp = ii_box(PS, q1, cy, cx, m, n), Qp = ii_box(PQ, q1, cy, cx, m, n);
+            const long long var = mn * Qp - Sp * Sp;
+            cS[i] = (int)Sp;
+            cI[i] = var > 0 ? sqrtf((float)mn / (float)var) : 0.f;
         }
         // emit centre row cy, one shift row (sy) at a time: block-wide prefix
         // sums of the column sums turn each n-column window sum into one
@@ -309,8 +350,8 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
                 const int64_t li = (int64_t)my * Lx + mx;
                 // rho = (mn X - S_hat S) / (mn Omega_hat Omega): exact integer
                 // numerator, FP32 finish (flat windows have 1/Omega = 0 -> 0)
-                const long long num = mn * X - (long long)cst[2 * gxi] * (long long)wsum[li];
-                const float rho = ((float)num * inv_sigma[li]) * (cst[2 * gxi + 1] / (float)mn);
+                const long long num = mn * X - (long long)cS[gxi] * (long long)wsum[li];
+                const float rho = ((float)num * inv_sigma[li]) * (cI[gxi] / (float)mn);
                 if (rco) rco[(int64_t)my * Lx + mx] = rho;
                 if (rho < cut) ++local;
             }
@@ -322,31 +363,60 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
     }
 }
 
+struct RcoGeom {
+    bool ok;
+    int GXS, Wmax, threads, strips, bands, GYB;
+    size_t smem;
+};
+
+// Launch geometry: strips of GXS group columns (one thread per pivot column
+// of the strip), bands of GYB group rows; shared memory = H slide rows of
+// column prefix sums and their warp totals, the per-centre statistics of one
+// group row and the packed image ring.
 template <int H>
-cudaError_t launch_rho_co_h(const uint8_t *P, const uint8_t *I, int p, int q, int m, int n,
-                            const float *wsum, const float *inv_sigma, const double *PS,
-                            const double *PQ, float cut, float *rco,
-                            unsigned long long *count, cudaStream_t s) {
+RcoGeom rco_geom(int p, int q, int m, int n) {
     constexpr int R = RcoCfg<H>::R;
     constexpr int MAXT = RcoCfg<H>::MAXT;
+    constexpr size_t kSmemMax = 227 * 1024;
+    RcoGeom g{};
     const int Ly = p - m + 1, Lx = q - n + 1;
     const int Gy = groups_along(Ly, H), Gx = groups_along(Lx, H);
-    if (n + H > MAXT) return cudaErrorInvalidValue;
-    int GXS = (MAXT - n) / H + 1;
-    if (GXS > Gx) GXS = Gx;
-    const int Wmax = (GXS - 1) * H + n;
-    const int threads = ((Wmax + 31) / 32) * 32;
-    const int strips = (Gx + GXS - 1) / GXS;
+    // window sums of uint8 products are kept in 32 bits
+    if (n + H > MAXT || (uint64_t)m * n * 65025u > 0xffffffffull) return g;
+    const int csw = rco_csw(rco_ring(m, H));
+    auto smem_for = [&](int gxs, int *wmax) {
+        *wmax = (gxs - 1) * H + n;
+        return (size_t)H * (*wmax + 1 + 32) * sizeof(unsigned) + 2 * (size_t)gxs * sizeof(float) +
+               (size_t)(*wmax + 2 * R) * csw * sizeof(unsigned);
+    };
+    // widest strip within the thread limit, narrowed until tall windows' ring fits
+    g.GXS = std::min((MAXT - n) / H + 1, Gx);
+    g.smem = smem_for(g.GXS, &g.Wmax);
+    while (g.smem > kSmemMax && g.GXS > 1) {
+        g.GXS = std::max(1, g.GXS - std::max(1, g.GXS / 8));
+        g.smem = smem_for(g.GXS, &g.Wmax);
+    }
+    g.ok = g.smem <= kSmemMax;
+    g.threads = ((g.Wmax + 31) / 32) * 32;
+    g.strips = (Gx + g.GXS - 1) / g.GXS;
     const int target = num_sms() * 2;
-    int bands = (target + strips - 1) / strips;
-    if (bands > Gy) bands = Gy;
-    if (bands < 1) bands = 1;
-    int GYB = (Gy + bands - 1) / bands;
-    bands = (Gy + GYB - 1) / GYB;
-    const int ring_w = ((Wmax + 2 * R) + 15) & ~15;
-    const size_t smem = (size_t)H * (Wmax + 1 + 32) * sizeof(unsigned) + 2 * (size_t)GXS * sizeof(float) +
-                        (size_t)(m + 2 * R + 1 + H) * ring_w;
-    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    g.bands = (target + g.strips - 1) / g.strips;
+    if (g.bands > Gy) g.bands = Gy;
+    if (g.bands < 1) g.bands = 1;
+    g.GYB = (Gy + g.bands - 1) / g.bands;
+    g.bands = (Gy + g.GYB - 1) / g.GYB;
+    return g;
+}
+
+template <int H>
+cudaError_t launch_rho_co_h(const uint8_t *P, const uint8_t *I, int p, int q, int m, int n,
+                            const int *wsum, const float *inv_sigma, const long long *PS,
+                            const long long *PQ, float cut, float *rco,
+                            unsigned long long *count, cudaStream_t s) {
+    const int Ly = p - m + 1, Lx = q - n + 1;
+    const RcoGeom g = rco_geom<H>(p, q, m, n);
+    if (!g.ok) return cudaErrorInvalidValue;
+    const size_t smem = g.smem;
     static size_t attr = 0;
     if (smem > attr) {
         cudaError_t e = cudaFuncSetAttribute(rho_co_kernel<H>,
@@ -354,10 +424,10 @@ cudaError_t launch_rho_co_h(const uint8_t *P, const uint8_t *I, int p, int q, in
         if (e != cudaSuccess) return e;
         attr = smem;
     }
-    dim3 grid(strips, bands);
+    dim3 grid(g.strips, g.bands);
     LaunchScope ls_rho_co_kernel("rho_co_kernel", s);
-    rho_co_kernel<H><<<grid, threads, smem, s>>>(P, I, p, q, m, n, Ly, Lx, wsum, inv_sigma, PS, PQ,
-                                                 GXS, GYB, ring_w, cut, rco, count);
+    rho_co_kernel<H><<<grid, g.threads, smem, s>>>(P, I, p, q, m, n, Ly, Lx, wsum, inv_sigma, PS,
+                                                   PQ, g.GXS, g.GYB, cut, rco, count);
     return cudaGetLastError();
 }
 
@@ -388,19 +458,30 @@ cudaError_t launch_blur(const uint8_t *I, int p, int q, const uint8_t *level_map
     return cudaGetLastError();
 }
 
-cudaError_t launch_blur_corr(const double *IIS, const double *IIQ, const double *PS,
-                             const double *PQ, const double *PX, int p, int q, int m, int n,
+cudaError_t launch_blur_corr(const int *wsum, const float *inv_sigma, const long long *PS,
+                             const long long *PQ, const long long *PX, int p, int q, int m, int n,
                              float lambda, int block, int *fail, float *R, cudaStream_t s) {
     const int Ly = p - m + 1, Lx = q - n + 1;
     LaunchScope ls_blur_corr_kernel("blur_corr_kernel", s);
     blur_corr_kernel<<<grid_for((int64_t)Ly * Lx, 256), 256, 0, s>>>(
-        IIS, IIQ, PS, PQ, PX, q, Ly, Lx, m, n, lambda, block, fail, R);
+        wsum, inv_sigma, PS, PQ, PX, q, Ly, Lx, m, n, lambda, block, fail, R);
     return cudaGetLastError();
 }
 
+bool rho_co_supported(int p, int q, int m, int n, int h) {
+    switch (h) {
+        case 1: return rco_geom<1>(p, q, m, n).ok;
+        case 3: return rco_geom<3>(p, q, m, n).ok;
+        case 5: return rco_geom<5>(p, q, m, n).ok;
+        case 7: return rco_geom<7>(p, q, m, n).ok;
+        case 9: return rco_geom<9>(p, q, m, n).ok;
+        default: return false;
+    }
+}
+
 cudaError_t launch_rho_co(const uint8_t *P, const uint8_t *I, int p, int q, int m, int n,
-                          int h, const float *wsum, const float *inv_sigma, const double *PS,
-                          const double *PQ, float cut, float *rco,
+                          int h, const int *wsum, const float *inv_sigma, const long long *PS,
+                          const long long *PQ, float cut, float *rco,
                           unsigned long long *count, cudaStream_t s) {
     switch (h) {
         case 1: return launch_rho_co_h<1>(P, I, p, q, m, n, wsum, inv_sigma, PS, PQ, cut, rco, count, s);
@@ -412,7 +493,7 @@ cudaError_t launch_rho_co(const uint8_t *P, const uint8_t *I, int p, int q, int 
     }
 }
 
-cudaError_t launch_centre_stats(const double *PS, const double *PQ, int p, int q, int m, int n,
+cudaError_t launch_centre_stats(const long long *PS, const long long *PQ, int p, int q, int m, int n,
                                 int h, int Ly, int Lx, float *c_inv_sigma, float *c_efac,
                                 cudaStream_t s) {
     const int64_t G = (int64_t)groups_along(Ly, h) * groups_along(Lx, h);

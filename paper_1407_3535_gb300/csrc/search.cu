@@ -796,19 +796,19 @@ __device__ inline void stage_rows(const uint8_t *I, const uint8_t *img_end, int 
 // staging buffer (wbuf: 2 x kStageRows x WB bytes) the window goes through
 // shared memory; without, it is read straight from global memory.
 __device__ inline void warp_rho32(const uint8_t *__restrict__ I, int q, int Lx,
-                                  const double *__restrict__ IIS, const double *__restrict__ IIQ,
+                                  const long long *__restrict__ IIS,
+                                  const long long *__restrict__ IIQ,
                                   const float *__restrict__ tm, int m, int n, int npad,
                                   const float *__restrict__ inv_sigma, float ist, int idx,
                                   uint8_t *wbuf, const uint8_t *img_end, float &rho, float &eps) {
     const int lane = threadIdx.x & 31;
     const int64_t q1 = q + 1;
-    const double mn = (double)m * n;
+    const long long mn = (long long)m * n;
     const int y = idx / Lx, x = idx % Lx;
-    const double S = IIS[(int64_t)(y + m) * q1 + x + n] - IIS[(int64_t)y * q1 + x + n]
-                   - IIS[(int64_t)(y + m) * q1 + x] + IIS[(int64_t)y * q1 + x];
-    const double Q = IIQ[(int64_t)(y + m) * q1 + x + n] - IIQ[(int64_t)y * q1 + x + n]
-                   - IIQ[(int64_t)(y + m) * q1 + x] + IIQ[(int64_t)y * q1 + x];
-    const float a = (float)rint(S / mn);
+    const long long S = ii_box(IIS, q1, y, x, m, n);
+    const long long Q = ii_box(IIQ, q1, y, x, m, n);
+    // any integer in [0, 255] keeps |v| <= 255; the nearest to the mean keeps it small
+    const float a = rintf((float)S / (float)mn);
     const uint8_t *bp = I + (int64_t)y * q + x;
     float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
     if (wbuf) {
@@ -864,10 +864,9 @@ __device__ inline void warp_rho32(const uint8_t *__restrict__ I, int q, int Lx,
         const float is = inv_sigma[idx];
         rho = (acc * ist) * is;
         if (is > 0.f) {
-            const double var = mn * Q - S * S;
-            const double da = (double)a;
-            const double c2 = Q - 2.0 * da * S + mn * da * da;   // sum (I - a)^2
-            eps = eps_bound(kacc, (float)sqrt(mn * c2 / var));
+            const long long ia = (long long)a;
+            const long long c2 = Q - 2 * ia * S + mn * ia * ia;   // sum (I - a)^2, exact
+            eps = eps_bound(kacc, sqrtf((float)mn * ((float)c2 / win_var(mn, S, Q))));
         }
     }
 }
@@ -894,8 +893,8 @@ __device__ inline const float *stage_template(const float *tf, int m, int npad, 
 // Survivors [s_begin, min(n_surv, s_end)) in bucket order, skipping those whose
 // bound has fallen below the running certain lower bound of the maximum.
 __global__ void __launch_bounds__(256)
-survivors_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__restrict__ IIS,
-                 const double *__restrict__ IIQ, const float *__restrict__ tf, int m, int n,
+survivors_kernel(const uint8_t *__restrict__ I, int q, int Lx, const long long *__restrict__ IIS,
+                 const long long *__restrict__ IIQ, const float *__restrict__ tf, int m, int n,
                  int npad, const float *__restrict__ inv_sigma, TmplState *st,
                  const int *__restrict__ surv, const float *__restrict__ surv_ub, float *surv_rho,
                  float *surv_eps, int cap, int tmpl_in_smem, int s_begin, int s_end,
@@ -968,7 +967,7 @@ survivor_cut_kernel(TmplState *st, const int *__restrict__ bucket_end) {
 // them); raises the certain lower bound of the maximum before scan 2.
 __global__ void __launch_bounds__(256)
 group_members_kernel(const uint8_t *__restrict__ I, int q, int Ly, int Lx, int h,
-                     const double *__restrict__ IIS, const double *__restrict__ IIQ,
+                     const long long *__restrict__ IIS, const long long *__restrict__ IIQ,
                      const float *__restrict__ tf, size_t tsz, int m, int n, int npad,
                      const float *__restrict__ inv_sigma, TmplState *st,
                      const int *__restrict__ cand, int tmpl_in_smem) {
@@ -1199,8 +1198,8 @@ static size_t tmpl_smem(int m, int npad, int *in_smem) {
     return *in_smem ? smem : 0;
 }
 
-cudaError_t launch_survivors(const uint8_t *I, int pimg, int q, int Lx, const double *IIS,
-                             const double *IIQ, const float *tf, int m, int n, int npad,
+cudaError_t launch_survivors(const uint8_t *I, int pimg, int q, int Lx, const long long *IIS,
+                             const long long *IIQ, const float *tf, int m, int n, int npad,
                              const float *inv_sigma, TmplState *st, const int *surv,
                              const float *surv_ub, float *surv_rho, float *surv_eps, int cap,
                              const int *bucket_end, cudaStream_t s) {
@@ -1238,8 +1237,8 @@ cudaError_t launch_survivors(const uint8_t *I, int pimg, int q, int Lx, const do
     return cudaGetLastError();
 }
 
-cudaError_t launch_group_members(const uint8_t *I, int q, int Ly, int Lx, int h, const double *IIS,
-                                 const double *IIQ, const float *tf, size_t tsz, int m, int n,
+cudaError_t launch_group_members(const uint8_t *I, int q, int Ly, int Lx, int h, const long long *IIS,
+                                 const long long *IIQ, const float *tf, size_t tsz, int m, int n,
                                  int npad, const float *inv_sigma, int T, TmplState *st,
                                  const int *cand_topk, int topk, cudaStream_t s) {
     int in_smem = 0;

@@ -1,10 +1,10 @@
-// Local statistics: FP64 integral images and per-window sum / sum of squares
+// Local statistics: int64 integral images and per-window sum / sum of squares
 // (Algorithm 3's Run-Sum S, Q and Omega = sqrt(Q - S^2/mn); the "four
 // operations" per window of Section 3.1).
 //
-// The integral images hold integer values (pixels are integers in [0,255]),
-// so every entry is exact in FP64 up to 2^53; window sums taken from them are
-// exact, and mn*Q - S^2 is exact for mn <= 2^18.
+// Pixels are integers in [0,255], so the integral images, the window sums
+// taken from them and mn*Q - S^2 (for windows up to 2^23 pixels) are exact
+// integers; only the final 1/Omega is rounded (FP32).
 #include "common.cuh"
 
 namespace opta {
@@ -19,7 +19,7 @@ constexpr int kRowThreads = 256;
 // consecutive 32-byte runs (coalesced).  Sums are exact in int64.
 __global__ void __launch_bounds__(kRowThreads)
 ii_rows_kernel(const uint8_t *__restrict__ A, const uint8_t *__restrict__ B, int p, int q,
-               double *o0, double *o1, double *o2) {
+               long long *o0, long long *o1, long long *o2) {
     __shared__ long long wsum[3][kRowThreads / 32];
     __shared__ long long carry[3];
     const int y = blockIdx.x;
@@ -27,11 +27,11 @@ ii_rows_kernel(const uint8_t *__restrict__ A, const uint8_t *__restrict__ B, int
     const uint8_t *a = A + (int64_t)y * q;
     const uint8_t *b = B ? B + (int64_t)y * q : nullptr;
     const int64_t q1 = q + 1;
-    double *d0 = o0 + (int64_t)(y + 1) * q1;
-    double *d1 = o1 + (int64_t)(y + 1) * q1;
-    double *d2 = (b && o2) ? o2 + (int64_t)(y + 1) * q1 : nullptr;
+    long long *d0 = o0 + (int64_t)(y + 1) * q1;
+    long long *d1 = o1 + (int64_t)(y + 1) * q1;
+    long long *d2 = (b && o2) ? o2 + (int64_t)(y + 1) * q1 : nullptr;
     if (tid == 0) {
-        d0[0] = 0.0; d1[0] = 0.0; if (d2) d2[0] = 0.0;
+        d0[0] = 0; d1[0] = 0; if (d2) d2[0] = 0;
         carry[0] = carry[1] = carry[2] = 0;
     }
     __syncthreads();
@@ -65,9 +65,9 @@ ii_rows_kernel(const uint8_t *__restrict__ A, const uint8_t *__restrict__ B, int
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             if (xs + k < q) {
-                d0[xs + k + 1] = (double)(e0 + p0[k]);
-                d1[xs + k + 1] = (double)(e1 + p1[k]);
-                if (d2) d2[xs + k + 1] = (double)(e2 + p2[k]);
+                d0[xs + k + 1] = e0 + p0[k];
+                d1[xs + k + 1] = e1 + p1[k];
+                if (d2) d2[xs + k + 1] = e2 + p2[k];
             }
         }
         __syncthreads();
@@ -80,13 +80,13 @@ ii_rows_kernel(const uint8_t *__restrict__ A, const uint8_t *__restrict__ B, int
 
 // Column pass over rows 1..p of up to three arrays, 32 columns x 32 row segments.
 __global__ void __launch_bounds__(1024)
-ii_cols_kernel(int p, int q, double *o0, double *o1, double *o2) {
+ii_cols_kernel(int p, int q, long long *o0, long long *o1, long long *o2) {
     const int64_t q1 = q + 1;
     const int x = blockIdx.x * 32 + threadIdx.x;
     const int seg = threadIdx.y;
     const int seglen = (p + 31) / 32;
     const int r0 = 1 + seg * seglen, r1 = min(p + 1, r0 + seglen);
-    double a0 = 0, a1 = 0, a2 = 0;
+    long long a0 = 0, a1 = 0, a2 = 0;
     if (x < q1) {
         for (int r = r0; r < r1; ++r) {
             a0 += o0[r * q1 + x];
@@ -94,20 +94,20 @@ ii_cols_kernel(int p, int q, double *o0, double *o1, double *o2) {
             if (o2) a2 += o2[r * q1 + x];
         }
     }
-    __shared__ double sh[3][32][33];
+    __shared__ long long sh[3][32][33];
     sh[0][seg][threadIdx.x] = a0; sh[1][seg][threadIdx.x] = a1; sh[2][seg][threadIdx.x] = a2;
     __syncthreads();
     if (seg == 0) {
-        double c0 = 0, c1 = 0, c2 = 0;
+        long long c0 = 0, c1 = 0, c2 = 0;
         for (int k = 0; k < 32; ++k) {
-            const double t0 = sh[0][k][threadIdx.x], t1 = sh[1][k][threadIdx.x], t2 = sh[2][k][threadIdx.x];
+            const long long t0 = sh[0][k][threadIdx.x], t1 = sh[1][k][threadIdx.x], t2 = sh[2][k][threadIdx.x];
             sh[0][k][threadIdx.x] = c0; sh[1][k][threadIdx.x] = c1; sh[2][k][threadIdx.x] = c2;
             c0 += t0; c1 += t1; c2 += t2;
         }
     }
     __syncthreads();
     if (x >= q1) return;
-    double c0 = sh[0][seg][threadIdx.x], c1 = sh[1][seg][threadIdx.x], c2 = sh[2][seg][threadIdx.x];
+    long long c0 = sh[0][seg][threadIdx.x], c1 = sh[1][seg][threadIdx.x], c2 = sh[2][seg][threadIdx.x];
     for (int r = r0; r < r1; ++r) {
         c0 += o0[r * q1 + x]; o0[r * q1 + x] = c0;
         c1 += o1[r * q1 + x]; o1[r * q1 + x] = c1;
@@ -115,34 +115,29 @@ ii_cols_kernel(int p, int q, double *o0, double *o1, double *o2) {
     }
 }
 
-__device__ inline double box(const double *II, int64_t q1, int y, int x, int m, int n) {
-    return II[(int64_t)(y + m) * q1 + x + n] - II[(int64_t)y * q1 + x + n]
-         - II[(int64_t)(y + m) * q1 + x] + II[(int64_t)y * q1 + x];
-}
-
-__global__ void window_stats_kernel(const double *__restrict__ IIS, const double *__restrict__ IIQ,
-                                    int q, int Ly, int Lx, int m, int n,
-                                    float *inv_sigma, float *efac128, float *wsum) {
+__global__ void window_stats_kernel(const long long *__restrict__ IIS,
+                                    const long long *__restrict__ IIQ, int q, int Ly, int Lx,
+                                    int m, int n, float *inv_sigma, float *efac128, int *wsum) {
     const int64_t L = (int64_t)Ly * Lx;
     const int64_t q1 = q + 1;
-    const double mn = (double)m * n;
+    const long long mn = (long long)m * n;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int y = (int)(i / Lx), x = (int)(i % Lx);
-        const double S = box(IIS, q1, y, x, m, n);
-        const double Q = box(IIQ, q1, y, x, m, n);
-        const double var = mn * Q - S * S;          // exact: mn * Omega^2
+        const long long S = ii_box(IIS, q1, y, x, m, n);
+        const long long Q = ii_box(IIQ, q1, y, x, m, n);
+        const float fv = win_var(mn, S, Q);         // mn * Omega^2
         float inv = 0.f, ef = 0.f;
-        if (var > 0.0) {
+        if (fv > 0.f) {
             // FP32 finish (a few ulp; the error bounds that use 1/Omega allow 8u)
-            const float fv = (float)var, fmn = (float)mn;
+            const float fmn = (float)mn;
             inv = sqrtf(fmn / fv);
-            const double c2 = Q - 256.0 * S + 16384.0 * mn;   // sum (I - 128)^2, exact
+            const long long c2 = Q - 256 * S + 16384 * mn;   // sum (I - 128)^2, exact
             ef = sqrtf(fmn * (float)c2 / fv);
         }
         inv_sigma[i] = inv;
         if (efac128) efac128[i] = ef;
-        if (wsum) wsum[i] = (float)S;   // exact: window sums of 8-bit pixels < 2^24
+        if (wsum) wsum[i] = (int)S;
     }
 }
 
@@ -191,14 +186,14 @@ static int grid_for(int64_t n, int threads) {
     return (int)b;
 }
 
-cudaError_t launch_integrals(const uint8_t *A, const uint8_t *B, int p, int q,
-                             double *o0, double *o1, double *o2, cudaStream_t s) {
+cudaError_t launch_integrals(const uint8_t *A, const uint8_t *B, int p, int q, long long *o0,
+                             long long *o1, long long *o2, cudaStream_t s) {
     const int64_t q1 = q + 1;
     cudaError_t e;
     // first row zero
-    if ((e = cudaMemsetAsync(o0, 0, q1 * sizeof(double), s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(o1, 0, q1 * sizeof(double), s)) != cudaSuccess) return e;
-    if (B && o2 && (e = cudaMemsetAsync(o2, 0, q1 * sizeof(double), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(o0, 0, q1 * sizeof(long long), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(o1, 0, q1 * sizeof(long long), s)) != cudaSuccess) return e;
+    if (B && o2 && (e = cudaMemsetAsync(o2, 0, q1 * sizeof(long long), s)) != cudaSuccess) return e;
     {
         LaunchScope ls("ii_rows_kernel", s);
         ii_rows_kernel<<<p, kRowThreads, 0, s>>>(A, B, p, q, o0, o1, (B ? o2 : nullptr));
@@ -206,14 +201,15 @@ cudaError_t launch_integrals(const uint8_t *A, const uint8_t *B, int p, int q,
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
         LaunchScope ls("ii_cols_kernel", s);
-        ii_cols_kernel<<<(int)((q1 + 31) / 32), dim3(32, 32), 0, s>>>(p, q, o0, o1, (B ? o2 : nullptr));
+        ii_cols_kernel<<<(int)((q1 + 31) / 32), dim3(32, 32), 0, s>>>(p, q, o0, o1,
+                                                                     (B ? o2 : nullptr));
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_window_stats(const double *IIS, const double *IIQ, int p, int q,
+cudaError_t launch_window_stats(const long long *IIS, const long long *IIQ, int p, int q,
                                 int m, int n, float *inv_sigma, float *efac128,
-                                cudaStream_t s, float *wsum) {
+                                cudaStream_t s, int *wsum) {
     const int Ly = p - m + 1, Lx = q - n + 1;
     LaunchScope ls_window_stats_kernel("window_stats_kernel", s);
     window_stats_kernel<<<grid_for((int64_t)Ly * Lx, 256), 256, 0, s>>>(

@@ -170,6 +170,21 @@ def test_template_equals_image(opta):
     h.close()
 
 
+def test_template_above_the_group_kernel_limit(opta):
+    """A template of more than 66051 pixels (the group auto-correlation sums
+    are 32-bit) is refused with OPTA_ERR_TOO_LARGE, before any kernel; the
+    exhaustive search still serves it."""
+    img = synth.white_blur_image(300, seed=9)
+    t = img[10:270, 20:280].astype(np.float32)              # 260 x 260 > 66051 pixels
+    h = opta.optA_prepare(_cuda(img), opta.opta_params_default())
+    with pytest.raises(opta.OptaError) as ei:
+        opta.optA_search(h, [_cuda(t)])
+    assert ei.value.code == 8
+    h.close()
+    z = opta.zncc_full(_cuda(img), _cuda(t))
+    assert (z.y, z.x) == (10, 20) and abs(z.rho - 1.0) <= 1e-6
+
+
 # ---------------------------------------------------------------------------
 # Pruned search with the OptA preparation (blur levels + EGS)
 # ---------------------------------------------------------------------------
