@@ -36,6 +36,10 @@ opta_status map_err(cudaError_t e) {
 
 constexpr int kMaxRadius = 9;
 constexpr int kChunk = 128;   // templates per batch (tensor-core N = 2 * chunk <= 256)
+// Device bytes the per-template scan-2 arrays of one batch may take (28 bytes
+// per location and template: survivor index, bound, rho, error bound,
+// candidate index and its FP64 rho).
+constexpr size_t kScan2Budget = (size_t)8 << 30;
 
 // Device allocation that keeps a running byte count.
 struct DevMem {
@@ -83,10 +87,13 @@ struct opta_handle {
     std::map<std::pair<int, int>, SizeState *> sizes;
     // search scratch (grown on demand)
     size_t capL = 0, capG = 0, capT = 0, capN = 0;
+    size_t capS2 = 0;                         // template slots of the scan-2 arrays (stride capL)
+    size_t capCC = 0;                         // chunk-count entries
+    int *chunk_cnt = nullptr;                 // capS2 x ceil(capL / 4096)
     float *rho_tc = nullptr;
     float2 *tc = nullptr;
     int *surv = nullptr;
-    float *surv_rho = nullptr, *surv_eps = nullptr, *surv_ub = nullptr, *ubbuf = nullptr;
+    float *surv_rho = nullptr, *surv_eps = nullptr, *surv_ub = nullptr;
     int *bucket_cnt = nullptr, *bucket_cur = nullptr;
     int *cand = nullptr;
     double *cand_rho = nullptr;
@@ -405,22 +412,36 @@ opta_status grow(opta_handle *H, T *&p, size_t &cap_field_unused, size_t old_n, 
     return H->mem.alloc(&p, new_n);
 }
 
-// Make the search scratch large enough for L locations, G groups (times the
-// templates of one chunk: RT = chunk * G), chunk template slots of T = m*npad
-// elements each (TS = chunk * T), a B buffer of `Bbytes` and N templates.
-opta_status ensure_scratch(opta_handle *H, size_t L, size_t RT, size_t T, size_t TS,
+// Templates per scan-2 launch for L locations and a chunk of `chunk`.
+int scan2_batch(size_t L, int chunk) {
+    const size_t per = 28 * std::max<size_t>(L, 1);
+    size_t tb = kScan2Budget / per;
+    tb = std::min<size_t>(tb, (size_t)std::min(chunk, kScan2MaxT));
+    return (int)std::max<size_t>(tb, 1);
+}
+
+// Make the search scratch large enough for L locations per template and TB
+// scan-2 template slots, G groups (times the templates of one chunk: RT =
+// chunk * G), chunk template slots of T = m*npad elements each (TS = chunk *
+// T), a B buffer of `Bbytes` and N templates.
+opta_status ensure_scratch(opta_handle *H, size_t L, size_t TB, size_t RT, size_t T, size_t TS,
                            size_t Bbytes, size_t N) {
     size_t dummy = 0;
     const size_t G = RT;
-    if (L > H->capL) {
-        TRY(grow(H, H->surv, dummy, H->capL, L));
-        TRY(grow(H, H->surv_rho, dummy, H->capL, L));
-        TRY(grow(H, H->surv_eps, dummy, H->capL, L));
-        TRY(grow(H, H->surv_ub, dummy, H->capL, L));
-        TRY(grow(H, H->ubbuf, dummy, H->capL, L));
-        TRY(grow(H, H->cand, dummy, H->capL + kTopkMax, L + kTopkMax));
-        TRY(grow(H, H->cand_rho, dummy, H->capL + kTopkMax, L + kTopkMax));
-        H->capL = L;
+    if (L > H->capL || TB > H->capS2) {
+        const size_t nL = std::max(L, H->capL), nS = std::max(TB, H->capS2);
+        const size_t oldn = H->capL * H->capS2, newn = nL * nS;
+        TRY(grow(H, H->surv, dummy, oldn, newn));
+        TRY(grow(H, H->surv_rho, dummy, oldn, newn));
+        TRY(grow(H, H->surv_eps, dummy, oldn, newn));
+        TRY(grow(H, H->surv_ub, dummy, oldn, newn));
+        TRY(grow(H, H->cand, dummy, oldn, newn));
+        TRY(grow(H, H->cand_rho, dummy, oldn, newn));
+        const size_t cc = nS * ((nL + kScan2ChunkLoc - 1) / kScan2ChunkLoc);
+        TRY(grow(H, H->chunk_cnt, dummy, H->capCC, cc));
+        H->capCC = cc;
+        H->capL = nL;
+        H->capS2 = nS;
     }
     if (G > H->capG) {
         TRY(grow(H, H->rho_tc, dummy, H->capG, G));
@@ -433,8 +454,8 @@ opta_status ensure_scratch(opta_handle *H, size_t L, size_t RT, size_t T, size_t
         TRY(H->mem.alloc(&H->cand_topk, (size_t)kChunk * kTopkMax));
         TRY(H->mem.alloc(&H->cand_rho_topk, (size_t)kChunk * kTopkMax));
         TRY(H->mem.alloc(&H->tin, (size_t)kChunk));
-        TRY(H->mem.alloc(&H->bucket_cnt, kUbBuckets));
-        TRY(H->mem.alloc(&H->bucket_cur, kUbBuckets));
+        TRY(H->mem.alloc(&H->bucket_cnt, (size_t)kScan2MaxT * kUbBuckets));
+        TRY(H->mem.alloc(&H->bucket_cur, (size_t)kScan2MaxT * kUbBuckets));
     }
     if (T > H->capT) {
         TRY(grow(H, H->tstage, dummy, H->capT, T));
@@ -466,7 +487,7 @@ bool use_mma(const opta_handle *H) { return H->prm.precision == 1; }
 
 // Scratch needed by a batch of templates (sizes already prepared).
 opta_status size_scratch(opta_handle *H, const opta_template *t, int n_t) {
-    size_t maxL = 0, maxRT = 0, maxT = 0, maxTS = 0, maxB = 0;
+    size_t maxL = 0, maxRT = 0, maxT = 0, maxTS = 0, maxB = 0, maxTB = 1;
     std::map<std::pair<int, int>, int> count;
     for (int i = 0; i < n_t; ++i) count[std::make_pair(t[i].rows, t[i].cols)]++;
     for (auto &kv : count) {
@@ -475,13 +496,14 @@ opta_status size_scratch(opta_handle *H, const opta_template *t, int n_t) {
         const size_t chunk = (size_t)std::min(kv.second, kChunk);
         const size_t G = (size_t)S->Gy * S->Gx;
         maxL = std::max(maxL, (size_t)S->Ly * S->Lx);
+        maxTB = std::max(maxTB, (size_t)scan2_batch((size_t)S->Ly * S->Lx, (int)chunk));
         maxRT = std::max(maxRT, chunk * G);
         maxT = std::max(maxT, chunk * (size_t)m * n);
         maxTS = std::max(maxTS, chunk * (size_t)m * npad);
         const size_t N = ((2 * chunk + 15) / 16) * 16;
         if (use_mma(H)) maxB = std::max(maxB, (size_t)m * Kp * N * 2);
     }
-    return ensure_scratch(H, maxL, maxRT, maxT, maxTS, maxB, (size_t)n_t);
+    return ensure_scratch(H, maxL, maxTB, maxRT, maxT, maxTS, maxB, (size_t)n_t);
 }
 
 // Template statistics and scan 1 (Section 6: rho(t, pivot) at every centre)
@@ -540,30 +562,47 @@ opta_status enqueue_scan1(opta_handle *H, const opta_template *const *t, int n, 
     return OPTA_OK;
 }
 
-// Scan 2 (Eq. SEC), survivors and FP64 argmax, template by template, of the
-// chunk whose scan 1 and threshold are done.
+// Scan 2 (Eq. SEC), survivors and FP64 argmax of the chunk whose scan 1 and
+// threshold are done, in batches of scan2_batch() templates per launch.
 opta_status enqueue_scan2(opta_handle *H, const opta_template *const *t, int n, TmplState *st,
                           float *ub_map, uint8_t *surv_map, cudaStream_t s) {
     const int m = t[0]->rows, nn = t[0]->cols, npad = (nn + 7) & ~7;
     SizeState *S = H->sizes[std::make_pair(m, nn)];
-    const int capL = (int)H->capL;
+    const int64_t L = (int64_t)S->Ly * S->Lx;
     const int64_t G = (int64_t)S->Gy * S->Gx;
     const size_t tsz = (size_t)m * npad, dsz = (size_t)m * nn;
-    for (int k = 0; k < n; ++k) {
-        const float *tf = H->tf + k * tsz;
-        const double *td = H->td + k * dsz;
-        TmplState *sk = st + k;
-        CK(launch_bound_compact(H->tc + k * G, S->theta_co, S->Ly, S->Lx, S->h, sk, H->surv,
-                                H->surv_ub, capL, reinterpret_cast<int *>(H->ubbuf), ub_map, surv_map,
-                                H->bucket_cnt, H->bucket_cur, s));
-        CK(launch_survivors(H->I8, H->p, H->q, S->Lx, H->IIS, H->IIQ, tf, m, nn, npad, S->inv_sigma, sk,
-                            H->surv, H->surv_ub, H->surv_rho, H->surv_eps, capL, H->bucket_cur,
-                            s));
-        CK(launch_surv_candidates(sk, H->surv, H->surv_ub, H->surv_rho, H->surv_eps, H->cand,
-                                  capL, s));
-        CK(launch_refine64(H->I8, H->q, S->Lx, td, m, nn, sk, H->cand, H->cand_rho, capL, false, s));
-        CK(launch_final_argmax(sk, H->cand, H->cand_rho, capL, H->cand_topk + k * kTopkMax,
-                               H->cand_rho_topk + k * kTopkMax, s));
+    const int TB = std::min(scan2_batch((size_t)L, n), (int)H->capS2);
+    const int64_t scap = (int64_t)H->capL;
+    const int64_t nchunks = (L + kScan2ChunkLoc - 1) / kScan2ChunkLoc;
+    if (TB < 1 || ((ub_map || surv_map) && n != 1)) return OPTA_ERR_INVALID_ARG;
+    for (int k0 = 0; k0 < n; k0 += TB) {
+        const int T = std::min(TB, n - k0);
+        Scan2Batch B;
+        B.T = T;
+        B.st = st + k0;
+        B.tc = H->tc + k0 * G;
+        B.tc_stride = G;
+        B.tf = H->tf + k0 * tsz;
+        B.tsz = tsz;
+        B.surv = H->surv;
+        B.surv_ub = H->surv_ub;
+        B.surv_rho = H->surv_rho;
+        B.surv_eps = H->surv_eps;
+        B.scap = scap;
+        B.cand = H->cand;
+        B.ccap = scap;
+        B.chunk_cnt = H->chunk_cnt;
+        B.nchunks = nchunks;
+        B.bucket_cnt = H->bucket_cnt;
+        B.bucket_cur = H->bucket_cur;
+        CK(launch_bound_compact(B, S->theta_co, S->Ly, S->Lx, S->h, ub_map, surv_map, s));
+        CK(launch_survivors(B, H->I8, H->p, H->q, S->Lx, H->IIS, H->IIQ, m, nn, npad,
+                            S->inv_sigma, s));
+        CK(launch_surv_candidates(B, s));
+        CK(launch_refine64(H->I8, H->q, S->Lx, H->td + k0 * dsz, dsz, m, nn, T, st + k0, H->cand,
+                           H->cand_rho, scap, s));
+        CK(launch_final_argmax(T, st + k0, H->cand, H->cand_rho, scap, H->cand_topk + k0 * kTopkMax,
+                               H->cand_rho_topk + k0 * kTopkMax, s));
     }
     return OPTA_OK;
 }
@@ -687,7 +726,7 @@ opta_status optA_destroy(opta_handle *h) {
         delete S;
     }
     void *ptrs[] = {h->I8, h->IIS, h->IIQ, h->rho_tc, h->tc, h->surv, h->surv_rho, h->surv_eps,
-                    h->surv_ub, h->ubbuf, h->bucket_cnt, h->bucket_cur, h->Bmma, h->dev_err,
+                    h->surv_ub, h->chunk_cnt, h->bucket_cnt, h->bucket_cur, h->Bmma, h->dev_err,
                     h->cand_topk, h->cand_rho_topk, h->tin,
                     h->cand, h->cand_rho, h->topk_v, h->topk_i, h->tf, h->tstage, h->td,
                     h->states, h->weights, h->radius};
@@ -925,8 +964,8 @@ opta_status zncc_full(const opta_image *img, const opta_template *t, float *rho_
     ZCK(launch_tmpl_prep(tdev, ld, m, n, npad, tf, td, st, 0, s));
     ZCK(launch_zncc_map(I8, p, q, tf, m, n, npad, inv, ef, st, map, s));
     ZCK(launch_map_candidates(map, ef, L, m, n, st, cand, (int)L, s));
-    ZCK(launch_refine64(I8, q, Lx, td, m, n, st, cand, cand_rho, (int)L, false, s));
-    ZCK(launch_final_argmax(st, cand, cand_rho, (int)L, nullptr, nullptr, s));
+    ZCK(launch_refine64(I8, q, Lx, td, (size_t)m * n, m, n, 1, st, cand, cand_rho, L, s));
+    ZCK(launch_final_argmax(1, st, cand, cand_rho, L, nullptr, nullptr, s));
     TmplState hs;
     ZCK(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
     ZCK(cudaStreamSynchronize(s));

@@ -90,6 +90,10 @@ struct TmplState {
 // Survivors are bucketed by their upper bound (bucket 0 = highest) so that
 // they are evaluated roughly in decreasing bound order.
 constexpr int kUbBuckets = 256;
+// Templates per scan-2 launch (their histograms share one block's shared memory).
+constexpr int kScan2MaxT = 16;
+// Locations per scan-2 chunk (the unit of the per-chunk survivor counts).
+constexpr int kScan2ChunkLoc = 4096;
 
 // Device pointer and row stride of one template of a batch.
 struct TmplIn {
@@ -133,13 +137,16 @@ cudaError_t launch_zncc_map(const uint8_t *I, int p, int q, const float *tf, int
 cudaError_t launch_map_candidates(const float *map, const float *efac128, int64_t L, int m,
                                   int n, TmplState *st, int *cand, int cap, cudaStream_t s);
 
-// FP64 recomputation of rho at the candidate locations [0, n_cand).
-cudaError_t launch_refine64(const uint8_t *I, int q, int Lx, const double *td, int m, int n,
-                            TmplState *st, const int *cand, double *cand_rho, int cap,
-                            bool topk_range, cudaStream_t s);
-// Final argmax over candidates and threshold centres (nullable) -> st->best_idx / best_rho.
-cudaError_t launch_final_argmax(TmplState *st, const int *cand, const double *cand_rho, int cap,
-                                const int *cand_topk, const double *cand_rho_topk, cudaStream_t s);
+// FP64 recomputation of rho at the candidate locations [0, n_cand) of T
+// templates (template k: td + k * dsz, st + k, cand / cand_rho + k * ccap).
+cudaError_t launch_refine64(const uint8_t *I, int q, int Lx, const double *td, size_t dsz, int m,
+                            int n, int T, TmplState *st, const int *cand, double *cand_rho,
+                            int64_t ccap, cudaStream_t s);
+// Final argmax over the candidates and threshold centres (nullable; kTopkMax
+// per template) of T templates -> st->best_idx / best_rho.
+cudaError_t launch_final_argmax(int T, TmplState *st, const int *cand, const double *cand_rho,
+                                int64_t ccap, const int *cand_topk, const double *cand_rho_topk,
+                                cudaStream_t s);
 // FP64 rho at the threshold centres of T templates (kTopkMax slots each).
 cudaError_t launch_refine64_topk(const uint8_t *I, int q, int Lx, const double *td, size_t dsz,
                                  int m, int n, int T, TmplState *st, const int *cand_topk,
@@ -175,22 +182,38 @@ cudaError_t launch_group_members(const uint8_t *I, int q, int Ly, int Lx, int h,
                                  const long long *IIQ, const float *tf, size_t tsz, int m, int n,
                                  int npad, const float *inv_sigma, int T, TmplState *st,
                                  const int *cand_topk, int topk, cudaStream_t s);
-// Scan 2: bound of every location, bucket histogram of the survivors and
-// survivor count per chunk of 4096 locations (chunk_cnt: ceil(L/4096) ints),
-// then compaction of the survivors in bucket order with their upper bound;
-// ub_map / surv_map (nullable) receive the full maps.
-cudaError_t launch_bound_compact(const float2 *tc, const float2 *theta_co, int Ly, int Lx, int h,
-                                 TmplState *st, int *surv, float *surv_ub, int cap, int *chunk_cnt,
-                                 float *ub_map, uint8_t *surv_map, int *bucket_cnt,
-                                 int *bucket_cur, cudaStream_t s);
-cudaError_t launch_survivors(const uint8_t *I, int pimg, int q, int Lx, const long long *IIS,
-                             const long long *IIQ, const float *tf, int m, int n, int npad,
-                             const float *inv_sigma, TmplState *st, const int *surv,
-                             const float *surv_ub, float *surv_rho, float *surv_eps, int cap,
-                             const int *bucket_end, cudaStream_t s);
-cudaError_t launch_surv_candidates(TmplState *st, const int *surv, const float *surv_ub,
-                                   const float *surv_rho, const float *surv_eps, int *cand,
-                                   int cap, cudaStream_t s);
+// Scan 2 of a batch of T same-size templates: per-template arrays, each at
+// its own stride.
+struct Scan2Batch {
+    int T;
+    TmplState *st;                       // T states
+    const float2 *tc;                    // scan-1 angle intervals, template k at k * tc_stride
+    int64_t tc_stride;
+    const float *tf;                     // FP32 templates (m x npad), k * tsz
+    size_t tsz;
+    int *surv;                           // survivor lists (bucket order), k * scap
+    float *surv_ub, *surv_rho, *surv_eps;
+    int64_t scap;
+    int *cand;                           // candidates, k * ccap
+    int64_t ccap;
+    int *chunk_cnt;                      // survivors per chunk of 4096 locations, k * nchunks
+    int64_t nchunks;
+    int *bucket_cnt, *bucket_cur;        // k * kUbBuckets
+};
+
+// Bound of every location against each template's threshold, bucket
+// histograms of the survivors, survivor counts per chunk, then compaction of
+// the survivors in bucket order with their upper bound.  The auto-correlation
+// intervals (theta_co) are read once for the whole batch.  ub_map / surv_map
+// (nullable; T == 1 only) receive the full maps.
+cudaError_t launch_bound_compact(const Scan2Batch &B, const float2 *theta_co, int Ly, int Lx,
+                                 int h, float *ub_map, uint8_t *surv_map, cudaStream_t s);
+// Cut of the skippable buckets, then one bound-ordered sweep over the
+// survivors of all T templates (FP32 rho, running lower bound per template).
+cudaError_t launch_survivors(const Scan2Batch &B, const uint8_t *I, int pimg, int q, int Lx,
+                             const long long *IIS, const long long *IIQ, int m, int n, int npad,
+                             const float *inv_sigma, cudaStream_t s);
+cudaError_t launch_surv_candidates(const Scan2Batch &B, cudaStream_t s);
 
 // --- preparation ---
 // Blur with per-block sigma-level index (uint8 map; level 0 = copy) and weight table.

@@ -169,8 +169,8 @@ extern "C" opta_status zncc_full_noalloc(const opta_image *img, const opta_templ
     NA(launch_tmpl_prep(tdev, tld, m, n, npad, tf, td, st, 0, s));
     NA(launch_zncc_map(I8, p, q, tf, m, n, npad, inv, ef, st, map, s));
     NA(launch_map_candidates(map, ef, L, m, n, st, cand, (int)L, s));
-    NA(launch_refine64(I8, q, Lx, td, m, n, st, cand, crho, (int)L, false, s));
-    NA(launch_final_argmax(st, cand, crho, (int)L, nullptr, nullptr, s));
+    NA(launch_refine64(I8, q, Lx, td, (size_t)m * n, m, n, 1, st, cand, crho, L, s));
+    NA(launch_final_argmax(1, st, cand, crho, L, nullptr, nullptr, s));
     TmplState hs;
     NA(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
     NA(cudaStreamSynchronize(s));

@@ -13,6 +13,8 @@
 // FP64 candidates safe.
 #include <algorithm>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace opta {
@@ -234,30 +236,41 @@ __global__ void map_candidates_kernel(const float *__restrict__ map, const float
 // ---------------------------------------------------------------------------
 // FP64 recomputation of Eq. rho1 at candidate locations (two passes, as the
 // definition reads).  One block per candidate.
-// Candidates [0, n_cand) of one template.
+// Candidates [0, n_cand) of template blockIdx.y of a batch.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 refine64_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__restrict__ td,
-                int m, int n, TmplState *st, const int *__restrict__ cand, double *cand_rho,
-                int mode, int cap) {
+                size_t dsz, int m, int n, TmplState *st, const int *__restrict__ cand,
+                double *cand_rho, int64_t ccap) {
     __shared__ double sh[32];
+    st += blockIdx.y;
     if (st->flat) return;
-    (void)mode;
-    const int from = 0, to = min(st->n_cand, cap);
+    td += blockIdx.y * dsz;
+    cand += blockIdx.y * ccap;
+    cand_rho += blockIdx.y * ccap;
+    const int to = (int)min((int64_t)st->n_cand, ccap);
     const int mn = m * n;
-    for (int c = from + blockIdx.x; c < to; c += gridDim.x) {
+    const int r0 = (int)threadIdx.x / n, c0 = (int)threadIdx.x - r0 * n;   // start of this thread
+    const int dr = (int)blockDim.x / n, dc = (int)blockDim.x - dr * n;    // its stride in (row, col)
+    for (int c = blockIdx.x; c < to; c += gridDim.x) {
         const int idx = cand[c];
         const int y = idx / Lx, x = idx % Lx;
+        const uint8_t *w = I + (int64_t)y * q + x;
         long long si = 0;
-        for (int i = threadIdx.x; i < mn; i += blockDim.x)
-            si += I[(int64_t)(y + i / n) * q + x + (i % n)];
+        for (int i = threadIdx.x, r = r0, cc = c0; i < mn; i += blockDim.x) {
+            si += w[(int64_t)r * q + cc];
+            r += dr; cc += dc;
+            if (cc >= n) { cc -= n; ++r; }
+        }
         const double S = block_sum_d((double)si, sh);
         const double mu = S / (double)mn;
         double num = 0.0, vv = 0.0;
-        for (int i = threadIdx.x; i < mn; i += blockDim.x) {
-            const double d = (double)I[(int64_t)(y + i / n) * q + x + (i % n)] - mu;
+        for (int i = threadIdx.x, r = r0, cc = c0; i < mn; i += blockDim.x) {
+            const double d = (double)w[(int64_t)r * q + cc] - mu;
             num += td[i] * d;
             vv += d * d;
+            r += dr; cc += dc;
+            if (cc >= n) { cc -= n; ++r; }
         }
         num = block_sum_d(num, sh);
         vv = block_sum_d(vv, sh);
@@ -299,14 +312,18 @@ refine64_topk_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double 
 }
 
 // Argmax of (rho64, -index) over the survivor candidates and the threshold
-// centres of one template; one block.
+// centres of one template; one block per template of a batch.
 __global__ void __launch_bounds__(256)
 final_argmax_kernel(TmplState *st, const int *__restrict__ cand,
-                    const double *__restrict__ cand_rho, int cap, const int *__restrict__ ctk,
+                    const double *__restrict__ cand_rho, int64_t ccap, const int *__restrict__ ctk,
                     const double *__restrict__ crtk) {
     __shared__ double sv[256];
     __shared__ int si[256];
-    const int nc = min(st->n_cand, cap);
+    st += blockIdx.x;
+    cand += blockIdx.x * ccap;
+    cand_rho += blockIdx.x * ccap;
+    if (ctk) { ctk += blockIdx.x * kTopkMax; crtk += blockIdx.x * kTopkMax; }
+    const int nc = (int)min((int64_t)st->n_cand, ccap);
     double bv = -3.0;
     int bi = 0x7fffffff;
     if (!st->flat) {
@@ -591,19 +608,13 @@ __device__ inline int gap_bucket(float gap, float lim) {
 // SC_PER each).  gap = max(0, tc.lo - co.hi, co.lo - tc.hi) is the smallest
 // angle between t and the location allowed by the two intervals, so
 // rho <= cos(gap).  It is computed with subtractions and maxima only, so the
-// two passes below obtain bit-identical values.
+// two passes below obtain bit-identical values.  One launch serves a batch
+// of templates of one size: a thread loads its locations' auto-correlation
+// intervals and group indices once and tests them against every template.
 constexpr int SC_PER = 16;
 constexpr int kChunkLoc = 256 * SC_PER;
-
-__device__ inline float loc_gap(const float2 *__restrict__ tc, const float2 *__restrict__ theta_co,
-                                int Gx, int64_t i, int y, int x, int gyrow, float inv_h) {
-    // x / h by a rounded reciprocal: exact for x < 2^20 and h <= 9
-    const int gx = (int)(((float)x + 0.5f) * inv_h);
-    const float2 t = tc[gyrow * Gx + gx];
-    const float2 c = theta_co[i];
-    (void)y;
-    return fmaxf(0.f, fmaxf(t.x - c.y, c.x - t.y));
-}
+static_assert(kChunkLoc == kScan2ChunkLoc, "scan-2 chunk size");
+constexpr int kS2MaxT = kScan2MaxT;
 
 // Row/column of location i, advanced incrementally by `step` locations.
 struct LocCursor {
@@ -619,60 +630,101 @@ struct LocCursor {
     }
 };
 
-// Pass 1: survivor histogram by bucket, and the survivor count of every chunk.
+// This thread's SC_PER locations of chunk c: auto-correlation intervals and
+// group (centre) indices; gi = -1 past the end.
+__device__ inline void load_chunk(const float2 *__restrict__ theta_co, int64_t c, int64_t L,
+                                  int Lx, int Gx, float inv_h, float2 (&co)[SC_PER],
+                                  int (&gi)[SC_PER]) {
+    LocCursor cur(c * kChunkLoc + threadIdx.x, Lx);
+#pragma unroll
+    for (int k = 0; k < SC_PER; ++k) {
+        const int64_t i = c * kChunkLoc + k * 256 + threadIdx.x;
+        if (k) cur.advance(256, Lx);
+        gi[k] = -1;
+        co[k] = make_float2(0.f, 0.f);
+        if (i < L) {
+            // y / h, x / h by a rounded reciprocal: exact for y, x < 2^20 and h <= 9
+            const int gy = (int)(((float)cur.y + 0.5f) * inv_h);
+            const int gx = (int)(((float)cur.x + 0.5f) * inv_h);
+            gi[k] = gy * Gx + gx;
+            co[k] = theta_co[i];
+        }
+    }
+}
+
+__device__ inline float loc_gap(float2 t, float2 c) {
+    return fmaxf(0.f, fmaxf(t.x - c.y, c.x - t.y));
+}
+
+// Pass 1: survivor histogram by bucket and survivor count of every chunk,
+// per template of the batch.
 __global__ void __launch_bounds__(256)
-bound_hist_kernel(const float2 *__restrict__ tc, const float2 *__restrict__ theta_co, int Ly,
-                  int Lx, int h, TmplState *st, int *chunk_cnt, float *ub_map,
-                  uint8_t *surv_map, int *bucket_cnt) {
-    __shared__ int hist[kUbBuckets];
-    __shared__ int ccount;
-    if (st->flat) return;
-    for (int i = threadIdx.x; i < kUbBuckets; i += blockDim.x) hist[i] = 0;
+bound_hist_kernel(const Scan2Batch B, const float2 *__restrict__ theta_co, int Ly, int Lx,
+                  int h, float *ub_map, uint8_t *surv_map) {
+    __shared__ int hist[kS2MaxT][kUbBuckets];
+    __shared__ int ccount[kS2MaxT];
+    __shared__ float lims[kS2MaxT];
+    const int T = B.T;
+    for (int i = threadIdx.x; i < T * kUbBuckets; i += blockDim.x) hist[i / kUbBuckets][i % kUbBuckets] = 0;
+    if ((int)threadIdx.x < T)
+        lims[threadIdx.x] = B.st[threadIdx.x].flat ? -1.f : B.st[threadIdx.x].theta_lim;
     const int Gx = groups_along(Lx, h);
-    const float lim = st->theta_lim;
     const float inv_h = 1.f / (float)h;
     const int64_t L = (int64_t)Ly * Lx;
     const int64_t nchunks = (L + kChunkLoc - 1) / kChunkLoc;
+    const int lane = threadIdx.x & 31;
     for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        if (threadIdx.x == 0) ccount = 0;
+        if ((int)threadIdx.x < T) ccount[threadIdx.x] = 0;
         __syncthreads();
-        int mine = 0;
-        LocCursor cur(c * kChunkLoc + threadIdx.x, Lx);
+        float2 co[SC_PER];
+        int gi[SC_PER];
+        load_chunk(theta_co, c, L, Lx, Gx, inv_h, co, gi);
+        for (int t = 0; t < T; ++t) {
+            const float lim = lims[t];
+            if (lim < 0.f) continue;                       // flat template (uniform)
+            const float2 *tct = B.tc + t * B.tc_stride;
+            int mine = 0;
 #pragma unroll 4
-        for (int k = 0; k < SC_PER; ++k) {
-            const int64_t i = c * kChunkLoc + k * 256 + threadIdx.x;
-            bool f = false;
-            int b = -1;
-            if (k) cur.advance(256, Lx);
-            if (i < L) {
-                const int gyrow = (int)(((float)cur.y + 0.5f) * inv_h);
-                const float gap = loc_gap(tc, theta_co, Gx, i, cur.y, cur.x, gyrow, inv_h);
-                f = gap <= lim;
-                if (ub_map) ub_map[i] = cosf(gap) + kCosMargin;
-                if (surv_map) surv_map[i] = f ? 1 : 0;
-                if (f) b = gap_bucket(gap, lim);
+            for (int k = 0; k < SC_PER; ++k) {
+                bool f = false;
+                int b = -1;
+                if (gi[k] >= 0) {
+                    const float gap = loc_gap(tct[gi[k]], co[k]);
+                    f = gap <= lim;
+                    if (ub_map || surv_map) {
+                        const int64_t i = c * kChunkLoc + k * 256 + threadIdx.x;
+                        if (ub_map) ub_map[i] = cosf(gap) + kCosMargin;
+                        if (surv_map) surv_map[i] = f ? 1 : 0;
+                    }
+                    if (f) b = gap_bucket(gap, lim);
+                }
+                if (__any_sync(0xffffffffu, f)) {
+                    const unsigned peers = __match_any_sync(0xffffffffu, b);
+                    if (f && lane == __ffs(peers) - 1) atomicAdd(&hist[t][b], __popc(peers));
+                }
+                mine += f ? 1 : 0;
             }
-            if (__any_sync(0xffffffffu, f)) {
-                const unsigned peers = __match_any_sync(0xffffffffu, b);
-                if (f && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[b], __popc(peers));
-            }
-            mine += f ? 1 : 0;
+            for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+            if (lane == 0 && mine) atomicAdd(&ccount[t], mine);
         }
-        for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
-        if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&ccount, mine);
         __syncthreads();
-        if (threadIdx.x == 0) chunk_cnt[c] = ccount;
+        if ((int)threadIdx.x < T) B.chunk_cnt[threadIdx.x * B.nchunks + c] = ccount[threadIdx.x];
+        __syncthreads();
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kUbBuckets; i += blockDim.x)
-        if (hist[i]) atomicAdd(&bucket_cnt[i], hist[i]);
+    for (int i = threadIdx.x; i < T * kUbBuckets; i += blockDim.x) {
+        const int v = hist[i / kUbBuckets][i % kUbBuckets];
+        if (v) atomicAdd(&B.bucket_cnt[i], v);
+    }
 }
 
 // Exclusive scan of the bucket counts into write cursors; total survivors.
-__global__ void bucket_scan_kernel(TmplState *st, const int *__restrict__ bucket_cnt,
-                                   int *bucket_cur) {
+// One warp per template: each lane owns kUbBuckets/32 consecutive buckets.
+__global__ void bucket_scan_kernel(const Scan2Batch B) {
+    TmplState *st = B.st + blockIdx.x;
     if (st->flat) return;
-    // one warp: each lane owns kUbBuckets/32 consecutive buckets
+    const int *bucket_cnt = B.bucket_cnt + blockIdx.x * kUbBuckets;
+    int *bucket_cur = B.bucket_cur + blockIdx.x * kUbBuckets;
     constexpr int PER = kUbBuckets / 32;
     const int lane = threadIdx.x & 31;
     if (threadIdx.x >= 32) return;
@@ -691,58 +743,66 @@ __global__ void bucket_scan_kernel(TmplState *st, const int *__restrict__ bucket
 }
 
 // Pass 2: scatter the survivors into their bucket ranges (bucket 0 = largest
-// bound first) together with their bound cos(gap) + margin.  Only chunks with
-// survivors are revisited; their gaps are recomputed bit-identically.  Each
-// block counts a chunk per bucket in shared memory and reserves every bucket's
-// slice with one global atomic.
+// bound first) together with their bound cos(gap) + margin.  Only (chunk,
+// template) pairs with survivors are revisited; their gaps are recomputed
+// bit-identically.  Each block counts a chunk per bucket in shared memory and
+// reserves every bucket's slice with one global atomic.
 __global__ void __launch_bounds__(256)
-bound_scatter_kernel(const float2 *__restrict__ tc, const float2 *__restrict__ theta_co, int Ly,
-                     int Lx, int h, const int *__restrict__ chunk_cnt, TmplState *st, int *surv,
-                     float *surv_ub, int cap, int *bucket_cur) {
+bound_scatter_kernel(const Scan2Batch B, const float2 *__restrict__ theta_co, int Ly, int Lx,
+                     int h) {
     __shared__ int cnt[kUbBuckets];
     __shared__ int basep[kUbBuckets];
-    if (st->flat) return;
+    const int T = B.T;
     const int Gx = groups_along(Lx, h);
-    const float lim = st->theta_lim;
     const float inv_h = 1.f / (float)h;
     const int64_t L = (int64_t)Ly * Lx;
     const int64_t nchunks = (L + kChunkLoc - 1) / kChunkLoc;
     for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        if (chunk_cnt[c] == 0) continue;   // uniform over the block
-        for (int b = threadIdx.x; b < kUbBuckets; b += blockDim.x) cnt[b] = 0;
-        __syncthreads();
-        float g[SC_PER];
-        int bk[SC_PER];
-        LocCursor cur(c * kChunkLoc + threadIdx.x, Lx);
-#pragma unroll
-        for (int k = 0; k < SC_PER; ++k) {
-            const int64_t i = c * kChunkLoc + k * 256 + threadIdx.x;
-            if (k) cur.advance(256, Lx);
-            g[k] = i < L ? loc_gap(tc, theta_co, Gx, i, cur.y, cur.x,
-                                   (int)(((float)cur.y + 0.5f) * inv_h), inv_h)
-                         : 4.f;
-            bk[k] = g[k] <= lim ? gap_bucket(g[k], lim) : -1;
-            if (bk[k] >= 0) atomicAdd(&cnt[bk[k]], 1);
-        }
-        __syncthreads();
-        for (int b = threadIdx.x; b < kUbBuckets; b += blockDim.x) {
-            const int n = cnt[b];
-            basep[b] = n ? atomicAdd(&bucket_cur[b], n) : 0;
-            cnt[b] = 0;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < SC_PER; ++k) {
-            if (bk[k] < 0) continue;
-            const int pos = basep[bk[k]] + atomicAdd(&cnt[bk[k]], 1);
-            if (pos < cap) {
-                surv[pos] = (int)(c * kChunkLoc + k * 256 + threadIdx.x);
-                surv_ub[pos] = cosf(g[k]) + kCosMargin;
-            } else {
-                atomicOr(&st->overflow, 1);
+        bool loaded = false;
+        float2 co[SC_PER];
+        int gi[SC_PER];
+        for (int t = 0; t < T; ++t) {
+            if (B.chunk_cnt[t * B.nchunks + c] == 0) continue;   // uniform over the block
+            TmplState *st = B.st + t;
+            if (!loaded) {
+                load_chunk(theta_co, c, L, Lx, Gx, inv_h, co, gi);
+                loaded = true;
             }
+            const float lim = st->theta_lim;
+            const float2 *tct = B.tc + t * B.tc_stride;
+            int *bucket_cur = B.bucket_cur + t * kUbBuckets;
+            int *surv = B.surv + t * B.scap;
+            float *surv_ub = B.surv_ub + t * B.scap;
+            for (int b = threadIdx.x; b < kUbBuckets; b += blockDim.x) cnt[b] = 0;
+            __syncthreads();
+            float g[SC_PER];
+            int bk[SC_PER];
+#pragma unroll
+            for (int k = 0; k < SC_PER; ++k) {
+                g[k] = gi[k] >= 0 ? loc_gap(tct[gi[k]], co[k]) : 4.f;
+                bk[k] = g[k] <= lim ? gap_bucket(g[k], lim) : -1;
+                if (bk[k] >= 0) atomicAdd(&cnt[bk[k]], 1);
+            }
+            __syncthreads();
+            for (int b = threadIdx.x; b < kUbBuckets; b += blockDim.x) {
+                const int n = cnt[b];
+                basep[b] = n ? atomicAdd(&bucket_cur[b], n) : 0;
+                cnt[b] = 0;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < SC_PER; ++k) {
+                if (bk[k] < 0) continue;
+                const int pos = basep[bk[k]] + atomicAdd(&cnt[bk[k]], 1);
+                if (pos < B.scap) {
+                    surv[pos] = (int)(c * kChunkLoc + k * 256 + threadIdx.x);
+                    surv_ub[pos] = cosf(g[k]) + kCosMargin;
+                } else {
+                    atomicOr(&st->overflow, 1);
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
@@ -890,20 +950,25 @@ __device__ inline const float *stage_template(const float *tf, int m, int npad, 
     return tsm;
 }
 
-// Survivors [s_begin, min(n_surv, s_end)) in bucket order, skipping those whose
-// bound has fallen below the running certain lower bound of the maximum.
+// Survivors of template blockIdx.y of a batch, in bucket order, skipping
+// those whose bound has fallen below the running certain lower bound of the
+// maximum.
 __global__ void __launch_bounds__(256)
-survivors_kernel(const uint8_t *__restrict__ I, int q, int Lx, const long long *__restrict__ IIS,
-                 const long long *__restrict__ IIQ, const float *__restrict__ tf, int m, int n,
-                 int npad, const float *__restrict__ inv_sigma, TmplState *st,
-                 const int *__restrict__ surv, const float *__restrict__ surv_ub, float *surv_rho,
-                 float *surv_eps, int cap, int tmpl_in_smem, int s_begin, int s_end,
+survivors_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, int Lx,
+                 const long long *__restrict__ IIS, const long long *__restrict__ IIQ, int m,
+                 int n, int npad, const float *__restrict__ inv_sigma, int tmpl_in_smem,
                  int stage, const uint8_t *img_end) {
     extern __shared__ float4 ssm4[];
+    TmplState *st = B.st + blockIdx.y;
     if (st->flat) return;
+    const float *tf = B.tf + blockIdx.y * B.tsz;
+    const int *surv = B.surv + blockIdx.y * B.scap;
+    const float *surv_ub = B.surv_ub + blockIdx.y * B.scap;
+    float *surv_rho = B.surv_rho + blockIdx.y * B.scap;
+    float *surv_eps = B.surv_eps + blockIdx.y * B.scap;
     // blocks whose first entry lies beyond the survivor list have nothing to do
-    const int ns0 = min(min(min(st->n_surv, cap), s_end), st->n_surv_eff);
-    if (s_begin + blockIdx.x * (int)(blockDim.x >> 5) >= ns0) return;
+    const int ns0 = (int)min((int64_t)min(st->n_surv, st->n_surv_eff), B.scap);
+    if ((int)blockIdx.x * (int)(blockDim.x >> 5) >= ns0) return;
     const float *tm = stage_template(tf, m, npad, tmpl_in_smem, reinterpret_cast<float *>(ssm4));
     uint8_t *wbuf = nullptr;
     if (stage) {
@@ -921,21 +986,34 @@ survivors_kernel(const uint8_t *__restrict__ I, int q, int Lx, const long long *
     // one survivor per warp, interleaved so that all warps advance through
     // the bound-ordered list together; a survivor whose bound has fallen below
     // the running certain lower bound of the maximum is skipped (Eq. SEC with
-    // the best rho_tb found so far)
-    for (int s = s_begin + warp; s < ns; s += nwarps) {
-        const float lim = __shfl_sync(0xffffffffu, key_float(*lo_key), 0);
-        const float ub = __shfl_sync(0xffffffffu, surv_ub[s], 0);
-        if (ub < lim) continue;
-        float rho, eps;
-        warp_rho32(I, q, Lx, IIS, IIQ, tm, m, n, npad, inv_sigma, ist, surv[s], wbuf, img_end,
-                   rho, eps);
-        if (lane == 0) {
-            surv_rho[s] = rho;
-            surv_eps[s] = eps;
-            atomicMax(&st->lo_key, float_key(rho - eps));
-            ++evaluated;
+    // the best rho_tb found so far).  The warp's next 32 entries are read in
+    // one round (a lane each), so skipped entries cost no dependent load.
+    for (int64_t base = warp; base < ns; base += 32 * (int64_t)nwarps) {
+        const int64_t sl = base + (int64_t)lane * nwarps;
+        const bool have = sl < ns;
+        const float ubl = have ? surv_ub[sl] : -4.f;
+        const int idxl = have ? surv[sl] : 0;
+        const float lim0 = __shfl_sync(0xffffffffu, key_float(*lo_key), 0);
+        unsigned pend = __ballot_sync(0xffffffffu, have && ubl >= lim0);
+        while (pend) {
+            const int k = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const float ub = __shfl_sync(0xffffffffu, ubl, k);
+            const int idx = __shfl_sync(0xffffffffu, idxl, k);
+            const float lim = __shfl_sync(0xffffffffu, key_float(*lo_key), 0);
+            if (ub < lim) continue;
+            float rho, eps;
+            warp_rho32(I, q, Lx, IIS, IIQ, tm, m, n, npad, inv_sigma, ist, idx, wbuf, img_end,
+                       rho, eps);
+            if (lane == 0) {
+                const int64_t s = base + (int64_t)k * nwarps;
+                surv_rho[s] = rho;
+                surv_eps[s] = eps;
+                atomicMax(&st->lo_key, float_key(rho - eps));
+                ++evaluated;
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
     if (lane == 0 && evaluated) atomicAdd(&st->n_eval, evaluated);
 }
@@ -946,8 +1024,10 @@ survivors_kernel(const uint8_t *__restrict__ I, int q, int Lx, const long long *
 // (gap/lim)^2 in [b/NB, (b+1)/NB), i.e. bounds <= cos(lim sqrt(b/NB)) + margin
 // (evaluated with a relative slack on the angle and a doubled margin).
 __global__ void __launch_bounds__(kUbBuckets)
-survivor_cut_kernel(TmplState *st, const int *__restrict__ bucket_end) {
+survivor_cut_kernel(const Scan2Batch B) {
     __shared__ int first;
+    TmplState *st = B.st + blockIdx.x;
+    const int *bucket_end = B.bucket_cur + blockIdx.x * kUbBuckets;
     if (st->flat) return;
     if (threadIdx.x == 0) first = kUbBuckets;
     __syncthreads();
@@ -995,13 +1075,17 @@ group_members_kernel(const uint8_t *__restrict__ I, int q, int Ly, int Lx, int h
     }
 }
 
-__global__ void surv_candidates_kernel(TmplState *st, const int *__restrict__ surv,
-                                       const float *__restrict__ surv_ub,
-                                       const float *__restrict__ surv_rho,
-                                       const float *__restrict__ surv_eps, int *cand, int cap) {
+__global__ void surv_candidates_kernel(const Scan2Batch B) {
+    TmplState *st = B.st + blockIdx.y;
     if (st->flat) return;
+    const int *surv = B.surv + blockIdx.y * B.scap;
+    const float *surv_ub = B.surv_ub + blockIdx.y * B.scap;
+    const float *surv_rho = B.surv_rho + blockIdx.y * B.scap;
+    const float *surv_eps = B.surv_eps + blockIdx.y * B.scap;
+    int *cand = B.cand + blockIdx.y * B.ccap;
+    const int cap = (int)B.ccap;
     const float lstar = key_float(st->lo_key);
-    const int ns = min(st->n_surv, cap);
+    const int ns = (int)min((int64_t)st->n_surv, B.scap);
     for (int base = blockIdx.x * blockDim.x; base < ns; base += gridDim.x * blockDim.x) {
         const int s = base + threadIdx.x;
         bool f = false;
@@ -1063,19 +1147,20 @@ cudaError_t launch_map_candidates(const float *map, const float *efac128, int64_
     return cudaGetLastError();
 }
 
-cudaError_t launch_refine64(const uint8_t *I, int q, int Lx, const double *td, int m, int n,
-                            TmplState *st, const int *cand, double *cand_rho, int cap,
-                            bool topk_range, cudaStream_t s) {
+cudaError_t launch_refine64(const uint8_t *I, int q, int Lx, const double *td, size_t dsz, int m,
+                            int n, int T, TmplState *st, const int *cand, double *cand_rho,
+                            int64_t ccap, cudaStream_t s) {
+    const int bx = std::max(1, num_sms() * 2 / std::min(T, 8));
     LaunchScope ls_refine64_kernel("refine64_kernel", s);
-    refine64_kernel<<<num_sms() * 2, 256, 0, s>>>(I, q, Lx, td, m, n, st, cand, cand_rho,
-                                                   topk_range ? 0 : 1, cap);
+    refine64_kernel<<<dim3(bx, T), 256, 0, s>>>(I, q, Lx, td, dsz, m, n, st, cand, cand_rho, ccap);
     return cudaGetLastError();
 }
 
-cudaError_t launch_final_argmax(TmplState *st, const int *cand, const double *cand_rho, int cap,
-                                const int *cand_topk, const double *cand_rho_topk, cudaStream_t s) {
+cudaError_t launch_final_argmax(int T, TmplState *st, const int *cand, const double *cand_rho,
+                                int64_t ccap, const int *cand_topk, const double *cand_rho_topk,
+                                cudaStream_t s) {
     LaunchScope ls_final_argmax_kernel("final_argmax_kernel", s);
-    final_argmax_kernel<<<1, 256, 0, s>>>(st, cand, cand_rho, cap, cand_topk, cand_rho_topk);
+    final_argmax_kernel<<<T, 256, 0, s>>>(st, cand, cand_rho, ccap, cand_topk, cand_rho_topk);
     return cudaGetLastError();
 }
 
@@ -1157,31 +1242,29 @@ cudaError_t launch_threshold(TmplState *st, const double *cand_rho_topk, int T, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_bound_compact(const float2 *tc, const float2 *theta_co, int Ly, int Lx, int h,
-                                 TmplState *st, int *surv, float *surv_ub, int cap, int *chunk_cnt,
-                                 float *ub_map, uint8_t *surv_map, int *bucket_cnt,
-                                 int *bucket_cur, cudaStream_t s) {
+cudaError_t launch_bound_compact(const Scan2Batch &B, const float2 *theta_co, int Ly, int Lx,
+                                 int h, float *ub_map, uint8_t *surv_map, cudaStream_t s) {
+    if (B.T < 1 || B.T > kS2MaxT || ((ub_map || surv_map) && B.T != 1)) return cudaErrorInvalidValue;
     const int64_t L = (int64_t)Ly * Lx;
     const int64_t nchunks = (L + kChunkLoc - 1) / kChunkLoc;
+    if (nchunks > B.nchunks) return cudaErrorInvalidValue;
     int grid = (int)std::min<int64_t>(nchunks, (int64_t)num_sms() * 8);
     if (grid < 1) grid = 1;
-    cudaError_t e = cudaMemsetAsync(bucket_cnt, 0, kUbBuckets * sizeof(int), s);
+    cudaError_t e = cudaMemsetAsync(B.bucket_cnt, 0, (size_t)B.T * kUbBuckets * sizeof(int), s);
     if (e != cudaSuccess) return e;
     {
         LaunchScope ls("bound_hist_kernel", s);
-        bound_hist_kernel<<<grid, 256, 0, s>>>(tc, theta_co, Ly, Lx, h, st, chunk_cnt, ub_map,
-                                               surv_map, bucket_cnt);
+        bound_hist_kernel<<<grid, 256, 0, s>>>(B, theta_co, Ly, Lx, h, ub_map, surv_map);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
         LaunchScope ls("bucket_scan_kernel", s);
-        bucket_scan_kernel<<<1, 32, 0, s>>>(st, bucket_cnt, bucket_cur);
+        bucket_scan_kernel<<<B.T, 32, 0, s>>>(B);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
         LaunchScope ls("bound_scatter_kernel", s);
-        bound_scatter_kernel<<<grid, 256, 0, s>>>(tc, theta_co, Ly, Lx, h, chunk_cnt, st, surv,
-                                                  surv_ub, cap, bucket_cur);
+        bound_scatter_kernel<<<grid, 256, 0, s>>>(B, theta_co, Ly, Lx, h);
     }
     return cudaGetLastError();
 }
@@ -1198,11 +1281,9 @@ static size_t tmpl_smem(int m, int npad, int *in_smem) {
     return *in_smem ? smem : 0;
 }
 
-cudaError_t launch_survivors(const uint8_t *I, int pimg, int q, int Lx, const long long *IIS,
-                             const long long *IIQ, const float *tf, int m, int n, int npad,
-                             const float *inv_sigma, TmplState *st, const int *surv,
-                             const float *surv_ub, float *surv_rho, float *surv_eps, int cap,
-                             const int *bucket_end, cudaStream_t s) {
+cudaError_t launch_survivors(const Scan2Batch &B, const uint8_t *I, int pimg, int q, int Lx,
+                             const long long *IIS, const long long *IIQ, int m, int n, int npad,
+                             const float *inv_sigma, cudaStream_t s) {
     int in_smem = 0;
     size_t smem = tmpl_smem(m, npad, &in_smem);
     smem = (smem + 15) & ~(size_t)15;
@@ -1211,29 +1292,41 @@ cudaError_t launch_survivors(const uint8_t *I, int pimg, int q, int Lx, const lo
     const int WB = 16 * ((n + 30) / 16);
     const int stage = in_smem && n <= 256 ? 1 : 0;
     if (stage) smem += (size_t)8 * 2 * kStageRows * WB;
+    static std::mutex mu;
     static size_t attr = 0;
-    if (smem > attr) {
-        cudaError_t e = cudaFuncSetAttribute(survivors_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = smem;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (smem > attr) {
+            cudaError_t e = cudaFuncSetAttribute(survivors_kernel,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr = smem;
+        }
     }
     const uint8_t *iend = I + (int64_t)q * pimg;
     // buckets whose largest bound is below the certain lower bound already
     // reached (threshold centres and their groups) are cut off, then one sweep
     {
         LaunchScope ls("survivor_cut_kernel", s);
-        survivor_cut_kernel<<<1, kUbBuckets, 0, s>>>(st, bucket_end);
+        survivor_cut_kernel<<<B.T, kUbBuckets, 0, s>>>(B);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    // one sweep for the whole batch: num_sms * 4 blocks for one template,
+    // fewer per template (down to num_sms) when several share the launch
+    const int bx = std::max(num_sms(), num_sms() * 4 / std::min(B.T, 4));
     {
         LaunchScope ls("survivors_kernel", s);
-        survivors_kernel<<<num_sms() * 4, 256, smem, s>>>(I, q, Lx, IIS, IIQ, tf, m, n, npad,
-                                                          inv_sigma, st, surv, surv_ub, surv_rho,
-                                                          surv_eps, cap, in_smem, 0, 0x7fffffff,
-                                                          stage, iend);
+        survivors_kernel<<<dim3(bx, B.T), 256, smem, s>>>(B, I, q, Lx, IIS, IIQ, m, n, npad,
+                                                          inv_sigma, in_smem, stage, iend);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_surv_candidates(const Scan2Batch &B, cudaStream_t s) {
+    LaunchScope ls("surv_candidates_kernel", s);
+    const int bx = std::max(1, num_sms() * 4 / std::min(B.T, 4));
+    surv_candidates_kernel<<<dim3(bx, B.T), 256, 0, s>>>(B);
     return cudaGetLastError();
 }
 
@@ -1256,13 +1349,5 @@ cudaError_t launch_group_members(const uint8_t *I, int q, int Ly, int Lx, int h,
     return cudaGetLastError();
 }
 
-cudaError_t launch_surv_candidates(TmplState *st, const int *surv, const float *surv_ub,
-                                   const float *surv_rho, const float *surv_eps, int *cand,
-                                   int cap, cudaStream_t s) {
-    LaunchScope ls_surv_candidates_kernel("surv_candidates_kernel", s);
-    surv_candidates_kernel<<<num_sms() * 4, 256, 0, s>>>(st, surv, surv_ub, surv_rho, surv_eps,
-                                                         cand, cap);
-    return cudaGetLastError();
-}
 
 }  // namespace opta

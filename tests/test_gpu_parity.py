@@ -209,6 +209,25 @@ def test_opta_blur_egs_many_sizes(opta, decay):
     h.close()
 
 
+def test_many_templates_of_one_size_cross_batches(opta):
+    """Twenty templates of one size: scan 2 runs them in launches of at most
+    16 templates, so this covers a full batch, a ragged one and a flat
+    template inside a batch (its neighbours must be unaffected)."""
+    img = synth.aerial_image(384, n_octaves=7, n_prims=30, seed=31)
+    ts = synth.make_templates(img, [(20, 28)] * 20, seed=32, noise=3.0)
+    flat = np.full((20, 28), 7.0, dtype=np.float32)
+    datas = [t.data for t in ts[:9]] + [flat] + [t.data for t in ts[9:]]
+    h = opta.optA_prepare(_cuda(img), opta.opta_params_default())
+    res = opta.optA_search(h, [_cuda(d) for d in datas])
+    assert len(res) == 21
+    for i, (d, r) in enumerate(zip(datas, res)):
+        if i == 9:
+            assert r.status == 2           # OPTA_ERR_FLAT_TEMPLATE
+            continue
+        _check_best(r, ref.zncc_map(img, d), f"batch template {i}")
+    h.close()
+
+
 def test_search_is_deterministic(opta):
     img = synth.aerial_image(384, n_octaves=7, n_prims=30, seed=7)
     ts = synth.make_templates(img, [24, 32], seed=8, noise=3.0)
