@@ -71,6 +71,7 @@ struct SizeState {
     int *wsum = nullptr;           // L window sums of I
     float *rho_co = nullptr;       // L
     float2 *theta_co = nullptr;    // L angle intervals of rho_co
+    float2 *gco = nullptr;         // G union of the members' angle intervals per group
     float *c_inv_sigma = nullptr;  // G
     float *c_efac = nullptr;       // G
     std::vector<float> sigma_map;
@@ -88,8 +89,7 @@ struct opta_handle {
     // search scratch (grown on demand)
     size_t capL = 0, capG = 0, capT = 0, capN = 0;
     size_t capS2 = 0;                         // template slots of the scan-2 arrays (stride capL)
-    size_t capCC = 0;                         // chunk-count entries
-    int *chunk_cnt = nullptr;                 // capS2 x ceil(capL / 4096)
+    int *ucnt = nullptr;                      // kScan2MaxT unordered-survivor counters
     float *rho_tc = nullptr;
     float2 *tc = nullptr;
     int *surv = nullptr;
@@ -291,6 +291,7 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
             H->mem.release(S->wsum, L);
             H->mem.release(S->rho_co, L);
             H->mem.release(S->theta_co, L);
+            H->mem.release(S->gco, (size_t)S->Gy * S->Gx);
             H->mem.release(S->c_inv_sigma, (size_t)S->Gy * S->Gx);
             H->mem.release(S->c_efac, (size_t)S->Gy * S->Gx);
             if (S->P_owned) H->mem.release(S->P, (size_t)p * q);
@@ -397,6 +398,8 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     PCK(launch_rho_co(S->P, H->I8, p, q, m, n, S->h, S->wsum, S->inv_sigma, PS, PQ, 0.f, S->rho_co,
                       nullptr, s));
     PCK(launch_theta_co(S->rho_co, L, S->theta_co, s));
+    PTRY(H->mem.alloc(&S->gco, G));
+    PCK(launch_group_co(S->theta_co, S->Ly, S->Lx, S->h, S->gco, s));
     PCK(launch_centre_stats(PS, PQ, p, q, m, n, S->h, S->Ly, S->Lx, S->c_inv_sigma, S->c_efac, s));
     PCK(cudaStreamSynchronize(s));
     H->sizes[key] = S;
@@ -437,9 +440,6 @@ opta_status ensure_scratch(opta_handle *H, size_t L, size_t TB, size_t RT, size_
         TRY(grow(H, H->surv_ub, dummy, oldn, newn));
         TRY(grow(H, H->cand, dummy, oldn, newn));
         TRY(grow(H, H->cand_rho, dummy, oldn, newn));
-        const size_t cc = nS * ((nL + kScan2ChunkLoc - 1) / kScan2ChunkLoc);
-        TRY(grow(H, H->chunk_cnt, dummy, H->capCC, cc));
-        H->capCC = cc;
         H->capL = nL;
         H->capS2 = nS;
     }
@@ -456,6 +456,7 @@ opta_status ensure_scratch(opta_handle *H, size_t L, size_t TB, size_t RT, size_
         TRY(H->mem.alloc(&H->tin, (size_t)kChunk));
         TRY(H->mem.alloc(&H->bucket_cnt, (size_t)kScan2MaxT * kUbBuckets));
         TRY(H->mem.alloc(&H->bucket_cur, (size_t)kScan2MaxT * kUbBuckets));
+        TRY(H->mem.alloc(&H->ucnt, (size_t)kScan2MaxT));
     }
     if (T > H->capT) {
         TRY(grow(H, H->tstage, dummy, H->capT, T));
@@ -573,7 +574,6 @@ opta_status enqueue_scan2(opta_handle *H, const opta_template *const *t, int n, 
     const size_t tsz = (size_t)m * npad, dsz = (size_t)m * nn;
     const int TB = std::min(scan2_batch((size_t)L, n), (int)H->capS2);
     const int64_t scap = (int64_t)H->capL;
-    const int64_t nchunks = (L + kScan2ChunkLoc - 1) / kScan2ChunkLoc;
     if (TB < 1 || ((ub_map || surv_map) && n != 1)) return OPTA_ERR_INVALID_ARG;
     for (int k0 = 0; k0 < n; k0 += TB) {
         const int T = std::min(TB, n - k0);
@@ -591,11 +591,10 @@ opta_status enqueue_scan2(opta_handle *H, const opta_template *const *t, int n, 
         B.scap = scap;
         B.cand = H->cand;
         B.ccap = scap;
-        B.chunk_cnt = H->chunk_cnt;
-        B.nchunks = nchunks;
+        B.ucnt = H->ucnt;
         B.bucket_cnt = H->bucket_cnt;
         B.bucket_cur = H->bucket_cur;
-        CK(launch_bound_compact(B, S->theta_co, S->Ly, S->Lx, S->h, ub_map, surv_map, s));
+        CK(launch_bound_compact(B, S->theta_co, S->gco, S->Ly, S->Lx, S->h, ub_map, surv_map, s));
         CK(launch_survivors(B, H->I8, H->p, H->q, S->Lx, H->IIS, H->IIQ, m, nn, npad,
                             S->inv_sigma, s));
         CK(launch_surv_candidates(B, s));
@@ -721,12 +720,13 @@ opta_status optA_destroy(opta_handle *h) {
     for (auto &kv : h->sizes) {
         SizeState *S = kv.second;
         cudaFree(S->inv_sigma); cudaFree(S->wsum); cudaFree(S->rho_co); cudaFree(S->theta_co);
+        cudaFree(S->gco);
         cudaFree(S->c_inv_sigma); cudaFree(S->c_efac);
         if (S->P_owned) cudaFree(S->P);
         delete S;
     }
     void *ptrs[] = {h->I8, h->IIS, h->IIQ, h->rho_tc, h->tc, h->surv, h->surv_rho, h->surv_eps,
-                    h->surv_ub, h->chunk_cnt, h->bucket_cnt, h->bucket_cur, h->Bmma, h->dev_err,
+                    h->surv_ub, h->ucnt, h->bucket_cnt, h->bucket_cur, h->Bmma, h->dev_err,
                     h->cand_topk, h->cand_rho_topk, h->tin,
                     h->cand, h->cand_rho, h->topk_v, h->topk_i, h->tf, h->tstage, h->td,
                     h->states, h->weights, h->radius};

@@ -92,8 +92,7 @@ struct TmplState {
 constexpr int kUbBuckets = 256;
 // Templates per scan-2 launch (their histograms share one block's shared memory).
 constexpr int kScan2MaxT = 16;
-// Locations per scan-2 chunk (the unit of the per-chunk survivor counts).
-constexpr int kScan2ChunkLoc = 4096;
+
 
 // Device pointer and row stride of one template of a batch.
 struct TmplIn {
@@ -196,18 +195,21 @@ struct Scan2Batch {
     int64_t scap;
     int *cand;                           // candidates, k * ccap
     int64_t ccap;
-    int *chunk_cnt;                      // survivors per chunk of 4096 locations, k * nchunks
-    int64_t nchunks;
+    int *ucnt;                           // unordered survivors found, per template
     int *bucket_cnt, *bucket_cur;        // k * kUbBuckets
 };
 
-// Bound of every location against each template's threshold, bucket
-// histograms of the survivors, survivor counts per chunk, then compaction of
-// the survivors in bucket order with their upper bound.  The auto-correlation
-// intervals (theta_co) are read once for the whole batch.  ub_map / surv_map
-// (nullable; T == 1 only) receive the full maps.
-cudaError_t launch_bound_compact(const Scan2Batch &B, const float2 *theta_co, int Ly, int Lx,
-                                 int h, float *ub_map, uint8_t *surv_map, cudaStream_t s);
+// Bound of every location against each template's threshold (group test
+// on the group union intervals gco first, members of passing groups only),
+// bucket histograms of the survivors, then the survivors in bucket order
+// with their upper bound.  ub_map / surv_map (nullable; T == 1 only)
+// receive the full maps.
+cudaError_t launch_bound_compact(const Scan2Batch &B, const float2 *theta_co, const float2 *gco,
+                                 int Ly, int Lx, int h, float *ub_map, uint8_t *surv_map,
+                                 cudaStream_t s);
+// Per group: the union (lowest lo, highest hi) of its members' angle intervals.
+cudaError_t launch_group_co(const float2 *theta_co, int Ly, int Lx, int h, float2 *gco,
+                            cudaStream_t s);
 // Cut of the skippable buckets, then one bound-ordered sweep over the
 // survivors of all T templates (FP32 rho, running lower bound per template).
 cudaError_t launch_survivors(const Scan2Batch &B, const uint8_t *I, int pimg, int q, int Lx,

@@ -144,7 +144,7 @@ template <int H>
 struct RcoCfg {
     static constexpr int R = (H - 1) / 2;
     static constexpr int NS = H * H;
-    static constexpr int MAXT = H >= 9 ? 512 : (H >= 7 ? 640 : 1024);
+    static constexpr int MAXT = H >= 9 ? 448 : (H >= 7 ? 640 : 1024);
     static constexpr int KW = (H + 3) / 4;           // pivot words per batch
     static constexpr int BATCH = 4 * KW;             // rows per batch (>= H)
     static constexpr int NA = (H + BATCH + 2) / 4;   // aligned image words per column and batch
@@ -157,14 +157,40 @@ struct RcoCfg {
 __host__ __device__ inline int rco_ring(int m, int H) { return (m + (H - 1) + 1 + H + 3) & ~3; }
 __host__ __device__ inline int rco_csw(int ring) { return (ring >> 2) | 1; }
 
-// cs[sy][sx] += (or -=) sum_{k<cnt} P(prow+k, jc) * I(prow+k+sy-R, cx0+j+sx-R)
-// for cnt <= BATCH rows; image row rr lives in ring slot (rr + R) % RING.
-template <int H, bool SUB>
-__device__ __forceinline__ void rco_batch(int (&cs)[H * H], const uint8_t *__restrict__ P, int q,
-                                          int jc, int prow, int cnt, const unsigned *ringw, int j,
-                                          int CSW, int RW4, int RING) {
-    constexpr int KW = RcoCfg<H>::KW, NA = RcoCfg<H>::NA;
-    unsigned pw[KW];
+// Emission geometry: the column sums of one shift row are scanned in
+// segments of SL = 32 * PL columns (PL a power of two), one warp per (shift
+// column, segment); lane l holds PL consecutive columns at a padded stride
+// PLS (odd, or 1: conflict-free).  A window sum adds the totals of the
+// segments it spans to the difference of two in-segment prefixes.
+struct RcoScan {
+    int PL, lgPL, PLS, SL, lgSL, NSEG, RS;
+};
+__host__ __device__ inline RcoScan rco_scan(int Wmax, int H, int nwarps) {
+    RcoScan g;
+    int nseg = nwarps / H;
+    if (nseg < 1) nseg = 1;
+    const int need = (Wmax + nseg * 32 - 1) / (nseg * 32);   // columns per lane
+    g.PL = 1;
+    g.lgPL = 0;
+    while (g.PL < need) { g.PL <<= 1; ++g.lgPL; }
+    g.PLS = g.PL == 1 ? 1 : g.PL + 1;
+    g.SL = 32 * g.PL;
+    g.lgSL = g.lgPL + 5;
+    g.NSEG = (Wmax + g.SL - 1) / g.SL;
+    g.RS = g.NSEG * 32 * g.PLS;
+    return g;
+}
+__device__ inline int rco_addr(int c, const RcoScan &g) {
+    const int seg = c >> g.lgSL, w = c & (g.SL - 1);
+    return (seg * 32 + (w >> g.lgPL)) * g.PLS + (w & (g.PL - 1));
+}
+
+// Pivot column jc, rows [prow, prow + cnt), packed 4 rows per word (zero
+// past cnt, cnt <= BATCH): the loads are issued together.
+template <int H>
+__device__ __forceinline__ void rco_pcol(unsigned (&pw)[RcoCfg<H>::KW], const uint8_t *__restrict__ P,
+                                         int q, int jc, int prow, int cnt) {
+    constexpr int KW = RcoCfg<H>::KW;
 #pragma unroll
     for (int w = 0; w < KW; ++w) {
         pw[w] = 0u;
@@ -174,6 +200,16 @@ __device__ __forceinline__ void rco_batch(int (&cs)[H * H], const uint8_t *__res
             if (k < cnt) pw[w] |= (unsigned)P[(int64_t)(prow + k) * q + jc] << (8 * b);
         }
     }
+}
+
+// cs[sy][sx] += (or -=) sum_{k<cnt} P(prow+k, jc) * I(prow+k+sy-R, cx0+j+sx-R)
+// for the packed pivot words pw of rows [prow, prow + cnt); image row rr
+// lives in ring slot (rr + R) % RING.
+template <int H, bool SUB>
+__device__ __forceinline__ void rco_batch(int (&cs)[H * H], const unsigned (&pw)[RcoCfg<H>::KW],
+                                          int prow, const unsigned *ringw, int j, int CSW, int RW4,
+                                          int RING) {
+    constexpr int KW = RcoCfg<H>::KW, NA = RcoCfg<H>::NA;
     const int slot0 = prow % RING;                  // slot of image row prow - R
     const unsigned sh = (unsigned)(slot0 & 3) * 8u;
     int woff[NA + 1];
@@ -210,6 +246,24 @@ __device__ __forceinline__ void rco_batch(int (&cs)[H * H], const uint8_t *__res
     }
 }
 
+// Shared-memory words of one CTA (host and device agree on the layout):
+// two emission buffers of H scanned shift rows and their segment totals,
+// the per-centre statistics and the image ring.
+struct RcoSmem {
+    int hsc, segt, cst, ring, total;
+};
+__host__ __device__ inline RcoSmem rco_smem(int H, int Wmax, int GXS, int R, int CSW,
+                                            const RcoScan &g) {
+    RcoSmem l;
+    int o = 0;
+    l.hsc = o;  o += 2 * H * g.RS;
+    l.segt = o; o += 2 * H * g.NSEG;
+    l.cst = o;  o += 2 * GXS;
+    l.ring = o; o += (Wmax + 2 * R) * CSW;
+    l.total = o;
+    return l;
+}
+
 template <int H>
 __global__ void __launch_bounds__(RcoCfg<H>::MAXT, 1)
 rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int p, int q,
@@ -219,139 +273,191 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
               float *rco, unsigned long long *count) {
     constexpr int R = RcoCfg<H>::R;
     constexpr int NS = RcoCfg<H>::NS;
+    constexpr int KW = RcoCfg<H>::KW;
     constexpr int BATCH = RcoCfg<H>::BATCH;
-    extern __shared__ int rsm[];
+    extern __shared__ unsigned rsm[];
     const int Gy = groups_along(Ly, H), Gx = groups_along(Lx, H);
     const int gx0 = blockIdx.x * GXS, gy0 = blockIdx.y * GYB;
     if (gx0 >= Gx || gy0 >= Gy) return;
     const int gx1 = min(Gx, gx0 + GXS), gy1 = min(Gy, gy0 + GYB);
+    const int ngx = gx1 - gx0;
     const int cx0 = group_centre_of(gx0, Lx, H);
     const int W = group_centre_of(gx1 - 1, Lx, H) + n - cx0;   // pivot columns
+    const int Wmax = (GXS - 1) * H + n;
     const int RING = rco_ring(m, H), RW4 = RING >> 2, CSW = rco_csw(RING);
-    // per shift column sx: prefix sums of the column sums over the W pivot
-    // columns (H x (W+1), unsigned: differences of wrapped prefixes are exact
-    // because every window sum is < 2^32), warp totals, per-centre pivot
-    // statistics, then the image ring
-    unsigned *hs = reinterpret_cast<unsigned *>(rsm);
-    unsigned *wtot = hs + H * (W + 1);
-    int *cS = reinterpret_cast<int *>(wtot + H * 32);             // per centre: S_hat
-    float *cI = reinterpret_cast<float *>(cS + GXS);              // per centre: 1/Omega_hat
-    unsigned *ringw = reinterpret_cast<unsigned *>(cI + GXS);     // (W + 2R) columns x CSW words
+    const int nwarps = blockDim.x >> 5;
+    const RcoScan sg = rco_scan(Wmax, H, nwarps);
+    const RcoSmem L = rco_smem(H, Wmax, GXS, R, CSW, sg);
+    unsigned *hsc = rsm + L.hsc;                                  // 2 x H x RS scanned sums
+    unsigned *segt = rsm + L.segt;                                // 2 x H x NSEG segment totals
+    int *cS = reinterpret_cast<int *>(rsm + L.cst);               // per centre: S_hat
+    float *cI = reinterpret_cast<float *>(rsm + L.cst + GXS);     // per centre: 1/Omega_hat
+    unsigned *ringw = rsm + L.ring;                               // (W + 2R) columns x CSW words
     uint8_t *ring8 = reinterpret_cast<uint8_t *>(ringw);
     const int j = threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool active = j < W;
-    const int jc = cx0 + j;
     const int64_t q1 = q + 1;
     const long long mn = (long long)m * n;
     const int RW = W + 2 * R;                                     // ring columns used
+    const int addr_j = rco_addr(j, sg);
 
-    // rows [r0, r0 + cnt) into their ring slots, all loads of all rows in flight
-    auto load_rows = [&](int r0, int cnt) {
-        for (int c = threadIdx.x; c < cnt * RW; c += blockDim.x) {
-            const int k = c / RW, col = c - k * RW;
-            const int rr = r0 + k;
-            const int slot = (rr + R) % RING;
-            const int ry = min(max(rr, 0), p - 1);
-            const int xx = min(max(cx0 - R + col, 0), q - 1);
-            ring8[(col * CSW + (slot >> 2)) * 4 + (slot & 3)] = I[(int64_t)ry * q + xx];
+    // image rows [r0, r0 + cnt) into their ring slots: columns across the
+    // threads; a thread's rows are independent loads, issued together
+    auto ring_put = [&](int rr, int col, uint8_t v) {
+        const int slot = (rr + R) % RING;
+        ring8[(col * CSW + (slot >> 2)) * 4 + (slot & 3)] = v;
+    };
+    auto img_at = [&](int rr, int col) {
+        return I[(int64_t)min(max(rr, 0), p - 1) * q + min(max(cx0 - R + col, 0), q - 1)];
+    };
+    auto load_rows = [&](int r0, int cnt) {          // any cnt (the initial fill)
+        for (int col = threadIdx.x; col < RW; col += blockDim.x) {
+#pragma unroll 4
+            for (int k = 0; k < cnt; ++k) ring_put(r0 + k, col, img_at(r0 + k, col));
         }
     };
+    auto load_step = [&](int r0, int cnt) {          // cnt <= H rows of one slide batch
+        for (int col = threadIdx.x; col < RW; col += blockDim.x) {
+            uint8_t v[H];
+#pragma unroll
+            for (int k = 0; k < H; ++k) v[k] = k < cnt ? img_at(r0 + k, col) : (uint8_t)0;
+#pragma unroll
+            for (int k = 0; k < H; ++k)
+                if (k < cnt) ring_put(r0 + k, col, v[k]);
+        }
+    };
+    const int jc = cx0 + j;
 
     int r = group_centre_of(gy0, Ly, H);
     load_rows(r - R, m + 2 * R + 1);
-    __syncthreads();
-
     int cs[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) cs[s] = 0;
+    __syncthreads();
     if (active) {
-        for (int b0 = 0; b0 < m; b0 += BATCH)
-            rco_batch<H, false>(cs, P, q, jc, r + b0, min(BATCH, m - b0), ringw, j, CSW, RW4, RING);
+        for (int b0 = 0; b0 < m; b0 += BATCH) {
+            unsigned pw[KW];
+            rco_pcol<H>(pw, P, q, jc, r + b0, min(BATCH, m - b0));
+            rco_batch<H, false>(cs, pw, r + b0, ringw, j, CSW, RW4, RING);
+        }
     }
     unsigned long long local = 0;
+    int ebuf = 0;
+    const int ntask = ngx * H;
     for (int gy = gy0; gy < gy1; ++gy) {
         const int cy = group_centre_of(gy, Ly, H);
         const int steps = cy - r;            // 0 for the first row, <= H after
+        // pivot statistics of this row's centres, loads issued before the slide
+        long long Sp = 0, Qp = 0;
+        if ((int)threadIdx.x < ngx) {
+            const int cx = group_centre_of(gx0 + threadIdx.x, Lx, H);
+            Sp = ii_box(PS, q1, cy, cx, m, n);
+            Qp = ii_box(PQ, q1, cy, cx, m, n);
+        }
         if (steps > 0) {
-            // the batch needs rows up to r + steps - 1 + m + R; load the new ones
-            load_rows(r + m + R + 1, steps);
+            // this column's pivot rows entering and leaving the window, then
+            // the image rows up to r + steps - 1 + m + R the batch needs
+            unsigned pa[KW], pr[KW];
+            if (active) {
+                rco_pcol<H>(pa, P, q, jc, r + m, steps);
+                rco_pcol<H>(pr, P, q, jc, r, steps);
+            }
+            load_step(r + m + R + 1, steps);
             __syncthreads();
             if (active) {
-                rco_batch<H, false>(cs, P, q, jc, r + m, steps, ringw, j, CSW, RW4, RING);
-                rco_batch<H, true>(cs, P, q, jc, r, steps, ringw, j, CSW, RW4, RING);
+                rco_batch<H, false>(cs, pa, r + m, ringw, j, CSW, RW4, RING);
+                rco_batch<H, true>(cs, pr, r, ringw, j, CSW, RW4, RING);
             }
             r += steps;
             __syncthreads();   // nobody reads the dead rows the next batch overwrites
         }
-        // pivot statistics of this row's centres (exact sums, FP32 1/Omega_hat)
-        for (int i = threadIdx.x; i < gx1 - gx0; i += blockDim.x) {
-            const int cx = group_centre_of(gx0 + i, Lx, H);
-            const long long Sp = ii_box(PS, q1, cy, cx, m, n), Qp = ii_box(PQ, q1, cy, cx, m, n);
+        if ((int)threadIdx.x < ngx) {
             const long long var = mn * Qp - Sp * Sp;
-            cS[i] = (int)Sp;
-            cI[i] = var > 0 ? sqrtf((float)mn / (float)var) : 0.f;
+            cS[threadIdx.x] = (int)Sp;
+            cI[threadIdx.x] = var > 0 ? sqrtf((float)mn / (float)var) : 0.f;
         }
-        // emit centre row cy, one shift row (sy) at a time: block-wide prefix
-        // sums of the column sums turn each n-column window sum into one
-        // difference
+        // emit centre row cy, one shift row (sy) at a time
         const int gys = gy * H, gye = min(gys + H, Ly);
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 #pragma unroll
         for (int syi = 0; syi < H; ++syi) {
             const int my = cy + syi - R;
             if (my < gys || my >= gye) continue;   // uniform over the block
-            unsigned v[H];
-#pragma unroll
-            for (int sxi = 0; sxi < H; ++sxi) v[sxi] = active ? (unsigned)cs[syi * H + sxi] : 0u;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-                for (int sxi = 0; sxi < H; ++sxi) {
-                    const unsigned t = __shfl_up_sync(0xffffffffu, v[sxi], o);
-                    if (lane >= o) v[sxi] += t;
+            unsigned *hb = hsc + ebuf * H * sg.RS;
+            unsigned *sb = segt + ebuf * H * sg.NSEG;
+            ebuf ^= 1;
+            // this thread's first task (centre gxi, shift column sxi): its
+            // member's window sum and 1/Omega, loaded before the scan
+            int t_gxi = 0, t_sxi = 0, t_mx = -1;
+            int t_ws = 0;
+            float t_iw = 0.f;
+            if ((int)threadIdx.x < ntask) {
+                t_gxi = threadIdx.x / H;
+                t_sxi = threadIdx.x - t_gxi * H;
+                const int gx = gx0 + t_gxi;
+                const int mx = group_centre_of(gx, Lx, H) + t_sxi - R;
+                if (mx >= gx * H && mx < min(gx * H + H, Lx)) {
+                    t_mx = mx;
+                    const int64_t li = (int64_t)my * Lx + mx;
+                    t_ws = wsum[li];
+                    t_iw = inv_sigma[li];
                 }
             }
-            __syncthreads();   // previous readers of hs / wtot are done
-            if (lane == 31) {
-#pragma unroll
-                for (int sxi = 0; sxi < H; ++sxi) wtot[sxi * 32 + warp] = v[sxi];
-            }
-            __syncthreads();
-            if (warp == 0) {
-#pragma unroll
-                for (int sxi = 0; sxi < H; ++sxi) {
-                    const unsigned t = lane < nwarps ? wtot[sxi * 32 + lane] : 0u;
-                    unsigned inc = t;
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const unsigned u2 = __shfl_up_sync(0xffffffffu, inc, o);
-                        if (lane >= o) inc += u2;
-                    }
-                    wtot[sxi * 32 + lane] = inc - t;
-                }
-            }
-            __syncthreads();
             if (active) {
 #pragma unroll
-                for (int sxi = 0; sxi < H; ++sxi)
-                    hs[sxi * (W + 1) + j + 1] = v[sxi] + wtot[sxi * 32 + warp];
+                for (int sxi = 0; sxi < H; ++sxi) hb[sxi * sg.RS + addr_j] = (unsigned)cs[syi * H + sxi];
             }
-            if (threadIdx.x < H) hs[threadIdx.x * (W + 1)] = 0u;
             __syncthreads();
-            const int ntask = (gx1 - gx0) * H;
+            // segment scans: item = (shift column, segment)
+            for (int item = warp; item < H * sg.NSEG; item += nwarps) {
+                const int sxi = item / sg.NSEG, seg = item - sxi * sg.NSEG;
+                unsigned *lp = hb + sxi * sg.RS + (seg * 32 + lane) * sg.PLS;
+                const int c0 = seg * sg.SL + lane * sg.PL;
+                unsigned tot = 0u;
+                for (int i = 0; i < sg.PL; ++i) tot += (c0 + i < W) ? lp[i] : 0u;
+                unsigned inc = tot;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned u = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += u;
+                }
+                unsigned run = inc - tot;
+                for (int i = 0; i < sg.PL; ++i) {
+                    run += (c0 + i < W) ? lp[i] : 0u;
+                    lp[i] = run;   // inclusive prefix within the segment
+                }
+                if (lane == 31) sb[sxi * sg.NSEG + seg] = inc;
+            }
+            __syncthreads();
             for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
-                const int gxi = task / H, sxi = task % H;
-                const int gx = gx0 + gxi;
-                const int cx = group_centre_of(gx, Lx, H);
-                const int mx = cx + sxi - R;
-                const int gxs = gx * H, gxe = min(gxs + H, Lx);
-                if (mx < gxs || mx >= gxe) continue;
-                const unsigned *pre = hs + sxi * (W + 1) + (cx - cx0);
-                const long long X = (long long)(unsigned)(pre[n] - pre[0]);
-                const int64_t li = (int64_t)my * Lx + mx;
+                int gxi, sxi, mx, ws;
+                float iw;
+                if (task == (int)threadIdx.x) {
+                    gxi = t_gxi; sxi = t_sxi; mx = t_mx; ws = t_ws; iw = t_iw;
+                } else {
+                    gxi = task / H;
+                    sxi = task - gxi * H;
+                    const int gx = gx0 + gxi;
+                    mx = group_centre_of(gx, Lx, H) + sxi - R;
+                    if (mx < gx * H || mx >= min(gx * H + H, Lx)) mx = -1;
+                    ws = mx >= 0 ? wsum[(int64_t)my * Lx + mx] : 0;
+                    iw = mx >= 0 ? inv_sigma[(int64_t)my * Lx + mx] : 0.f;
+                }
+                if (mx < 0) continue;
+                // X = window sum over pivot columns [c1, c1 + n) of shift column sxi
+                const int c1 = group_centre_of(gx0 + gxi, Lx, H) - cx0, c2 = c1 + n - 1;
+                const unsigned *row = hb + sxi * sg.RS;
+                unsigned X = row[rco_addr(c2, sg)];
+                int s1 = 0;
+                if (c1 > 0) {
+                    X -= row[rco_addr(c1 - 1, sg)];
+                    s1 = (c1 - 1) >> sg.lgSL;
+                }
+                for (int sgi = s1; sgi < (c2 >> sg.lgSL); ++sgi) X += sb[sxi * sg.NSEG + sgi];
                 // rho = (mn X - S_hat S) / (mn Omega_hat Omega): exact integer
                 // numerator, FP32 finish (flat windows have 1/Omega = 0 -> 0)
-                const long long num = mn * X - (long long)cS[gxi] * (long long)wsum[li];
-                const float rho = ((float)num * inv_sigma[li]) * (cI[gxi] / (float)mn);
+                const long long num = mn * (long long)X - (long long)cS[gxi] * (long long)ws;
+                const float rho = ((float)num * iw) * (cI[gxi] / (float)mn);
                 if (rco) rco[(int64_t)my * Lx + mx] = rho;
                 if (rho < cut) ++local;
             }
@@ -365,7 +471,7 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
 
 struct RcoGeom {
     bool ok;
-    int GXS, Wmax, threads, strips, bands, GYB;
+    int GXS, Wmax, threads, strips;
     size_t smem;
 };
 
@@ -386,8 +492,9 @@ RcoGeom rco_geom(int p, int q, int m, int n) {
     const int csw = rco_csw(rco_ring(m, H));
     auto smem_for = [&](int gxs, int *wmax) {
         *wmax = (gxs - 1) * H + n;
-        return (size_t)H * (*wmax + 1 + 32) * sizeof(unsigned) + 2 * (size_t)gxs * sizeof(float) +
-               (size_t)(*wmax + 2 * R) * csw * sizeof(unsigned);
+        const int threads = ((*wmax + 31) / 32) * 32;
+        const RcoScan sg = rco_scan(*wmax, H, threads / 32);
+        return (size_t)rco_smem(H, *wmax, gxs, R, csw, sg).total * sizeof(unsigned);
     };
     // widest strip within the thread limit, narrowed until tall windows' ring fits
     g.GXS = std::min((MAXT - n) / H + 1, Gx);
@@ -399,12 +506,7 @@ RcoGeom rco_geom(int p, int q, int m, int n) {
     g.ok = g.smem <= kSmemMax;
     g.threads = ((g.Wmax + 31) / 32) * 32;
     g.strips = (Gx + g.GXS - 1) / g.GXS;
-    const int target = num_sms() * 2;
-    g.bands = (target + g.strips - 1) / g.strips;
-    if (g.bands > Gy) g.bands = Gy;
-    if (g.bands < 1) g.bands = 1;
-    g.GYB = (Gy + g.bands - 1) / g.bands;
-    g.bands = (Gy + g.GYB - 1) / g.GYB;
+    (void)Gy;
     return g;
 }
 
@@ -424,10 +526,24 @@ cudaError_t launch_rho_co_h(const uint8_t *P, const uint8_t *I, int p, int q, in
         if (e != cudaSuccess) return e;
         attr = smem;
     }
-    dim3 grid(g.strips, g.bands);
+    // one wave: strips x bands CTAs fill the SMs once (each CTA slides its
+    // band from one initial build, so fewer, taller bands pay it less often)
+    static int bps = 0;
+    if (bps == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, rho_co_kernel<H>, g.threads, smem) !=
+                cudaSuccess || bps < 1) {
+            cudaGetLastError();
+            bps = 1;
+        }
+    }
+    const int Gy = groups_along(Ly, H);
+    int bands = std::max(1, std::min(Gy, num_sms() * bps / g.strips));
+    const int GYB = (Gy + bands - 1) / bands;
+    bands = (Gy + GYB - 1) / GYB;
+    dim3 grid(g.strips, bands);
     LaunchScope ls_rho_co_kernel("rho_co_kernel", s);
     rho_co_kernel<H><<<grid, g.threads, smem, s>>>(P, I, p, q, m, n, Ly, Lx, wsum, inv_sigma, PS,
-                                                   PQ, g.GXS, g.GYB, cut, rco, count);
+                                                   PQ, g.GXS, GYB, cut, rco, count);
     return cudaGetLastError();
 }
 

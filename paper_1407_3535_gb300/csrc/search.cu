@@ -604,112 +604,132 @@ __device__ inline int gap_bucket(float gap, float lim) {
     return b < 0 ? 0 : (b >= kUbBuckets ? kUbBuckets - 1 : b);
 }
 
-// Scan 2 works on chunks of kChunkLoc consecutive locations (256 threads x
-// SC_PER each).  gap = max(0, tc.lo - co.hi, co.lo - tc.hi) is the smallest
-// angle between t and the location allowed by the two intervals, so
-// rho <= cos(gap).  It is computed with subtractions and maxima only, so the
-// two passes below obtain bit-identical values.  One launch serves a batch
-// of templates of one size: a thread loads its locations' auto-correlation
-// intervals and group indices once and tests them against every template.
+// Scan 2, group first.  gap = max(0, tc.lo - co.hi, co.lo - tc.hi) is the
+// smallest angle between t and a location allowed by the two intervals, so
+// rho <= cos(gap); a location survives iff gap <= theta_lim.  Per group the
+// union of its members' intervals (gco: lowest lo, highest hi) gives a
+// group test that every group holding a survivor passes (FP32 subtraction
+// is monotone), so members are read only for the (template, group) pairs
+// that pass.  Pass A histograms the survivors by bucket and appends them,
+// unordered, with their gap; pass B moves them into bucket order.  Gaps are
+// computed with subtractions and maxima only, so every pass that recomputes
+// one obtains the same value.
 constexpr int SC_PER = 16;
 constexpr int kChunkLoc = 256 * SC_PER;
-static_assert(kChunkLoc == kScan2ChunkLoc, "scan-2 chunk size");
 constexpr int kS2MaxT = kScan2MaxT;
-
-// Row/column of location i, advanced incrementally by `step` locations.
-struct LocCursor {
-    int y, x;
-    __device__ LocCursor(int64_t i, int Lx) {
-        const int ii = (int)i;
-        y = ii / Lx;
-        x = ii - y * Lx;
-    }
-    __device__ void advance(int step, int Lx) {
-        x += step;
-        while (x >= Lx) { x -= Lx; ++y; }
-    }
-};
-
-// This thread's SC_PER locations of chunk c: auto-correlation intervals and
-// group (centre) indices; gi = -1 past the end.
-__device__ inline void load_chunk(const float2 *__restrict__ theta_co, int64_t c, int64_t L,
-                                  int Lx, int Gx, float inv_h, float2 (&co)[SC_PER],
-                                  int (&gi)[SC_PER]) {
-    LocCursor cur(c * kChunkLoc + threadIdx.x, Lx);
-#pragma unroll
-    for (int k = 0; k < SC_PER; ++k) {
-        const int64_t i = c * kChunkLoc + k * 256 + threadIdx.x;
-        if (k) cur.advance(256, Lx);
-        gi[k] = -1;
-        co[k] = make_float2(0.f, 0.f);
-        if (i < L) {
-            // y / h, x / h by a rounded reciprocal: exact for y, x < 2^20 and h <= 9
-            const int gy = (int)(((float)cur.y + 0.5f) * inv_h);
-            const int gx = (int)(((float)cur.x + 0.5f) * inv_h);
-            gi[k] = gy * Gx + gx;
-            co[k] = theta_co[i];
-        }
-    }
-}
+constexpr int kPassGroups = 256;   // groups per pass-A tile (one per thread)
 
 __device__ inline float loc_gap(float2 t, float2 c) {
     return fmaxf(0.f, fmaxf(t.x - c.y, c.x - t.y));
 }
 
-// Pass 1: survivor histogram by bucket and survivor count of every chunk,
-// per template of the batch.
+// Group union intervals of the auto-correlation map (per template size).
+__global__ void group_co_kernel(const float2 *__restrict__ theta_co, int Ly, int Lx, int h,
+                                float2 *gco) {
+    const int Gy = groups_along(Ly, h), Gx = groups_along(Lx, h);
+    const int64_t G = (int64_t)Gy * Gx;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int gy = (int)(g / Gx), gx = (int)(g - (int64_t)gy * Gx);
+        const int y0 = gy * h, x0 = gx * h, y1 = min(y0 + h, Ly), x1 = min(x0 + h, Lx);
+        float lo = 4.f, hi = -4.f;
+        for (int y = y0; y < y1; ++y)
+            for (int x = x0; x < x1; ++x) {
+                const float2 c = theta_co[(int64_t)y * Lx + x];
+                lo = fminf(lo, c.x);
+                hi = fmaxf(hi, c.y);
+            }
+        gco[g] = make_float2(lo, hi);
+    }
+}
+
+// Pass A: group tests of a tile of groups against every template of the
+// batch, then the members of the passing pairs: bucket histogram and the
+// unordered survivor list (index in surv_eps as int, gap in surv_rho) of
+// each template.
 __global__ void __launch_bounds__(256)
-bound_hist_kernel(const Scan2Batch B, const float2 *__restrict__ theta_co, int Ly, int Lx,
-                  int h, float *ub_map, uint8_t *surv_map) {
+bound_pass_kernel(const Scan2Batch B, const float2 *__restrict__ gco,
+                  const float2 *__restrict__ theta_co, int Ly, int Lx, int h) {
     __shared__ int hist[kS2MaxT][kUbBuckets];
-    __shared__ int ccount[kS2MaxT];
     __shared__ float lims[kS2MaxT];
+    __shared__ unsigned short queue[kS2MaxT * kPassGroups];   // (t << 8) | group in tile
+    __shared__ int qn;
     const int T = B.T;
     for (int i = threadIdx.x; i < T * kUbBuckets; i += blockDim.x) hist[i / kUbBuckets][i % kUbBuckets] = 0;
     if ((int)threadIdx.x < T)
         lims[threadIdx.x] = B.st[threadIdx.x].flat ? -1.f : B.st[threadIdx.x].theta_lim;
-    const int Gx = groups_along(Lx, h);
-    const float inv_h = 1.f / (float)h;
-    const int64_t L = (int64_t)Ly * Lx;
-    const int64_t nchunks = (L + kChunkLoc - 1) / kChunkLoc;
+    const int Gy = groups_along(Ly, h), Gx = groups_along(Lx, h);
+    const int64_t G = (int64_t)Gy * Gx;
+    const int hh = h * h;
     const int lane = threadIdx.x & 31;
-    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        if ((int)threadIdx.x < T) ccount[threadIdx.x] = 0;
+    for (int64_t g0 = (int64_t)blockIdx.x * kPassGroups; g0 < G;
+         g0 += (int64_t)gridDim.x * kPassGroups) {
+        if (threadIdx.x == 0) qn = 0;
         __syncthreads();
-        float2 co[SC_PER];
-        int gi[SC_PER];
-        load_chunk(theta_co, c, L, Lx, Gx, inv_h, co, gi);
+        const int64_t g = g0 + threadIdx.x;
+        const float2 gc = g < G ? gco[g] : make_float2(4.f, -4.f);   // empty group: fails
         for (int t = 0; t < T; ++t) {
             const float lim = lims[t];
-            if (lim < 0.f) continue;                       // flat template (uniform)
-            const float2 *tct = B.tc + t * B.tc_stride;
-            int mine = 0;
-#pragma unroll 4
-            for (int k = 0; k < SC_PER; ++k) {
-                bool f = false;
-                int b = -1;
-                if (gi[k] >= 0) {
-                    const float gap = loc_gap(tct[gi[k]], co[k]);
-                    f = gap <= lim;
-                    if (ub_map || surv_map) {
-                        const int64_t i = c * kChunkLoc + k * 256 + threadIdx.x;
-                        if (ub_map) ub_map[i] = cosf(gap) + kCosMargin;
-                        if (surv_map) surv_map[i] = f ? 1 : 0;
-                    }
-                    if (f) b = gap_bucket(gap, lim);
-                }
-                if (__any_sync(0xffffffffu, f)) {
-                    const unsigned peers = __match_any_sync(0xffffffffu, b);
-                    if (f && lane == __ffs(peers) - 1) atomicAdd(&hist[t][b], __popc(peers));
-                }
-                mine += f ? 1 : 0;
+            bool pass = false;
+            if (lim >= 0.f && g < G) {
+                const float2 tv = B.tc[t * B.tc_stride + g];
+                pass = fmaxf(tv.x - gc.y, gc.x - tv.y) <= lim;
             }
-            for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
-            if (lane == 0 && mine) atomicAdd(&ccount[t], mine);
+            const unsigned msk = __ballot_sync(0xffffffffu, pass);
+            if (msk) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&qn, __popc(msk));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (pass)
+                    queue[base + __popc(msk & ((1u << lane) - 1u))] =
+                        (unsigned short)((t << 8) | threadIdx.x);
+            }
         }
         __syncthreads();
-        if ((int)threadIdx.x < T) B.chunk_cnt[threadIdx.x * B.nchunks + c] = ccount[threadIdx.x];
-        __syncthreads();
+        const int nitem = qn * hh;
+        for (int ib = 0; ib < nitem; ib += blockDim.x) {   // uniform trip count
+            const int item = ib + threadIdx.x;
+            bool f = false;
+            int t = 0, li = 0, b = 0;
+            float gap = 0.f;
+            if (item < nitem) {
+                const int e = item / hh, mem = item - e * hh;
+                const int code = queue[e];
+                t = code >> 8;
+                const int64_t gg = g0 + (code & 255);
+                const int gy = (int)(gg / Gx), gx = (int)(gg - (int64_t)gy * Gx);
+                const int my = gy * h + mem / h, mx = gx * h + mem % h;
+                if (my < Ly && mx < Lx) {
+                    li = my * Lx + mx;
+                    gap = loc_gap(B.tc[t * B.tc_stride + gg], theta_co[li]);
+                    f = gap <= lims[t];
+                    if (f) {
+                        b = gap_bucket(gap, lims[t]);
+                        atomicAdd(&hist[t][b], 1);
+                    }
+                }
+            }
+            // append to template t's unordered list, aggregated over the
+            // lanes of the warp that share t
+            const unsigned fm = __ballot_sync(0xffffffffu, f);
+            if (fm) {
+                const unsigned peers = __match_any_sync(0xffffffffu, f ? t : -1);
+                const int leader = __ffs(peers) - 1;
+                int base = 0;
+                if (f && lane == leader) base = atomicAdd(&B.ucnt[t], __popc(peers));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (f) {
+                    const int64_t pos = base + __popc(peers & ((1u << lane) - 1u));
+                    if (pos < B.scap) {
+                        reinterpret_cast<int *>(B.surv_eps)[t * B.scap + pos] = li;
+                        B.surv_rho[t * B.scap + pos] = gap;
+                    } else {
+                        atomicOr(&B.st[t].overflow, 1);
+                    }
+                }
+            }
+        }
+        __syncthreads();   // the queue is refilled
     }
     __syncthreads();
     for (int i = threadIdx.x; i < T * kUbBuckets; i += blockDim.x) {
@@ -742,67 +762,74 @@ __global__ void bucket_scan_kernel(const Scan2Batch B) {
     if (lane == 31) { st->n_surv = incl; st->n_surv_eff = incl; }
 }
 
-// Pass 2: scatter the survivors into their bucket ranges (bucket 0 = largest
-// bound first) together with their bound cos(gap) + margin.  Only (chunk,
-// template) pairs with survivors are revisited; their gaps are recomputed
-// bit-identically.  Each block counts a chunk per bucket in shared memory and
-// reserves every bucket's slice with one global atomic.
+// Pass B: the unordered survivors of template blockIdx.y into their bucket
+// ranges (bucket 0 = largest bound first) with their bound cos(gap) +
+// margin.  Each block counts a slice per bucket in shared memory and
+// reserves every bucket's part with one global atomic.
 __global__ void __launch_bounds__(256)
-bound_scatter_kernel(const Scan2Batch B, const float2 *__restrict__ theta_co, int Ly, int Lx,
-                     int h) {
+bound_sort_kernel(const Scan2Batch B) {
     __shared__ int cnt[kUbBuckets];
     __shared__ int basep[kUbBuckets];
-    const int T = B.T;
-    const int Gx = groups_along(Lx, h);
-    const float inv_h = 1.f / (float)h;
-    const int64_t L = (int64_t)Ly * Lx;
-    const int64_t nchunks = (L + kChunkLoc - 1) / kChunkLoc;
-    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        bool loaded = false;
-        float2 co[SC_PER];
-        int gi[SC_PER];
-        for (int t = 0; t < T; ++t) {
-            if (B.chunk_cnt[t * B.nchunks + c] == 0) continue;   // uniform over the block
-            TmplState *st = B.st + t;
-            if (!loaded) {
-                load_chunk(theta_co, c, L, Lx, Gx, inv_h, co, gi);
-                loaded = true;
-            }
-            const float lim = st->theta_lim;
-            const float2 *tct = B.tc + t * B.tc_stride;
-            int *bucket_cur = B.bucket_cur + t * kUbBuckets;
-            int *surv = B.surv + t * B.scap;
-            float *surv_ub = B.surv_ub + t * B.scap;
-            for (int b = threadIdx.x; b < kUbBuckets; b += blockDim.x) cnt[b] = 0;
-            __syncthreads();
-            float g[SC_PER];
-            int bk[SC_PER];
+    const int t = blockIdx.y;
+    TmplState *st = B.st + t;
+    if (st->flat) return;
+    const int64_t n = min((int64_t)B.ucnt[t], B.scap);
+    if ((int64_t)blockIdx.x * kChunkLoc >= n) return;   // uniform
+    const float lim = st->theta_lim;
+    const int *uidx = reinterpret_cast<const int *>(B.surv_eps) + t * B.scap;
+    const float *ugap = B.surv_rho + t * B.scap;
+    int *bucket_cur = B.bucket_cur + t * kUbBuckets;
+    int *surv = B.surv + t * B.scap;
+    float *surv_ub = B.surv_ub + t * B.scap;
+    for (int64_t base = (int64_t)blockIdx.x * kChunkLoc; base < n;
+         base += (int64_t)gridDim.x * kChunkLoc) {
+        for (int i = threadIdx.x; i < kUbBuckets; i += blockDim.x) cnt[i] = 0;
+        __syncthreads();
+        float g[SC_PER];
+        int ix[SC_PER], bk[SC_PER];
 #pragma unroll
-            for (int k = 0; k < SC_PER; ++k) {
-                g[k] = gi[k] >= 0 ? loc_gap(tct[gi[k]], co[k]) : 4.f;
-                bk[k] = g[k] <= lim ? gap_bucket(g[k], lim) : -1;
-                if (bk[k] >= 0) atomicAdd(&cnt[bk[k]], 1);
+        for (int k = 0; k < SC_PER; ++k) {
+            const int64_t e = base + k * 256 + threadIdx.x;
+            bk[k] = -1;
+            if (e < n) {
+                g[k] = ugap[e];
+                ix[k] = uidx[e];
+                bk[k] = gap_bucket(g[k], lim);
+                atomicAdd(&cnt[bk[k]], 1);
             }
-            __syncthreads();
-            for (int b = threadIdx.x; b < kUbBuckets; b += blockDim.x) {
-                const int n = cnt[b];
-                basep[b] = n ? atomicAdd(&bucket_cur[b], n) : 0;
-                cnt[b] = 0;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int k = 0; k < SC_PER; ++k) {
-                if (bk[k] < 0) continue;
-                const int pos = basep[bk[k]] + atomicAdd(&cnt[bk[k]], 1);
-                if (pos < B.scap) {
-                    surv[pos] = (int)(c * kChunkLoc + k * 256 + threadIdx.x);
-                    surv_ub[pos] = cosf(g[k]) + kCosMargin;
-                } else {
-                    atomicOr(&st->overflow, 1);
-                }
-            }
-            __syncthreads();
         }
+        __syncthreads();
+        for (int i = threadIdx.x; i < kUbBuckets; i += blockDim.x) {
+            const int c = cnt[i];
+            basep[i] = c ? atomicAdd(&bucket_cur[i], c) : 0;
+            cnt[i] = 0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < SC_PER; ++k) {
+            if (bk[k] < 0) continue;
+            const int pos = basep[bk[k]] + atomicAdd(&cnt[bk[k]], 1);
+            surv[pos] = ix[k];
+            surv_ub[pos] = cosf(g[k]) + kCosMargin;
+        }
+        __syncthreads();
+    }
+}
+
+// Full bound and survivor maps of one template (verification output).
+__global__ void bound_map_kernel(const Scan2Batch B, const float2 *__restrict__ theta_co, int Ly,
+                                 int Lx, int h, float *ub_map, uint8_t *surv_map) {
+    const TmplState *st = B.st;
+    if (st->flat) return;
+    const float lim = st->theta_lim;
+    const int Gx = groups_along(Lx, h);
+    const int64_t L = (int64_t)Ly * Lx;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / Lx), x = (int)(i - (int64_t)y * Lx);
+        const float gap = loc_gap(B.tc[(int64_t)(y / h) * Gx + x / h], theta_co[i]);
+        if (ub_map) ub_map[i] = cosf(gap) + kCosMargin;
+        if (surv_map) surv_map[i] = gap <= lim ? 1 : 0;
     }
 }
 
@@ -1242,19 +1269,19 @@ cudaError_t launch_threshold(TmplState *st, const double *cand_rho_topk, int T, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_bound_compact(const Scan2Batch &B, const float2 *theta_co, int Ly, int Lx,
-                                 int h, float *ub_map, uint8_t *surv_map, cudaStream_t s) {
+cudaError_t launch_bound_compact(const Scan2Batch &B, const float2 *theta_co, const float2 *gco,
+                                 int Ly, int Lx, int h, float *ub_map, uint8_t *surv_map,
+                                 cudaStream_t s) {
     if (B.T < 1 || B.T > kS2MaxT || ((ub_map || surv_map) && B.T != 1)) return cudaErrorInvalidValue;
-    const int64_t L = (int64_t)Ly * Lx;
-    const int64_t nchunks = (L + kChunkLoc - 1) / kChunkLoc;
-    if (nchunks > B.nchunks) return cudaErrorInvalidValue;
-    int grid = (int)std::min<int64_t>(nchunks, (int64_t)num_sms() * 8);
-    if (grid < 1) grid = 1;
+    const int64_t G = (int64_t)groups_along(Ly, h) * groups_along(Lx, h);
+    const int64_t tiles = (G + kPassGroups - 1) / kPassGroups;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)num_sms() * 8));
     cudaError_t e = cudaMemsetAsync(B.bucket_cnt, 0, (size_t)B.T * kUbBuckets * sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B.ucnt, 0, (size_t)B.T * sizeof(int), s);
     if (e != cudaSuccess) return e;
     {
-        LaunchScope ls("bound_hist_kernel", s);
-        bound_hist_kernel<<<grid, 256, 0, s>>>(B, theta_co, Ly, Lx, h, ub_map, surv_map);
+        LaunchScope ls("bound_pass_kernel", s);
+        bound_pass_kernel<<<grid, 256, 0, s>>>(B, gco, theta_co, Ly, Lx, h);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
@@ -1263,15 +1290,30 @@ cudaError_t launch_bound_compact(const Scan2Batch &B, const float2 *theta_co, in
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
-        LaunchScope ls("bound_scatter_kernel", s);
-        bound_scatter_kernel<<<grid, 256, 0, s>>>(B, theta_co, Ly, Lx, h);
+        LaunchScope ls("bound_sort_kernel", s);
+        bound_sort_kernel<<<dim3(std::max(1, num_sms() * 4 / B.T), B.T), 256, 0, s>>>(B);
     }
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ub_map || surv_map) {
+        const int64_t L = (int64_t)Ly * Lx;
+        LaunchScope ls("bound_map_kernel", s);
+        bound_map_kernel<<<grid_cap(L, 256, 8), 256, 0, s>>>(B, theta_co, Ly, Lx, h, ub_map, surv_map);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 cudaError_t launch_theta_co(const float *rho_co, int64_t L, float2 *theta_co, cudaStream_t s) {
     LaunchScope ls("theta_co_kernel", s);
     theta_co_kernel<<<grid_cap(L, 256, 16), 256, 0, s>>>(rho_co, L, theta_co);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_co(const float2 *theta_co, int Ly, int Lx, int h, float2 *gco,
+                            cudaStream_t s) {
+    const int64_t G = (int64_t)groups_along(Ly, h) * groups_along(Lx, h);
+    LaunchScope ls("group_co_kernel", s);
+    group_co_kernel<<<grid_cap(G, 256, 16), 256, 0, s>>>(theta_co, Ly, Lx, h, gco);
     return cudaGetLastError();
 }
 

@@ -95,6 +95,26 @@ def test_rho_co_map_and_retained_count(opta, h):
     assert abs(cnt - exp_cnt) <= near
 
 
+@pytest.mark.parametrize("h", [1, 3, 5, 7, 9])
+def test_rho_co_wide_strips(opta, h):
+    """A 400 x 1300 image with 12 x 100 windows: several CTA strips per group
+    row, emission rows split into several scanned segments, and a blurred
+    pivot (P != I)."""
+    img = synth.aerial_image(1300, 8, 40, seed=71)[:400].copy()
+    img[100:160, 300:700] = 17                   # flat windows
+    m, n = 12, 100
+    P = ref.quantise_pivot(ref.blur(img, np.full((7, 21), 1.0), 64))
+    Ly, Lx = 400 - m + 1, 1300 - n + 1
+    R = torch.empty(Ly * Lx, dtype=torch.float32, device="cuda")
+    cnt = opta.opta_dbg_rho_co(_cuda(P), _cuda(img), m, n, h, R, rho_cut=0.6)
+    got = R.cpu().numpy().reshape(Ly, Lx)
+    exp = ref.rho_co_map(P, img, m, n, h)
+    assert np.max(np.abs(got - exp)) <= 2e-6
+    exp_cnt = int(np.count_nonzero(exp < 0.6))
+    near = int(np.count_nonzero(np.abs(exp - 0.6) < 2e-6))
+    assert abs(cnt - exp_cnt) <= near
+
+
 def test_opta_decisions_match_oracle(opta):
     """The OptA level loop's choices (group side, per-block sigma) equal the
     oracle's on a case without decisions within rounding of a threshold."""
