@@ -216,8 +216,15 @@ opta_status egs_cost(opta_handle *H, SizeState *S, const uint8_t *P, const long 
                      cudaStream_t s) {
     const float cut = (float)std::sqrt(1.0 - H->prm.rho_th * H->prm.rho_th);
     CK(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), s));
-    CK(launch_rho_co(P, H->I8, H->p, H->q, S->m, S->n, h, S->wsum, S->inv_sigma, PS, PQ, cut, nullptr,
-                     dcount, s));
+    if (h == 1 && P == H->I8) {
+        // unblurred pivots, one location per group: every member is its own
+        // centre, rho_co = 1 except on flat windows (rho_co = 0 there), so
+        // the retained count is the number of flat windows
+        CK(launch_count_zero(S->inv_sigma, (int64_t)S->Ly * S->Lx, dcount, s));
+    } else {
+        CK(launch_rho_co(P, H->I8, H->p, H->q, S->m, S->n, h, S->wsum, S->inv_sigma, PS, PQ, cut,
+                         nullptr, dcount, s));
+    }
     unsigned long long c = 0;
     CK(cudaMemcpyAsync(&c, dcount, sizeof(c), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

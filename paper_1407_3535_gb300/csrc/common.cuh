@@ -114,6 +114,10 @@ cudaError_t launch_window_stats(const long long *IIS, const long long *IIQ, int 
                                 int m, int n, float *inv_sigma, float *efac128,
                                 cudaStream_t s, int *wsum = nullptr);
 
+// count += number of zeros in x[0, n) (count is not cleared).
+cudaError_t launch_count_zero(const float *x, int64_t n, unsigned long long *count,
+                              cudaStream_t s);
+
 // Convert a float32 image holding integers in [0,255] into uint8; bad = 1 otherwise.
 cudaError_t launch_ingest_f32(const float *src, int64_t ld, int p, int q, uint8_t *dst,
                               int *bad, cudaStream_t s);

@@ -157,32 +157,34 @@ struct RcoCfg {
 __host__ __device__ inline int rco_ring(int m, int H) { return (m + (H - 1) + 1 + H + 3) & ~3; }
 __host__ __device__ inline int rco_csw(int ring) { return (ring >> 2) | 1; }
 
-// Emission geometry: the column sums of one shift row are scanned in
-// segments of SL = 32 * PL columns (PL a power of two), one warp per (shift
-// column, segment); lane l holds PL consecutive columns at a padded stride
-// PLS (odd, or 1: conflict-free).  A window sum adds the totals of the
-// segments it spans to the difference of two in-segment prefixes.
+// Emission geometry (compile time, sized for MAXT columns): the column sums
+// of one shift row are scanned in NSEG segments of SL = 32 * PL columns (PL
+// a power of two), one warp per (shift column, segment); lane l holds PL
+// consecutive columns at a padded stride PLS (odd, or 1: conflict-free).  A
+// window sum adds the totals of the segments it spans to the difference of
+// two in-segment prefixes.
+template <int H>
 struct RcoScan {
-    int PL, lgPL, PLS, SL, lgSL, NSEG, RS;
+    static constexpr int MAXT = RcoCfg<H>::MAXT;
+    static constexpr int NW = MAXT / 32;                              // warps at most
+    // segments per row wanted (at least 2: at most 8 columns per lane for
+    // the widest rows, so the scan does not compete with the H*H slide
+    // accumulators for registers)
+    static constexpr int NSEG0 = NW / H > 2 ? NW / H : 2;
+    static constexpr int NEED = (MAXT + NSEG0 * 32 - 1) / (NSEG0 * 32);
+    static constexpr int PL = NEED <= 1 ? 1 : NEED <= 2 ? 2 : NEED <= 4 ? 4 : NEED <= 8 ? 8
+                              : NEED <= 16 ? 16 : 32;
+    static constexpr int LGPL = PL == 1 ? 0 : PL == 2 ? 1 : PL == 4 ? 2 : PL == 8 ? 3 : PL == 16 ? 4 : 5;
+    static constexpr int PLS = PL == 1 ? 1 : PL + 1;
+    static constexpr int SL = 32 * PL, LGSL = LGPL + 5;
+    static constexpr int NSEG = (MAXT + SL - 1) / SL;
+    static constexpr int RS = NSEG * 32 * PLS;                        // words per shift row
 };
-__host__ __device__ inline RcoScan rco_scan(int Wmax, int H, int nwarps) {
-    RcoScan g;
-    int nseg = nwarps / H;
-    if (nseg < 1) nseg = 1;
-    const int need = (Wmax + nseg * 32 - 1) / (nseg * 32);   // columns per lane
-    g.PL = 1;
-    g.lgPL = 0;
-    while (g.PL < need) { g.PL <<= 1; ++g.lgPL; }
-    g.PLS = g.PL == 1 ? 1 : g.PL + 1;
-    g.SL = 32 * g.PL;
-    g.lgSL = g.lgPL + 5;
-    g.NSEG = (Wmax + g.SL - 1) / g.SL;
-    g.RS = g.NSEG * 32 * g.PLS;
-    return g;
-}
-__device__ inline int rco_addr(int c, const RcoScan &g) {
-    const int seg = c >> g.lgSL, w = c & (g.SL - 1);
-    return (seg * 32 + (w >> g.lgPL)) * g.PLS + (w & (g.PL - 1));
+template <int H>
+__device__ __forceinline__ int rco_addr(int c) {
+    using G = RcoScan<H>;
+    const int seg = c >> G::LGSL, w = c & (G::SL - 1);
+    return (seg * 32 + (w >> G::LGPL)) * G::PLS + (w & (G::PL - 1));
 }
 
 // Pivot column jc, rows [prow, prow + cnt), packed 4 rows per word (zero
@@ -252,12 +254,13 @@ __device__ __forceinline__ void rco_batch(int (&cs)[H * H], const unsigned (&pw)
 struct RcoSmem {
     int hsc, segt, cst, ring, total;
 };
-__host__ __device__ inline RcoSmem rco_smem(int H, int Wmax, int GXS, int R, int CSW,
-                                            const RcoScan &g) {
+template <int H>
+__host__ __device__ inline RcoSmem rco_smem(int Wmax, int GXS, int CSW) {
+    constexpr int R = RcoCfg<H>::R;
     RcoSmem l;
     int o = 0;
-    l.hsc = o;  o += 2 * H * g.RS;
-    l.segt = o; o += 2 * H * g.NSEG;
+    l.hsc = o;  o += 2 * H * RcoScan<H>::RS;
+    l.segt = o; o += 2 * H * RcoScan<H>::NSEG;
     l.cst = o;  o += 2 * GXS;
     l.ring = o; o += (Wmax + 2 * R) * CSW;
     l.total = o;
@@ -286,12 +289,12 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
     const int Wmax = (GXS - 1) * H + n;
     const int RING = rco_ring(m, H), RW4 = RING >> 2, CSW = rco_csw(RING);
     const int nwarps = blockDim.x >> 5;
-    const RcoScan sg = rco_scan(Wmax, H, nwarps);
-    const RcoSmem L = rco_smem(H, Wmax, GXS, R, CSW, sg);
+    using SG = RcoScan<H>;
+    const RcoSmem L = rco_smem<H>(Wmax, GXS, CSW);
     unsigned *hsc = rsm + L.hsc;                                  // 2 x H x RS scanned sums
     unsigned *segt = rsm + L.segt;                                // 2 x H x NSEG segment totals
     int *cS = reinterpret_cast<int *>(rsm + L.cst);               // per centre: S_hat
-    float *cI = reinterpret_cast<float *>(rsm + L.cst + GXS);     // per centre: 1/Omega_hat
+    float *cI = reinterpret_cast<float *>(rsm + L.cst + GXS);     // per centre: 1/(mn Omega_hat)
     unsigned *ringw = rsm + L.ring;                               // (W + 2R) columns x CSW words
     uint8_t *ring8 = reinterpret_cast<uint8_t *>(ringw);
     const int j = threadIdx.x;
@@ -300,7 +303,7 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
     const int64_t q1 = q + 1;
     const long long mn = (long long)m * n;
     const int RW = W + 2 * R;                                     // ring columns used
-    const int addr_j = rco_addr(j, sg);
+    const int addr_j = rco_addr<H>(j);
 
     // image rows [r0, r0 + cnt) into their ring slots: columns across the
     // threads; a thread's rows are independent loads, issued together
@@ -375,7 +378,8 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
         if ((int)threadIdx.x < ngx) {
             const long long var = mn * Qp - Sp * Sp;
             cS[threadIdx.x] = (int)Sp;
-            cI[threadIdx.x] = var > 0 ? sqrtf((float)mn / (float)var) : 0.f;
+            // 1 / (mn Omega_hat) = sqrt(mn / var) / mn
+            cI[threadIdx.x] = var > 0 ? sqrtf((float)mn / (float)var) / (float)mn : 0.f;
         }
         // emit centre row cy, one shift row (sy) at a time
         const int gys = gy * H, gye = min(gys + H, Ly);
@@ -383,38 +387,22 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
         for (int syi = 0; syi < H; ++syi) {
             const int my = cy + syi - R;
             if (my < gys || my >= gye) continue;   // uniform over the block
-            unsigned *hb = hsc + ebuf * H * sg.RS;
-            unsigned *sb = segt + ebuf * H * sg.NSEG;
+            unsigned *hb = hsc + ebuf * (H * SG::RS);
+            unsigned *sb = segt + ebuf * (H * SG::NSEG);
             ebuf ^= 1;
-            // this thread's first task (centre gxi, shift column sxi): its
-            // member's window sum and 1/Omega, loaded before the scan
-            int t_gxi = 0, t_sxi = 0, t_mx = -1;
-            int t_ws = 0;
-            float t_iw = 0.f;
-            if ((int)threadIdx.x < ntask) {
-                t_gxi = threadIdx.x / H;
-                t_sxi = threadIdx.x - t_gxi * H;
-                const int gx = gx0 + t_gxi;
-                const int mx = group_centre_of(gx, Lx, H) + t_sxi - R;
-                if (mx >= gx * H && mx < min(gx * H + H, Lx)) {
-                    t_mx = mx;
-                    const int64_t li = (int64_t)my * Lx + mx;
-                    t_ws = wsum[li];
-                    t_iw = inv_sigma[li];
-                }
-            }
             if (active) {
 #pragma unroll
-                for (int sxi = 0; sxi < H; ++sxi) hb[sxi * sg.RS + addr_j] = (unsigned)cs[syi * H + sxi];
+                for (int sxi = 0; sxi < H; ++sxi) hb[sxi * SG::RS + addr_j] = (unsigned)cs[syi * H + sxi];
             }
             __syncthreads();
             // segment scans: item = (shift column, segment)
-            for (int item = warp; item < H * sg.NSEG; item += nwarps) {
-                const int sxi = item / sg.NSEG, seg = item - sxi * sg.NSEG;
-                unsigned *lp = hb + sxi * sg.RS + (seg * 32 + lane) * sg.PLS;
-                const int c0 = seg * sg.SL + lane * sg.PL;
+            for (int item = warp; item < H * SG::NSEG; item += nwarps) {
+                const int sxi = item / SG::NSEG, seg = item - sxi * SG::NSEG;
+                unsigned *lp = hb + sxi * SG::RS + (seg * 32 + lane) * SG::PLS;
+                const int c0 = seg * SG::SL + lane * SG::PL;
                 unsigned tot = 0u;
-                for (int i = 0; i < sg.PL; ++i) tot += (c0 + i < W) ? lp[i] : 0u;
+#pragma unroll
+                for (int i = 0; i < SG::PL; ++i) tot += (c0 + i < W) ? lp[i] : 0u;
                 unsigned inc = tot;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -422,43 +410,39 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
                     if (lane >= o) inc += u;
                 }
                 unsigned run = inc - tot;
-                for (int i = 0; i < sg.PL; ++i) {
+#pragma unroll
+                for (int i = 0; i < SG::PL; ++i) {
                     run += (c0 + i < W) ? lp[i] : 0u;
                     lp[i] = run;   // inclusive prefix within the segment
                 }
-                if (lane == 31) sb[sxi * sg.NSEG + seg] = inc;
+                if (lane == 31) sb[sxi * SG::NSEG + seg] = inc;
             }
             __syncthreads();
+            // task = (centre gxi, shift column sxi): X = window sum over pivot
+            // columns [c1, c1 + n); rho = (mn X - S_hat S) / (mn Omega_hat
+            // Omega): exact integer numerator, FP32 finish (flat windows have
+            // 1/Omega = 0 -> 0)
             for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
-                int gxi, sxi, mx, ws;
-                float iw;
-                if (task == (int)threadIdx.x) {
-                    gxi = t_gxi; sxi = t_sxi; mx = t_mx; ws = t_ws; iw = t_iw;
-                } else {
-                    gxi = task / H;
-                    sxi = task - gxi * H;
-                    const int gx = gx0 + gxi;
-                    mx = group_centre_of(gx, Lx, H) + sxi - R;
-                    if (mx < gx * H || mx >= min(gx * H + H, Lx)) mx = -1;
-                    ws = mx >= 0 ? wsum[(int64_t)my * Lx + mx] : 0;
-                    iw = mx >= 0 ? inv_sigma[(int64_t)my * Lx + mx] : 0.f;
-                }
-                if (mx < 0) continue;
-                // X = window sum over pivot columns [c1, c1 + n) of shift column sxi
-                const int c1 = group_centre_of(gx0 + gxi, Lx, H) - cx0, c2 = c1 + n - 1;
-                const unsigned *row = hb + sxi * sg.RS;
-                unsigned X = row[rco_addr(c2, sg)];
+                const int gxi = task / H, sxi = task - gxi * H;
+                const int gx = gx0 + gxi;
+                const int cxg = group_centre_of(gx, Lx, H);
+                const int mx = cxg + sxi - R;
+                if (mx < gx * H || mx >= min(gx * H + H, Lx)) continue;
+                const int64_t li = (int64_t)my * Lx + mx;
+                const int ws = wsum[li];
+                const float iw = inv_sigma[li];
+                const int c1 = cxg - cx0, c2 = c1 + n - 1;
+                const unsigned *row = hb + sxi * SG::RS;
+                unsigned X = row[rco_addr<H>(c2)];
                 int s1 = 0;
                 if (c1 > 0) {
-                    X -= row[rco_addr(c1 - 1, sg)];
-                    s1 = (c1 - 1) >> sg.lgSL;
+                    X -= row[rco_addr<H>(c1 - 1)];
+                    s1 = (c1 - 1) >> SG::LGSL;
                 }
-                for (int sgi = s1; sgi < (c2 >> sg.lgSL); ++sgi) X += sb[sxi * sg.NSEG + sgi];
-                // rho = (mn X - S_hat S) / (mn Omega_hat Omega): exact integer
-                // numerator, FP32 finish (flat windows have 1/Omega = 0 -> 0)
+                for (int sgi = s1; sgi < (c2 >> SG::LGSL); ++sgi) X += sb[sxi * SG::NSEG + sgi];
                 const long long num = mn * (long long)X - (long long)cS[gxi] * (long long)ws;
-                const float rho = ((float)num * iw) * (cI[gxi] / (float)mn);
-                if (rco) rco[(int64_t)my * Lx + mx] = rho;
+                const float rho = ((float)num * iw) * cI[gxi];
+                if (rco) rco[li] = rho;
                 if (rho < cut) ++local;
             }
         }
@@ -492,9 +476,7 @@ RcoGeom rco_geom(int p, int q, int m, int n) {
     const int csw = rco_csw(rco_ring(m, H));
     auto smem_for = [&](int gxs, int *wmax) {
         *wmax = (gxs - 1) * H + n;
-        const int threads = ((*wmax + 31) / 32) * 32;
-        const RcoScan sg = rco_scan(*wmax, H, threads / 32);
-        return (size_t)rco_smem(H, *wmax, gxs, R, csw, sg).total * sizeof(unsigned);
+        return (size_t)rco_smem<H>(*wmax, gxs, csw).total * sizeof(unsigned);
     };
     // widest strip within the thread limit, narrowed until tall windows' ring fits
     g.GXS = std::min((MAXT - n) / H + 1, Gx);

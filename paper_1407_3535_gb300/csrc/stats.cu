@@ -115,6 +115,17 @@ ii_cols_kernel(int p, int q, long long *o0, long long *o1, long long *o2) {
     }
 }
 
+// Number of zero entries (flat windows: 1/Omega = 0) of x[0, n).
+__global__ void count_zero_kernel(const float *__restrict__ x, int64_t n,
+                                  unsigned long long *count) {
+    unsigned long long c = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        c += x[i] == 0.f ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
 __global__ void window_stats_kernel(const long long *__restrict__ IIS,
                                     const long long *__restrict__ IIQ, int q, int Ly, int Lx,
                                     int m, int n, float *inv_sigma, float *efac128, int *wsum) {
@@ -204,6 +215,13 @@ cudaError_t launch_integrals(const uint8_t *A, const uint8_t *B, int p, int q, l
         ii_cols_kernel<<<(int)((q1 + 31) / 32), dim3(32, 32), 0, s>>>(p, q, o0, o1,
                                                                      (B ? o2 : nullptr));
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_zero(const float *x, int64_t n, unsigned long long *count,
+                              cudaStream_t s) {
+    LaunchScope ls("count_zero_kernel", s);
+    count_zero_kernel<<<grid_for(n, 256), 256, 0, s>>>(x, n, count);
     return cudaGetLastError();
 }
 
