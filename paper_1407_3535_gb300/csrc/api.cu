@@ -85,6 +85,7 @@ struct opta_handle {
     DevMem mem;
     uint8_t *I8 = nullptr;
     long long *IIS = nullptr, *IIQ = nullptr;
+    unsigned *IIS32 = nullptr, *IIQ32 = nullptr;   // the same modulo 2^32 (level-0 pivots)
     std::map<std::pair<int, int>, SizeState *> sizes;
     // search scratch (grown on demand)
     size_t capL = 0, capG = 0, capT = 0, capN = 0;
@@ -204,15 +205,16 @@ bool valid_template(const opta_template *t, int p, int q) {
 // ---------------------------------------------------------------------------
 struct PrepScratch {
     uint8_t *Pcur = nullptr, *Pacc = nullptr;
-    long long *PS = nullptr, *PQ = nullptr, *PX = nullptr;
+    unsigned *PS = nullptr, *PQ = nullptr, *PX = nullptr;
+    unsigned *PSa = nullptr, *PQa = nullptr;   // integrals of the accepted pivot (Pacc)
     int *fail = nullptr;
     uint8_t *lvl = nullptr;
     unsigned long long *count = nullptr;
     size_t nII = 0;
 };
 
-opta_status egs_cost(opta_handle *H, SizeState *S, const uint8_t *P, const long long *PS,
-                     const long long *PQ, int h, unsigned long long *dcount, long long *cost,
+opta_status egs_cost(opta_handle *H, SizeState *S, const uint8_t *P, const unsigned *PS,
+                     const unsigned *PQ, int h, unsigned long long *dcount, long long *cost,
                      cudaStream_t s) {
     const float cut = (float)std::sqrt(1.0 - H->prm.rho_th * H->prm.rho_th);
     CK(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), s));
@@ -242,8 +244,8 @@ int h_limit(int p, int q, int m, int n, int hmax) {
 }
 
 // Algorithm 2: grow h by 2 while the cost drops by more than xi of the last.
-opta_status egs(opta_handle *H, SizeState *S, const uint8_t *P, const long long *PS,
-                const long long *PQ, int h_start, unsigned long long *dcount, int *h_out,
+opta_status egs(opta_handle *H, SizeState *S, const uint8_t *P, const unsigned *PS,
+                const unsigned *PQ, int h_start, unsigned long long *dcount, int *h_out,
                 long long *c_out, cudaStream_t s) {
     const int hmax = h_limit(H->p, H->q, S->m, S->n, H->prm.h_max);
     int h = std::min(h_start, hmax);
@@ -290,6 +292,8 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
         if (W.PS) cudaFree(W.PS);
         if (W.PQ) cudaFree(W.PQ);
         if (W.PX) cudaFree(W.PX);
+        if (W.PSa) cudaFree(W.PSa);
+        if (W.PQa) cudaFree(W.PQa);
         if (W.fail) cudaFree(W.fail);
         if (W.lvl) cudaFree(W.lvl);
         if (W.count) cudaFree(W.count);
@@ -321,16 +325,18 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     if (prm.fixed_h > 0) {
         h_best = std::min(prm.fixed_h, h_limit(p, q, m, n, 9));
     } else {
-        PTRY(egs(H, S, H->I8, H->IIS, H->IIQ, 1, W.count, &h_best, &c_best, s));
+        PTRY(egs(H, S, H->I8, H->IIS32, H->IIQ32, 1, W.count, &h_best, &c_best, s));
     }
     int level_best = 0;
     if (prm.blur && prm.n_levels > 0 && prm.fixed_h == 0) {
         const size_t nII = (size_t)(p + 1) * (q + 1);
         PCK(cudaMalloc(&W.Pcur, (size_t)p * q));
         PCK(cudaMalloc(&W.Pacc, (size_t)p * q));
-        PCK(cudaMalloc(&W.PS, nII * sizeof(long long)));
-        PCK(cudaMalloc(&W.PQ, nII * sizeof(long long)));
-        PCK(cudaMalloc(&W.PX, nII * sizeof(long long)));
+        PCK(cudaMalloc(&W.PS, nII * sizeof(unsigned)));
+        PCK(cudaMalloc(&W.PQ, nII * sizeof(unsigned)));
+        PCK(cudaMalloc(&W.PX, nII * sizeof(unsigned)));
+        PCK(cudaMalloc(&W.PSa, nII * sizeof(unsigned)));
+        PCK(cudaMalloc(&W.PQa, nII * sizeof(unsigned)));
         PCK(cudaMalloc(&W.fail, (size_t)bp * bq * sizeof(int)));
         PCK(cudaMalloc(&W.lvl, (size_t)bp * bq));
         const float lam = (float)lambda_of(prm.rho_th, prm.rho_max);
@@ -344,7 +350,7 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
             std::vector<uint8_t> cand(cur_level);
             for (size_t b = 0; b < cand.size(); ++b) if (!frozen[b]) cand[b] = (uint8_t)k;
             PTRY(blur_to(H, W, cand, W.Pcur, s));
-            PCK(launch_integrals(W.Pcur, H->I8, p, q, W.PS, W.PQ, W.PX, s));
+            PCK(launch_integrals32(W.Pcur, H->I8, p, q, W.PS, W.PQ, W.PX, s));
             PCK(cudaMemsetAsync(W.fail, 0, (size_t)bp * bq * sizeof(int), s));
             PCK(launch_blur_corr(S->wsum, S->inv_sigma, W.PS, W.PQ, W.PX, p, q, m, n, lam, block,
                                  W.fail, nullptr, s));
@@ -358,7 +364,7 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
             }
             if (any) {
                 PTRY(blur_to(H, W, cand, W.Pcur, s));
-                PCK(launch_integrals(W.Pcur, nullptr, p, q, W.PS, W.PQ, nullptr, s));
+                PCK(launch_integrals32(W.Pcur, nullptr, p, q, W.PS, W.PQ, nullptr, s));
             }
             int hk = 0;
             long long ck = 0;
@@ -370,6 +376,8 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
                 c_best = ck;
                 level_best = k;
                 std::swap(W.Pcur, W.Pacc);
+                std::swap(W.PS, W.PSa);
+                std::swap(W.PQ, W.PQa);
                 best_is_image = false;
             } else {
                 break;
@@ -384,19 +392,19 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     S->Gy = groups_along(S->Ly, S->h);
     S->Gx = groups_along(S->Lx, S->h);
     const int64_t G = (int64_t)S->Gy * S->Gx;
-    const long long *PS = H->IIS, *PQ = H->IIQ;
+    const unsigned *PS = H->IIS32, *PQ = H->IIQ32;
     if (best_is_image) {
         S->P = H->I8;
         S->P_owned = false;
     } else {
-        // the accepted pivot moves into the size state; its integrals are recomputed
+        // the accepted pivot moves into the size state; its integrals were
+        // kept when it was accepted
         H->mem.bytes += (size_t)p * q;
         S->P = W.Pacc;
         S->P_owned = true;
         W.Pacc = nullptr;
-        PCK(launch_integrals(S->P, nullptr, p, q, W.PS, W.PQ, nullptr, s));
-        PS = W.PS;
-        PQ = W.PQ;
+        PS = W.PSa;
+        PQ = W.PQa;
     }
     PTRY(H->mem.alloc(&S->rho_co, L));
     PTRY(H->mem.alloc(&S->theta_co, L));
@@ -732,7 +740,7 @@ opta_status optA_destroy(opta_handle *h) {
         if (S->P_owned) cudaFree(S->P);
         delete S;
     }
-    void *ptrs[] = {h->I8, h->IIS, h->IIQ, h->rho_tc, h->tc, h->surv, h->surv_rho, h->surv_eps,
+    void *ptrs[] = {h->I8, h->IIS, h->IIQ, h->IIS32, h->IIQ32, h->rho_tc, h->tc, h->surv, h->surv_rho, h->surv_eps,
                     h->surv_ub, h->ucnt, h->bucket_cnt, h->bucket_cur, h->Bmma, h->dev_err,
                     h->cand_topk, h->cand_rho_topk, h->tin,
                     h->cand, h->cand_rho, h->topk_v, h->topk_i, h->tf, h->tstage, h->td,
@@ -770,7 +778,10 @@ opta_status optA_prepare(const opta_image *img, const opta_params *prm, const in
     const size_t nII = (size_t)(p + 1) * (q + 1);
     if ((st = H->mem.alloc(&H->IIS, nII)) != OPTA_OK) return fail(st);
     if ((st = H->mem.alloc(&H->IIQ, nII)) != OPTA_OK) return fail(st);
+    if ((st = H->mem.alloc(&H->IIS32, nII)) != OPTA_OK) return fail(st);
+    if ((st = H->mem.alloc(&H->IIQ32, nII)) != OPTA_OK) return fail(st);
     cudaError_t e = launch_integrals(H->I8, nullptr, p, q, H->IIS, H->IIQ, nullptr, s);
+    if (e == cudaSuccess) e = launch_integrals32(H->I8, nullptr, p, q, H->IIS32, H->IIQ32, nullptr, s);
     if (e != cudaSuccess) return fail(map_err(e));
     if ((st = setup_tables(H)) != OPTA_OK) return fail(st);
     for (int i = 0; i < n_sizes; ++i)
@@ -1058,18 +1069,21 @@ opta_status opta_dbg_blur_corr(const uint8_t *P_dev, const uint8_t *I_dev, int32
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t nII = (size_t)(p + 1) * (q + 1);
     const size_t L = (size_t)(p - m + 1) * (q - n + 1);
-    long long *b[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    long long *b[2] = {nullptr, nullptr};
+    unsigned *u[3] = {nullptr, nullptr, nullptr};
     float *inv = nullptr;
     int *ws = nullptr;
     for (auto &x : b) CK(cudaMallocAsync(&x, nII * sizeof(long long), s));
+    for (auto &x : u) CK(cudaMallocAsync(&x, nII * sizeof(unsigned), s));
     CK(cudaMallocAsync(&inv, L * sizeof(float), s));
     CK(cudaMallocAsync(&ws, L * sizeof(int), s));
     cudaError_t e = launch_integrals(I_dev, nullptr, p, q, b[0], b[1], nullptr, s);
     if (e == cudaSuccess) e = launch_window_stats(b[0], b[1], p, q, m, n, inv, nullptr, s, ws);
-    if (e == cudaSuccess) e = launch_integrals(P_dev, I_dev, p, q, b[2], b[3], b[4], s);
+    if (e == cudaSuccess) e = launch_integrals32(P_dev, I_dev, p, q, u[0], u[1], u[2], s);
     if (e == cudaSuccess)
-        e = launch_blur_corr(ws, inv, b[2], b[3], b[4], p, q, m, n, 0.f, 64, nullptr, R_dev, s);
+        e = launch_blur_corr(ws, inv, u[0], u[1], u[2], p, q, m, n, 0.f, 64, nullptr, R_dev, s);
     for (auto &x : b) cudaFreeAsync(x, s);
+    for (auto &x : u) cudaFreeAsync(x, s);
     cudaFreeAsync(inv, s);
     cudaFreeAsync(ws, s);
     cudaError_t e2 = cudaStreamSynchronize(s);
@@ -1086,25 +1100,28 @@ opta_status opta_dbg_rho_co(const uint8_t *P_dev, const uint8_t *I_dev, int32_t 
     if (h < 1 || h > 9 || h % 2 == 0 || h_limit(p, q, m, n, h) != h) return OPTA_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t nII = (size_t)(p + 1) * (q + 1);
-    long long *b[4] = {nullptr, nullptr, nullptr, nullptr};
+    long long *b[2] = {nullptr, nullptr};
+    unsigned *u[2] = {nullptr, nullptr};
     float *inv = nullptr;
     int *ws = nullptr;
     unsigned long long *cnt = nullptr;
     const size_t L = (size_t)(p - m + 1) * (q - n + 1);
     for (auto &x : b) CK(cudaMallocAsync(&x, nII * sizeof(long long), s));
+    for (auto &x : u) CK(cudaMallocAsync(&x, nII * sizeof(unsigned), s));
     CK(cudaMallocAsync(&inv, L * sizeof(float), s));
     CK(cudaMallocAsync(&ws, L * sizeof(int), s));
     CK(cudaMallocAsync(&cnt, sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
     cudaError_t e = launch_integrals(I_dev, nullptr, p, q, b[0], b[1], nullptr, s);
     if (e == cudaSuccess) e = launch_window_stats(b[0], b[1], p, q, m, n, inv, nullptr, s, ws);
-    if (e == cudaSuccess) e = launch_integrals(P_dev, nullptr, p, q, b[2], b[3], nullptr, s);
+    if (e == cudaSuccess) e = launch_integrals32(P_dev, nullptr, p, q, u[0], u[1], nullptr, s);
     if (e == cudaSuccess)
-        e = launch_rho_co(P_dev, I_dev, p, q, m, n, h, ws, inv, b[2], b[3], (float)rho_cut,
+        e = launch_rho_co(P_dev, I_dev, p, q, m, n, h, ws, inv, u[0], u[1], (float)rho_cut,
                           rco_dev, cnt, s);
     unsigned long long hc = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s);
     for (auto &x : b) cudaFreeAsync(x, s);
+    for (auto &x : u) cudaFreeAsync(x, s);
     cudaFreeAsync(inv, s);
     cudaFreeAsync(ws, s);
     cudaFreeAsync(cnt, s);

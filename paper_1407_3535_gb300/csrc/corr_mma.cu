@@ -1,7 +1,7 @@
 // Scan 1 (Section 6) on the 5th-generation tensor cores: rho(t, pivot block)
 // at every group centre for a batch of same-size templates at once.
 //
-// For one centre row cy and 128 consecutive centres along x (spacing h):
+// For a centre row cy and 128 consecutive centres along x (spacing h):
 //
 //   D[i][j] = sum_{u<m} sum_{v<Kp} A_u[i][v] * B_u[j][v]
 //   A_u[i][v] = P(cy + u, cx0 + h*i + v) - 128            (bf16, exact)
@@ -18,8 +18,14 @@
 // sits at byte (h*a + c)*128 + 16*b + 2*d, i.e. a descriptor with leading
 // (K) byte offset 128 and stride (M) byte offset 128*h; core matrices
 // overlap, which costs nothing.  B_u arrives by one bulk copy from a buffer
-// already laid out as core matrices.  Two stages (A and B) overlap the build
-// of the next template row with the MMAs of the current one.
+// already laid out as core matrices.
+//
+// A CTA takes RC centre rows cy_k (k < RC, about h apart) of the same 128
+// centres and walks the pivot rows r: the Hankel operand of row r is built
+// once and feeds every accumulator k with u = r - cy_k in [0, m), against
+// template row u (RC tiles of B per pivot row, accumulator k at TMEM column
+// k * N).  Two stages (A and the B tiles) overlap the build of the next
+// pivot row with the MMAs of the current one.
 //
 // Error bound of the numerator: the hi/lo split represents each template
 // value to within 2^-16 relative; FP32 accumulation in TMEM is bounded by
@@ -44,6 +50,7 @@ struct CorrMmaArgs {
     const __nv_bfloat16 *B;    // [m][Kp/8][N/8][8][8]
     int m, n, Kp, N;
     int h, Ly, Lx, Gx, Gx_u;   // Gx_u: leading groups whose centres are uniform (cx0 + h*i)
+    int Gy, RC;                // group rows; centre rows per CTA (1, 2 or 4)
     int T;                     // templates (planes 2t, 2t+1)
     const float *c_inv_sigma;  // per group
     const float *c_efac;       // per group: ||P - 128|| / sigma_hat
@@ -59,7 +66,10 @@ __device__ inline float eps_mma(int steps, float efac) {
     return ((float)(4 * steps + 16) * kU32 + 1.55e-5f) * 1.01f * efac + 8.f * kU32;
 }
 
-__global__ void __launch_bounds__(128, 1) corr_mma_kernel(const CorrMmaArgs a) {
+constexpr int kMmaThreads = 256;
+constexpr int kMaxRC = 4;
+
+__global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaArgs a) {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t *b_full = reinterpret_cast<uint64_t *>(smem);   // [2]
     uint64_t *mma_done = b_full + 2;                         // [2]
@@ -67,20 +77,21 @@ __global__ void __launch_bounds__(128, 1) corr_mma_kernel(const CorrMmaArgs a) {
     const int WA = 15 * a.h + a.Kp / 8;
     const uint32_t abytes = (uint32_t)WA * 128u;
     const uint32_t bbytes = (uint32_t)a.N * a.Kp * 2u;
-    uint8_t *Abuf[2], *Bbuf[2];
-    Abuf[0] = smem + 1024;
-    Abuf[1] = Abuf[0] + round_up(abytes, 1024);
-    Bbuf[0] = Abuf[1] + round_up(abytes, 1024);
-    Bbuf[1] = Bbuf[0] + round_up(bbytes, 1024);
+    const uint32_t astride = round_up(abytes, 1024), bstride = round_up(bbytes, 1024);
+    uint8_t *Abase = smem + 1024;
+    uint8_t *Bbase = Abase + 2 * astride;                    // [2][RC] tiles
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int gy = blockIdx.y;
+    const int gy0 = blockIdx.y * a.RC;
+    const int nrow = min(a.RC, a.Gy - gy0);
     const int gx0 = blockIdx.x * kMmaM;
-    const int cy = group_centre_of(gy, a.Ly, a.h);
     const int cx0 = group_centre_of(gx0, a.Lx, a.h);
+    int cyk[kMaxRC];
+#pragma unroll
+    for (int k = 0; k < kMaxRC; ++k) cyk[k] = k < nrow ? group_centre_of(gy0 + k, a.Ly, a.h) : 0;
 
     uint32_t ncols = 32;
-    while ((int)ncols < a.N) ncols <<= 1;
+    while ((int)ncols < a.RC * a.N) ncols <<= 1;
     if (tid == 0) {
         tc5::mbar_init(&b_full[0], 1);
         tc5::mbar_init(&b_full[1], 1);
@@ -99,21 +110,37 @@ __global__ void __launch_bounds__(128, 1) corr_mma_kernel(const CorrMmaArgs a) {
     const uint32_t idesc = tc5::idesc_bf16_f32(kMmaM, a.N);
 
     bool ok = true;
-    int last_issue = -1;          // last template row whose copy/MMAs thread 0 issued
+    int last_issue = -1;          // last step whose copies/MMAs thread 0 issued
     bool last_committed = false;
-    for (int u = 0; u < a.m; ++u) {
-        const int s = u & 1;
-        if (u >= 2 && !tc5::mbar_wait(&mma_done[s], ((u - 2) >> 1) & 1, kWaitNs)) ok = false;
+    int step = 0;
+    const int r_end = group_centre_of(gy0 + nrow - 1, a.Ly, a.h) + a.m;
+    for (int r = cyk[0]; r < r_end; ++r) {
+        // template row u_k of accumulator k at this pivot row (-1: none)
+        int uk[kMaxRC];
+        int nvalid = 0;
+#pragma unroll
+        for (int k = 0; k < kMaxRC; ++k) {
+            const int u = r - cyk[k];
+            uk[k] = (k < nrow && u >= 0 && u < a.m) ? u : -1;
+            nvalid += uk[k] >= 0 ? 1 : 0;
+        }
+        if (nvalid == 0) continue;                 // a gap between centre rows wider than m
+        const int s = step & 1;
+        if (step >= 2 && !tc5::mbar_wait(&mma_done[s], ((step - 2) >> 1) & 1, kWaitNs)) ok = false;
         if (!__syncthreads_and(ok)) { ok = false; break; }
         if (tid == 0) {
-            tc5::mbar_arrive_expect_tx(&b_full[s], bbytes);
-            tc5::bulk_g2s(Bbuf[s], a.B + (size_t)u * a.N * a.Kp, bbytes, &b_full[s]);
-            last_issue = u;
+            tc5::mbar_arrive_expect_tx(&b_full[s], (uint32_t)nvalid * bbytes);
+#pragma unroll
+            for (int k = 0; k < kMaxRC; ++k)
+                if (uk[k] >= 0)
+                    tc5::bulk_g2s(Bbase + (s * a.RC + k) * bstride, a.B + (size_t)uk[k] * a.N * a.Kp,
+                                  bbytes, &b_full[s]);
+            last_issue = step;
             last_committed = false;
         }
-        // build A_u: segment w, copy b = pixels cx0 + h*b + 8w .. +7 of row cy + u
-        const uint8_t *row = a.V + (size_t)(cy + u) * a.q;
-        uint8_t *Ab = Abuf[s];
+        // build A_r: segment w, copy b = pixels cx0 + h*b + 8w .. +7 of row r
+        const uint8_t *row = a.V + (size_t)r * a.q;
+        uint8_t *Ab = Abase + s * astride;
         for (int j = tid; j < WA * 8; j += blockDim.x) {
             const int w = j >> 3, b = j & 7;
             const int x = cx0 + a.h * b + 8 * w;
@@ -130,23 +157,29 @@ __global__ void __launch_bounds__(128, 1) corr_mma_kernel(const CorrMmaArgs a) {
         tc5::fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {
-            if (!tc5::mbar_wait(&b_full[s], (u >> 1) & 1, kWaitNs)) {
+            if (!tc5::mbar_wait(&b_full[s], (step >> 1) & 1, kWaitNs)) {
                 ok = false;
             } else {
                 tc5::tc_fence_after();
-                const uint32_t abase = tc5::smem_u32(Ab), bbase = tc5::smem_u32(Bbuf[s]);
+                const uint32_t abase = tc5::smem_u32(Ab);
                 const uint32_t blbo = (uint32_t)(a.N / 8) * 128u;
-                for (int kk = 0; kk < a.Kp / 16; ++kk) {
-                    const uint64_t ad = tc5::smem_desc(abase + kk * 256, 128, 128u * a.h);
-                    const uint64_t bd = tc5::smem_desc(bbase + kk * 2 * blbo, blbo, 128);
-                    tc5::mma_bf16(tmem, ad, bd, idesc, (u > 0 || kk > 0));
+#pragma unroll
+                for (int k = 0; k < kMaxRC; ++k) {
+                    if (uk[k] < 0) continue;
+                    const uint32_t bbase = tc5::smem_u32(Bbase + (s * a.RC + k) * bstride);
+                    for (int kk = 0; kk < a.Kp / 16; ++kk) {
+                        const uint64_t ad = tc5::smem_desc(abase + kk * 256, 128, 128u * a.h);
+                        const uint64_t bd = tc5::smem_desc(bbase + kk * 2 * blbo, blbo, 128);
+                        tc5::mma_bf16(tmem + (uint32_t)(k * a.N), ad, bd, idesc, (uk[k] > 0 || kk > 0));
+                    }
                 }
                 tc5::mma_commit(&mma_done[s]);
                 last_committed = true;
             }
         }
+        ++step;
     }
-    // drain: thread 0 waits (bounded) for its last copy and last MMA batch
+    // drain: thread 0 waits (bounded) for its last copies and last MMA batch
     if (tid == 0 && last_issue >= 0) {
         const int s = last_issue & 1;
         const uint32_t ph = (last_issue >> 1) & 1;
@@ -162,25 +195,30 @@ __global__ void __launch_bounds__(128, 1) corr_mma_kernel(const CorrMmaArgs a) {
     tc5::tc_fence_after();
 
     if (ok) {
-        const int i = warp * 32 + lane;                 // TMEM lane = accumulator row
+        // warp w reads TMEM lanes 32 * (w % 4) .. + 31; warps 0-3 take the
+        // even accumulators, warps 4-7 the odd ones
+        const int wl = warp & 3;
+        const int i = wl * 32 + lane;                   // TMEM lane = accumulator row
         const int gx = gx0 + i;
         const bool valid = gx < a.Gx_u;
-        const int64_t g = (int64_t)gy * a.Gx + gx;
-        float cis = 0.f, cef = 0.f;
-        if (valid) { cis = a.c_inv_sigma[g]; cef = a.c_efac[g]; }
         const int steps = a.m * (a.Kp / 16);
-        for (int c0 = 0; c0 < a.N; c0 += 8) {
-            float v[8];
-            tc5::tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        for (int k = warp >> 2; k < nrow; k += 2) {
+            const int64_t g = (int64_t)(gy0 + k) * a.Gx + gx;
+            float cis = 0.f, cef = 0.f;
+            if (valid) { cis = a.c_inv_sigma[g]; cef = a.c_efac[g]; }
+            for (int c0 = 0; c0 < a.N; c0 += 8) {
+                float v[8];
+                tc5::tmem_ld8(tmem + ((uint32_t)(wl * 32) << 16) + (uint32_t)(k * a.N + c0), v);
 #pragma unroll
-            for (int k = 0; k < 8; k += 2) {
-                const int t = (c0 + k) >> 1;
-                if (valid && t < a.T) {
-                    const float num = v[k] + v[k + 1];
-                    const float r = (num * a.st[t].inv_sigma) * cis;
-                    const float e = cis > 0.f ? eps_mma(steps, cef) : 0.f;
-                    a.rho_tc[t * a.gstride + g] = r;
-                    a.tc[t * a.gstride + g] = angle_interval(r, e);
+                for (int q2 = 0; q2 < 8; q2 += 2) {
+                    const int t = (c0 + q2) >> 1;
+                    if (valid && t < a.T) {
+                        const float num = v[q2] + v[q2 + 1];
+                        const float rr = (num * a.st[t].inv_sigma) * cis;
+                        const float e = cis > 0.f ? eps_mma(steps, cef) : 0.f;
+                        a.rho_tc[t * a.gstride + g] = rr;
+                        a.tc[t * a.gstride + g] = angle_interval(rr, e);
+                    }
                 }
             }
         }
@@ -214,9 +252,9 @@ __global__ void tmpl_split_kernel(const float *__restrict__ tf, size_t tsz, int 
 
 }  // namespace
 
-size_t corr_mma_smem(int h, int Kp, int N) {
+size_t corr_mma_smem(int h, int Kp, int N, int RC) {
     const uint32_t WA = 15u * h + Kp / 8;
-    return 1024 + 2 * round_up(WA * 128u, 1024) + 2 * round_up((uint32_t)N * Kp * 2u, 1024);
+    return 1024 + 2 * round_up(WA * 128u, 1024) + 2 * (size_t)RC * round_up((uint32_t)N * Kp * 2u, 1024);
 }
 
 cudaError_t launch_tmpl_split(const float *tf, size_t tsz, int T, int m, int n, int npad, int Kp,
@@ -239,11 +277,14 @@ cudaError_t launch_corr_mma(const uint8_t *V, int p, int q, const void *B, int m
     *Gx_u_out = Gx_u;
     if (Gx_u <= 0) return cudaSuccess;
     if (N % 16 != 0 || N < 16 || N > 256 || Kp % 16 != 0) return cudaErrorInvalidValue;
-    size_t smem = corr_mma_smem(h, Kp, N);
+    // centre rows per CTA: as many as TMEM (512 columns) and shared memory hold
+    int RC = kMaxRC;
+    while (RC > 1 && (RC * N > 512 || corr_mma_smem(h, Kp, N, RC) > 227 * 1024 || RC > Gy)) RC >>= 1;
+    size_t smem = corr_mma_smem(h, Kp, N, RC);
     // never more resident CTAs per SM than TMEM can hold (512 columns): pad the
     // shared-memory request so that 228 KB / (request + 1 KB) <= 512 / ncols
     int ncols = 32;
-    while (ncols < N) ncols <<= 1;
+    while (ncols < RC * N) ncols <<= 1;
     const int max_ctas = 512 / ncols;
     const size_t floor_req = (size_t)(228 * 1024) / (size_t)(max_ctas + 1) + 1;
     if (smem + 1024 < floor_req) smem = floor_req - 1024 + 16;
@@ -260,12 +301,13 @@ cudaError_t launch_corr_mma(const uint8_t *V, int p, int q, const void *B, int m
     a.B = static_cast<const __nv_bfloat16 *>(B);
     a.m = m; a.n = n; a.Kp = Kp; a.N = N;
     a.h = h; a.Ly = Ly; a.Lx = Lx; a.Gx = Gx; a.Gx_u = Gx_u;
+    a.Gy = Gy; a.RC = RC;
     a.T = T;
     a.c_inv_sigma = c_inv_sigma; a.c_efac = c_efac;
     a.st = st; a.rho_tc = rho_tc; a.tc = tc; a.gstride = gstride; a.err = err;
-    dim3 grid((Gx_u + kMmaM - 1) / kMmaM, Gy);
+    dim3 grid((Gx_u + kMmaM - 1) / kMmaM, (Gy + RC - 1) / RC);
     LaunchScope ls("corr_mma_kernel", s);
-    corr_mma_kernel<<<grid, 128, smem, s>>>(a);
+    corr_mma_kernel<<<grid, kMmaThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

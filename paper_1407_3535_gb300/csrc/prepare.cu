@@ -68,8 +68,8 @@ __global__ void blur_kernel(const uint8_t *__restrict__ I, int p, int q,
 
 // R_oo(x) = rho(P window, I window) (Algorithm 3) and the lambda test.
 __global__ void blur_corr_kernel(const int *__restrict__ wsum, const float *__restrict__ inv_sigma,
-                                 const long long *__restrict__ PS, const long long *__restrict__ PQ,
-                                 const long long *__restrict__ PX, int q, int Ly, int Lx, int m,
+                                 const unsigned *__restrict__ PS, const unsigned *__restrict__ PQ,
+                                 const unsigned *__restrict__ PX, int q, int Ly, int Lx, int m,
                                  int n, float lambda, int block, int *fail, float *R) {
     const int64_t L = (int64_t)Ly * Lx;
     const int64_t q1 = q + 1;
@@ -79,8 +79,8 @@ __global__ void blur_corr_kernel(const int *__restrict__ wsum, const float *__re
          i += (int64_t)gridDim.x * blockDim.x) {
         const int ii = (int)i;
         const int y = ii / Lx, x = ii - y * Lx;
-        const long long Sp = ii_box(PS, q1, y, x, m, n), Qp = ii_box(PQ, q1, y, x, m, n);
-        const long long X = ii_box(PX, q1, y, x, m, n);
+        const long long Sp = ii_box32(PS, q1, y, x, m, n), Qp = ii_box32(PQ, q1, y, x, m, n);
+        const long long X = ii_box32(PX, q1, y, x, m, n);
         const long long dA = mn * Qp - Sp * Sp;                        // exact
         const long long num = mn * X - Sp * (long long)wsum[i];        // exact
         const float iw = inv_sigma[i];                                 // 0: flat I window
@@ -96,7 +96,7 @@ __global__ void blur_corr_kernel(const int *__restrict__ wsum, const float *__re
 }
 
 // Per-centre pivot statistics.
-__global__ void centre_stats_kernel(const long long *__restrict__ PS, const long long *__restrict__ PQ,
+__global__ void centre_stats_kernel(const unsigned *__restrict__ PS, const unsigned *__restrict__ PQ,
                                     int q, int m, int n, int h, int Ly, int Lx,
                                     float *c_inv_sigma, float *c_efac) {
     const int Gy = groups_along(Ly, h), Gx = groups_along(Lx, h);
@@ -107,7 +107,7 @@ __global__ void centre_stats_kernel(const long long *__restrict__ PS, const long
          g += (int64_t)gridDim.x * blockDim.x) {
         const int cy = group_centre_of((int)(g / Gx), Ly, h);
         const int cx = group_centre_of((int)(g % Gx), Lx, h);
-        const long long S = ii_box(PS, q1, cy, cx, m, n), Q = ii_box(PQ, q1, cy, cx, m, n);
+        const long long S = ii_box32(PS, q1, cy, cx, m, n), Q = ii_box32(PQ, q1, cy, cx, m, n);
         const long long imn = (long long)m * n;
         const long long var = imn * Q - S * S;   // exact
         float is = 0.f, ef = 0.f;
@@ -271,8 +271,8 @@ template <int H>
 __global__ void __launch_bounds__(RcoCfg<H>::MAXT, 1)
 rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int p, int q,
               int m, int n, int Ly, int Lx, const int *__restrict__ wsum,
-              const float *__restrict__ inv_sigma, const long long *__restrict__ PS,
-              const long long *__restrict__ PQ, int GXS, int GYB, float cut,
+              const float *__restrict__ inv_sigma, const unsigned *__restrict__ PS,
+              const unsigned *__restrict__ PQ, int GXS, int GYB, float cut,
               float *rco, unsigned long long *count) {
     constexpr int R = RcoCfg<H>::R;
     constexpr int NS = RcoCfg<H>::NS;
@@ -355,8 +355,8 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
         long long Sp = 0, Qp = 0;
         if ((int)threadIdx.x < ngx) {
             const int cx = group_centre_of(gx0 + threadIdx.x, Lx, H);
-            Sp = ii_box(PS, q1, cy, cx, m, n);
-            Qp = ii_box(PQ, q1, cy, cx, m, n);
+            Sp = ii_box32(PS, q1, cy, cx, m, n);
+            Qp = ii_box32(PQ, q1, cy, cx, m, n);
         }
         if (steps > 0) {
             // this column's pivot rows entering and leaving the window, then
@@ -494,8 +494,8 @@ RcoGeom rco_geom(int p, int q, int m, int n) {
 
 template <int H>
 cudaError_t launch_rho_co_h(const uint8_t *P, const uint8_t *I, int p, int q, int m, int n,
-                            const int *wsum, const float *inv_sigma, const long long *PS,
-                            const long long *PQ, float cut, float *rco,
+                            const int *wsum, const float *inv_sigma, const unsigned *PS,
+                            const unsigned *PQ, float cut, float *rco,
                             unsigned long long *count, cudaStream_t s) {
     const int Ly = p - m + 1, Lx = q - n + 1;
     const RcoGeom g = rco_geom<H>(p, q, m, n);
@@ -556,8 +556,8 @@ cudaError_t launch_blur(const uint8_t *I, int p, int q, const uint8_t *level_map
     return cudaGetLastError();
 }
 
-cudaError_t launch_blur_corr(const int *wsum, const float *inv_sigma, const long long *PS,
-                             const long long *PQ, const long long *PX, int p, int q, int m, int n,
+cudaError_t launch_blur_corr(const int *wsum, const float *inv_sigma, const unsigned *PS,
+                             const unsigned *PQ, const unsigned *PX, int p, int q, int m, int n,
                              float lambda, int block, int *fail, float *R, cudaStream_t s) {
     const int Ly = p - m + 1, Lx = q - n + 1;
     LaunchScope ls_blur_corr_kernel("blur_corr_kernel", s);
@@ -578,8 +578,8 @@ bool rho_co_supported(int p, int q, int m, int n, int h) {
 }
 
 cudaError_t launch_rho_co(const uint8_t *P, const uint8_t *I, int p, int q, int m, int n,
-                          int h, const int *wsum, const float *inv_sigma, const long long *PS,
-                          const long long *PQ, float cut, float *rco,
+                          int h, const int *wsum, const float *inv_sigma, const unsigned *PS,
+                          const unsigned *PQ, float cut, float *rco,
                           unsigned long long *count, cudaStream_t s) {
     switch (h) {
         case 1: return launch_rho_co_h<1>(P, I, p, q, m, n, wsum, inv_sigma, PS, PQ, cut, rco, count, s);
@@ -591,7 +591,7 @@ cudaError_t launch_rho_co(const uint8_t *P, const uint8_t *I, int p, int q, int 
     }
 }
 
-cudaError_t launch_centre_stats(const long long *PS, const long long *PQ, int p, int q, int m, int n,
+cudaError_t launch_centre_stats(const unsigned *PS, const unsigned *PQ, int p, int q, int m, int n,
                                 int h, int Ly, int Lx, float *c_inv_sigma, float *c_efac,
                                 cudaStream_t s) {
     const int64_t G = (int64_t)groups_along(Ly, h) * groups_along(Lx, h);

@@ -17,9 +17,10 @@ constexpr int kRowThreads = 256;
 // One block per row; tiles of 4 * 256 pixels: each thread takes 4 consecutive
 // pixels, the block scans the thread totals, and consecutive threads write
 // consecutive 32-byte runs (coalesced).  Sums are exact in int64.
+template <typename T>
 __global__ void __launch_bounds__(kRowThreads)
 ii_rows_kernel(const uint8_t *__restrict__ A, const uint8_t *__restrict__ B, int p, int q,
-               long long *o0, long long *o1, long long *o2) {
+               T *o0, T *o1, T *o2) {
     __shared__ long long wsum[3][kRowThreads / 32];
     __shared__ long long carry[3];
     const int y = blockIdx.x;
@@ -27,9 +28,9 @@ ii_rows_kernel(const uint8_t *__restrict__ A, const uint8_t *__restrict__ B, int
     const uint8_t *a = A + (int64_t)y * q;
     const uint8_t *b = B ? B + (int64_t)y * q : nullptr;
     const int64_t q1 = q + 1;
-    long long *d0 = o0 + (int64_t)(y + 1) * q1;
-    long long *d1 = o1 + (int64_t)(y + 1) * q1;
-    long long *d2 = (b && o2) ? o2 + (int64_t)(y + 1) * q1 : nullptr;
+    T *d0 = o0 + (int64_t)(y + 1) * q1;
+    T *d1 = o1 + (int64_t)(y + 1) * q1;
+    T *d2 = (b && o2) ? o2 + (int64_t)(y + 1) * q1 : nullptr;
     if (tid == 0) {
         d0[0] = 0; d1[0] = 0; if (d2) d2[0] = 0;
         carry[0] = carry[1] = carry[2] = 0;
@@ -65,9 +66,9 @@ ii_rows_kernel(const uint8_t *__restrict__ A, const uint8_t *__restrict__ B, int
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             if (xs + k < q) {
-                d0[xs + k + 1] = e0 + p0[k];
-                d1[xs + k + 1] = e1 + p1[k];
-                if (d2) d2[xs + k + 1] = e2 + p2[k];
+                d0[xs + k + 1] = (T)(e0 + p0[k]);
+                d1[xs + k + 1] = (T)(e1 + p1[k]);
+                if (d2) d2[xs + k + 1] = (T)(e2 + p2[k]);
             }
         }
         __syncthreads();
@@ -79,14 +80,15 @@ ii_rows_kernel(const uint8_t *__restrict__ A, const uint8_t *__restrict__ B, int
 }
 
 // Column pass over rows 1..p of up to three arrays, 32 columns x 32 row segments.
+template <typename T>
 __global__ void __launch_bounds__(1024)
-ii_cols_kernel(int p, int q, long long *o0, long long *o1, long long *o2) {
+ii_cols_kernel(int p, int q, T *o0, T *o1, T *o2) {
     const int64_t q1 = q + 1;
     const int x = blockIdx.x * 32 + threadIdx.x;
     const int seg = threadIdx.y;
     const int seglen = (p + 31) / 32;
     const int r0 = 1 + seg * seglen, r1 = min(p + 1, r0 + seglen);
-    long long a0 = 0, a1 = 0, a2 = 0;
+    T a0 = 0, a1 = 0, a2 = 0;
     if (x < q1) {
         for (int r = r0; r < r1; ++r) {
             a0 += o0[r * q1 + x];
@@ -94,20 +96,20 @@ ii_cols_kernel(int p, int q, long long *o0, long long *o1, long long *o2) {
             if (o2) a2 += o2[r * q1 + x];
         }
     }
-    __shared__ long long sh[3][32][33];
+    __shared__ T sh[3][32][33];
     sh[0][seg][threadIdx.x] = a0; sh[1][seg][threadIdx.x] = a1; sh[2][seg][threadIdx.x] = a2;
     __syncthreads();
     if (seg == 0) {
-        long long c0 = 0, c1 = 0, c2 = 0;
+        T c0 = 0, c1 = 0, c2 = 0;
         for (int k = 0; k < 32; ++k) {
-            const long long t0 = sh[0][k][threadIdx.x], t1 = sh[1][k][threadIdx.x], t2 = sh[2][k][threadIdx.x];
+            const T t0 = sh[0][k][threadIdx.x], t1 = sh[1][k][threadIdx.x], t2 = sh[2][k][threadIdx.x];
             sh[0][k][threadIdx.x] = c0; sh[1][k][threadIdx.x] = c1; sh[2][k][threadIdx.x] = c2;
             c0 += t0; c1 += t1; c2 += t2;
         }
     }
     __syncthreads();
     if (x >= q1) return;
-    long long c0 = sh[0][seg][threadIdx.x], c1 = sh[1][seg][threadIdx.x], c2 = sh[2][seg][threadIdx.x];
+    T c0 = sh[0][seg][threadIdx.x], c1 = sh[1][seg][threadIdx.x], c2 = sh[2][seg][threadIdx.x];
     for (int r = r0; r < r1; ++r) {
         c0 += o0[r * q1 + x]; o0[r * q1 + x] = c0;
         c1 += o1[r * q1 + x]; o1[r * q1 + x] = c1;
@@ -197,25 +199,36 @@ static int grid_for(int64_t n, int threads) {
     return (int)b;
 }
 
-cudaError_t launch_integrals(const uint8_t *A, const uint8_t *B, int p, int q, long long *o0,
-                             long long *o1, long long *o2, cudaStream_t s) {
+template <typename T>
+static cudaError_t integrals_impl(const uint8_t *A, const uint8_t *B, int p, int q, T *o0, T *o1,
+                                  T *o2, cudaStream_t s) {
     const int64_t q1 = q + 1;
     cudaError_t e;
     // first row zero
-    if ((e = cudaMemsetAsync(o0, 0, q1 * sizeof(long long), s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(o1, 0, q1 * sizeof(long long), s)) != cudaSuccess) return e;
-    if (B && o2 && (e = cudaMemsetAsync(o2, 0, q1 * sizeof(long long), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(o0, 0, q1 * sizeof(T), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(o1, 0, q1 * sizeof(T), s)) != cudaSuccess) return e;
+    if (B && o2 && (e = cudaMemsetAsync(o2, 0, q1 * sizeof(T), s)) != cudaSuccess) return e;
     {
         LaunchScope ls("ii_rows_kernel", s);
-        ii_rows_kernel<<<p, kRowThreads, 0, s>>>(A, B, p, q, o0, o1, (B ? o2 : nullptr));
+        ii_rows_kernel<T><<<p, kRowThreads, 0, s>>>(A, B, p, q, o0, o1, (B ? o2 : nullptr));
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
         LaunchScope ls("ii_cols_kernel", s);
-        ii_cols_kernel<<<(int)((q1 + 31) / 32), dim3(32, 32), 0, s>>>(p, q, o0, o1,
-                                                                     (B ? o2 : nullptr));
+        ii_cols_kernel<T><<<(int)((q1 + 31) / 32), dim3(32, 32), 0, s>>>(p, q, o0, o1,
+                                                                        (B ? o2 : nullptr));
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_integrals(const uint8_t *A, const uint8_t *B, int p, int q, long long *o0,
+                             long long *o1, long long *o2, cudaStream_t s) {
+    return integrals_impl<long long>(A, B, p, q, o0, o1, o2, s);
+}
+
+cudaError_t launch_integrals32(const uint8_t *A, const uint8_t *B, int p, int q, unsigned *o0,
+                               unsigned *o1, unsigned *o2, cudaStream_t s) {
+    return integrals_impl<unsigned>(A, B, p, q, o0, o1, o2, s);
 }
 
 cudaError_t launch_count_zero(const float *x, int64_t n, unsigned long long *count,
