@@ -572,7 +572,7 @@ opta_status enqueue_scan1(opta_handle *H, const opta_template *const *t, int n, 
                    H->topk_i, H->cand_topk, s));
     CK(launch_refine64_topk(H->I8, H->q, S->Lx, H->td, dsz, m, nn, n, st, H->cand_topk,
                             H->cand_rho_topk, s));
-    CK(launch_group_members(H->I8, H->q, S->Ly, S->Lx, S->h, H->IIS, H->IIQ, H->tf, tsz, m, nn,
+    CK(launch_group_members(H->I8, H->q, S->Ly, S->Lx, S->h, S->wsum, H->tf, tsz, m, nn,
                             npad, S->inv_sigma, n, st, H->cand_topk, H->prm.topk, s));
     CK(launch_threshold(st, H->cand_rho_topk, n, s));
     return OPTA_OK;
@@ -610,8 +610,7 @@ opta_status enqueue_scan2(opta_handle *H, const opta_template *const *t, int n, 
         B.bucket_cnt = H->bucket_cnt;
         B.bucket_cur = H->bucket_cur;
         CK(launch_bound_compact(B, S->theta_co, S->gco, S->Ly, S->Lx, S->h, ub_map, surv_map, s));
-        CK(launch_survivors(B, H->I8, H->p, H->q, S->Lx, H->IIS, H->IIQ, m, nn, npad,
-                            S->inv_sigma, s));
+        CK(launch_survivors(B, H->I8, H->p, H->q, S->Lx, S->wsum, m, nn, npad, S->inv_sigma, s));
         CK(launch_surv_candidates(B, s));
         CK(launch_refine64(H->I8, H->q, S->Lx, H->td + k0 * dsz, dsz, m, nn, T, st + k0, H->cand,
                            H->cand_rho, scap, s));

@@ -194,8 +194,8 @@ cudaError_t launch_topk(const float *rho_tc, int64_t gstride, int Gy, int Gx, in
                         cudaStream_t s);
 cudaError_t launch_threshold(TmplState *st, const double *cand_rho_topk, int T, cudaStream_t s);
 // FP32 rho at the members of the threshold centres' groups (raises lo_key).
-cudaError_t launch_group_members(const uint8_t *I, int q, int Ly, int Lx, int h, const long long *IIS,
-                                 const long long *IIQ, const float *tf, size_t tsz, int m, int n,
+cudaError_t launch_group_members(const uint8_t *I, int q, int Ly, int Lx, int h, const int *wsum,
+                                 const float *tf, size_t tsz, int m, int n,
                                  int npad, const float *inv_sigma, int T, TmplState *st,
                                  const int *cand_topk, int topk, cudaStream_t s);
 // Scan 2 of a batch of T same-size templates: per-template arrays, each at
@@ -230,8 +230,8 @@ cudaError_t launch_group_co(const float2 *theta_co, int Ly, int Lx, int h, float
 // Cut of the skippable buckets, then one bound-ordered sweep over the
 // survivors of all T templates (FP32 rho, running lower bound per template).
 cudaError_t launch_survivors(const Scan2Batch &B, const uint8_t *I, int pimg, int q, int Lx,
-                             const long long *IIS, const long long *IIQ, int m, int n, int npad,
-                             const float *inv_sigma, cudaStream_t s);
+                             const int *wsum, int m, int n, int npad, const float *inv_sigma,
+                             cudaStream_t s);
 cudaError_t launch_surv_candidates(const Scan2Batch &B, cudaStream_t s);
 
 // --- preparation ---

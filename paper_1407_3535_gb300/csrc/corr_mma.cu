@@ -67,7 +67,7 @@ __device__ inline float eps_mma(int steps, float efac) {
 }
 
 constexpr int kMmaThreads = 256;
-constexpr int kMaxRC = 4;
+constexpr int kMaxRC = 2;   // 4 fills TMEM (one CTA per SM) and measured slower
 
 __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaArgs a) {
     extern __shared__ __align__(1024) uint8_t smem[];

@@ -15,6 +15,17 @@ namespace opta {
 
 namespace {
 
+// 4-byte asynchronous global -> shared copies (visible to the issuing thread
+// after cp_async_wait_all).
+__device__ inline void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 constexpr int kMaxRadius = 9;
 
 // One CTA per block x block output tile; sigma (level) fixed per tile.
@@ -250,9 +261,10 @@ __device__ __forceinline__ void rco_batch(int (&cs)[H * H], const unsigned (&pw)
 
 // Shared-memory words of one CTA (host and device agree on the layout):
 // two emission buffers of H scanned shift rows and their segment totals,
-// the per-centre statistics and the image ring.
+// the per-centre statistics, each thread's member inputs of one group row
+// (window sum and 1/Omega per shift row) and the image ring.
 struct RcoSmem {
-    int hsc, segt, cst, ring, total;
+    int hsc, segt, cst, tin, ring, total;
 };
 template <int H>
 __host__ __device__ inline RcoSmem rco_smem(int Wmax, int GXS, int CSW) {
@@ -262,6 +274,7 @@ __host__ __device__ inline RcoSmem rco_smem(int Wmax, int GXS, int CSW) {
     l.hsc = o;  o += 2 * H * RcoScan<H>::RS;
     l.segt = o; o += 2 * H * RcoScan<H>::NSEG;
     l.cst = o;  o += 2 * GXS;
+    l.tin = o;  o += 2 * H * RcoCfg<H>::MAXT;
     l.ring = o; o += (Wmax + 2 * R) * CSW;
     l.total = o;
     return l;
@@ -295,6 +308,8 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
     unsigned *segt = rsm + L.segt;                                // 2 x H x NSEG segment totals
     int *cS = reinterpret_cast<int *>(rsm + L.cst);               // per centre: S_hat
     float *cI = reinterpret_cast<float *>(rsm + L.cst + GXS);     // per centre: 1/(mn Omega_hat)
+    int *tws = reinterpret_cast<int *>(rsm + L.tin);             // [H][MAXT] member window sums
+    float *tiw = reinterpret_cast<float *>(rsm + L.tin + H * RcoCfg<H>::MAXT);   // [H][MAXT] 1/Omega
     unsigned *ringw = rsm + L.ring;                               // (W + 2R) columns x CSW words
     uint8_t *ring8 = reinterpret_cast<uint8_t *>(ringw);
     const int j = threadIdx.x;
@@ -351,6 +366,29 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
     for (int gy = gy0; gy < gy1; ++gy) {
         const int cy = group_centre_of(gy, Ly, H);
         const int steps = cy - r;            // 0 for the first row, <= H after
+        // this thread's first task (centre gxi, shift column sxi): its member's
+        // window sum and 1/Omega for every shift row of the group row, copied
+        // to shared memory while the slide runs
+        {
+            const int gys0 = gy * H, gye0 = min(gys0 + H, Ly);
+            if ((int)threadIdx.x < ntask) {
+                const int gxi = threadIdx.x / H, sxi = threadIdx.x - gxi * H;
+                const int gx = gx0 + gxi;
+                const int mx = group_centre_of(gx, Lx, H) + sxi - R;
+                if (mx >= gx * H && mx < min(gx * H + H, Lx)) {
+#pragma unroll 1
+                    for (int syi = 0; syi < H; ++syi) {
+                        const int my = cy + syi - R;
+                        if (my >= gys0 && my < gye0) {
+                            const int64_t li = (int64_t)my * Lx + mx;
+                            cp_async4(tws + syi * RcoCfg<H>::MAXT + threadIdx.x, wsum + li);
+                            cp_async4(tiw + syi * RcoCfg<H>::MAXT + threadIdx.x, inv_sigma + li);
+                        }
+                    }
+                }
+            }
+            cp_async_commit();
+        }
         // pivot statistics of this row's centres, loads issued before the slide
         long long Sp = 0, Qp = 0;
         if ((int)threadIdx.x < ngx) {
@@ -381,6 +419,7 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
             // 1 / (mn Omega_hat) = sqrt(mn / var) / mn
             cI[threadIdx.x] = var > 0 ? sqrtf((float)mn / (float)var) / (float)mn : 0.f;
         }
+        cp_async_wait_all();   // this thread's member inputs (read by this thread only)
         // emit centre row cy, one shift row (sy) at a time
         const int gys = gy * H, gye = min(gys + H, Ly);
 #pragma unroll
@@ -429,8 +468,15 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
                 const int mx = cxg + sxi - R;
                 if (mx < gx * H || mx >= min(gx * H + H, Lx)) continue;
                 const int64_t li = (int64_t)my * Lx + mx;
-                const int ws = wsum[li];
-                const float iw = inv_sigma[li];
+                int ws;
+                float iw;
+                if (task == (int)threadIdx.x) {
+                    ws = tws[syi * RcoCfg<H>::MAXT + threadIdx.x];
+                    iw = tiw[syi * RcoCfg<H>::MAXT + threadIdx.x];
+                } else {
+                    ws = wsum[li];
+                    iw = inv_sigma[li];
+                }
                 const int c1 = cxg - cx0, c2 = c1 + n - 1;
                 const unsigned *row = hb + sxi * SG::RS;
                 unsigned X = row[rco_addr<H>(c2)];

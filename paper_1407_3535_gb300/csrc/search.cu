@@ -883,17 +883,15 @@ __device__ inline void stage_rows(const uint8_t *I, const uint8_t *img_end, int 
 // staging buffer (wbuf: 2 x kStageRows x WB bytes) the window goes through
 // shared memory; without, it is read straight from global memory.
 __device__ inline void warp_rho32(const uint8_t *__restrict__ I, int q, int Lx,
-                                  const long long *__restrict__ IIS,
-                                  const long long *__restrict__ IIQ,
+                                  const int *__restrict__ wsum,
                                   const float *__restrict__ tm, int m, int n, int npad,
                                   const float *__restrict__ inv_sigma, float ist, int idx,
                                   uint8_t *wbuf, const uint8_t *img_end, float &rho, float &eps) {
     const int lane = threadIdx.x & 31;
-    const int64_t q1 = q + 1;
     const long long mn = (long long)m * n;
     const int y = idx / Lx, x = idx % Lx;
-    const long long S = ii_box(IIS, q1, y, x, m, n);
-    const long long Q = ii_box(IIQ, q1, y, x, m, n);
+    const long long S = wsum[idx];                 // exact window sum (per-size map)
+    const float is = inv_sigma[idx];
     // any integer in [0, 255] keeps |v| <= 255; the nearest to the mean keeps it small
     const float a = rintf((float)S / (float)mn);
     const uint8_t *bp = I + (int64_t)y * q + x;
@@ -948,12 +946,13 @@ __device__ inline void warp_rho32(const uint8_t *__restrict__ I, int q, int Lx,
         // accumulation depth per lane: ceil(n/32) per row, then at most m row
         // partial sums into one chain, the chain merges and 5 shuffle levels
         const int kacc = ((n + 31) / 32) + m + 8;
-        const float is = inv_sigma[idx];
         rho = (acc * ist) * is;
         if (is > 0.f) {
-            const long long ia = (long long)a;
-            const long long c2 = Q - 2 * ia * S + mn * ia * ia;   // sum (I - a)^2, exact
-            eps = eps_bound(kacc, sqrtf((float)mn * ((float)c2 / win_var(mn, S, Q))));
+            // ||I - a||^2 = Omega^2 + (S - a mn)^2 / mn, so ||I - a|| / Omega =
+            // sqrt(1 + dS^2 / mn * (1/Omega)^2) with dS = S - a mn exact
+            const long long dS = S - (long long)a * mn;
+            const float r2 = ((float)(dS * dS) / (float)mn) * (is * is);
+            eps = eps_bound(kacc, sqrtf(1.f + r2));
         }
     }
 }
@@ -982,9 +981,9 @@ __device__ inline const float *stage_template(const float *tf, int m, int npad, 
 // maximum.
 __global__ void __launch_bounds__(256)
 survivors_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, int Lx,
-                 const long long *__restrict__ IIS, const long long *__restrict__ IIQ, int m,
-                 int n, int npad, const float *__restrict__ inv_sigma, int tmpl_in_smem,
-                 int stage, const uint8_t *img_end) {
+                 const int *__restrict__ wsum, int m, int n, int npad,
+                 const float *__restrict__ inv_sigma, int tmpl_in_smem, int stage,
+                 const uint8_t *img_end) {
     extern __shared__ float4 ssm4[];
     TmplState *st = B.st + blockIdx.y;
     if (st->flat) return;
@@ -1014,34 +1013,130 @@ survivors_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, int L
     // the bound-ordered list together; a survivor whose bound has fallen below
     // the running certain lower bound of the maximum is skipped (Eq. SEC with
     // the best rho_tb found so far).  The warp's next 32 entries are read in
-    // one round (a lane each), so skipped entries cost no dependent load.
+    // one round (a lane each), so skipped entries cost no dependent load; the
+    // lower bound is read once per round and kept current with the values
+    // the warp's own atomic maxima return (a stale bound only skips less).
+    float lim = -4.f;
     for (int64_t base = warp; base < ns; base += 32 * (int64_t)nwarps) {
         const int64_t sl = base + (int64_t)lane * nwarps;
         const bool have = sl < ns;
         const float ubl = have ? surv_ub[sl] : -4.f;
         const int idxl = have ? surv[sl] : 0;
-        const float lim0 = __shfl_sync(0xffffffffu, key_float(*lo_key), 0);
-        unsigned pend = __ballot_sync(0xffffffffu, have && ubl >= lim0);
+        lim = fmaxf(lim, __shfl_sync(0xffffffffu, key_float(*lo_key), 0));
+        unsigned pend = __ballot_sync(0xffffffffu, have && ubl >= lim);
         while (pend) {
             const int k = __ffs(pend) - 1;
             pend &= pend - 1;
             const float ub = __shfl_sync(0xffffffffu, ubl, k);
             const int idx = __shfl_sync(0xffffffffu, idxl, k);
-            const float lim = __shfl_sync(0xffffffffu, key_float(*lo_key), 0);
             if (ub < lim) continue;
             float rho, eps;
-            warp_rho32(I, q, Lx, IIS, IIQ, tm, m, n, npad, inv_sigma, ist, idx, wbuf, img_end,
-                       rho, eps);
+            warp_rho32(I, q, Lx, wsum, tm, m, n, npad, inv_sigma, ist, idx, wbuf, img_end, rho,
+                       eps);
+            unsigned seen = 0u;
             if (lane == 0) {
                 const int64_t s = base + (int64_t)k * nwarps;
                 surv_rho[s] = rho;
                 surv_eps[s] = eps;
-                atomicMax(&st->lo_key, float_key(rho - eps));
+                const unsigned mine = float_key(rho - eps);
+                seen = max(atomicMax(&st->lo_key, mine), mine);
                 ++evaluated;
             }
+            lim = fmaxf(lim, key_float(__shfl_sync(0xffffffffu, seen, 0)));
             __syncwarp();
         }
     }
+    if (lane == 0 && evaluated) atomicAdd(&st->n_eval, evaluated);
+}
+
+// Survivors of small templates (m * n <= kLaneMaxMN): one lane per survivor.
+// A warp takes 32 consecutive entries of its interleaved share of the
+// bound-ordered list; each lane evaluates its own window from 32-bit words
+// (funnel-shifted to the window's alignment), the template comes from
+// shared memory by broadcast.  Per-row partial sums keep the accumulation
+// depth at n + m + 2, the same error bound as the warp form.
+constexpr int kLaneMaxMN = 2304;   // above this the warp form is faster (fewer, longer dot products)
+
+__global__ void __launch_bounds__(256)
+survivors_lane_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, int Lx,
+                      const int *__restrict__ wsum, int m, int n, int npad,
+                      const float *__restrict__ inv_sigma, const uint8_t *img_end) {
+    extern __shared__ float4 lsm4[];
+    TmplState *st = B.st + blockIdx.y;
+    if (st->flat) return;
+    const int *surv = B.surv + blockIdx.y * B.scap;
+    const float *surv_ub = B.surv_ub + blockIdx.y * B.scap;
+    float *surv_rho = B.surv_rho + blockIdx.y * B.scap;
+    float *surv_eps = B.surv_eps + blockIdx.y * B.scap;
+    const int ns = (int)min((int64_t)min(st->n_surv, st->n_surv_eff), B.scap);
+    if ((int)blockIdx.x * (int)(blockDim.x >> 5) >= ns) return;   // uniform
+    const float *tm = stage_template(B.tf + blockIdx.y * B.tsz, m, npad, 1,
+                                     reinterpret_cast<float *>(lsm4));
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const float ist = st->inv_sigma;
+    const long long mn = (long long)m * n;
+    const int kacc = n + m + 2;
+    volatile unsigned int *lo_key = &st->lo_key;
+    const uintptr_t iend = reinterpret_cast<uintptr_t>(img_end);
+    float lim = -4.f;
+    int evaluated = 0;
+    for (int64_t base = warp; base < ns; base += 32 * (int64_t)nwarps) {
+        const int64_t sl = base + (int64_t)lane * nwarps;
+        lim = fmaxf(lim, __shfl_sync(0xffffffffu, key_float(*lo_key), 0));
+        bool act = false;
+        int idx = 0;
+        if (sl < ns) {
+            act = surv_ub[sl] >= lim;
+            idx = surv[sl];
+        }
+        float lo = -4.f;
+        if (act) {
+            const int y = idx / Lx, x = idx - (idx / Lx) * Lx;
+            const long long S = wsum[idx];
+            const float is = inv_sigma[idx];
+            const float a = rintf((float)S / (float)mn);
+            float tot = 0.f;
+            const uint8_t *wp = I + (int64_t)y * q + x;
+            for (int u = 0; u < m; ++u) {
+                const uintptr_t ra = reinterpret_cast<uintptr_t>(wp + (int64_t)u * q);
+                const uint32_t *wr = reinterpret_cast<const uint32_t *>(ra & ~(uintptr_t)3);
+                const unsigned sh = (unsigned)(ra & 3) * 8u;
+                const float *tr = tm + u * npad;
+                uint32_t w0 = wr[0];
+                float racc = 0.f;
+                for (int v = 0; v < n; v += 4) {
+                    // the next word, unless it starts past the image
+                    const uint32_t *nx = wr + (v >> 2) + 1;
+                    const uint32_t w1 = reinterpret_cast<uintptr_t>(nx) < iend ? *nx : 0u;
+                    const uint32_t wv = __funnelshift_r(w0, w1, sh);
+                    w0 = w1;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b)
+                        if (v + b < n) racc = fmaf(tr[v + b], (float)((wv >> (8 * b)) & 255u) - a, racc);
+                }
+                tot += racc;
+            }
+            const float rho = (tot * ist) * is;
+            float eps = 0.f;
+            if (is > 0.f) {
+                const long long dS = S - (long long)a * mn;
+                const float r2 = ((float)(dS * dS) / (float)mn) * (is * is);
+                eps = eps_bound(kacc, sqrtf(1.f + r2));
+            }
+            surv_rho[sl] = rho;
+            surv_eps[sl] = eps;
+            lo = rho - eps;
+            ++evaluated;
+        }
+        // one atomic per warp: the largest certain lower bound of the round
+        const unsigned key = __reduce_max_sync(0xffffffffu, act ? float_key(lo) : 0u);
+        unsigned seen = 0u;
+        if (lane == 0 && key) seen = max(atomicMax(&st->lo_key, key), key);
+        lim = fmaxf(lim, key_float(__shfl_sync(0xffffffffu, seen, 0)));
+    }
+    evaluated = __reduce_add_sync(0xffffffffu, evaluated);
     if (lane == 0 && evaluated) atomicAdd(&st->n_eval, evaluated);
 }
 
@@ -1074,7 +1169,7 @@ survivor_cut_kernel(const Scan2Batch B) {
 // them); raises the certain lower bound of the maximum before scan 2.
 __global__ void __launch_bounds__(256)
 group_members_kernel(const uint8_t *__restrict__ I, int q, int Ly, int Lx, int h,
-                     const long long *__restrict__ IIS, const long long *__restrict__ IIQ,
+                     const int *__restrict__ wsum,
                      const float *__restrict__ tf, size_t tsz, int m, int n, int npad,
                      const float *__restrict__ inv_sigma, TmplState *st,
                      const int *__restrict__ cand, int tmpl_in_smem) {
@@ -1096,7 +1191,7 @@ group_members_kernel(const uint8_t *__restrict__ I, int q, int Ly, int Lx, int h
     for (int j = warp; j < hy * hx; j += nw) {
         const int idx = (y0 + j / hx) * Lx + x0 + j % hx;
         float rho, eps;
-        warp_rho32(I, q, Lx, IIS, IIQ, tm, m, n, npad, inv_sigma, ist, idx, nullptr, nullptr, rho,
+        warp_rho32(I, q, Lx, wsum, tm, m, n, npad, inv_sigma, ist, idx, nullptr, nullptr, rho,
                    eps);
         if ((threadIdx.x & 31) == 0) atomicMax(&st->lo_key, float_key(rho - eps));
     }
@@ -1324,8 +1419,8 @@ static size_t tmpl_smem(int m, int npad, int *in_smem) {
 }
 
 cudaError_t launch_survivors(const Scan2Batch &B, const uint8_t *I, int pimg, int q, int Lx,
-                             const long long *IIS, const long long *IIQ, int m, int n, int npad,
-                             const float *inv_sigma, cudaStream_t s) {
+                             const int *wsum, int m, int n, int npad, const float *inv_sigma,
+                             cudaStream_t s) {
     int in_smem = 0;
     size_t smem = tmpl_smem(m, npad, &in_smem);
     smem = (smem + 15) & ~(size_t)15;
@@ -1357,9 +1452,28 @@ cudaError_t launch_survivors(const Scan2Batch &B, const uint8_t *I, int pimg, in
     // one sweep for the whole batch: num_sms * 4 blocks for one template,
     // fewer per template (down to num_sms) when several share the launch
     const int bx = std::max(num_sms(), num_sms() * 4 / std::min(B.T, 4));
+    if ((int64_t)m * n <= kLaneMaxMN) {
+        const size_t lsmem = ((size_t)m * npad * sizeof(float) + 15) & ~(size_t)15;
+        static std::mutex lmu;
+        static size_t lattr = 0;
+        {
+            std::lock_guard<std::mutex> lk(lmu);
+            if (lsmem > lattr) {
+                cudaError_t e2 = cudaFuncSetAttribute(survivors_lane_kernel,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)lsmem);
+                if (e2 != cudaSuccess) return e2;
+                lattr = lsmem;
+            }
+        }
+        LaunchScope ls("survivors_lane_kernel", s);
+        survivors_lane_kernel<<<dim3(bx, B.T), 256, lsmem, s>>>(B, I, q, Lx, wsum, m, n, npad,
+                                                                inv_sigma, iend);
+        return cudaGetLastError();
+    }
     {
         LaunchScope ls("survivors_kernel", s);
-        survivors_kernel<<<dim3(bx, B.T), 256, smem, s>>>(B, I, q, Lx, IIS, IIQ, m, n, npad,
+        survivors_kernel<<<dim3(bx, B.T), 256, smem, s>>>(B, I, q, Lx, wsum, m, n, npad,
                                                           inv_sigma, in_smem, stage, iend);
     }
     return cudaGetLastError();
@@ -1372,8 +1486,8 @@ cudaError_t launch_surv_candidates(const Scan2Batch &B, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_group_members(const uint8_t *I, int q, int Ly, int Lx, int h, const long long *IIS,
-                                 const long long *IIQ, const float *tf, size_t tsz, int m, int n,
+cudaError_t launch_group_members(const uint8_t *I, int q, int Ly, int Lx, int h, const int *wsum,
+                                 const float *tf, size_t tsz, int m, int n,
                                  int npad, const float *inv_sigma, int T, TmplState *st,
                                  const int *cand_topk, int topk, cudaStream_t s) {
     int in_smem = 0;
@@ -1386,7 +1500,7 @@ cudaError_t launch_group_members(const uint8_t *I, int q, int Ly, int Lx, int h,
         attr = smem;
     }
     LaunchScope ls("group_members_kernel", s);
-    group_members_kernel<<<dim3(topk, T), 256, smem, s>>>(I, q, Ly, Lx, h, IIS, IIQ, tf, tsz, m, n,
+    group_members_kernel<<<dim3(topk, T), 256, smem, s>>>(I, q, Ly, Lx, h, wsum, tf, tsz, m, n,
                                                           npad, inv_sigma, st, cand_topk, in_smem);
     return cudaGetLastError();
 }
