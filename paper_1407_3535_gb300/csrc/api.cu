@@ -5,8 +5,11 @@
 #include <cmath>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
 #include <map>
+#include <mutex>
 #include <new>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -41,9 +44,10 @@ constexpr int kChunk = 128;   // templates per batch (tensor-core N = 2 * chunk 
 // candidate index and its FP64 rho).
 constexpr size_t kScan2Budget = (size_t)8 << 30;
 
-// Device allocation that keeps a running byte count.
+// Device allocation that keeps a running byte count (host threads that
+// prepare sizes concurrently share it).
 struct DevMem {
-    size_t bytes = 0;
+    std::atomic<size_t> bytes{0};
     template <class T>
     opta_status alloc(T **p, size_t count) {
         *p = nullptr;
@@ -87,6 +91,8 @@ struct opta_handle {
     long long *IIS = nullptr, *IIQ = nullptr;
     unsigned *IIS32 = nullptr, *IIQ32 = nullptr;   // the same modulo 2^32 (level-0 pivots)
     std::map<std::pair<int, int>, SizeState *> sizes;
+    std::mutex sizes_mu;                      // guards `sizes` while sizes are prepared concurrently
+    cudaMemPool_t pool = nullptr;             // stream-ordered scratch of the preparation
     // search scratch (grown on demand)
     size_t capL = 0, capG = 0, capT = 0, capN = 0;
     size_t capS2 = 0;                         // template slots of the scan-2 arrays (stride capL)
@@ -271,9 +277,17 @@ opta_status blur_to(opta_handle *H, PrepScratch &W, const std::vector<uint8_t> &
     return OPTA_OK;
 }
 
+bool size_ready(opta_handle *H, const std::pair<int, int> &key) {
+    std::lock_guard<std::mutex> lk(H->sizes_mu);
+    return H->sizes.count(key) != 0;
+}
+
+// Preparation of one size on stream s.  Scratch comes from the handle's
+// stream-ordered pool (allocation and release without a device-wide
+// synchronisation), so sizes may be prepared by several host threads at once.
 opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     auto key = std::make_pair(m, n);
-    if (H->sizes.count(key)) return OPTA_OK;
+    if (size_ready(H, key)) return OPTA_OK;
     const int p = H->p, q = H->q;
     if (h_limit(p, q, m, n, 1) < 1) return OPTA_ERR_TOO_LARGE;
     SizeState *S = new (std::nothrow) SizeState();
@@ -286,17 +300,13 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     S->sigma_map.assign((size_t)bp * bq, 0.f);
 
     PrepScratch W;
+    auto scratch = [&](auto **ptr, size_t bytes) {
+        return cudaMallocFromPoolAsync(reinterpret_cast<void **>(ptr), bytes, H->pool, s);
+    };
     auto cleanup = [&](opta_status st) {
-        if (W.Pcur) cudaFree(W.Pcur);
-        if (W.Pacc && W.Pacc != S->P) cudaFree(W.Pacc);
-        if (W.PS) cudaFree(W.PS);
-        if (W.PQ) cudaFree(W.PQ);
-        if (W.PX) cudaFree(W.PX);
-        if (W.PSa) cudaFree(W.PSa);
-        if (W.PQa) cudaFree(W.PQa);
-        if (W.fail) cudaFree(W.fail);
-        if (W.lvl) cudaFree(W.lvl);
-        if (W.count) cudaFree(W.count);
+        void *bufs[] = {W.Pcur, W.Pacc, W.PS, W.PQ, W.PX, W.PSa, W.PQa, W.fail, W.lvl, W.count};
+        for (void *b : bufs)
+            if (b) cudaFreeAsync(b, s);
         if (st != OPTA_OK) {
             H->mem.release(S->inv_sigma, L);
             H->mem.release(S->wsum, L);
@@ -316,7 +326,7 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     PTRY(H->mem.alloc(&S->inv_sigma, L));
     PTRY(H->mem.alloc(&S->wsum, L));
     PCK(launch_window_stats(H->IIS, H->IIQ, p, q, m, n, S->inv_sigma, nullptr, s, S->wsum));
-    PCK(cudaMalloc(&W.count, sizeof(unsigned long long)));
+    PCK(scratch(&W.count, sizeof(unsigned long long)));
 
     // Level 0: unblurred pivots (P = I).
     int h_best = 1;
@@ -330,15 +340,15 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     int level_best = 0;
     if (prm.blur && prm.n_levels > 0 && prm.fixed_h == 0) {
         const size_t nII = (size_t)(p + 1) * (q + 1);
-        PCK(cudaMalloc(&W.Pcur, (size_t)p * q));
-        PCK(cudaMalloc(&W.Pacc, (size_t)p * q));
-        PCK(cudaMalloc(&W.PS, nII * sizeof(unsigned)));
-        PCK(cudaMalloc(&W.PQ, nII * sizeof(unsigned)));
-        PCK(cudaMalloc(&W.PX, nII * sizeof(unsigned)));
-        PCK(cudaMalloc(&W.PSa, nII * sizeof(unsigned)));
-        PCK(cudaMalloc(&W.PQa, nII * sizeof(unsigned)));
-        PCK(cudaMalloc(&W.fail, (size_t)bp * bq * sizeof(int)));
-        PCK(cudaMalloc(&W.lvl, (size_t)bp * bq));
+        PCK(scratch(&W.Pcur, (size_t)p * q));
+        PCK(scratch(&W.Pacc, (size_t)p * q));
+        PCK(scratch(&W.PS, nII * sizeof(unsigned)));
+        PCK(scratch(&W.PQ, nII * sizeof(unsigned)));
+        PCK(scratch(&W.PX, nII * sizeof(unsigned)));
+        PCK(scratch(&W.PSa, nII * sizeof(unsigned)));
+        PCK(scratch(&W.PQa, nII * sizeof(unsigned)));
+        PCK(scratch(&W.fail, (size_t)bp * bq * sizeof(int)));
+        PCK(scratch(&W.lvl, (size_t)bp * bq));
         const float lam = (float)lambda_of(prm.rho_th, prm.rho_max);
         std::vector<uint8_t> cur_level((size_t)bp * bq, 0);   // accepted level index per block
         std::vector<char> frozen((size_t)bp * bq, 0);
@@ -397,12 +407,11 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
         S->P = H->I8;
         S->P_owned = false;
     } else {
-        // the accepted pivot moves into the size state; its integrals were
-        // kept when it was accepted
-        H->mem.bytes += (size_t)p * q;
-        S->P = W.Pacc;
+        // the accepted pivot is copied into the size state; its integrals
+        // were kept when it was accepted
+        PTRY(H->mem.alloc(&S->P, (size_t)p * q));
         S->P_owned = true;
-        W.Pacc = nullptr;
+        PCK(cudaMemcpyAsync(S->P, W.Pacc, (size_t)p * q, cudaMemcpyDeviceToDevice, s));
         PS = W.PSa;
         PQ = W.PQa;
     }
@@ -417,10 +426,60 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     PCK(launch_group_co(S->theta_co, S->Ly, S->Lx, S->h, S->gco, s));
     PCK(launch_centre_stats(PS, PQ, p, q, m, n, S->h, S->Ly, S->Lx, S->c_inv_sigma, S->c_efac, s));
     PCK(cudaStreamSynchronize(s));
-    H->sizes[key] = S;
+    {
+        std::lock_guard<std::mutex> lk(H->sizes_mu);
+        H->sizes[key] = S;
+    }
     return cleanup(OPTA_OK);
 #undef PTRY
 #undef PCK
+}
+
+// Prepare every size of `todo` not prepared yet.  Several sizes run at once,
+// one host thread and stream each (their level loops wait on the host
+// between kernels, so one size's waits overlap another's kernels); the work
+// queued on `s` before the call is awaited first.
+opta_status prepare_sizes(opta_handle *H, const std::vector<std::pair<int, int>> &todo,
+                          cudaStream_t s) {
+    std::vector<std::pair<int, int>> need;
+    for (const auto &k : todo)
+        if (!size_ready(H, k) && std::find(need.begin(), need.end(), k) == need.end())
+            need.push_back(k);
+    if (need.empty()) return OPTA_OK;
+    if (need.size() == 1) return prepare_size(H, need[0].first, need[0].second, s);
+    cudaEvent_t ready = nullptr;
+    CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    CK(cudaEventRecord(ready, s));
+    std::vector<opta_status> st(need.size(), OPTA_OK);
+    std::atomic<size_t> next{0};
+    auto worker = [&]() {
+        cudaSetDevice(H->device);
+        cudaStream_t ws = nullptr;
+        if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamWaitEvent(ws, ready, 0) != cudaSuccess) {
+            cudaGetLastError();
+            for (size_t i = next++; i < need.size(); i = next++) st[i] = OPTA_ERR_CUDA;
+            if (ws) cudaStreamDestroy(ws);
+            return;
+        }
+        for (size_t i = next++; i < need.size(); i = next++)
+            st[i] = prepare_size(H, need[i].first, need[i].second, ws);
+        cudaStreamSynchronize(ws);
+        cudaStreamDestroy(ws);
+    };
+    const size_t nth = std::min<size_t>(need.size(), 8);
+    std::vector<std::thread> threads;
+    try {
+        for (size_t t = 0; t < nth; ++t) threads.emplace_back(worker);
+    } catch (...) {
+        // no threads to be had: the caller's thread takes the rest
+    }
+    if (threads.empty()) worker();
+    for (auto &t : threads) t.join();
+    cudaEventDestroy(ready);
+    for (opta_status x : st)
+        if (x != OPTA_OK) return x;
+    return OPTA_OK;
 }
 
 template <class T>
@@ -745,6 +804,10 @@ opta_status optA_destroy(opta_handle *h) {
                     h->cand, h->cand_rho, h->topk_v, h->topk_i, h->tf, h->tstage, h->td,
                     h->states, h->weights, h->radius};
     for (void *p : ptrs) if (p) cudaFree(p);
+    if (h->pool) {
+        cudaDeviceSynchronize();   // stream-ordered frees of the preparation have completed
+        cudaMemPoolDestroy(h->pool);
+    }
     cudaSetDevice(cur);
     delete h;
     return OPTA_OK;
@@ -766,6 +829,20 @@ opta_status optA_prepare(const opta_image *img, const opta_params *prm, const in
     opta_handle *H = new (std::nothrow) opta_handle();
     if (!H) return OPTA_ERR_OOM;
     cudaGetDevice(&H->device);
+    {
+        // the preparation's scratch pool keeps its memory between calls
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = H->device;
+        if (cudaMemPoolCreate(&H->pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            delete H;
+            return OPTA_ERR_CUDA;
+        }
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(H->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
     H->prm = P;
     H->p = img->rows;
     H->q = img->cols;
@@ -783,8 +860,11 @@ opta_status optA_prepare(const opta_image *img, const opta_params *prm, const in
     if (e == cudaSuccess) e = launch_integrals32(H->I8, nullptr, p, q, H->IIS32, H->IIQ32, nullptr, s);
     if (e != cudaSuccess) return fail(map_err(e));
     if ((st = setup_tables(H)) != OPTA_OK) return fail(st);
-    for (int i = 0; i < n_sizes; ++i)
-        if ((st = prepare_size(H, sizes_mn[2 * i], sizes_mn[2 * i + 1], s)) != OPTA_OK) return fail(st);
+    {
+        std::vector<std::pair<int, int>> todo;
+        for (int i = 0; i < n_sizes; ++i) todo.emplace_back(sizes_mn[2 * i], sizes_mn[2 * i + 1]);
+        if ((st = prepare_sizes(H, todo, s)) != OPTA_OK) return fail(st);
+    }
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(map_err(e));
     *out = H;
@@ -797,17 +877,13 @@ opta_status optA_search(opta_handle *h, const opta_template *t, int32_t n_t, opt
     if (h->busy) return OPTA_ERR_BUSY;
     BusyGuard guard(h);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    size_t maxL = 0, maxG = 0, maxT = 0;
+    std::vector<std::pair<int, int>> todo;
     for (int i = 0; i < n_t; ++i) {
         if (!valid_template(&t[i], h->p, h->q)) return OPTA_ERR_INVALID_ARG;
-        TRY(prepare_size(h, t[i].rows, t[i].cols, s));
-        SizeState *S = h->sizes[std::make_pair(t[i].rows, t[i].cols)];
-        maxL = std::max(maxL, (size_t)S->Ly * S->Lx);
-        maxG = std::max(maxG, (size_t)S->Gy * S->Gx);
-        maxT = std::max(maxT, (size_t)t[i].rows * ((t[i].cols + 7) & ~7));
+        todo.emplace_back(t[i].rows, t[i].cols);
     }
+    TRY(prepare_sizes(h, todo, s));
     if (n_t == 0) return OPTA_OK;
-    (void)maxL; (void)maxG; (void)maxT;
     TRY(size_scratch(h, t, n_t));
     std::vector<int> order;
     TRY(enqueue_all(h, t, n_t, order, s));
@@ -919,7 +995,7 @@ opta_status optA_debug_maps(opta_handle *h, int32_t m, int32_t n, uint8_t *pivot
 
 opta_status optA_memory_bytes(const opta_handle *h, size_t *bytes) {
     if (!h || !bytes) return OPTA_ERR_INVALID_ARG;
-    *bytes = h->mem.bytes;
+    *bytes = h->mem.bytes.load();
     return OPTA_OK;
 }
 

@@ -267,6 +267,11 @@ int topk_blocks(int G);
 
 // Counts every kernel launch of the library and, when per-kernel timing is
 // enabled (opta_dbg_profile_enable), brackets it with CUDA events on its stream.
+// Raise func's dynamic shared-memory limit to at least `bytes`; *cur holds
+// the limit already set (one per kernel, guarded by a library-wide lock so
+// that host threads may launch concurrently).
+cudaError_t ensure_smem(const void *func, size_t bytes, size_t *cur);
+
 class LaunchScope {
   public:
     LaunchScope(const char *name, cudaStream_t s);

@@ -290,11 +290,9 @@ cudaError_t launch_corr_mma(const uint8_t *V, int p, int q, const void *B, int m
     if (smem + 1024 < floor_req) smem = floor_req - 1024 + 16;
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     static size_t attr = 0;
-    if (smem > attr) {
-        cudaError_t e = cudaFuncSetAttribute(corr_mma_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(corr_mma_kernel), smem, &attr);
         if (e != cudaSuccess) return e;
-        attr = smem;
     }
     CorrMmaArgs a;
     a.V = V; a.p = p; a.q = q;

@@ -548,21 +548,17 @@ cudaError_t launch_rho_co_h(const uint8_t *P, const uint8_t *I, int p, int q, in
     if (!g.ok) return cudaErrorInvalidValue;
     const size_t smem = g.smem;
     static size_t attr = 0;
-    if (smem > attr) {
-        cudaError_t e = cudaFuncSetAttribute(rho_co_kernel<H>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(rho_co_kernel<H>), smem, &attr);
         if (e != cudaSuccess) return e;
-        attr = smem;
     }
     // one wave: strips x bands CTAs fill the SMs once (each CTA slides its
     // band from one initial build, so fewer, taller bands pay it less often)
-    static int bps = 0;
-    if (bps == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, rho_co_kernel<H>, g.threads, smem) !=
-                cudaSuccess || bps < 1) {
-            cudaGetLastError();
-            bps = 1;
-        }
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, rho_co_kernel<H>, g.threads, smem) !=
+            cudaSuccess || bps < 1) {
+        cudaGetLastError();
+        bps = 1;
     }
     const int Gy = groups_along(Ly, H);
     int bands = std::max(1, std::min(Gy, num_sms() * bps / g.strips));
@@ -591,11 +587,9 @@ cudaError_t launch_blur(const uint8_t *I, int p, int q, const uint8_t *level_map
     const int ih = block + 2 * kMaxRadius;
     const size_t smem = (size_t)(ih * ih + ih * block) * sizeof(float);
     static size_t attr = 0;
-    if (smem > attr) {
-        cudaError_t e = cudaFuncSetAttribute(blur_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(blur_kernel), smem, &attr);
         if (e != cudaSuccess) return e;
-        attr = smem;
     }
     LaunchScope ls_blur_kernel("blur_kernel", s);
     blur_kernel<<<dim3(bq, bp), 256, smem, s>>>(I, p, q, level_map, block, weights, radius, P);

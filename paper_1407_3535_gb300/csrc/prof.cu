@@ -57,6 +57,16 @@ LaunchScope::~LaunchScope() {
     g_recs.push_back({name_, static_cast<cudaEvent_t>(a_), b});
 }
 
+cudaError_t ensure_smem(const void *func, size_t bytes, size_t *cur) {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    if (bytes <= *cur) return cudaSuccess;
+    const cudaError_t e =
+        cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) *cur = bytes;
+    return e;
+}
+
 }  // namespace opta
 
 using namespace opta;

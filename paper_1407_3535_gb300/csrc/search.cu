@@ -1246,12 +1246,10 @@ cudaError_t launch_tmpl_prep_batch(const TmplIn *tin, int T, int m, int n, int n
 cudaError_t launch_zncc_map(const uint8_t *I, int p, int q, const float *tf, int m, int n,
                             int npad, const float *inv_sigma, const float *efac128,
                             TmplState *st, float *map, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(zncc_map_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZT_SMEM);
+    static size_t attr = 0;
+    {
+        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(zncc_map_kernel), ZT_SMEM, &attr);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     const int Ly = p - m + 1, Lx = q - n + 1;
     dim3 grid((Lx + ZT_X - 1) / ZT_X, (Ly + ZT_Y - 1) / ZT_Y);
@@ -1304,11 +1302,9 @@ cudaError_t launch_centre_rho(const uint8_t *P, int p, int q, const float *tf, i
     const int tile_rows = (CT_Y - 1) * h + CT_MT;
     const size_t smem = (size_t)(tile_rows * tile_w + CT_MT * CT_NT) * sizeof(float);
     static size_t attr = 0;
-    if (smem > attr) {
-        cudaError_t e = cudaFuncSetAttribute(centre_rho_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(centre_rho_kernel), smem, &attr);
         if (e != cudaSuccess) return e;
-        attr = smem;
     }
     if (gx_begin >= Gx) return cudaSuccess;
     dim3 grid((Gx - gx_begin + CT_X - 1) / CT_X, (Gy + CT_Y - 1) / CT_Y);
@@ -1429,16 +1425,10 @@ cudaError_t launch_survivors(const Scan2Batch &B, const uint8_t *I, int pimg, in
     const int WB = 16 * ((n + 30) / 16);
     const int stage = in_smem && n <= 256 ? 1 : 0;
     if (stage) smem += (size_t)8 * 2 * kStageRows * WB;
-    static std::mutex mu;
     static size_t attr = 0;
     {
-        std::lock_guard<std::mutex> lk(mu);
-        if (smem > attr) {
-            cudaError_t e = cudaFuncSetAttribute(survivors_kernel,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            attr = smem;
-        }
+        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(survivors_kernel), smem, &attr);
+        if (e != cudaSuccess) return e;
     }
     const uint8_t *iend = I + (int64_t)q * pimg;
     // buckets whose largest bound is below the certain lower bound already
@@ -1454,17 +1444,11 @@ cudaError_t launch_survivors(const Scan2Batch &B, const uint8_t *I, int pimg, in
     const int bx = std::max(num_sms(), num_sms() * 4 / std::min(B.T, 4));
     if ((int64_t)m * n <= kLaneMaxMN) {
         const size_t lsmem = ((size_t)m * npad * sizeof(float) + 15) & ~(size_t)15;
-        static std::mutex lmu;
         static size_t lattr = 0;
         {
-            std::lock_guard<std::mutex> lk(lmu);
-            if (lsmem > lattr) {
-                cudaError_t e2 = cudaFuncSetAttribute(survivors_lane_kernel,
-                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      (int)lsmem);
-                if (e2 != cudaSuccess) return e2;
-                lattr = lsmem;
-            }
+            const cudaError_t e2 =
+                ensure_smem(reinterpret_cast<const void *>(survivors_lane_kernel), lsmem, &lattr);
+            if (e2 != cudaSuccess) return e2;
         }
         LaunchScope ls("survivors_lane_kernel", s);
         survivors_lane_kernel<<<dim3(bx, B.T), 256, lsmem, s>>>(B, I, q, Lx, wsum, m, n, npad,
@@ -1493,11 +1477,9 @@ cudaError_t launch_group_members(const uint8_t *I, int q, int Ly, int Lx, int h,
     int in_smem = 0;
     const size_t smem = tmpl_smem(m, npad, &in_smem);
     static size_t attr = 0;
-    if (smem > attr) {
-        cudaError_t e = cudaFuncSetAttribute(group_members_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(group_members_kernel), smem, &attr);
         if (e != cudaSuccess) return e;
-        attr = smem;
     }
     LaunchScope ls("group_members_kernel", s);
     group_members_kernel<<<dim3(topk, T), 256, smem, s>>>(I, q, Ly, Lx, h, wsum, tf, tsz, m, n,

@@ -181,13 +181,12 @@ __global__ void ingest_u8_kernel(const uint8_t *__restrict__ src, int64_t ld, in
 }  // namespace
 
 int num_sms() {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
+    static const int sms = [] {
+        int dev = 0, v = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 132;
-    }
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 132;
+    }();
     return sms;
 }
 
