@@ -32,6 +32,11 @@
 // 4u per accumulation step (one step per MMA) -- see eps_mma below.
 #include <cuda_bf16.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
 #include "common.cuh"
 #include "tc5.cuh"
 
@@ -67,7 +72,7 @@ __device__ inline float eps_mma(int steps, float efac) {
 }
 
 constexpr int kMmaThreads = 256;
-constexpr int kMaxRC = 2;   // 4 fills TMEM (one CTA per SM) and measured slower
+constexpr int kMaxRC = 4;   // centre rows per CTA (the launcher measures 1, 2 and 4)
 
 __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaArgs a) {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -266,6 +271,24 @@ cudaError_t launch_tmpl_split(const float *tf, size_t tsz, int T, int m, int n, 
     return cudaGetLastError();
 }
 
+namespace {
+
+// Centre rows per CTA, in the order preferred before measurement: more rows
+// amortise each pivot row's operand build over more MMAs, fewer leave TMEM
+// room for more resident CTAs.
+constexpr int kRcs[] = {2, 1, 4};
+
+struct MmaTuneKey {
+    int m, n, N, h, p, q;
+    bool operator<(const MmaTuneKey &o) const {
+        return std::tie(m, n, N, h, p, q) < std::tie(o.m, o.n, o.N, o.h, o.p, o.q);
+    }
+};
+std::mutex g_tune_mu;
+std::map<MmaTuneKey, int> g_tuned;   // chosen centre rows per CTA
+
+}  // namespace
+
 cudaError_t launch_corr_mma(const uint8_t *V, int p, int q, const void *B, int m, int n, int Kp,
                             int N, int h, int Ly, int Lx, int T, const float *c_inv_sigma,
                             const float *c_efac, const TmplState *st, float *rho_tc, float2 *tc,
@@ -277,36 +300,81 @@ cudaError_t launch_corr_mma(const uint8_t *V, int p, int q, const void *B, int m
     *Gx_u_out = Gx_u;
     if (Gx_u <= 0) return cudaSuccess;
     if (N % 16 != 0 || N < 16 || N > 256 || Kp % 16 != 0) return cudaErrorInvalidValue;
-    // centre rows per CTA: as many as TMEM (512 columns) and shared memory hold
-    int RC = kMaxRC;
-    while (RC > 1 && (RC * N > 512 || corr_mma_smem(h, Kp, N, RC) > 227 * 1024 || RC > Gy)) RC >>= 1;
-    size_t smem = corr_mma_smem(h, Kp, N, RC);
-    // never more resident CTAs per SM than TMEM can hold (512 columns): pad the
-    // shared-memory request so that 228 KB / (request + 1 KB) <= 512 / ncols
-    int ncols = 32;
-    while (ncols < RC * N) ncols <<= 1;
-    const int max_ctas = 512 / ncols;
-    const size_t floor_req = (size_t)(228 * 1024) / (size_t)(max_ctas + 1) + 1;
-    if (smem + 1024 < floor_req) smem = floor_req - 1024 + 16;
-    if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    static size_t attr = 0;
-    {
-        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(corr_mma_kernel), smem, &attr);
-        if (e != cudaSuccess) return e;
-    }
+    // RC accumulators of N columns within TMEM's 512, shared memory within 227 KB
+    auto fits = [&](int rc) {
+        return rc <= kMaxRC && rc * N <= 512 && rc <= Gy && corr_mma_smem(h, Kp, N, rc) <= 227 * 1024;
+    };
     CorrMmaArgs a;
     a.V = V; a.p = p; a.q = q;
     a.B = static_cast<const __nv_bfloat16 *>(B);
     a.m = m; a.n = n; a.Kp = Kp; a.N = N;
     a.h = h; a.Ly = Ly; a.Lx = Lx; a.Gx = Gx; a.Gx_u = Gx_u;
-    a.Gy = Gy; a.RC = RC;
+    a.Gy = Gy;
     a.T = T;
     a.c_inv_sigma = c_inv_sigma; a.c_efac = c_efac;
     a.st = st; a.rho_tc = rho_tc; a.tc = tc; a.gstride = gstride; a.err = err;
-    dim3 grid((Gx_u + kMmaM - 1) / kMmaM, (Gy + RC - 1) / RC);
-    LaunchScope ls("corr_mma_kernel", s);
-    corr_mma_kernel<<<grid, kMmaThreads, smem, s>>>(a);
-    return cudaGetLastError();
+    auto launch = [&](int rc) -> cudaError_t {
+        size_t smem = corr_mma_smem(h, Kp, N, rc);
+        // never more resident CTAs per SM than TMEM can hold (512 columns):
+        // pad the request so that 228 KB / (request + 1 KB) <= 512 / ncols
+        int ncols = 32;
+        while (ncols < rc * N) ncols <<= 1;
+        const int max_ctas = 512 / ncols;
+        const size_t floor_req = (size_t)(228 * 1024) / (size_t)(max_ctas + 1) + 1;
+        if (smem + 1024 < floor_req) smem = floor_req - 1024 + 16;
+        if (smem > 227 * 1024) return cudaErrorInvalidValue;
+        static size_t attr = 0;
+        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(corr_mma_kernel), smem, &attr);
+        if (e != cudaSuccess) return e;
+        a.RC = rc;
+        dim3 grid((Gx_u + kMmaM - 1) / kMmaM, (Gy + rc - 1) / rc);
+        LaunchScope ls("corr_mma_kernel", s);
+        corr_mma_kernel<<<grid, kMmaThreads, smem, s>>>(a);
+        return cudaGetLastError();
+    };
+    // autotuning: the first launch of a shape times every fitting choice of
+    // RC on the real operands (all write the same output, after one untimed
+    // launch) and keeps the fastest for the launches that follow
+    const MmaTuneKey key{m, n, N, h, p, q};
+    int chosen = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) chosen = it->second;
+    }
+    if (chosen > 0) return launch(chosen);
+    std::vector<int> cand;
+    for (int rc : kRcs)
+        if (fits(rc)) cand.push_back(rc);
+    if (cand.empty()) return cudaErrorInvalidValue;
+    // a stream being captured into a graph cannot be timed: first choice
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        cap = cudaStreamCaptureStatusActive;
+    }
+    if (cand.size() == 1 || cap != cudaStreamCaptureStatusNone) return launch(cand[0]);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = launch(cand[0]);
+    float best = 1e30f;
+    for (int rc : cand) {
+        if (e != cudaSuccess) break;
+        e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = launch(rc);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best) { best = ms; chosen = rc; }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = chosen;
+    return cudaSuccess;   // the measured launches left the output
 }
 
 }  // namespace opta
