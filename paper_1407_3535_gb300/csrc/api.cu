@@ -97,7 +97,6 @@ struct opta_handle {
     size_t capS2 = 0;                         // template slots of the scan-2 arrays (stride capL)
     int *ucnt = nullptr;                      // kScan2MaxT unordered-survivor counters
     float *rho_tc = nullptr;
-    float2 *tc = nullptr;
     int *surv = nullptr;
     float *surv_rho = nullptr, *surv_eps = nullptr, *surv_ub = nullptr;
     int *bucket_cnt = nullptr, *bucket_cur = nullptr;
@@ -496,7 +495,6 @@ opta_status ensure_scratch(opta_handle *H, size_t L, size_t TB, size_t RT, size_
     }
     if (G > H->capG) {
         TRY(grow(H, H->rho_tc, dummy, H->capG, G));
-        TRY(grow(H, H->tc, dummy, H->capG, G));
         H->capG = G;
     }
     if (!H->topk_v) {
@@ -536,6 +534,14 @@ opta_status ensure_scratch(opta_handle *H, size_t L, size_t TB, size_t RT, size_
 }
 
 bool use_mma(const opta_handle *H) { return H->prm.precision == 1; }
+
+// Scan-1 error factor A of an m x n size (e = A * ||P - 128|| / sigma_hat +
+// kScan1EpsB): the largest over the kernels that compute its centres.
+float scan1_eps_factor(const opta_handle *H, int m, int n) {
+    const int npad = (n + 7) & ~7, Kp = (n + 15) & ~15;
+    if (use_mma(H)) return std::max(scan1_epsA_mma(m, Kp), scan1_epsA_fp32(centre_column_kacc(m, n)));
+    return scan1_epsA_fp32(centre_rho_kacc(m, npad));
+}
 
 // Scratch needed by a batch of templates (sizes already prepared).
 opta_status size_scratch(opta_handle *H, const opta_template *t, int n_t) {
@@ -591,16 +597,14 @@ opta_status enqueue_scan1(opta_handle *H, const opta_template *const *t, int n, 
         CK(launch_tmpl_split(H->tf, tsz, n, m, nn, npad, Kp, N, H->Bmma, s));
         int Gx_u = S->Gx;
         CK(launch_corr_mma(S->P, H->p, H->q, H->Bmma, m, nn, Kp, N, S->h, S->Ly, S->Lx, n,
-                           S->c_inv_sigma, S->c_efac, st, H->rho_tc, H->tc, G, H->dev_err,
-                           &Gx_u, s));
+                           S->c_inv_sigma, st, H->rho_tc, G, H->dev_err, &Gx_u, s));
         for (int gx = Gx_u; gx < S->Gx; ++gx)
             CK(launch_centre_column(S->P, H->q, H->tf, m, nn, npad, tsz, S->h, S->Ly, S->Lx, gx, n,
-                                    S->c_inv_sigma, S->c_efac, st, H->rho_tc, H->tc, G, s));
+                                    S->c_inv_sigma, st, H->rho_tc, G, s));
     } else {
         for (int k = 0; k < n; ++k)
             CK(launch_centre_rho(S->P, H->p, H->q, H->tf + k * tsz, m, nn, npad, S->h, S->Ly,
-                                 S->Lx, S->c_inv_sigma, S->c_efac, st + k, H->rho_tc + k * G,
-                                 H->tc + k * G, 0, s));
+                                 S->Lx, S->c_inv_sigma, st + k, H->rho_tc + k * G, 0, s));
     }
     // threshold (Section 6): top-k centres, their exact rho, the members of
     // their groups -- batched over the chunk
@@ -631,8 +635,10 @@ opta_status enqueue_scan2(opta_handle *H, const opta_template *const *t, int n, 
         Scan2Batch B;
         B.T = T;
         B.st = st + k0;
-        B.tc = H->tc + k0 * G;
+        B.rho_tc = H->rho_tc + k0 * G;
         B.tc_stride = G;
+        B.c_efac = S->c_efac;
+        B.epsA = scan1_eps_factor(H, m, nn);
         B.tf = H->tf + k0 * tsz;
         B.tsz = tsz;
         B.surv = H->surv;
@@ -775,7 +781,7 @@ opta_status optA_destroy(opta_handle *h) {
         if (S->P_owned) cudaFree(S->P);
         delete S;
     }
-    void *ptrs[] = {h->I8, h->IIS, h->IIQ, h->rho_tc, h->tc, h->surv, h->surv_rho, h->surv_eps,
+    void *ptrs[] = {h->I8, h->IIS, h->IIQ, h->rho_tc, h->surv, h->surv_rho, h->surv_eps,
                     h->surv_ub, h->ucnt, h->bucket_cnt, h->bucket_cur, h->Bmma, h->dev_err,
                     h->cand_topk, h->cand_rho_topk, h->tin,
                     h->cand, h->cand_rho, h->topk_v, h->topk_i, h->tf, h->tstage, h->td,
@@ -919,7 +925,9 @@ opta_status optA_debug_scan1(opta_handle *h, const opta_template *t, int32_t n_t
     if (rho_dev)
         CK(cudaMemcpyAsync(rho_dev, h->rho_tc, n_t * G * sizeof(float), cudaMemcpyDeviceToDevice, s));
     if (theta_dev)
-        CK(cudaMemcpyAsync(theta_dev, h->tc, n_t * G * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+        CK(launch_centre_intervals(h->rho_tc, (int64_t)G, n_t, S->c_efac,
+                                   scan1_eps_factor(h, t[0].rows, t[0].cols),
+                                   reinterpret_cast<float2 *>(theta_dev), s));
     int herr = 0;
     CK(cudaMemcpyAsync(&herr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

@@ -67,6 +67,26 @@ __device__ inline float2 angle_interval(float r, float e) {
                        acosf(fmaxf(-1.f, r - e)) + kAngMargin);
 }
 
+// Error bounds of scan 1's rho(t, pivot block): e = A * efac + kScan1EpsB,
+// efac = ||P - 128|| / sigma_hat of the centre.  Tensor-core form: the hi/lo
+// bf16 split holds t' to 2^-16 relative and the TMEM FP32 accumulation adds
+// at most 4u per MMA step (m * Kp/16 steps); FP32 CUDA-core forms: k
+// roundings per term.
+__host__ __device__ inline float scan1_epsA_mma(int m, int Kp) {
+    return ((float)(4 * m * (Kp / 16) + 16) * kU32 + 1.55e-5f) * 1.01f;
+}
+__host__ __device__ inline float scan1_epsA_fp32(int k) { return (float)(k + 2) * kU32 * 1.01f; }
+constexpr float kScan1EpsB = 8.f * kU32;
+// roundings per term of the FP32 scan-1 kernels (centre tiles, one column)
+__host__ __device__ inline int centre_rho_kacc(int m, int npad) { return 64 + m * ((npad + 63) / 64) + 1; }
+__host__ __device__ inline int centre_column_kacc(int m, int n) { return m * ((n + 31) / 32) + 6; }
+
+// Angle interval certain to contain acos of a centre's exact rho(t, pivot)
+// (the largest bound over the kernels that compute centres of the size).
+__device__ inline float2 centre_interval(float rho, float efac, float epsA) {
+    return angle_interval(rho, fmaf(epsA, efac, kScan1EpsB));
+}
+
 // Per-template device state, one per template in flight.
 struct TmplState {
     double mu;          // template mean (FP64)
@@ -161,18 +181,20 @@ cudaError_t launch_refine64_topk(const uint8_t *I, int q, int Lx, const double *
 // group columns gx >= gx_begin (FP32 CUDA cores).
 cudaError_t launch_centre_rho(const uint8_t *P, int p, int q, const float *tf, int m, int n,
                               int npad, int h, int Ly, int Lx, const float *c_inv_sigma,
-                              const float *c_efac, TmplState *st, float *rho_tc,
-                              float2 *tc, int gx_begin, cudaStream_t s);
+                              TmplState *st, float *rho_tc, int gx_begin, cudaStream_t s);
 // Tensor-core scan 1 for T same-size templates (planes of B), see corr_mma.cu.
 cudaError_t launch_corr_mma(const uint8_t *V, int p, int q, const void *B, int m, int n, int Kp,
                             int N, int h, int Ly, int Lx, int T, const float *c_inv_sigma,
-                            const float *c_efac, const TmplState *st, float *rho_tc, float2 *tc,
-                            int64_t gstride, int *err, int *Gx_u_out, cudaStream_t s);
+                            const TmplState *st, float *rho_tc, int64_t gstride, int *err,
+                            int *Gx_u_out, cudaStream_t s);
 // rho_tc of one group column for a chunk of templates (warp per centre).
 cudaError_t launch_centre_column(const uint8_t *P, int q, const float *tf, int m, int n, int npad,
                                  size_t tsz, int h, int Ly, int Lx, int gx, int T,
-                                 const float *c_inv_sigma, const float *c_efac, const TmplState *st,
-                                 float *rho_tc, float2 *tc, int64_t gstride, cudaStream_t s);
+                                 const float *c_inv_sigma, const TmplState *st, float *rho_tc,
+                                 int64_t gstride, cudaStream_t s);
+// Angle intervals of scan-1 values (verification output): T x G float2.
+cudaError_t launch_centre_intervals(const float *rho_tc, int64_t G, int T, const float *c_efac,
+                                    float epsA, float2 *out, cudaStream_t s);
 cudaError_t launch_tmpl_split(const float *tf, size_t tsz, int T, int m, int n, int npad, int Kp,
                               int N, void *B, cudaStream_t s);
 // Threshold centres of T templates: rho_tc of template k at k * gstride;
@@ -191,8 +213,10 @@ cudaError_t launch_group_members(const uint8_t *I, int q, int Ly, int Lx, int h,
 struct Scan2Batch {
     int T;
     TmplState *st;                       // T states
-    const float2 *tc;                    // scan-1 angle intervals, template k at k * tc_stride
+    const float *rho_tc;                 // scan-1 rho per centre, template k at k * tc_stride
     int64_t tc_stride;
+    const float *c_efac;                 // per centre: ||P - 128|| / sigma_hat
+    float epsA;                          // scan-1 error bound factor of the size
     const float *tf;                     // FP32 templates (m x npad), k * tsz
     size_t tsz;
     int *surv;                           // survivor lists (bucket order), k * scap

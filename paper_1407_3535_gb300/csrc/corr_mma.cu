@@ -29,7 +29,8 @@
 //
 // Error bound of the numerator: the hi/lo split represents each template
 // value to within 2^-16 relative; FP32 accumulation in TMEM is bounded by
-// 4u per accumulation step (one step per MMA) -- see eps_mma below.
+// 4u per accumulation step (one step per MMA) -- scan1_epsA_mma.  The angle
+// intervals that scan 2 needs are formed there from rho and this bound.
 #include <cuda_bf16.h>
 
 #include <map>
@@ -58,18 +59,12 @@ struct CorrMmaArgs {
     int Gy, RC;                // group rows; centre rows per CTA (1, 2 or 4)
     int T;                     // templates (planes 2t, 2t+1)
     const float *c_inv_sigma;  // per group
-    const float *c_efac;       // per group: ||P - 128|| / sigma_hat
     const TmplState *st;       // T states
     float *rho_tc;             // [T][gstride]
-    float2 *tc;                // [T][gstride]
     int64_t gstride;
     int *err;
 };
 
-__device__ inline float eps_mma(int steps, float efac) {
-    // 2^-16 split error + 4u per TMEM accumulation step + final products
-    return ((float)(4 * steps + 16) * kU32 + 1.55e-5f) * 1.01f * efac + 8.f * kU32;
-}
 
 constexpr int kMmaThreads = 256;
 constexpr int kMaxRC = 4;   // centre rows per CTA (the launcher measures 1, 2 and 4)
@@ -206,11 +201,9 @@ __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaA
         const int i = wl * 32 + lane;                   // TMEM lane = accumulator row
         const int gx = gx0 + i;
         const bool valid = gx < a.Gx_u;
-        const int steps = a.m * (a.Kp / 16);
         for (int k = warp >> 2; k < nrow; k += 2) {
             const int64_t g = (int64_t)(gy0 + k) * a.Gx + gx;
-            float cis = 0.f, cef = 0.f;
-            if (valid) { cis = a.c_inv_sigma[g]; cef = a.c_efac[g]; }
+            const float cis = valid ? a.c_inv_sigma[g] : 0.f;
             for (int c0 = 0; c0 < a.N; c0 += 8) {
                 float v[8];
                 tc5::tmem_ld8(tmem + ((uint32_t)(wl * 32) << 16) + (uint32_t)(k * a.N + c0), v);
@@ -219,10 +212,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaA
                     const int t = (c0 + q2) >> 1;
                     if (valid && t < a.T) {
                         const float num = v[q2] + v[q2 + 1];
-                        const float rr = (num * a.st[t].inv_sigma) * cis;
-                        const float e = cis > 0.f ? eps_mma(steps, cef) : 0.f;
-                        a.rho_tc[t * a.gstride + g] = rr;
-                        a.tc[t * a.gstride + g] = angle_interval(rr, e);
+                        a.rho_tc[t * a.gstride + g] = (num * a.st[t].inv_sigma) * cis;
                     }
                 }
             }
@@ -291,8 +281,8 @@ std::map<MmaTuneKey, int> g_tuned;   // chosen centre rows per CTA
 
 cudaError_t launch_corr_mma(const uint8_t *V, int p, int q, const void *B, int m, int n, int Kp,
                             int N, int h, int Ly, int Lx, int T, const float *c_inv_sigma,
-                            const float *c_efac, const TmplState *st, float *rho_tc, float2 *tc,
-                            int64_t gstride, int *err, int *Gx_u_out, cudaStream_t s) {
+                            const TmplState *st, float *rho_tc, int64_t gstride, int *err,
+                            int *Gx_u_out, cudaStream_t s) {
     const int Gy = groups_along(Ly, h), Gx = groups_along(Lx, h);
     // centres along x are uniform (g*h + (h-1)/2) except possibly the last group
     int Gx_u = Gx;
@@ -311,8 +301,8 @@ cudaError_t launch_corr_mma(const uint8_t *V, int p, int q, const void *B, int m
     a.h = h; a.Ly = Ly; a.Lx = Lx; a.Gx = Gx; a.Gx_u = Gx_u;
     a.Gy = Gy;
     a.T = T;
-    a.c_inv_sigma = c_inv_sigma; a.c_efac = c_efac;
-    a.st = st; a.rho_tc = rho_tc; a.tc = tc; a.gstride = gstride; a.err = err;
+    a.c_inv_sigma = c_inv_sigma;
+    a.st = st; a.rho_tc = rho_tc; a.gstride = gstride; a.err = err;
     auto launch = [&](int rc) -> cudaError_t {
         size_t smem = corr_mma_smem(h, Kp, N, rc);
         // never more resident CTAs per SM than TMEM can hold (512 columns):

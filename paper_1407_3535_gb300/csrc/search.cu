@@ -370,8 +370,8 @@ __device__ inline int centre_kacc(int m, int npad) {
 __global__ void __launch_bounds__(128)
 centre_rho_kernel(const uint8_t *__restrict__ P, int p, int q, const float *__restrict__ tf,
                   int m, int n, int npad, int h, int Ly, int Lx,
-                  const float *__restrict__ c_inv_sigma, const float *__restrict__ c_efac,
-                  TmplState *st, float *rho_tc, float2 *tc, int tile_w, int gx_begin) {
+                  const float *__restrict__ c_inv_sigma, TmplState *st, float *rho_tc,
+                  int tile_w, int gx_begin) {
     extern __shared__ float4 csm4[];
     float *tile = reinterpret_cast<float *>(csm4);
     const int tile_rows = (CT_Y - 1) * h + CT_MT;
@@ -423,7 +423,6 @@ centre_rho_kernel(const uint8_t *__restrict__ P, int p, int q, const float *__re
         const float is = c_inv_sigma[g];
         const float r = (acc * st->inv_sigma) * is;
         rho_tc[g] = r;
-        tc[g] = angle_interval(r, is > 0.f ? eps_bound(centre_kacc(m, npad), c_efac[g]) : 0.f);
     }
 }
 
@@ -433,14 +432,13 @@ centre_rho_kernel(const uint8_t *__restrict__ P, int p, int q, const float *__re
 __global__ void __launch_bounds__(256)
 centre_column_kernel(const uint8_t *__restrict__ P, int q, const float *__restrict__ tf, int m,
                      int n, int npad, size_t tsz, int h, int Ly, int Lx, int gx, int T,
-                     const float *__restrict__ c_inv_sigma, const float *__restrict__ c_efac,
-                     const TmplState *__restrict__ st, float *rho_tc, float2 *tc, int64_t gstride) {
+                     const float *__restrict__ c_inv_sigma,
+                     const TmplState *__restrict__ st, float *rho_tc, int64_t gstride) {
     const int Gy = groups_along(Ly, h), Gx = groups_along(Lx, h);
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int cx = group_centre_of(gx, Lx, h);
-    const int kacc = m * ((n + 31) / 32) + 6;
     for (int w = warp; w < T * Gy; w += nwarps) {
         const int k = w / Gy, gy = w % Gy;
         const int cy = group_centre_of(gy, Ly, h);
@@ -454,9 +452,7 @@ centre_column_kernel(const uint8_t *__restrict__ P, int q, const float *__restri
         if (lane == 0) {
             const int64_t g = (int64_t)gy * Gx + gx;
             const float is = c_inv_sigma[g];
-            const float r = (acc * st[k].inv_sigma) * is;
-            rho_tc[k * gstride + g] = r;
-            tc[k * gstride + g] = angle_interval(r, is > 0.f ? eps_bound(kacc, c_efac[g]) : 0.f);
+            rho_tc[k * gstride + g] = (acc * st[k].inv_sigma) * is;
         }
     }
 }
@@ -668,11 +664,12 @@ bound_pass_kernel(const Scan2Batch B, const float2 *__restrict__ gco,
         __syncthreads();
         const int64_t g = g0 + threadIdx.x;
         const float2 gc = g < G ? gco[g] : make_float2(4.f, -4.f);   // empty group: fails
+        const float cef = g < G ? B.c_efac[g] : 0.f;
         for (int t = 0; t < T; ++t) {
             const float lim = lims[t];
             bool pass = false;
             if (lim >= 0.f && g < G) {
-                const float2 tv = B.tc[t * B.tc_stride + g];
+                const float2 tv = centre_interval(B.rho_tc[t * B.tc_stride + g], cef, B.epsA);
                 pass = fmaxf(tv.x - gc.y, gc.x - tv.y) <= lim;
             }
             const unsigned msk = __ballot_sync(0xffffffffu, pass);
@@ -701,7 +698,8 @@ bound_pass_kernel(const Scan2Batch B, const float2 *__restrict__ gco,
                 const int my = gy * h + mem / h, mx = gx * h + mem % h;
                 if (my < Ly && mx < Lx) {
                     li = my * Lx + mx;
-                    gap = loc_gap(B.tc[t * B.tc_stride + gg], theta_co[li]);
+                    const float2 tv = centre_interval(B.rho_tc[t * B.tc_stride + gg], B.c_efac[gg], B.epsA);
+                    gap = loc_gap(tv, theta_co[li]);
                     f = gap <= lims[t];
                     if (f) {
                         b = gap_bucket(gap, lims[t]);
@@ -827,7 +825,8 @@ __global__ void bound_map_kernel(const Scan2Batch B, const float2 *__restrict__ 
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int y = (int)(i / Lx), x = (int)(i - (int64_t)y * Lx);
-        const float gap = loc_gap(B.tc[(int64_t)(y / h) * Gx + x / h], theta_co[i]);
+        const int64_t g = (int64_t)(y / h) * Gx + x / h;
+        const float gap = loc_gap(centre_interval(B.rho_tc[g], B.c_efac[g], B.epsA), theta_co[i]);
         if (ub_map) ub_map[i] = cosf(gap) + kCosMargin;
         if (surv_map) surv_map[i] = gap <= lim ? 1 : 0;
     }
@@ -1295,8 +1294,7 @@ cudaError_t launch_refine64_topk(const uint8_t *I, int q, int Lx, const double *
 
 cudaError_t launch_centre_rho(const uint8_t *P, int p, int q, const float *tf, int m, int n,
                               int npad, int h, int Ly, int Lx, const float *c_inv_sigma,
-                              const float *c_efac, TmplState *st, float *rho_tc, float2 *tc,
-                              int gx_begin, cudaStream_t s) {
+                              TmplState *st, float *rho_tc, int gx_begin, cudaStream_t s) {
     const int Gy = groups_along(Ly, h), Gx = groups_along(Lx, h);
     const int tile_w = ((CT_X - 1) * h + CT_NT + 3) & ~3;
     const int tile_rows = (CT_Y - 1) * h + CT_MT;
@@ -1310,7 +1308,7 @@ cudaError_t launch_centre_rho(const uint8_t *P, int p, int q, const float *tf, i
     dim3 grid((Gx - gx_begin + CT_X - 1) / CT_X, (Gy + CT_Y - 1) / CT_Y);
     LaunchScope ls_centre_rho_kernel("centre_rho_kernel", s);
     centre_rho_kernel<<<grid, CT_Y * CT_X, smem, s>>>(P, p, q, tf, m, n, npad, h, Ly, Lx,
-                                                     c_inv_sigma, c_efac, st, rho_tc, tc, tile_w,
+                                                     c_inv_sigma, st, rho_tc, tile_w,
                                                      gx_begin);
     return cudaGetLastError();
 }
@@ -1324,12 +1322,12 @@ int topk_blocks(int G) {
 
 cudaError_t launch_centre_column(const uint8_t *P, int q, const float *tf, int m, int n, int npad,
                                  size_t tsz, int h, int Ly, int Lx, int gx, int T,
-                                 const float *c_inv_sigma, const float *c_efac, const TmplState *st,
-                                 float *rho_tc, float2 *tc, int64_t gstride, cudaStream_t s) {
+                                 const float *c_inv_sigma, const TmplState *st, float *rho_tc,
+                                 int64_t gstride, cudaStream_t s) {
     const int Gy = groups_along(Ly, h);
     LaunchScope ls("centre_column_kernel", s);
     centre_column_kernel<<<grid_cap((int64_t)T * Gy * 32, 256, 8), 256, 0, s>>>(
-        P, q, tf, m, n, npad, tsz, h, Ly, Lx, gx, T, c_inv_sigma, c_efac, st, rho_tc, tc, gstride);
+        P, q, tf, m, n, npad, tsz, h, Ly, Lx, gx, T, c_inv_sigma, st, rho_tc, gstride);
     return cudaGetLastError();
 }
 
@@ -1392,6 +1390,23 @@ cudaError_t launch_bound_compact(const Scan2Batch &B, const float2 *theta_co, co
         e = cudaGetLastError();
     }
     return e;
+}
+
+namespace {
+__global__ void centre_intervals_kernel(const float *__restrict__ rho_tc, int64_t G, int T,
+                                        const float *__restrict__ c_efac, float epsA, float2 *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)T * G;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = centre_interval(rho_tc[i], c_efac[i % G], epsA);
+}
+}  // namespace
+
+cudaError_t launch_centre_intervals(const float *rho_tc, int64_t G, int T, const float *c_efac,
+                                    float epsA, float2 *out, cudaStream_t s) {
+    LaunchScope ls("centre_intervals_kernel", s);
+    centre_intervals_kernel<<<grid_cap((int64_t)T * G, 256, 8), 256, 0, s>>>(rho_tc, G, T, c_efac,
+                                                                            epsA, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_theta_co(const float *rho_co, int64_t L, float2 *theta_co, cudaStream_t s) {
