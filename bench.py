@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-brute", action="store_true")
+    ap.add_argument("--case", default=None,
+                    help="one kernel for a profiler capture instead of the benchmark: "
+                         "scan1:<side>, rho_co:<h> or blur_corr:<side> (see run_case)")
     return ap.parse_args()
 
 
@@ -198,8 +201,57 @@ def run_reference(args):
 ALGO = {}   # kernel -> (kind, per-launch work function) filled in main
 
 
+def run_case(spec: str):
+    """Single-kernel cases on the 4096^2 bench image for profiler captures
+    (``ncu -k <kernel> -s <n> -c 1``); each makes the same call twice and the
+    second call's launch is the one to capture.
+
+    scan1:<s>      prepare one s x s size, then search 32 templates of it twice
+                   (the first search also tunes scan 1's tiles: 4 corr_mma
+                   launches precede the second search's one)
+    rho_co:<h>     the auto-correlation map of 64 x 64 windows, group side h
+    blur_corr:<s>  the blur correlation of s x s windows against a sigma = 2 pivot
+    """
+    import torch
+    import paper_1407_3535_gb300 as opta
+
+    kind, _, arg = spec.partition(":")
+    v = int(arg)
+    img = synth.config_image(4)
+    p, q = img.shape
+    I = torch.from_numpy(img).cuda()
+    out = {}
+    if kind == "scan1":
+        ts = [torch.from_numpy(t.data).cuda()
+              for t in synth.make_templates(img, [(v, v)] * 32, seed=99, noise=3.0)]
+        h = opta.optA_prepare(I, opta.opta_params_default(), sizes=[(v, v)])
+        for _ in range(2):
+            res = opta.optA_search(h, ts)
+        out = {"group_h": opta.optA_size_info(h, v, v)["group_h"],
+               "ok": all(r.status == 0 for r in res)}
+        h.close()
+    elif kind == "rho_co":
+        R = torch.empty((p - 63) * (q - 63), dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            c = opta.opta_dbg_rho_co(I, I, 64, 64, v, R)
+        out = {"retained": c}
+    elif kind == "blur_corr":
+        P = torch.empty_like(I)
+        opta.opta_dbg_blur(I, np.full(((p + 63) // 64, (q + 63) // 64), 2.0), 64, P)
+        R = torch.empty((p - v + 1) * (q - v + 1), dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            opta.opta_dbg_blur_corr(P, I, v, v, R)
+        out = {"min_R": float(R.min())}
+    else:
+        raise SystemExit(f"unknown case {spec!r}")
+    torch.cuda.synchronize()
+    print(json.dumps({"case": spec, **out}))
+
+
 def main():
     args = parse()
+    if args.case:
+        return run_case(args.case)
     if args.impl == "reference":
         return run_reference(args)
     import torch
@@ -332,6 +384,10 @@ def main():
         hh.close()
     e2e_value = L_all / float(np.mean(e2e_times)) if world == 1 else L_step / float(np.mean(e2e_times)) * world
 
+    # the literal mode (Section 4.3) on the same batch: its speed, and how far
+    # its answers land from the exact maxima found above
+    literal = literal_report(opta, dimg, dts, sizes, res_prof, stream, flush, L_step)
+
     # exhaustive GPU search on the same GPU (a sample of templates, one per size)
     brute = None
     if not args.no_brute:
@@ -405,6 +461,7 @@ def main():
                               "mean_best": float(np.mean([r.rho for r in res_prof])),
                               "min_best": float(np.min([r.rho for r in res_prof]))},
         "brute_force": brute,
+        "literal_mode": literal,
         "kernels_ms": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
         "prepare_kernels_ms": {k: [round(v[0], 3), v[1]] for k, v in
                                sorted(prof_prep.items(), key=lambda kv: -kv[1][0])},
@@ -419,6 +476,39 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def literal_report(opta, dimg, dts, sizes, exact, stream, flush, L_step):
+    """One warm-up and one timed step (prepare + search, L2 flushed) of the
+    literal mode; localisation error = Chebyshev distance in pixels between
+    its answer and the exact maximum, a miss = any non-zero error."""
+    import torch
+    prm = opta.opta_params_default()
+    prm.literal = 1
+    h = opta.optA_prepare(dimg, prm, sizes=sizes, stream=stream)
+    opta.optA_search(h, dts, stream=stream)
+    h.close()
+    flush.zero_()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e2 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h = opta.optA_prepare(dimg, prm, sizes=sizes, stream=stream)
+    e1.record(stream)
+    res = opta.optA_search(h, dts, stream=stream)
+    e2.record(stream)
+    e2.synchronize()
+    h.close()
+    ms = e0.elapsed_time(e2)
+    err = np.array([max(abs(r.y - e.y), abs(r.x - e.x)) for r, e in zip(res, exact)])
+    hat = np.array([max(abs(r.y_hat - e.y), abs(r.x_hat - e.x)) for r, e in zip(res, exact)])
+    loss = np.array([e.rho - r.rho for r, e in zip(res, exact)])
+    return {"value": L_step / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms,
+            "split_ms": {"prepare": e0.elapsed_time(e1), "search": e1.elapsed_time(e2)},
+            "miss_rate": float(np.mean(err > 0)),
+            "loc_err_px": {"mean": float(err.mean()), "max": int(err.max())},
+            "blurred_max_err_px": {"mean": float(hat.mean()), "max": int(hat.max())},
+            "rho_loss": {"mean": float(loss.mean()), "max": float(loss.max())},
+            "rematch_d": sorted({int(r.rematch_d) for r in res})}
 
 
 # Templates of at most this many pixels have their survivors evaluated one

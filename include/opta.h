@@ -93,6 +93,12 @@ typedef struct opta_result {
     double rho_threshold;  /* scan-1 threshold (max exact rho over the threshold centres) */
     int32_t group_h;       /* group side h (1 for zncc_full) */
     int32_t status;        /* opta_status of this template */
+    int32_t y_hat, x_hat;  /* maximum on the image the search ran on: the blurred
+                              pivot in the literal mode (Section 4.3), before the
+                              local re-match on I; equal to (y, x) otherwise */
+    int32_t rematch_d;     /* half-width d of the re-match neighbourhood (literal
+                              mode: ceil(3 sigma_max) of the accepted blur map); 0 otherwise */
+    int32_t reserved;
 } opta_result;
 
 /* Method parameters (Section 7 defaults via opta_params_default). */
@@ -109,7 +115,14 @@ typedef struct opta_params {
     int32_t topk;           /* 8: centres re-evaluated on I for the threshold (1..16) */
     int32_t precision;      /* scan 1 (centre rho): 1 = bf16 hi/lo split products on the
                                tensor cores, FP32 accumulation (default); 0 = FP32 CUDA cores */
-    int32_t reserved[7];
+    int32_t literal;        /* 0 (default): exact search of I with blurred pivots bounding it.
+                               1: the procedure of Section 4.3 -- EGS measures the blurred
+                               image's own auto-correlation, the pruned search finds the
+                               exact maximum on the blurred image Î, and t is then matched
+                               with I in FP64 over the (2d+1) x (2d+1) neighbourhood of that
+                               location, d = ceil(3 sigma_max) of the accepted blur map.
+                               Fast but not exact: the result may miss the maximum on I. */
+    int32_t reserved[6];
 } opta_params;
 
 typedef struct opta_handle opta_handle;

@@ -20,7 +20,14 @@ answer; they are written here in the paper's order for diagnostic parity:
 * ``blur_corr_map``   -- R_oo of Algorithm 3.
 * ``rho_co_map``      -- Algorithm 1 (pivot = blurred centre block).
 * ``egs``             -- Algorithm 2 with Eq. co's retained count.
-* ``opta``            -- Algorithm 3 under the readings listed in the design doc.
+* ``opta``            -- Algorithm 3 under the readings stated in its docstring.
+
+The paper's own procedure (Section 4.3), which searches the blurred image
+and re-matches locally, is written out too (``opta_literal``,
+``literal_search``).  Its answer is not the exact maximum in general; it is
+pinned through the cases where it must be (no blur, or a neighbourhood that
+covers every location), and how far it lands from the maximum otherwise is
+measured, not pinned (the paper's images are not available).
 """
 from __future__ import annotations
 
@@ -274,11 +281,12 @@ DEFAULT_LEVELS = (0.5, 1.0, 2.0, 3.0)
 
 
 def opta(I, m, n, rho_th=0.8, rho_max=0.95, xi=0.005, block=64,
-         levels=DEFAULT_LEVELS, h_max=9, threads=0):
+         levels=DEFAULT_LEVELS, h_max=9, threads=0, literal=False):
     """Algorithm 3 under the reading: level k raises every still-active block to
     sigma_k; a block whose windows (by top-left, non-flat I windows only) reach
     a blur-correlation below lambda (Eq. misDec) reverts to its previous sigma
     and is frozen; the level is kept if EGS's cost falls by more than xi.
+    With literal=True, EGS measures rho(P, P) (see ``opta_literal``).
 
     Returns dict(sigma_map, pivot (uint8), h, cost, trace)."""
     I = np.asarray(I, dtype=np.float64)
@@ -288,7 +296,7 @@ def opta(I, m, n, rho_th=0.8, rho_max=0.95, xi=0.005, block=64,
     sig = np.zeros((bp, bq))
     frozen = np.zeros((bp, bq), dtype=bool)
     P = quantise_pivot(I)
-    h, cost = egs(P, I, m, n, 1, rho_th, xi, h_max, threads)
+    h, cost = egs(P, P if literal else I, m, n, 1, rho_th, xi, h_max, threads)
     trace = [dict(level=0, sigma=0.0, h=h, cost=cost, frozen=0)]
     flat = flat_windows(I, m, n)
     Ly, Lx = p - m + 1, q - n + 1
@@ -308,10 +316,44 @@ def opta(I, m, n, rho_th=0.8, rho_max=0.95, xi=0.005, block=64,
         new_frozen = frozen | fail
         if fail.any():
             Pk = quantise_pivot(blur(I, new_sig, block, threads))
-        hk, ck = egs(Pk, I, m, n, h, rho_th, xi, h_max, threads)
+        hk, ck = egs(Pk, Pk if literal else I, m, n, h, rho_th, xi, h_max, threads)
         trace.append(dict(level=k, sigma=s, h=hk, cost=ck, frozen=int(new_frozen.sum())))
         if cost - ck > xi * cost:
             sig, frozen, P, h, cost = new_sig, new_frozen, Pk, hk, ck
         else:
             break
     return dict(sigma_map=sig, pivot=P, h=h, cost=cost, trace=trace)
+
+
+# ---------------------------------------------------------------------------
+# Section 4.3 as printed: search the blurred image, re-match locally on I
+# ---------------------------------------------------------------------------
+def opta_literal(I, m, n, **kw):
+    """Algorithm 3 as Section 4.3 uses it: EGS measures the blurred image's own
+    auto-correlation, rho(centre window of P, member window of P), instead of
+    the pivot form rho(P, I).  Same level loop and return value as ``opta``."""
+    return opta(I, m, n, literal=True, **kw)
+
+
+def literal_support(sigma_map) -> int:
+    """Half-width d of the re-match neighbourhood: the blur support (Section
+    4.3 uses the (2d+1) x (2d+1) filter size) of the largest sigma applied."""
+    s = float(np.max(sigma_map)) if np.size(sigma_map) else 0.0
+    return blur_support(s)
+
+
+def literal_search(I, P, t, d, threads=0):
+    """Section 4.3: the best match of t on the blurred image P (exact argmax
+    over P, ties to the lowest row-major index), then t matched with I in the
+    (2d+1) x (2d+1) neighbourhood of that location (clipped to the location
+    grid), FP64, same tie rule.  Returns (y, x, rho on I, y_hat, x_hat)."""
+    rP = zncc_map(P, t, threads)
+    yh, xh, _ = argmax_first(rP)
+    Ly, Lx = rP.shape
+    y0, y1 = max(0, yh - d), min(Ly, yh + d + 1)
+    x0, x1 = max(0, xh - d), min(Lx, xh + d + 1)
+    ys, xs = np.meshgrid(np.arange(y0, y1), np.arange(x0, x1), indexing="ij")
+    vals = rho_at(I, t, ys.ravel(), xs.ravel(), threads).reshape(ys.shape)
+    wy, wx, best = argmax_first(vals)
+    return y0 + wy, x0 + wx, best, yh, xh
+

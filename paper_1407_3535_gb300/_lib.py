@@ -35,17 +35,18 @@ class OptaResult(ctypes.Structure):
     _fields_ = [("y", c_int32), ("x", c_int32), ("rho", c_double),
                 ("n_locations", c_int64), ("n_centres", c_int64), ("n_survivors", c_int64),
                 ("n_candidates", c_int64), ("n_evaluated", c_int64), ("rho_threshold", c_double),
-                ("group_h", c_int32), ("status", c_int32)]
+                ("group_h", c_int32), ("status", c_int32), ("y_hat", c_int32),
+                ("x_hat", c_int32), ("rematch_d", c_int32), ("reserved", c_int32)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
 class OptaParams(ctypes.Structure):
     _fields_ = [("rho_th", c_double), ("rho_max", c_double), ("xi", c_double),
                 ("block", c_int32), ("n_levels", c_int32), ("sigma_levels", c_float * 8),
                 ("h_max", c_int32), ("fixed_h", c_int32), ("blur", c_int32), ("topk", c_int32),
-                ("precision", c_int32), ("reserved", c_int32 * 7)]
+                ("precision", c_int32), ("literal", c_int32), ("reserved", c_int32 * 6)]
 
 
 class OptaSizeInfo(ctypes.Structure):

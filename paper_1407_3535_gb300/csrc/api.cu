@@ -79,6 +79,14 @@ struct SizeState {
     float *c_inv_sigma = nullptr;  // G
     float *c_efac = nullptr;       // G
     std::vector<float> sigma_map;
+    // The image the search runs on (its members) with its window statistics:
+    // I with wsum / inv_sigma, or in the literal mode (Section 4.3) the
+    // accepted pivot with statistics of its own (owned when M_owned).
+    const uint8_t *M = nullptr;
+    int *wsumM = nullptr;
+    float *invM = nullptr;
+    bool M_owned = false;
+    int d = 0;                     // literal mode: half-width of the re-match on I
 };
 
 }  // namespace
@@ -133,6 +141,7 @@ bool valid_params(const opta_params &p) {
     if (p.fixed_h < 0 || p.fixed_h > 9 || (p.fixed_h > 0 && p.fixed_h % 2 == 0)) return false;
     if (p.topk < 1 || p.topk > kTopkMax) return false;
     if (p.precision != 0 && p.precision != 1) return false;
+    if (p.literal != 0 && p.literal != 1) return false;
     return true;
 }
 
@@ -212,19 +221,31 @@ struct PrepScratch {
     int *fail = nullptr;
     uint8_t *lvl = nullptr;
     unsigned long long *count = nullptr;
+    // literal mode: integral images and window statistics of a candidate pivot
+    long long *IIS = nullptr, *IIQ = nullptr;
+    int *wsumP = nullptr;
+    float *invP = nullptr;
 };
 
-opta_status egs_cost(opta_handle *H, SizeState *S, const uint8_t *P, int h,
+// Members of the auto-correlation EGS measures: image M (I, or the candidate
+// pivot itself in the literal mode) with its window sums and 1/Omega.
+struct Members {
+    const uint8_t *M;
+    const int *wsum;
+    const float *inv;
+};
+
+opta_status egs_cost(opta_handle *H, SizeState *S, const uint8_t *P, const Members &M, int h,
                      unsigned long long *dcount, long long *cost, cudaStream_t s) {
     const float cut = (float)std::sqrt(1.0 - H->prm.rho_th * H->prm.rho_th);
     CK(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), s));
-    if (h == 1 && P == H->I8) {
-        // unblurred pivots, one location per group: every member is its own
-        // centre, rho_co = 1 except on flat windows (rho_co = 0 there), so
-        // the retained count is the number of flat windows
-        CK(launch_count_zero(S->inv_sigma, (int64_t)S->Ly * S->Lx, dcount, s));
+    if (h == 1 && P == M.M) {
+        // pivots equal to the members, one location per group: every member
+        // is its own centre, rho_co = 1 except on flat windows (rho_co = 0
+        // there), so the retained count is the number of flat windows
+        CK(launch_count_zero(M.inv, (int64_t)S->Ly * S->Lx, dcount, s));
     } else {
-        CK(launch_rho_co(P, H->I8, H->p, H->q, S->m, S->n, h, S->wsum, S->inv_sigma, cut,
+        CK(launch_rho_co(P, M.M, H->p, H->q, S->m, S->n, h, M.wsum, M.inv, cut,
                          nullptr, dcount, nullptr, nullptr, s));
     }
     unsigned long long c = 0;
@@ -244,15 +265,15 @@ int h_limit(int p, int q, int m, int n, int hmax) {
 }
 
 // Algorithm 2: grow h by 2 while the cost drops by more than xi of the last.
-opta_status egs(opta_handle *H, SizeState *S, const uint8_t *P, int h_start,
+opta_status egs(opta_handle *H, SizeState *S, const uint8_t *P, const Members &M, int h_start,
                 unsigned long long *dcount, int *h_out, long long *c_out, cudaStream_t s) {
     const int hmax = h_limit(H->p, H->q, S->m, S->n, H->prm.h_max);
     int h = std::min(h_start, hmax);
     long long c = 0;
-    TRY(egs_cost(H, S, P, h, dcount, &c, s));
+    TRY(egs_cost(H, S, P, M, h, dcount, &c, s));
     while (h + 2 <= hmax) {
         long long c2 = 0;
-        TRY(egs_cost(H, S, P, h + 2, dcount, &c2, s));
+        TRY(egs_cost(H, S, P, M, h + 2, dcount, &c2, s));
         if ((double)(c - c2) > H->prm.xi * (double)c) { h += 2; c = c2; }
         else break;
     }
@@ -297,10 +318,14 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
         return cudaMallocFromPoolAsync(reinterpret_cast<void **>(ptr), bytes, H->pool, s);
     };
     auto cleanup = [&](opta_status st) {
-        void *bufs[] = {W.Pcur, W.Pacc, W.fail, W.lvl, W.count};
+        void *bufs[] = {W.Pcur, W.Pacc, W.fail, W.lvl, W.count, W.IIS, W.IIQ, W.wsumP, W.invP};
         for (void *b : bufs)
             if (b) cudaFreeAsync(b, s);
         if (st != OPTA_OK) {
+            if (S->M_owned) {
+                H->mem.release(S->wsumM, L);
+                H->mem.release(S->invM, L);
+            }
             H->mem.release(S->inv_sigma, L);
             H->mem.release(S->wsum, L);
             H->mem.release(S->rho_co, L);
@@ -320,6 +345,20 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     PTRY(H->mem.alloc(&S->wsum, L));
     PCK(launch_window_stats(H->IIS, H->IIQ, p, q, m, n, S->inv_sigma, nullptr, s, S->wsum));
     PCK(scratch(&W.count, sizeof(unsigned long long)));
+    const bool literal = prm.literal != 0;
+    const Members on_image{H->I8, S->wsum, S->inv_sigma};
+    const size_t nII = (size_t)(p + 1) * (q + 1);
+    // literal mode: window statistics of pivot P into (wsum, inv) via scratch integrals
+    auto pivot_stats = [&](const uint8_t *P, int *wsum, float *inv) -> cudaError_t {
+        if (!W.IIS) {
+            cudaError_t e = scratch(&W.IIS, nII * sizeof(long long));
+            if (e == cudaSuccess) e = scratch(&W.IIQ, nII * sizeof(long long));
+            if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = launch_integrals(P, nullptr, p, q, W.IIS, W.IIQ, nullptr, s);
+        if (e == cudaSuccess) e = launch_window_stats(W.IIS, W.IIQ, p, q, m, n, inv, nullptr, s, wsum);
+        return e;
+    };
 
     // Level 0: unblurred pivots (P = I).
     int h_best = 1;
@@ -328,7 +367,7 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     if (prm.fixed_h > 0) {
         h_best = std::min(prm.fixed_h, h_limit(p, q, m, n, 9));
     } else {
-        PTRY(egs(H, S, H->I8, 1, W.count, &h_best, &c_best, s));
+        PTRY(egs(H, S, H->I8, on_image, 1, W.count, &h_best, &c_best, s));
     }
     int level_best = 0;
     if (prm.blur && prm.n_levels > 0 && prm.fixed_h == 0) {
@@ -361,7 +400,18 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
             if (any) PTRY(blur_to(H, W, cand, W.Pcur, s));
             int hk = 0;
             long long ck = 0;
-            PTRY(egs(H, S, W.Pcur, h_best, W.count, &hk, &ck, s));
+            if (literal) {
+                // Section 4.3: the cost is that of searching the blurred image,
+                // so EGS measures its own auto-correlation
+                if (!W.wsumP) {
+                    PCK(scratch(&W.wsumP, (size_t)L * sizeof(int)));
+                    PCK(scratch(&W.invP, (size_t)L * sizeof(float)));
+                }
+                PCK(pivot_stats(W.Pcur, W.wsumP, W.invP));
+                PTRY(egs(H, S, W.Pcur, Members{W.Pcur, W.wsumP, W.invP}, h_best, W.count, &hk, &ck, s));
+            } else {
+                PTRY(egs(H, S, W.Pcur, on_image, h_best, W.count, &hk, &ck, s));
+            }
             if ((double)(c_best - ck) > prm.xi * (double)c_best) {
                 cur_level = cand;
                 frozen = new_frozen;
@@ -392,11 +442,29 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
         S->P_owned = true;
         PCK(cudaMemcpyAsync(S->P, W.Pacc, (size_t)p * q, cudaMemcpyDeviceToDevice, s));
     }
+    S->M = H->I8;
+    S->wsumM = S->wsum;
+    S->invM = S->inv_sigma;
+    if (literal) {
+        float smax = 0.f;
+        for (float v : S->sigma_map) smax = std::max(smax, v);
+        S->d = smax > 0.f ? (int)std::ceil(3.0 * (double)smax) : 0;
+        if (!best_is_image) {
+            // the search runs on the accepted pivot, with its own statistics
+            S->M = S->P;
+            S->wsumM = nullptr;
+            S->invM = nullptr;
+            S->M_owned = true;
+            PTRY(H->mem.alloc(&S->wsumM, L));
+            PTRY(H->mem.alloc(&S->invM, L));
+            PCK(pivot_stats(S->P, S->wsumM, S->invM));
+        }
+    }
     PTRY(H->mem.alloc(&S->rho_co, L));
     PTRY(H->mem.alloc(&S->theta_co, L));
     PTRY(H->mem.alloc(&S->c_inv_sigma, G));
     PTRY(H->mem.alloc(&S->c_efac, G));
-    PCK(launch_rho_co(S->P, H->I8, p, q, m, n, S->h, S->wsum, S->inv_sigma, 0.f, S->rho_co,
+    PCK(launch_rho_co(S->P, S->M, p, q, m, n, S->h, S->wsumM, S->invM, 0.f, S->rho_co,
                       nullptr, S->c_inv_sigma, S->c_efac, s));
     PCK(launch_theta_co(S->rho_co, L, S->theta_co, s));
     PTRY(H->mem.alloc(&S->gco, G));
@@ -610,10 +678,10 @@ opta_status enqueue_scan1(opta_handle *H, const opta_template *const *t, int n, 
     // their groups -- batched over the chunk
     CK(launch_topk(H->rho_tc, G, S->Gy, S->Gx, S->h, S->Ly, S->Lx, H->prm.topk, n, st, H->topk_v,
                    H->topk_i, H->cand_topk, s));
-    CK(launch_refine64_topk(H->I8, H->q, S->Lx, H->td, dsz, m, nn, n, st, H->cand_topk,
+    CK(launch_refine64_topk(S->M, H->q, S->Lx, H->td, dsz, m, nn, n, st, H->cand_topk,
                             H->cand_rho_topk, s));
-    CK(launch_group_members(H->I8, H->q, S->Ly, S->Lx, S->h, S->wsum, H->tf, tsz, m, nn,
-                            npad, S->inv_sigma, n, st, H->cand_topk, H->prm.topk, s));
+    CK(launch_group_members(S->M, H->q, S->Ly, S->Lx, S->h, S->wsumM, H->tf, tsz, m, nn,
+                            npad, S->invM, n, st, H->cand_topk, H->prm.topk, s));
     CK(launch_threshold(st, H->cand_rho_topk, n, s));
     return OPTA_OK;
 }
@@ -652,12 +720,20 @@ opta_status enqueue_scan2(opta_handle *H, const opta_template *const *t, int n, 
         B.bucket_cnt = H->bucket_cnt;
         B.bucket_cur = H->bucket_cur;
         CK(launch_bound_compact(B, S->theta_co, S->gco, S->Ly, S->Lx, S->h, ub_map, surv_map, s));
-        CK(launch_survivors(B, H->I8, H->p, H->q, S->Lx, S->wsum, m, nn, npad, S->inv_sigma, s));
+        CK(launch_survivors(B, S->M, H->p, H->q, S->Lx, S->wsumM, m, nn, npad, S->invM, s));
         CK(launch_surv_candidates(B, s));
-        CK(launch_refine64(H->I8, H->q, S->Lx, H->td + k0 * dsz, dsz, m, nn, T, st + k0, H->cand,
+        CK(launch_refine64(S->M, H->q, S->Lx, H->td + k0 * dsz, dsz, m, nn, T, st + k0, H->cand,
                            H->cand_rho, scap, s));
         CK(launch_final_argmax(T, st + k0, H->cand, H->cand_rho, scap, H->cand_topk + k0 * kTopkMax,
                                H->cand_rho_topk + k0 * kTopkMax, s));
+        if (H->prm.literal) {
+            // Section 4.3: t matched with I in FP64 over the (2d+1)^2
+            // neighbourhood of the maximum found on the blurred image
+            CK(launch_rematch_window(T, st + k0, S->Ly, S->Lx, S->d, H->cand, scap, s));
+            CK(launch_refine64(H->I8, H->q, S->Lx, H->td + k0 * dsz, dsz, m, nn, T, st + k0,
+                               H->cand, H->cand_rho, scap, s));
+            CK(launch_final_argmax(T, st + k0, H->cand, H->cand_rho, scap, nullptr, nullptr, s));
+        }
     }
     return OPTA_OK;
 }
@@ -695,7 +771,7 @@ void fill_result(const TmplState &st, const SizeState *S, int Lx, int64_t L, int
     r->group_h = h;
     r->n_centres = n_centres;
     r->n_survivors = st.n_surv;
-    r->n_candidates = st.n_cand;
+    r->n_candidates = st.n_cand + st.n_cand_search;
     r->n_evaluated = st.n_eval;
     r->rho_threshold = st.thr;
     if (st.flat) {
@@ -706,8 +782,11 @@ void fill_result(const TmplState &st, const SizeState *S, int Lx, int64_t L, int
     r->y = st.best_idx / Lx;
     r->x = st.best_idx % Lx;
     r->rho = st.best_rho;
+    const int hat = st.hat_idx >= 0 ? st.hat_idx : st.best_idx;
+    r->y_hat = hat / Lx;
+    r->x_hat = hat % Lx;
+    r->rematch_d = st.hat_idx >= 0 ? S->d : 0;
     r->status = st.overflow ? OPTA_ERR_CUDA : OPTA_OK;
-    (void)S;
 }
 
 struct BusyGuard {
@@ -779,6 +858,7 @@ opta_status optA_destroy(opta_handle *h) {
         cudaFree(S->gco);
         cudaFree(S->c_inv_sigma); cudaFree(S->c_efac);
         if (S->P_owned) cudaFree(S->P);
+        if (S->M_owned) { cudaFree(S->wsumM); cudaFree(S->invM); }
         delete S;
     }
     void *ptrs[] = {h->I8, h->IIS, h->IIQ, h->rho_tc, h->surv, h->surv_rho, h->surv_eps,

@@ -106,6 +106,8 @@ struct TmplState {
     int n_eval;               // survivors evaluated (not skipped by the running threshold)
     float theta_lim;          // survive iff angular gap <= theta_lim (from thr_lo)
     int n_surv_eff;           // survivors past this index are known to be skippable
+    int hat_idx;              // literal mode: maximum on the blurred image (-1 otherwise)
+    int n_cand_search;        // literal mode: candidates of the search before the re-match
 };
 
 // Survivors are bucketed by their upper bound (bucket 0 = highest) so that
@@ -171,6 +173,9 @@ cudaError_t launch_refine64(const uint8_t *I, int q, int Lx, const double *td, s
 cudaError_t launch_final_argmax(int T, TmplState *st, const int *cand, const double *cand_rho,
                                 int64_t ccap, const int *cand_topk, const double *cand_rho_topk,
                                 cudaStream_t s);
+// Literal mode: candidates := the (2d+1)^2 neighbourhood of best_idx.
+cudaError_t launch_rematch_window(int T, TmplState *st, int Ly, int Lx, int d, int *cand,
+                                  int64_t ccap, cudaStream_t s);
 // FP64 rho at the threshold centres of T templates (kTopkMax slots each).
 cudaError_t launch_refine64_topk(const uint8_t *I, int q, int Lx, const double *td, size_t dsz,
                                  int m, int n, int T, TmplState *st, const int *cand_topk,

@@ -189,6 +189,8 @@ extern "C" opta_status zncc_full_noalloc(const opta_image *img, const opta_templ
     best->y = hs.best_idx / Lx;
     best->x = hs.best_idx % Lx;
     best->rho = hs.best_rho;
+    best->y_hat = best->y;
+    best->x_hat = best->x;
     best->status = hs.overflow ? OPTA_ERR_CUDA : OPTA_OK;
     return (opta_status)best->status;
 }

@@ -104,6 +104,8 @@ tmpl_prep_kernel(const float *__restrict__ t, int64_t ld, const TmplIn *__restri
         st->overflow = 0;
         st->n_eval = 0;
         st->n_surv_eff = 0x7fffffff;
+        st->hat_idx = -1;
+        st->n_cand_search = 0;
     }
 }
 
@@ -353,6 +355,30 @@ final_argmax_kernel(TmplState *st, const int *__restrict__ cand,
     if (threadIdx.x == 0) {
         if (st->flat || si[0] == 0x7fffffff) { st->best_idx = 0; st->best_rho = 0.0; }
         else { st->best_idx = si[0]; st->best_rho = sv[0]; }
+    }
+}
+
+// Literal mode (Section 4.3): the maximum found on the blurred image becomes
+// hat_idx, and the candidates are replaced by its (2d+1) x (2d+1)
+// neighbourhood clipped to the location grid, in row-major order (so the
+// final argmax's lowest-index tie rule is the row-major one).  One block per
+// template of a batch; ccap >= Ly * Lx.
+__global__ void __launch_bounds__(256)
+rematch_window_kernel(TmplState *st, int Ly, int Lx, int d, int *cand, int64_t ccap) {
+    st += blockIdx.x;
+    cand += blockIdx.x * ccap;
+    if (st->flat) return;
+    const int c = st->best_idx;
+    const int yc = c / Lx, xc = c - yc * Lx;
+    const int y0 = max(0, yc - d), y1 = min(Ly, yc + d + 1);
+    const int x0 = max(0, xc - d), x1 = min(Lx, xc + d + 1);
+    const int w = x1 - x0, cnt = (y1 - y0) * w;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) cand[i] = (y0 + i / w) * Lx + x0 + i % w;
+    __syncthreads();   // every thread has read best_idx before it is replaced
+    if (threadIdx.x == 0) {
+        st->hat_idx = c;
+        st->n_cand_search = st->n_cand;
+        st->n_cand = cnt;
     }
 }
 
@@ -1280,6 +1306,14 @@ cudaError_t launch_final_argmax(int T, TmplState *st, const int *cand, const dou
                                 cudaStream_t s) {
     LaunchScope ls_final_argmax_kernel("final_argmax_kernel", s);
     final_argmax_kernel<<<T, 256, 0, s>>>(st, cand, cand_rho, ccap, cand_topk, cand_rho_topk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rematch_window(int T, TmplState *st, int Ly, int Lx, int d, int *cand,
+                                  int64_t ccap, cudaStream_t s) {
+    if (d < 0 || (int64_t)(2 * d + 1) * (2 * d + 1) > ccap) return cudaErrorInvalidValue;
+    LaunchScope ls("rematch_window_kernel", s);
+    rematch_window_kernel<<<T, 256, 0, s>>>(st, Ly, Lx, d, cand, ccap);
     return cudaGetLastError();
 }
 

@@ -306,3 +306,64 @@ def test_opta_invariants():
     # rho_max = rho_th gives lambda = 1: no block may ever be blurred
     res1 = ref.opta(img, 16, 16, rho_th=0.8, rho_max=0.8)
     assert np.all(res1["sigma_map"] == 0.0)
+
+
+# ---------------------------------------------------------------------------
+# Section 4.3: search on the blurred image, local re-match on I
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("s,d", [(0.0, 0), (0.5, 2), (1.0, 3), (2.0, 6), (3.0, 9)])
+def test_literal_support_is_filter_half_width(s, d):
+    smap = np.array([[0.0, s], [0.0, 0.0]])
+    assert ref.literal_support(smap) == d
+
+
+def test_literal_search_reduces_to_exact_search():
+    img = synth.aerial_image(96, n_octaves=5, n_prims=8, seed=21).astype(np.float64)
+    t = img[30:42, 50:61] + np.random.default_rng(2).normal(0, 3.0, (12, 11))
+    y, x, r = ref.best_match(img, t)
+    # no blur and no neighbourhood: the search on P = I is the exact search
+    assert ref.literal_search(img, ref.quantise_pivot(img), t, 0)[:3] == (y, x, r)
+    # a neighbourhood covering every location: exact whatever P is
+    P = ref.quantise_pivot(ref.blur(img, np.full((2, 2), 3.0), 64))
+    Ly, Lx = img.shape[0] - 11, img.shape[1] - 10
+    assert ref.literal_search(img, P, t, max(Ly, Lx))[:3] == (y, x, r)
+
+
+def test_literal_search_stays_in_the_neighbourhood():
+    img = synth.aerial_image(96, n_octaves=5, n_prims=8, seed=22).astype(np.float64)
+    P = ref.quantise_pivot(ref.blur(img, np.full((2, 2), 2.0), 64))
+    t = img[60:76, 10:26].copy()
+    y, x, r, yh, xh = ref.literal_search(img, P, t, 3)
+    # (y_hat, x_hat) is the exact maximum on P; (y, x) the best of I within d
+    assert (yh, xh) == ref.best_match(P, t)[:2]
+    assert abs(y - yh) <= 3 and abs(x - xh) <= 3
+    assert r == ref.rho_at(img, t, [y], [x])[0]
+    ys, xs = np.meshgrid(np.arange(max(0, yh - 3), yh + 4), np.arange(max(0, xh - 3), xh + 4), indexing="ij")
+    assert r >= ref.rho_at(img, t, ys.ravel(), xs.ravel()).max()
+
+
+def test_opta_literal_measures_the_pivot_auto_correlation(monkeypatch):
+    """EGS in the literal mode receives the candidate pivot on both sides."""
+    img = synth.aerial_image(128, n_octaves=5, n_prims=8, seed=23).astype(np.float64)
+    seen = []
+    real = ref.egs
+
+    def spy(P, I, *a, **k):
+        seen.append((P, I))
+        return real(P, I, *a, **k)
+
+    monkeypatch.setattr(ref, "egs", spy)
+    res = ref.opta_literal(img, 16, 16)
+    assert len(seen) >= 2 and all(a is b for a, b in seen)
+    assert res["pivot"].dtype == np.uint8
+    seen.clear()
+    ref.opta(img, 16, 16)
+    assert all(b is not a for a, b in seen[1:])
+
+
+def test_opta_literal_without_blur_is_opta():
+    """lambda = 1 forbids every blur, so P = I and both modes measure rho(I, I)."""
+    img = synth.aerial_image(128, n_octaves=5, n_prims=8, seed=24).astype(np.float64)
+    a = ref.opta_literal(img, 16, 16, rho_th=0.8, rho_max=0.8)
+    b = ref.opta(img, 16, 16, rho_th=0.8, rho_max=0.8)
+    assert np.all(a["sigma_map"] == 0) and a["h"] == b["h"] and a["cost"] == b["cost"]
