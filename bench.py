@@ -210,7 +210,8 @@ def run_case(spec: str):
                    (the first search also tunes scan 1's tiles: 4 corr_mma
                    launches precede the second search's one)
     rho_co:<h>     the auto-correlation map of 64 x 64 windows, group side h
-    blur_corr:<s>  the blur correlation of s x s windows against a sigma = 2 pivot
+    blur_corr:<s>  the lambda test of s x s windows against a sigma = 2 pivot
+                   (blur correlation, block flags only, as in the preparation)
     """
     import torch
     import paper_1407_3535_gb300 as opta
@@ -238,10 +239,10 @@ def run_case(spec: str):
     elif kind == "blur_corr":
         P = torch.empty_like(I)
         opta.opta_dbg_blur(I, np.full(((p + 63) // 64, (q + 63) // 64), 2.0), 64, P)
-        R = torch.empty((p - v + 1) * (q - v + 1), dtype=torch.float32, device="cuda")
+        F = torch.empty(((p + 63) // 64) * ((q + 63) // 64), dtype=torch.int32, device="cuda")
         for _ in range(2):
-            opta.opta_dbg_blur_corr(P, I, v, v, R)
-        out = {"min_R": float(R.min())}
+            opta.opta_dbg_blur_corr(P, I, v, v, None, lam=0.947350, block=64, fail_dev=F)
+        out = {"failed_blocks": int(F.sum())}
     else:
         raise SystemExit(f"unknown case {spec!r}")
     torch.cuda.synchronize()

@@ -33,10 +33,16 @@ opta_status opta_dbg_blur(const uint8_t *I_dev, int32_t p, int32_t q,
                           uint8_t *P_dev, void *stream);
 
 /* Blur correlation R_oo(x) = rho(P window at x, I window at x)
- * (Algorithm 3); R_dev receives (p-m+1)(q-n+1) floats. */
+ * (Algorithm 3); R_dev (nullable if fail_dev is given) receives
+ * (p-m+1)(q-n+1) floats.  If fail_dev is
+ * not null it receives the lambda test (Eq. misDec) per block of
+ * block x block locations by top-left (ceil(p/block) x ceil(q/block)
+ * int32, row-major): 1 where a window with a non-flat I block has
+ * R_oo < lambda, else 0. */
 opta_status opta_dbg_blur_corr(const uint8_t *P_dev, const uint8_t *I_dev,
                                int32_t p, int32_t q, int32_t m, int32_t n,
-                               float *R_dev, void *stream);
+                               float *R_dev, float lambda, int32_t block,
+                               int32_t *fail_dev, void *stream);
 
 /* Pivot auto-correlation (Algorithm 1 with the pivot block read from P):
  * rco_dev[x] = rho(P window at the centre of x's group, I window at x) for
@@ -61,6 +67,11 @@ opta_status optA_debug_maps(opta_handle *h, int32_t m, int32_t n,
  * angle interval [lo, hi] certain to contain acos of the exact value. */
 opta_status optA_debug_scan1(opta_handle *h, const opta_template *t, int32_t n_t,
                              float *rho_dev, float *theta_dev, void *stream);
+
+/* The kernels' int64 -> float conversion (FP32 pipe, no 64-bit conversion
+ * instruction) applied to n device values: out_dev[i] = v_dev[i] rounded to
+ * the nearest float (ties to even) for |v| < 2^46, within 1 ulp beyond. */
+opta_status opta_dbg_i64_to_f32(const int64_t *v_dev, float *out_dev, int64_t n, void *stream);
 
 /* Number of kernel launches the library has issued in this process. */
 uint64_t opta_dbg_launch_count(void);

@@ -18,7 +18,7 @@ __all__ = [
     "OptaError", "opta_params_default", "optA_prepare", "optA_search", "zncc_full",
     "zncc_full_noalloc",
     "optA_debug_bounds", "optA_size_info", "optA_memory_bytes", "optA_destroy",
-    "optA_debug_maps", "opta_dbg_window_stats", "opta_dbg_blur", "opta_dbg_blur_corr",
+    "optA_debug_maps", "opta_dbg_window_stats", "opta_dbg_blur", "opta_dbg_blur_corr", "opta_dbg_i64_to_f32",
     "opta_dbg_rho_co", "opta_dbg_launch_count", "opta_dbg_profile_enable",
     "opta_dbg_profile_read", "optA_debug_scan1", "Handle", "lib", "OptaResult",
 ]
@@ -264,10 +264,19 @@ def opta_dbg_blur(I_dev, sigma_map, block: int, P_dev, stream=None):
                                c_void_p(P_dev.data_ptr()), _stream(stream)), "opta_dbg_blur")
 
 
-def opta_dbg_blur_corr(P_dev, I_dev, m: int, n: int, R_dev, stream=None):
+def opta_dbg_i64_to_f32(v_dev, out_dev, stream=None):
+    _check(lib().opta_dbg_i64_to_f32(c_void_p(v_dev.data_ptr()), c_void_p(out_dev.data_ptr()),
+                                     v_dev.numel(), _stream(stream)), "opta_dbg_i64_to_f32")
+
+
+def opta_dbg_blur_corr(P_dev, I_dev, m: int, n: int, R_dev, lam: float = 0.0, block: int = 64,
+                       fail_dev=None, stream=None):
     p, q = I_dev.shape
     _check(lib().opta_dbg_blur_corr(c_void_p(P_dev.data_ptr()), c_void_p(I_dev.data_ptr()),
-                                    p, q, m, n, c_void_p(R_dev.data_ptr()), _stream(stream)),
+                                    p, q, m, n, c_void_p(R_dev.data_ptr() if R_dev is not None else 0),
+                                    c_float(lam), block,
+                                    c_void_p(fail_dev.data_ptr() if fail_dev is not None else 0),
+                                    _stream(stream)),
            "opta_dbg_blur_corr")
 
 

@@ -79,13 +79,14 @@ SIGNATURES = {
     "opta_dbg_blur": (c_int32, [c_void_p, c_int32, c_int32, POINTER(c_float), c_int32, c_void_p,
                                 c_void_p]),
     "opta_dbg_blur_corr": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32,
-                                     c_void_p, c_void_p]),
+                                     c_void_p, c_float, c_int32, c_void_p, c_void_p]),
     "opta_dbg_rho_co": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32,
                                   c_void_p, c_double, POINTER(c_int64), c_void_p]),
     "optA_debug_maps": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p,
                                   POINTER(c_float), c_void_p]),
     "optA_debug_scan1": (c_int32, [c_void_p, POINTER(OptaTemplate), c_int32, c_void_p, c_void_p,
                                    c_void_p]),
+    "opta_dbg_i64_to_f32": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p]),
     "opta_dbg_launch_count": (ctypes.c_uint64, []),
     "opta_dbg_profile_enable": (None, [c_int32]),
     "opta_dbg_profile_read": (c_int32, [ctypes.c_char_p, c_int32, POINTER(c_double),

@@ -1199,10 +1199,22 @@ opta_status opta_dbg_blur(const uint8_t *I_dev, int32_t p, int32_t q, const floa
     return OPTA_OK;
 }
 
+opta_status opta_dbg_i64_to_f32(const int64_t *v_dev, float *out_dev, int64_t n, void *stream) {
+    if (n < 0 || (n > 0 && (!v_dev || !out_dev))) return OPTA_ERR_INVALID_ARG;
+    if (n == 0) return OPTA_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(launch_i64_to_f32(reinterpret_cast<const long long *>(v_dev), out_dev, n, s));
+    CK(cudaStreamSynchronize(s));
+    return OPTA_OK;
+}
+
 opta_status opta_dbg_blur_corr(const uint8_t *P_dev, const uint8_t *I_dev, int32_t p, int32_t q,
-                               int32_t m, int32_t n, float *R_dev, void *stream) {
-    if (!P_dev || !I_dev || !R_dev || p < 1 || q < 1 || m < 1 || n < 1 || m > p || n > q)
+                               int32_t m, int32_t n, float *R_dev, float lambda, int32_t block,
+                               int32_t *fail_dev, void *stream) {
+    if (!P_dev || !I_dev || (!R_dev && !fail_dev) || p < 1 || q < 1 || m < 1 || n < 1 || m > p ||
+        n > q)
         return OPTA_ERR_INVALID_ARG;
+    if (fail_dev && (block < 1 || block > 4096)) return OPTA_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t nII = (size_t)(p + 1) * (q + 1);
     const size_t L = (size_t)(p - m + 1) * (q - n + 1);
@@ -1215,8 +1227,12 @@ opta_status opta_dbg_blur_corr(const uint8_t *P_dev, const uint8_t *I_dev, int32
     CK(cudaMallocAsync(&ws, L * sizeof(int), s));
     cudaError_t e = launch_integrals(I_dev, nullptr, p, q, b[0], b[1], nullptr, s);
     if (e == cudaSuccess) e = launch_window_stats(b[0], b[1], p, q, m, n, inv, nullptr, s, ws);
+    if (e == cudaSuccess && fail_dev)
+        e = cudaMemsetAsync(fail_dev, 0,
+                            sizeof(int32_t) * ((p + block - 1) / block) * ((q + block - 1) / block), s);
     if (e == cudaSuccess)
-        e = launch_blur_corr(P_dev, I_dev, ws, inv, p, q, m, n, 0.f, 64, nullptr, R_dev, s);
+        e = launch_blur_corr(P_dev, I_dev, ws, inv, p, q, m, n, lambda, fail_dev ? block : 64,
+                             fail_dev, R_dev, s);
     for (auto &x : b) cudaFreeAsync(x, s);
     cudaFreeAsync(inv, s);
     cudaFreeAsync(ws, s);

@@ -34,11 +34,30 @@ __device__ inline long long ii_box(const long long *__restrict__ II, int64_t q1,
 }
 
 
+// int64 -> FP32 on the FP32 pipe.  The 64-bit integer conversion runs on
+// the FP64 pipe, which GB300 has little of; here the value is split into
+// two 22-bit chunks and a signed top chunk, each converted exactly by the
+// magic-number method (an integer c with |c| < 2^22 added to the bit pattern
+// of 1.5 * 2^23 gives the float 1.5 * 2^23 + c; Hacker's Delight, 2nd ed.,
+// section 17-2), then summed.  The upper sum is exact for |v| < 2^46 (a
+// multiple of 2^22 below 2^46 has at most 24 significant bits), so the
+// result is v correctly rounded there; beyond, two roundings (< 1 ulp).
+__device__ __forceinline__ float i64_to_f32(long long v) {
+    constexpr float kMagic = 12582912.f;                            // 1.5 * 2^23
+    const unsigned lo = (unsigned)v & 0x3fffffu;                     // bits 0 .. 21
+    const unsigned mid = (unsigned)(v >> 22) & 0x3fffffu;            // bits 22 .. 43
+    const int hi = (int)(v >> 44);                                   // bits 44 .. 63 (signed)
+    const float flo = __uint_as_float(0x4b400000u + lo) - kMagic;
+    const float fmid = __uint_as_float(0x4b400000u + mid) - kMagic;
+    const float fhi = __int_as_float(0x4b400000 + hi) - kMagic;
+    return fmaf(fhi, 17592186044416.f, fmid * 4194304.f) + flo;     // 2^44, 2^22
+}
+
 // mn * Q - S * S (= mn^2 * variance) of a window of mn 8-bit pixels with sum S
 // and square sum Q, as FP32.  Exact in int64 up to 2^23 pixels (the product
 // stays below 2^62); larger windows take it from FP64 products.
 __device__ inline float win_var(long long mn, long long S, long long Q) {
-    if (mn <= (1ll << 23)) return (float)(mn * Q - S * S);
+    if (mn <= (1ll << 23)) return i64_to_f32(mn * Q - S * S);
     return (float)((double)mn * (double)Q - (double)S * (double)S);
 }
 
@@ -138,6 +157,8 @@ cudaError_t launch_window_stats(const long long *IIS, const long long *IIQ, int 
                                 cudaStream_t s, int *wsum = nullptr);
 
 // count += number of zeros in x[0, n) (count is not cleared).
+// out[i] = i64_to_f32(v[i]) (the conversion the kernels use; tested alone).
+cudaError_t launch_i64_to_f32(const long long *v, float *out, int64_t n, cudaStream_t s);
 cudaError_t launch_count_zero(const float *x, int64_t n, unsigned long long *count,
                               cudaStream_t s);
 

@@ -272,27 +272,35 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
 
     // image rows [r0, r0 + cnt) into their ring slots: columns across the
     // threads; a thread's rows are independent loads, issued together
-    auto ring_put = [&](int rr, int col, uint8_t v) {
-        const int slot = (rr + R) % RING;
+    auto ring_put = [&](int slot, int col, uint8_t v) {
         ring8[(col * CSW + (slot >> 2)) * 4 + (slot & 3)] = v;
     };
     auto img_at = [&](int rr, int col) {
         return I[(int64_t)min(max(rr, 0), p - 1) * q + min(max(cx0 - R + col, 0), q - 1)];
     };
     auto load_rows = [&](int r0, int cnt) {          // any cnt (the initial fill)
+        const int slot0 = (r0 + R) % RING;
         for (int col = threadIdx.x; col < RW; col += blockDim.x) {
+            int slot = slot0;
 #pragma unroll 4
-            for (int k = 0; k < cnt; ++k) ring_put(r0 + k, col, img_at(r0 + k, col));
+            for (int k = 0; k < cnt; ++k) {
+                ring_put(slot, col, img_at(r0 + k, col));
+                slot = slot + 1 == RING ? 0 : slot + 1;
+            }
         }
     };
     auto load_step = [&](int r0, int cnt) {          // cnt <= H rows of one slide batch
+        const int slot0 = (r0 + R) % RING;
         for (int col = threadIdx.x; col < RW; col += blockDim.x) {
             uint8_t v[H];
 #pragma unroll
             for (int k = 0; k < H; ++k) v[k] = k < cnt ? img_at(r0 + k, col) : (uint8_t)0;
+            int slot = slot0;
 #pragma unroll
-            for (int k = 0; k < H; ++k)
-                if (k < cnt) ring_put(r0 + k, col, v[k]);
+            for (int k = 0; k < H; ++k) {
+                if (k < cnt) ring_put(slot, col, v[k]);
+                slot = slot + 1 == RING ? 0 : slot + 1;
+            }
         }
     };
     const int jc = cx0 + j;
@@ -333,6 +341,20 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
         for (int sgi = s1; sgi < (c2 >> SG::LGSL); ++sgi) X += segrow[sgi];
         return X;
     };
+
+    // constants of this thread's first emission task (centre gxi, shift
+    // column sxi): its member column and the scanned-row addresses of its
+    // centre's n pivot columns; further tasks (n < H only) take the loop
+    const int t0_gxi = (int)threadIdx.x / H, t0_sxi = (int)threadIdx.x - t0_gxi * H;
+    int t0_mx, t0_c1;
+    bool t0_ok;
+    {
+        const int gx = gx0 + t0_gxi;
+        const int cxg = group_centre_of(gx, Lx, H);
+        t0_mx = cxg + t0_sxi - R;
+        t0_ok = (int)threadIdx.x < ngx * H && t0_mx >= gx * H && t0_mx < min(gx * H + H, Lx);
+        t0_c1 = cxg - cx0;
+    }
 
     int r = group_centre_of(gy0, Ly, H);
     load_rows(r - R, m + 2 * R + 1);
@@ -432,13 +454,13 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
                 const long long var = mn * Qp - Sp * Sp;   // exact
                 cS[threadIdx.x] = (int)Sp;
                 // 1 / (mn Omega_hat) = sqrt(mn / var) / mn
-                const float fmn = (float)mn, fv = (float)var;
+                const float fmn = i64_to_f32(mn), fv = i64_to_f32(var);
                 cI[threadIdx.x] = var > 0 ? sqrtf(fmn / fv) / fmn : 0.f;
                 if (c_inv_sigma) {
                     // per-centre statistics of scan 1: 1/sigma_hat and ||P - 128|| / sigma_hat
                     const int64_t g = (int64_t)gy * Gx + gx;
                     c_inv_sigma[g] = var > 0 ? sqrtf(fmn / fv) : 0.f;
-                    c_efac[g] = var > 0 ? sqrtf(fmn * (float)(Qp - 256 * Sp + 16384 * mn) / fv) : 0.f;
+                    c_efac[g] = var > 0 ? sqrtf(fmn * i64_to_f32(Qp - 256 * Sp + 16384 * mn) / fv) : 0.f;
                 }
             }
         }
@@ -463,25 +485,27 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
             // columns [c1, c1 + n); rho = (mn X - S_hat S) / (mn Omega_hat
             // Omega): exact integer numerator, FP32 finish (flat windows have
             // 1/Omega = 0 -> 0)
-            for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
+            if (t0_ok) {
+                const unsigned X = window(hb + t0_sxi * SG::RS, sb + t0_sxi * SG::NSEG, t0_c1);
+                const int ws = tws[syi * RcoCfg<H>::MAXT + threadIdx.x];
+                const float iw = tiw[syi * RcoCfg<H>::MAXT + threadIdx.x];
+                const long long num = mn * (long long)X - (long long)cS[t0_gxi] * (long long)ws;
+                const float rho = (i64_to_f32(num) * iw) * cI[t0_gxi];
+                if (rco) rco[(int64_t)my * Lx + t0_mx] = rho;
+                if (rho < cut) ++local;
+            }
+            for (int task = threadIdx.x + blockDim.x; task < ntask; task += blockDim.x) {
                 const int gxi = task / H, sxi = task - gxi * H;
                 const int gx = gx0 + gxi;
                 const int cxg = group_centre_of(gx, Lx, H);
                 const int mx = cxg + sxi - R;
                 if (mx < gx * H || mx >= min(gx * H + H, Lx)) continue;
                 const int64_t li = (int64_t)my * Lx + mx;
-                int ws;
-                float iw;
-                if (task == (int)threadIdx.x) {
-                    ws = tws[syi * RcoCfg<H>::MAXT + threadIdx.x];
-                    iw = tiw[syi * RcoCfg<H>::MAXT + threadIdx.x];
-                } else {
-                    ws = wsum[li];
-                    iw = inv_sigma[li];
-                }
+                const int ws = wsum[li];
+                const float iw = inv_sigma[li];
                 const unsigned X = window(hb + sxi * SG::RS, sb + sxi * SG::NSEG, cxg - cx0);
                 const long long num = mn * (long long)X - (long long)cS[gxi] * (long long)ws;
-                const float rho = ((float)num * iw) * cI[gxi];
+                const float rho = (i64_to_f32(num) * iw) * cI[gxi];
                 if (rco) rco[li] = rho;
                 if (rho < cut) ++local;
             }
@@ -496,70 +520,119 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
 // R_oo(x) = rho(P window, I window) at every location (Algorithm 3) and the
 // lambda test, straight from P and I.  A CTA takes a strip of output columns
 // (one thread per input column: the strip's n - 1 extra columns included)
-// and a band of output rows; each thread slides its column's sums of P, P^2
-// and P*I down the window rows, kBcRows output rows per round, and the
-// window sums over n columns come from segmented prefix scans as in the
-// auto-correlation kernel.  I's window statistics come from the window-sum
-// and 1/Omega maps.
-constexpr int kBcRows = 8;
-constexpr int kBcThreads = 1024;
+// and a band of output rows.  Each thread slides its column's sums of P, P^2
+// and P*I down the window rows, kBcRows output rows per round, into shared
+// memory; one warp then turns each such row into running sums along the
+// strip (32 consecutive columns per lane, rows padded to 33 words per lane
+// so that the lanes' accesses fall in distinct banks), and each window sum
+// over n columns is the difference of two running sums (modulo 2^32: the
+// window sums themselves fit in 32 bits).  I's window statistics come from
+// the window-sum and 1/Omega maps, copied to shared memory (cp.async) for a
+// round's rows while its sums slide and are scanned; the slide's image bytes
+// of a round are loaded together, four rows per register.
+constexpr int kBcRows = 10;                  // output rows per round (3 scanned rows each)
+constexpr int kBcThreads = 1024;             // input columns per strip at most
+constexpr int kBcLaneW = 33;                 // words per lane in a scanned row
+constexpr int kBcRS = 32 * kBcLaneW;         // words per scanned row
+
+__device__ __forceinline__ int bc_addr(int c) { return (c >> 5) * kBcLaneW + (c & 31); }
+
+constexpr size_t kBcSmem = (size_t)3 * kBcRows * kBcRS * sizeof(unsigned) +   // scanned rows
+                           (size_t)2 * kBcRows * kBcThreads * sizeof(int);        // member statistics
 
 __global__ void __launch_bounds__(kBcThreads, 1)
 blur_corr_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int p, int q,
                  int m, int n, int Ly, int Lx, const int *__restrict__ wsum,
                  const float *__restrict__ inv_sigma, int WO, int BR, float lambda, int block,
                  int *fail, float *R) {
-    using SG = RcoScan<1>;   // scan geometry for up to 1024 columns
-    extern __shared__ unsigned bcs[];
-    unsigned *hb = bcs;                                  // 3 * kBcRows rows x RS
-    unsigned *sb = bcs + 3 * kBcRows * SG::RS;           // 3 * kBcRows rows x NSEG
+    extern __shared__ unsigned bcs[];        // 3 * kBcRows rows x kBcRS
+    int *tws = reinterpret_cast<int *>(bcs + 3 * kBcRows * kBcRS);          // [kBcRows][kBcThreads]
+    float *tiw = reinterpret_cast<float *>(tws + kBcRows * kBcThreads);     // [kBcRows][kBcThreads]
     const int x0 = blockIdx.x * WO, y0 = blockIdx.y * BR;
     if (x0 >= Lx || y0 >= Ly) return;
     const int wo = min(WO, Lx - x0), y1 = min(Ly, y0 + BR);
-    const int W = wo + n - 1;                            // input columns of the strip
+    const int W = wo + n - 1;                // input columns of the strip
     const int j = threadIdx.x, lane = j & 31, warp = j >> 5, nwarps = blockDim.x >> 5;
     const bool active = j < W;
     const int xc = x0 + j;
     const long long mn = (long long)m * n;
+    const float fmn = i64_to_f32(mn);
     const int bq = (q + block - 1) / block;
-    const int addr_j = rco_addr<1>(j);
+    const int aj = bc_addr(j);
+    const int lane_cnt = W - 32 * lane;      // columns of the strip held by this lane in a scan
+    // lambda test: one flag per thread and block row (the thread's x is fixed)
+    const int bx = (x0 + j) / block;
+    int by = y0 / block, by_end = (by + 1) * block;
+    bool failed = false;
     // column sums over the window rows [y, y + m)
     unsigned sp = 0u, sq = 0u, sx = 0u;
     if (active) {
-        for (int u = 0; u < m; ++u) {
-            const unsigned pv = P[(int64_t)(y0 + u) * q + xc], iv = I[(int64_t)(y0 + u) * q + xc];
+        const uint8_t *pc = P + (int64_t)y0 * q + xc, *ic = I + (int64_t)y0 * q + xc;
+#pragma unroll 8
+        for (int u = 0; u < m; ++u, pc += q, ic += q) {
+            const unsigned pv = *pc, iv = *ic;
             sp += pv;
             sq += pv * pv;
             sx += pv * iv;
         }
     }
+    constexpr int kBcW = (kBcRows + 3) / 4;  // packed words per slid image row set
     for (int yr = y0; yr < y1; yr += kBcRows) {
         const int nr = min(kBcRows, y1 - yr);
-        // the sums of rows yr .. yr + nr - 1, sliding between them
+        // member statistics of the round's locations, copied while the sums slide
+        if (j < wo) {
+            for (int k = 0; k < nr; ++k) {
+                const int64_t li = (int64_t)(yr + k) * Lx + x0 + j;
+                cp_async4(tws + k * kBcThreads + j, wsum + li);
+                cp_async4(tiw + k * kBcThreads + j, inv_sigma + li);
+            }
+        }
+        cp_async_commit();
+        // the column sums of rows yr .. yr + nr - 1, sliding between them
+        // (nsl steps: not past the band's last row)
+        const int nsl = min(nr, y1 - 1 - yr);
+        if (active) {
+            const uint8_t *pa = P + (int64_t)(yr + m) * q + xc, *ia = I + (int64_t)(yr + m) * q + xc;
+            const uint8_t *po = P + (int64_t)yr * q + xc, *io = I + (int64_t)yr * q + xc;
+            unsigned wa[kBcW], wai[kBcW], wo_[kBcW], woi[kBcW];
 #pragma unroll
-        for (int k = 0; k < kBcRows; ++k) {
-            if (k < nr && active) {
-                hb[(3 * k) * SG::RS + addr_j] = sp;
-                hb[(3 * k + 1) * SG::RS + addr_j] = sq;
-                hb[(3 * k + 2) * SG::RS + addr_j] = sx;
-                const int y = yr + k;
-                if (y + 1 < y1) {
-                    const unsigned pa = P[(int64_t)(y + m) * q + xc], ia = I[(int64_t)(y + m) * q + xc];
-                    const unsigned po = P[(int64_t)y * q + xc], io = I[(int64_t)y * q + xc];
-                    sp += pa - po;
-                    sq += pa * pa - po * po;
-                    sx += pa * ia - po * io;
+            for (int w = 0; w < kBcW; ++w) wa[w] = wai[w] = wo_[w] = woi[w] = 0u;
+#pragma unroll
+            for (int k = 0; k < kBcRows; ++k) {
+                if (k < nsl) {
+                    const int sh = 8 * (k & 3);
+                    wa[k >> 2] |= (unsigned)pa[(int64_t)k * q] << sh;
+                    wai[k >> 2] |= (unsigned)ia[(int64_t)k * q] << sh;
+                    wo_[k >> 2] |= (unsigned)po[(int64_t)k * q] << sh;
+                    woi[k >> 2] |= (unsigned)io[(int64_t)k * q] << sh;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kBcRows; ++k) {
+                if (k < nr) {
+                    bcs[(3 * k) * kBcRS + aj] = sp;
+                    bcs[(3 * k + 1) * kBcRS + aj] = sq;
+                    bcs[(3 * k + 2) * kBcRS + aj] = sx;
+                    const int sh = 8 * (k & 3);
+                    const unsigned a = (wa[k >> 2] >> sh) & 255u, ai = (wai[k >> 2] >> sh) & 255u;
+                    const unsigned o = (wo_[k >> 2] >> sh) & 255u, oi = (woi[k >> 2] >> sh) & 255u;
+                    sp += a - o;             // zero past the slid rows
+                    sq += a * a - o * o;
+                    sx += a * ai - o * oi;
                 }
             }
         }
         __syncthreads();
-        for (int item = warp; item < 3 * nr * SG::NSEG; item += nwarps) {
-            const int row = item / SG::NSEG, seg = item - row * SG::NSEG;
-            unsigned *lp = hb + row * SG::RS + (seg * 32 + lane) * SG::PLS;
-            const int c0 = seg * SG::SL + lane * SG::PL;
+        // running sums along each row, one warp per row
+        for (int row = warp; row < 3 * nr; row += nwarps) {
+            unsigned *lp = bcs + row * kBcRS + lane * kBcLaneW;
+            unsigned v[32];
             unsigned tot = 0u;
 #pragma unroll
-            for (int i = 0; i < SG::PL; ++i) tot += (c0 + i < W) ? lp[i] : 0u;
+            for (int i = 0; i < 32; ++i) {
+                v[i] = i < lane_cnt ? lp[i] : 0u;
+                tot += v[i];
+            }
             unsigned inc = tot;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -568,46 +641,47 @@ blur_corr_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, i
             }
             unsigned run = inc - tot;
 #pragma unroll
-            for (int i = 0; i < SG::PL; ++i) {
-                run += (c0 + i < W) ? lp[i] : 0u;
+            for (int i = 0; i < 32; ++i) {
+                run += v[i];
                 lp[i] = run;
             }
-            if (lane == 31) sb[row * SG::NSEG + seg] = inc;
         }
+        cp_async_wait_all();   // this thread's member statistics (read by this thread only)
         __syncthreads();
         if (j < wo) {
             const int x = x0 + j;
-            const int c2 = j + n - 1;
-            const int s1 = j > 0 ? (j - 1) >> SG::LGSL : 0, s2 = c2 >> SG::LGSL;
-            const int a2 = rco_addr<1>(c2), a1 = j > 0 ? rco_addr<1>(j - 1) : -1;
+            const int a2 = bc_addr(j + n - 1), a1 = j > 0 ? bc_addr(j - 1) : 0;
+            const unsigned keep = j > 0 ? 0xffffffffu : 0u;   // running sum before column 0 is 0
             for (int k = 0; k < nr; ++k) {
-                unsigned win[3];
-#pragma unroll
-                for (int t = 0; t < 3; ++t) {
-                    const unsigned *row = hb + (3 * k + t) * SG::RS;
-                    const unsigned *srow = sb + (3 * k + t) * SG::NSEG;
-                    unsigned v = row[a2];
-                    if (a1 >= 0) v -= row[a1];
-                    for (int sgi = s1; sgi < s2; ++sgi) v += srow[sgi];
-                    win[t] = v;
-                }
+                const unsigned *r0 = bcs + (3 * k) * kBcRS;
+                const unsigned Sp = r0[a2] - (r0[a1] & keep);
+                const unsigned Qp = r0[kBcRS + a2] - (r0[kBcRS + a1] & keep);
+                const unsigned X = r0[2 * kBcRS + a2] - (r0[2 * kBcRS + a1] & keep);
                 const int y = yr + k;
                 const int64_t i = (int64_t)y * Lx + x;
-                const long long Sp = win[0], Qp = win[1], X = win[2];
-                const long long dA = mn * Qp - Sp * Sp;                   // exact
-                const long long num = mn * X - Sp * (long long)wsum[i];   // exact
-                const float iw = inv_sigma[i];                            // 0: flat I window
+                const long long dA = mn * (long long)Qp - (long long)Sp * Sp;   // exact
+                const long long num = mn * (long long)X - (long long)Sp * tws[k * kBcThreads + j];   // exact
+                const float iw = tiw[k * kBcThreads + j];                    // 0: flat I window
                 float r = 0.f;
-                if (dA > 0 && iw > 0.f)
-                    r = ((float)num * iw) * (sqrtf((float)mn / (float)dA) / (float)mn);
+                if (dA > 0 && iw > 0.f) r = (i64_to_f32(num) * iw) * rsqrtf(i64_to_f32(dA) * fmn);
                 if (R) R[i] = r;
-                if (fail && iw > 0.f && r < lambda) {
-                    int *f = fail + (y / block) * bq + (x / block);
-                    if (*f == 0) atomicOr(f, 1);
+                if (y >= by_end) {
+                    if (failed && fail) {
+                        int *f = fail + by * bq + bx;
+                        if (*f == 0) atomicOr(f, 1);
+                    }
+                    failed = false;
+                    by = y / block;
+                    by_end = (by + 1) * block;
                 }
+                failed |= iw > 0.f && r < lambda;
             }
         }
         __syncthreads();   // the next round overwrites the scanned rows
+    }
+    if (failed && fail && j < wo) {
+        int *f = fail + by * bq + bx;
+        if (*f == 0) atomicOr(f, 1);
     }
 }
 
@@ -712,26 +786,27 @@ cudaError_t launch_blur(const uint8_t *I, int p, int q, const uint8_t *level_map
 cudaError_t launch_blur_corr(const uint8_t *P, const uint8_t *I, const int *wsum,
                              const float *inv_sigma, int p, int q, int m, int n, float lambda,
                              int block, int *fail, float *R, cudaStream_t s) {
-    using SG = RcoScan<1>;
     const int Ly = p - m + 1, Lx = q - n + 1;
-    if (n > kBcThreads) return cudaErrorInvalidValue;
-    const int WO = kBcThreads - n + 1;
-    const int strips = (Lx + WO - 1) / WO;
-    // bands of at least 2m rows (the initial m rows of each band amortised)
-    // and about two CTAs per SM in all
-    int bands = std::max(1, std::min((Ly + 2 * m - 1) / (2 * m), (2 * num_sms() + strips - 1) / strips));
+    // one thread per strip column; window sums of uint8 products in 32 bits
+    if (n > kBcThreads || (uint64_t)m * n * 65025u > 0xffffffffull) return cudaErrorInvalidValue;
+    // strips of equal width (one input column per thread), and bands so that
+    // all CTAs run in one wave, one per SM
+    const int strips = (Lx + (kBcThreads - n + 1) - 1) / (kBcThreads - n + 1);
+    const int WO = (Lx + strips - 1) / strips;
+    const int threads = ((WO + n - 1) + 31) & ~31;
+    int bands = std::max(1, std::min(Ly, num_sms() / strips));
     const int BR = (Ly + bands - 1) / bands;
     bands = (Ly + BR - 1) / BR;
-    const size_t smem = (size_t)3 * kBcRows * (SG::RS + SG::NSEG) * sizeof(unsigned);
+    const size_t smem = kBcSmem;
     static size_t attr = 0;
     {
         const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(blur_corr_kernel), smem, &attr);
         if (e != cudaSuccess) return e;
     }
     LaunchScope ls_blur_corr_kernel("blur_corr_kernel", s);
-    blur_corr_kernel<<<dim3(strips, bands), kBcThreads, smem, s>>>(P, I, p, q, m, n, Ly, Lx, wsum,
-                                                                  inv_sigma, WO, BR, lambda, block,
-                                                                  fail, R);
+    blur_corr_kernel<<<dim3(strips, bands), threads, smem, s>>>(P, I, p, q, m, n, Ly, Lx, wsum,
+                                                               inv_sigma, WO, BR, lambda, block,
+                                                               fail, R);
     return cudaGetLastError();
 }
 

@@ -976,7 +976,7 @@ __device__ inline void warp_rho32(const uint8_t *__restrict__ I, int q, int Lx,
             // ||I - a||^2 = Omega^2 + (S - a mn)^2 / mn, so ||I - a|| / Omega =
             // sqrt(1 + dS^2 / mn * (1/Omega)^2) with dS = S - a mn exact
             const long long dS = S - (long long)a * mn;
-            const float r2 = ((float)(dS * dS) / (float)mn) * (is * is);
+            const float r2 = (i64_to_f32(dS * dS) / i64_to_f32(mn)) * (is * is);
             eps = eps_bound(kacc, sqrtf(1.f + r2));
         }
     }
@@ -1147,7 +1147,7 @@ survivors_lane_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, 
             float eps = 0.f;
             if (is > 0.f) {
                 const long long dS = S - (long long)a * mn;
-                const float r2 = ((float)(dS * dS) / (float)mn) * (is * is);
+                const float r2 = (i64_to_f32(dS * dS) / i64_to_f32(mn)) * (is * is);
                 eps = eps_bound(kacc, sqrtf(1.f + r2));
             }
             surv_rho[sl] = rho;

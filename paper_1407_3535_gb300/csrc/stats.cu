@@ -5,6 +5,8 @@
 // Pixels are integers in [0,255], so the integral images, the window sums
 // taken from them and mn*Q - S^2 (for windows up to 2^23 pixels) are exact
 // integers; only the final 1/Omega is rounded (FP32).
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace opta {
@@ -128,30 +130,38 @@ __global__ void count_zero_kernel(const float *__restrict__ x, int64_t n,
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
 }
 
+// One thread per location: rows over blockIdx.y (grid-strided), columns over
+// blockIdx.x * blockDim.x + threadIdx.x.
 __global__ void window_stats_kernel(const long long *__restrict__ IIS,
                                     const long long *__restrict__ IIQ, int q, int Ly, int Lx,
                                     int m, int n, float *inv_sigma, float *efac128, int *wsum) {
-    const int64_t L = (int64_t)Ly * Lx;
     const int64_t q1 = q + 1;
     const long long mn = (long long)m * n;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int y = (int)(i / Lx), x = (int)(i % Lx);
+    const float fmn = i64_to_f32(mn);
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= Lx) return;
+    for (int y = blockIdx.y; y < Ly; y += gridDim.y) {
+        const int64_t i = (int64_t)y * Lx + x;
         const long long S = ii_box(IIS, q1, y, x, m, n);
         const long long Q = ii_box(IIQ, q1, y, x, m, n);
         const float fv = win_var(mn, S, Q);         // mn * Omega^2
         float inv = 0.f, ef = 0.f;
         if (fv > 0.f) {
             // FP32 finish (a few ulp; the error bounds that use 1/Omega allow 8u)
-            const float fmn = (float)mn;
             inv = sqrtf(fmn / fv);
             const long long c2 = Q - 256 * S + 16384 * mn;   // sum (I - 128)^2, exact
-            ef = sqrtf(fmn * (float)c2 / fv);
+            ef = sqrtf(fmn * i64_to_f32(c2) / fv);
         }
         inv_sigma[i] = inv;
         if (efac128) efac128[i] = ef;
         if (wsum) wsum[i] = (int)S;
     }
+}
+
+__global__ void i64_to_f32_kernel(const long long *__restrict__ v, float *out, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = i64_to_f32(v[i]);
 }
 
 __global__ void ingest_f32_kernel(const float *__restrict__ src, int64_t ld, int p, int q,
@@ -237,9 +247,17 @@ cudaError_t launch_window_stats(const long long *IIS, const long long *IIQ, int 
                                 int m, int n, float *inv_sigma, float *efac128,
                                 cudaStream_t s, int *wsum) {
     const int Ly = p - m + 1, Lx = q - n + 1;
+    const int bx = (Lx + 255) / 256;
+    const int by = std::max(1, std::min(Ly, (8 * num_sms() + bx - 1) / bx));
     LaunchScope ls_window_stats_kernel("window_stats_kernel", s);
-    window_stats_kernel<<<grid_for((int64_t)Ly * Lx, 256), 256, 0, s>>>(
-        IIS, IIQ, q, Ly, Lx, m, n, inv_sigma, efac128, wsum);
+    window_stats_kernel<<<dim3(bx, by), 256, 0, s>>>(IIS, IIQ, q, Ly, Lx, m, n, inv_sigma, efac128,
+                                                     wsum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_i64_to_f32(const long long *v, float *out, int64_t n, cudaStream_t s) {
+    LaunchScope ls("i64_to_f32_kernel", s);
+    i64_to_f32_kernel<<<grid_for(n, 256), 256, 0, s>>>(v, out, n);
     return cudaGetLastError();
 }
 

@@ -78,6 +78,51 @@ def test_blur_correlation(opta, m, n):
     assert np.max(np.abs(got - exp)) <= 2e-6
 
 
+@pytest.mark.parametrize("shape,m,n", [((300, 2500), 20, 20), ((700, 900), 48, 40),
+                                       ((130, 1100), 9, 1000)])
+def test_blur_corr_strips_bands_and_lambda_flags(opta, shape, m, n):
+    """Several strips and bands (band edges inside blocks), windows up to
+    1000 columns wide, flat windows; R against the oracle, and the lambda
+    test's block flags wherever no window sits within rounding of lambda."""
+    p, q = shape
+    img = synth.aerial_image(max(shape), 7, 30, seed=41)[:p, :q].copy()
+    img[50:120, 100:400] = 77                    # flat windows
+    bp, bq = (p + 63) // 64, (q + 63) // 64
+    smap = np.full((bp, bq), 2.0)
+    smap[::2, ::3] = 0.5
+    P = ref.quantise_pivot(ref.blur(img, smap, 64))
+    Ly, Lx = p - m + 1, q - n + 1
+    exp = ref.blur_corr_map(P, img, m, n)
+    live = ~ref.flat_windows(img, m, n)
+    blocks = [(by, bx) for by in range(bp) for bx in range(bq) if by * 64 < Ly and bx * 64 < Lx]
+
+    def cut(a, by, bx):
+        return a[by * 64:(by + 1) * 64, bx * 64:(bx + 1) * 64]
+
+    # lambda at the median of the blocks' smallest R: both outcomes occur
+    mins = [cut(np.where(live, exp, 2.0), by, bx).min() for by, bx in blocks]
+    lam = float(np.median(mins))
+    R = torch.empty(Ly * Lx, dtype=torch.float32, device="cuda")
+    F = torch.empty(bp * bq, dtype=torch.int32, device="cuda")
+    opta.opta_dbg_blur_corr(_cuda(P), _cuda(img), m, n, R, lam=lam, block=64, fail_dev=F)
+    got = R.cpu().numpy().reshape(Ly, Lx)
+    assert np.max(np.abs(got - exp)) <= 2e-6
+    flags = F.cpu().numpy().reshape(bp, bq)
+    seen = set()
+    for by in range(bp):
+        for bx in range(bq):
+            if (by, bx) not in blocks:
+                assert flags[by, bx] == 0          # no window has its top-left there
+                continue
+            e, lv = cut(exp, by, bx), cut(live, by, bx)
+            sure_fail = np.any((e < lam - 2e-6) & lv)
+            sure_pass = not np.any((e < lam + 2e-6) & lv)
+            if sure_fail or sure_pass:
+                assert flags[by, bx] == int(sure_fail), (by, bx)
+                seen.add(bool(sure_fail))
+    assert seen == {True, False}
+
+
 @pytest.mark.parametrize("h", [1, 3, 5, 7, 9])
 def test_rho_co_map_and_retained_count(opta, h):
     img = synth.aerial_image(150, 7, 10, seed=7)
@@ -131,3 +176,26 @@ def test_opta_decisions_match_oracle(opta):
     diff = np.abs(pivot.cpu().numpy().astype(int) - res["pivot"].astype(int))
     assert diff.max() <= 1 and np.count_nonzero(diff) <= 1e-3 * diff.size
     h.close()
+
+
+def test_i64_to_f32_is_correctly_rounded(opta):
+    """The kernels' int64 -> float conversion against exact integer
+    arithmetic: the nearest float (ties to even) for |v| < 2^46, within one
+    ulp beyond."""
+    rng = np.random.default_rng(9)
+    edge = [0, 1, -1, 2**22 - 1, 2**22, -2**22, -2**22 - 1, 2**23 + 1, 2**24 + 1, -(2**24 + 1),
+            2**24 + 3, 2**44 - 1, -(2**44), 2**45 - 1, -(2**45) + 3, 2**46 - 1, -(2**46) + 1,
+            2**46, 2**62 + 12345, -(2**62) - 7, 2**63 - 1, -(2**63)]
+    vals = list(edge)
+    for e in range(1, 63):
+        vals += [int(v) for v in rng.integers(-(2**e), 2**e, 200)]
+    v = np.array(vals, dtype=np.int64)
+    out = torch.empty(v.size, dtype=torch.float32, device="cuda")
+    opta.opta_dbg_i64_to_f32(_cuda(v), out)
+    got = out.cpu().numpy()
+    for gi, vi in zip(got.tolist(), vals):
+        if abs(vi) < 2**46:
+            assert gi == float(np.float32(float(vi))), vi   # float(vi) is exact below 2^53
+        else:
+            ulp = float(np.spacing(np.float32(abs(gi))))
+            assert abs(int(gi) - vi) <= ulp, vi
