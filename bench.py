@@ -212,12 +212,13 @@ def run_case(spec: str):
     rho_co:<h>     the auto-correlation map of 64 x 64 windows, group side h
     blur_corr:<s>  the lambda test of s x s windows against a sigma = 2 pivot
                    (blur correlation, block flags only, as in the preparation)
+    blur:<sigma>   the blur of every 64 x 64 block with one sigma (<= 3)
     """
     import torch
     import paper_1407_3535_gb300 as opta
 
     kind, _, arg = spec.partition(":")
-    v = int(arg)
+    v = float(arg) if kind == "blur" else int(arg)
     img = synth.config_image(4)
     p, q = img.shape
     I = torch.from_numpy(img).cuda()
@@ -243,6 +244,11 @@ def run_case(spec: str):
         for _ in range(2):
             opta.opta_dbg_blur_corr(P, I, v, v, None, lam=0.947350, block=64, fail_dev=F)
         out = {"failed_blocks": int(F.sum())}
+    elif kind == "blur":
+        P = torch.empty_like(I)
+        for _ in range(2):
+            opta.opta_dbg_blur(I, np.full(((p + 63) // 64, (q + 63) // 64), v), 64, P)
+        out = {"mean": float(P.float().mean())}
     else:
         raise SystemExit(f"unknown case {spec!r}")
     torch.cuda.synchronize()

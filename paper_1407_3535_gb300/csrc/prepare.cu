@@ -28,12 +28,80 @@ __device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" :
 
 constexpr int kMaxRadius = 9;
 
-// One CTA per block x block output tile; sigma (level) fixed per tile.
-// Threads are 64 columns x 4 rows; each pass walks its rows and columns in
-// strides of those (no per-element index division).
-constexpr int kBlurTX = 64, kBlurTY = 4;
+// One CTA per block x block output tile; sigma (level) fixed per tile and
+// its radius R a template parameter (taps unrolled).  The tile and its
+// R-wide halo (clamped to the image) are staged in shared memory as floats.
+// The horizontal pass gives each thread kBlurCB consecutive outputs of one
+// row, whose kBlurCB + 2R inputs it reads once into registers (a warp's
+// threads take consecutive rows; row strides are odd, so they fall in
+// distinct banks); the vertical pass gives each thread kBlurRB consecutive
+// rows of one column.  Each output is w0 s0 + sum_j w_j (s_j + s_-j),
+// accumulated in that order in FP32, then rounded to the nearest integer.
+constexpr int kBlurThreads = 256;
+constexpr int kBlurCB = 8;
+constexpr int kBlurRB = 16;
 
-__global__ void __launch_bounds__(kBlurTX * kBlurTY)
+__host__ __device__ inline size_t blur_smem_floats(int block, int R) {
+    const int ih = block + 2 * R, iw = block + 2 * R;
+    return (size_t)ih * (iw | 1) + (size_t)ih * (block | 1) + kBlurCB + 2 * R;
+}
+
+template <int R>
+__device__ __forceinline__ void blur_tile(const uint8_t *__restrict__ I, int p, int q, int y0,
+                                          int x0, int bh, int bw, const float *__restrict__ wg,
+                                          uint8_t *P, float *bsm) {
+    constexpr int CB = kBlurCB, RB = kBlurRB;
+    float w[R + 1];
+#pragma unroll
+    for (int k = 0; k <= R; ++k) w[k] = wg[k];
+    const int iw = bw + 2 * R, ih = bh + 2 * R;
+    const int ist = iw | 1, hst = bw | 1;
+    float *in = bsm;                 // ih x ist
+    float *hb = bsm + ih * ist;      // ih x hst
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = warp; r < ih; r += kBlurThreads / 32) {
+        const uint8_t *src = I + (int64_t)min(max(y0 - R + r, 0), p - 1) * q;
+        for (int c = lane; c < iw; c += 32) in[r * ist + c] = (float)src[min(max(x0 - R + c, 0), q - 1)];
+    }
+    __syncthreads();
+    const int ng = (bw + CB - 1) / CB;
+    for (int item = threadIdx.x; item < ih * ng; item += kBlurThreads) {
+        const int g = item / ih, r = item - g * ih;
+        const int c0 = g * CB;
+        const float *src = in + r * ist + c0;   // reads past the row land in the slack or the
+        float sv[CB + 2 * R];                   // next row and only feed outputs past bw
+#pragma unroll
+        for (int k = 0; k < CB + 2 * R; ++k) sv[k] = src[k];
+#pragma unroll
+        for (int o = 0; o < CB; ++o) {
+            float a = w[0] * sv[o + R];
+#pragma unroll
+            for (int t = 1; t <= R; ++t) a = fmaf(w[t], sv[o + R + t] + sv[o + R - t], a);
+            if (c0 + o < bw) hb[r * hst + c0 + o] = a;
+        }
+    }
+    __syncthreads();
+    const int nrg = (bh + RB - 1) / RB;
+    for (int item = threadIdx.x; item < bw * nrg; item += kBlurThreads) {
+        const int g = item / bw, c = item - g * bw;
+        const int r0 = g * RB;
+        float sv[RB + 2 * R];
+#pragma unroll
+        for (int k = 0; k < RB + 2 * R; ++k) sv[k] = r0 + k < ih ? hb[(r0 + k) * hst + c] : 0.f;
+#pragma unroll
+        for (int o = 0; o < RB; ++o) {
+            float a = w[0] * sv[o + R];
+#pragma unroll
+            for (int t = 1; t <= R; ++t) a = fmaf(w[t], sv[o + R + t] + sv[o + R - t], a);
+            if (r0 + o < bh) {
+                a = fminf(fmaxf(rintf(a), 0.f), 255.f);
+                P[(int64_t)(y0 + r0 + o) * q + x0 + c] = (uint8_t)a;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlurThreads)
 blur_kernel(const uint8_t *__restrict__ I, int p, int q, const uint8_t *__restrict__ level_map,
             int block, const float *__restrict__ weights, const int *__restrict__ radius,
             uint8_t *P) {
@@ -44,38 +112,24 @@ blur_kernel(const uint8_t *__restrict__ I, int p, int q, const uint8_t *__restri
     const int lev = level_map[by * bq + bx];
     const int R = lev > 0 ? radius[lev] : 0;
     const int bh = min(block, p - y0), bw = min(block, q - x0);
-    const int tx = threadIdx.x % kBlurTX, ty = threadIdx.x / kBlurTX;
-    if (R == 0) {
-        for (int r = ty; r < bh; r += kBlurTY)
-            for (int c = tx; c < bw; c += kBlurTX)
-                P[(int64_t)(y0 + r) * q + x0 + c] = I[(int64_t)(y0 + r) * q + x0 + c];
-        return;
-    }
     const float *w = weights + lev * (kMaxRadius + 1);
-    const int iw = bw + 2 * R, ih = bh + 2 * R;
-    float *in = bsm;                 // ih x iw
-    float *hb = bsm + ih * iw;       // ih x bw
-    for (int r = ty; r < ih; r += kBlurTY) {
-        const uint8_t *src = I + (int64_t)min(max(y0 - R + r, 0), p - 1) * q;
-        for (int c = tx; c < iw; c += kBlurTX) in[r * iw + c] = (float)src[min(max(x0 - R + c, 0), q - 1)];
+    switch (R) {
+        case 1: blur_tile<1>(I, p, q, y0, x0, bh, bw, w, P, bsm); return;
+        case 2: blur_tile<2>(I, p, q, y0, x0, bh, bw, w, P, bsm); return;
+        case 3: blur_tile<3>(I, p, q, y0, x0, bh, bw, w, P, bsm); return;
+        case 4: blur_tile<4>(I, p, q, y0, x0, bh, bw, w, P, bsm); return;
+        case 5: blur_tile<5>(I, p, q, y0, x0, bh, bw, w, P, bsm); return;
+        case 6: blur_tile<6>(I, p, q, y0, x0, bh, bw, w, P, bsm); return;
+        case 7: blur_tile<7>(I, p, q, y0, x0, bh, bw, w, P, bsm); return;
+        case 8: blur_tile<8>(I, p, q, y0, x0, bh, bw, w, P, bsm); return;
+        case 9: blur_tile<9>(I, p, q, y0, x0, bh, bw, w, P, bsm); return;
+        default: break;
     }
-    __syncthreads();
-    for (int r = ty; r < ih; r += kBlurTY)
-        for (int c = tx; c < bw; c += kBlurTX) {
-            const float *src = in + r * iw + c + R;
-            float a = w[0] * src[0];
-            for (int j = 1; j <= R; ++j) a = fmaf(w[j], src[j] + src[-j], a);
-            hb[r * bw + c] = a;
-        }
-    __syncthreads();
-    for (int r = ty; r < bh; r += kBlurTY)
-        for (int c = tx; c < bw; c += kBlurTX) {
-            const float *src = hb + (r + R) * bw + c;
-            float a = w[0] * src[0];
-            for (int j = 1; j <= R; ++j) a = fmaf(w[j], src[j * bw] + src[-j * bw], a);
-            a = fminf(fmaxf(rintf(a), 0.f), 255.f);
-            P[(int64_t)(y0 + r) * q + x0 + c] = (uint8_t)a;
-        }
+    // R = 0: the block is copied
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = warp; r < bh; r += kBlurThreads / 32)
+        for (int c = lane; c < bw; c += 32)
+            P[(int64_t)(y0 + r) * q + x0 + c] = I[(int64_t)(y0 + r) * q + x0 + c];
 }
 
 
@@ -718,8 +772,12 @@ RcoGeom rco_geom(int p, int q, int m, int n) {
         g.smem = smem_for(g.GXS, &g.Wmax);
     }
     g.ok = g.smem <= kSmemMax;
-    g.threads = ((g.Wmax + 31) / 32) * 32;
+    // strips of equal width (narrower than the limit: the last strip is not
+    // left with a remainder while the others carry the rest)
     g.strips = (Gx + g.GXS - 1) / g.GXS;
+    g.GXS = (Gx + g.strips - 1) / g.strips;
+    g.smem = smem_for(g.GXS, &g.Wmax);
+    g.threads = ((g.Wmax + 31) / 32) * 32;
     (void)Gy;
     return g;
 }
@@ -770,16 +828,15 @@ static int grid_for(int64_t n, int threads) {
 cudaError_t launch_blur(const uint8_t *I, int p, int q, const uint8_t *level_map, int block,
                         const float *weights, const int *radius, uint8_t *P, cudaStream_t s) {
     const int bp = (p + block - 1) / block, bq = (q + block - 1) / block;
-    const int ih = block + 2 * kMaxRadius;
-    const size_t smem = (size_t)(ih * ih + ih * block) * sizeof(float);
+    const size_t smem = blur_smem_floats(block, kMaxRadius) * sizeof(float);
     static size_t attr = 0;
     {
         const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(blur_kernel), smem, &attr);
         if (e != cudaSuccess) return e;
     }
     LaunchScope ls_blur_kernel("blur_kernel", s);
-    blur_kernel<<<dim3(bq, bp), kBlurTX * kBlurTY, smem, s>>>(I, p, q, level_map, block, weights,
-                                                           radius, P);
+    blur_kernel<<<dim3(bq, bp), kBlurThreads, smem, s>>>(I, p, q, level_map, block, weights,
+                                                        radius, P);
     return cudaGetLastError();
 }
 

@@ -66,6 +66,29 @@ def test_blur_matches_definition(opta):
     assert np.array_equal(got[:64, :64], img[:64, :64].astype(int))
 
 
+@pytest.mark.parametrize("block", [8, 32, 128])
+def test_blur_every_radius_and_block_size(opta, block):
+    """Sigmas whose supports ceil(3 sigma) take every radius 1..9, on blocks
+    of 8, 32 and 128 pixels with ragged edge blocks."""
+    img = synth.aerial_image(300, 7, 12, seed=15)[:221, :283].copy()
+    bp, bq = (221 + block - 1) // block, (283 + block - 1) // block
+    sig = [0.0, 0.3, 0.6, 1.0, 1.2, 1.5, 2.0, 2.2, 2.6, 3.0]     # radii 0, 1, 2, 3, 4, 5, 6, 7, 8, 9
+    rng = np.random.default_rng(block)
+    smap = np.array(sig)[rng.integers(0, len(sig), (bp, bq))]
+    # at most 8 distinct non-zero sigmas per call: split the map in two calls
+    for keep in (sig[1:6], sig[6:]):
+        sm = np.where(np.isin(smap, keep), smap, 0.0)
+        P = torch.empty(img.shape, dtype=torch.uint8, device="cuda")
+        opta.opta_dbg_blur(_cuda(img), sm, block, P)
+        got = P.cpu().numpy().astype(int)
+        exp_f = ref.blur(img, sm, block)
+        exp = ref.quantise_pivot(exp_f).astype(int)
+        diff = np.abs(got - exp)
+        assert diff.max() <= 1
+        frac = np.abs(exp_f - np.floor(exp_f) - 0.5)
+        assert np.all(frac[diff == 1] < 1e-4)
+
+
 @pytest.mark.parametrize("m,n", [(16, 16), (11, 27)])
 def test_blur_correlation(opta, m, n):
     img = synth.aerial_image(180, 7, 10, seed=6)
