@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-brute", action="store_true")
+    ap.add_argument("--serve-full", action="store_true",
+                    help="serve the four resident images of the serving configuration "
+                         "(4096^2 .. 16384^2) instead of 4096^2 and 2048^2")
     ap.add_argument("--case", default=None,
                     help="one kernel for a profiler capture instead of the benchmark: "
                          "scan1:<side>, rho_co:<h> or blur_corr:<side> (see run_case)")
@@ -346,6 +349,7 @@ def main():
     e2.synchronize()
     prep_ms, search_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
     size_info = {f"{m}x{n}": opta.optA_size_info(h, m, n) for (m, n) in sizes}
+    mem_bytes = opta.optA_memory_bytes(h)   # prepared sizes + the search context of the batch
 
     # per-template query latency on the prepared handle (one template per call)
     lat = []
@@ -357,6 +361,23 @@ def main():
         b.synchronize()
         lat.append(a.elapsed_time(b))
     lat = np.array(lat)
+
+    # the same batched search replayed as one captured CUDA graph
+    graph = None
+    g = opta.SearchGraph(h, dts, stream=stream)
+    gt = []
+    for rep in range(4):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        gres = g.launch(stream=stream)
+        b.record(stream)
+        b.synchronize()
+        gt.append(a.elapsed_time(b))
+    assert [(r.y, r.x, r.rho) for r in gres] == [(r.y, r.x, r.rho) for r in results]
+    graph = {"nodes": g.nodes(), "search_ms": float(np.median(gt[1:])), "eager_search_ms": search_ms,
+             "value": L_step / (float(np.median(gt[1:])) / 1000.0)}
+    g.close()
 
     # per-kernel device time of one search pass (CUDA events on the launch stream)
     opta.opta_dbg_profile_read()
@@ -394,6 +415,9 @@ def main():
     # the literal mode (Section 4.3) on the same batch: its speed, and how far
     # its answers land from the exact maxima found above
     literal = literal_report(opta, dimg, dts, sizes, res_prof, stream, flush, L_step)
+
+    # the serving loop over resident images, Poisson arrivals at swept rates
+    serving = serving_report(opta, img, ts, full=args.serve_full) if world == 1 else None
 
     # exhaustive GPU search on the same GPU (a sample of templates, one per size)
     brute = None
@@ -468,10 +492,13 @@ def main():
                               "mean_best": float(np.mean([r.rho for r in res_prof])),
                               "min_best": float(np.min([r.rho for r in res_prof]))},
         "brute_force": brute,
+        "graph_search": graph,
         "literal_mode": literal,
+        "serving": serving,
         "kernels_ms": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
         "prepare_kernels_ms": {k: [round(v[0], 3), v[1]] for k, v in
                                sorted(prof_prep.items(), key=lambda kv: -kv[1][0])},
+        "device_bytes_handle_and_search_ctx": int(mem_bytes),
         "group_sizes": {k: v["group_h"] for k, v in size_info.items()},
         "per_size": per_size,
         "blur_levels": {k: v["level"] for k, v in size_info.items()},
@@ -483,6 +510,66 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+SERVE_SIZES = [16, 24, 32, 48, 64, 96, 128]
+
+
+def serving_report(opta, img, ts, full=False, n_req=400, workers=4, max_batch=64):
+    """The serving loop (opta.Server): images prepared once and kept resident,
+    template queries of sizes uniform in {16..128} (crops + affine intensity
+    + noise) submitted from the host as Poisson arrivals; requests join the
+    next free worker's batch.  First a burst of n_req requests measures the
+    saturated rate; then arrivals at 25, 50 and 90 % of it.  Latency =
+    completion - submission on the server's clock."""
+    import torch
+    if full:
+        images = [img] + [synth.aerial_image(s, n_octaves=max(3, int(np.log2(s)) - 3),
+                                             n_prims=800 * s * s // 4096 ** 2, seed=2004 + s)
+                          for s in (8192, 12288, 16384)]
+    else:
+        images = [img, synth.config_image(2)]
+    pools = [[t.data for t in ts]] + [
+        [t.data for t in synth.make_templates(im, synth.batch_sizes(64, 3000 + k), seed=3000 + k,
+                                              noise=3.0)]
+        for k, im in enumerate(images[1:])]
+    sizes = [(s, s) for s in SERVE_SIZES]
+    srv = opta.Server(n_workers=workers, max_batch=max_batch)
+    t0 = time.perf_counter()
+    ids = [srv.add_image(torch.from_numpy(im).cuda(), sizes=sizes) for im in images]
+    prep_s = time.perf_counter() - t0
+    rng = np.random.default_rng(2026)
+
+    def run(rate, n):
+        picks = []
+        next_t = time.perf_counter()
+        for k in range(n):
+            i = k % len(ids)
+            t = pools[i][int(rng.integers(0, len(pools[i])))]
+            if rate:
+                next_t += rng.exponential(1.0 / rate)
+                while time.perf_counter() < next_t:
+                    pass
+            srv.submit(ids[i], t)
+            picks.append((images[i].shape, t.shape))
+        done = []
+        while len(done) < n:
+            done += srv.wait(min_count=1, capacity=4096, timeout_ms=300000)
+        lat = np.array([(c.t_done - c.t_submit) * 1e3 for c in done])
+        span = max(c.t_done for c in done) - min(c.t_submit for c in done)
+        locs = sum((ish[0] - tsh[0] + 1) * (ish[1] - tsh[1] + 1) for ish, tsh in picks)
+        assert all(c.status == 0 for c in done), [c.status for c in done if c.status]
+        return {"offered_rps": rate, "achieved_rps": n / span, "locations_per_s": locs / span,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_batch": float(np.mean([c.batch_size for c in done]))}
+
+    run(None, 64)                       # warm-up (scratch grown, tiles tuned)
+    sat = run(None, n_req)
+    rates = [run(f * sat["achieved_rps"], n_req) for f in (0.25, 0.5, 0.9)]
+    srv.close()
+    return {"images": [f"{im.shape[0]}x{im.shape[1]}" for im in images], "workers": workers,
+            "max_batch": max_batch, "prepare_s": prep_s, "requests_per_rate": n_req,
+            "saturated": sat, "poisson": rates}
 
 
 def literal_report(opta, dimg, dts, sizes, exact, stream, flush, L_step):

@@ -126,6 +126,8 @@ typedef struct opta_params {
 } opta_params;
 
 typedef struct opta_handle opta_handle;
+typedef struct opta_search_ctx opta_search_ctx;
+typedef struct opta_graph opta_graph;
 
 /* Per-template-size preparation summary (see optA_size_info). */
 typedef struct opta_size_info {
@@ -178,6 +180,54 @@ opta_status optA_search(opta_handle *h, const opta_template *t, int32_t n_t,
                         opta_result *out, void *stream);
 
 /*
+ * Search contexts: the scratch memory and per-template state of a search,
+ * apart from the prepared images.  A context serves any handle on the
+ * device of the handle it was created with.  Searches through different
+ * contexts may run at the same time, from different host threads on
+ * different streams, on one handle or several, and their kernels overlap on
+ * the device; a context runs one search at a time (a second concurrent call
+ * returns OPTA_ERR_BUSY).  Sizes not prepared yet are prepared by the first
+ * search that needs them, one preparation per handle at a time.
+ * optA_search uses a context of its own.  A context grows its scratch on
+ * demand and keeps it until it is destroyed (the handles it served may be
+ * destroyed first, once no search through it is running on them).
+ */
+opta_status optA_ctx_create(const opta_handle *h, opta_search_ctx **out);
+opta_status optA_ctx_destroy(opta_search_ctx *ctx);
+/* Device bytes currently held by the context's scratch. */
+opta_status optA_ctx_memory_bytes(const opta_search_ctx *ctx, size_t *bytes);
+/* Device bytes `ctx` would hold after searching the n_t templates `t` on
+ * handle h: its scratch grows to the larger of what it holds and what the
+ * batch needs, and keeps it (sizes not prepared yet are counted at their
+ * largest).  For admission control by device memory; no device work. */
+opta_status optA_ctx_bytes_after(opta_handle *h, const opta_search_ctx *ctx,
+                                 const opta_template *t, int32_t n_t, size_t *bytes);
+/* optA_search through context `ctx` (created on h's device). */
+opta_status optA_search_ctx(opta_handle *h, opta_search_ctx *ctx, const opta_template *t,
+                            int32_t n_t, opta_result *out, void *stream);
+
+/*
+ * The batched search as one CUDA graph, for searching the same set of
+ * template sizes again and again (new template data each time).
+ * optA_graph_create copies the n_t templates (host or device data) into
+ * device buffers the graph owns, runs one ordinary search (which prepares
+ * the sizes, sizes the scratch and tunes scan 1's tiles), then captures the
+ * whole batched search -- every kernel launch and the copy of its results
+ * to pinned host memory -- into a graph on a stream of its own.  The graph
+ * has its own search context; handle h must outlive it.
+ * optA_graph_set_template replaces template i's data (same size; host or
+ * device source, queued on `stream`); optA_graph_launch replays the graph
+ * on `stream`, waits, and fills out[0..n_t) as optA_search would.
+ */
+opta_status optA_graph_create(opta_handle *h, const opta_template *t, int32_t n_t, void *stream,
+                              opta_graph **out);
+opta_status optA_graph_set_template(opta_graph *g, int32_t i, const opta_template *t, void *stream);
+opta_status optA_graph_launch(opta_graph *g, opta_result *out, void *stream);
+/* Number of nodes (kernel launches, copies, memsets) in the captured graph. */
+opta_status optA_graph_info(const opta_graph *g, int64_t *nodes);
+opta_status optA_graph_destroy(opta_graph *g);
+
+/*
  * Exhaustive search: rho at all locations and its argmax (Eq. rho1).  Same
  * image domain as optA_prepare (integers in [0, 255]; OPTA_ERR_UNSUPPORTED
  * otherwise).  `rho_map` (nullable) is a DEVICE buffer of
@@ -222,7 +272,8 @@ opta_status optA_debug_bounds(opta_handle *h, const opta_template *t,
 /* Summary of the preparation of size (m, n) (prepared on demand). */
 opta_status optA_size_info(opta_handle *h, int32_t m, int32_t n, opta_size_info *info);
 
-/* Device bytes currently owned by the handle. */
+/* Device bytes currently owned by the handle (its own search context
+ * included, other contexts not). */
 opta_status optA_memory_bytes(const opta_handle *h, size_t *bytes);
 
 /* Release the handle and all its device memory (NULL is accepted). */

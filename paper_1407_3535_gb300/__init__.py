@@ -20,7 +20,7 @@ __all__ = [
     "optA_debug_bounds", "optA_size_info", "optA_memory_bytes", "optA_destroy",
     "optA_debug_maps", "opta_dbg_window_stats", "opta_dbg_blur", "opta_dbg_blur_corr", "opta_dbg_i64_to_f32",
     "opta_dbg_rho_co", "opta_dbg_launch_count", "opta_dbg_profile_enable",
-    "opta_dbg_profile_read", "optA_debug_scan1", "Handle", "lib", "OptaResult",
+    "opta_dbg_profile_read", "optA_debug_scan1", "Handle", "lib", "OptaResult", "SearchContext", "SearchGraph", "Server",
 ]
 
 lib = _lib.lib
@@ -158,8 +158,42 @@ def optA_prepare(image, params: OptaParams | None = None, sizes=None, stream=Non
     return Handle(out.value, img.rows, img.cols)
 
 
-def optA_search(handle: Handle, templates, stream=None, check: bool = True):
-    """Best match per template: list of OptaResult (status per template)."""
+class SearchContext:
+    """Owns an opta_search_ctx*: search scratch usable with any handle on the
+    device of the handle it is created with (see optA_ctx_create)."""
+
+    def __init__(self, handle: Handle):
+        out = c_void_p(0)
+        _check(lib().optA_ctx_create(handle.ptr, byref(out)), "optA_ctx_create")
+        self._ptr = out
+
+    @property
+    def ptr(self):
+        if not self._ptr:
+            raise ValueError("context closed")
+        return self._ptr
+
+    def memory_bytes(self) -> int:
+        b = c_size_t(0)
+        _check(lib().optA_ctx_memory_bytes(self.ptr, byref(b)), "optA_ctx_memory_bytes")
+        return b.value
+
+    def close(self):
+        if self._ptr:
+            _check(lib().optA_ctx_destroy(self._ptr), "optA_ctx_destroy")
+            self._ptr = c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def optA_search(handle: Handle, templates, stream=None, check: bool = True,
+                ctx: SearchContext | None = None):
+    """Best match per template: list of OptaResult (status per template).
+    With `ctx`, the search runs through that context (optA_search_ctx)."""
     if not isinstance(templates, (list, tuple)):
         templates = [templates]
     n = len(templates)
@@ -170,10 +204,146 @@ def optA_search(handle: Handle, templates, stream=None, check: bool = True):
         descs[i] = d
         keep.append(k)
     out = (OptaResult * max(n, 1))()
-    code = lib().optA_search(handle.ptr, descs, n, out, _stream(stream))
+    if ctx is None:
+        code = lib().optA_search(handle.ptr, descs, n, out, _stream(stream))
+    else:
+        code = lib().optA_search_ctx(handle.ptr, ctx.ptr, descs, n, out, _stream(stream))
     if check and code not in (0, 2):
         raise OptaError(code, "optA_search")
     return [out[i] for i in range(n)]
+
+
+class SearchGraph:
+    """optA_graph_*: the batched search of a fixed list of template sizes
+    captured as one CUDA graph; set(i, t) replaces template i's data,
+    launch() replays the graph and returns the results."""
+
+    def __init__(self, handle: Handle, templates, stream=None):
+        n = len(templates)
+        descs = (OptaTemplate * n)()
+        keep = []
+        for i, t in enumerate(templates):
+            d, k = _template(t)
+            descs[i] = d
+            keep.append(k)
+        out = c_void_p(0)
+        _check(lib().optA_graph_create(handle.ptr, descs, n, _stream(stream), byref(out)),
+               "optA_graph_create")
+        del keep
+        self._ptr, self.n, self._handle = out, n, handle
+
+    @property
+    def ptr(self):
+        if not self._ptr:
+            raise ValueError("graph closed")
+        return self._ptr
+
+    def set(self, i: int, template, stream=None):
+        """Replace template i's data (same size).  A host array is copied
+        before the call returns; a device tensor is copied on `stream`, so
+        launch on the same stream (and keep the tensor until then)."""
+        d, keep = _template(template)
+        _check(lib().optA_graph_set_template(self.ptr, i, byref(d), _stream(stream)),
+               "optA_graph_set_template")
+        return keep
+
+    def launch(self, stream=None, check: bool = True):
+        out = (OptaResult * self.n)()
+        code = lib().optA_graph_launch(self.ptr, out, _stream(stream))
+        if check and code not in (0, 2):
+            raise OptaError(code, "optA_graph_launch")
+        return [out[i] for i in range(self.n)]
+
+    def nodes(self) -> int:
+        n = c_int64(0)
+        _check(lib().optA_graph_info(self.ptr, byref(n)), "optA_graph_info")
+        return n.value
+
+    def close(self):
+        if self._ptr:
+            lib().optA_graph_destroy(self._ptr)
+            self._ptr = c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """The serving loop of include/opta_serve.h: resident prepared images,
+    template queries batched by worker threads as they arrive, admission by
+    a device-memory budget.  Templates are host arrays (copied on submit)."""
+
+    def __init__(self, n_workers: int = 4, max_batch: int = 64, memory_budget: int = 0):
+        from ._lib import OptaServerConfig
+        cfg = OptaServerConfig()
+        lib().opta_server_config_default(byref(cfg))
+        cfg.n_workers, cfg.max_batch, cfg.memory_budget = n_workers, max_batch, memory_budget
+        out = c_void_p(0)
+        _check(lib().opta_server_create(byref(cfg), byref(out)), "opta_server_create")
+        self._ptr = out
+
+    @property
+    def ptr(self):
+        if not self._ptr:
+            raise ValueError("server closed")
+        return self._ptr
+
+    def add_image(self, image, params: OptaParams | None = None, sizes=None) -> int:
+        img, keep = _image(image)
+        sz = list(sizes or [])
+        arr = (c_int32 * (2 * len(sz) or 1))()
+        for i, sm in enumerate(sz):
+            m, n = (sm, sm) if isinstance(sm, int) else sm
+            arr[2 * i], arr[2 * i + 1] = int(m), int(n)
+        iid = c_int32(0)
+        code = lib().opta_server_add_image(self.ptr, byref(img),
+                                           byref(params) if params is not None else None,
+                                           arr if sz else None, len(sz), byref(iid))
+        del keep
+        _check(code, "opta_server_add_image")
+        return iid.value
+
+    def submit(self, image_id: int, template) -> int:
+        import numpy as np
+        t = np.ascontiguousarray(template, dtype=np.float32)
+        d = OptaTemplate(t.shape[0], t.shape[1], t.shape[1], 0, 0, t.ctypes.data)
+        rid = ctypes.c_uint64(0)
+        _check(lib().opta_server_submit(self.ptr, image_id, byref(d), byref(rid)), "opta_server_submit")
+        return rid.value
+
+    def wait(self, min_count: int = 1, capacity: int = 1024, timeout_ms: int = -1):
+        """Finished requests (OptaCompletion list, oldest first)."""
+        from ._lib import OptaCompletion
+        buf = (OptaCompletion * max(capacity, 1))()
+        n = c_int32(0)
+        _check(lib().opta_server_wait(self.ptr, buf, capacity, min_count, timeout_ms, byref(n)),
+               "opta_server_wait")
+        return [buf[i] for i in range(n.value)]
+
+    def pending(self) -> int:
+        n = c_int64(0)
+        _check(lib().opta_server_pending(self.ptr, byref(n)), "opta_server_pending")
+        return n.value
+
+    def close(self):
+        if self._ptr:
+            lib().opta_server_destroy(self._ptr)
+            self._ptr = c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def zncc_full(image, template, rho_map=None, stream=None, check: bool = True) -> OptaResult:

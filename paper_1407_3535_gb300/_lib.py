@@ -49,6 +49,17 @@ class OptaParams(ctypes.Structure):
                 ("precision", c_int32), ("literal", c_int32), ("reserved", c_int32 * 6)]
 
 
+class OptaServerConfig(ctypes.Structure):
+    _fields_ = [("n_workers", c_int32), ("max_batch", c_int32), ("memory_budget", c_int64),
+                ("reserved", c_int32 * 8)]
+
+
+class OptaCompletion(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_uint64), ("image_id", c_int32), ("batch_size", c_int32),
+                ("worker", c_int32), ("status", c_int32), ("t_submit", c_double),
+                ("t_start", c_double), ("t_done", c_double), ("result", OptaResult)]
+
+
 class OptaSizeInfo(ctypes.Structure):
     _fields_ = [("m", c_int32), ("n", c_int32), ("group_h", c_int32), ("level", c_int32),
                 ("cost", c_int64), ("n_groups", c_int64), ("blocks_y", c_int32),
@@ -64,6 +75,29 @@ SIGNATURES = {
     "opta_status_str": (c_char_p, [c_int32]),
     "optA_prepare": (c_int32, [POINTER(OptaImage), POINTER(OptaParams), POINTER(c_int32), c_int32,
                                c_void_p, POINTER(c_void_p)]),
+    "optA_ctx_create": (c_int32, [c_void_p, POINTER(c_void_p)]),
+    "optA_ctx_destroy": (c_int32, [c_void_p]),
+    "optA_ctx_memory_bytes": (c_int32, [c_void_p, POINTER(c_size_t)]),
+    "optA_search_ctx": (c_int32, [c_void_p, c_void_p, POINTER(OptaTemplate), c_int32,
+                                  POINTER(OptaResult), c_void_p]),
+    "optA_ctx_bytes_after": (c_int32, [c_void_p, c_void_p, POINTER(OptaTemplate), c_int32,
+                                       POINTER(c_size_t)]),
+    "opta_server_config_default": (None, [POINTER(OptaServerConfig)]),
+    "opta_server_create": (c_int32, [POINTER(OptaServerConfig), POINTER(c_void_p)]),
+    "opta_server_add_image": (c_int32, [c_void_p, POINTER(OptaImage), c_void_p, c_void_p, c_int32,
+                                        POINTER(c_int32)]),
+    "opta_server_submit": (c_int32, [c_void_p, c_int32, POINTER(OptaTemplate),
+                                     POINTER(ctypes.c_uint64)]),
+    "opta_server_wait": (c_int32, [c_void_p, POINTER(OptaCompletion), c_int32, c_int32, c_int32,
+                                   POINTER(c_int32)]),
+    "opta_server_pending": (c_int32, [c_void_p, POINTER(c_int64)]),
+    "opta_server_destroy": (c_int32, [c_void_p]),
+    "optA_graph_create": (c_int32, [c_void_p, POINTER(OptaTemplate), c_int32, c_void_p,
+                                    POINTER(c_void_p)]),
+    "optA_graph_set_template": (c_int32, [c_void_p, c_int32, POINTER(OptaTemplate), c_void_p]),
+    "optA_graph_launch": (c_int32, [c_void_p, POINTER(OptaResult), c_void_p]),
+    "optA_graph_info": (c_int32, [c_void_p, POINTER(c_int64)]),
+    "optA_graph_destroy": (c_int32, [c_void_p]),
     "optA_search": (c_int32, [c_void_p, POINTER(OptaTemplate), c_int32, POINTER(OptaResult),
                               c_void_p]),
     "zncc_full": (c_int32, [POINTER(OptaImage), POINTER(OptaTemplate), c_void_p,

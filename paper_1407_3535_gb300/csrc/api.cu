@@ -9,6 +9,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <shared_mutex>
 #include <thread>
 #include <utility>
 #include <vector>
@@ -91,16 +92,13 @@ struct SizeState {
 
 }  // namespace
 
-struct opta_handle {
-    int p = 0, q = 0, device = 0;
-    opta_params prm;
+// Search scratch and per-template states of one search context: searches
+// of one handle through different contexts may run concurrently (each on
+// its own stream); a context runs one search at a time.
+struct opta_search_ctx {
+    int device = 0;
     DevMem mem;
-    uint8_t *I8 = nullptr;
-    long long *IIS = nullptr, *IIQ = nullptr;
-    std::map<std::pair<int, int>, SizeState *> sizes;
-    std::mutex sizes_mu;                      // guards `sizes` while sizes are prepared concurrently
-    cudaMemPool_t pool = nullptr;             // stream-ordered scratch of the preparation
-    // search scratch (grown on demand)
+    std::atomic<bool> busy{false};
     size_t capL = 0, capG = 0, capT = 0, capN = 0;
     size_t capS2 = 0;                         // template slots of the scan-2 arrays (stride capL)
     int *ucnt = nullptr;                      // kScan2MaxT unordered-survivor counters
@@ -114,17 +112,36 @@ struct opta_handle {
     int *topk_i = nullptr;
     int *cand_topk = nullptr;                 // chunk x kTopkMax threshold centres
     double *cand_rho_topk = nullptr;
-    TmplIn *tin = nullptr;                    // chunk template descriptors
+    TmplIn *tin = nullptr;                    // template descriptors, one slot per template
     float *tf = nullptr, *tstage = nullptr;   // tf: chunk of templates, m x npad each
     double *td = nullptr;                     // chunk of templates, m x n each
     TmplState *states = nullptr;
+    // pinned host mirrors, one slot per template (read by copies queued on a
+    // stream, so a slot is not rewritten until its search has finished; and
+    // copies from pinned memory can be captured in a CUDA graph)
+    TmplIn *tin_host = nullptr;
+    TmplState *states_host = nullptr;
+    int *err_host = nullptr;
     size_t capTS = 0, capB = 0, capRT = 0;    // template-slot, B-buffer, rho_tc capacities
     void *Bmma = nullptr;                     // bf16 hi/lo planes of a chunk (core-matrix layout)
     int *dev_err = nullptr;                   // set by a kernel whose bounded wait gave up
+};
+
+struct opta_handle {
+    int p = 0, q = 0, device = 0;
+    opta_params prm;
+    DevMem mem;
+    uint8_t *I8 = nullptr;
+    long long *IIS = nullptr, *IIQ = nullptr;
+    std::map<std::pair<int, int>, SizeState *> sizes;
+    std::shared_mutex sizes_rw;               // `sizes`: shared while searches use it, exclusive to insert
+    cudaMemPool_t pool = nullptr;             // stream-ordered scratch of the preparation
+    opta_search_ctx *dctx = nullptr;          // the context of optA_search (created on first use)
+    std::mutex prep_mu;                       // one preparation of new sizes at a time
     // blur tables
     float *weights = nullptr;
     int *radius = nullptr;
-    bool busy = false;
+    std::atomic<bool> busy{false};
 };
 
 namespace {
@@ -292,8 +309,15 @@ opta_status blur_to(opta_handle *H, PrepScratch &W, const std::vector<uint8_t> &
 }
 
 bool size_ready(opta_handle *H, const std::pair<int, int> &key) {
-    std::lock_guard<std::mutex> lk(H->sizes_mu);
+    std::shared_lock<std::shared_mutex> lk(H->sizes_rw);
     return H->sizes.count(key) != 0;
+}
+
+// The prepared state of a size (nullptr if not prepared); the caller holds
+// sizes_rw (shared or exclusive) or is the only thread using the handle.
+SizeState *size_of(opta_handle *H, const std::pair<int, int> &key) {
+    auto it = H->sizes.find(key);
+    return it == H->sizes.end() ? nullptr : it->second;
 }
 
 // Preparation of one size on stream s.  Scratch comes from the handle's
@@ -471,7 +495,7 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     PCK(launch_group_co(S->theta_co, S->Ly, S->Lx, S->h, S->gco, s));
     PCK(cudaStreamSynchronize(s));
     {
-        std::lock_guard<std::mutex> lk(H->sizes_mu);
+        std::unique_lock<std::shared_mutex> lk(H->sizes_rw);
         H->sizes[key] = S;
     }
     return cleanup(OPTA_OK);
@@ -527,10 +551,9 @@ opta_status prepare_sizes(opta_handle *H, const std::vector<std::pair<int, int>>
 }
 
 template <class T>
-opta_status grow(opta_handle *H, T *&p, size_t &cap_field_unused, size_t old_n, size_t new_n) {
-    (void)cap_field_unused;
-    H->mem.release(p, old_n);
-    return H->mem.alloc(&p, new_n);
+opta_status grow(DevMem &mem, T *&p, size_t old_n, size_t new_n) {
+    mem.release(p, old_n);
+    return mem.alloc(&p, new_n);
 }
 
 // Templates per scan-2 launch for L locations and a chunk of `chunk`.
@@ -545,58 +568,72 @@ int scan2_batch(size_t L, int chunk) {
 // scan-2 template slots, G groups (times the templates of one chunk: RT =
 // chunk * G), chunk template slots of T = m*npad elements each (TS = chunk *
 // T), a B buffer of `Bbytes` and N templates.
-opta_status ensure_scratch(opta_handle *H, size_t L, size_t TB, size_t RT, size_t T, size_t TS,
+opta_status ensure_scratch(opta_search_ctx *X, size_t L, size_t TB, size_t RT, size_t T, size_t TS,
                            size_t Bbytes, size_t N) {
-    size_t dummy = 0;
     const size_t G = RT;
-    if (L > H->capL || TB > H->capS2) {
-        const size_t nL = std::max(L, H->capL), nS = std::max(TB, H->capS2);
-        const size_t oldn = H->capL * H->capS2, newn = nL * nS;
-        TRY(grow(H, H->surv, dummy, oldn, newn));
-        TRY(grow(H, H->surv_rho, dummy, oldn, newn));
-        TRY(grow(H, H->surv_eps, dummy, oldn, newn));
-        TRY(grow(H, H->surv_ub, dummy, oldn, newn));
-        TRY(grow(H, H->cand, dummy, oldn, newn));
-        TRY(grow(H, H->cand_rho, dummy, oldn, newn));
-        H->capL = nL;
-        H->capS2 = nS;
+    if (L > X->capL || TB > X->capS2) {
+        const size_t nL = std::max(L, X->capL), nS = std::max(TB, X->capS2);
+        const size_t oldn = X->capL * X->capS2, newn = nL * nS;
+        TRY(grow(X->mem, X->surv, oldn, newn));
+        TRY(grow(X->mem, X->surv_rho, oldn, newn));
+        TRY(grow(X->mem, X->surv_eps, oldn, newn));
+        TRY(grow(X->mem, X->surv_ub, oldn, newn));
+        TRY(grow(X->mem, X->cand, oldn, newn));
+        TRY(grow(X->mem, X->cand_rho, oldn, newn));
+        X->capL = nL;
+        X->capS2 = nS;
     }
-    if (G > H->capG) {
-        TRY(grow(H, H->rho_tc, dummy, H->capG, G));
-        H->capG = G;
+    if (G > X->capG) {
+        TRY(grow(X->mem, X->rho_tc, X->capG, G));
+        X->capG = G;
     }
-    if (!H->topk_v) {
-        TRY(H->mem.alloc(&H->topk_v, (size_t)kChunk * 256 * kTopkMax));
-        TRY(H->mem.alloc(&H->topk_i, (size_t)kChunk * 256 * kTopkMax));
-        TRY(H->mem.alloc(&H->cand_topk, (size_t)kChunk * kTopkMax));
-        TRY(H->mem.alloc(&H->cand_rho_topk, (size_t)kChunk * kTopkMax));
-        TRY(H->mem.alloc(&H->tin, (size_t)kChunk));
-        TRY(H->mem.alloc(&H->bucket_cnt, (size_t)kScan2MaxT * kUbBuckets));
-        TRY(H->mem.alloc(&H->bucket_cur, (size_t)kScan2MaxT * kUbBuckets));
-        TRY(H->mem.alloc(&H->ucnt, (size_t)kScan2MaxT));
+    if (!X->topk_v) {
+        TRY(X->mem.alloc(&X->topk_v, (size_t)kChunk * 256 * kTopkMax));
+        TRY(X->mem.alloc(&X->topk_i, (size_t)kChunk * 256 * kTopkMax));
+        TRY(X->mem.alloc(&X->cand_topk, (size_t)kChunk * kTopkMax));
+        TRY(X->mem.alloc(&X->cand_rho_topk, (size_t)kChunk * kTopkMax));
+        TRY(X->mem.alloc(&X->bucket_cnt, (size_t)kScan2MaxT * kUbBuckets));
+        TRY(X->mem.alloc(&X->bucket_cur, (size_t)kScan2MaxT * kUbBuckets));
+        TRY(X->mem.alloc(&X->ucnt, (size_t)kScan2MaxT));
     }
-    if (T > H->capT) {
-        TRY(grow(H, H->tstage, dummy, H->capT, T));
-        H->capT = T;
+    if (T > X->capT) {
+        TRY(grow(X->mem, X->tstage, X->capT, T));
+        X->capT = T;
     }
-    if (TS > H->capTS) {
-        TRY(grow(H, H->tf, dummy, H->capTS, TS));
-        TRY(grow(H, H->td, dummy, H->capTS, TS));
-        H->capTS = TS;
+    if (TS > X->capTS) {
+        TRY(grow(X->mem, X->tf, X->capTS, TS));
+        TRY(grow(X->mem, X->td, X->capTS, TS));
+        X->capTS = TS;
     }
-    if (Bbytes > H->capB) {
-        uint8_t *b = static_cast<uint8_t *>(H->Bmma);
-        TRY(grow(H, b, dummy, H->capB, Bbytes));
-        H->Bmma = b;
-        H->capB = Bbytes;
+    if (Bbytes > X->capB) {
+        uint8_t *b = static_cast<uint8_t *>(X->Bmma);
+        TRY(grow(X->mem, b, X->capB, Bbytes));
+        X->Bmma = b;
+        X->capB = Bbytes;
     }
-    if (!H->dev_err) {
-        TRY(H->mem.alloc(&H->dev_err, 1));
-        CK(cudaMemset(H->dev_err, 0, sizeof(int)));
+    if (!X->dev_err) {
+        TRY(X->mem.alloc(&X->dev_err, 1));
+        CK(cudaMemset(X->dev_err, 0, sizeof(int)));
     }
-    if (N > H->capN) {
-        TRY(grow(H, H->states, dummy, H->capN, N));
-        H->capN = N;
+    if (N > X->capN) {
+        TRY(grow(X->mem, X->states, X->capN, N));
+        TRY(grow(X->mem, X->tin, X->capN, N));
+        if (X->tin_host) cudaFreeHost(X->tin_host);
+        if (X->states_host) cudaFreeHost(X->states_host);
+        X->tin_host = nullptr;
+        X->states_host = nullptr;
+        if (cudaMallocHost(&X->tin_host, N * sizeof(TmplIn)) != cudaSuccess ||
+            cudaMallocHost(&X->states_host, N * sizeof(TmplState)) != cudaSuccess) {
+            cudaGetLastError();
+            return OPTA_ERR_OOM;
+        }
+        X->capN = N;
+    }
+    if (!X->err_host) {
+        if (cudaMallocHost(&X->err_host, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return OPTA_ERR_OOM;
+        }
     }
     return OPTA_OK;
 }
@@ -612,43 +649,59 @@ float scan1_eps_factor(const opta_handle *H, int m, int n) {
 }
 
 // Scratch needed by a batch of templates (sizes already prepared).
-opta_status size_scratch(opta_handle *H, const opta_template *t, int n_t) {
-    size_t maxL = 0, maxRT = 0, maxT = 0, maxTS = 0, maxB = 0, maxTB = 1;
+// Scratch capacities a batch of templates needs: L locations per template,
+// TB scan-2 slots, RT = chunk x G centre values, T / TS template elements of
+// a chunk, B bytes of tensor-core operands and N template states.  A size
+// not prepared yet is planned at its largest (h = 1: G = L).
+struct ScratchPlan {
+    size_t L = 0, TB = 1, RT = 0, T = 0, TS = 0, B = 0, N = 0;
+};
+
+ScratchPlan plan_scratch(opta_handle *H, const opta_template *t, int n_t) {
+    ScratchPlan c;
     std::map<std::pair<int, int>, int> count;
     for (int i = 0; i < n_t; ++i) count[std::make_pair(t[i].rows, t[i].cols)]++;
     for (auto &kv : count) {
-        SizeState *S = H->sizes[kv.first];
+        SizeState *S = size_of(H, kv.first);
         const int m = kv.first.first, n = kv.first.second, npad = (n + 7) & ~7, Kp = (n + 15) & ~15;
         const size_t chunk = (size_t)std::min(kv.second, kChunk);
-        const size_t G = (size_t)S->Gy * S->Gx;
-        maxL = std::max(maxL, (size_t)S->Ly * S->Lx);
-        maxTB = std::max(maxTB, (size_t)scan2_batch((size_t)S->Ly * S->Lx, (int)chunk));
-        maxRT = std::max(maxRT, chunk * G);
-        maxT = std::max(maxT, chunk * (size_t)m * n);
-        maxTS = std::max(maxTS, chunk * (size_t)m * npad);
+        const size_t L = (size_t)(H->p - m + 1) * (H->q - n + 1);
+        const size_t G = S ? (size_t)S->Gy * S->Gx : L;
+        c.L = std::max(c.L, L);
+        c.TB = std::max(c.TB, (size_t)scan2_batch(L, (int)chunk));
+        c.RT = std::max(c.RT, chunk * G);
+        c.T = std::max(c.T, chunk * (size_t)m * n);
+        c.TS = std::max(c.TS, chunk * (size_t)m * npad);
         const size_t N = ((2 * chunk + 15) / 16) * 16;
-        if (use_mma(H)) maxB = std::max(maxB, (size_t)m * Kp * N * 2);
+        if (use_mma(H)) c.B = std::max(c.B, (size_t)m * Kp * N * 2);
     }
-    return ensure_scratch(H, maxL, maxTB, maxRT, maxT, maxTS, maxB, (size_t)n_t);
+    c.N = (size_t)n_t;
+    return c;
+}
+
+opta_status size_scratch(opta_handle *H, opta_search_ctx *X, const opta_template *t, int n_t) {
+    const ScratchPlan c = plan_scratch(H, t, n_t);
+    return ensure_scratch(X, c.L, c.TB, c.RT, c.T, c.TS, c.B, c.N);
 }
 
 // Template statistics and scan 1 (Section 6: rho(t, pivot) at every centre)
 // of templates t[0..n) -- all of one size -- into the chunk slots; states
 // st[0..n).  No host synchronisation.
-opta_status enqueue_scan1(opta_handle *H, const opta_template *const *t, int n, TmplState *st,
+opta_status enqueue_scan1(opta_handle *H, opta_search_ctx *X, const opta_template *const *t, int n, TmplState *st,
                           cudaStream_t s) {
     const int m = t[0]->rows, nn = t[0]->cols, npad = (nn + 7) & ~7, Kp = (nn + 15) & ~15;
-    SizeState *S = H->sizes[std::make_pair(m, nn)];
+    SizeState *S = size_of(H, std::make_pair(m, nn));
     const int64_t G = (int64_t)S->Gy * S->Gx;
     const size_t tsz = (size_t)m * npad, dsz = (size_t)m * nn;
     // template statistics (Eq. rho1's mu_t, sigma_t) of the whole chunk in one launch
-    std::vector<TmplIn> tin(n);
+    const ptrdiff_t slot0 = st - X->states;
+    TmplIn *tin = X->tin_host + slot0;
     for (int k = 0; k < n; ++k) {
         if (t[k]->on_device) {
             tin[k].data = t[k]->data;
             tin[k].ld = t[k]->stride_elems;
         } else {
-            float *slot = H->tstage + (size_t)k * m * nn;
+            float *slot = X->tstage + (size_t)k * m * nn;
             CK(cudaMemcpy2DAsync(slot, (size_t)nn * sizeof(float), t[k]->data,
                                  (size_t)t[k]->stride_elems * sizeof(float),
                                  (size_t)nn * sizeof(float), m, cudaMemcpyHostToDevice, s));
@@ -656,83 +709,84 @@ opta_status enqueue_scan1(opta_handle *H, const opta_template *const *t, int n, 
             tin[k].ld = nn;
         }
     }
-    CK(cudaMemcpyAsync(H->tin, tin.data(), n * sizeof(TmplIn), cudaMemcpyHostToDevice, s));
-    CK(launch_tmpl_prep_batch(H->tin, n, m, nn, npad, H->tf, tsz, H->td, dsz, st, H->prm.topk, s));
+    CK(cudaMemcpyAsync(X->tin + slot0, tin, n * sizeof(TmplIn), cudaMemcpyHostToDevice, s));
+    CK(launch_tmpl_prep_batch(X->tin + slot0, n, m, nn, npad, X->tf, tsz, X->td, dsz, st,
+                              H->prm.topk, s));
     // scan 1: rho(t, pivot) at every centre
     if (use_mma(H)) {
         const int N = ((2 * n + 15) / 16) * 16;
-        CK(cudaMemsetAsync(H->Bmma, 0, (size_t)m * Kp * N * 2, s));
-        CK(launch_tmpl_split(H->tf, tsz, n, m, nn, npad, Kp, N, H->Bmma, s));
+        CK(cudaMemsetAsync(X->Bmma, 0, (size_t)m * Kp * N * 2, s));
+        CK(launch_tmpl_split(X->tf, tsz, n, m, nn, npad, Kp, N, X->Bmma, s));
         int Gx_u = S->Gx;
-        CK(launch_corr_mma(S->P, H->p, H->q, H->Bmma, m, nn, Kp, N, S->h, S->Ly, S->Lx, n,
-                           S->c_inv_sigma, st, H->rho_tc, G, H->dev_err, &Gx_u, s));
+        CK(launch_corr_mma(S->P, H->p, H->q, X->Bmma, m, nn, Kp, N, S->h, S->Ly, S->Lx, n,
+                           S->c_inv_sigma, st, X->rho_tc, G, X->dev_err, &Gx_u, s));
         for (int gx = Gx_u; gx < S->Gx; ++gx)
-            CK(launch_centre_column(S->P, H->q, H->tf, m, nn, npad, tsz, S->h, S->Ly, S->Lx, gx, n,
-                                    S->c_inv_sigma, st, H->rho_tc, G, s));
+            CK(launch_centre_column(S->P, H->q, X->tf, m, nn, npad, tsz, S->h, S->Ly, S->Lx, gx, n,
+                                    S->c_inv_sigma, st, X->rho_tc, G, s));
     } else {
         for (int k = 0; k < n; ++k)
-            CK(launch_centre_rho(S->P, H->p, H->q, H->tf + k * tsz, m, nn, npad, S->h, S->Ly,
-                                 S->Lx, S->c_inv_sigma, st + k, H->rho_tc + k * G, 0, s));
+            CK(launch_centre_rho(S->P, H->p, H->q, X->tf + k * tsz, m, nn, npad, S->h, S->Ly,
+                                 S->Lx, S->c_inv_sigma, st + k, X->rho_tc + k * G, 0, s));
     }
     // threshold (Section 6): top-k centres, their exact rho, the members of
     // their groups -- batched over the chunk
-    CK(launch_topk(H->rho_tc, G, S->Gy, S->Gx, S->h, S->Ly, S->Lx, H->prm.topk, n, st, H->topk_v,
-                   H->topk_i, H->cand_topk, s));
-    CK(launch_refine64_topk(S->M, H->q, S->Lx, H->td, dsz, m, nn, n, st, H->cand_topk,
-                            H->cand_rho_topk, s));
-    CK(launch_group_members(S->M, H->q, S->Ly, S->Lx, S->h, S->wsumM, H->tf, tsz, m, nn,
-                            npad, S->invM, n, st, H->cand_topk, H->prm.topk, s));
-    CK(launch_threshold(st, H->cand_rho_topk, n, s));
+    CK(launch_topk(X->rho_tc, G, S->Gy, S->Gx, S->h, S->Ly, S->Lx, H->prm.topk, n, st, X->topk_v,
+                   X->topk_i, X->cand_topk, s));
+    CK(launch_refine64_topk(S->M, H->q, S->Lx, X->td, dsz, m, nn, n, st, X->cand_topk,
+                            X->cand_rho_topk, s));
+    CK(launch_group_members(S->M, H->q, S->Ly, S->Lx, S->h, S->wsumM, X->tf, tsz, m, nn,
+                            npad, S->invM, n, st, X->cand_topk, H->prm.topk, s));
+    CK(launch_threshold(st, X->cand_rho_topk, n, s));
     return OPTA_OK;
 }
 
 // Scan 2 (Eq. SEC), survivors and FP64 argmax of the chunk whose scan 1 and
 // threshold are done, in batches of scan2_batch() templates per launch.
-opta_status enqueue_scan2(opta_handle *H, const opta_template *const *t, int n, TmplState *st,
+opta_status enqueue_scan2(opta_handle *H, opta_search_ctx *X, const opta_template *const *t, int n, TmplState *st,
                           float *ub_map, uint8_t *surv_map, cudaStream_t s) {
     const int m = t[0]->rows, nn = t[0]->cols, npad = (nn + 7) & ~7;
-    SizeState *S = H->sizes[std::make_pair(m, nn)];
+    SizeState *S = size_of(H, std::make_pair(m, nn));
     const int64_t L = (int64_t)S->Ly * S->Lx;
     const int64_t G = (int64_t)S->Gy * S->Gx;
     const size_t tsz = (size_t)m * npad, dsz = (size_t)m * nn;
-    const int TB = std::min(scan2_batch((size_t)L, n), (int)H->capS2);
-    const int64_t scap = (int64_t)H->capL;
+    const int TB = std::min(scan2_batch((size_t)L, n), (int)X->capS2);
+    const int64_t scap = (int64_t)X->capL;
     if (TB < 1 || ((ub_map || surv_map) && n != 1)) return OPTA_ERR_INVALID_ARG;
     for (int k0 = 0; k0 < n; k0 += TB) {
         const int T = std::min(TB, n - k0);
         Scan2Batch B;
         B.T = T;
         B.st = st + k0;
-        B.rho_tc = H->rho_tc + k0 * G;
+        B.rho_tc = X->rho_tc + k0 * G;
         B.tc_stride = G;
         B.c_efac = S->c_efac;
         B.epsA = scan1_eps_factor(H, m, nn);
-        B.tf = H->tf + k0 * tsz;
+        B.tf = X->tf + k0 * tsz;
         B.tsz = tsz;
-        B.surv = H->surv;
-        B.surv_ub = H->surv_ub;
-        B.surv_rho = H->surv_rho;
-        B.surv_eps = H->surv_eps;
+        B.surv = X->surv;
+        B.surv_ub = X->surv_ub;
+        B.surv_rho = X->surv_rho;
+        B.surv_eps = X->surv_eps;
         B.scap = scap;
-        B.cand = H->cand;
+        B.cand = X->cand;
         B.ccap = scap;
-        B.ucnt = H->ucnt;
-        B.bucket_cnt = H->bucket_cnt;
-        B.bucket_cur = H->bucket_cur;
+        B.ucnt = X->ucnt;
+        B.bucket_cnt = X->bucket_cnt;
+        B.bucket_cur = X->bucket_cur;
         CK(launch_bound_compact(B, S->theta_co, S->gco, S->Ly, S->Lx, S->h, ub_map, surv_map, s));
         CK(launch_survivors(B, S->M, H->p, H->q, S->Lx, S->wsumM, m, nn, npad, S->invM, s));
         CK(launch_surv_candidates(B, s));
-        CK(launch_refine64(S->M, H->q, S->Lx, H->td + k0 * dsz, dsz, m, nn, T, st + k0, H->cand,
-                           H->cand_rho, scap, s));
-        CK(launch_final_argmax(T, st + k0, H->cand, H->cand_rho, scap, H->cand_topk + k0 * kTopkMax,
-                               H->cand_rho_topk + k0 * kTopkMax, s));
+        CK(launch_refine64(S->M, H->q, S->Lx, X->td + k0 * dsz, dsz, m, nn, T, st + k0, X->cand,
+                           X->cand_rho, scap, s));
+        CK(launch_final_argmax(T, st + k0, X->cand, X->cand_rho, scap, X->cand_topk + k0 * kTopkMax,
+                               X->cand_rho_topk + k0 * kTopkMax, s));
         if (H->prm.literal) {
             // Section 4.3: t matched with I in FP64 over the (2d+1)^2
             // neighbourhood of the maximum found on the blurred image
-            CK(launch_rematch_window(T, st + k0, S->Ly, S->Lx, S->d, H->cand, scap, s));
-            CK(launch_refine64(H->I8, H->q, S->Lx, H->td + k0 * dsz, dsz, m, nn, T, st + k0,
-                               H->cand, H->cand_rho, scap, s));
-            CK(launch_final_argmax(T, st + k0, H->cand, H->cand_rho, scap, nullptr, nullptr, s));
+            CK(launch_rematch_window(T, st + k0, S->Ly, S->Lx, S->d, X->cand, scap, s));
+            CK(launch_refine64(H->I8, H->q, S->Lx, X->td + k0 * dsz, dsz, m, nn, T, st + k0,
+                               X->cand, X->cand_rho, scap, s));
+            CK(launch_final_argmax(T, st + k0, X->cand, X->cand_rho, scap, nullptr, nullptr, s));
         }
     }
     return OPTA_OK;
@@ -740,7 +794,7 @@ opta_status enqueue_scan2(opta_handle *H, const opta_template *const *t, int n, 
 
 // Group templates by size (stable) and enqueue them chunk by chunk; order[i]
 // is the input index of the template whose state is states[i].
-opta_status enqueue_all(opta_handle *H, const opta_template *t, int n_t, std::vector<int> &order,
+opta_status enqueue_all(opta_handle *H, opta_search_ctx *X, const opta_template *t, int n_t, std::vector<int> &order,
                         cudaStream_t s) {
     order.resize(n_t);
     for (int i = 0; i < n_t; ++i) order[i] = i;
@@ -757,8 +811,8 @@ opta_status enqueue_all(opta_handle *H, const opta_template *t, int n_t, std::ve
             chunk.push_back(&t[order[j]]);
             ++j;
         }
-        TRY(enqueue_scan1(H, chunk.data(), (int)chunk.size(), H->states + i, s));
-        TRY(enqueue_scan2(H, chunk.data(), (int)chunk.size(), H->states + i, nullptr, nullptr, s));
+        TRY(enqueue_scan1(H, X, chunk.data(), (int)chunk.size(), X->states + i, s));
+        TRY(enqueue_scan2(H, X, chunk.data(), (int)chunk.size(), X->states + i, nullptr, nullptr, s));
         i = j;
     }
     return OPTA_OK;
@@ -794,6 +848,99 @@ struct BusyGuard {
     explicit BusyGuard(opta_handle *hh) : h(hh) { h->busy = true; }
     ~BusyGuard() { h->busy = false; }
 };
+
+// Releases a context claimed with compare_exchange on its busy flag.
+struct CtxGuard {
+    opta_search_ctx *x;
+    explicit CtxGuard(opta_search_ctx *xx) : x(xx) {}
+    ~CtxGuard() { x->busy.store(false); }
+};
+
+void free_ctx(opta_search_ctx *X) {
+    void *ptrs[] = {X->rho_tc, X->surv, X->surv_rho, X->surv_eps, X->surv_ub, X->ucnt,
+                    X->bucket_cnt, X->bucket_cur, X->Bmma, X->dev_err, X->cand_topk,
+                    X->cand_rho_topk, X->tin, X->cand, X->cand_rho, X->topk_v, X->topk_i,
+                    X->tf, X->tstage, X->td, X->states};
+    for (void *p : ptrs) if (p) cudaFree(p);
+    if (X->tin_host) cudaFreeHost(X->tin_host);
+    if (X->states_host) cudaFreeHost(X->states_host);
+    if (X->err_host) cudaFreeHost(X->err_host);
+    delete X;
+}
+
+}  // namespace
+
+// A captured batched search (optA_graph_*): its own context, the templates'
+// device buffers and the instantiated graph.
+struct opta_graph {
+    opta_handle *h = nullptr;
+    opta_search_ctx *X = nullptr;
+    int n_t = 0;
+    float *tbuf = nullptr;
+    std::vector<opta_template> desc;
+    std::vector<int> order;
+    cudaStream_t s = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    size_t nodes = 0;
+};
+
+namespace {
+
+void destroy_graph(opta_graph *G) {
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    if (G->graph) cudaGraphDestroy(G->graph);
+    if (G->s) cudaStreamDestroy(G->s);
+    if (G->tbuf) cudaFree(G->tbuf);
+    if (G->X) free_ctx(G->X);
+    delete G;
+}
+
+opta_status default_ctx(opta_handle *H) {
+    if (H->dctx) return OPTA_OK;
+    opta_search_ctx *X = new (std::nothrow) opta_search_ctx();
+    if (!X) return OPTA_ERR_OOM;
+    X->device = H->device;
+    H->dctx = X;
+    return OPTA_OK;
+}
+
+// One search through context X (claimed by the caller): missing sizes are
+// prepared first (one preparation at a time per handle), then the prepared
+// sizes are read under a shared lock while the search's kernels run on s.
+opta_status search_in(opta_handle *H, opta_search_ctx *X, const opta_template *t, int32_t n_t,
+                      opta_result *out, cudaStream_t s) {
+    std::vector<std::pair<int, int>> todo;
+    for (int i = 0; i < n_t; ++i) {
+        if (!valid_template(&t[i], H->p, H->q)) return OPTA_ERR_INVALID_ARG;
+        todo.emplace_back(t[i].rows, t[i].cols);
+    }
+    {
+        std::lock_guard<std::mutex> pl(H->prep_mu);
+        TRY(prepare_sizes(H, todo, s));
+    }
+    if (n_t == 0) return OPTA_OK;
+    std::shared_lock<std::shared_mutex> rl(H->sizes_rw);
+    TRY(size_scratch(H, X, t, n_t));
+    std::vector<int> order;
+    TRY(enqueue_all(H, X, t, n_t, order, s));
+    CK(cudaMemcpyAsync(X->states_host, X->states, sizeof(TmplState) * n_t, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(X->err_host, X->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const TmplState *hs = X->states_host;
+    const int herr = *X->err_host;
+    opta_status first = OPTA_OK;
+    for (int k = 0; k < n_t; ++k) {
+        const int i = order[k];
+        SizeState *S = size_of(H, std::make_pair(t[i].rows, t[i].cols));
+        fill_result(hs[k], S, S->Lx, (int64_t)S->Ly * S->Lx, S->h, (int64_t)S->Gy * S->Gx, &out[i]);
+        if (herr) out[i].status = OPTA_ERR_TIMEOUT;
+    }
+    for (int i = 0; i < n_t; ++i)
+        if (first == OPTA_OK && out[i].status != OPTA_OK) first = (opta_status)out[i].status;
+    if (herr) CK(cudaMemsetAsync(X->dev_err, 0, sizeof(int), s));
+    return first;
+}
 
 opta_status setup_tables(opta_handle *H) {
     std::vector<float> w;
@@ -861,12 +1008,9 @@ opta_status optA_destroy(opta_handle *h) {
         if (S->M_owned) { cudaFree(S->wsumM); cudaFree(S->invM); }
         delete S;
     }
-    void *ptrs[] = {h->I8, h->IIS, h->IIQ, h->rho_tc, h->surv, h->surv_rho, h->surv_eps,
-                    h->surv_ub, h->ucnt, h->bucket_cnt, h->bucket_cur, h->Bmma, h->dev_err,
-                    h->cand_topk, h->cand_rho_topk, h->tin,
-                    h->cand, h->cand_rho, h->topk_v, h->topk_i, h->tf, h->tstage, h->td,
-                    h->states, h->weights, h->radius};
+    void *ptrs[] = {h->I8, h->IIS, h->IIQ, h->weights, h->radius};
     for (void *p : ptrs) if (p) cudaFree(p);
+    if (h->dctx) free_ctx(h->dctx);
     if (h->pool) {
         cudaDeviceSynchronize();   // stream-ordered frees of the preparation have completed
         cudaMemPoolDestroy(h->pool);
@@ -931,38 +1075,217 @@ opta_status optA_prepare(const opta_image *img, const opta_params *prm, const in
     return OPTA_OK;
 }
 
+opta_status optA_ctx_create(const opta_handle *h, opta_search_ctx **out) {
+    if (!h || !out) return OPTA_ERR_INVALID_ARG;
+    *out = nullptr;
+    opta_search_ctx *X = new (std::nothrow) opta_search_ctx();
+    if (!X) return OPTA_ERR_OOM;
+    X->device = h->device;
+    *out = X;
+    return OPTA_OK;
+}
+
+opta_status optA_ctx_destroy(opta_search_ctx *X) {
+    if (!X) return OPTA_OK;
+    if (X->busy.load()) return OPTA_ERR_BUSY;
+    free_ctx(X);
+    return OPTA_OK;
+}
+
+opta_status optA_ctx_memory_bytes(const opta_search_ctx *X, size_t *bytes) {
+    if (!X || !bytes) return OPTA_ERR_INVALID_ARG;
+    *bytes = X->mem.bytes.load();
+    return OPTA_OK;
+}
+
+opta_status optA_ctx_bytes_after(opta_handle *h, const opta_search_ctx *X,
+                                 const opta_template *t, int32_t n_t, size_t *bytes) {
+    if (!h || !X || !bytes || n_t < 0 || (n_t > 0 && !t)) return OPTA_ERR_INVALID_ARG;
+    for (int i = 0; i < n_t; ++i)
+        if (!valid_template(&t[i], h->p, h->q)) return OPTA_ERR_INVALID_ARG;
+    ScratchPlan c;
+    {
+        std::shared_lock<std::shared_mutex> rl(h->sizes_rw);
+        c = plan_scratch(h, t, n_t);
+    }
+    // the capacities ensure_scratch keeps: the larger of the held and the needed
+    const size_t L = std::max(c.L, X->capL), TB = std::max(c.TB, X->capS2);
+    const size_t RT = std::max(c.RT, X->capG), T = std::max(c.T, X->capT);
+    const size_t TS = std::max(c.TS, X->capTS), B = std::max(c.B, X->capB);
+    const size_t N = std::max(c.N, X->capN);
+    const size_t fixed = (size_t)kChunk * 256 * kTopkMax * (sizeof(float) + sizeof(int)) +
+                         (size_t)kChunk * kTopkMax * (sizeof(int) + sizeof(double)) +
+                         (size_t)kScan2MaxT * (2 * kUbBuckets + 1) * sizeof(int) + sizeof(int);
+    *bytes = L * TB * (4 * sizeof(float) + sizeof(int) + sizeof(double)) + RT * sizeof(float) +
+             T * sizeof(float) + TS * (sizeof(float) + sizeof(double)) + B +
+             N * (sizeof(TmplState) + sizeof(TmplIn)) + fixed;
+    return OPTA_OK;
+}
+
+opta_status optA_search_ctx(opta_handle *h, opta_search_ctx *X, const opta_template *t,
+                            int32_t n_t, opta_result *out, void *stream) {
+    if (!h || !X || X->device != h->device || n_t < 0 || (n_t > 0 && (!t || !out)))
+        return OPTA_ERR_INVALID_ARG;
+    bool idle = false;
+    if (!X->busy.compare_exchange_strong(idle, true)) return OPTA_ERR_BUSY;
+    CtxGuard guard(X);
+    return search_in(h, X, t, n_t, out, static_cast<cudaStream_t>(stream));
+}
+
+opta_status optA_graph_create(opta_handle *h, const opta_template *t, int32_t n_t, void *stream,
+                              opta_graph **out) {
+    if (!h || !out || n_t < 1 || !t) return OPTA_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int i = 0; i < n_t; ++i)
+        if (!valid_template(&t[i], h->p, h->q)) return OPTA_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    opta_graph *G = new (std::nothrow) opta_graph();
+    if (!G) return OPTA_ERR_OOM;
+    G->h = h;
+    G->n_t = n_t;
+    auto fail = [&](opta_status st) {
+        destroy_graph(G);
+        return st;
+    };
+    if (optA_ctx_create(h, &G->X) != OPTA_OK) return fail(OPTA_ERR_OOM);
+    // the templates' device buffers (64-byte aligned), filled with the given data
+    std::vector<size_t> off(n_t);
+    size_t total = 0;
+    for (int i = 0; i < n_t; ++i) {
+        off[i] = total;
+        total += ((size_t)t[i].rows * t[i].cols + 15) & ~(size_t)15;
+    }
+    if (cudaMalloc(&G->tbuf, total * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(OPTA_ERR_OOM);
+    }
+    G->desc.resize(n_t);
+    for (int i = 0; i < n_t; ++i) {
+        opta_template &d = G->desc[i];
+        std::memset(&d, 0, sizeof(d));
+        d.rows = t[i].rows;
+        d.cols = t[i].cols;
+        d.stride_elems = t[i].cols;
+        d.on_device = 1;
+        d.data = G->tbuf + off[i];
+        if (cudaMemcpy2DAsync(G->tbuf + off[i], (size_t)d.cols * sizeof(float), t[i].data,
+                              (size_t)t[i].stride_elems * sizeof(float), (size_t)d.cols * sizeof(float),
+                              d.rows, cudaMemcpyDefault, s) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(OPTA_ERR_CUDA);
+        }
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(map_err(cudaGetLastError()));
+    // one search as it runs without the graph: prepares the sizes, grows the
+    // scratch to its final size and tunes scan 1's tiles
+    {
+        std::vector<opta_result> warm(n_t);
+        G->X->busy.store(true);
+        const opta_status st = search_in(h, G->X, G->desc.data(), n_t, warm.data(), s);
+        G->X->busy.store(false);
+        if (st != OPTA_OK && st != OPTA_ERR_FLAT_TEMPLATE) return fail(st);
+    }
+    if (cudaStreamCreateWithFlags(&G->s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(OPTA_ERR_CUDA);
+    }
+    // capture: the whole batched search, then the copies of its results to
+    // the context's pinned mirrors
+    std::shared_lock<std::shared_mutex> rl(h->sizes_rw);
+    opta_search_ctx *X = G->X;
+    if (cudaStreamBeginCapture(G->s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(OPTA_ERR_CUDA);
+    }
+    opta_status st = OPTA_OK;
+    if (cudaMemsetAsync(X->dev_err, 0, sizeof(int), G->s) != cudaSuccess) st = OPTA_ERR_CUDA;
+    if (st == OPTA_OK) st = enqueue_all(h, X, G->desc.data(), n_t, G->order, G->s);
+    if (st == OPTA_OK &&
+        (cudaMemcpyAsync(X->states_host, X->states, sizeof(TmplState) * n_t,
+                         cudaMemcpyDeviceToHost, G->s) != cudaSuccess ||
+         cudaMemcpyAsync(X->err_host, X->dev_err, sizeof(int), cudaMemcpyDeviceToHost, G->s) !=
+             cudaSuccess))
+        st = OPTA_ERR_CUDA;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(G->s, &graph);
+    if (st == OPTA_OK && ec != cudaSuccess) st = map_err(ec);
+    if (st != OPTA_OK) {
+        cudaGetLastError();
+        if (graph) cudaGraphDestroy(graph);
+        rl.unlock();
+        return fail(st);
+    }
+    G->graph = graph;
+    if (cudaGraphInstantiate(&G->exec, graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        rl.unlock();
+        return fail(OPTA_ERR_CUDA);
+    }
+    size_t nodes = 0;
+    cudaGraphGetNodes(graph, nullptr, &nodes);
+    G->nodes = nodes;
+    *out = G;
+    return OPTA_OK;
+}
+
+opta_status optA_graph_set_template(opta_graph *G, int32_t i, const opta_template *t, void *stream) {
+    if (!G || !t || !t->data || i < 0 || i >= G->n_t) return OPTA_ERR_INVALID_ARG;
+    const opta_template &d = G->desc[i];
+    if (t->rows != d.rows || t->cols != d.cols || t->stride_elems < t->cols) return OPTA_ERR_INVALID_ARG;
+    CK(cudaMemcpy2DAsync(const_cast<float *>(d.data), (size_t)d.cols * sizeof(float), t->data,
+                         (size_t)t->stride_elems * sizeof(float), (size_t)d.cols * sizeof(float),
+                         d.rows, cudaMemcpyDefault, static_cast<cudaStream_t>(stream)));
+    return OPTA_OK;
+}
+
+opta_status optA_graph_launch(opta_graph *G, opta_result *out, void *stream) {
+    if (!G || !out) return OPTA_ERR_INVALID_ARG;
+    opta_search_ctx *X = G->X;
+    bool idle = false;
+    if (!X->busy.compare_exchange_strong(idle, true)) return OPTA_ERR_BUSY;
+    CtxGuard cg(X);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaGraphLaunch(G->exec, s));
+    CK(cudaStreamSynchronize(s));
+    std::shared_lock<std::shared_mutex> rl(G->h->sizes_rw);
+    const int herr = *X->err_host;
+    opta_status first = OPTA_OK;
+    for (int k = 0; k < G->n_t; ++k) {
+        const int i = G->order[k];
+        const opta_template &d = G->desc[i];
+        SizeState *S = size_of(G->h, std::make_pair(d.rows, d.cols));
+        fill_result(X->states_host[k], S, S->Lx, (int64_t)S->Ly * S->Lx, S->h,
+                    (int64_t)S->Gy * S->Gx, &out[i]);
+        if (herr) out[i].status = OPTA_ERR_TIMEOUT;
+    }
+    for (int i = 0; i < G->n_t; ++i)
+        if (first == OPTA_OK && out[i].status != OPTA_OK) first = (opta_status)out[i].status;
+    return first;
+}
+
+opta_status optA_graph_info(const opta_graph *G, int64_t *nodes) {
+    if (!G || !nodes) return OPTA_ERR_INVALID_ARG;
+    *nodes = (int64_t)G->nodes;
+    return OPTA_OK;
+}
+
+opta_status optA_graph_destroy(opta_graph *G) {
+    if (!G) return OPTA_OK;
+    if (G->X && G->X->busy.load()) return OPTA_ERR_BUSY;
+    destroy_graph(G);
+    return OPTA_OK;
+}
+
 opta_status optA_search(opta_handle *h, const opta_template *t, int32_t n_t, opta_result *out,
                         void *stream) {
     if (!h || n_t < 0 || (n_t > 0 && (!t || !out))) return OPTA_ERR_INVALID_ARG;
     if (h->busy) return OPTA_ERR_BUSY;
     BusyGuard guard(h);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    std::vector<std::pair<int, int>> todo;
-    for (int i = 0; i < n_t; ++i) {
-        if (!valid_template(&t[i], h->p, h->q)) return OPTA_ERR_INVALID_ARG;
-        todo.emplace_back(t[i].rows, t[i].cols);
-    }
-    TRY(prepare_sizes(h, todo, s));
-    if (n_t == 0) return OPTA_OK;
-    TRY(size_scratch(h, t, n_t));
-    std::vector<int> order;
-    TRY(enqueue_all(h, t, n_t, order, s));
-    std::vector<TmplState> hs(n_t);
-    int herr = 0;
-    CK(cudaMemcpyAsync(hs.data(), h->states, sizeof(TmplState) * n_t, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&herr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    opta_status first = OPTA_OK;
-    for (int k = 0; k < n_t; ++k) {
-        const int i = order[k];
-        SizeState *S = h->sizes[std::make_pair(t[i].rows, t[i].cols)];
-        fill_result(hs[k], S, S->Lx, (int64_t)S->Ly * S->Lx, S->h, (int64_t)S->Gy * S->Gx, &out[i]);
-        if (herr) out[i].status = OPTA_ERR_TIMEOUT;
-    }
-    for (int i = 0; i < n_t; ++i)
-        if (first == OPTA_OK && out[i].status != OPTA_OK) first = (opta_status)out[i].status;
-    if (herr) CK(cudaMemsetAsync(h->dev_err, 0, sizeof(int), s));
-    return first;
+    TRY(default_ctx(h));
+    bool idle = false;
+    if (!h->dctx->busy.compare_exchange_strong(idle, true)) return OPTA_ERR_BUSY;
+    CtxGuard cg(h->dctx);
+    return search_in(h, h->dctx, t, n_t, out, static_cast<cudaStream_t>(stream));
 }
 
 opta_status optA_debug_bounds(opta_handle *h, const opta_template *t, float *ub_map,
@@ -971,16 +1294,23 @@ opta_status optA_debug_bounds(opta_handle *h, const opta_template *t, float *ub_
     if (!valid_template(t, h->p, h->q)) return OPTA_ERR_INVALID_ARG;
     if (h->busy) return OPTA_ERR_BUSY;
     BusyGuard guard(h);
+    TRY(default_ctx(h));
+    opta_search_ctx *X = h->dctx;
+    bool idle = false;
+    if (!X->busy.compare_exchange_strong(idle, true)) return OPTA_ERR_BUSY;
+    CtxGuard cg(X);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    TRY(prepare_size(h, t->rows, t->cols, s));
-    SizeState *S = h->sizes[std::make_pair(t->rows, t->cols)];
-    (void)S;
-    TRY(size_scratch(h, t, 1));
+    {
+        std::lock_guard<std::mutex> pl(h->prep_mu);
+        TRY(prepare_size(h, t->rows, t->cols, s));
+    }
+    std::shared_lock<std::shared_mutex> rl(h->sizes_rw);
+    TRY(size_scratch(h, X, t, 1));
     const opta_template *one = t;
-    TRY(enqueue_scan1(h, &one, 1, h->states, s));
-    TRY(enqueue_scan2(h, &one, 1, h->states, ub_map, survived, s));
+    TRY(enqueue_scan1(h, X, &one, 1, X->states, s));
+    TRY(enqueue_scan2(h, X, &one, 1, X->states, ub_map, survived, s));
     TmplState st;
-    CK(cudaMemcpyAsync(&st, h->states, sizeof(st), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&st, X->states, sizeof(st), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return st.flat ? OPTA_ERR_FLAT_TEMPLATE : OPTA_OK;
 }
@@ -994,25 +1324,34 @@ opta_status optA_debug_scan1(opta_handle *h, const opta_template *t, int32_t n_t
     }
     if (h->busy) return OPTA_ERR_BUSY;
     BusyGuard guard(h);
+    TRY(default_ctx(h));
+    opta_search_ctx *X = h->dctx;
+    bool idle = false;
+    if (!X->busy.compare_exchange_strong(idle, true)) return OPTA_ERR_BUSY;
+    CtxGuard cg(X);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    TRY(prepare_size(h, t[0].rows, t[0].cols, s));
-    SizeState *S = h->sizes[std::make_pair(t[0].rows, t[0].cols)];
-    TRY(size_scratch(h, t, n_t));
+    {
+        std::lock_guard<std::mutex> pl(h->prep_mu);
+        TRY(prepare_size(h, t[0].rows, t[0].cols, s));
+    }
+    std::shared_lock<std::shared_mutex> rl(h->sizes_rw);
+    SizeState *S = size_of(h, std::make_pair(t[0].rows, t[0].cols));
+    TRY(size_scratch(h, X, t, n_t));
     std::vector<const opta_template *> ptrs(n_t);
     for (int i = 0; i < n_t; ++i) ptrs[i] = &t[i];
-    TRY(enqueue_scan1(h, ptrs.data(), n_t, h->states, s));
+    TRY(enqueue_scan1(h, X, ptrs.data(), n_t, X->states, s));
     const size_t G = (size_t)S->Gy * S->Gx;
     if (rho_dev)
-        CK(cudaMemcpyAsync(rho_dev, h->rho_tc, n_t * G * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(rho_dev, X->rho_tc, n_t * G * sizeof(float), cudaMemcpyDeviceToDevice, s));
     if (theta_dev)
-        CK(launch_centre_intervals(h->rho_tc, (int64_t)G, n_t, S->c_efac,
+        CK(launch_centre_intervals(X->rho_tc, (int64_t)G, n_t, S->c_efac,
                                    scan1_eps_factor(h, t[0].rows, t[0].cols),
                                    reinterpret_cast<float2 *>(theta_dev), s));
     int herr = 0;
-    CK(cudaMemcpyAsync(&herr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&herr, X->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (herr) {
-        CK(cudaMemset(h->dev_err, 0, sizeof(int)));
+        CK(cudaMemset(X->dev_err, 0, sizeof(int)));
         return OPTA_ERR_TIMEOUT;
     }
     return OPTA_OK;
@@ -1022,8 +1361,12 @@ opta_status optA_size_info(opta_handle *h, int32_t m, int32_t n, opta_size_info 
     if (!h || !info || m < 1 || n < 1 || m > h->p || n > h->q || n > 1024) return OPTA_ERR_INVALID_ARG;
     if (h->busy) return OPTA_ERR_BUSY;
     BusyGuard guard(h);
-    TRY(prepare_size(h, m, n, nullptr));
-    SizeState *S = h->sizes[std::make_pair(m, n)];
+    {
+        std::lock_guard<std::mutex> pl(h->prep_mu);
+        TRY(prepare_size(h, m, n, nullptr));
+    }
+    std::shared_lock<std::shared_mutex> rl(h->sizes_rw);
+    SizeState *S = size_of(h, std::make_pair(m, n));
     std::memset(info, 0, sizeof(*info));
     info->m = m; info->n = n;
     info->group_h = S->h;
@@ -1042,8 +1385,12 @@ opta_status optA_debug_maps(opta_handle *h, int32_t m, int32_t n, uint8_t *pivot
     if (h->busy) return OPTA_ERR_BUSY;
     BusyGuard guard(h);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    TRY(prepare_size(h, m, n, s));
-    SizeState *S = h->sizes[std::make_pair(m, n)];
+    {
+        std::lock_guard<std::mutex> pl(h->prep_mu);
+        TRY(prepare_size(h, m, n, s));
+    }
+    std::shared_lock<std::shared_mutex> rl(h->sizes_rw);
+    SizeState *S = size_of(h, std::make_pair(m, n));
     if (pivot_dev)
         CK(cudaMemcpyAsync(pivot_dev, S->P, (size_t)h->p * h->q, cudaMemcpyDeviceToDevice, s));
     if (rho_co_dev)
@@ -1057,7 +1404,7 @@ opta_status optA_debug_maps(opta_handle *h, int32_t m, int32_t n, uint8_t *pivot
 
 opta_status optA_memory_bytes(const opta_handle *h, size_t *bytes) {
     if (!h || !bytes) return OPTA_ERR_INVALID_ARG;
-    *bytes = h->mem.bytes.load();
+    *bytes = h->mem.bytes.load() + (h->dctx ? h->dctx->mem.bytes.load() : 0);
     return OPTA_OK;
 }
 

@@ -58,10 +58,20 @@ __device__ __forceinline__ void blur_tile(const uint8_t *__restrict__ I, int p, 
     const int ist = iw | 1, hst = bw | 1;
     float *in = bsm;                 // ih x ist
     float *hb = bsm + ih * ist;      // ih x hst
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int r = warp; r < ih; r += kBlurThreads / 32) {
-        const uint8_t *src = I + (int64_t)min(max(y0 - R + r, 0), p - 1) * q;
-        for (int c = lane; c < iw; c += 32) in[r * ist + c] = (float)src[min(max(x0 - R + c, 0), q - 1)];
+    {
+        // element i = (r, c) of the ih x iw tile, walked in strides of the
+        // block (row and column advanced without division); unrolled so
+        // that the loads of several elements are in flight together
+        const int dr = kBlurThreads / iw, dc = kBlurThreads - dr * iw;
+        int r = (int)threadIdx.x / iw, c = (int)threadIdx.x - r * iw;
+#pragma unroll 4
+        for (int i = threadIdx.x; i < ih * iw; i += kBlurThreads) {
+            const int yy = min(max(y0 - R + r, 0), p - 1), xx = min(max(x0 - R + c, 0), q - 1);
+            in[r * ist + c] = (float)I[(int64_t)yy * q + xx];
+            r += dr;
+            c += dc;
+            if (c >= iw) { c -= iw; ++r; }
+        }
     }
     __syncthreads();
     const int ng = (bw + CB - 1) / CB;

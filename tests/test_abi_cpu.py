@@ -19,7 +19,7 @@ def libopta():
 
 def _declared_functions():
     names = []
-    for h in ("opta.h", "opta_debug.h"):
+    for h in ("opta.h", "opta_debug.h", "opta_serve.h"):
         txt = open(os.path.join(ROOT, "include", h)).read()
         txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
         for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(",
