@@ -244,6 +244,16 @@ struct PrepScratch {
     float *invP = nullptr;
 };
 
+// Outputs of one EGS evaluation (h >= 3): the auto-correlation map and the
+// per-centre pivot statistics, kept so that the configuration finally
+// accepted need not be evaluated again.  Three slots: the accepted
+// configuration's, the best of the current EGS run and its next candidate.
+struct EvalSlot {
+    float *rco = nullptr, *cinv = nullptr, *cefac = nullptr;
+    int h = 0;        // group side evaluated into the slot (0: none)
+};
+constexpr int kEvalSlots = 3;
+
 // Members of the auto-correlation EGS measures: image M (I, or the candidate
 // pivot itself in the literal mode) with its window sums and 1/Omega.
 struct Members {
@@ -252,8 +262,10 @@ struct Members {
     const float *inv;
 };
 
-opta_status egs_cost(opta_handle *H, SizeState *S, const uint8_t *P, const Members &M, int h,
-                     unsigned long long *dcount, long long *cost, cudaStream_t s) {
+// Queue the retained count of group side h (Algorithm 2's n_r) into dcount.
+opta_status egs_launch(opta_handle *H, SizeState *S, const uint8_t *P, const Members &M, int h,
+                       unsigned long long *dcount, cudaStream_t s, EvalSlot *out) {
+    if (out) out->h = 0;
     const float cut = (float)std::sqrt(1.0 - H->prm.rho_th * H->prm.rho_th);
     CK(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), s));
     if (h == 1 && P == M.M) {
@@ -262,14 +274,25 @@ opta_status egs_cost(opta_handle *H, SizeState *S, const uint8_t *P, const Membe
         // there), so the retained count is the number of flat windows
         CK(launch_count_zero(M.inv, (int64_t)S->Ly * S->Lx, dcount, s));
     } else {
+        // the slots hold the centre statistics of h >= 3 (at most a ninth of L)
+        const bool keep = out && out->rco && h >= 3;
         CK(launch_rho_co(P, M.M, H->p, H->q, S->m, S->n, h, M.wsum, M.inv, cut,
-                         nullptr, dcount, nullptr, nullptr, s));
+                         keep ? out->rco : nullptr, dcount, keep ? out->cinv : nullptr,
+                         keep ? out->cefac : nullptr, s));
+        if (keep) out->h = h;
     }
-    unsigned long long c = 0;
-    CK(cudaMemcpyAsync(&c, dcount, sizeof(c), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    *cost = (long long)groups_along(S->Ly, h) * groups_along(S->Lx, h) + (long long)c;
     S->n_evals++;
+    return OPTA_OK;
+}
+
+// Wait for k queued counts (group sides hs[]) and turn them into costs
+// (groups + retained, Eq. objfunc).
+opta_status egs_read(SizeState *S, const int *hs, int k, const unsigned long long *dcount,
+                     unsigned long long *host, long long *cost, cudaStream_t s) {
+    CK(cudaMemcpyAsync(host, dcount, (size_t)k * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < k; ++i)
+        cost[i] = (long long)groups_along(S->Ly, hs[i]) * groups_along(S->Lx, hs[i]) + (long long)host[i];
     return OPTA_OK;
 }
 
@@ -282,29 +305,55 @@ int h_limit(int p, int q, int m, int n, int hmax) {
 }
 
 // Algorithm 2: grow h by 2 while the cost drops by more than xi of the last.
+// With slots (nullable): evaluations go to slots other than `avoid`, and
+// *best_slot receives the slot holding the chosen h's outputs (-1: none).
+// dcount: two device counters.  The first two sides (h and h + 2, both
+// always evaluated when h + 2 is allowed) are queued together and read with
+// one wait; each further side takes one more.
 opta_status egs(opta_handle *H, SizeState *S, const uint8_t *P, const Members &M, int h_start,
-                unsigned long long *dcount, int *h_out, long long *c_out, cudaStream_t s) {
+                unsigned long long *dcount, int *h_out, long long *c_out, cudaStream_t s,
+                EvalSlot *slots = nullptr, int avoid = -1, int *best_slot = nullptr) {
     const int hmax = h_limit(H->p, H->q, S->m, S->n, H->prm.h_max);
+    auto pick = [&](int a, int b) {   // a slot other than a and b
+        for (int k = 0; k < kEvalSlots; ++k)
+            if (k != a && k != b) return k;
+        return -1;
+    };
+    auto slot = [&](int k) { return k >= 0 ? &slots[k] : nullptr; };
+    unsigned long long host[2];
+    long long cost[2];
     int h = std::min(h_start, hmax);
-    long long c = 0;
-    TRY(egs_cost(H, S, P, M, h, dcount, &c, s));
-    while (h + 2 <= hmax) {
-        long long c2 = 0;
-        TRY(egs_cost(H, S, P, M, h + 2, dcount, &c2, s));
-        if ((double)(c - c2) > H->prm.xi * (double)c) { h += 2; c = c2; }
-        else break;
+    int best = slots ? pick(avoid, -1) : -1;
+    const bool pair = h + 2 <= hmax;
+    int cand = slots ? pick(avoid, best) : -1;
+    TRY(egs_launch(H, S, P, M, h, dcount, s, slot(best)));
+    if (pair) TRY(egs_launch(H, S, P, M, h + 2, dcount + 1, s, slot(cand)));
+    const int hs[2] = {h, h + 2};
+    TRY(egs_read(S, hs, pair ? 2 : 1, dcount, host, cost, s));
+    long long c = cost[0];
+    bool grow = pair;
+    long long c2 = cost[1];
+    while (grow) {
+        if (!((double)(c - c2) > H->prm.xi * (double)c)) break;
+        h += 2; c = c2; best = cand;
+        if (h + 2 > hmax) break;
+        cand = slots ? pick(avoid, best) : -1;
+        TRY(egs_launch(H, S, P, M, h + 2, dcount, s, slot(cand)));
+        const int hn[1] = {h + 2};
+        TRY(egs_read(S, hn, 1, dcount, host, cost, s));
+        c2 = cost[0];
     }
     *h_out = h;
     *c_out = c;
+    if (best_slot) *best_slot = (best >= 0 && slots[best].h == h) ? best : -1;
     return OPTA_OK;
 }
 
 opta_status blur_to(opta_handle *H, PrepScratch &W, const std::vector<uint8_t> &levels,
                     uint8_t *P, cudaStream_t s) {
     CK(cudaMemcpyAsync(W.lvl, levels.data(), levels.size(), cudaMemcpyHostToDevice, s));
+    // (a copy from pageable memory has taken the host data when it returns)
     CK(launch_blur(H->I8, H->p, H->q, W.lvl, H->prm.block, H->weights, H->radius, P, s));
-    // levels is a host vector: keep the copy ordered before it can change
-    CK(cudaStreamSynchronize(s));
     return OPTA_OK;
 }
 
@@ -338,6 +387,7 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     S->sigma_map.assign((size_t)bp * bq, 0.f);
 
     PrepScratch W;
+    EvalSlot slots[kEvalSlots];
     auto scratch = [&](auto **ptr, size_t bytes) {
         return cudaMallocFromPoolAsync(reinterpret_cast<void **>(ptr), bytes, H->pool, s);
     };
@@ -345,6 +395,11 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
         void *bufs[] = {W.Pcur, W.Pacc, W.fail, W.lvl, W.count, W.IIS, W.IIQ, W.wsumP, W.invP};
         for (void *b : bufs)
             if (b) cudaFreeAsync(b, s);
+        for (EvalSlot &e : slots) {
+            void *eb[] = {e.rco, e.cinv, e.cefac};
+            for (void *b : eb)
+                if (b) cudaFreeAsync(b, s);
+        }
         if (st != OPTA_OK) {
             if (S->M_owned) {
                 H->mem.release(S->wsumM, L);
@@ -368,7 +423,7 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     PTRY(H->mem.alloc(&S->inv_sigma, L));
     PTRY(H->mem.alloc(&S->wsum, L));
     PCK(launch_window_stats(H->IIS, H->IIQ, p, q, m, n, S->inv_sigma, nullptr, s, S->wsum));
-    PCK(scratch(&W.count, sizeof(unsigned long long)));
+    PCK(scratch(&W.count, 2 * sizeof(unsigned long long)));
     const bool literal = prm.literal != 0;
     const Members on_image{H->I8, S->wsum, S->inv_sigma};
     const size_t nII = (size_t)(p + 1) * (q + 1);
@@ -388,10 +443,19 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     int h_best = 1;
     long long c_best = 0;
     bool best_is_image = true;
+    int acc = -1;   // slot holding the accepted configuration's map (-1: none)
+    EvalSlot *sl = nullptr;
     if (prm.fixed_h > 0) {
         h_best = std::min(prm.fixed_h, h_limit(p, q, m, n, 9));
     } else {
-        PTRY(egs(H, S, H->I8, on_image, 1, W.count, &h_best, &c_best, s));
+        const size_t G3 = (size_t)groups_along(S->Ly, 3) * groups_along(S->Lx, 3);
+        for (EvalSlot &e : slots) {
+            PCK(scratch(&e.rco, (size_t)L * sizeof(float)));
+            PCK(scratch(&e.cinv, G3 * sizeof(float)));
+            PCK(scratch(&e.cefac, G3 * sizeof(float)));
+        }
+        sl = slots;
+        PTRY(egs(H, S, H->I8, on_image, 1, W.count, &h_best, &c_best, s, sl, -1, &acc));
     }
     int level_best = 0;
     if (prm.blur && prm.n_levels > 0 && prm.fixed_h == 0) {
@@ -424,6 +488,7 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
             if (any) PTRY(blur_to(H, W, cand, W.Pcur, s));
             int hk = 0;
             long long ck = 0;
+            int kslot = -1;
             if (literal) {
                 // Section 4.3: the cost is that of searching the blurred image,
                 // so EGS measures its own auto-correlation
@@ -432,9 +497,10 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
                     PCK(scratch(&W.invP, (size_t)L * sizeof(float)));
                 }
                 PCK(pivot_stats(W.Pcur, W.wsumP, W.invP));
-                PTRY(egs(H, S, W.Pcur, Members{W.Pcur, W.wsumP, W.invP}, h_best, W.count, &hk, &ck, s));
+                PTRY(egs(H, S, W.Pcur, Members{W.Pcur, W.wsumP, W.invP}, h_best, W.count, &hk, &ck,
+                         s, sl, acc, &kslot));
             } else {
-                PTRY(egs(H, S, W.Pcur, on_image, h_best, W.count, &hk, &ck, s));
+                PTRY(egs(H, S, W.Pcur, on_image, h_best, W.count, &hk, &ck, s, sl, acc, &kslot));
             }
             if ((double)(c_best - ck) > prm.xi * (double)c_best) {
                 cur_level = cand;
@@ -442,6 +508,7 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
                 h_best = hk;
                 c_best = ck;
                 level_best = k;
+                acc = kslot;
                 std::swap(W.Pcur, W.Pacc);
                 best_is_image = false;
             } else {
@@ -488,8 +555,18 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     PTRY(H->mem.alloc(&S->theta_co, L));
     PTRY(H->mem.alloc(&S->c_inv_sigma, G));
     PTRY(H->mem.alloc(&S->c_efac, G));
-    PCK(launch_rho_co(S->P, S->M, p, q, m, n, S->h, S->wsumM, S->invM, 0.f, S->rho_co,
-                      nullptr, S->c_inv_sigma, S->c_efac, s));
+    if (acc >= 0 && slots[acc].h == S->h) {
+        // the accepted configuration was evaluated by EGS: its outputs are kept
+        PCK(cudaMemcpyAsync(S->rho_co, slots[acc].rco, (size_t)L * sizeof(float),
+                            cudaMemcpyDeviceToDevice, s));
+        PCK(cudaMemcpyAsync(S->c_inv_sigma, slots[acc].cinv, (size_t)G * sizeof(float),
+                            cudaMemcpyDeviceToDevice, s));
+        PCK(cudaMemcpyAsync(S->c_efac, slots[acc].cefac, (size_t)G * sizeof(float),
+                            cudaMemcpyDeviceToDevice, s));
+    } else {
+        PCK(launch_rho_co(S->P, S->M, p, q, m, n, S->h, S->wsumM, S->invM, 0.f, S->rho_co,
+                          nullptr, S->c_inv_sigma, S->c_efac, s));
+    }
     PCK(launch_theta_co(S->rho_co, L, S->theta_co, s));
     PTRY(H->mem.alloc(&S->gco, G));
     PCK(launch_group_co(S->theta_co, S->Ly, S->Lx, S->h, S->gco, s));

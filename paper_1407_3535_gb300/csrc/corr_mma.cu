@@ -66,14 +66,52 @@ struct CorrMmaArgs {
 };
 
 
+// bf16 pair (low half first) of bytes k and k + 1 of w, each minus 128:
+// a byte b placed under the exponent of 2^23 (bit pattern 0x4B0000bb) is the
+// float 2^23 + b, so subtracting 2^23 + 128 gives b - 128 exactly, and a
+// float integer of at most 8 significant bits is exact in its top 16 bits.
+template <int K>
+__device__ __forceinline__ uint32_t bytes_bf16x2(uint32_t w) {
+    const float f0 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7650 + K)) - 8388736.f;
+    const float f1 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7650 + K + 1)) - 8388736.f;
+    return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+}
+
 constexpr int kMmaThreads = 256;
+// The raw words of one operand item (8 pixels from column x of a row):
+// three aligned words and the byte shift that aligns them, or, at the right
+// edge, the 8 clamped pixels in words 0-1 with no shift.
+struct ItemWords {
+    uint32_t w0, w1, w2, sh;
+};
+
+// the right edge, out of line (the last few items of a row only)
+__device__ __noinline__ ItemWords item_words_edge(const uint8_t *row, int x, int q) {
+    ItemWords r;
+    r.w0 = r.w1 = r.w2 = r.sh = 0u;
+    for (int d = 0; d < 4; ++d) r.w0 |= (uint32_t)row[min(x + d, q - 1)] << (8 * d);
+    for (int d = 0; d < 4; ++d) r.w1 |= (uint32_t)row[min(x + 4 + d, q - 1)] << (8 * d);
+    return r;
+}
+
+__device__ __forceinline__ ItemWords item_words(const uint8_t *row, int x, int q) {
+    if (x + 12 > q) return item_words_edge(row, x, q);
+    // the 12 bytes from the aligned word at or below row + x lie in the row
+    ItemWords r;
+    const uintptr_t ad = reinterpret_cast<uintptr_t>(row + x);
+    const uint32_t *wp = reinterpret_cast<const uint32_t *>(ad & ~(uintptr_t)3);
+    r.w0 = wp[0]; r.w1 = wp[1]; r.w2 = wp[2];
+    r.sh = (uint32_t)(ad & 3) * 8u;
+    return r;
+}
 constexpr int kMaxRC = 4;   // centre rows per CTA (the launcher measures 1, 2 and 4)
 
 __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaArgs a) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint64_t *b_full = reinterpret_cast<uint64_t *>(smem);   // [2]
-    uint64_t *mma_done = b_full + 2;                         // [2]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_done + 2);
+    uint64_t *b_full = reinterpret_cast<uint64_t *>(smem);   // [2] B tiles landed
+    uint64_t *mma_done = b_full + 2;                         // [2] MMAs of the stage completed
+    uint64_t *a_full = mma_done + 2;                         // [2] A written by the 7 builder warps
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(a_full + 2);
     const int WA = 15 * a.h + a.Kp / 8;
     const uint32_t abytes = (uint32_t)WA * 128u;
     const uint32_t bbytes = (uint32_t)a.N * a.Kp * 2u;
@@ -97,6 +135,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaA
         tc5::mbar_init(&b_full[1], 1);
         tc5::mbar_init(&mma_done[0], 1);
         tc5::mbar_init(&mma_done[1], 1);
+        tc5::mbar_init(&a_full[0], kMmaThreads / 32 - 1);
+        tc5::mbar_init(&a_full[1], kMmaThreads / 32 - 1);
         tc5::fence_mbar_init();
     }
     if (warp == 0) {
@@ -110,13 +150,10 @@ __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaA
     const uint32_t idesc = tc5::idesc_bf16_f32(kMmaM, a.N);
 
     bool ok = true;
-    int last_issue = -1;          // last step whose copies/MMAs thread 0 issued
-    bool last_committed = false;
-    int step = 0;
     const int r_end = group_centre_of(gy0 + nrow - 1, a.Ly, a.h) + a.m;
-    for (int r = cyk[0]; r < r_end; ++r) {
-        // template row u_k of accumulator k at this pivot row (-1: none)
-        int uk[kMaxRC];
+    // template row u_k of accumulator k at pivot row r (-1: none); both roles
+    // walk the same rows and count the same steps
+    auto rows_of = [&](int r, int (&uk)[kMaxRC]) {
         int nvalid = 0;
 #pragma unroll
         for (int k = 0; k < kMaxRC; ++k) {
@@ -124,44 +161,35 @@ __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaA
             uk[k] = (k < nrow && u >= 0 && u < a.m) ? u : -1;
             nvalid += uk[k] >= 0 ? 1 : 0;
         }
-        if (nvalid == 0) continue;                 // a gap between centre rows wider than m
-        const int s = step & 1;
-        if (step >= 2 && !tc5::mbar_wait(&mma_done[s], ((step - 2) >> 1) & 1, kWaitNs)) ok = false;
-        if (!__syncthreads_and(ok)) { ok = false; break; }
-        if (tid == 0) {
-            tc5::mbar_arrive_expect_tx(&b_full[s], (uint32_t)nvalid * bbytes);
+        return nvalid;
+    };
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer of the B tiles and issuer of the MMAs: step k waits for
+            // its stage to be released by the MMAs of step k - 2, queues the B
+            // tiles, waits for the builders' A and the tiles, issues, commits
+            int step = 0, last = -1, pending = -1;   // last committed, copies not yet consumed
+            for (int r = cyk[0]; r < r_end; ++r) {
+                int uk[kMaxRC];
+                const int nvalid = rows_of(r, uk);
+                if (nvalid == 0) continue;
+                const int s = step & 1;
+                const uint32_t ph = (step >> 1) & 1;
+                if (step >= 2 && !tc5::mbar_wait(&mma_done[s], ph ^ 1u, kWaitNs)) { ok = false; break; }
+                tc5::mbar_arrive_expect_tx(&b_full[s], (uint32_t)nvalid * bbytes);
 #pragma unroll
-            for (int k = 0; k < kMaxRC; ++k)
-                if (uk[k] >= 0)
-                    tc5::bulk_g2s(Bbase + (s * a.RC + k) * bstride, a.B + (size_t)uk[k] * a.N * a.Kp,
-                                  bbytes, &b_full[s]);
-            last_issue = step;
-            last_committed = false;
-        }
-        // build A_r: segment w, copy b = pixels cx0 + h*b + 8w .. +7 of row r
-        const uint8_t *row = a.V + (size_t)r * a.q;
-        uint8_t *Ab = Abase + s * astride;
-        for (int j = tid; j < WA * 8; j += blockDim.x) {
-            const int w = j >> 3, b = j & 7;
-            const int x = cx0 + a.h * b + 8 * w;
-            uint32_t pk[4];
-#pragma unroll
-            for (int d = 0; d < 8; d += 2) {
-                const int xa = min(x + d, a.q - 1), xb = min(x + d + 1, a.q - 1);
-                const __nv_bfloat162 v2 =
-                    __floats2bfloat162_rn((float)row[xa] - 128.f, (float)row[xb] - 128.f);
-                pk[d >> 1] = *reinterpret_cast<const uint32_t *>(&v2);
-            }
-            *reinterpret_cast<uint4 *>(Ab + w * 128 + b * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-        }
-        tc5::fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            if (!tc5::mbar_wait(&b_full[s], (step >> 1) & 1, kWaitNs)) {
-                ok = false;
-            } else {
+                for (int k = 0; k < kMaxRC; ++k)
+                    if (uk[k] >= 0)
+                        tc5::bulk_g2s(Bbase + (s * a.RC + k) * bstride, a.B + (size_t)uk[k] * a.N * a.Kp,
+                                      bbytes, &b_full[s]);
+                pending = step;
+                if (!tc5::mbar_wait(&a_full[s], ph, kWaitNs) || !tc5::mbar_wait(&b_full[s], ph, kWaitNs)) {
+                    ok = false;
+                    break;
+                }
+                pending = -1;
                 tc5::tc_fence_after();
-                const uint32_t abase = tc5::smem_u32(Ab);
+                const uint32_t abase = tc5::smem_u32(Abase + s * astride);
                 const uint32_t blbo = (uint32_t)(a.N / 8) * 128u;
 #pragma unroll
                 for (int k = 0; k < kMaxRC; ++k) {
@@ -174,20 +202,46 @@ __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaA
                     }
                 }
                 tc5::mma_commit(&mma_done[s]);
-                last_committed = true;
+                last = step;
+                ++step;
             }
+            // drain (bounded): copies still in flight, then the last MMA batch
+            if (pending >= 0) tc5::mbar_wait(&b_full[pending & 1], (pending >> 1) & 1, kWaitNs);
+            if (last >= 0 && !tc5::mbar_wait(&mma_done[last & 1], (last >> 1) & 1, kWaitNs)) ok = false;
         }
-        ++step;
-    }
-    // drain: thread 0 waits (bounded) for its last copies and last MMA batch
-    if (tid == 0 && last_issue >= 0) {
-        const int s = last_issue & 1;
-        const uint32_t ph = (last_issue >> 1) & 1;
-        if (last_committed) {
-            if (!tc5::mbar_wait(&mma_done[s], ph, kWaitNs)) ok = false;
-        } else {
-            tc5::mbar_wait(&b_full[s], ph, kWaitNs);
-            ok = false;
+    } else {
+        // builders (warps 1..7): step k writes A of stage k & 1 once the MMAs
+        // of step k - 2 released it (lane 0 waits; the warp follows it)
+        const int btid = tid - 32;
+        constexpr int kBuilders = kMmaThreads - 32;
+        int step = 0;
+        for (int r = cyk[0]; r < r_end; ++r) {
+            int uk[kMaxRC];
+            if (rows_of(r, uk) == 0) continue;
+            const int s = step & 1;
+            const uint32_t ph = (step >> 1) & 1;
+            if (step >= 2) {
+                bool w_ok = true;
+                if (lane == 0) w_ok = tc5::mbar_wait(&mma_done[s], ph ^ 1u, kWaitNs);
+                w_ok = __shfl_sync(0xffffffffu, w_ok ? 1 : 0, 0) != 0;
+                __syncwarp();
+                if (!w_ok) { ok = false; break; }
+            }
+            // A_r: segment w, copy b = pixels cx0 + h*b + 8w .. +7 of row r
+            const uint8_t *row = a.V + (size_t)r * a.q;
+            uint8_t *Ab = Abase + s * astride;
+            for (int j = btid; j < WA * 8; j += kBuilders) {
+                const ItemWords iw = item_words(row, cx0 + a.h * (j & 7) + 8 * (j >> 3), a.q);
+                const uint32_t lo = __funnelshift_r(iw.w0, iw.w1, iw.sh);
+                const uint32_t hi = __funnelshift_r(iw.w1, iw.w2, iw.sh);
+                *reinterpret_cast<uint4 *>(Ab + (j >> 3) * 128 + (j & 7) * 16) =
+                    make_uint4(bytes_bf16x2<0>(lo), bytes_bf16x2<2>(lo), bytes_bf16x2<0>(hi),
+                               bytes_bf16x2<2>(hi));
+            }
+            tc5::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) tc5::mbar_arrive(&a_full[s]);
+            ++step;
         }
     }
     tc5::tc_fence_before();

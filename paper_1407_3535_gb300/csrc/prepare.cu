@@ -374,10 +374,14 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
         for (int item = warp; item < nrows * SG::NSEG; item += nwarps) {
             const int row = item / SG::NSEG, seg = item - row * SG::NSEG;
             unsigned *lp = hb + row * SG::RS + (seg * 32 + lane) * SG::PLS;
-            const int c0 = seg * SG::SL + lane * SG::PL;
+            const int cnt = W - (seg * SG::SL + lane * SG::PL);   // this lane's columns below W
+            unsigned v[SG::PL];                                   // read once, kept for pass 2
             unsigned tot = 0u;
 #pragma unroll
-            for (int i = 0; i < SG::PL; ++i) tot += (c0 + i < W) ? lp[i] : 0u;
+            for (int i = 0; i < SG::PL; ++i) {
+                v[i] = i < cnt ? lp[i] : 0u;
+                tot += v[i];
+            }
             unsigned inc = tot;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -387,8 +391,8 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
             unsigned run = inc - tot;
 #pragma unroll
             for (int i = 0; i < SG::PL; ++i) {
-                run += (c0 + i < W) ? lp[i] : 0u;
-                lp[i] = run;   // inclusive prefix within the segment
+                run += v[i];
+                lp[i] = run;   // inclusive prefix within the segment (past W: never read)
             }
             if (lane == 31) sb[row * SG::NSEG + seg] = inc;
         }

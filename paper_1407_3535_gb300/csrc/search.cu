@@ -535,13 +535,23 @@ topk_stage1_kernel(const float *__restrict__ rho_tc, int G, int64_t gstride, int
     for (int j = 0; j < TOPK_PER_THREAD; ++j) { v[j] = -INFINITY; ix[j] = -1; }
     const int chunk = (G + gridDim.x - 1) / gridDim.x;
     const int g0 = blockIdx.x * chunk, g1 = min(G, g0 + chunk);
-    for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
-        float x = rho_tc[g];
-        int xi = g;
-        if (x > v[TOPK_PER_THREAD - 1]) {
+    // four values in flight per thread, then inserted into its sorted list
+    for (int g = g0 + threadIdx.x; g < g1; g += 4 * blockDim.x) {
+        float xs[4];
 #pragma unroll
-            for (int j = 0; j < TOPK_PER_THREAD; ++j) {
-                if (x > v[j]) { float tv = v[j]; int ti = ix[j]; v[j] = x; ix[j] = xi; x = tv; xi = ti; }
+        for (int u = 0; u < 4; ++u) {
+            const int gi = g + u * blockDim.x;
+            xs[u] = gi < g1 ? rho_tc[gi] : -INFINITY;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            float x = xs[u];
+            int xi = g + u * blockDim.x;
+            if (x > v[TOPK_PER_THREAD - 1]) {
+#pragma unroll
+                for (int j = 0; j < TOPK_PER_THREAD; ++j) {
+                    if (x > v[j]) { float tv = v[j]; int ti = ix[j]; v[j] = x; ix[j] = xi; x = tv; xi = ti; }
+                }
             }
         }
     }
@@ -1348,7 +1358,7 @@ cudaError_t launch_centre_rho(const uint8_t *P, int p, int q, const float *tf, i
 }
 
 int topk_blocks(int G) {
-    int nb = (G + 4095) / 4096;
+    int nb = (G + 16383) / 16384;
     if (nb > 256) nb = 256;
     if (nb < 1) nb = 1;
     return nb;

@@ -36,6 +36,7 @@ def _cuda(a):
     ((257, 391), (17, 23), 7, 3),       # Kp padded to 32, truncated last groups
     ((200, 300), (40, 48), 1, 2),       # h = 1: every location is a centre
     ((333, 333), (24, 24), 9, 7),
+    ((160, 1203), (12, 300), 7, 2),     # wide template: operand items past the prefetched ones
 ])
 def test_scan1_intervals_contain_exact(opta, precision, shape, tshape, h, count):
     img = synth.aerial_image(max(shape), 7, 12, seed=h + 10 * count)[:shape[0], :shape[1]].copy()
