@@ -25,7 +25,11 @@
 // once and feeds every accumulator k with u = r - cy_k in [0, m), against
 // template row u (RC tiles of B per pivot row, accumulator k at TMEM column
 // k * N).  Two stages (A and the B tiles) overlap the build of the next
-// pivot row with the MMAs of the current one.
+// pivot row with the MMAs of the current one, and the work is split by
+// warp: lane 0 of warp 0 queues the B tiles (bulk copies) and issues and
+// commits the MMAs, warps 1-7 build the Hankel operand; the stages change
+// hands through mbarriers (operand written, tiles landed, MMAs done), so
+// neither side waits for the other at a CTA barrier.
 //
 // Error bound of the numerator: the hi/lo split represents each template
 // value to within 2^-16 relative; FP32 accumulation in TMEM is bounded by
