@@ -271,23 +271,25 @@ __device__ __forceinline__ void rco_batch(int (&cs)[H * H], const unsigned (&pw)
 }
 
 // Shared-memory words of one CTA (host and device agree on the layout):
-// two emission buffers of H scanned shift rows and their segment totals,
-// the per-centre statistics, each thread's member inputs of one group row
-// (window sum and 1/Omega per shift row), each thread's pivot column sums
-// and the image ring.
+// one emission buffer of K * H scanned shift rows plus the two rows of the
+// pivot statistics (rows of NSr segments: as many as the strip's columns
+// need), their segment totals, the per-centre statistics, each thread's
+// pivot column sums and the image ring.
 struct RcoSmem {
-    int hsc, segt, cst, tin, psq, ring, total;
+    int hsc, segt, cst, psq, ring, total, nseg, rs;
 };
 template <int H>
-__host__ __device__ inline RcoSmem rco_smem(int Wmax, int GXS, int CSW) {
+__host__ __device__ inline RcoSmem rco_smem(int Wmax, int GXS, int CSW, int K) {
     constexpr int R = RcoCfg<H>::R;
+    using SG = RcoScan<H>;
     RcoSmem l;
+    l.nseg = (Wmax + SG::SL - 1) / SG::SL;
+    l.rs = l.nseg * 32 * SG::PLS;
+    const int rows = K * H + 2;
     int o = 0;
-    constexpr int HB = H > 2 ? H : 2;   // rows per emission buffer (>= 2: the centre statistics)
-    l.hsc = o;  o += 2 * HB * RcoScan<H>::RS;
-    l.segt = o; o += 2 * HB * RcoScan<H>::NSEG;
+    l.hsc = o;  o += rows * l.rs;
+    l.segt = o; o += rows * l.nseg;
     l.cst = o;  o += 2 * GXS;
-    l.tin = o;  o += 2 * H * RcoCfg<H>::MAXT;
     l.psq = o;  o += 2 * RcoCfg<H>::MAXT;
     l.ring = o; o += (Wmax + 2 * R) * CSW;
     l.total = o;
@@ -298,7 +300,7 @@ template <int H>
 __global__ void __launch_bounds__(RcoCfg<H>::MAXT, 1)
 rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int p, int q,
               int m, int n, int Ly, int Lx, const int *__restrict__ wsum,
-              const float *__restrict__ inv_sigma, int GXS, int GYB, float cut, float *rco,
+              const float *__restrict__ inv_sigma, int GXS, int GYB, int K, float cut, float *rco,
               unsigned long long *count, float *c_inv_sigma, float *c_efac) {
     constexpr int R = RcoCfg<H>::R;
     constexpr int NS = RcoCfg<H>::NS;
@@ -316,14 +318,12 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
     const int RING = rco_ring(m, H), RW4 = RING >> 2, CSW = rco_csw(RING);
     const int nwarps = blockDim.x >> 5;
     using SG = RcoScan<H>;
-    const RcoSmem L = rco_smem<H>(Wmax, GXS, CSW);
-    constexpr int HB = H > 2 ? H : 2;
-    unsigned *hsc = rsm + L.hsc;                                  // 2 x HB x RS scanned sums
-    unsigned *segt = rsm + L.segt;                                // 2 x HB x NSEG segment totals
+    const RcoSmem L = rco_smem<H>(Wmax, GXS, CSW, K);
+    const int NSr = L.nseg, RSr = L.rs;                           // segments and words per scanned row
+    unsigned *hsc = rsm + L.hsc;                                  // (K H + 2) x RSr scanned sums
+    unsigned *segt = rsm + L.segt;                                // (K H + 2) x NSr segment totals
     int *cS = reinterpret_cast<int *>(rsm + L.cst);               // per centre: S_hat
     float *cI = reinterpret_cast<float *>(rsm + L.cst + GXS);     // per centre: 1/(mn Omega_hat)
-    int *tws = reinterpret_cast<int *>(rsm + L.tin);             // [H][MAXT] member window sums
-    float *tiw = reinterpret_cast<float *>(rsm + L.tin + H * RcoCfg<H>::MAXT);   // [H][MAXT] 1/Omega
     unsigned *psq = rsm + L.psq;                                  // [2][MAXT] column sums of P, P^2
     unsigned *ringw = rsm + L.ring;                               // (W + 2R) columns x CSW words
     uint8_t *ring8 = reinterpret_cast<uint8_t *>(ringw);
@@ -371,9 +371,9 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
     // inclusive prefix of rows [0, nrows) of buffer hb, segment by segment
     // (segment totals in sb); item = (row, segment)
     auto scan_rows = [&](unsigned *hb, unsigned *sb, int nrows) {
-        for (int item = warp; item < nrows * SG::NSEG; item += nwarps) {
-            const int row = item / SG::NSEG, seg = item - row * SG::NSEG;
-            unsigned *lp = hb + row * SG::RS + (seg * 32 + lane) * SG::PLS;
+        for (int item = warp; item < nrows * NSr; item += nwarps) {
+            const int row = item / NSr, seg = item - row * NSr;
+            unsigned *lp = hb + row * RSr + (seg * 32 + lane) * SG::PLS;
             const int cnt = W - (seg * SG::SL + lane * SG::PL);   // this lane's columns below W
             unsigned v[SG::PL];                                   // read once, kept for pass 2
             unsigned tot = 0u;
@@ -394,7 +394,7 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
                 run += v[i];
                 lp[i] = run;   // inclusive prefix within the segment (past W: never read)
             }
-            if (lane == 31) sb[row * SG::NSEG + seg] = inc;
+            if (lane == 31) sb[row * NSr + seg] = inc;
         }
     };
     // sum of a scanned row over pivot columns [c1, c1 + n) (modulo 2^32)
@@ -449,34 +449,10 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
         *pq_j = pq;
     }
     unsigned long long local = 0;
-    int ebuf = 0;
     const int ntask = ngx * H;
     for (int gy = gy0; gy < gy1; ++gy) {
         const int cy = group_centre_of(gy, Ly, H);
         const int steps = cy - r;            // 0 for the first row, <= H after
-        // this thread's first task (centre gxi, shift column sxi): its member's
-        // window sum and 1/Omega for every shift row of the group row, copied
-        // to shared memory while the slide runs
-        {
-            const int gys0 = gy * H, gye0 = min(gys0 + H, Ly);
-            if ((int)threadIdx.x < ntask) {
-                const int gxi = threadIdx.x / H, sxi = threadIdx.x - gxi * H;
-                const int gx = gx0 + gxi;
-                const int mx = group_centre_of(gx, Lx, H) + sxi - R;
-                if (mx >= gx * H && mx < min(gx * H + H, Lx)) {
-#pragma unroll 1
-                    for (int syi = 0; syi < H; ++syi) {
-                        const int my = cy + syi - R;
-                        if (my >= gys0 && my < gye0) {
-                            const int64_t li = (int64_t)my * Lx + mx;
-                            cp_async4(tws + syi * RcoCfg<H>::MAXT + threadIdx.x, wsum + li);
-                            cp_async4(tiw + syi * RcoCfg<H>::MAXT + threadIdx.x, inv_sigma + li);
-                        }
-                    }
-                }
-            }
-            cp_async_commit();
-        }
         if (steps > 0) {
             // this column's pivot rows entering and leaving the window, then
             // the image rows up to r + steps - 1 + m + R the batch needs
@@ -502,80 +478,99 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
             r += steps;
             __syncthreads();   // nobody reads the dead rows the next batch overwrites
         }
-        // pivot statistics of this row's centres: window sums of the column
-        // sums of P and P^2 (exact, < 2^32), scanned like the cross sums
-        {
-            unsigned *hb = hsc + ebuf * (HB * SG::RS);
-            unsigned *sb = segt + ebuf * (HB * SG::NSEG);
-            ebuf ^= 1;
-            if (active) {
-                hb[addr_j] = *ps_j;
-                hb[SG::RS + addr_j] = *pq_j;
-            }
-            __syncthreads();
-            scan_rows(hb, sb, 2);
-            __syncthreads();
-            if ((int)threadIdx.x < ngx) {
-                const int gx = gx0 + threadIdx.x;
-                const int c1 = group_centre_of(gx, Lx, H) - cx0;
-                const long long Sp = window(hb, sb, c1), Qp = window(hb + SG::RS, sb + SG::NSEG, c1);
-                const long long var = mn * Qp - Sp * Sp;   // exact
-                cS[threadIdx.x] = (int)Sp;
-                // 1 / (mn Omega_hat) = sqrt(mn / var) / mn
-                const float fmn = i64_to_f32(mn), fv = i64_to_f32(var);
-                cI[threadIdx.x] = var > 0 ? sqrtf(fmn / fv) / fmn : 0.f;
-                if (c_inv_sigma) {
-                    // per-centre statistics of scan 1: 1/sigma_hat and ||P - 128|| / sigma_hat
-                    const int64_t g = (int64_t)gy * Gx + gx;
-                    c_inv_sigma[g] = var > 0 ? sqrtf(fmn / fv) : 0.f;
-                    c_efac[g] = var > 0 ? sqrtf(fmn * i64_to_f32(Qp - 256 * Sp + 16384 * mn) / fv) : 0.f;
+        // emission of centre row cy in chunks of K shift rows (sy): the chunk's
+        // K H column-sum rows (and, in the first chunk, the column sums of P
+        // and P^2 for the pivot statistics) are stored, scanned together and
+        // read by the tasks
+        const int gys = gy * H, gye = min(gys + H, Ly);
+        for (int k0 = 0; k0 < H; k0 += K) {
+            const int kn = min(K, H - k0);
+            const bool first = k0 == 0;
+            const int rb = first ? 2 : 0;              // first shift row of the chunk
+            if (!first) __syncthreads();               // the previous chunk's tasks are done
+            // this thread's first task's member statistics for the chunk's
+            // shift rows, brought into L1 now and read after the scan
+#pragma unroll
+            for (int syi = 0; syi < H; ++syi) {
+                const int my = cy + syi - R;
+                if (t0_ok && syi >= k0 && syi < k0 + kn && my >= gys && my < gye) {
+                    const int64_t li = (int64_t)my * Lx + t0_mx;
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(wsum + li));
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(inv_sigma + li));
                 }
             }
-        }
-        cp_async_wait_all();   // this thread's member inputs (read by this thread only)
-        // emit centre row cy, one shift row (sy) at a time
-        const int gys = gy * H, gye = min(gys + H, Ly);
-#pragma unroll
-        for (int syi = 0; syi < H; ++syi) {
-            const int my = cy + syi - R;
-            if (my < gys || my >= gye) continue;   // uniform over the block
-            unsigned *hb = hsc + ebuf * (HB * SG::RS);
-            unsigned *sb = segt + ebuf * (HB * SG::NSEG);
-            ebuf ^= 1;
             if (active) {
+                if (first) {
+                    hsc[addr_j] = *ps_j;
+                    hsc[RSr + addr_j] = *pq_j;
+                }
 #pragma unroll
-                for (int sxi = 0; sxi < H; ++sxi) hb[sxi * SG::RS + addr_j] = (unsigned)cs[syi * H + sxi];
+                for (int syi = 0; syi < H; ++syi) {
+                    if (syi < k0 || syi >= k0 + kn) continue;
+#pragma unroll
+                    for (int sxi = 0; sxi < H; ++sxi)
+                        hsc[(rb + (syi - k0) * H + sxi) * RSr + addr_j] = (unsigned)cs[syi * H + sxi];
+                }
             }
             __syncthreads();
-            scan_rows(hb, sb, H);
+            scan_rows(hsc, segt, rb + kn * H);
             __syncthreads();
+            if (first) {
+                // pivot statistics of this row's centres: window sums of the
+                // column sums of P and P^2 (exact, < 2^32)
+                if ((int)threadIdx.x < ngx) {
+                    const int gx = gx0 + threadIdx.x;
+                    const int c1 = group_centre_of(gx, Lx, H) - cx0;
+                    const long long Sp = window(hsc, segt, c1), Qp = window(hsc + RSr, segt + NSr, c1);
+                    const long long var = mn * Qp - Sp * Sp;   // exact
+                    cS[threadIdx.x] = (int)Sp;
+                    // 1 / (mn Omega_hat) = sqrt(mn / var) / mn
+                    const float fmn = i64_to_f32(mn), fv = i64_to_f32(var);
+                    cI[threadIdx.x] = var > 0 ? sqrtf(fmn / fv) / fmn : 0.f;
+                    if (c_inv_sigma) {
+                        // per-centre statistics of scan 1: 1/sigma_hat and ||P - 128|| / sigma_hat
+                        const int64_t g = (int64_t)gy * Gx + gx;
+                        c_inv_sigma[g] = var > 0 ? sqrtf(fmn / fv) : 0.f;
+                        c_efac[g] = var > 0 ? sqrtf(fmn * i64_to_f32(Qp - 256 * Sp + 16384 * mn) / fv) : 0.f;
+                    }
+                }
+                __syncthreads();
+            }
             // task = (centre gxi, shift column sxi): X = window sum over pivot
             // columns [c1, c1 + n); rho = (mn X - S_hat S) / (mn Omega_hat
             // Omega): exact integer numerator, FP32 finish (flat windows have
             // 1/Omega = 0 -> 0)
-            if (t0_ok) {
-                const unsigned X = window(hb + t0_sxi * SG::RS, sb + t0_sxi * SG::NSEG, t0_c1);
-                const int ws = tws[syi * RcoCfg<H>::MAXT + threadIdx.x];
-                const float iw = tiw[syi * RcoCfg<H>::MAXT + threadIdx.x];
-                const long long num = mn * (long long)X - (long long)cS[t0_gxi] * (long long)ws;
-                const float rho = (i64_to_f32(num) * iw) * cI[t0_gxi];
-                if (rco) rco[(int64_t)my * Lx + t0_mx] = rho;
-                if (rho < cut) ++local;
-            }
-            for (int task = threadIdx.x + blockDim.x; task < ntask; task += blockDim.x) {
-                const int gxi = task / H, sxi = task - gxi * H;
-                const int gx = gx0 + gxi;
-                const int cxg = group_centre_of(gx, Lx, H);
-                const int mx = cxg + sxi - R;
-                if (mx < gx * H || mx >= min(gx * H + H, Lx)) continue;
-                const int64_t li = (int64_t)my * Lx + mx;
-                const int ws = wsum[li];
-                const float iw = inv_sigma[li];
-                const unsigned X = window(hb + sxi * SG::RS, sb + sxi * SG::NSEG, cxg - cx0);
-                const long long num = mn * (long long)X - (long long)cS[gxi] * (long long)ws;
-                const float rho = (i64_to_f32(num) * iw) * cI[gxi];
-                if (rco) rco[li] = rho;
-                if (rho < cut) ++local;
+#pragma unroll
+            for (int syi = 0; syi < H; ++syi) {
+                if (syi < k0 || syi >= k0 + kn) continue;
+                const int my = cy + syi - R;
+                if (my < gys || my >= gye) continue;   // uniform over the block
+                const int row = rb + (syi - k0) * H;
+                if (t0_ok) {
+                    const int64_t li = (int64_t)my * Lx + t0_mx;
+                    const int ws = wsum[li];
+                    const float iw = inv_sigma[li];
+                    const unsigned X = window(hsc + (row + t0_sxi) * RSr, segt + (row + t0_sxi) * NSr, t0_c1);
+                    const long long num = mn * (long long)X - (long long)cS[t0_gxi] * (long long)ws;
+                    const float rho = (i64_to_f32(num) * iw) * cI[t0_gxi];
+                    if (rco) rco[li] = rho;
+                    if (rho < cut) ++local;
+                }
+                for (int task = threadIdx.x + blockDim.x; task < ntask; task += blockDim.x) {
+                    const int gxi = task / H, sxi = task - gxi * H;
+                    const int gx = gx0 + gxi;
+                    const int cxg = group_centre_of(gx, Lx, H);
+                    const int mx = cxg + sxi - R;
+                    if (mx < gx * H || mx >= min(gx * H + H, Lx)) continue;
+                    const int64_t li = (int64_t)my * Lx + mx;
+                    const int ws = wsum[li];
+                    const float iw = inv_sigma[li];
+                    const unsigned X = window(hsc + (row + sxi) * RSr, segt + (row + sxi) * NSr, cxg - cx0);
+                    const long long num = mn * (long long)X - (long long)cS[gxi] * (long long)ws;
+                    const float rho = (i64_to_f32(num) * iw) * cI[gxi];
+                    if (rco) rco[li] = rho;
+                    if (rho < cut) ++local;
+                }
             }
         }
     }
@@ -755,7 +750,7 @@ blur_corr_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, i
 
 struct RcoGeom {
     bool ok;
-    int GXS, Wmax, threads, strips;
+    int GXS, Wmax, threads, strips, K;
     size_t smem;
 };
 
@@ -765,7 +760,6 @@ struct RcoGeom {
 // group row and the packed image ring.
 template <int H>
 RcoGeom rco_geom(int p, int q, int m, int n) {
-    constexpr int R = RcoCfg<H>::R;
     constexpr int MAXT = RcoCfg<H>::MAXT;
     constexpr size_t kSmemMax = 227 * 1024;
     RcoGeom g{};
@@ -774,23 +768,34 @@ RcoGeom rco_geom(int p, int q, int m, int n) {
     // window sums of uint8 products are kept in 32 bits
     if (n + H > MAXT || (uint64_t)m * n * 65025u > 0xffffffffull) return g;
     const int csw = rco_csw(rco_ring(m, H));
-    auto smem_for = [&](int gxs, int *wmax) {
+    auto smem_for = [&](int gxs, int k, int *wmax) {
         *wmax = (gxs - 1) * H + n;
-        return (size_t)rco_smem<H>(*wmax, gxs, csw).total * sizeof(unsigned);
+        return (size_t)rco_smem<H>(*wmax, gxs, csw, k).total * sizeof(unsigned);
     };
-    // widest strip within the thread limit, narrowed until tall windows' ring fits
+    // the most shift rows per emission (K) that fit beside the image ring
+    auto best_k = [&](int gxs, size_t *smem, int *wmax) {
+        for (int k = H; k >= 1; --k) {
+            *smem = smem_for(gxs, k, wmax);
+            if (*smem <= kSmemMax) return k;
+        }
+        return 0;
+    };
+    // widest strip within the thread limit, narrowed until the ring and one
+    // shift row per emission fit
     g.GXS = std::min((MAXT - n) / H + 1, Gx);
-    g.smem = smem_for(g.GXS, &g.Wmax);
-    while (g.smem > kSmemMax && g.GXS > 1) {
+    g.K = best_k(g.GXS, &g.smem, &g.Wmax);
+    while (g.K == 0 && g.GXS > 1) {
         g.GXS = std::max(1, g.GXS - std::max(1, g.GXS / 8));
-        g.smem = smem_for(g.GXS, &g.Wmax);
+        g.K = best_k(g.GXS, &g.smem, &g.Wmax);
     }
-    g.ok = g.smem <= kSmemMax;
+    g.ok = g.K > 0;
+    if (!g.ok) return g;
     // strips of equal width (narrower than the limit: the last strip is not
-    // left with a remainder while the others carry the rest)
+    // left with a remainder while the others carry the rest), then again the
+    // most shift rows per emission at that width
     g.strips = (Gx + g.GXS - 1) / g.GXS;
     g.GXS = (Gx + g.strips - 1) / g.strips;
-    g.smem = smem_for(g.GXS, &g.Wmax);
+    g.K = best_k(g.GXS, &g.smem, &g.Wmax);
     g.threads = ((g.Wmax + 31) / 32) * 32;
     (void)Gy;
     return g;
@@ -825,7 +830,8 @@ cudaError_t launch_rho_co_h(const uint8_t *P, const uint8_t *I, int p, int q, in
     dim3 grid(g.strips, bands);
     LaunchScope ls_rho_co_kernel("rho_co_kernel", s);
     rho_co_kernel<H><<<grid, g.threads, smem, s>>>(P, I, p, q, m, n, Ly, Lx, wsum, inv_sigma,
-                                                   g.GXS, GYB, cut, rco, count, c_inv_sigma, c_efac);
+                                                   g.GXS, GYB, g.K, cut, rco, count, c_inv_sigma,
+                                                   c_efac);
     return cudaGetLastError();
 }
 
