@@ -67,7 +67,8 @@ __device__ __forceinline__ void blur_tile(const uint8_t *__restrict__ I, int p, 
 #pragma unroll 4
         for (int i = threadIdx.x; i < ih * iw; i += kBlurThreads) {
             const int yy = min(max(y0 - R + r, 0), p - 1), xx = min(max(x0 - R + c, 0), q - 1);
-            in[r * ist + c] = (float)I[(int64_t)yy * q + xx];
+            // the byte under the exponent of 2^23 is the float 2^23 + b: minus 2^23, b exactly
+            in[r * ist + c] = __uint_as_float(0x4B000000u | I[(int64_t)yy * q + xx]) - 8388608.f;
             r += dr;
             c += dc;
             if (c >= iw) { c -= iw; ++r; }

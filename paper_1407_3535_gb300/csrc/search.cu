@@ -917,6 +917,10 @@ __device__ inline void stage_rows(const uint8_t *I, const uint8_t *img_end, int 
 // the whole warp, and its error bound; results valid in lane 0.  With a
 // staging buffer (wbuf: 2 x kStageRows x WB bytes) the window goes through
 // shared memory; without, it is read straight from global memory.
+// A byte b as the float 2^23 + b (b under the exponent of 2^23): one logic
+// operation instead of an integer-to-float conversion.
+__device__ __forceinline__ float u8f(uint32_t b) { return __uint_as_float(0x4B000000u | b); }
+
 __device__ inline void warp_rho32(const uint8_t *__restrict__ I, int q, int Lx,
                                   const int *__restrict__ wsum,
                                   const float *__restrict__ tm, int m, int n, int npad,
@@ -929,6 +933,7 @@ __device__ inline void warp_rho32(const uint8_t *__restrict__ I, int q, int Lx,
     const float is = inv_sigma[idx];
     // any integer in [0, 255] keeps |v| <= 255; the nearest to the mean keeps it small
     const float a = rintf((float)S / (float)mn);
+    const float ca = 8388608.f + a;   // 2^23 + a: u8f(b) - ca = b - a, exactly
     const uint8_t *bp = I + (int64_t)y * q + x;
     float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
     if (wbuf) {
@@ -951,7 +956,7 @@ __device__ inline void warp_rho32(const uint8_t *__restrict__ I, int q, int Lx,
                 const uint8_t *sb = buf + r * WB + (int)(reinterpret_cast<uintptr_t>(row) & 15);
                 const float *tr = tm + (u0 + r) * npad;
                 float racc = 0.f;
-                for (int v = lane; v < n; v += 32) racc = fmaf(tr[v], (float)sb[v] - a, racc);
+                for (int v = lane; v < n; v += 32) racc = fmaf(tr[v], u8f(sb[v]) - ca, racc);
                 if (r & 1) acc1 += racc; else acc0 += racc;
             }
             __syncwarp();   // the buffer is refilled two chunks later
@@ -962,17 +967,17 @@ __device__ inline void warp_rho32(const uint8_t *__restrict__ I, int q, int Lx,
             const uint8_t *r0 = bp + (int64_t)u * q;
             const float *t0 = tm + u * npad;
             for (int v = lane; v < n; v += 32) {
-                const float i0 = (float)r0[v], i1 = (float)r0[q + v];
-                const float i2 = (float)r0[2 * (int64_t)q + v], i3 = (float)r0[3 * (int64_t)q + v];
-                acc0 = fmaf(t0[v], i0 - a, acc0);
-                acc1 = fmaf(t0[npad + v], i1 - a, acc1);
-                acc2 = fmaf(t0[2 * npad + v], i2 - a, acc2);
-                acc3 = fmaf(t0[3 * npad + v], i3 - a, acc3);
+                const float i0 = u8f(r0[v]), i1 = u8f(r0[q + v]);
+                const float i2 = u8f(r0[2 * (int64_t)q + v]), i3 = u8f(r0[3 * (int64_t)q + v]);
+                acc0 = fmaf(t0[v], i0 - ca, acc0);
+                acc1 = fmaf(t0[npad + v], i1 - ca, acc1);
+                acc2 = fmaf(t0[2 * npad + v], i2 - ca, acc2);
+                acc3 = fmaf(t0[3 * npad + v], i3 - ca, acc3);
             }
         }
         for (; u < m; ++u)
             for (int v = lane; v < n; v += 32)
-                acc0 = fmaf(tm[u * npad + v], (float)bp[(int64_t)u * q + v] - a, acc0);
+                acc0 = fmaf(tm[u * npad + v], u8f(bp[(int64_t)u * q + v]) - ca, acc0);
     }
     const float acc = warp_sum_f((acc0 + acc2) + (acc1 + acc3));
     rho = 0.f;
@@ -1132,6 +1137,7 @@ survivors_lane_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, 
             const long long S = wsum[idx];
             const float is = inv_sigma[idx];
             const float a = rintf((float)S / (float)mn);
+            const float ca = 8388608.f + a;   // 2^23 + a: byte b - a = float(0x4B0000bb) - ca, exactly
             float tot = 0.f;
             const uint8_t *wp = I + (int64_t)y * q + x;
             for (int u = 0; u < m; ++u) {
@@ -1149,7 +1155,9 @@ survivors_lane_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, 
                     w0 = w1;
 #pragma unroll
                     for (int b = 0; b < 4; ++b)
-                        if (v + b < n) racc = fmaf(tr[v + b], (float)((wv >> (8 * b)) & 255u) - a, racc);
+                        if (v + b < n)
+                            racc = fmaf(tr[v + b],
+                                        __uint_as_float(__byte_perm(wv, 0x4B000000u, 0x7650 + b)) - ca, racc);
                 }
                 tot += racc;
             }
