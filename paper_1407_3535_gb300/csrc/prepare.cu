@@ -180,36 +180,6 @@ struct RcoCfg {
 __host__ __device__ inline int rco_ring(int m, int H) { return (m + (H - 1) + 1 + H + 3) & ~3; }
 __host__ __device__ inline int rco_csw(int ring) { return (ring >> 2) | 1; }
 
-// Emission geometry (compile time, sized for MAXT columns): the column sums
-// of one shift row are scanned in NSEG segments of SL = 32 * PL columns (PL
-// a power of two), one warp per (shift column, segment); lane l holds PL
-// consecutive columns at a padded stride PLS (odd, or 1: conflict-free).  A
-// window sum adds the totals of the segments it spans to the difference of
-// two in-segment prefixes.
-template <int H>
-struct RcoScan {
-    static constexpr int MAXT = RcoCfg<H>::MAXT;
-    static constexpr int NW = MAXT / 32;                              // warps at most
-    // segments per row wanted (at least 2: at most 8 columns per lane for
-    // the widest rows, so the scan does not compete with the H*H slide
-    // accumulators for registers)
-    static constexpr int NSEG0 = NW / H > 2 ? NW / H : 2;
-    static constexpr int NEED = (MAXT + NSEG0 * 32 - 1) / (NSEG0 * 32);
-    static constexpr int PL = NEED <= 1 ? 1 : NEED <= 2 ? 2 : NEED <= 4 ? 4 : NEED <= 8 ? 8
-                              : NEED <= 16 ? 16 : 32;
-    static constexpr int LGPL = PL == 1 ? 0 : PL == 2 ? 1 : PL == 4 ? 2 : PL == 8 ? 3 : PL == 16 ? 4 : 5;
-    static constexpr int PLS = PL == 1 ? 1 : PL + 1;
-    static constexpr int SL = 32 * PL, LGSL = LGPL + 5;
-    static constexpr int NSEG = (MAXT + SL - 1) / SL;
-    static constexpr int RS = NSEG * 32 * PLS;                        // words per shift row
-};
-template <int H>
-__device__ __forceinline__ int rco_addr(int c) {
-    using G = RcoScan<H>;
-    const int seg = c >> G::LGSL, w = c & (G::SL - 1);
-    return (seg * 32 + (w >> G::LGPL)) * G::PLS + (w & (G::PL - 1));
-}
-
 // Pivot column jc, rows [prow, prow + cnt), packed 4 rows per word (zero
 // past cnt, cnt <= BATCH): the loads are issued together.
 template <int H>
@@ -272,24 +242,25 @@ __device__ __forceinline__ void rco_batch(int (&cs)[H * H], const unsigned (&pw)
 }
 
 // Shared-memory words of one CTA (host and device agree on the layout):
-// one emission buffer of K * H scanned shift rows plus the two rows of the
-// pivot statistics (rows of NSr segments: as many as the strip's columns
-// need), their segment totals, the per-centre statistics, each thread's
-// pivot column sums and the image ring.
+// one emission buffer of K * H column-sum rows plus the two rows of the
+// pivot statistics, their block prefixes (see block_rows), the per-centre
+// statistics, each thread's pivot column sums and the image ring.
 struct RcoSmem {
-    int hsc, segt, cst, psq, ring, total, nseg, rs;
+    int hsc, pre, cst, psq, ring, total;
+    int nb, bpl, rwc, rwp;   // blocks per row, blocks per lane, words per column row / prefix row
 };
 template <int H>
-__host__ __device__ inline RcoSmem rco_smem(int Wmax, int GXS, int CSW, int K) {
+__host__ __device__ inline RcoSmem rco_smem(int Wmax, int GXS, int CSW, int K, int n) {
     constexpr int R = RcoCfg<H>::R;
-    using SG = RcoScan<H>;
     RcoSmem l;
-    l.nseg = (Wmax + SG::SL - 1) / SG::SL;
-    l.rs = l.nseg * 32 * SG::PLS;
+    l.nb = GXS + n / H + 1;              // blocks of H columns the windows reach
+    l.bpl = ((l.nb + 31) / 32) | 1;      // blocks per lane (odd: the lanes' strides miss each other's banks)
+    l.rwc = l.nb * H;                    // the columns the blocks read (> Wmax)
+    l.rwp = 2 * l.nb + 2;
     const int rows = K * H + 2;
     int o = 0;
-    l.hsc = o;  o += rows * l.rs;
-    l.segt = o; o += rows * l.nseg;
+    l.hsc = o;  o += rows * l.rwc;
+    l.pre = o;  o += rows * l.rwp;
     l.cst = o;  o += 2 * GXS;
     l.psq = o;  o += 2 * RcoCfg<H>::MAXT;
     l.ring = o; o += (Wmax + 2 * R) * CSW;
@@ -318,11 +289,10 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
     const int Wmax = (GXS - 1) * H + n;
     const int RING = rco_ring(m, H), RW4 = RING >> 2, CSW = rco_csw(RING);
     const int nwarps = blockDim.x >> 5;
-    using SG = RcoScan<H>;
-    const RcoSmem L = rco_smem<H>(Wmax, GXS, CSW, K);
-    const int NSr = L.nseg, RSr = L.rs;                           // segments and words per scanned row
-    unsigned *hsc = rsm + L.hsc;                                  // (K H + 2) x RSr scanned sums
-    unsigned *segt = rsm + L.segt;                                // (K H + 2) x NSr segment totals
+    const RcoSmem L = rco_smem<H>(Wmax, GXS, CSW, K, n);
+    const int NB = L.nb, BPL = L.bpl, RWc = L.rwc, RWp = L.rwp;
+    unsigned *hsc = rsm + L.hsc;                                  // (K H + 2) x RWc column sums
+    unsigned *pre = rsm + L.pre;                                  // (K H + 2) x RWp block prefixes
     int *cS = reinterpret_cast<int *>(rsm + L.cst);               // per centre: S_hat
     float *cI = reinterpret_cast<float *>(rsm + L.cst + GXS);     // per centre: 1/(mn Omega_hat)
     unsigned *psq = rsm + L.psq;                                  // [2][MAXT] column sums of P, P^2
@@ -333,7 +303,6 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
     const bool active = j < W;
     const long long mn = (long long)m * n;
     const int RW = W + 2 * R;                                     // ring columns used
-    const int addr_j = rco_addr<H>(j);
 
     // image rows [r0, r0 + cnt) into their ring slots: columns across the
     // threads; a thread's rows are independent loads, issued together
@@ -369,60 +338,83 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
         }
     };
     const int jc = cx0 + j;
-    // inclusive prefix of rows [0, nrows) of buffer hb, segment by segment
-    // (segment totals in sb); item = (row, segment)
-    auto scan_rows = [&](unsigned *hb, unsigned *sb, int nrows) {
-        for (int item = warp; item < nrows * NSr; item += nwarps) {
-            const int row = item / NSr, seg = item - row * NSr;
-            unsigned *lp = hb + row * RSr + (seg * 32 + lane) * SG::PLS;
-            const int cnt = W - (seg * SG::SL + lane * SG::PL);   // this lane's columns below W
-            unsigned v[SG::PL];                                   // read once, kept for pass 2
-            unsigned tot = 0u;
+    // Window sums at the centres.  The strip's centres are H columns apart
+    // (centre gxi at column gxi * H), so a row of column sums is cut into
+    // blocks of H columns: with n = a H + b, the window of centre gxi is
+    // blocks gxi .. gxi + a - 1 plus the first b columns of block gxi + a.
+    // One warp per row: each lane sums BPL consecutive blocks, the lane
+    // totals are scanned, and the lane writes PrefB[k] (the sum of blocks
+    // 0 .. k - 1) and PB[k] (the first b columns of block k).  The image's
+    // last group, when shorter than H, has its centre dl columns before its
+    // block: its window also takes the last dl columns of the block before
+    // and a partial of b2 columns at its end (computed by lane 0).  Columns
+    // past the strip hold stale sums; they only reach blocks no window uses.
+    const int na = n / H, nb = n - na * H;
+    int gxs = -1, dl = 0, a2 = 0, b2 = 0;
+    if (gx1 == Gx && ngx >= 2) {
+        const int ls = Lx - (Gx - 1) * H;   // size of the image's last group
+        if (ls < H) {
+            gxs = ngx - 1;
+            dl = R - (ls - 1) / 2;
+            a2 = (n - dl) / H;
+            b2 = n - dl - a2 * H;
+        }
+    }
+    auto block_rows = [&](int nrows) {
+        for (int rr = warp; rr < nrows; rr += nwarps) {
+            const unsigned *cr = hsc + rr * RWc;
+            unsigned *pr = pre + rr * RWp;
+            const int k0 = lane * BPL, k1 = min(NB, k0 + BPL);
+            // one read of the lane's columns: block partials and prefixes
+            // relative to the lane's first block, then the lane offsets
+            unsigned run = 0u;
+            for (int k = k0; k < k1; ++k) {
+                const unsigned *cb = cr + k * H;
+                unsigned pb = 0u, bs = 0u;
 #pragma unroll
-            for (int i = 0; i < SG::PL; ++i) {
-                v[i] = i < cnt ? lp[i] : 0u;
-                tot += v[i];
+                for (int c = 0; c < H; ++c) {
+                    const unsigned v = cb[c];
+                    pb += c < nb ? v : 0u;
+                    bs += v;
+                }
+                pr[k] = run;
+                pr[NB + k] = pb;
+                run += bs;
             }
-            unsigned inc = tot;
+            unsigned inc = run;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const unsigned u = __shfl_up_sync(0xffffffffu, inc, o);
                 if (lane >= o) inc += u;
             }
-            unsigned run = inc - tot;
-#pragma unroll
-            for (int i = 0; i < SG::PL; ++i) {
-                run += v[i];
-                lp[i] = run;   // inclusive prefix within the segment (past W: never read)
+            const unsigned off = inc - run;
+            for (int k = k0; k < k1; ++k) pr[k] += off;
+            if (gxs >= 0 && lane == 0) {
+                unsigned s1 = 0u, s2 = 0u;
+                for (int c = gxs * H - dl; c < gxs * H; ++c) s1 += cr[c];
+                for (int c = (gxs + a2) * H; c < (gxs + a2) * H + b2; ++c) s2 += cr[c];
+                pr[2 * NB] = s1;
+                pr[2 * NB + 1] = s2;
             }
-            if (lane == 31) sb[row * NSr + seg] = inc;
         }
     };
-    // sum of a scanned row over pivot columns [c1, c1 + n) (modulo 2^32)
-    auto window = [&](const unsigned *row, const unsigned *segrow, int c1) {
-        const int c2 = c1 + n - 1;
-        unsigned X = row[rco_addr<H>(c2)];
-        int s1 = 0;
-        if (c1 > 0) {
-            X -= row[rco_addr<H>(c1 - 1)];
-            s1 = (c1 - 1) >> SG::LGSL;
-        }
-        for (int sgi = s1; sgi < (c2 >> SG::LGSL); ++sgi) X += segrow[sgi];
-        return X;
+    // sum of a row over the window of centre gxi (modulo 2^32)
+    auto xsum = [&](const unsigned *pr, int gxi) -> unsigned {
+        if (gxi == gxs) return pr[2 * NB] + (pr[gxs + a2] - pr[gxs]) + pr[2 * NB + 1];
+        return (pr[gxi + na] - pr[gxi]) + pr[NB + gxi + na];
     };
 
     // constants of this thread's first emission task (centre gxi, shift
-    // column sxi): its member column and the scanned-row addresses of its
-    // centre's n pivot columns; further tasks (n < H only) take the loop
+    // column sxi): its member column; further tasks (n < H only) take the
+    // loop
     const int t0_gxi = (int)threadIdx.x / H, t0_sxi = (int)threadIdx.x - t0_gxi * H;
-    int t0_mx, t0_c1;
+    int t0_mx;
     bool t0_ok;
     {
         const int gx = gx0 + t0_gxi;
         const int cxg = group_centre_of(gx, Lx, H);
         t0_mx = cxg + t0_sxi - R;
         t0_ok = (int)threadIdx.x < ngx * H && t0_mx >= gx * H && t0_mx < min(gx * H + H, Lx);
-        t0_c1 = cxg - cx0;
     }
 
     int r = group_centre_of(gy0, Ly, H);
@@ -481,8 +473,8 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
         }
         // emission of centre row cy in chunks of K shift rows (sy): the chunk's
         // K H column-sum rows (and, in the first chunk, the column sums of P
-        // and P^2 for the pivot statistics) are stored, scanned together and
-        // read by the tasks
+        // and P^2 for the pivot statistics) are stored, cut into blocks
+        // together and read by the tasks
         const int gys = gy * H, gye = min(gys + H, Ly);
         for (int k0 = 0; k0 < H; k0 += K) {
             const int kn = min(K, H - k0);
@@ -502,27 +494,26 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
             }
             if (active) {
                 if (first) {
-                    hsc[addr_j] = *ps_j;
-                    hsc[RSr + addr_j] = *pq_j;
+                    hsc[j] = *ps_j;
+                    hsc[RWc + j] = *pq_j;
                 }
 #pragma unroll
                 for (int syi = 0; syi < H; ++syi) {
                     if (syi < k0 || syi >= k0 + kn) continue;
 #pragma unroll
                     for (int sxi = 0; sxi < H; ++sxi)
-                        hsc[(rb + (syi - k0) * H + sxi) * RSr + addr_j] = (unsigned)cs[syi * H + sxi];
+                        hsc[(rb + (syi - k0) * H + sxi) * RWc + j] = (unsigned)cs[syi * H + sxi];
                 }
             }
             __syncthreads();
-            scan_rows(hsc, segt, rb + kn * H);
+            block_rows(rb + kn * H);
             __syncthreads();
             if (first) {
                 // pivot statistics of this row's centres: window sums of the
                 // column sums of P and P^2 (exact, < 2^32)
                 if ((int)threadIdx.x < ngx) {
                     const int gx = gx0 + threadIdx.x;
-                    const int c1 = group_centre_of(gx, Lx, H) - cx0;
-                    const long long Sp = window(hsc, segt, c1), Qp = window(hsc + RSr, segt + NSr, c1);
+                    const long long Sp = xsum(pre, threadIdx.x), Qp = xsum(pre + RWp, threadIdx.x);
                     const long long var = mn * Qp - Sp * Sp;   // exact
                     cS[threadIdx.x] = (int)Sp;
                     // 1 / (mn Omega_hat) = sqrt(mn / var) / mn
@@ -551,7 +542,7 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
                     const int64_t li = (int64_t)my * Lx + t0_mx;
                     const int ws = wsum[li];
                     const float iw = inv_sigma[li];
-                    const unsigned X = window(hsc + (row + t0_sxi) * RSr, segt + (row + t0_sxi) * NSr, t0_c1);
+                    const unsigned X = xsum(pre + (row + t0_sxi) * RWp, t0_gxi);
                     const long long num = mn * (long long)X - (long long)cS[t0_gxi] * (long long)ws;
                     const float rho = (i64_to_f32(num) * iw) * cI[t0_gxi];
                     if (rco) rco[li] = rho;
@@ -566,7 +557,7 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
                     const int64_t li = (int64_t)my * Lx + mx;
                     const int ws = wsum[li];
                     const float iw = inv_sigma[li];
-                    const unsigned X = window(hsc + (row + sxi) * RSr, segt + (row + sxi) * NSr, cxg - cx0);
+                    const unsigned X = xsum(pre + (row + sxi) * RWp, gxi);
                     const long long num = mn * (long long)X - (long long)cS[gxi] * (long long)ws;
                     const float rho = (i64_to_f32(num) * iw) * cI[gxi];
                     if (rco) rco[li] = rho;
@@ -771,7 +762,7 @@ RcoGeom rco_geom(int p, int q, int m, int n) {
     const int csw = rco_csw(rco_ring(m, H));
     auto smem_for = [&](int gxs, int k, int *wmax) {
         *wmax = (gxs - 1) * H + n;
-        return (size_t)rco_smem<H>(*wmax, gxs, csw, k).total * sizeof(unsigned);
+        return (size_t)rco_smem<H>(*wmax, gxs, csw, k, n).total * sizeof(unsigned);
     };
     // the most shift rows per emission (K) that fit beside the image ring
     auto best_k = [&](int gxs, size_t *smem, int *wmax) {
