@@ -183,6 +183,27 @@ def test_rho_co_wide_strips(opta, h):
     assert abs(cnt - exp_cnt) <= near
 
 
+@pytest.mark.parametrize("h", [5, 7])
+def test_rho_co_tall_windows_in_several_emission_chunks(opta, h):
+    """128 x 128 windows across a 4090-wide image: shared memory holds fewer
+    than h shift rows per emission, so every group row is emitted in several
+    chunks; the image's last group is short (a centre off the block grid)."""
+    img = synth.aerial_image(4096, 8, 60, seed=91)[:150, :4090].copy()
+    img[10:60, 1000:1600] = 40                   # flat windows
+    m = n = 128
+    P = ref.quantise_pivot(ref.blur(img, np.full((3, 64), 1.0), 64))
+    Ly, Lx = 150 - m + 1, 4090 - n + 1
+    assert Lx % h != 0
+    R = torch.empty(Ly * Lx, dtype=torch.float32, device="cuda")
+    cnt = opta.opta_dbg_rho_co(_cuda(P), _cuda(img), m, n, h, R, rho_cut=0.6)
+    got = R.cpu().numpy().reshape(Ly, Lx)
+    exp = ref.rho_co_map(P, img, m, n, h)
+    assert np.max(np.abs(got - exp)) <= 2e-6
+    exp_cnt = int(np.count_nonzero(exp < 0.6))
+    near = int(np.count_nonzero(np.abs(exp - 0.6) < 2e-6))
+    assert abs(cnt - exp_cnt) <= near
+
+
 def test_opta_decisions_match_oracle(opta):
     """The OptA level loop's choices (group side, per-block sigma) equal the
     oracle's on a case without decisions within rounding of a threshold."""
