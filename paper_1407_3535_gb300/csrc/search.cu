@@ -685,11 +685,9 @@ bound_pass_kernel(const Scan2Batch B, const float2 *__restrict__ gco,
     __shared__ int hist[kS2MaxT][kUbBuckets];
     __shared__ float lims[kS2MaxT];
     __shared__ unsigned short queue[kS2MaxT * kPassGroups];   // (t << 8) | group in tile
-    __shared__ unsigned short dyx[81];                        // member k of a group: (dy << 8) | dx
     __shared__ int qn;
     const int T = B.T;
     for (int i = threadIdx.x; i < T * kUbBuckets; i += blockDim.x) hist[i / kUbBuckets][i % kUbBuckets] = 0;
-    for (int i = threadIdx.x; i < h * h; i += blockDim.x) dyx[i] = (unsigned short)(((i / h) << 8) | (i % h));
     if ((int)threadIdx.x < T)
         lims[threadIdx.x] = B.st[threadIdx.x].flat ? -1.f : B.st[threadIdx.x].theta_lim;
     const int Gy = groups_along(Ly, h), Gx = groups_along(Lx, h);
@@ -721,47 +719,46 @@ bound_pass_kernel(const Scan2Batch B, const float2 *__restrict__ gco,
             }
         }
         __syncthreads();
-        // members of the passing (group, template) pairs: a warp per pair,
-        // its centre interval formed once, the lanes over the h * h members
-        // (one append per warp: they all belong to template t)
-        const int nq = qn;
-        const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-        for (int e = warp; e < nq; e += nwarps) {
-            const int code = queue[e];
-            const int t = code >> 8;
-            const int gg = (int)(g0 + (code & 255));
-            const int gy = gg / Gx, gx = gg - gy * Gx;
-            const float2 tv = centre_interval(B.rho_tc[t * B.tc_stride + gg], B.c_efac[gg], B.epsA);
-            const float lim = lims[t];
-            const int y0 = gy * h, x0 = gx * h;
-            const int ny = min(h, Ly - y0), nx = min(h, Lx - x0);
-            for (int m0 = 0; m0 < hh; m0 += 32) {   // uniform over the warp
-                const int mem = m0 + lane;
-                bool f = false;
-                int li = 0;
-                float gap = 0.f;
-                if (mem < hh) {
-                    const int dy = dyx[mem] >> 8, dx = dyx[mem] & 255;
-                    if (dy < ny && dx < nx) {
-                        li = (y0 + dy) * Lx + x0 + dx;
-                        gap = loc_gap(tv, theta_co[li]);
-                        f = gap <= lim;
-                        if (f) atomicAdd(&hist[t][gap_bucket(gap, lim)], 1);
+        const int nitem = qn * hh;
+        for (int ib = 0; ib < nitem; ib += blockDim.x) {   // uniform trip count
+            const int item = ib + threadIdx.x;
+            bool f = false;
+            int t = 0, li = 0, b = 0;
+            float gap = 0.f;
+            if (item < nitem) {
+                const int e = item / hh, mem = item - e * hh;
+                const int code = queue[e];
+                t = code >> 8;
+                const int64_t gg = g0 + (code & 255);
+                const int gy = (int)(gg / Gx), gx = (int)(gg - (int64_t)gy * Gx);
+                const int my = gy * h + mem / h, mx = gx * h + mem % h;
+                if (my < Ly && mx < Lx) {
+                    li = my * Lx + mx;
+                    const float2 tv = centre_interval(B.rho_tc[t * B.tc_stride + gg], B.c_efac[gg], B.epsA);
+                    gap = loc_gap(tv, theta_co[li]);
+                    f = gap <= lims[t];
+                    if (f) {
+                        b = gap_bucket(gap, lims[t]);
+                        atomicAdd(&hist[t][b], 1);
                     }
                 }
-                const unsigned fm = __ballot_sync(0xffffffffu, f);
-                if (fm) {
-                    int base = 0;
-                    if (lane == 0) base = atomicAdd(&B.ucnt[t], __popc(fm));
-                    base = __shfl_sync(0xffffffffu, base, 0);
-                    if (f) {
-                        const int64_t pos = base + __popc(fm & ((1u << lane) - 1u));
-                        if (pos < B.scap) {
-                            reinterpret_cast<int *>(B.surv_eps)[t * B.scap + pos] = li;
-                            B.surv_rho[t * B.scap + pos] = gap;
-                        } else {
-                            atomicOr(&B.st[t].overflow, 1);
-                        }
+            }
+            // append to template t's unordered list, aggregated over the
+            // lanes of the warp that share t
+            const unsigned fm = __ballot_sync(0xffffffffu, f);
+            if (fm) {
+                const unsigned peers = __match_any_sync(0xffffffffu, f ? t : -1);
+                const int leader = __ffs(peers) - 1;
+                int base = 0;
+                if (f && lane == leader) base = atomicAdd(&B.ucnt[t], __popc(peers));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (f) {
+                    const int64_t pos = base + __popc(peers & ((1u << lane) - 1u));
+                    if (pos < B.scap) {
+                        reinterpret_cast<int *>(B.surv_eps)[t * B.scap + pos] = li;
+                        B.surv_rho[t * B.scap + pos] = gap;
+                    } else {
+                        atomicOr(&B.st[t].overflow, 1);
                     }
                 }
             }
