@@ -387,28 +387,46 @@ def main():
     opta.opta_dbg_profile_enable(False)
     prof = opta.opta_dbg_profile_read()
     h.close()
-    # and of one preparation
-    opta.opta_dbg_profile_enable(True)
-    hp = opta.optA_prepare(dimg, prm, sizes=sizes, stream=stream)
-    torch.cuda.synchronize()
-    opta.opta_dbg_profile_enable(False)
-    prof_prep = opta.opta_dbg_profile_read()
-    hp.close()
+    # and of the preparation, one size at a time on the launch stream: the
+    # sizes' kernels then do not overlap, so each launch's events time it
+    # alone (the image-level kernels are taken from the first size only)
+    prep_by_size = {}
+    for sz in sizes:
+        opta.opta_dbg_profile_enable(True)
+        hp = opta.optA_prepare(dimg, prm, sizes=[sz], stream=stream)
+        torch.cuda.synchronize()
+        opta.opta_dbg_profile_enable(False)
+        one = opta.opta_dbg_profile_read()
+        hp.close()
+        if sz != sizes[0]:
+            one = {k: v for k, v in one.items() if k not in IMAGE_LEVEL_KERNELS}
+        prep_by_size[sz] = one
+    prof_prep = {}
+    for one in prep_by_size.values():
+        for k, (ms_, nl_) in one.items():
+            a = prof_prep.setdefault(k, [0.0, 0])
+            a[0] += ms_
+            a[1] += nl_
 
-    # end to end through the C ABI with host buffers
-    host_img = np.ascontiguousarray(img)
-    host_ts = [np.ascontiguousarray(t.data) for t in ts]
-    h2d = host_img.nbytes + sum(t.nbytes for t in host_ts)
+    # end to end through the C ABI with host buffers (pinned): the image and
+    # the templates are copied to the device, and the results back, inside
+    # each timed step; one untimed step first
+    host_img = torch.from_numpy(np.ascontiguousarray(img)).pin_memory()
+    host_ts = [torch.from_numpy(np.ascontiguousarray(t.data, dtype=np.float32)).pin_memory()
+               for t in ts]
+    h2d = host_img.numel() * host_img.element_size() + sum(t.numel() * t.element_size() for t in host_ts)
     d2h = ctypes.sizeof(opta.OptaResult) * len(host_ts)
     e2e_times = []
-    for _ in range(max(1, min(args.steps, 3))):
+    for it in range(1 + max(3, min(args.steps, 5))):
         flush.zero_()
+        torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         hh = opta.optA_prepare(host_img, prm, sizes=sizes, stream=stream)
         opta.optA_search(hh, host_ts, stream=stream)
         torch.cuda.synchronize()
-        e2e_times.append(time.perf_counter() - t0)
+        if it > 0:
+            e2e_times.append(time.perf_counter() - t0)
         hh.close()
     e2e_value = L_all / float(np.mean(e2e_times)) if world == 1 else L_step / float(np.mean(e2e_times)) * world
 
@@ -448,7 +466,7 @@ def main():
                  "speedup_of_opta_search": (L_step / (search_ms / 1000.0)) / brute_rate,
                  "speedup_of_opta_step": value / brute_rate if world == 1 else None}
 
-    roof = roofline(prof, ts, res_prof, size_info, img.shape, clocks)
+    roof = roofline(prof, prep_by_size, ts, res_prof, img.shape)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -478,7 +496,9 @@ def main():
                    "l2": "512 MiB buffer written before every timed step",
                    "parallelism": f"templates sharded over {world} GPU(s)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+                "d2h_bytes_per_step": int(d2h), "steps": len(e2e_times),
+                "ms_per_step": 1000.0 * float(np.mean(e2e_times)),
+                "ms_min": 1000.0 * float(np.min(e2e_times))},
         "gpu_launches": int(launches),
         "clocks": clocks,
         "roofline": roof,
@@ -498,6 +518,7 @@ def main():
         "kernels_ms": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
         "prepare_kernels_ms": {k: [round(v[0], 3), v[1]] for k, v in
                                sorted(prof_prep.items(), key=lambda kv: -kv[1][0])},
+        "prepare_serial_device_ms": round(sum(v[0] for v in prof_prep.values()), 3),
         "device_bytes_handle_and_search_ctx": int(mem_bytes),
         "group_sizes": {k: v["group_h"] for k, v in size_info.items()},
         "per_size": per_size,
@@ -675,25 +696,79 @@ def kernel_roofline(name, tot_ms, nl, ts, results, shape, pk, src):
             "launches": nl, "avg_launch_ms": tot_ms / nl, "peak_source": note}
 
 
-def roofline(prof, ts, results, size_info, shape, clocks):
-    """Roofline of the kernel with the largest share of the search pass, plus
-    the other main kernels under `others`."""
+# preparation kernels run once per image, not once per size
+IMAGE_LEVEL_KERNELS = ("ingest_u8_kernel", "ii_rows_kernel", "ii_cols_kernel")
+
+# DRAM bytes per launch over algorithmic bytes per launch, from one ncu
+# capture of each kernel on a 4096^2 image with 64x64 windows
+# (`bench.py --case rho_co:5`: 200.6 MB read + written against 212 MB;
+# `bench.py --case blur_corr:64`: 185.6 MB against 164 MB).  The traffic of
+# the bench's launches is this ratio times their algorithmic bytes.
+TRAFFIC_RATIO = {"rho_co_kernel": 200.6 / 212.0, "blur_corr_kernel": 185.6 / 164.0}
+
+
+def prep_roofline(name, prep_by_size, shape, pk, src):
+    """Algorithmic bytes of the preparation kernel `name` over the launches
+    of every size (one size at a time, so the launches do not overlap),
+    divided by their device time.  `rho_co_kernel` gathers the launches of
+    every group side H (timed as rho_co_kernel<H>)."""
+    p, q = shape
+    tot_b = tot_ms = 0.0
+    nl = 0
+    for (m, n), prof in prep_by_size.items():
+        Ly, Lx = p - m + 1, q - n + 1
+        L = Ly * Lx
+        for k, (ms_, cnt) in prof.items():
+            if name == "rho_co_kernel" and k.startswith("rho_co_kernel<"):
+                H = int(k[len("rho_co_kernel<"):-1])
+                G = ((Ly + H - 1) // H) * ((Lx + H - 1) // H)
+                # P and I read once; window sums and 1/sigma per location
+                # read, rho_co per location written; per centre 1/sigma and
+                # the error factor written
+                b = 2.0 * p * q + 12.0 * L + 8.0 * G
+            elif name == "blur_corr_kernel" and k == name:
+                # P and I read once; window sums and 1/sigma per location read
+                b = 2.0 * p * q + 8.0 * L
+            else:
+                continue
+            tot_b += cnt * b
+            tot_ms += ms_
+            nl += cnt
+    if nl == 0 or tot_ms <= 0:
+        return None
+    avg_s = tot_ms / nl / 1000.0
+    achieved = tot_b / nl / avg_s / 1e9
+    peak = pk.get("hbm_gbs", 6800.0)
+    ratio = TRAFFIC_RATIO.get(name)
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": ratio * tot_b / nl if ratio else None,
+            "launches": nl, "avg_launch_ms": tot_ms / nl, "total_ms": tot_ms,
+            "algorithmic_bytes_per_launch": tot_b / nl,
+            "peak_source": f"HBM copy bandwidth ({src})"}
+
+
+def roofline(prof, prep_by_size, ts, results, shape):
+    """Roofline of the kernel with the largest device time in a step (the
+    search pass, plus the preparation timed one size at a time), the other
+    main kernels under `others`."""
     if not prof:
         return None
     pk, src = peaks()
-    order = sorted(prof.items(), key=lambda kv: -kv[1][0])
-    main = None
-    others = []
-    for name, (tot_ms, nl) in order:
+    rows = []
+    for name, (tot_ms, nl) in prof.items():
         r = kernel_roofline(name, tot_ms, nl, ts, results, shape, pk, src)
-        if r is None:
-            continue
-        if main is None:
-            main = r
-        else:
-            others.append(r)
-    if main is not None:
-        main["others"] = others
+        if r is not None:
+            r["total_ms"] = tot_ms
+            rows.append(r)
+    for name in ("rho_co_kernel", "blur_corr_kernel"):
+        r = prep_roofline(name, prep_by_size, shape, pk, src)
+        if r is not None:
+            rows.append(r)
+    if not rows:
+        return None
+    rows.sort(key=lambda r: -r["total_ms"])
+    main = rows[0]
+    main["others"] = rows[1:]
     return main
 
 

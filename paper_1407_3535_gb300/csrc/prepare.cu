@@ -167,7 +167,10 @@ template <int H>
 struct RcoCfg {
     static constexpr int R = (H - 1) / 2;
     static constexpr int NS = H * H;
-    static constexpr int MAXT = H >= 9 ? 448 : (H >= 7 ? 640 : 1024);
+    // threads per CTA at most (one per pivot column and per image ring
+    // column): the H^2 column sums, the next row's slide data held across an
+    // emission and the emission's 64-bit finish share 65536 / MAXT registers
+    static constexpr int MAXT = H >= 9 ? 448 : (H >= 7 ? 640 : (H >= 5 ? 896 : 1024));
     static constexpr int KW = (H + 3) / 4;           // pivot words per batch
     static constexpr int BATCH = 4 * KW;             // rows per batch (>= H)
     static constexpr int NA = (H + BATCH + 2) / 4;   // aligned image words per column and batch
@@ -239,6 +242,39 @@ __device__ __forceinline__ void rco_batch(int (&cs)[H * H], const unsigned (&pw)
             else cs[sy * H + sx] += (int)acc;
         }
     }
+}
+
+// One lane's blocks [k0, k1) of a column-sum row cr (blocks of H columns):
+// pr[k] = the sum of blocks k0 .. k - 1, pr[NB + k] = the sum of block k's
+// first NBc columns; returns the sum of all the lane's blocks.  NBc is a
+// template parameter so that the split of a block costs no selects.
+template <int H, int NBc>
+__device__ __forceinline__ unsigned rco_blocks(const unsigned *cr, unsigned *pr, int k0, int k1,
+                                               int NB) {
+    unsigned run = 0u;
+    for (int k = k0; k < k1; ++k) {
+        const unsigned *cb = cr + k * H;
+        unsigned pb = 0u;
+#pragma unroll
+        for (int c = 0; c < NBc; ++c) pb += cb[c];
+        unsigned bs = pb;
+#pragma unroll
+        for (int c = NBc; c < H; ++c) bs += cb[c];
+        pr[k] = run;
+        pr[NB + k] = pb;
+        run += bs;
+    }
+    return run;
+}
+
+// rco_blocks for the run-time split nb in [0, H) (uniform over the CTA)
+template <int H, int NBc = 0>
+__device__ __forceinline__ unsigned rco_blocks_nb(int nb, const unsigned *cr, unsigned *pr, int k0,
+                                                  int k1, int NB) {
+    if constexpr (NBc + 1 < H) {
+        if (nb != NBc) return rco_blocks_nb<H, NBc + 1>(nb, cr, pr, k0, k1, NB);
+    }
+    return rco_blocks<H, NBc>(cr, pr, k0, k1, NB);
 }
 
 // Shared-memory words of one CTA (host and device agree on the layout):
@@ -323,20 +359,6 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
             }
         }
     };
-    auto load_step = [&](int r0, int cnt) {          // cnt <= H rows of one slide batch
-        const int slot0 = (r0 + R) % RING;
-        for (int col = threadIdx.x; col < RW; col += blockDim.x) {
-            uint8_t v[H];
-#pragma unroll
-            for (int k = 0; k < H; ++k) v[k] = k < cnt ? img_at(r0 + k, col) : (uint8_t)0;
-            int slot = slot0;
-#pragma unroll
-            for (int k = 0; k < H; ++k) {
-                if (k < cnt) ring_put(slot, col, v[k]);
-                slot = slot + 1 == RING ? 0 : slot + 1;
-            }
-        }
-    };
     const int jc = cx0 + j;
     // Window sums at the centres.  The strip's centres are H columns apart
     // (centre gxi at column gxi * H), so a row of column sums is cut into
@@ -367,20 +389,7 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
             const int k0 = lane * BPL, k1 = min(NB, k0 + BPL);
             // one read of the lane's columns: block partials and prefixes
             // relative to the lane's first block, then the lane offsets
-            unsigned run = 0u;
-            for (int k = k0; k < k1; ++k) {
-                const unsigned *cb = cr + k * H;
-                unsigned pb = 0u, bs = 0u;
-#pragma unroll
-                for (int c = 0; c < H; ++c) {
-                    const unsigned v = cb[c];
-                    pb += c < nb ? v : 0u;
-                    bs += v;
-                }
-                pr[k] = run;
-                pr[NB + k] = pb;
-                run += bs;
-            }
+            const unsigned run = rco_blocks_nb<H>(nb, cr, pr, k0, k1, NB);
             unsigned inc = run;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -443,18 +452,38 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
     }
     unsigned long long local = 0;
     const int ntask = ngx * H;
+    // The next group row's slide data (this column's pivot bytes entering
+    // and leaving the window, and the image rows up to r + steps - 1 + m + R
+    // for ring column j) is loaded into registers before this row's emission
+    // and stored and used after it, so that the loads' latency hides behind
+    // the emission.  The ring slots it overwrites hold rows above r - R that
+    // no slide reads again (the emission does not read the ring).
+    unsigned pa[KW], pr[KW];
+    uint8_t iv[H];
+    int steps = 0;                           // rows to the next centre row (<= H)
+    auto fetch = [&](int gy) {
+        steps = gy < gy1 ? group_centre_of(gy, Ly, H) - r : 0;
+        if (steps <= 0) return;
+        if (active) {
+            rco_pcol<H>(pa, P, q, jc, r + m, steps);
+            rco_pcol<H>(pr, P, q, jc, r, steps);
+        }
+        if (j < RW) {
+#pragma unroll
+            for (int k = 0; k < H; ++k) iv[k] = k < steps ? img_at(r + m + R + 1 + k, j) : (uint8_t)0;
+        }
+    };
     for (int gy = gy0; gy < gy1; ++gy) {
         const int cy = group_centre_of(gy, Ly, H);
-        const int steps = cy - r;            // 0 for the first row, <= H after
-        if (steps > 0) {
-            // this column's pivot rows entering and leaving the window, then
-            // the image rows up to r + steps - 1 + m + R the batch needs
-            unsigned pa[KW], pr[KW];
-            if (active) {
-                rco_pcol<H>(pa, P, q, jc, r + m, steps);
-                rco_pcol<H>(pr, P, q, jc, r, steps);
+        if (gy > gy0 && steps > 0) {
+            if (j < RW) {
+                int slot = (r + m + 2 * R + 1) % RING;
+#pragma unroll
+                for (int k = 0; k < H; ++k) {
+                    if (k < steps) ring_put(slot, j, iv[k]);
+                    slot = slot + 1 == RING ? 0 : slot + 1;
+                }
             }
-            load_step(r + m + R + 1, steps);
             __syncthreads();
             if (active) {
                 rco_batch<H, false>(cs, pa, r + m, ringw, j, CSW, RW4, RING);
@@ -469,8 +498,10 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
                 *pq_j += dpq;
             }
             r += steps;
-            __syncthreads();   // nobody reads the dead rows the next batch overwrites
+            // (no barrier: the emission reads no ring slot, and its first
+            // barrier orders this slide before the next ring stores)
         }
+        fetch(gy + 1);
         // emission of centre row cy in chunks of K shift rows (sy): the chunk's
         // K H column-sum rows (and, in the first chunk, the column sums of P
         // and P^2 for the pivot statistics) are stored, cut into blocks
@@ -758,7 +789,7 @@ RcoGeom rco_geom(int p, int q, int m, int n) {
     const int Ly = p - m + 1, Lx = q - n + 1;
     const int Gy = groups_along(Ly, H), Gx = groups_along(Lx, H);
     // window sums of uint8 products are kept in 32 bits
-    if (n + H > MAXT || (uint64_t)m * n * 65025u > 0xffffffffull) return g;
+    if (n + 2 * H > MAXT || (uint64_t)m * n * 65025u > 0xffffffffull) return g;
     const int csw = rco_csw(rco_ring(m, H));
     auto smem_for = [&](int gxs, int k, int *wmax) {
         *wmax = (gxs - 1) * H + n;
@@ -774,7 +805,7 @@ RcoGeom rco_geom(int p, int q, int m, int n) {
     };
     // widest strip within the thread limit, narrowed until the ring and one
     // shift row per emission fit
-    g.GXS = std::min((MAXT - n) / H + 1, Gx);
+    g.GXS = std::min((MAXT - n - (H - 1)) / H + 1, Gx);
     g.K = best_k(g.GXS, &g.smem, &g.Wmax);
     while (g.K == 0 && g.GXS > 1) {
         g.GXS = std::max(1, g.GXS - std::max(1, g.GXS / 8));
@@ -788,7 +819,8 @@ RcoGeom rco_geom(int p, int q, int m, int n) {
     g.strips = (Gx + g.GXS - 1) / g.GXS;
     g.GXS = (Gx + g.strips - 1) / g.strips;
     g.K = best_k(g.GXS, &g.smem, &g.Wmax);
-    g.threads = ((g.Wmax + 31) / 32) * 32;
+    // a thread per pivot column and per image ring column (W + 2R of them)
+    g.threads = ((g.Wmax + (H - 1) + 31) / 32) * 32;
     (void)Gy;
     return g;
 }
@@ -820,7 +852,13 @@ cudaError_t launch_rho_co_h(const uint8_t *P, const uint8_t *I, int p, int q, in
     const int GYB = (Gy + bands - 1) / bands;
     bands = (Gy + GYB - 1) / GYB;
     dim3 grid(g.strips, bands);
-    LaunchScope ls_rho_co_kernel("rho_co_kernel", s);
+    // launches are timed under the group side's name, so that the work of
+    // each (the H^2 shifts it slides) can be told apart
+    static_assert(H >= 1 && H <= 9 && (H & 1), "odd group sides up to 9");
+    static const char *const kName[10] = {"", "rho_co_kernel<1>", "", "rho_co_kernel<3>", "",
+                                          "rho_co_kernel<5>", "", "rho_co_kernel<7>", "",
+                                          "rho_co_kernel<9>"};
+    LaunchScope ls_rho_co_kernel(kName[H], s);
     rho_co_kernel<H><<<grid, g.threads, smem, s>>>(P, I, p, q, m, n, Ly, Lx, wsum, inv_sigma,
                                                    g.GXS, GYB, g.K, cut, rco, count, c_inv_sigma,
                                                    c_efac);
