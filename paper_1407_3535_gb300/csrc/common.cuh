@@ -53,6 +53,12 @@ __device__ __forceinline__ float i64_to_f32(long long v) {
     return fmaf(fhi, 17592186044416.f, fmid * 4194304.f) + flo;     // 2^44, 2^22
 }
 
+// a * b - c * d exactly, for 32-bit unsigned a, b and 32-bit signed c, d:
+// two widening 32 x 32 -> 64 products (no 64 x 64 multiply)
+__device__ __forceinline__ long long mul_sub_wide(unsigned a, unsigned b, int c, int d) {
+    return (long long)((unsigned long long)a * b) - (long long)c * (long long)d;
+}
+
 // mn * Q - S * S (= mn^2 * variance) of a window of mn 8-bit pixels with sum S
 // and square sum Q, as FP32.  Exact in int64 up to 2^23 pixels (the product
 // stays below 2^62); larger windows take it from FP64 products.

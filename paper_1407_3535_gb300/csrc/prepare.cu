@@ -338,6 +338,7 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool active = j < W;
     const long long mn = (long long)m * n;
+    const unsigned mn32 = (unsigned)mn;                           // < 2^17 (see rco_geom)
     const int RW = W + 2 * R;                                     // ring columns used
 
     // image rows [r0, r0 + cnt) into their ring slots: columns across the
@@ -450,14 +451,17 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
         *ps_j = ps;
         *pq_j = pq;
     }
-    unsigned long long local = 0;
+    unsigned local = 0;                      // this thread's locations below the cut
     const int ntask = ngx * H;
     // The next group row's slide data (this column's pivot bytes entering
     // and leaving the window, and the image rows up to r + steps - 1 + m + R
-    // for ring column j) is loaded into registers before this row's emission
-    // and stored and used after it, so that the loads' latency hides behind
-    // the emission.  The ring slots it overwrites hold rows above r - R that
-    // no slide reads again (the emission does not read the ring).
+    // for ring column j) is loaded into registers before this row's emission,
+    // the image rows stored into the ring after the emission's block pass and
+    // the pivot bytes slid after its tasks, so that the loads' latency hides
+    // behind the emission and the emission's last barrier also publishes the
+    // ring rows (no barrier between one row's tasks and the next row's
+    // slide).  The ring slots it overwrites hold rows above r - R that no
+    // slide reads again (the emission does not read the ring).
     unsigned pa[KW], pr[KW];
     uint8_t iv[H];
     int steps = 0;                           // rows to the next centre row (<= H)
@@ -476,15 +480,6 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
     for (int gy = gy0; gy < gy1; ++gy) {
         const int cy = group_centre_of(gy, Ly, H);
         if (gy > gy0 && steps > 0) {
-            if (j < RW) {
-                int slot = (r + m + 2 * R + 1) % RING;
-#pragma unroll
-                for (int k = 0; k < H; ++k) {
-                    if (k < steps) ring_put(slot, j, iv[k]);
-                    slot = slot + 1 == RING ? 0 : slot + 1;
-                }
-            }
-            __syncthreads();
             if (active) {
                 rco_batch<H, false>(cs, pa, r + m, ringw, j, CSW, RW4, RING);
                 rco_batch<H, true>(cs, pr, r, ringw, j, CSW, RW4, RING);
@@ -499,7 +494,9 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
             }
             r += steps;
             // (no barrier: the emission reads no ring slot, and its first
-            // barrier orders this slide before the next ring stores)
+            // barrier orders this slide before the next ring stores; the
+            // emission's hsc stores do not touch the prefixes that other
+            // threads' tasks of the previous row may still read)
         }
         fetch(gy + 1);
         // emission of centre row cy in chunks of K shift rows (sy): the chunk's
@@ -540,6 +537,16 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
             block_rows(rb + kn * H);
             __syncthreads();
             if (first) {
+                // the next row's image rows into the ring (their loads were
+                // issued before this emission)
+                if (steps > 0 && j < RW) {
+                    int slot = (r + m + 2 * R + 1) % RING;
+#pragma unroll
+                    for (int k = 0; k < H; ++k) {
+                        if (k < steps) ring_put(slot, j, iv[k]);
+                        slot = slot + 1 == RING ? 0 : slot + 1;
+                    }
+                }
                 // pivot statistics of this row's centres: window sums of the
                 // column sums of P and P^2 (exact, < 2^32)
                 if ((int)threadIdx.x < ngx) {
@@ -574,7 +581,7 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
                     const int ws = wsum[li];
                     const float iw = inv_sigma[li];
                     const unsigned X = xsum(pre + (row + t0_sxi) * RWp, t0_gxi);
-                    const long long num = mn * (long long)X - (long long)cS[t0_gxi] * (long long)ws;
+                    const long long num = mul_sub_wide(mn32, X, cS[t0_gxi], ws);
                     const float rho = (i64_to_f32(num) * iw) * cI[t0_gxi];
                     if (rco) rco[li] = rho;
                     if (rho < cut) ++local;
@@ -589,7 +596,7 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
                     const int ws = wsum[li];
                     const float iw = inv_sigma[li];
                     const unsigned X = xsum(pre + (row + sxi) * RWp, gxi);
-                    const long long num = mn * (long long)X - (long long)cS[gxi] * (long long)ws;
+                    const long long num = mul_sub_wide(mn32, X, cS[gxi], ws);
                     const float rho = (i64_to_f32(num) * iw) * cI[gxi];
                     if (rco) rco[li] = rho;
                     if (rho < cut) ++local;
@@ -598,8 +605,9 @@ rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int 
         }
     }
     if (count) {
-        for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
-        if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
+        unsigned long long tot = local;
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        if ((threadIdx.x & 31) == 0 && tot) atomicAdd(count, tot);
     }
 }
 
@@ -642,6 +650,7 @@ blur_corr_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, i
     const bool active = j < W;
     const int xc = x0 + j;
     const long long mn = (long long)m * n;
+    const unsigned mn32 = (unsigned)mn;      // < 2^17 (window sums of products fit 32 bits)
     const float fmn = i64_to_f32(mn);
     const int bq = (q + block - 1) / block;
     const int aj = bc_addr(j);
@@ -745,8 +754,8 @@ blur_corr_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, i
                 const unsigned X = r0[2 * kBcRS + a2] - (r0[2 * kBcRS + a1] & keep);
                 const int y = yr + k;
                 const int64_t i = (int64_t)y * Lx + x;
-                const long long dA = mn * (long long)Qp - (long long)Sp * Sp;   // exact
-                const long long num = mn * (long long)X - (long long)Sp * tws[k * kBcThreads + j];   // exact
+                const long long dA = mul_sub_wide(mn32, Qp, (int)Sp, (int)Sp);                  // exact
+                const long long num = mul_sub_wide(mn32, X, (int)Sp, tws[k * kBcThreads + j]);   // exact
                 const float iw = tiw[k * kBcThreads + j];                    // 0: flat I window
                 float r = 0.f;
                 if (dA > 0 && iw > 0.f) r = (i64_to_f32(num) * iw) * rsqrtf(i64_to_f32(dA) * fmn);
