@@ -417,16 +417,20 @@ def main():
     h2d = host_img.numel() * host_img.element_size() + sum(t.numel() * t.element_size() for t in host_ts)
     d2h = ctypes.sizeof(opta.OptaResult) * len(host_ts)
     e2e_times = []
+    e2e_calls = []          # host time in (prepare, search) per timed step, ms
     for it in range(1 + max(3, min(args.steps, 5))):
         flush.zero_()
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         hh = opta.optA_prepare(host_img, prm, sizes=sizes, stream=stream)
+        t1 = time.perf_counter()
         opta.optA_search(hh, host_ts, stream=stream)
         torch.cuda.synchronize()
+        t2 = time.perf_counter()
         if it > 0:
-            e2e_times.append(time.perf_counter() - t0)
+            e2e_times.append(t2 - t0)
+            e2e_calls.append([round(1000.0 * (t1 - t0), 2), round(1000.0 * (t2 - t1), 2)])
         hh.close()
     e2e_value = L_all / float(np.mean(e2e_times)) if world == 1 else L_step / float(np.mean(e2e_times)) * world
 
@@ -498,7 +502,8 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "steps": len(e2e_times),
                 "ms_per_step": 1000.0 * float(np.mean(e2e_times)),
-                "ms_min": 1000.0 * float(np.min(e2e_times))},
+                "samples_ms": [round(1000.0 * t, 2) for t in e2e_times],
+                "host_call_ms": e2e_calls},
         "gpu_launches": int(launches),
         "clocks": clocks,
         "roofline": roof,
