@@ -72,8 +72,8 @@ def dist_env():
 
 def workload(size: int, count: int):
     if size == 4096:
-        img = synth.config_image(4)
-        ts = synth.config_templates(4, img, count=count)
+        img = synth.workload_image("aerial4096_batch256")
+        ts = synth.workload_templates("aerial4096_batch256", img, count=count)
     else:
         img = synth.aerial_image(size, n_octaves=max(3, int(np.log2(size)) - 3),
                                  n_prims=max(4, 800 * size * size // 4096 ** 2), seed=2004)
@@ -222,7 +222,7 @@ def run_case(spec: str):
 
     kind, _, arg = spec.partition(":")
     v = float(arg) if kind == "blur" else int(arg)
-    img = synth.config_image(4)
+    img = synth.workload_image("aerial4096_batch256")
     p, q = img.shape
     I = torch.from_numpy(img).cuda()
     out = {}
@@ -554,7 +554,7 @@ def serving_report(opta, img, ts, full=False, n_req=400, workers=4, max_batch=64
                                              n_prims=800 * s * s // 4096 ** 2, seed=2004 + s)
                           for s in (8192, 12288, 16384)]
     else:
-        images = [img, synth.config_image(2)]
+        images = [img, synth.workload_image("aerial2048_32and64")]
     pools = [[t.data for t in ts]] + [
         [t.data for t in synth.make_templates(im, synth.batch_sizes(64, 3000 + k), seed=3000 + k,
                                               noise=3.0)]

@@ -28,7 +28,7 @@ import numpy as np
 
 __all__ = [
     "white_blur_image", "aerial_image", "make_templates", "Template",
-    "CONFIGS", "config_image", "config_templates", "BATCH_SIZES",
+    "WORKLOADS", "workload_image", "workload_templates", "BATCH_SIZES",
 ]
 
 # Square template sizes of the uneven-size batch (4096^2 image, 256 templates).
@@ -152,27 +152,27 @@ def make_templates(img: np.ndarray, sizes, seed: int, noise: float,
 
 
 # ---------------------------------------------------------------------------
-# The five workloads.  "image" recipes are (kind, kwargs); "templates" give the
-# template sizes, seed and noise.
+# The workloads, by image and template sizes.  "image" recipes are (kind,
+# kwargs); "templates" give the template sizes, seed and noise.
 # ---------------------------------------------------------------------------
-CONFIGS = {
-    1: dict(image=("white_blur", dict(size=256, seed=1001)),
+WORKLOADS = {
+    "white256_16": dict(image=("white_blur", dict(size=256, seed=1001)),
             templates=dict(sizes=[16], seed=1101, noise=5.0),
             group=3, blur=False),
-    2: dict(image=("aerial", dict(size=2048, n_octaves=8, n_prims=200, seed=2002)),
+    "aerial2048_32and64": dict(image=("aerial", dict(size=2048, n_octaves=8, n_prims=200, seed=2002)),
             templates=dict(sizes=[32] * 8 + [64] * 8, seed=2102, noise=3.0),
             group=0, blur=True),
-    3: dict(image=("aerial", dict(size=8192, n_octaves=12, n_prims=3200, seed=2003)),
+    "aerial8192_128": dict(image=("aerial", dict(size=8192, n_octaves=12, n_prims=3200, seed=2003)),
             templates=dict(sizes=[128] * 16, seed=2103, noise=3.0),
             group=0, blur=True),
-    4: dict(image=("aerial", dict(size=4096, n_octaves=9, n_prims=800, seed=2004)),
+    "aerial4096_batch256": dict(image=("aerial", dict(size=4096, n_octaves=9, n_prims=800, seed=2004)),
             templates=dict(sizes=None, seed=2104, noise=3.0, count=256),
             group=0, blur=True),
 }
 
 
-def config_image(k: int) -> np.ndarray:
-    kind, kw = CONFIGS[k]["image"]
+def workload_image(k: str) -> np.ndarray:
+    kind, kw = WORKLOADS[k]["image"]
     if kind == "white_blur":
         return white_blur_image(**kw)
     return aerial_image(**kw)
@@ -184,8 +184,8 @@ def batch_sizes(count: int, seed: int) -> list:
     return [int(BATCH_SIZES[i]) for i in rng.integers(0, len(BATCH_SIZES), size=count)]
 
 
-def config_templates(k: int, img: np.ndarray, count: int | None = None) -> list:
-    tc = CONFIGS[k]["templates"]
+def workload_templates(k: str, img: np.ndarray, count: int | None = None) -> list:
+    tc = WORKLOADS[k]["templates"]
     sizes = tc["sizes"]
     if sizes is None:
         sizes = batch_sizes(tc["count"], tc["seed"])

@@ -60,8 +60,8 @@ def _run(opta, img, ts):
 
 
 def test_batched_4096_one_template_per_size(opta):
-    img = synth.config_image(4)
-    ts = synth.config_templates(4, img)
+    img = synth.workload_image("aerial4096_batch256")
+    ts = synth.workload_templates("aerial4096_batch256", img)
     seen, pick = set(), []
     for t in ts:
         if t.data.shape not in seen:
@@ -72,14 +72,14 @@ def test_batched_4096_one_template_per_size(opta):
 
 
 def test_aerial_2048_sixteen_templates(opta):
-    img = synth.config_image(2)
-    ts = synth.config_templates(2, img)
+    img = synth.workload_image("aerial2048_32and64")
+    ts = synth.workload_templates("aerial2048_32and64", img)
     res, zres = _run(opta, img, ts)
     _check_full(opta, img, ts, None, res, zres, seed=2)
 
 
 def test_precision_8192_four_templates(opta):
-    img = synth.config_image(3)
-    ts = synth.config_templates(3, img, count=4)
+    img = synth.workload_image("aerial8192_128")
+    ts = synth.workload_templates("aerial8192_128", img, count=4)
     res, zres = _run(opta, img, ts)
     _check_full(opta, img, ts, None, res, zres, seed=3)
