@@ -951,13 +951,37 @@ __device__ inline void warp_rho32(const uint8_t *__restrict__ I, int q, int Lx,
                 cp_async_wait<0>();
             }
             __syncwarp();
-            for (int r = 0; r < rows; ++r) {
-                const uint8_t *row = I + (int64_t)(y + u0 + r) * q + x;
-                const uint8_t *sb = buf + r * WB + (int)(reinterpret_cast<uintptr_t>(row) & 15);
-                const float *tr = tm + (u0 + r) * npad;
+            // four columns per lane and step (one funnel-shifted word of the
+            // staged row, four byte_perm conversions, a 16-byte template
+            // read); with n / 4 <= 16 the half-warps take two rows at once
+            const int n4 = n >> 2;
+            const int rpp = n4 <= 16 ? 2 : 1;               // rows per pass
+            const int lr = rpp == 2 ? lane >> 4 : 0;        // this lane's row in the pass
+            const int lg = rpp == 2 ? lane & 15 : lane;     // its first column group
+            const int gstep = rpp == 2 ? 16 : 32;
+            for (int r0 = 0; r0 < rows; r0 += rpp) {
+                const int r = r0 + lr;
                 float racc = 0.f;
-                for (int v = lane; v < n; v += 32) racc = fmaf(tr[v], u8f(sb[v]) - ca, racc);
-                if (r & 1) acc1 += racc; else acc0 += racc;
+                if (r < rows) {
+                    const uint8_t *row = I + (int64_t)(y + u0 + r) * q + x;
+                    const int off = (int)(reinterpret_cast<uintptr_t>(row) & 15);
+                    const uint8_t *sb = buf + r * WB;
+                    const unsigned *sw = reinterpret_cast<const unsigned *>(sb);
+                    const float *tr = tm + (u0 + r) * npad;
+                    for (int g = lg; g < n4; g += gstep) {
+                        const int b0 = off + 4 * g;
+                        const unsigned w =
+                            __funnelshift_r(sw[b0 >> 2], sw[(b0 >> 2) + 1], 8u * (unsigned)(b0 & 3));
+                        const float4 tv = *reinterpret_cast<const float4 *>(tr + 4 * g);
+                        racc = fmaf(tv.x, __uint_as_float(__byte_perm(w, 0x4b000000u, 0x7440)) - ca, racc);
+                        racc = fmaf(tv.y, __uint_as_float(__byte_perm(w, 0x4b000000u, 0x7441)) - ca, racc);
+                        racc = fmaf(tv.z, __uint_as_float(__byte_perm(w, 0x4b000000u, 0x7442)) - ca, racc);
+                        racc = fmaf(tv.w, __uint_as_float(__byte_perm(w, 0x4b000000u, 0x7443)) - ca, racc);
+                    }
+                    for (int v = 4 * n4 + lg; v < n; v += gstep)
+                        racc = fmaf(tr[v], u8f(sb[off + v]) - ca, racc);
+                }
+                if (r0 & 2) acc1 += racc; else acc0 += racc;
             }
             __syncwarp();   // the buffer is refilled two chunks later
         }
@@ -983,9 +1007,12 @@ __device__ inline void warp_rho32(const uint8_t *__restrict__ I, int q, int Lx,
     rho = 0.f;
     eps = 0.f;
     if (lane == 0) {
-        // accumulation depth per lane: ceil(n/32) per row, then at most m row
-        // partial sums into one chain, the chain merges and 5 shuffle levels
-        const int kacc = ((n + 31) / 32) + m + 8;
+        // accumulation depth per lane: per row ceil(n/32) (one column per
+        // lane and step) or 4 ceil(n/4 / 16) + 1 (four columns per lane and
+        // step, a half-warp per row when n/4 <= 16, then the tail column),
+        // then at most m row partial sums into one chain, the chain merges
+        // and 5 shuffle levels
+        const int kacc = max((n + 31) / 32, 4 * ((n / 4 + 15) / 16) + 1) + m + 8;
         rho = (acc * ist) * is;
         if (is > 0.f) {
             // ||I - a||^2 = Omega^2 + (S - a mn)^2 / mn, so ||I - a|| / Omega =
@@ -1491,7 +1518,8 @@ cudaError_t launch_survivors(const Scan2Batch &B, const uint8_t *I, int pimg, in
     // rows are narrow enough
     const int WB = 16 * ((n + 30) / 16);
     const int stage = in_smem && n <= 256 ? 1 : 0;
-    if (stage) smem += (size_t)8 * 2 * kStageRows * WB;
+    // (+16: a staged row's last word pair may reach 3 bytes past its row)
+    if (stage) smem += (size_t)8 * 2 * kStageRows * WB + 16;
     static size_t attr = 0;
     {
         const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(survivors_kernel), smem, &attr);
