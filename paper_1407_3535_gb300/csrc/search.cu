@@ -1174,17 +1174,32 @@ survivors_lane_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, 
                 const float *tr = tm + u * npad;
                 uint32_t w0 = wr[0];
                 float racc = 0.f;
-                for (int v = 0; v < n; v += 4) {
-                    // the next word, unless it starts past the image
-                    const uint32_t *nx = wr + (v >> 2) + 1;
-                    const uint32_t w1 = reinterpret_cast<uintptr_t>(nx) < iend ? *nx : 0u;
-                    const uint32_t wv = __funnelshift_r(w0, w1, sh);
-                    w0 = w1;
+                if ((n & 3) == 0 && reinterpret_cast<uintptr_t>(wr + (n >> 2) + 1) <= iend) {
+                    // whole words of the row inside the image: four template
+                    // values per 16-byte read (the same for every lane)
+                    for (int v = 0; v < n; v += 4) {
+                        const uint32_t w1 = wr[(v >> 2) + 1];
+                        const uint32_t wv = __funnelshift_r(w0, w1, sh);
+                        w0 = w1;
+                        const float4 tv = *reinterpret_cast<const float4 *>(tr + v);
+                        racc = fmaf(tv.x, __uint_as_float(__byte_perm(wv, 0x4B000000u, 0x7650)) - ca, racc);
+                        racc = fmaf(tv.y, __uint_as_float(__byte_perm(wv, 0x4B000000u, 0x7651)) - ca, racc);
+                        racc = fmaf(tv.z, __uint_as_float(__byte_perm(wv, 0x4B000000u, 0x7652)) - ca, racc);
+                        racc = fmaf(tv.w, __uint_as_float(__byte_perm(wv, 0x4B000000u, 0x7653)) - ca, racc);
+                    }
+                } else {
+                    for (int v = 0; v < n; v += 4) {
+                        // the next word, unless it starts past the image
+                        const uint32_t *nx = wr + (v >> 2) + 1;
+                        const uint32_t w1 = reinterpret_cast<uintptr_t>(nx) < iend ? *nx : 0u;
+                        const uint32_t wv = __funnelshift_r(w0, w1, sh);
+                        w0 = w1;
 #pragma unroll
-                    for (int b = 0; b < 4; ++b)
-                        if (v + b < n)
-                            racc = fmaf(tr[v + b],
-                                        __uint_as_float(__byte_perm(wv, 0x4B000000u, 0x7650 + b)) - ca, racc);
+                        for (int b = 0; b < 4; ++b)
+                            if (v + b < n)
+                                racc = fmaf(tr[v + b],
+                                            __uint_as_float(__byte_perm(wv, 0x4B000000u, 0x7650 + b)) - ca, racc);
+                    }
                 }
                 tot += racc;
             }
