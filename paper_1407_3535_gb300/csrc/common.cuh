@@ -104,7 +104,12 @@ __host__ __device__ inline float scan1_epsA_fp32(int k) { return (float)(k + 2) 
 constexpr float kScan1EpsB = 8.f * kU32;
 // roundings per term of the FP32 scan-1 kernels (centre tiles, one column)
 __host__ __device__ inline int centre_rho_kacc(int m, int npad) { return 64 + m * ((npad + 63) / 64) + 1; }
-__host__ __device__ inline int centre_column_kacc(int m, int n) { return m * ((n + 31) / 32) + 6; }
+// (the column kernel: a lane's chain over its rows, four columns per step,
+// two rows per pass when n / 4 <= 16, then the tail column)
+__host__ __device__ inline int centre_column_kacc(int m, int n) {
+    const int rpp = n / 4 <= 16 ? 2 : 1, gstep = rpp == 2 ? 16 : 32;
+    return ((m + rpp - 1) / rpp) * (4 * ((n / 4 + gstep - 1) / gstep) + 1) + 6;
+}
 
 // Angle interval certain to contain acos of a centre's exact rho(t, pivot)
 // (the largest bound over the kernels that compute centres of the size).

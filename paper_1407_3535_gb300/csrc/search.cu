@@ -470,10 +470,29 @@ centre_column_kernel(const uint8_t *__restrict__ P, int q, const float *__restri
         const int cy = group_centre_of(gy, Ly, h);
         const float *tm = tf + (size_t)k * tsz;
         const uint8_t *bp = P + (int64_t)cy * q + cx;
+        // four columns per lane and step (a 16-byte template read, byte
+        // loads turned into b - 128 exactly by the 2^23 magic); half-warps
+        // take two rows at once when n / 4 <= 16 (centre_column_kacc)
+        const int n4 = n >> 2;
+        const int rpp = n4 <= 16 ? 2 : 1;
+        const int lr = rpp == 2 ? lane >> 4 : 0, lg = rpp == 2 ? lane & 15 : lane;
+        const int gstep = rpp == 2 ? 16 : 32;
+        constexpr float kC = 8388608.f + 128.f;
         float acc = 0.f;
-        for (int u = 0; u < m; ++u)
-            for (int v = lane; v < n; v += 32)
-                acc = fmaf(tm[u * npad + v], (float)bp[(int64_t)u * q + v] - 128.f, acc);
+        for (int u = lr; u < m; u += rpp) {
+            const uint8_t *br = bp + (int64_t)u * q;
+            const float *tr = tm + u * npad;
+            for (int g = lg; g < n4; g += gstep) {
+                const float4 tv = *reinterpret_cast<const float4 *>(tr + 4 * g);
+                const uint8_t *b4 = br + 4 * g;
+                acc = fmaf(tv.x, __uint_as_float(0x4B000000u | b4[0]) - kC, acc);
+                acc = fmaf(tv.y, __uint_as_float(0x4B000000u | b4[1]) - kC, acc);
+                acc = fmaf(tv.z, __uint_as_float(0x4B000000u | b4[2]) - kC, acc);
+                acc = fmaf(tv.w, __uint_as_float(0x4B000000u | b4[3]) - kC, acc);
+            }
+            for (int v = 4 * n4 + lg; v < n; v += gstep)
+                acc = fmaf(tr[v], __uint_as_float(0x4B000000u | br[v]) - kC, acc);
+        }
         acc = warp_sum_f(acc);
         if (lane == 0) {
             const int64_t g = (int64_t)gy * Gx + gx;
