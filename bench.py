@@ -470,7 +470,7 @@ def main():
                  "speedup_of_opta_search": (L_step / (search_ms / 1000.0)) / brute_rate,
                  "speedup_of_opta_step": value / brute_rate if world == 1 else None}
 
-    roof = roofline(prof, prep_by_size, ts, res_prof, img.shape)
+    roof = roofline(prof, prep_by_size, ts, res_prof, img.shape, prm.egs_sample)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -712,7 +712,22 @@ IMAGE_LEVEL_KERNELS = ("ingest_u8_kernel", "ii_rows_kernel", "ii_cols_kernel")
 TRAFFIC_RATIO = {"rho_co_kernel": 200.6 / 212.0, "blur_corr_kernel": 185.6 / 164.0}
 
 
-def prep_roofline(name, prep_by_size, shape, pk, src):
+def egs_sample_rows(Ly, h, m, sample):
+    """Location rows EGS counts for group side h (runs of 8 group rows,
+    every sample-th run; all rows when sample <= 1) and the image rows
+    their windows cover."""
+    if sample <= 1:
+        return Ly, Ly + m - 1
+    G = (Ly + h - 1) // h
+    rows = img_rows = 0
+    for g0 in range(0, G, 8 * sample):
+        r0, r1 = g0 * h, min((g0 + 8) * h, Ly)
+        rows += r1 - r0
+        img_rows += r1 - r0 + m - 1
+    return rows, img_rows
+
+
+def prep_roofline(name, prep_by_size, shape, pk, src, egs_sample=4):
     """Algorithmic bytes of the preparation kernel `name` over the launches
     of every size (one size at a time, so the launches do not overlap),
     divided by their device time.  `rho_co_kernel` gathers the launches of
@@ -724,7 +739,14 @@ def prep_roofline(name, prep_by_size, shape, pk, src):
         Ly, Lx = p - m + 1, q - n + 1
         L = Ly * Lx
         for k, (ms_, cnt) in prof.items():
-            if name == "rho_co_kernel" and k.startswith("rho_co_kernel<"):
+            if name == "rho_co_count" and k.startswith("rho_co_count<"):
+                # EGS's count-only trials over its sample of group rows: the
+                # image rows the sampled windows cover (P and I), and window
+                # sums and 1/sigma of the sampled locations; nothing written
+                H = int(k[len("rho_co_count<"):-1])
+                rows, img_rows = egs_sample_rows(Ly, H, m, egs_sample)
+                b = 2.0 * q * img_rows + 8.0 * rows * Lx
+            elif name == "rho_co_kernel" and k.startswith("rho_co_kernel<"):
                 H = int(k[len("rho_co_kernel<"):-1])
                 G = ((Ly + H - 1) // H) * ((Lx + H - 1) // H)
                 # P and I read once; window sums and 1/sigma per location
@@ -752,7 +774,7 @@ def prep_roofline(name, prep_by_size, shape, pk, src):
             "peak_source": f"HBM copy bandwidth ({src})"}
 
 
-def roofline(prof, prep_by_size, ts, results, shape):
+def roofline(prof, prep_by_size, ts, results, shape, egs_sample=4):
     """Roofline of the kernel with the largest device time in a step (the
     search pass, plus the preparation timed one size at a time), the other
     main kernels under `others`."""
@@ -765,8 +787,8 @@ def roofline(prof, prep_by_size, ts, results, shape):
         if r is not None:
             r["total_ms"] = tot_ms
             rows.append(r)
-    for name in ("rho_co_kernel", "blur_corr_kernel"):
-        r = prep_roofline(name, prep_by_size, shape, pk, src)
+    for name in ("rho_co_kernel", "rho_co_count", "blur_corr_kernel"):
+        r = prep_roofline(name, prep_by_size, shape, pk, src, egs_sample)
         if r is not None:
             rows.append(r)
     if not rows:

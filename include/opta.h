@@ -122,7 +122,14 @@ typedef struct opta_params {
                                with I in FP64 over the (2d+1) x (2d+1) neighbourhood of that
                                location, d = ceil(3 sigma_max) of the accepted blur map.
                                Fast but not exact: the result may miss the maximum on I. */
-    int32_t reserved[6];
+    int32_t egs_sample;     /* 4: Algorithm 2's retained count n_r is taken over a systematic
+                               sample of the location grid -- the group rows g with
+                               (g / 8) % egs_sample == 0, in runs of 8 group rows -- and
+                               scaled to the grid; 0 or 1 counts every location as
+                               Algorithm 2 does.  EGS's trials count only, and the
+                               accepted configuration's map is computed once.  Speed
+                               only: the search's answer does not depend on it.  <= 64. */
+    int32_t reserved[5];
 } opta_params;
 
 typedef struct opta_handle opta_handle;
@@ -251,10 +258,11 @@ opta_status zncc_full(const opta_image *img, const opta_template *t,
  * with p*q <= 262144 pixels, and m * round_up(n, 8) <= 4096 template
  * elements; larger problems return OPTA_ERR_TOO_LARGE before touching the
  * GPU.  The first call on each device looks up the array's device address
- * (on that device, which must be current); make that first call before any
- * stream capture.  All calls share the array: calls that overlap on the GPU
- * (e.g. from two streams or threads) race and must be serialised by the
- * caller.  Calls no cudaMalloc/cudaFree.  Synchronises `stream`.
+ * (on that device, which must be current).  Never call it while `stream`
+ * is being captured into a graph: every call reads its result back into
+ * host memory and synchronises `stream`.  All calls share the array: calls
+ * that overlap on the GPU (e.g. from two streams or threads) race and must
+ * be serialised by the caller.  Calls no cudaMalloc/cudaFree.
  */
 opta_status zncc_full_noalloc(const opta_image *img, const opta_template *t,
                               float *rho_map, opta_result *best, void *stream);

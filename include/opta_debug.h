@@ -73,6 +73,16 @@ opta_status optA_debug_scan1(opta_handle *h, const opta_template *t, int32_t n_t
  * the nearest float (ties to even) for |v| < 2^46, within 1 ulp beyond. */
 opta_status opta_dbg_i64_to_f32(const int64_t *v_dev, float *out_dev, int64_t n, void *stream);
 
+/* Failure detection of the tensor-core scan 1 (its mbarrier waits are
+ * bounded).  Later scan-1 launches give up any wait for progress after
+ * `wait_ns` nanoseconds (0 restores the default of 2 s); with `stall` = 1
+ * the thread that issues the MMAs first waits on a barrier that no thread
+ * ever arrives at, so every launch runs out of its budget.  A launch that
+ * gives up still waits (up to 2 s) for its own copies and MMAs in flight,
+ * releases its tensor memory and returns; the search then reports
+ * OPTA_ERR_TIMEOUT and the handle stays usable.  Process-wide; for tests. */
+void opta_dbg_scan1_wait(uint64_t wait_ns, int32_t stall);
+
 /* Number of kernel launches the library has issued in this process. */
 uint64_t opta_dbg_launch_count(void);
 

@@ -115,6 +115,74 @@ def zncc_map(img: np.ndarray, t: np.ndarray, threads: int = 0) -> np.ndarray:
     return out
 
 
+def zncc_map_fft(img: np.ndarray, t: np.ndarray, workers: int = -1) -> np.ndarray:
+    """Eq. rho1 at every location, for images too large for the direct loop.
+
+    The numerator sum_{u,v} t'(u,v) I(y+u, x+v), with t' = t - mu_t (its sum
+    is zero, so the window mean of I drops out), is one cross-correlation,
+    taken here with a library FFT in FP64 over the whole image (no location
+    reaches past the image, so the transform's wrap-around never enters).
+    The window sums S and Q of I come from integral images; for integer
+    images they are exact int64, so sigma_o^2 = (mn Q - S^2) / mn is exact up
+    to its final rounding and a flat window is recognised exactly (rho := 0).
+    The FFT's rounding error is of order 1e-16 log2(pq) ||t'|| ||I - 128||,
+    far below the 1e-6 that the tests resolve."""
+    return next(zncc_maps_fft(img, [t], workers))
+
+
+def zncc_maps_fft(img: np.ndarray, templates, workers: int = -1):
+    """``zncc_map_fft`` for several templates of one image, yielding one map
+    per template in order (the image's transform and integral images are
+    taken once)."""
+    from scipy import fft as sfft
+    I = np.asarray(img, dtype=np.float64)
+    p, q = I.shape
+    F_I = sfft.rfft2(I - 128.0, workers=workers)
+    exact = bool(np.all(I == np.rint(I)) and np.abs(I).max() < 2 ** 20)
+    if exact:
+        Ii = I.astype(np.int64)
+        iis = np.zeros((p + 1, q + 1), dtype=np.int64)
+        iiq = np.zeros((p + 1, q + 1), dtype=np.int64)
+        iis[1:, 1:] = Ii.cumsum(0).cumsum(1)
+        iiq[1:, 1:] = (Ii * Ii).cumsum(0).cumsum(1)
+        del Ii
+    else:
+        iis = np.zeros((p + 1, q + 1)); iiq = np.zeros((p + 1, q + 1))
+        iis[1:, 1:] = I.cumsum(0).cumsum(1)
+        iiq[1:, 1:] = (I * I).cumsum(0).cumsum(1)
+    var_of = {}
+    for t in templates:
+        T = np.asarray(t, dtype=np.float64)
+        m, n = T.shape
+        if m > p or n > q:
+            raise ValueError("template larger than image")
+        Ly, Lx = p - m + 1, q - n + 1
+        mn = m * n
+        if (m, n) not in var_of:
+            S = iis[m:, n:] - iis[:Ly, n:] - iis[m:, :Lx] + iis[:Ly, :Lx]
+            Q = iiq[m:, n:] - iiq[:Ly, n:] - iiq[m:, :Lx] + iiq[:Ly, :Lx]
+            if exact:
+                var = (mn * Q - S * S).astype(np.float64) / mn
+            else:
+                var = np.maximum(Q - S * S / mn, 0.0)
+            var_of = {(m, n): var}          # one size at a time is kept
+        var = var_of[(m, n)]
+        tz = T - T.mean()
+        st = math.sqrt(float((tz * tz).sum()))
+        out = np.zeros((Ly, Lx))
+        if st > 0.0:
+            pad = np.zeros((p, q))
+            pad[:m, :n] = tz
+            F = np.conj(sfft.rfft2(pad, workers=workers))
+            del pad
+            F *= F_I
+            num = sfft.irfft2(F, s=(p, q), workers=workers)[:Ly, :Lx]
+            del F
+            ok = var > 0
+            out[ok] = num[ok] / (st * np.sqrt(var[ok]))
+        yield out
+
+
 def rho_at(img: np.ndarray, t: np.ndarray, ys, xs, threads: int = 0) -> np.ndarray:
     """Eq. rho1 at the listed locations (C, FP64)."""
     I, Ip = _d(img); T, Tp = _d(t)
@@ -248,23 +316,43 @@ def flat_windows(img: np.ndarray, m: int, n: int) -> np.ndarray:
 # ---------------------------------------------------------------------------
 # Section 3: EGS (Algorithm 2)
 # ---------------------------------------------------------------------------
-def egs_cost(rco: np.ndarray, h: int, rho_th: float) -> int:
+EGS_RUN = 8   # group rows per run of EGS's systematic sample
+
+
+def egs_sample_rows(Ly: int, h: int, sample: int = 1) -> np.ndarray:
+    """Boolean mask of the location rows EGS counts for group side h: the
+    rows of the group rows g with (g // EGS_RUN) % sample == 0 (every row
+    when sample <= 1).  Reading: Algorithm 2's n_r only steers the choice of
+    h and blur level, so it may be estimated from a systematic sample of the
+    location grid; sample = 1 is the count as printed."""
+    g = np.arange(Ly) // h
+    if sample <= 1:
+        return np.ones(Ly, dtype=bool)
+    return (g // EGS_RUN) % sample == 0
+
+
+def egs_cost(rco: np.ndarray, h: int, rho_th: float, sample: int = 1) -> int:
     """Total estimated cost in units of one rho evaluation (Section 3.3, Eq. objfunc):
     number of groups (centre evaluations) + retained count n_r (Eq. co, strict `<`
-    as in Algorithm 2)."""
+    as in Algorithm 2).  With sample > 1, n_r is counted over the sampled rows and
+    scaled by Ly / (rows sampled), rounded to the nearest integer (halves up)."""
     Ly, Lx = rco.shape
-    return n_groups(Ly, Lx, h) + int(np.count_nonzero(rco < egs_rho_cut(rho_th)))
+    rows = egs_sample_rows(Ly, h, sample)
+    cnt = int(np.count_nonzero(rco[rows] < egs_rho_cut(rho_th)))
+    ns = int(rows.sum())
+    n_r = (cnt * Ly + ns // 2) // ns
+    return n_groups(Ly, Lx, h) + n_r
 
 
-def egs(P, I, m, n, h_start, rho_th, xi, h_max=9, threads=0, log=None):
+def egs(P, I, m, n, h_start, rho_th, xi, h_max=9, threads=0, log=None, sample=1):
     """Algorithm 2: grow the square group size by 2 while the cost falls by more
     than the fraction xi of the previous cost; returns (h_e, cost_e)."""
     h = h_start
-    c_prev = egs_cost(rho_co_map(P, I, m, n, h, threads), h, rho_th)
+    c_prev = egs_cost(rho_co_map(P, I, m, n, h, threads), h, rho_th, sample)
     if log is not None:
         log.append((h, c_prev))
     while h + 2 <= h_max:
-        c_new = egs_cost(rho_co_map(P, I, m, n, h + 2, threads), h + 2, rho_th)
+        c_new = egs_cost(rho_co_map(P, I, m, n, h + 2, threads), h + 2, rho_th, sample)
         if log is not None:
             log.append((h + 2, c_new))
         if c_prev - c_new > xi * c_prev:
@@ -281,14 +369,17 @@ DEFAULT_LEVELS = (0.5, 1.0, 2.0, 3.0)
 
 
 def opta(I, m, n, rho_th=0.8, rho_max=0.95, xi=0.005, block=64,
-         levels=DEFAULT_LEVELS, h_max=9, threads=0, literal=False):
+         levels=DEFAULT_LEVELS, h_max=9, threads=0, literal=False, sample=1):
     """Algorithm 3 under the reading: level k raises every still-active block to
     sigma_k; a block whose windows (by top-left, non-flat I windows only) reach
     a blur-correlation below lambda (Eq. misDec) reverts to its previous sigma
     and is frozen; the level is kept if EGS's cost falls by more than xi.
-    With literal=True, EGS measures rho(P, P) (see ``opta_literal``).
+    With literal=True, EGS measures rho(P, P) (see ``opta_literal``); sample
+    is EGS's count sample (``egs_sample_rows``).
 
-    Returns dict(sigma_map, pivot (uint8), h, cost, trace)."""
+    Returns dict(sigma_map, pivot (uint8), h, cost, trace).  Each trace entry
+    after level 0 also holds the blocks that failed the lambda test at that
+    level (``fail``) and the frozen blocks after it (``frozen_map``)."""
     I = np.asarray(I, dtype=np.float64)
     p, q = I.shape
     bp, bq = (p + block - 1) // block, (q + block - 1) // block
@@ -296,7 +387,7 @@ def opta(I, m, n, rho_th=0.8, rho_max=0.95, xi=0.005, block=64,
     sig = np.zeros((bp, bq))
     frozen = np.zeros((bp, bq), dtype=bool)
     P = quantise_pivot(I)
-    h, cost = egs(P, P if literal else I, m, n, 1, rho_th, xi, h_max, threads)
+    h, cost = egs(P, P if literal else I, m, n, 1, rho_th, xi, h_max, threads, sample=sample)
     trace = [dict(level=0, sigma=0.0, h=h, cost=cost, frozen=0)]
     flat = flat_windows(I, m, n)
     Ly, Lx = p - m + 1, q - n + 1
@@ -316,8 +407,9 @@ def opta(I, m, n, rho_th=0.8, rho_max=0.95, xi=0.005, block=64,
         new_frozen = frozen | fail
         if fail.any():
             Pk = quantise_pivot(blur(I, new_sig, block, threads))
-        hk, ck = egs(Pk, Pk if literal else I, m, n, h, rho_th, xi, h_max, threads)
-        trace.append(dict(level=k, sigma=s, h=hk, cost=ck, frozen=int(new_frozen.sum())))
+        hk, ck = egs(Pk, Pk if literal else I, m, n, h, rho_th, xi, h_max, threads, sample=sample)
+        trace.append(dict(level=k, sigma=s, h=hk, cost=ck, frozen=int(new_frozen.sum()),
+                          fail=fail.copy(), frozen_map=new_frozen.copy()))
         if cost - ck > xi * cost:
             sig, frozen, P, h, cost = new_sig, new_frozen, Pk, hk, ck
         else:

@@ -19,7 +19,7 @@ __all__ = [
     "zncc_full_noalloc",
     "optA_debug_bounds", "optA_size_info", "optA_memory_bytes", "optA_destroy",
     "optA_debug_maps", "opta_dbg_window_stats", "opta_dbg_blur", "opta_dbg_blur_corr", "opta_dbg_i64_to_f32",
-    "opta_dbg_rho_co", "opta_dbg_launch_count", "opta_dbg_profile_enable",
+    "opta_dbg_rho_co", "opta_dbg_launch_count", "opta_dbg_profile_enable", "opta_dbg_scan1_wait",
     "opta_dbg_profile_read", "optA_debug_scan1", "Handle", "lib", "OptaResult", "SearchContext", "SearchGraph", "Server",
 ]
 
@@ -458,6 +458,12 @@ def opta_dbg_rho_co(P_dev, I_dev, m: int, n: int, h: int, rco_dev=None, rho_cut:
                                  m, n, h, c_void_p(rco_dev.data_ptr() if rco_dev is not None else 0),
                                  c_double(rho_cut), byref(cnt), _stream(stream)), "opta_dbg_rho_co")
     return int(cnt.value)
+
+
+def opta_dbg_scan1_wait(wait_ns: int = 0, stall: bool = False) -> None:
+    """Budget of scan 1's waits for progress (0: the default) and its stall
+    switch (include/opta_debug.h); for the failure-detection test."""
+    lib().opta_dbg_scan1_wait(int(wait_ns), 1 if stall else 0)
 
 
 def opta_dbg_launch_count() -> int:

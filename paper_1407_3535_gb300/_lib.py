@@ -46,7 +46,8 @@ class OptaParams(ctypes.Structure):
     _fields_ = [("rho_th", c_double), ("rho_max", c_double), ("xi", c_double),
                 ("block", c_int32), ("n_levels", c_int32), ("sigma_levels", c_float * 8),
                 ("h_max", c_int32), ("fixed_h", c_int32), ("blur", c_int32), ("topk", c_int32),
-                ("precision", c_int32), ("literal", c_int32), ("reserved", c_int32 * 6)]
+                ("precision", c_int32), ("literal", c_int32), ("egs_sample", c_int32),
+                ("reserved", c_int32 * 5)]
 
 
 class OptaServerConfig(ctypes.Structure):
@@ -122,6 +123,7 @@ SIGNATURES = {
                                    c_void_p]),
     "opta_dbg_i64_to_f32": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p]),
     "opta_dbg_launch_count": (ctypes.c_uint64, []),
+    "opta_dbg_scan1_wait": (None, [ctypes.c_uint64, c_int32]),
     "opta_dbg_profile_enable": (None, [c_int32]),
     "opta_dbg_profile_read": (c_int32, [ctypes.c_char_p, c_int32, POINTER(c_double),
                                         POINTER(c_int64), c_int32]),

@@ -159,6 +159,7 @@ bool valid_params(const opta_params &p) {
     if (p.topk < 1 || p.topk > kTopkMax) return false;
     if (p.precision != 0 && p.precision != 1) return false;
     if (p.literal != 0 && p.literal != 1) return false;
+    if (p.egs_sample < 0 || p.egs_sample > 64) return false;
     return true;
 }
 
@@ -244,16 +245,6 @@ struct PrepScratch {
     float *invP = nullptr;
 };
 
-// Outputs of one EGS evaluation (h >= 3): the auto-correlation map and the
-// per-centre pivot statistics, kept so that the configuration finally
-// accepted need not be evaluated again.  Three slots: the accepted
-// configuration's, the best of the current EGS run and its next candidate.
-struct EvalSlot {
-    float *rco = nullptr, *cinv = nullptr, *cefac = nullptr;
-    int h = 0;        // group side evaluated into the slot (0: none)
-};
-constexpr int kEvalSlots = 3;
-
 // Members of the auto-correlation EGS measures: image M (I, or the candidate
 // pivot itself in the literal mode) with its window sums and 1/Omega.
 struct Members {
@@ -262,37 +253,53 @@ struct Members {
     const float *inv;
 };
 
-// Queue the retained count of group side h (Algorithm 2's n_r) into dcount.
+// Location rows EGS counts for group side h: the rows of the group rows g
+// with (g / kEgsRun) % sample == 0 (every row when sample == 1).
+int64_t egs_rows(int Ly, int h, int sample) {
+    if (sample <= 1) return Ly;
+    const int Gy = groups_along(Ly, h);
+    int64_t rows = 0;
+    for (int g0 = 0; g0 < Gy; g0 += kEgsRun * sample) {
+        const int g1 = std::min(Gy, g0 + kEgsRun);
+        rows += std::min<int64_t>((int64_t)g1 * h, Ly) - (int64_t)g0 * h;
+    }
+    return rows;
+}
+
+// Queue the retained count of group side h (Algorithm 2's n_r) over EGS's
+// sample of the location grid into dcount.  Counts only: no map is stored.
 opta_status egs_launch(opta_handle *H, SizeState *S, const uint8_t *P, const Members &M, int h,
-                       unsigned long long *dcount, cudaStream_t s, EvalSlot *out) {
-    if (out) out->h = 0;
+                       unsigned long long *dcount, cudaStream_t s) {
     const float cut = (float)std::sqrt(1.0 - H->prm.rho_th * H->prm.rho_th);
+    const int sample = std::max(1, H->prm.egs_sample);
     CK(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), s));
     if (h == 1 && P == M.M) {
         // pivots equal to the members, one location per group: every member
         // is its own centre, rho_co = 1 except on flat windows (rho_co = 0
         // there), so the retained count is the number of flat windows
-        CK(launch_count_zero(M.inv, (int64_t)S->Ly * S->Lx, dcount, s));
+        CK(launch_count_zero(M.inv, S->Ly, S->Lx, 1, sample, dcount, s));
     } else {
-        // the slots hold the centre statistics of h >= 3 (at most a ninth of L)
-        const bool keep = out && out->rco && h >= 3;
-        CK(launch_rho_co(P, M.M, H->p, H->q, S->m, S->n, h, M.wsum, M.inv, cut,
-                         keep ? out->rco : nullptr, dcount, keep ? out->cinv : nullptr,
-                         keep ? out->cefac : nullptr, s));
-        if (keep) out->h = h;
+        CK(launch_rho_co(P, M.M, H->p, H->q, S->m, S->n, h, M.wsum, M.inv, cut, nullptr, dcount,
+                         nullptr, nullptr, s, sample));
     }
     S->n_evals++;
     return OPTA_OK;
 }
 
 // Wait for k queued counts (group sides hs[]) and turn them into costs
-// (groups + retained, Eq. objfunc).
-opta_status egs_read(SizeState *S, const int *hs, int k, const unsigned long long *dcount,
-                     unsigned long long *host, long long *cost, cudaStream_t s) {
+// (groups + retained, Eq. objfunc); a sampled count is scaled to the whole
+// grid by Ly / (rows sampled), rounded to the nearest integer.
+opta_status egs_read(opta_handle *H, SizeState *S, const int *hs, int k,
+                     const unsigned long long *dcount, unsigned long long *host, long long *cost,
+                     cudaStream_t s) {
     CK(cudaMemcpyAsync(host, dcount, (size_t)k * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    for (int i = 0; i < k; ++i)
-        cost[i] = (long long)groups_along(S->Ly, hs[i]) * groups_along(S->Lx, hs[i]) + (long long)host[i];
+    const int sample = std::max(1, H->prm.egs_sample);
+    for (int i = 0; i < k; ++i) {
+        const int64_t rows = egs_rows(S->Ly, hs[i], sample);
+        const long long nr = ((long long)host[i] * S->Ly + rows / 2) / rows;
+        cost[i] = (long long)groups_along(S->Ly, hs[i]) * groups_along(S->Lx, hs[i]) + nr;
+    }
     return OPTA_OK;
 }
 
@@ -305,47 +312,34 @@ int h_limit(int p, int q, int m, int n, int hmax) {
 }
 
 // Algorithm 2: grow h by 2 while the cost drops by more than xi of the last.
-// With slots (nullable): evaluations go to slots other than `avoid`, and
-// *best_slot receives the slot holding the chosen h's outputs (-1: none).
 // dcount: two device counters.  The first two sides (h and h + 2, both
 // always evaluated when h + 2 is allowed) are queued together and read with
 // one wait; each further side takes one more.
 opta_status egs(opta_handle *H, SizeState *S, const uint8_t *P, const Members &M, int h_start,
-                unsigned long long *dcount, int *h_out, long long *c_out, cudaStream_t s,
-                EvalSlot *slots = nullptr, int avoid = -1, int *best_slot = nullptr) {
+                unsigned long long *dcount, int *h_out, long long *c_out, cudaStream_t s) {
     const int hmax = h_limit(H->p, H->q, S->m, S->n, H->prm.h_max);
-    auto pick = [&](int a, int b) {   // a slot other than a and b
-        for (int k = 0; k < kEvalSlots; ++k)
-            if (k != a && k != b) return k;
-        return -1;
-    };
-    auto slot = [&](int k) { return k >= 0 ? &slots[k] : nullptr; };
     unsigned long long host[2];
     long long cost[2];
     int h = std::min(h_start, hmax);
-    int best = slots ? pick(avoid, -1) : -1;
     const bool pair = h + 2 <= hmax;
-    int cand = slots ? pick(avoid, best) : -1;
-    TRY(egs_launch(H, S, P, M, h, dcount, s, slot(best)));
-    if (pair) TRY(egs_launch(H, S, P, M, h + 2, dcount + 1, s, slot(cand)));
+    TRY(egs_launch(H, S, P, M, h, dcount, s));
+    if (pair) TRY(egs_launch(H, S, P, M, h + 2, dcount + 1, s));
     const int hs[2] = {h, h + 2};
-    TRY(egs_read(S, hs, pair ? 2 : 1, dcount, host, cost, s));
+    TRY(egs_read(H, S, hs, pair ? 2 : 1, dcount, host, cost, s));
     long long c = cost[0];
     bool grow = pair;
     long long c2 = cost[1];
     while (grow) {
         if (!((double)(c - c2) > H->prm.xi * (double)c)) break;
-        h += 2; c = c2; best = cand;
+        h += 2; c = c2;
         if (h + 2 > hmax) break;
-        cand = slots ? pick(avoid, best) : -1;
-        TRY(egs_launch(H, S, P, M, h + 2, dcount, s, slot(cand)));
+        TRY(egs_launch(H, S, P, M, h + 2, dcount, s));
         const int hn[1] = {h + 2};
-        TRY(egs_read(S, hn, 1, dcount, host, cost, s));
+        TRY(egs_read(H, S, hn, 1, dcount, host, cost, s));
         c2 = cost[0];
     }
     *h_out = h;
     *c_out = c;
-    if (best_slot) *best_slot = (best >= 0 && slots[best].h == h) ? best : -1;
     return OPTA_OK;
 }
 
@@ -387,7 +381,6 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     S->sigma_map.assign((size_t)bp * bq, 0.f);
 
     PrepScratch W;
-    EvalSlot slots[kEvalSlots];
     auto scratch = [&](auto **ptr, size_t bytes) {
         return cudaMallocFromPoolAsync(reinterpret_cast<void **>(ptr), bytes, H->pool, s);
     };
@@ -395,11 +388,6 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
         void *bufs[] = {W.Pcur, W.Pacc, W.fail, W.lvl, W.count, W.IIS, W.IIQ, W.wsumP, W.invP};
         for (void *b : bufs)
             if (b) cudaFreeAsync(b, s);
-        for (EvalSlot &e : slots) {
-            void *eb[] = {e.rco, e.cinv, e.cefac};
-            for (void *b : eb)
-                if (b) cudaFreeAsync(b, s);
-        }
         if (st != OPTA_OK) {
             if (S->M_owned) {
                 H->mem.release(S->wsumM, L);
@@ -443,19 +431,10 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     int h_best = 1;
     long long c_best = 0;
     bool best_is_image = true;
-    int acc = -1;   // slot holding the accepted configuration's map (-1: none)
-    EvalSlot *sl = nullptr;
     if (prm.fixed_h > 0) {
         h_best = std::min(prm.fixed_h, h_limit(p, q, m, n, 9));
     } else {
-        const size_t G3 = (size_t)groups_along(S->Ly, 3) * groups_along(S->Lx, 3);
-        for (EvalSlot &e : slots) {
-            PCK(scratch(&e.rco, (size_t)L * sizeof(float)));
-            PCK(scratch(&e.cinv, G3 * sizeof(float)));
-            PCK(scratch(&e.cefac, G3 * sizeof(float)));
-        }
-        sl = slots;
-        PTRY(egs(H, S, H->I8, on_image, 1, W.count, &h_best, &c_best, s, sl, -1, &acc));
+        PTRY(egs(H, S, H->I8, on_image, 1, W.count, &h_best, &c_best, s));
     }
     int level_best = 0;
     if (prm.blur && prm.n_levels > 0 && prm.fixed_h == 0) {
@@ -488,7 +467,6 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
             if (any) PTRY(blur_to(H, W, cand, W.Pcur, s));
             int hk = 0;
             long long ck = 0;
-            int kslot = -1;
             if (literal) {
                 // Section 4.3: the cost is that of searching the blurred image,
                 // so EGS measures its own auto-correlation
@@ -498,9 +476,9 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
                 }
                 PCK(pivot_stats(W.Pcur, W.wsumP, W.invP));
                 PTRY(egs(H, S, W.Pcur, Members{W.Pcur, W.wsumP, W.invP}, h_best, W.count, &hk, &ck,
-                         s, sl, acc, &kslot));
+                         s));
             } else {
-                PTRY(egs(H, S, W.Pcur, on_image, h_best, W.count, &hk, &ck, s, sl, acc, &kslot));
+                PTRY(egs(H, S, W.Pcur, on_image, h_best, W.count, &hk, &ck, s));
             }
             if ((double)(c_best - ck) > prm.xi * (double)c_best) {
                 cur_level = cand;
@@ -508,7 +486,6 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
                 h_best = hk;
                 c_best = ck;
                 level_best = k;
-                acc = kslot;
                 std::swap(W.Pcur, W.Pacc);
                 best_is_image = false;
             } else {
@@ -555,18 +532,10 @@ opta_status prepare_size(opta_handle *H, int m, int n, cudaStream_t s) {
     PTRY(H->mem.alloc(&S->theta_co, L));
     PTRY(H->mem.alloc(&S->c_inv_sigma, G));
     PTRY(H->mem.alloc(&S->c_efac, G));
-    if (acc >= 0 && slots[acc].h == S->h) {
-        // the accepted configuration was evaluated by EGS: its outputs are kept
-        PCK(cudaMemcpyAsync(S->rho_co, slots[acc].rco, (size_t)L * sizeof(float),
-                            cudaMemcpyDeviceToDevice, s));
-        PCK(cudaMemcpyAsync(S->c_inv_sigma, slots[acc].cinv, (size_t)G * sizeof(float),
-                            cudaMemcpyDeviceToDevice, s));
-        PCK(cudaMemcpyAsync(S->c_efac, slots[acc].cefac, (size_t)G * sizeof(float),
-                            cudaMemcpyDeviceToDevice, s));
-    } else {
-        PCK(launch_rho_co(S->P, S->M, p, q, m, n, S->h, S->wsumM, S->invM, 0.f, S->rho_co,
-                          nullptr, S->c_inv_sigma, S->c_efac, s));
-    }
+    // the accepted configuration's full map and centre statistics (EGS
+    // only counted, over its sample)
+    PCK(launch_rho_co(S->P, S->M, p, q, m, n, S->h, S->wsumM, S->invM, 0.f, S->rho_co, nullptr,
+                      S->c_inv_sigma, S->c_efac, s));
     PCK(launch_theta_co(S->rho_co, L, S->theta_co, s));
     PTRY(H->mem.alloc(&S->gco, G));
     PCK(launch_group_co(S->theta_co, S->Ly, S->Lx, S->h, S->gco, s));
@@ -920,6 +889,38 @@ void fill_result(const TmplState &st, const SizeState *S, int Lx, int64_t L, int
     r->status = st.overflow ? OPTA_ERR_CUDA : OPTA_OK;
 }
 
+}  // namespace
+
+namespace opta {
+
+opta_status exhaustive_run(const uint8_t *I8, int p, int q, const float *tdev, int64_t tld, int m,
+                           int n, const ExhaustiveBufs &b, opta_result *best, cudaStream_t s) {
+    const int npad = (n + 7) & ~7;
+    const int Lx = q - n + 1;
+    const int64_t L = (int64_t)(p - m + 1) * Lx;
+    cudaError_t e;
+#define XCK(x) do { if ((e = (x)) != cudaSuccess) return map_err(e); } while (0)
+    XCK(launch_integrals(I8, nullptr, p, q, b.IIS, b.IIQ, nullptr, s));
+    XCK(launch_window_stats(b.IIS, b.IIQ, p, q, m, n, b.inv, b.ef, s));
+    XCK(launch_tmpl_prep(tdev, tld, m, n, npad, b.tf, b.td, b.st, 0, s));
+    XCK(launch_zncc_map(I8, p, q, b.tf, m, n, npad, b.inv, b.ef, b.st, b.map, s));
+    XCK(launch_map_candidates(b.map, b.ef, L, m, n, b.st, b.cand, (int)L, s));
+    XCK(launch_refine64(I8, q, Lx, b.td, (size_t)m * n, m, n, 1, b.st, b.cand, b.crho, L, s));
+    XCK(launch_final_argmax(1, b.st, b.cand, b.crho, L, nullptr, nullptr, s));
+    TmplState hs;
+    XCK(cudaMemcpyAsync(&hs, b.st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    XCK(cudaStreamSynchronize(s));
+#undef XCK
+    fill_result(hs, nullptr, Lx, L, 1, L, best);
+    best->n_survivors = L;
+    best->n_evaluated = L;
+    return (opta_status)best->status;
+}
+
+}  // namespace opta
+
+namespace {
+
 struct BusyGuard {
     opta_handle *h;
     explicit BusyGuard(opta_handle *hh) : h(hh) { h->busy = true; }
@@ -1054,6 +1055,7 @@ void opta_params_default(opta_params *prm) {
     prm->blur = 1;
     prm->topk = 8;
     prm->precision = 1;
+    prm->egs_sample = 4;
 }
 
 const char *opta_status_str(opta_status s) {
@@ -1538,20 +1540,8 @@ opta_status zncc_full(const opta_image *img, const opta_template *t, float *rho_
         tdev = tst;
         ld = n;
     }
-    ZCK(launch_integrals(I8, nullptr, p, q, IIS, IIQ, nullptr, s));
-    ZCK(launch_window_stats(IIS, IIQ, p, q, m, n, inv, ef, s));
-    ZCK(launch_tmpl_prep(tdev, ld, m, n, npad, tf, td, st, 0, s));
-    ZCK(launch_zncc_map(I8, p, q, tf, m, n, npad, inv, ef, st, map, s));
-    ZCK(launch_map_candidates(map, ef, L, m, n, st, cand, (int)L, s));
-    ZCK(launch_refine64(I8, q, Lx, td, (size_t)m * n, m, n, 1, st, cand, cand_rho, L, s));
-    ZCK(launch_final_argmax(1, st, cand, cand_rho, L, nullptr, nullptr, s));
-    TmplState hs;
-    ZCK(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
-    ZCK(cudaStreamSynchronize(s));
-    fill_result(hs, nullptr, Lx, L, 1, L, best);
-    best->n_survivors = L;
-    best->n_evaluated = L;
-    return finish((opta_status)best->status);
+    const ExhaustiveBufs bufs{IIS, IIQ, inv, ef, map, tf, td, cand, cand_rho, st};
+    return finish(exhaustive_run(I8, p, q, tdev, ld, m, n, bufs, best, s));
 #undef ZCK
 }
 

@@ -167,11 +167,12 @@ cudaError_t launch_window_stats(const long long *IIS, const long long *IIQ, int 
                                 int m, int n, float *inv_sigma, float *efac128,
                                 cudaStream_t s, int *wsum = nullptr);
 
-// count += number of zeros in x[0, n) (count is not cleared).
 // out[i] = i64_to_f32(v[i]) (the conversion the kernels use; tested alone).
 cudaError_t launch_i64_to_f32(const long long *v, float *out, int64_t n, cudaStream_t s);
-cudaError_t launch_count_zero(const float *x, int64_t n, unsigned long long *count,
-                              cudaStream_t s);
+// count += number of zeros of the Ly x Lx map x over the rows EGS samples
+// for group side h (kEgsRun; every row when sample == 1); not cleared.
+cudaError_t launch_count_zero(const float *x, int Ly, int Lx, int h, int sample,
+                              unsigned long long *count, cudaStream_t s);
 
 // Convert a float32 image holding integers in [0,255] into uint8; bad = 1 otherwise.
 cudaError_t launch_ingest_f32(const float *src, int64_t ld, int p, int q, uint8_t *dst,
@@ -298,27 +299,56 @@ cudaError_t launch_blur_corr(const uint8_t *P, const uint8_t *I, const int *wsum
 // of a p x q image (its strip of window columns and ring of image rows must
 // fit the thread and shared-memory limits).
 bool rho_co_supported(int p, int q, int m, int n, int h);
+// EGS counts (Algorithm 2's n_r) over a systematic sample of the location
+// grid: the group rows g (of side h) with (g / kEgsRun) % sample == 0, in
+// runs of kEgsRun group rows; sample = 1 counts every location.
+constexpr int kEgsRun = 8;
 // Pivot auto-correlation map (rco, nullable) / retained count (count,
 // nullable) for odd group side h.  The member windows' statistics come from
 // the window-sum and 1/Omega maps of I, the centres' from the pivot itself;
 // c_inv_sigma / c_efac (nullable) receive the centres' 1/sigma_hat and
-// ||P - 128|| / sigma_hat for scan 1.
+// ||P - 128|| / sigma_hat for scan 1.  With sample > 1 only the count is
+// taken, over the sampled group rows (rco, c_inv_sigma and c_efac null).
 cudaError_t launch_rho_co(const uint8_t *P, const uint8_t *I, int p, int q, int m, int n,
                           int h, const int *wsum, const float *inv_sigma, float cut, float *rco,
                           unsigned long long *count, float *c_inv_sigma, float *c_efac,
-                          cudaStream_t s);
+                          cudaStream_t s, int sample = 1);
 // Angle intervals of the pivot auto-correlation map (kEcoBound wide).
 cudaError_t launch_theta_co(const float *rho_co, int64_t L, float2 *theta_co, cudaStream_t s);
 
+// Device buffers of one exhaustive search (zncc_full and its no-allocation
+// variant): integral images ((p+1)(q+1) each), per-location 1/Omega and
+// error factor, the rho map and the candidate indices (L each), their FP64
+// rho (L), the template as FP32 rows padded to a multiple of 8 columns and
+// as FP64 (m n), and its state.
+struct ExhaustiveBufs {
+    long long *IIS, *IIQ;
+    float *inv, *ef, *map, *tf;
+    double *td;
+    int *cand;
+    double *crho;
+    TmplState *st;
+};
+// The exhaustive search of template tdev (m x n, row stride tld, device)
+// on the uint8 image I8 (p x q, device): window statistics, rho at every
+// location, candidates within the map's error bound of its maximum, their
+// FP64 rho and the argmax (lowest row-major index on ties) into *best.
+// Synchronises s; returns best->status or OPTA_ERR_CUDA.
+opta_status exhaustive_run(const uint8_t *I8, int p, int q, const float *tdev, int64_t tld, int m,
+                           int n, const ExhaustiveBufs &b, opta_result *best, cudaStream_t s);
+
 int num_sms();
 int topk_blocks(int G);
+// Budget of scan 1's waits for progress (0: the default 2 s) and its stall
+// switch, for the verification hook opta_dbg_scan1_wait.
+void set_scan1_wait(uint64_t wait_ns, int stall);
 
 // Counts every kernel launch of the library and, when per-kernel timing is
 // enabled (opta_dbg_profile_enable), brackets it with CUDA events on its stream.
-// Raise func's dynamic shared-memory limit to at least `bytes`; *cur holds
-// the limit already set (one per kernel, guarded by a library-wide lock so
-// that host threads may launch concurrently).
-cudaError_t ensure_smem(const void *func, size_t bytes, size_t *cur);
+// Raise func's dynamic shared-memory limit on the current device to at
+// least `bytes` (the limits already set are kept per kernel and device,
+// under a library-wide lock so that host threads may launch concurrently).
+cudaError_t ensure_smem(const void *func, size_t bytes);
 
 class LaunchScope {
   public:

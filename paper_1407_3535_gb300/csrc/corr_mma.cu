@@ -37,6 +37,7 @@
 // intervals that scan 2 needs are formed there from rho and this bound.
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -51,6 +52,12 @@ namespace {
 
 constexpr int kMmaM = 128;
 constexpr uint64_t kWaitNs = 2000000000ull;   // every wait gives up after 2 s
+// Budget of the waits for progress (operand built, tiles landed, stage
+// released) and the stall switch, both set only by the verification hook
+// opta_dbg_scan1_wait; the drain at the end (copies and MMAs still in
+// flight) always waits up to kWaitNs.
+std::atomic<uint64_t> g_wait_ns{kWaitNs};
+std::atomic<int> g_stall{0};
 
 __host__ __device__ inline uint32_t round_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
@@ -67,6 +74,8 @@ struct CorrMmaArgs {
     float *rho_tc;             // [T][gstride]
     int64_t gstride;
     int *err;
+    uint64_t wait_ns;          // budget of each wait for progress
+    int stall;                 // 1: the issuer first waits on a barrier no thread arrives at
 };
 
 
@@ -115,7 +124,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaA
     uint64_t *b_full = reinterpret_cast<uint64_t *>(smem);   // [2] B tiles landed
     uint64_t *mma_done = b_full + 2;                         // [2] MMAs of the stage completed
     uint64_t *a_full = mma_done + 2;                         // [2] A written by the 7 builder warps
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(a_full + 2);
+    uint64_t *stall_bar = a_full + 2;                        // never completes (verification only)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(stall_bar + 1);
     const int WA = 15 * a.h + a.Kp / 8;
     const uint32_t abytes = (uint32_t)WA * 128u;
     const uint32_t bbytes = (uint32_t)a.N * a.Kp * 2u;
@@ -141,6 +151,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaA
         tc5::mbar_init(&mma_done[1], 1);
         tc5::mbar_init(&a_full[0], kMmaThreads / 32 - 1);
         tc5::mbar_init(&a_full[1], kMmaThreads / 32 - 1);
+        tc5::mbar_init(stall_bar, 1);
         tc5::fence_mbar_init();
     }
     if (warp == 0) {
@@ -173,13 +184,15 @@ __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaA
             // its stage to be released by the MMAs of step k - 2, queues the B
             // tiles, waits for the builders' A and the tiles, issues, commits
             int step = 0, last = -1, pending = -1;   // last committed, copies not yet consumed
-            for (int r = cyk[0]; r < r_end; ++r) {
+            // verification of the timeout path: a wait that cannot complete
+            if (a.stall && !tc5::mbar_wait(stall_bar, 0u, a.wait_ns)) ok = false;
+            for (int r = cyk[0]; ok && r < r_end; ++r) {
                 int uk[kMaxRC];
                 const int nvalid = rows_of(r, uk);
                 if (nvalid == 0) continue;
                 const int s = step & 1;
                 const uint32_t ph = (step >> 1) & 1;
-                if (step >= 2 && !tc5::mbar_wait(&mma_done[s], ph ^ 1u, kWaitNs)) { ok = false; break; }
+                if (step >= 2 && !tc5::mbar_wait(&mma_done[s], ph ^ 1u, a.wait_ns)) { ok = false; break; }
                 tc5::mbar_arrive_expect_tx(&b_full[s], (uint32_t)nvalid * bbytes);
 #pragma unroll
                 for (int k = 0; k < kMaxRC; ++k)
@@ -187,7 +200,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaA
                         tc5::bulk_g2s(Bbase + (s * a.RC + k) * bstride, a.B + (size_t)uk[k] * a.N * a.Kp,
                                       bbytes, &b_full[s]);
                 pending = step;
-                if (!tc5::mbar_wait(&a_full[s], ph, kWaitNs) || !tc5::mbar_wait(&b_full[s], ph, kWaitNs)) {
+                if (!tc5::mbar_wait(&a_full[s], ph, a.wait_ns) || !tc5::mbar_wait(&b_full[s], ph, a.wait_ns)) {
                     ok = false;
                     break;
                 }
@@ -226,7 +239,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaA
             const uint32_t ph = (step >> 1) & 1;
             if (step >= 2) {
                 bool w_ok = true;
-                if (lane == 0) w_ok = tc5::mbar_wait(&mma_done[s], ph ^ 1u, kWaitNs);
+                if (lane == 0) w_ok = tc5::mbar_wait(&mma_done[s], ph ^ 1u, a.wait_ns);
                 w_ok = __shfl_sync(0xffffffffu, w_ok ? 1 : 0, 0) != 0;
                 __syncwarp();
                 if (!w_ok) { ok = false; break; }
@@ -361,6 +374,8 @@ cudaError_t launch_corr_mma(const uint8_t *V, int p, int q, const void *B, int m
     a.T = T;
     a.c_inv_sigma = c_inv_sigma;
     a.st = st; a.rho_tc = rho_tc; a.gstride = gstride; a.err = err;
+    a.wait_ns = g_wait_ns.load();
+    a.stall = g_stall.load();
     auto launch = [&](int rc) -> cudaError_t {
         size_t smem = corr_mma_smem(h, Kp, N, rc);
         // never more resident CTAs per SM than TMEM can hold (512 columns):
@@ -371,8 +386,7 @@ cudaError_t launch_corr_mma(const uint8_t *V, int p, int q, const void *B, int m
         const size_t floor_req = (size_t)(228 * 1024) / (size_t)(max_ctas + 1) + 1;
         if (smem + 1024 < floor_req) smem = floor_req - 1024 + 16;
         if (smem > 227 * 1024) return cudaErrorInvalidValue;
-        static size_t attr = 0;
-        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(corr_mma_kernel), smem, &attr);
+        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(corr_mma_kernel), smem);
         if (e != cudaSuccess) return e;
         a.RC = rc;
         dim3 grid((Gx_u + kMmaM - 1) / kMmaM, (Gy + rc - 1) / rc);
@@ -423,6 +437,11 @@ cudaError_t launch_corr_mma(const uint8_t *V, int p, int q, const void *B, int m
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tuned[key] = chosen;
     return cudaSuccess;   // the measured launches left the output
+}
+
+void set_scan1_wait(uint64_t wait_ns, int stall) {
+    g_wait_ns.store(wait_ns ? wait_ns : kWaitNs);
+    g_stall.store(stall ? 1 : 0);
 }
 
 }  // namespace opta

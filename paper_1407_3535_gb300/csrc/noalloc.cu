@@ -11,8 +11,9 @@
 // Host code never dereferences the array's name (on the host it is only a
 // stand-in symbol); the device address is looked up once per device with
 // cudaGetSymbolAddress, on that device, the first time the entry point runs
-// there.  That first call should therefore come before any stream capture.
-// All calls share the one array: anything that must start at zero is cleared
+// there.  No call may be made while its stream is being captured into a
+// graph: every call reads its result back into host memory and waits for
+// the stream.  All calls share the one array: anything that must start at zero is cleared
 // by the kernels that use it, and calls that overlap on the GPU (for example
 // from two streams) race on the shared scratch and must be serialised by the
 // caller.
@@ -115,8 +116,6 @@ extern "C" opta_status zncc_full_noalloc(const opta_image *img, const opta_templ
     const opta_status sa = scratch_address(&base);
     if (sa != OPTA_OK) return sa;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int Ly = p - m + 1, Lx = q - n + 1;
-    const int64_t L = (int64_t)Ly * Lx;
     uint8_t *I8 = base + kLay.i8;
     float *stage = reinterpret_cast<float *>(base + kLay.stage);
     long long *IIS = reinterpret_cast<long long *>(base + kLay.iis);
@@ -163,34 +162,8 @@ extern "C" opta_status zncc_full_noalloc(const opta_image *img, const opta_templ
         tdev = tst;
         tld = n;
     }
-    // the same kernels as zncc_full, on the static scratch
-    NA(launch_integrals(I8, nullptr, p, q, IIS, IIQ, nullptr, s));
-    NA(launch_window_stats(IIS, IIQ, p, q, m, n, inv, ef, s));
-    NA(launch_tmpl_prep(tdev, tld, m, n, npad, tf, td, st, 0, s));
-    NA(launch_zncc_map(I8, p, q, tf, m, n, npad, inv, ef, st, map, s));
-    NA(launch_map_candidates(map, ef, L, m, n, st, cand, (int)L, s));
-    NA(launch_refine64(I8, q, Lx, td, (size_t)m * n, m, n, 1, st, cand, crho, L, s));
-    NA(launch_final_argmax(1, st, cand, crho, L, nullptr, nullptr, s));
-    TmplState hs;
-    NA(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
-    NA(cudaStreamSynchronize(s));
 #undef NA
-    std::memset(best, 0, sizeof(*best));
-    best->n_locations = L;
-    best->n_centres = L;
-    best->n_survivors = L;
-    best->n_evaluated = L;
-    best->n_candidates = hs.n_cand;
-    best->group_h = 1;
-    if (hs.flat) {
-        best->status = OPTA_ERR_FLAT_TEMPLATE;
-        return OPTA_ERR_FLAT_TEMPLATE;
-    }
-    best->y = hs.best_idx / Lx;
-    best->x = hs.best_idx % Lx;
-    best->rho = hs.best_rho;
-    best->y_hat = best->y;
-    best->x_hat = best->x;
-    best->status = hs.overflow ? OPTA_ERR_CUDA : OPTA_OK;
-    return (opta_status)best->status;
+    // the same steps as zncc_full, on the static scratch
+    const ExhaustiveBufs bufs{IIS, IIQ, inv, ef, map, tf, td, cand, crho, st};
+    return exhaustive_run(I8, p, q, tdev, tld, m, n, bufs, best, s);
 }

@@ -308,15 +308,17 @@ template <int H>
 __global__ void __launch_bounds__(RcoCfg<H>::MAXT, 1)
 rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int p, int q,
               int m, int n, int Ly, int Lx, const int *__restrict__ wsum,
-              const float *__restrict__ inv_sigma, int GXS, int GYB, int K, float cut, float *rco,
-              unsigned long long *count, float *c_inv_sigma, float *c_efac) {
+              const float *__restrict__ inv_sigma, int GXS, int GYB, int GYS, int K, float cut,
+              float *rco, unsigned long long *count, float *c_inv_sigma, float *c_efac) {
     constexpr int R = RcoCfg<H>::R;
     constexpr int NS = RcoCfg<H>::NS;
     constexpr int KW = RcoCfg<H>::KW;
     constexpr int BATCH = RcoCfg<H>::BATCH;
     extern __shared__ unsigned rsm[];
     const int Gy = groups_along(Ly, H), Gx = groups_along(Lx, H);
-    const int gx0 = blockIdx.x * GXS, gy0 = blockIdx.y * GYB;
+    // band blockIdx.y: group rows [gy0, gy0 + GYB), bands GYS apart (GYS =
+    // GYB: every group row; GYS > GYB: the sampled runs of a count)
+    const int gx0 = blockIdx.x * GXS, gy0 = blockIdx.y * GYS;
     if (gx0 >= Gx || gy0 >= Gy) return;
     const int gx1 = min(Gx, gx0 + GXS), gy1 = min(Gy, gy0 + GYB);
     const int ngx = gx1 - gx0;
@@ -838,14 +840,13 @@ template <int H>
 cudaError_t launch_rho_co_h(const uint8_t *P, const uint8_t *I, int p, int q, int m, int n,
                             const int *wsum, const float *inv_sigma, float cut, float *rco,
                             unsigned long long *count, float *c_inv_sigma, float *c_efac,
-                            cudaStream_t s) {
+                            int sample, cudaStream_t s) {
     const int Ly = p - m + 1, Lx = q - n + 1;
     const RcoGeom g = rco_geom<H>(p, q, m, n);
     if (!g.ok) return cudaErrorInvalidValue;
     const size_t smem = g.smem;
-    static size_t attr = 0;
     {
-        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(rho_co_kernel<H>), smem, &attr);
+        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(rho_co_kernel<H>), smem);
         if (e != cudaSuccess) return e;
     }
     // one wave: strips x bands CTAs fill the SMs once (each CTA slides its
@@ -857,9 +858,19 @@ cudaError_t launch_rho_co_h(const uint8_t *P, const uint8_t *I, int p, int q, in
         bps = 1;
     }
     const int Gy = groups_along(Ly, H);
-    int bands = std::max(1, std::min(Gy, num_sms() * bps / g.strips));
-    const int GYB = (Gy + bands - 1) / bands;
-    bands = (Gy + GYB - 1) / GYB;
+    int GYB, GYS, bands;
+    if (sample > 1) {
+        // a count over the sampled runs only: one band per run of kEgsRun
+        // group rows, every sample-th run
+        GYB = kEgsRun;
+        GYS = kEgsRun * sample;
+        bands = (Gy + GYS - 1) / GYS;
+    } else {
+        bands = std::max(1, std::min(Gy, num_sms() * bps / g.strips));
+        GYB = (Gy + bands - 1) / bands;
+        GYS = GYB;
+        bands = (Gy + GYB - 1) / GYB;
+    }
     dim3 grid(g.strips, bands);
     // launches are timed under the group side's name, so that the work of
     // each (the H^2 shifts it slides) can be told apart
@@ -867,10 +878,15 @@ cudaError_t launch_rho_co_h(const uint8_t *P, const uint8_t *I, int p, int q, in
     static const char *const kName[10] = {"", "rho_co_kernel<1>", "", "rho_co_kernel<3>", "",
                                           "rho_co_kernel<5>", "", "rho_co_kernel<7>", "",
                                           "rho_co_kernel<9>"};
-    LaunchScope ls_rho_co_kernel(kName[H], s);
+    // count-only launches (EGS trials) are timed apart from map emissions
+    static const char *const kCountName[10] = {"", "rho_co_count<1>", "", "rho_co_count<3>", "",
+                                               "rho_co_count<5>", "", "rho_co_count<7>", "",
+                                               "rho_co_count<9>"};
+    const bool count_only = !rco && !c_inv_sigma && !c_efac;
+    LaunchScope ls_rho_co_kernel(count_only ? kCountName[H] : kName[H], s);
     rho_co_kernel<H><<<grid, g.threads, smem, s>>>(P, I, p, q, m, n, Ly, Lx, wsum, inv_sigma,
-                                                   g.GXS, GYB, g.K, cut, rco, count, c_inv_sigma,
-                                                   c_efac);
+                                                   g.GXS, GYB, GYS, g.K, cut, rco, count,
+                                                   c_inv_sigma, c_efac);
     return cudaGetLastError();
 }
 
@@ -888,9 +904,8 @@ cudaError_t launch_blur(const uint8_t *I, int p, int q, const uint8_t *level_map
                         const float *weights, const int *radius, uint8_t *P, cudaStream_t s) {
     const int bp = (p + block - 1) / block, bq = (q + block - 1) / block;
     const size_t smem = blur_smem_floats(block, kMaxRadius) * sizeof(float);
-    static size_t attr = 0;
     {
-        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(blur_kernel), smem, &attr);
+        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(blur_kernel), smem);
         if (e != cudaSuccess) return e;
     }
     LaunchScope ls_blur_kernel("blur_kernel", s);
@@ -914,9 +929,8 @@ cudaError_t launch_blur_corr(const uint8_t *P, const uint8_t *I, const int *wsum
     const int BR = (Ly + bands - 1) / bands;
     bands = (Ly + BR - 1) / BR;
     const size_t smem = kBcSmem;
-    static size_t attr = 0;
     {
-        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(blur_corr_kernel), smem, &attr);
+        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(blur_corr_kernel), smem);
         if (e != cudaSuccess) return e;
     }
     LaunchScope ls_blur_corr_kernel("blur_corr_kernel", s);
@@ -940,13 +954,14 @@ bool rho_co_supported(int p, int q, int m, int n, int h) {
 cudaError_t launch_rho_co(const uint8_t *P, const uint8_t *I, int p, int q, int m, int n,
                           int h, const int *wsum, const float *inv_sigma, float cut, float *rco,
                           unsigned long long *count, float *c_inv_sigma, float *c_efac,
-                          cudaStream_t s) {
+                          cudaStream_t s, int sample) {
+    if (sample > 1 && (rco || c_inv_sigma || c_efac)) return cudaErrorInvalidValue;   // counts only
     switch (h) {
-        case 1: return launch_rho_co_h<1>(P, I, p, q, m, n, wsum, inv_sigma, cut, rco, count, c_inv_sigma, c_efac, s);
-        case 3: return launch_rho_co_h<3>(P, I, p, q, m, n, wsum, inv_sigma, cut, rco, count, c_inv_sigma, c_efac, s);
-        case 5: return launch_rho_co_h<5>(P, I, p, q, m, n, wsum, inv_sigma, cut, rco, count, c_inv_sigma, c_efac, s);
-        case 7: return launch_rho_co_h<7>(P, I, p, q, m, n, wsum, inv_sigma, cut, rco, count, c_inv_sigma, c_efac, s);
-        case 9: return launch_rho_co_h<9>(P, I, p, q, m, n, wsum, inv_sigma, cut, rco, count, c_inv_sigma, c_efac, s);
+        case 1: return launch_rho_co_h<1>(P, I, p, q, m, n, wsum, inv_sigma, cut, rco, count, c_inv_sigma, c_efac, sample, s);
+        case 3: return launch_rho_co_h<3>(P, I, p, q, m, n, wsum, inv_sigma, cut, rco, count, c_inv_sigma, c_efac, sample, s);
+        case 5: return launch_rho_co_h<5>(P, I, p, q, m, n, wsum, inv_sigma, cut, rco, count, c_inv_sigma, c_efac, sample, s);
+        case 7: return launch_rho_co_h<7>(P, I, p, q, m, n, wsum, inv_sigma, cut, rco, count, c_inv_sigma, c_efac, sample, s);
+        case 9: return launch_rho_co_h<9>(P, I, p, q, m, n, wsum, inv_sigma, cut, rco, count, c_inv_sigma, c_efac, sample, s);
         default: return cudaErrorInvalidValue;
     }
 }

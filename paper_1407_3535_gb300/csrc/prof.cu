@@ -5,6 +5,7 @@
 // CUDA event pair on the launching stream so that per-kernel device time can
 // be read back after the work completes (opta_dbg_profile_*).
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -57,13 +58,19 @@ LaunchScope::~LaunchScope() {
     g_recs.push_back({name_, static_cast<cudaEvent_t>(a_), b});
 }
 
-cudaError_t ensure_smem(const void *func, size_t bytes, size_t *cur) {
+cudaError_t ensure_smem(const void *func, size_t bytes) {
+    // the attribute applies to the device current when it is set, so the
+    // limit already raised is remembered per (kernel, device)
     static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> set;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lk(mu);
-    if (bytes <= *cur) return cudaSuccess;
-    const cudaError_t e =
-        cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess) *cur = bytes;
+    size_t &cur = set[std::make_pair(func, dev)];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
     return e;
 }
 
@@ -72,6 +79,8 @@ cudaError_t ensure_smem(const void *func, size_t bytes, size_t *cur) {
 using namespace opta;
 
 extern "C" {
+
+void opta_dbg_scan1_wait(uint64_t wait_ns, int32_t stall) { set_scan1_wait(wait_ns, stall); }
 
 uint64_t opta_dbg_launch_count(void) {
     std::lock_guard<std::mutex> lk(g_mu);

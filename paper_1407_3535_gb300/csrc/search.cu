@@ -1350,9 +1350,8 @@ cudaError_t launch_tmpl_prep_batch(const TmplIn *tin, int T, int m, int n, int n
 cudaError_t launch_zncc_map(const uint8_t *I, int p, int q, const float *tf, int m, int n,
                             int npad, const float *inv_sigma, const float *efac128,
                             TmplState *st, float *map, cudaStream_t s) {
-    static size_t attr = 0;
     {
-        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(zncc_map_kernel), ZT_SMEM, &attr);
+        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(zncc_map_kernel), ZT_SMEM);
         if (e != cudaSuccess) return e;
     }
     const int Ly = p - m + 1, Lx = q - n + 1;
@@ -1412,9 +1411,8 @@ cudaError_t launch_centre_rho(const uint8_t *P, int p, int q, const float *tf, i
     const int tile_w = ((CT_X - 1) * h + CT_NT + 3) & ~3;
     const int tile_rows = (CT_Y - 1) * h + CT_MT;
     const size_t smem = (size_t)(tile_rows * tile_w + CT_MT * CT_NT) * sizeof(float);
-    static size_t attr = 0;
     {
-        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(centre_rho_kernel), smem, &attr);
+        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(centre_rho_kernel), smem);
         if (e != cudaSuccess) return e;
     }
     if (gx_begin >= Gx) return cudaSuccess;
@@ -1554,9 +1552,8 @@ cudaError_t launch_survivors(const Scan2Batch &B, const uint8_t *I, int pimg, in
     const int stage = in_smem && n <= 256 ? 1 : 0;
     // (+16: a staged row's last word pair may reach 3 bytes past its row)
     if (stage) smem += (size_t)8 * 2 * kStageRows * WB + 16;
-    static size_t attr = 0;
     {
-        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(survivors_kernel), smem, &attr);
+        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(survivors_kernel), smem);
         if (e != cudaSuccess) return e;
     }
     const uint8_t *iend = I + (int64_t)q * pimg;
@@ -1573,10 +1570,9 @@ cudaError_t launch_survivors(const Scan2Batch &B, const uint8_t *I, int pimg, in
     const int bx = std::max(num_sms(), num_sms() * 4 / std::min(B.T, 4));
     if ((int64_t)m * n <= kLaneMaxMN) {
         const size_t lsmem = ((size_t)m * npad * sizeof(float) + 15) & ~(size_t)15;
-        static size_t lattr = 0;
         {
             const cudaError_t e2 =
-                ensure_smem(reinterpret_cast<const void *>(survivors_lane_kernel), lsmem, &lattr);
+                ensure_smem(reinterpret_cast<const void *>(survivors_lane_kernel), lsmem);
             if (e2 != cudaSuccess) return e2;
         }
         LaunchScope ls("survivors_lane_kernel", s);
@@ -1605,9 +1601,8 @@ cudaError_t launch_group_members(const uint8_t *I, int q, int Ly, int Lx, int h,
                                  const int *cand_topk, int topk, cudaStream_t s) {
     int in_smem = 0;
     const size_t smem = tmpl_smem(m, npad, &in_smem);
-    static size_t attr = 0;
     {
-        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(group_members_kernel), smem, &attr);
+        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(group_members_kernel), smem);
         if (e != cudaSuccess) return e;
     }
     LaunchScope ls("group_members_kernel", s);

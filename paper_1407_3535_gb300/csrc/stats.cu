@@ -5,6 +5,7 @@
 // Pixels are integers in [0,255], so the integral images, the window sums
 // taken from them and mn*Q - S^2 (for windows up to 2^23 pixels) are exact
 // integers; only the final 1/Omega is rounded (FP32).
+#include <atomic>
 #include <algorithm>
 
 #include "common.cuh"
@@ -119,13 +120,18 @@ ii_cols_kernel(int p, int q, T *o0, T *o1, T *o2) {
     }
 }
 
-// Number of zero entries (flat windows: 1/Omega = 0) of x[0, n).
-__global__ void count_zero_kernel(const float *__restrict__ x, int64_t n,
+// Number of zero entries (flat windows: 1/Omega = 0) of the Ly x Lx map x,
+// over the rows EGS samples for group side h (every row when sample == 1).
+__global__ void count_zero_kernel(const float *__restrict__ x, int Ly, int Lx, int h, int sample,
                                   unsigned long long *count) {
     unsigned long long c = 0;
+    const int64_t n = (int64_t)Ly * Lx;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int row = (int)(i / Lx);
+        if (sample > 1 && ((row / h) / kEgsRun) % sample != 0) continue;
         c += x[i] == 0.f ? 1 : 0;
+    }
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
 }
@@ -191,13 +197,22 @@ __global__ void ingest_u8_kernel(const uint8_t *__restrict__ src, int64_t ld, in
 }  // namespace
 
 int num_sms() {
-    static const int sms = [] {
-        int dev = 0, v = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-        return v > 0 ? v : 132;
-    }();
-    return sms;
+    // per device: the library may serve several GPUs of one process
+    constexpr int kDevs = 64;
+    static std::atomic<int> sms[kDevs];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevs) {
+        cudaGetLastError();
+        return 132;
+    }
+    int v = sms[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+        cudaGetLastError();
+        return 132;
+    }
+    sms[dev].store(v, std::memory_order_relaxed);
+    return v;
 }
 
 static int grid_for(int64_t n, int threads) {
@@ -236,10 +251,10 @@ cudaError_t launch_integrals(const uint8_t *A, const uint8_t *B, int p, int q, l
 }
 
 
-cudaError_t launch_count_zero(const float *x, int64_t n, unsigned long long *count,
-                              cudaStream_t s) {
+cudaError_t launch_count_zero(const float *x, int Ly, int Lx, int h, int sample,
+                              unsigned long long *count, cudaStream_t s) {
     LaunchScope ls("count_zero_kernel", s);
-    count_zero_kernel<<<grid_for(n, 256), 256, 0, s>>>(x, n, count);
+    count_zero_kernel<<<grid_for((int64_t)Ly * Lx, 256), 256, 0, s>>>(x, Ly, Lx, h, sample, count);
     return cudaGetLastError();
 }
 

@@ -204,13 +204,15 @@ def test_rho_co_tall_windows_in_several_emission_chunks(opta, h):
     assert abs(cnt - exp_cnt) <= near
 
 
-def test_opta_decisions_match_oracle(opta):
+@pytest.mark.parametrize("sample", [4, 1])
+def test_opta_decisions_match_oracle(opta, sample):
     """The OptA level loop's choices (group side, per-block sigma) equal the
-    oracle's on a case without decisions within rounding of a threshold."""
+    oracle's on a case without decisions within rounding of a threshold, for
+    EGS counting over its default sample and over every location."""
     img = synth.aerial_image(320, 7, 20, seed=77)
     m = n = 24
-    res = ref.opta(img, m, n)
-    h = opta.optA_prepare(_cuda(img), opta.opta_params_default(), sizes=[(m, n)])
+    res = ref.opta(img, m, n, sample=sample)
+    h = opta.optA_prepare(_cuda(img), opta.opta_params_default(egs_sample=sample), sizes=[(m, n)])
     info = opta.optA_size_info(h, m, n)
     pivot = torch.empty(img.shape, dtype=torch.uint8, device="cuda")
     smap = opta.optA_debug_maps(h, m, n, pivot=pivot)

@@ -278,11 +278,38 @@ def test_egs_cost_counts():
     assert ref.egs_cost(rco, 1, 0.8) == 6 + 2
 
 
+@pytest.mark.parametrize("Ly,h,sample", [(100, 1, 4), (241, 3, 4), (4033, 5, 4), (40, 9, 2), (7, 3, 4)])
+def test_egs_sample_rows_by_enumeration(Ly, h, sample):
+    """The sampled rows: group rows in runs of 8, every sample-th run (and
+    all rows of a group row, including the short last group)."""
+    want = np.zeros(Ly, dtype=bool)
+    groups = [list(range(g, min(g + h, Ly))) for g in range(0, Ly, h)]
+    for gi, rows in enumerate(groups):
+        if (gi // 8) % sample == 0:
+            want[rows] = True
+    assert np.array_equal(ref.egs_sample_rows(Ly, h, sample), want)
+    assert ref.egs_sample_rows(Ly, h, 1).all()
+
+
+def test_egs_sampled_cost_scales_the_sampled_count():
+    Ly, Lx, h = 96, 10, 3             # 32 group rows: runs 0..3, run 0 sampled (rows 0..23)
+    rco = np.ones((Ly, Lx))
+    rco[0:6, :4] = 0.0                # 24 retained inside the sample
+    rco[30:40, :] = 0.0               # 100 retained outside it
+    groups = 32 * 4
+    assert ref.egs_cost(rco, h, 0.8, sample=1) == groups + 124
+    # sampled rows 0..23 hold 24 retained: 24 * 96 / 24 = 96
+    assert ref.egs_cost(rco, h, 0.8, sample=4) == groups + 96
+    # rounding to nearest: 1 retained over 24 sampled rows of 96 -> 4
+    one = np.ones((Ly, Lx)); one[5, 5] = 0.0
+    assert ref.egs_cost(one, h, 0.8, sample=4) == groups + 4
+
+
 def test_egs_stop_rule(monkeypatch):
     """Algorithm 2 grows h while the cost drops by more than xi of the last cost."""
     costs = {1: 1000, 3: 500, 5: 498, 7: 100, 9: 100}
     monkeypatch.setattr(ref, "rho_co_map", lambda P, I, m, n, h, threads=0: h)
-    monkeypatch.setattr(ref, "egs_cost", lambda r, h, rho_th: costs[h])
+    monkeypatch.setattr(ref, "egs_cost", lambda r, h, rho_th, sample=1: costs[h])
     log = []
     assert ref.egs(None, None, 4, 4, 1, 0.8, 0.005, log=log) == (3, 500)
     assert log == [(1, 1000), (3, 500), (5, 498)]
@@ -367,3 +394,81 @@ def test_opta_literal_without_blur_is_opta():
     a = ref.opta_literal(img, 16, 16, rho_th=0.8, rho_max=0.8)
     b = ref.opta(img, 16, 16, rho_th=0.8, rho_max=0.8)
     assert np.all(a["sigma_map"] == 0) and a["h"] == b["h"] and a["cost"] == b["cost"]
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 3: which block a failing window freezes
+# ---------------------------------------------------------------------------
+def test_opta_freezes_the_block_of_the_failing_windows_top_left():
+    """A non-square image (3 x 4 blocks of 64) that is a linear ramp except
+    for one 8 x 8 patch of white noise.  Blurring a ramp changes it by less
+    than rounding, so only windows that reach the patch's blurred support can
+    fall below lambda (Eq. misDec): at sigma = 1 the blurred noise keeps a
+    correlation of about 0.56 with itself.  The patch sits where every such
+    window has its top-left corner in block (1, 3), while the bottom-right
+    corners of some lie in block (2, 3); so exactly block (1, 3) must fail
+    and freeze -- a swapped (row, column) block index or a window assigned
+    by another corner fails this."""
+    p, q = 192, 256
+    yy, xx = np.mgrid[0:p, 0:q]
+    img = np.rint(0.6 * yy + 0.45 * xx)
+    img[115:123, 226:234] = np.random.default_rng(5).integers(0, 256, (8, 8))
+    res = ref.opta(img, 8, 8, levels=(1.0,))
+    lvl = res["trace"][1]
+    want = np.zeros((3, 4), dtype=bool)
+    want[1, 3] = True
+    assert lvl["fail"].shape == (3, 4)
+    assert np.array_equal(lvl["fail"], want)
+    assert np.array_equal(lvl["frozen_map"], want)
+    assert lvl["frozen"] == 1
+    # the same ramp without the patch: nothing fails
+    clean = ref.opta(np.rint(0.6 * yy + 0.45 * xx), 8, 8, levels=(1.0,))
+    assert not clean["trace"][1]["fail"].any()
+    # a frozen block keeps its previous sigma: with a second level the
+    # patch's block stays at 0 wherever the loop stops
+    two = ref.opta(img, 8, 8, levels=(1.0, 2.0), xi=-1.0)   # accept every level
+    assert two["sigma_map"][1, 3] == 0.0
+    assert np.all(np.delete(two["sigma_map"].ravel(), 1 * 4 + 3) > 0.0)
+
+
+def test_quantise_pivot_rounds_half_to_even_and_clips():
+    got = ref.quantise_pivot(np.array([[0.5, 1.5, 2.5, -3.0], [300.0, 254.5, 254.49, 7.5]]))
+    assert got.dtype == np.uint8
+    assert got.tolist() == [[0, 2, 2, 0], [255, 254, 254, 8]]
+
+
+# ---------------------------------------------------------------------------
+# The FFT form of Eq. rho1 against the direct definition
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape,tshape,seed", [
+    ((61, 47), (9, 13), 1),        # ragged sizes
+    ((40, 40), (40, 40), 2),       # one location (template = image size)
+    ((33, 70), (1, 7), 3),         # one-row template
+    ((50, 64), (16, 16), 4),
+])
+def test_fft_map_equals_direct_definition(shape, tshape, seed):
+    rng = np.random.default_rng(seed)
+    img = rng.integers(0, 256, size=shape).astype(np.float64)
+    img[5:25, 3:30] = 200.0                                   # flat windows
+    t = rng.normal(100.0, 30.0, size=tshape)
+    a = ref.zncc_map(img, t)
+    b = ref.zncc_map_fft(img, t)
+    assert b.shape == a.shape
+    assert np.max(np.abs(a - b)) < 1e-12
+    assert np.array_equal(a == 0.0, b == 0.0) or np.all(np.abs(b[a == 0.0]) < 1e-12)
+
+
+def test_fft_map_non_integer_image_and_flat_template():
+    rng = np.random.default_rng(6)
+    img = rng.normal(size=(45, 52))
+    t = rng.normal(size=(7, 11))
+    assert np.max(np.abs(ref.zncc_map(img, t) - ref.zncc_map_fft(img, t))) < 1e-12
+    assert np.all(ref.zncc_map_fft(img, np.full((7, 11), 3.0)) == 0.0)
+
+
+def test_fft_map_exact_crop_and_affine_template():
+    img = synth.aerial_image(160, n_octaves=6, n_prims=8, seed=17)
+    t = 1.3 * img[40:72, 90:122].astype(np.float64) - 17.0
+    rho = ref.zncc_map_fft(img, t)
+    assert abs(rho[40, 90] - 1.0) < 1e-12
+    assert ref.argmax_first(rho)[:2] == (40, 90)
