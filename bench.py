@@ -54,9 +54,8 @@ def parse():
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-brute", action="store_true")
-    ap.add_argument("--serve-full", action="store_true",
-                    help="serve the four resident images of the serving configuration "
-                         "(4096^2 .. 16384^2) instead of 4096^2 and 2048^2")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the serving report (four resident images, 4096^2 .. 16384^2)")
     ap.add_argument("--case", default=None,
                     help="one kernel for a profiler capture instead of the benchmark: "
                          "scan1:<side>, rho_co:<h> or blur_corr:<side> (see run_case)")
@@ -216,6 +215,7 @@ def run_case(spec: str):
     blur_corr:<s>  the lambda test of s x s windows against a sigma = 2 pivot
                    (blur correlation, block flags only, as in the preparation)
     blur:<sigma>   the blur of every 64 x 64 block with one sigma (<= 3)
+    brute:<s>      the exhaustive search (zncc_full) of one s x s template
     """
     import torch
     import paper_1407_3535_gb300 as opta
@@ -247,6 +247,22 @@ def run_case(spec: str):
         for _ in range(2):
             opta.opta_dbg_blur_corr(P, I, v, v, None, lam=0.947350, block=64, fail_dev=F)
         out = {"failed_blocks": int(F.sum())}
+    elif kind == "brute":
+        t = torch.from_numpy(synth.make_templates(img, [(v, v)], seed=99, noise=3.0)[0].data).cuda()
+        r = opta.zncc_full(I, t)
+        torch.cuda.synchronize()
+        opta.opta_dbg_profile_read()
+        opta.opta_dbg_profile_enable(True)
+        a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        r = opta.zncc_full(I, t)
+        b.record()
+        b.synchronize()
+        opta.opta_dbg_profile_enable(False)
+        prof = opta.opta_dbg_profile_read()
+        out = {"y": r.y, "x": r.x, "rho": r.rho, "candidates": r.n_candidates,
+               "call_ms": a.elapsed_time(b),
+               "kernels_ms": {k: round(v[0], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}}
     elif kind == "blur":
         P = torch.empty_like(I)
         for _ in range(2):
@@ -438,8 +454,11 @@ def main():
     # its answers land from the exact maxima found above
     literal = literal_report(opta, dimg, dts, sizes, res_prof, stream, flush, L_step)
 
+    # the cost model's threshold swept, and the smoother workload
+    sweeps = sweep_report(opta, dimg, dts, sizes, stream, flush, L_step, len(ts)) if world == 1 else None
+
     # the serving loop over resident images, Poisson arrivals at swept rates
-    serving = serving_report(opta, img, ts, full=args.serve_full) if world == 1 else None
+    serving = serving_report(opta) if world == 1 and not args.no_serve else None
 
     # exhaustive GPU search on the same GPU (a sample of templates, one per size)
     brute = None
@@ -519,6 +538,8 @@ def main():
         "brute_force": brute,
         "graph_search": graph,
         "literal_mode": literal,
+        "rho_th_sweep": sweeps["rho_th_sweep"] if sweeps else None,
+        "smooth_workload": sweeps["smooth_workload"] if sweeps else None,
         "serving": serving,
         "kernels_ms": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
         "prepare_kernels_ms": {k: [round(v[0], 3), v[1]] for k, v in
@@ -539,63 +560,128 @@ def main():
 
 
 SERVE_SIZES = [16, 24, 32, 48, 64, 96, 128]
+SERVE_RATES = (10, 30, 100, 300, 1000, 3000)
 
 
-def serving_report(opta, img, ts, full=False, n_req=400, workers=4, max_batch=64):
-    """The serving loop (opta.Server): images prepared once and kept resident,
-    template queries of sizes uniform in {16..128} (crops + affine intensity
-    + noise) submitted from the host as Poisson arrivals; requests join the
-    next free worker's batch.  First a burst of n_req requests measures the
-    saturated rate; then arrivals at 25, 50 and 90 % of it.  Latency =
-    completion - submission on the server's clock."""
+def serving_report(opta, workers=4, max_batch=64, budget=64 << 30, seconds=5.0, max_req=2000):
+    """The serving workload: four images (4096^2, 8192^2, 12288^2, 16384^2;
+    synth.SERVE_IMAGES) prepared once for the seven template sizes and kept
+    resident in opta.Server; template queries (crops + affine intensity +
+    noise, sizes uniform over {16,24,32,48,64,96,128}, image uniform over the
+    four) arrive as open-loop Poisson streams at fixed offered rates, each
+    for `seconds` (at most max_req, at least 40 requests), after a burst that
+    measures the saturated rate.  Requests join the next free worker's batch
+    (continuous batching); batches are admitted while the workers' scratch
+    fits `budget`.  Latency = completion - submission on the server's clock."""
     import torch
-    if full:
-        images = [img] + [synth.aerial_image(s, n_octaves=max(3, int(np.log2(s)) - 3),
-                                             n_prims=800 * s * s // 4096 ** 2, seed=2004 + s)
-                          for s in (8192, 12288, 16384)]
-    else:
-        images = [img, synth.workload_image("aerial2048_32and64")]
-    pools = [[t.data for t in ts]] + [
-        [t.data for t in synth.make_templates(im, synth.batch_sizes(64, 3000 + k), seed=3000 + k,
-                                              noise=3.0)]
-        for k, im in enumerate(images[1:])]
-    sizes = [(s, s) for s in SERVE_SIZES]
-    srv = opta.Server(n_workers=workers, max_batch=max_batch)
+    sides = tuple(synth.SERVE_IMAGES)
     t0 = time.perf_counter()
-    ids = [srv.add_image(torch.from_numpy(im).cuda(), sizes=sizes) for im in images]
+    dev_imgs = [synth.serve_image(sd) for sd in sides]
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    pools, locs_of = [], []
+    for k, d in enumerate(dev_imgs):
+        host = d.cpu().numpy()
+        ts_k = synth.make_templates(host, synth.batch_sizes(64, 2105 + k), seed=2105 + k, noise=3.0)
+        pools.append([t.data for t in ts_k])
+        locs_of.append({t.data.shape: (host.shape[0] - t.data.shape[0] + 1) * (host.shape[1] - t.data.shape[1] + 1)
+                        for t in ts_k})
+        del host
+    sizes = [(sz, sz) for sz in SERVE_SIZES]
+    srv = opta.Server(n_workers=workers, max_batch=max_batch, memory_budget=budget)
+    t0 = time.perf_counter()
+    ids = [srv.add_image(d, sizes=sizes) for d in dev_imgs]
     prep_s = time.perf_counter() - t0
-    rng = np.random.default_rng(2026)
+    image_bytes = [srv.memory(i)[0] for i in ids]
+    del dev_imgs
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(2105)
 
     def run(rate, n):
         picks = []
         next_t = time.perf_counter()
-        for k in range(n):
-            i = k % len(ids)
+        for _ in range(n):
+            i = int(rng.integers(0, len(ids)))
             t = pools[i][int(rng.integers(0, len(pools[i])))]
             if rate:
                 next_t += rng.exponential(1.0 / rate)
                 while time.perf_counter() < next_t:
                     pass
             srv.submit(ids[i], t)
-            picks.append((images[i].shape, t.shape))
+            picks.append(locs_of[i][t.shape])
         done = []
         while len(done) < n:
-            done += srv.wait(min_count=1, capacity=4096, timeout_ms=300000)
+            done += srv.wait(min_count=1, capacity=4096, timeout_ms=600000)
         lat = np.array([(c.t_done - c.t_submit) * 1e3 for c in done])
         span = max(c.t_done for c in done) - min(c.t_submit for c in done)
-        locs = sum((ish[0] - tsh[0] + 1) * (ish[1] - tsh[1] + 1) for ish, tsh in picks)
         assert all(c.status == 0 for c in done), [c.status for c in done if c.status]
-        return {"offered_rps": rate, "achieved_rps": n / span, "locations_per_s": locs / span,
+        return {"offered_rps": rate, "requests": n, "achieved_rps": n / span,
+                "locations_per_s": sum(picks) / span,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "mean_batch": float(np.mean([c.batch_size for c in done]))}
 
     run(None, 64)                       # warm-up (scratch grown, tiles tuned)
-    sat = run(None, n_req)
-    rates = [run(f * sat["achieved_rps"], n_req) for f in (0.25, 0.5, 0.9)]
+    sat = run(None, 400)
+    rates = [run(r, int(min(max_req, max(40, r * seconds)))) for r in SERVE_RATES]
+    scratch = srv.memory(ids[0])[1]
     srv.close()
-    return {"images": [f"{im.shape[0]}x{im.shape[1]}" for im in images], "workers": workers,
-            "max_batch": max_batch, "prepare_s": prep_s, "requests_per_rate": n_req,
-            "saturated": sat, "poisson": rates}
+    return {"images": [f"{sd}x{sd}" for sd in sides], "template_sizes": SERVE_SIZES,
+            "workers": workers, "max_batch": max_batch, "memory_budget_bytes": budget,
+            "image_bytes": dict(zip([f"{sd}x{sd}" for sd in sides], image_bytes)),
+            "scratch_bytes_after": scratch, "generate_s": gen_s, "prepare_s": prep_s,
+            "seconds_per_rate": seconds, "saturated": sat, "poisson": rates}
+
+
+def step_report(opta, dimg, dts, sizes, prm, stream, flush, L_step, reps=2):
+    """One untimed and `reps` timed steps (prepare + search, L2 flushed before
+    each) with parameters prm: the median step, its split, and what the
+    preparation chose and the search kept."""
+    import torch
+    h = opta.optA_prepare(dimg, prm, sizes=sizes, stream=stream)
+    opta.optA_search(h, dts, stream=stream)
+    h.close()
+    times, split = [], []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h = opta.optA_prepare(dimg, prm, sizes=sizes, stream=stream)
+        e1.record(stream)
+        res = opta.optA_search(h, dts, stream=stream)
+        e2.record(stream)
+        e2.synchronize()
+        times.append(e0.elapsed_time(e2))
+        split.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
+        info = {f"{m}x{n}": opta.optA_size_info(h, m, n) for (m, n) in sizes}
+        h.close()
+    k = int(np.argsort(times)[len(times) // 2])
+    return {"ms_per_step": times[k], "value": L_step / (times[k] / 1000.0),
+            "split_ms": {"prepare": split[k][0], "search": split[k][1]},
+            "group_sides": {s_: v["group_h"] for s_, v in info.items()},
+            "blur_levels": {s_: v["level"] for s_, v in info.items()},
+            "survivor_frac": float(np.mean([r.n_survivors / r.n_locations for r in res])),
+            "evaluated_frac": float(np.mean([r.n_evaluated / r.n_locations for r in res]))}
+
+
+def sweep_report(opta, dimg, dts, sizes, stream, flush, L_step, n_templates):
+    """Sensitivity to rho_th, the cost model's threshold (Algorithms 2 and 3;
+    the paper's Section 7 sweeps it over 0.70 .. 0.90), on the bench batch;
+    and the default parameters on the smoother workload of the same sizes
+    (octave amplitudes 2^-o instead of equal ones)."""
+    import torch
+    sweep = []
+    for rth in (0.70, 0.75, 0.80, 0.85, 0.90):
+        prm = opta.opta_params_default(rho_th=rth)
+        sweep.append({"rho_th": rth, **step_report(opta, dimg, dts, sizes, prm, stream, flush, L_step)})
+    img2 = synth.aerial_image(4096, n_octaves=9, n_prims=800, seed=2004, decay=0.5)
+    ts2 = synth.make_templates(img2, synth.batch_sizes(n_templates, 2104), seed=2104, noise=3.0)
+    d2 = torch.from_numpy(img2).cuda()
+    dts2 = [torch.from_numpy(t.data).cuda() for t in ts2]
+    smooth = step_report(opta, d2, dts2, sorted({t.data.shape for t in ts2}),
+                         opta.opta_params_default(), stream, flush, n_locations(img2.shape, ts2))
+    smooth["workload"] = "4096^2, octave amplitudes 2^-o (decay 0.5), 800 primitives, same template sizes"
+    return {"rho_th_sweep": sweep, "smooth_workload": smooth}
 
 
 def literal_report(opta, dimg, dts, sizes, exact, stream, flush, L_step):

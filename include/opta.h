@@ -239,8 +239,13 @@ opta_status optA_graph_destroy(opta_graph *g);
  * image domain as optA_prepare (integers in [0, 255]; OPTA_ERR_UNSUPPORTED
  * otherwise).  `rho_map` (nullable) is a DEVICE buffer of
  * (p-m+1)(q-n+1) floats that receives the FP32 rho map; `best` (host)
- * receives the FP64-refined best match.  Allocates its scratch with
- * stream-ordered allocation and frees it before returning.  Synchronises.
+ * receives the FP64-refined best match.  The map is taken on the tensor
+ * cores (bf16 hi/lo split of t - mu_t, FP32 accumulation) for templates up
+ * to 128 x 128, on FP32 CUDA cores beyond; either way every candidate
+ * within the map's error bound of its maximum is re-evaluated in FP64.
+ * Allocates its scratch from a library pool of the current device (stream-
+ * ordered; the pool keeps up to 4 GiB between calls) and frees it before
+ * returning.  Synchronises.
  */
 opta_status zncc_full(const opta_image *img, const opta_template *t,
                       float *rho_map, opta_result *best, void *stream);

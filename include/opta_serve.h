@@ -79,6 +79,12 @@ opta_status opta_server_wait(opta_server *srv, opta_completion *out, int32_t cap
 /* Requests submitted and not yet returned by opta_server_wait. */
 opta_status opta_server_pending(opta_server *srv, int64_t *n);
 
+/* Device bytes held for resident image `image_id` (its integral images and
+ * prepared sizes; *image_bytes, nullable) and by the workers' search scratch
+ * together (*scratch_bytes, nullable; what the memory budget limits). */
+opta_status opta_server_memory(opta_server *srv, int32_t image_id, int64_t *image_bytes,
+                               int64_t *scratch_bytes);
+
 /* Finish the queued requests, stop the workers and release every image
  * and context (NULL is accepted). */
 opta_status opta_server_destroy(opta_server *srv);

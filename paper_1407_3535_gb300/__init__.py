@@ -323,6 +323,12 @@ class Server:
                "opta_server_wait")
         return [buf[i] for i in range(n.value)]
 
+    def memory(self, image_id: int):
+        """(device bytes of the resident image, bytes of the workers' scratch)."""
+        a, b = c_int64(0), c_int64(0)
+        _check(lib().opta_server_memory(self.ptr, image_id, byref(a), byref(b)), "opta_server_memory")
+        return a.value, b.value
+
     def pending(self) -> int:
         n = c_int64(0)
         _check(lib().opta_server_pending(self.ptr, byref(n)), "opta_server_pending")

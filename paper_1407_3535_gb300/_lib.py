@@ -92,6 +92,7 @@ SIGNATURES = {
     "opta_server_wait": (c_int32, [c_void_p, POINTER(OptaCompletion), c_int32, c_int32, c_int32,
                                    POINTER(c_int32)]),
     "opta_server_pending": (c_int32, [c_void_p, POINTER(c_int64)]),
+    "opta_server_memory": (c_int32, [c_void_p, c_int32, POINTER(c_int64), POINTER(c_int64)]),
     "opta_server_destroy": (c_int32, [c_void_p]),
     "optA_graph_create": (c_int32, [c_void_p, POINTER(OptaTemplate), c_int32, c_void_p,
                                     POINTER(c_void_p)]),

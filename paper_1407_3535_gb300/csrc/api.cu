@@ -903,17 +903,33 @@ opta_status exhaustive_run(const uint8_t *I8, int p, int q, const float *tdev, i
     XCK(launch_integrals(I8, nullptr, p, q, b.IIS, b.IIQ, nullptr, s));
     XCK(launch_window_stats(b.IIS, b.IIQ, p, q, m, n, b.inv, b.ef, s));
     XCK(launch_tmpl_prep(tdev, tld, m, n, npad, b.tf, b.td, b.st, 0, s));
-    XCK(launch_zncc_map(I8, p, q, b.tf, m, n, npad, b.inv, b.ef, b.st, b.map, s));
-    XCK(launch_map_candidates(b.map, b.ef, L, m, n, b.st, b.cand, (int)L, s));
+    const bool tc = b.Ipad && b.Bt && b.err && brute_mma_supported(m, n);
+    float epsA;
+    if (tc) {
+        // the map on the tensor cores (bf16 hi/lo split of t', FP32 accumulation)
+        const int qs = (q + 15) & ~15;
+        XCK(cudaMemsetAsync(b.err, 0, sizeof(int), s));
+        XCK(launch_pad_rows(I8, p, q, b.Ipad, qs, s));
+        XCK(launch_brute_tmpl(b.tf, m, n, npad, b.Bt, s));
+        XCK(launch_brute_mma(b.Ipad, qs, p, q, b.Bt, m, n, b.inv, b.ef, b.st, b.map, b.err, s));
+        epsA = brute_mma_epsA(m, n);
+    } else {
+        XCK(launch_zncc_map(I8, p, q, b.tf, m, n, npad, b.inv, b.ef, b.st, b.map, s));
+        epsA = zncc_map_epsA(m, n);
+    }
+    XCK(launch_map_candidates(b.map, b.ef, L, epsA, b.st, b.cand, (int)L, s));
     XCK(launch_refine64(I8, q, Lx, b.td, (size_t)m * n, m, n, 1, b.st, b.cand, b.crho, L, s));
     XCK(launch_final_argmax(1, b.st, b.cand, b.crho, L, nullptr, nullptr, s));
     TmplState hs;
+    int herr = 0;
     XCK(cudaMemcpyAsync(&hs, b.st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    if (tc) XCK(cudaMemcpyAsync(&herr, b.err, sizeof(int), cudaMemcpyDeviceToHost, s));
     XCK(cudaStreamSynchronize(s));
 #undef XCK
     fill_result(hs, nullptr, Lx, L, 1, L, best);
     best->n_survivors = L;
     best->n_evaluated = L;
+    if (herr) best->status = OPTA_ERR_TIMEOUT;
     return (opta_status)best->status;
 }
 
@@ -1487,6 +1503,37 @@ opta_status optA_memory_bytes(const opta_handle *h, size_t *bytes) {
     return OPTA_OK;
 }
 
+namespace {
+// The exhaustive search's scratch pool of each device: it keeps up to 4 GiB
+// between calls (what a repeated search of one image size needs), so calls
+// do not map and unmap their scratch every time.
+cudaMemPool_t exhaustive_pool() {
+    constexpr int kDevs = 64;
+    static std::mutex mu;
+    static cudaMemPool_t pools[kDevs] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevs) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        if (cudaMemPoolCreate(&pools[dev], &props) != cudaSuccess) {
+            cudaGetLastError();
+            pools[dev] = nullptr;
+            return nullptr;
+        }
+        uint64_t keep = (uint64_t)4 << 30;
+        cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    return pools[dev];
+}
+}  // namespace
+
 opta_status zncc_full(const opta_image *img, const opta_template *t, float *rho_map,
                       opta_result *best, void *stream) {
     if (!valid_image(img) || !best) return OPTA_ERR_INVALID_ARG;
@@ -1504,8 +1551,10 @@ opta_status zncc_full(const opta_image *img, const opta_template *t, float *rho_
     double *cand_rho = nullptr;
     TmplState *st = nullptr;
     std::vector<void *> owned;
+    cudaMemPool_t pool = exhaustive_pool();
+    if (!pool) return OPTA_ERR_CUDA;
     auto A = [&](auto **ptr, size_t bytes) -> cudaError_t {
-        cudaError_t e = cudaMallocAsync((void **)ptr, bytes ? bytes : 1, s);
+        cudaError_t e = cudaMallocFromPoolAsync((void **)ptr, bytes ? bytes : 1, pool, s);
         if (e == cudaSuccess) owned.push_back(*ptr);
         return e;
     };
@@ -1530,6 +1579,14 @@ opta_status zncc_full(const opta_image *img, const opta_template *t, float *rho_
     ZCK(A(&cand, L * sizeof(int)));
     ZCK(A(&cand_rho, L * sizeof(double)));
     ZCK(A(&st, sizeof(TmplState)));
+    uint8_t *Ipad = nullptr;
+    void *Bt = nullptr;
+    int *err = nullptr;
+    if (brute_mma_supported(m, n)) {
+        ZCK(A(&Ipad, (size_t)p * ((q + 15) & ~15)));
+        ZCK(A(&Bt, brute_tmpl_bytes(m, n)));
+        ZCK(A(&err, sizeof(int)));
+    }
     const float *tdev = t->data;
     int64_t ld = t->stride_elems;
     if (!t->on_device) {
@@ -1540,7 +1597,7 @@ opta_status zncc_full(const opta_image *img, const opta_template *t, float *rho_
         tdev = tst;
         ld = n;
     }
-    const ExhaustiveBufs bufs{IIS, IIQ, inv, ef, map, tf, td, cand, cand_rho, st};
+    const ExhaustiveBufs bufs{IIS, IIQ, inv, ef, map, tf, td, cand, cand_rho, st, Ipad, Bt, err};
     return finish(exhaustive_run(I8, p, q, tdev, ld, m, n, bufs, best, s));
 #undef ZCK
 }

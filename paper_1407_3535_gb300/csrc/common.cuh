@@ -193,8 +193,12 @@ cudaError_t launch_zncc_map(const uint8_t *I, int p, int q, const float *tf, int
                             int npad, const float *inv_sigma, const float *efac128,
                             TmplState *st, float *map, cudaStream_t s);
 // Candidates from a full FP32 map: map + eps >= lower bound.
-cudaError_t launch_map_candidates(const float *map, const float *efac128, int64_t L, int m,
-                                  int n, TmplState *st, int *cand, int cap, cudaStream_t s);
+// Error-bound coefficient of the FP32 CUDA-core map: eps = epsA * efac + 8u.
+float zncc_map_epsA(int m, int n);
+// Candidates: every location whose map value + eps (epsA * efac + 8u) reaches
+// the map's certain lower bound on the maximum.
+cudaError_t launch_map_candidates(const float *map, const float *efac128, int64_t L, float epsA,
+                                  TmplState *st, int *cand, int cap, cudaStream_t s);
 
 // FP64 recomputation of rho at the candidate locations [0, n_cand) of T
 // templates (template k: td + k * dsz, st + k, cand / cand_rho + k * ccap).
@@ -320,7 +324,9 @@ cudaError_t launch_theta_co(const float *rho_co, int64_t L, float2 *theta_co, cu
 // variant): integral images ((p+1)(q+1) each), per-location 1/Omega and
 // error factor, the rho map and the candidate indices (L each), their FP64
 // rho (L), the template as FP32 rows padded to a multiple of 8 columns and
-// as FP64 (m n), and its state.
+// as FP64 (m n), and its state.  With Ipad (p x round_up(q, 16) bytes), Bt
+// (brute_tmpl_bytes) and err (one int) the map is taken on the tensor cores
+// for templates brute_mma_supported accepts; otherwise on FP32 CUDA cores.
 struct ExhaustiveBufs {
     long long *IIS, *IIQ;
     float *inv, *ef, *map, *tf;
@@ -328,7 +334,21 @@ struct ExhaustiveBufs {
     int *cand;
     double *crho;
     TmplState *st;
+    uint8_t *Ipad = nullptr;
+    void *Bt = nullptr;
+    int *err = nullptr;
 };
+
+// The exhaustive map on the tensor cores (brute_mma.cu): templates up to
+// 128 x 128; the template tile (bytes) and its error-bound coefficient.
+bool brute_mma_supported(int m, int n);
+size_t brute_tmpl_bytes(int m, int n);
+float brute_mma_epsA(int m, int n);
+cudaError_t launch_brute_tmpl(const float *tf, int m, int n, int npad, void *B, cudaStream_t s);
+cudaError_t launch_pad_rows(const uint8_t *I, int p, int q, uint8_t *out, int qs, cudaStream_t s);
+cudaError_t launch_brute_mma(const uint8_t *Ipad, int qs, int p, int q, const void *B, int m, int n,
+                             const float *inv_sigma, const float *efac, TmplState *st, float *map,
+                             int *err, cudaStream_t s);
 // The exhaustive search of template tdev (m x n, row stride tld, device)
 // on the uint8 image I8 (p x q, device): window statistics, rho at every
 // location, candidates within the map's error bound of its maximum, their

@@ -79,17 +79,6 @@ struct CorrMmaArgs {
 };
 
 
-// bf16 pair (low half first) of bytes k and k + 1 of w, each minus 128:
-// a byte b placed under the exponent of 2^23 (bit pattern 0x4B0000bb) is the
-// float 2^23 + b, so subtracting 2^23 + 128 gives b - 128 exactly, and a
-// float integer of at most 8 significant bits is exact in its top 16 bits.
-template <int K>
-__device__ __forceinline__ uint32_t bytes_bf16x2(uint32_t w) {
-    const float f0 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7650 + K)) - 8388736.f;
-    const float f1 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7650 + K + 1)) - 8388736.f;
-    return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
-}
-
 constexpr int kMmaThreads = 256;
 // The raw words of one operand item (8 pixels from column x of a row):
 // three aligned words and the byte shift that aligns them, or, at the right
@@ -252,8 +241,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaA
                 const uint32_t lo = __funnelshift_r(iw.w0, iw.w1, iw.sh);
                 const uint32_t hi = __funnelshift_r(iw.w1, iw.w2, iw.sh);
                 *reinterpret_cast<uint4 *>(Ab + (j >> 3) * 128 + (j & 7) * 16) =
-                    make_uint4(bytes_bf16x2<0>(lo), bytes_bf16x2<2>(lo), bytes_bf16x2<0>(hi),
-                               bytes_bf16x2<2>(hi));
+                    make_uint4(tc5::bytes_bf16x2<0>(lo), tc5::bytes_bf16x2<2>(lo), tc5::bytes_bf16x2<0>(hi),
+                               tc5::bytes_bf16x2<2>(hi));
             }
             tc5::fence_proxy_async_smem();
             __syncwarp();

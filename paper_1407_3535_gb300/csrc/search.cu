@@ -219,7 +219,7 @@ __device__ inline void warp_append(bool flag, int value, int *counter, int *list
 }
 
 __global__ void map_candidates_kernel(const float *__restrict__ map, const float *__restrict__ efac,
-                                      int64_t L, int kacc, TmplState *st, int *cand, int cap) {
+                                      int64_t L, float epsA, TmplState *st, int *cand, int cap) {
     if (st->flat) return;
     const float lstar = key_float(st->lo_key);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -228,7 +228,7 @@ __global__ void map_candidates_kernel(const float *__restrict__ map, const float
         bool f = false;
         if (i < L) {
             const float ef = efac[i];
-            const float eps = ef > 0.f ? eps_bound(kacc, ef) : 0.f;
+            const float eps = ef > 0.f ? fmaf(epsA, ef, 8.f * kU32) : 0.f;
             f = map[i] + eps >= lstar;
         }
         warp_append(f, (int)i, &st->n_cand, cand, cap, &st->overflow);
@@ -1361,12 +1361,16 @@ cudaError_t launch_zncc_map(const uint8_t *I, int p, int q, const float *tf, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_map_candidates(const float *map, const float *efac128, int64_t L, int m,
-                                  int n, TmplState *st, int *cand, int cap, cudaStream_t s) {
+float zncc_map_epsA(int m, int n) {
     const int npad = (n + 7) & ~7;
     const int kacc = ZT_NT + m * ((npad + ZT_NT - 1) / ZT_NT) + 1;
+    return (float)(kacc + 2) * kU32 * 1.01f;   // eps_bound's coefficient of efac
+}
+
+cudaError_t launch_map_candidates(const float *map, const float *efac128, int64_t L, float epsA,
+                                  TmplState *st, int *cand, int cap, cudaStream_t s) {
     LaunchScope ls_map_candidates_kernel("map_candidates_kernel", s);
-    map_candidates_kernel<<<grid_cap(L, 256, 8), 256, 0, s>>>(map, efac128, L, kacc, st, cand, cap);
+    map_candidates_kernel<<<grid_cap(L, 256, 8), 256, 0, s>>>(map, efac128, L, epsA, st, cand, cap);
     return cudaGetLastError();
 }
 

@@ -332,6 +332,21 @@ opta_status opta_server_pending(opta_server *S, int64_t *n) {
     return OPTA_OK;
 }
 
+opta_status opta_server_memory(opta_server *S, int32_t image_id, int64_t *image_bytes,
+                               int64_t *scratch_bytes) {
+    if (!S) return OPTA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (image_bytes) {
+        if (image_id < 0 || image_id >= (int32_t)S->images.size()) return OPTA_ERR_INVALID_ARG;
+        size_t b = 0;
+        const opta_status st = optA_memory_bytes(S->images[image_id], &b);
+        if (st != OPTA_OK) return st;
+        *image_bytes = (int64_t)b;
+    }
+    if (scratch_bytes) *scratch_bytes = (int64_t)S->used;
+    return OPTA_OK;
+}
+
 opta_status opta_server_destroy(opta_server *S) {
     if (!S) return OPTA_OK;
     {

@@ -127,6 +127,43 @@ __device__ inline void mma_commit(uint64_t *bar) {
         : "memory");
 }
 
+// 32 lanes x 8 columns of zeros into TMEM: thread i of the warp clears
+// columns [col, col+8) of TMEM lane (warp's lane base + i).  Completion is
+// awaited by tmem_wait_st.
+__device__ inline void tmem_st8_zero(uint32_t taddr) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+        "r"(0u)
+        : "memory");
+}
+__device__ inline void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// ---- tensor-map (TMA) copies --------------------------------------------------
+// 2-D tile of the tensor map `tmap` (a __grid_constant__ kernel parameter)
+// at element coordinates (x, y) into shared memory, completing on `bar`.
+// x times the element size must be a multiple of 16 bytes.
+__device__ inline void tma_load_2d(void *dst_smem, const void *tmap, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst_smem)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ---- operand conversion ----------------------------------------------------------
+// bf16 pair (low half first) of bytes k and k + 1 of w, each minus 128:
+// a byte b placed under the exponent of 2^23 (bit pattern 0x4B0000bb) is the
+// float 2^23 + b, so subtracting 2^23 + 128 gives b - 128 exactly, and a
+// float integer of at most 8 significant bits is exact in its top 16 bits.
+template <int K>
+__device__ __forceinline__ uint32_t bytes_bf16x2(uint32_t w) {
+    const float f0 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7650 + K)) - 8388736.f;
+    const float f1 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7650 + K + 1)) - 8388736.f;
+    return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+}
+
 // 32 lanes x 8 columns of 32-bit TMEM data: thread i of the warp gets
 // columns [col, col+8) of TMEM lane (warp's lane base + i).
 __device__ inline void tmem_ld8(uint32_t taddr, float (&v)[8]) {

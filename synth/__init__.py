@@ -29,6 +29,7 @@ import numpy as np
 __all__ = [
     "white_blur_image", "aerial_image", "make_templates", "Template",
     "WORKLOADS", "workload_image", "workload_templates", "BATCH_SIZES",
+    "aerial_image_device", "SERVE_IMAGES", "serve_image",
 ]
 
 # Square template sizes of the uneven-size batch (4096^2 image, 256 templates).
@@ -135,18 +136,84 @@ def aerial_image(size: int, n_octaves: int, n_prims: int, seed: int,
     return out if as_float32 else out.astype(np.uint8)
 
 
+def aerial_image_device(size: int, n_octaves: int, n_prims: int, seed: int, device="cuda"):
+    """``aerial_image``'s recipe drawn on a torch device, for images too large
+    to draw quickly on the host (uint8 tensor of size x size on `device`).
+
+    Every random number comes from the same numpy PCG64 stream in the same
+    order as ``aerial_image``; the upsampling (bilinear, cell-centred, edge
+    clamped), the primitives and the final rescale run in float32 on the
+    device, so a pixel may differ by one grey level from the host version
+    where float rounding lands on a rounding boundary.  Octave amplitudes
+    are equal (decay 1)."""
+    import torch
+    import torch.nn.functional as F
+    rng = np.random.default_rng(seed)
+    acc = torch.zeros((size, size), dtype=torch.float32, device=device)
+    for o in range(n_octaves):
+        cells = max(2, size >> (n_octaves - o))
+        grid = torch.from_numpy(rng.standard_normal((cells, cells)).astype(np.float32)).to(device)
+        acc += F.interpolate(grid[None, None], size=(size, size), mode="bilinear",
+                             align_corners=False)[0, 0]
+        del grid
+    sd = float(acc.std())
+    n_rect = n_prims // 2
+    for _ in range(n_rect):
+        hgt = int(rng.integers(8, 257)); wid = int(rng.integers(8, 257))
+        y = int(rng.integers(0, size)); x = int(rng.integers(0, size))
+        amp = float(rng.uniform(-3.0, 3.0)) * sd
+        acc[y:min(size, y + hgt), x:min(size, x + wid)] += amp
+    for _ in range(n_prims - n_rect):
+        length = float(rng.integers(32, 513)); width = float(rng.integers(1, 4))
+        ang = float(rng.uniform(0.0, np.pi))
+        y0 = float(rng.uniform(0, size)); x0 = float(rng.uniform(0, size))
+        y1 = y0 + length * np.sin(ang); x1 = x0 + length * np.cos(ang)
+        amp = float(rng.uniform(-3.0, 3.0)) * sd
+        r = width / 2.0 + 1.0
+        ymin = int(max(0, np.floor(min(y0, y1) - r))); ymax = int(min(size, np.ceil(max(y0, y1) + r) + 1))
+        xmin = int(max(0, np.floor(min(x0, x1) - r))); xmax = int(min(size, np.ceil(max(x0, x1) + r) + 1))
+        if ymin >= ymax or xmin >= xmax:
+            continue
+        yy = torch.arange(ymin, ymax, dtype=torch.float32, device=device)[:, None]
+        xx = torch.arange(xmin, xmax, dtype=torch.float32, device=device)[None, :]
+        dy, dx = y1 - y0, x1 - x0
+        tpar = (((yy - y0) * dy + (xx - x0) * dx) / max(dy * dy + dx * dx, 1e-12)).clamp(0.0, 1.0)
+        d2 = (yy - (y0 + tpar * dy)) ** 2 + (xx - (x0 + tpar * dx)) ** 2
+        acc[ymin:ymax, xmin:xmax] += (d2 <= (width / 2.0) ** 2).to(torch.float32) * amp
+    lo, hi = float(acc.min()), float(acc.max())
+    if hi <= lo:
+        return torch.zeros((size, size), dtype=torch.uint8, device=device)
+    acc -= lo
+    acc *= 255.0 / (hi - lo)
+    return torch.round(acc).to(torch.uint8)
+
+
+# The serving workload: four resident images of the same generator (area-
+# scaled primitives, one octave more per doubling of the side), seeds
+# 2005..2008.
+SERVE_IMAGES = {4096: dict(n_octaves=9, n_prims=800, seed=2005),
+                8192: dict(n_octaves=10, n_prims=3200, seed=2006),
+                12288: dict(n_octaves=10, n_prims=7200, seed=2007),
+                16384: dict(n_octaves=11, n_prims=12800, seed=2008)}
+
+
+def serve_image(size: int, device="cuda"):
+    """One image of the serving workload, drawn on the device (uint8)."""
+    return aerial_image_device(size, device=device, **SERVE_IMAGES[size])
+
+
 def make_templates(img: np.ndarray, sizes, seed: int, noise: float,
                    gain=(0.8, 1.2), offset=(-20.0, 20.0)) -> list:
     """Crops at seeded top-left locations, a*x+b, plus N(0, noise^2). float32."""
     rng = np.random.default_rng(seed)
     p, q = img.shape
     out = []
-    src = img.astype(np.float64)
     for s in sizes:
         m, n = (s, s) if np.isscalar(s) else s
         y = int(rng.integers(0, p - m + 1)); x = int(rng.integers(0, q - n + 1))
         a = float(rng.uniform(*gain)); b = float(rng.uniform(*offset))
-        t = a * src[y:y + m, x:x + n] + b + rng.normal(0.0, noise, size=(m, n))
+        crop = np.asarray(img[y:y + m, x:x + n], dtype=np.float64)
+        t = a * crop + b + rng.normal(0.0, noise, size=(m, n))
         out.append(Template(np.ascontiguousarray(t.astype(np.float32)), y, x, a, b, noise))
     return out
 

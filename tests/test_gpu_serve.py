@@ -171,3 +171,63 @@ def test_graph_replays_the_batched_search(opta):
     assert [_key(r) for r in g.launch()] == ref1
     g.close()
     h.close()
+
+
+def test_serving_workload_four_resident_images_against_the_oracle(opta):
+    """The serving workload at its stated sizes: 4096^2, 8192^2, 12288^2 and
+    16384^2 images prepared once for the seven template sizes and resident
+    in one server (memory budget 64 GiB for the workers' scratch); 8 seeded
+    queries per image (sizes uniform over {16..128}) submitted together and
+    answered in mixed batches.  Each answer is checked against the CPU FP64
+    oracle: rho at the returned location (1e-5), and no location with a
+    larger oracle rho (+1e-6) among the crop location, 48 random locations,
+    and every location of two 384 x 384 windows (around the crop and around
+    the answer), computed in full."""
+    sides = tuple(synth.SERVE_IMAGES)
+    srv = opta.Server(n_workers=4, max_batch=64, memory_budget=64 << 30)
+    try:
+        queries = []
+        for k, sd in enumerate(sides):
+            d = synth.serve_image(sd)
+            host = d.cpu().numpy()
+            iid = srv.add_image(d, sizes=[(s, s) for s in synth.BATCH_SIZES])
+            del d
+            ts = synth.make_templates(host, synth.batch_sizes(8, 4105 + k), seed=4105 + k, noise=3.0)
+            queries.append((iid, host, ts))
+        torch.cuda.empty_cache()
+        rids = {}
+        for iid, host, ts in queries:
+            for j, t in enumerate(ts):
+                rids[srv.submit(iid, t.data)] = (iid, j)
+        done = []
+        while len(done) < len(rids):
+            done += srv.wait(min_count=1, capacity=256, timeout_ms=600000)
+        got = {rids[c.request_id]: c for c in done}
+        assert max(c.batch_size for c in done) > 1
+        rng = np.random.default_rng(4105)
+        W = 384
+        for iid, host, ts in queries:
+            img64 = host.astype(np.float64)
+            p, q = host.shape
+            for j, t in enumerate(ts):
+                c = got[(iid, j)]
+                r = c.result
+                assert c.status == 0 and r.status == 0, (host.shape, j, c.status)
+                m, n = t.data.shape
+                Ly, Lx = p - m + 1, q - n + 1
+                assert abs(ref.rho_at(img64, t.data, [r.y], [r.x])[0] - r.rho) <= 1e-5
+                ys = [t.y] + list(rng.integers(0, Ly, 48))
+                xs = [t.x] + list(rng.integers(0, Lx, 48))
+                vals = ref.rho_at(img64, t.data, ys, xs)
+                assert np.all(vals <= r.rho + 1e-6), (host.shape, j, float(vals.max() - r.rho))
+                for cy, cx in ((t.y, t.x), (r.y, r.x)):
+                    y0 = int(np.clip(cy - W // 2, 0, max(0, Ly - W)))
+                    x0 = int(np.clip(cx - W // 2, 0, max(0, Lx - W)))
+                    sub = img64[y0:y0 + W + m - 1, x0:x0 + W + n - 1]
+                    win = ref.zncc_map_fft(sub, t.data)
+                    assert win.max() <= r.rho + 1e-6, (host.shape, j, float(win.max() - r.rho))
+            del img64
+        img_bytes = [srv.memory(iid)[0] for iid, _, _ in queries]
+        assert all(b > 0 for b in img_bytes) and img_bytes == sorted(img_bytes)
+    finally:
+        srv.close()
