@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-brute", action="store_true")
+    ap.add_argument("--minimal", action="store_true",
+                    help="the timed steps and the JSON line only (for profiler launch lists)")
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the serving report (four resident images, 4096^2 .. 16384^2)")
     ap.add_argument("--case", default=None,
@@ -353,6 +355,15 @@ def main():
         L_all = float(L_step)
     value = L_all / (ms / 1000.0)
 
+    if args.minimal:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                              "gpu_launches": int(launches), "minimal": True}), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
     # search-only and prepare-only split (one extra step, not part of `value`)
     barrier()
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
@@ -531,6 +542,7 @@ def main():
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "mean": float(lat.mean())},
         "survivor_fraction": {"mean": float(np.mean(surv)), "max": float(np.max(surv))},
+        "dense_templates": int(sum(1 for r in res_prof if r.n_evaluated == r.n_locations)),
         "evaluated_fraction": {"mean": float(np.mean(evald)), "max": float(np.max(evald))},
         "threshold_vs_best": {"mean_thr": float(np.mean([r.rho_threshold for r in res_prof])),
                               "mean_best": float(np.mean([r.rho for r in res_prof])),
@@ -661,7 +673,8 @@ def step_report(opta, dimg, dts, sizes, prm, stream, flush, L_step, reps=2):
             "group_sides": {s_: v["group_h"] for s_, v in info.items()},
             "blur_levels": {s_: v["level"] for s_, v in info.items()},
             "survivor_frac": float(np.mean([r.n_survivors / r.n_locations for r in res])),
-            "evaluated_frac": float(np.mean([r.n_evaluated / r.n_locations for r in res]))}
+            "evaluated_frac": float(np.mean([r.n_evaluated / r.n_locations for r in res])),
+            "dense_templates": int(sum(1 for r in res if r.n_evaluated == r.n_locations))}
 
 
 def sweep_report(opta, dimg, dts, sizes, stream, flush, L_step, n_templates):
@@ -788,7 +801,7 @@ def kernel_roofline(name, tot_ms, nl, ts, results, shape, pk, src):
 
 
 # preparation kernels run once per image, not once per size
-IMAGE_LEVEL_KERNELS = ("ingest_u8_kernel", "ii_rows_kernel", "ii_cols_kernel")
+IMAGE_LEVEL_KERNELS = ("ingest_u8_kernel", "ii_rows_kernel", "ii_cols_kernel", "pad_rows_kernel")
 
 # DRAM bytes per launch over algorithmic bytes per launch, from one ncu
 # capture of each kernel on a 4096^2 image with 64x64 windows

@@ -122,14 +122,24 @@ typedef struct opta_params {
                                with I in FP64 over the (2d+1) x (2d+1) neighbourhood of that
                                location, d = ceil(3 sigma_max) of the accepted blur map.
                                Fast but not exact: the result may miss the maximum on I. */
-    int32_t egs_sample;     /* 4: Algorithm 2's retained count n_r is taken over a systematic
+    int32_t egs_sample;     /* 8: Algorithm 2's retained count n_r is taken over a systematic
                                sample of the location grid -- the group rows g with
                                (g / 8) % egs_sample == 0, in runs of 8 group rows -- and
                                scaled to the grid; 0 or 1 counts every location as
                                Algorithm 2 does.  EGS's trials count only, and the
                                accepted configuration's map is computed once.  Speed
                                only: the search's answer does not depend on it.  <= 64. */
-    int32_t reserved[5];
+    int32_t dense;          /* 1 (default): a template whose survivors left after a first
+                               sweep over the head of scan 2's bound-ordered survivor list
+                               (about 20 L/(m n) of them) and a second cut still exceed
+                               min(1/2, dense_cut/(m n)) of the locations has
+                               rho computed at every location on the tensor cores (the
+                               exhaustive map's kernel) instead of survivor by survivor;
+                               0: never; 2: every template with a survivor left after the
+                               cut, without the first sweep (for tests).
+                               Exact search of templates up to 128 x 128 only.  Speed only. */
+    float dense_cut;        /* 0 (default) means 100: see `dense` */
+    int32_t reserved[3];
 } opta_params;
 
 typedef struct opta_handle opta_handle;

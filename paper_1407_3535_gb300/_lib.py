@@ -47,7 +47,7 @@ class OptaParams(ctypes.Structure):
                 ("block", c_int32), ("n_levels", c_int32), ("sigma_levels", c_float * 8),
                 ("h_max", c_int32), ("fixed_h", c_int32), ("blur", c_int32), ("topk", c_int32),
                 ("precision", c_int32), ("literal", c_int32), ("egs_sample", c_int32),
-                ("reserved", c_int32 * 5)]
+                ("dense", c_int32), ("dense_cut", c_float), ("reserved", c_int32 * 3)]
 
 
 class OptaServerConfig(ctypes.Structure):

@@ -132,6 +132,8 @@ struct opta_handle {
     opta_params prm;
     DevMem mem;
     uint8_t *I8 = nullptr;
+    uint8_t *Ipad = nullptr;                  // I8 with rows padded to qs bytes (tensor-map copies)
+    int qs = 0;
     long long *IIS = nullptr, *IIQ = nullptr;
     std::map<std::pair<int, int>, SizeState *> sizes;
     std::shared_mutex sizes_rw;               // `sizes`: shared while searches use it, exclusive to insert
@@ -160,6 +162,8 @@ bool valid_params(const opta_params &p) {
     if (p.precision != 0 && p.precision != 1) return false;
     if (p.literal != 0 && p.literal != 1) return false;
     if (p.egs_sample < 0 || p.egs_sample > 64) return false;
+    if (p.dense < 0 || p.dense > 2) return false;
+    if (!(p.dense_cut >= 0.f && p.dense_cut < 1e9f)) return false;
     return true;
 }
 
@@ -686,6 +690,30 @@ opta_status ensure_scratch(opta_search_ctx *X, size_t L, size_t TB, size_t RT, s
 
 bool use_mma(const opta_handle *H) { return H->prm.precision == 1; }
 
+// Whether scan 2 may evaluate an m x n template densely on the tensor cores:
+// the exact search of I (not the literal mode's blurred image), sizes the
+// tensor-core map supports, and not switched off.
+bool dense_usable(const opta_handle *H, int m, int n) {
+    return H->prm.dense != 0 && !H->prm.literal && H->Ipad && brute_mma_supported(m, n);
+}
+
+// Survivors left after the cut, as a fraction of the locations, above which a
+// template takes the dense map.  The tensor-core map costs about the same per
+// location at every template size (about 11-19 G locations/s on 4096^2) and a
+// gathered survivor about 2 m n flops at 2-3.5 TFLOP/s, which would break
+// even near 80 / (m n) of the locations; but the sweep's running lower bound
+// skips most survivors of a template with a high maximum (at rho_th = 0.9 on
+// the 4096^2 batch it evaluated a fifth of them), so the cut sits higher:
+// dense_cut / (m n) (default 100), at most half, counted after a first
+// sweep over the head of the bound-ordered list (about a quarter of the dense
+// map's cost: 20 L / (m n) survivors), which has usually raised the running
+// lower bound to the maximum.  dense = 2: every template with a survivor left.
+float dense_frac(const opta_handle *H, int m, int n) {
+    if (H->prm.dense == 2) return -1.f;
+    const float c = H->prm.dense_cut > 0.f ? H->prm.dense_cut : 100.f;
+    return std::min(0.5f, c / ((float)m * (float)n));
+}
+
 // Scan-1 error factor A of an m x n size (e = A * ||P - 128|| / sigma_hat +
 // kScan1EpsB): the largest over the kernels that compute its centres.
 float scan1_eps_factor(const opta_handle *H, int m, int n) {
@@ -720,6 +748,9 @@ ScratchPlan plan_scratch(opta_handle *H, const opta_template *t, int n_t) {
         c.TS = std::max(c.TS, chunk * (size_t)m * npad);
         const size_t N = ((2 * chunk + 15) / 16) * 16;
         if (use_mma(H)) c.B = std::max(c.B, (size_t)m * Kp * N * 2);
+        // the template tiles of a scan-2 launch that may take the dense map
+        if (dense_usable(H, m, n))
+            c.B = std::max(c.B, (size_t)scan2_batch(L, (int)chunk) * brute_tmpl_bytes(m, n));
     }
     c.N = (size_t)n_t;
     return c;
@@ -797,6 +828,7 @@ opta_status enqueue_scan2(opta_handle *H, opta_search_ctx *X, const opta_templat
     const size_t tsz = (size_t)m * npad, dsz = (size_t)m * nn;
     const int TB = std::min(scan2_batch((size_t)L, n), (int)X->capS2);
     const int64_t scap = (int64_t)X->capL;
+    const bool dense = dense_usable(H, m, nn) && S->M == H->I8;
     if (TB < 1 || ((ub_map || surv_map) && n != 1)) return OPTA_ERR_INVALID_ARG;
     for (int k0 = 0; k0 < n; k0 += TB) {
         const int T = std::min(TB, n - k0);
@@ -819,8 +851,26 @@ opta_status enqueue_scan2(opta_handle *H, opta_search_ctx *X, const opta_templat
         B.ucnt = X->ucnt;
         B.bucket_cnt = X->bucket_cnt;
         B.bucket_cur = X->bucket_cur;
+        B.L = L;
+        B.dense_frac = dense ? dense_frac(H, m, nn) : 0.f;
+        // the first sweep: about a quarter of the dense map's cost (none when
+        // every template with a survivor is to take the dense map)
+        B.first_budget = H->prm.dense == 2
+                             ? 0
+                             : std::max<int64_t>(1024, (int64_t)(20.0 * (double)L / ((double)m * nn)));
+        B.phase = 0;
         CK(launch_bound_compact(B, S->theta_co, S->gco, S->Ly, S->Lx, S->h, ub_map, surv_map, s));
+        // the survivor cut marks the templates with many survivors left as
+        // dense; the sweep skips them
         CK(launch_survivors(B, S->M, H->p, H->q, S->Lx, S->wsumM, m, nn, npad, S->invM, s));
+        if (dense) {
+            // their rho at every location on the tensor cores (templates not
+            // marked are skipped on the device), into their rho slots
+            CK(launch_brute_tmpl(X->tf + k0 * tsz, tsz, T, m, nn, npad, X->Bmma, st + k0, s));
+            CK(launch_brute_mma(H->Ipad, H->qs, H->p, H->q, X->Bmma, m, nn, S->invM, nullptr, S->wsumM,
+                                st + k0, X->surv_rho, scap, T, 1, X->dev_err, s));
+            CK(launch_dense_candidates(B, S->wsumM, S->invM, m, nn, s));
+        }
         CK(launch_surv_candidates(B, s));
         CK(launch_refine64(S->M, H->q, S->Lx, X->td + k0 * dsz, dsz, m, nn, T, st + k0, X->cand,
                            X->cand_rho, scap, s));
@@ -910,8 +960,9 @@ opta_status exhaustive_run(const uint8_t *I8, int p, int q, const float *tdev, i
         const int qs = (q + 15) & ~15;
         XCK(cudaMemsetAsync(b.err, 0, sizeof(int), s));
         XCK(launch_pad_rows(I8, p, q, b.Ipad, qs, s));
-        XCK(launch_brute_tmpl(b.tf, m, n, npad, b.Bt, s));
-        XCK(launch_brute_mma(b.Ipad, qs, p, q, b.Bt, m, n, b.inv, b.ef, b.st, b.map, b.err, s));
+        XCK(launch_brute_tmpl(b.tf, 0, 1, m, n, npad, b.Bt, nullptr, s));
+        XCK(launch_brute_mma(b.Ipad, qs, p, q, b.Bt, m, n, b.inv, b.ef, nullptr, b.st, b.map, 0, 1, 0,
+                             b.err, s));
         epsA = brute_mma_epsA(m, n);
     } else {
         XCK(launch_zncc_map(I8, p, q, b.tf, m, n, npad, b.inv, b.ef, b.st, b.map, s));
@@ -1071,7 +1122,8 @@ void opta_params_default(opta_params *prm) {
     prm->blur = 1;
     prm->topk = 8;
     prm->precision = 1;
-    prm->egs_sample = 4;
+    prm->egs_sample = 8;
+    prm->dense = 1;
 }
 
 const char *opta_status_str(opta_status s) {
@@ -1103,7 +1155,7 @@ opta_status optA_destroy(opta_handle *h) {
         if (S->M_owned) { cudaFree(S->wsumM); cudaFree(S->invM); }
         delete S;
     }
-    void *ptrs[] = {h->I8, h->IIS, h->IIQ, h->weights, h->radius};
+    void *ptrs[] = {h->I8, h->Ipad, h->IIS, h->IIQ, h->weights, h->radius};
     for (void *p : ptrs) if (p) cudaFree(p);
     if (h->dctx) free_ctx(h->dctx);
     if (h->pool) {
@@ -1153,6 +1205,13 @@ opta_status optA_prepare(const opta_image *img, const opta_params *prm, const in
     opta_status st;
     if ((st = H->mem.alloc(&H->I8, (size_t)p * q)) != OPTA_OK) return fail(st);
     if ((st = ingest(img, H->I8, s)) != OPTA_OK) return fail(st);
+    // the image with 16-byte rows for the tensor-core map of survivor-heavy templates
+    H->qs = (q + 15) & ~15;
+    if ((st = H->mem.alloc(&H->Ipad, (size_t)p * H->qs)) != OPTA_OK) return fail(st);
+    {
+        const cudaError_t e0 = launch_pad_rows(H->I8, p, q, H->Ipad, H->qs, s);
+        if (e0 != cudaSuccess) return fail(map_err(e0));
+    }
     const size_t nII = (size_t)(p + 1) * (q + 1);
     if ((st = H->mem.alloc(&H->IIS, nII)) != OPTA_OK) return fail(st);
     if ((st = H->mem.alloc(&H->IIQ, nII)) != OPTA_OK) return fail(st);

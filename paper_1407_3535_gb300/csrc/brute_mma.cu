@@ -22,8 +22,11 @@
 // MMA after the next 16-column boundary touches its column, so columns are
 // read back 16 at a time while later rows' MMAs run.
 //
-// Warp roles (256 threads, one CTA per SM: the band takes all 512 TMEM
-// columns): warp 0 lane 0 loads the template tile (one bulk copy), the image
+// A persistent CTA per SM walks the work items (template, band of output
+// rows, tile of 128 columns); templates a scan-2 launch does not need
+// densely are skipped at the top of the loop.  Warp roles (256 threads; a
+// band takes all 512 TMEM columns): warp 0 lane 0 loads the template tile
+// (one bulk copy, again when the template changes), the image
 // rows (2-D tensor-map tiles of 8 rows x BW bytes into a ring) and issues
 // the MMAs; warps 1-3 build each image row's Hankel operand from the ring;
 // warps 4-7 clear the accumulator columns, then read 8 completed columns at
@@ -87,11 +90,15 @@ __host__ __device__ inline BruteGeom brute_geom(int m, int n) {
 
 struct BruteArgs {
     int p, q, m, n, Ly, Lx, RB;
-    const __nv_bfloat16 *B;     // [2Kp/8][NB/8][8][8] core matrices
+    int tiles, bands, T;        // work items: T templates x bands x column tiles
+    const __nv_bfloat16 *B;     // template k's tile at B + k * (bbytes / 2): [2Kp/8][NB/8][8][8]
     const float *inv_sigma;     // 1/Omega per location (0: flat window)
-    const float *efac;          // ||I - 128|| / Omega per location
-    TmplState *st;
-    float *map;
+    const float *efac;          // ||I - 128|| / Omega per location (null: from wsum)
+    const int *wsum;            // window sums (with inv_sigma, when efac is null)
+    TmplState *st;              // template k's state at st + k
+    float *map;                 // template k's map at map + k * map_stride
+    int64_t map_stride;
+    int dense_only;             // skip templates without st->dense
     int *err;
     float epsA;
 };
@@ -119,7 +126,6 @@ __device__ inline bool readback_all(bool v) {
 __global__ void __launch_bounds__(kBThreads, 1)
 brute_mma_kernel(const __grid_constant__ CUtensorMap tmap, const BruteArgs a) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    if (a.st->flat) return;   // uniform: before any barrier or TMEM allocation
     const BruteGeom g = brute_geom(a.m, a.n);
     uint64_t *img_full = reinterpret_cast<uint64_t *>(smem);   // [kNR] image box landed
     uint64_t *a_full = img_full + kNR;                          // [kNS] operand built (3 warps)
@@ -131,13 +137,7 @@ brute_mma_kernel(const __grid_constant__ CUtensorMap tmap, const BruteArgs a) {
     uint8_t *Bs = smem + g.off_b;
     uint8_t *As = smem + g.off_a;
     uint8_t *ring = smem + g.off_ring;
-
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int x0 = blockIdx.x * kBM;
-    const int y0 = blockIdx.y * a.RB;
-    const int yend = min(a.Ly, y0 + a.RB);
-    const int nsteps = (yend - y0) + a.m - 1;   // image rows y0 .. yend + m - 2
-    const int nbox = (nsteps + kBR - 1) / kBR;
 
     if (tid == 0) {
         for (int i = 0; i < kNR; ++i) tc5::mbar_init(&img_full[i], 1);
@@ -148,7 +148,6 @@ brute_mma_kernel(const __grid_constant__ CUtensorMap tmap, const BruteArgs a) {
         tc5::mbar_init(&acc_full[0], 1);
         tc5::mbar_init(&acc_full[1], 1);
         tc5::mbar_init(b_full, 1);
-        *epi_done = 0;
         tc5::fence_mbar_init();
     }
     if (warp == 0) {
@@ -159,166 +158,223 @@ brute_mma_kernel(const __grid_constant__ CUtensorMap tmap, const BruteArgs a) {
     __syncthreads();
     tc5::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    // the accumulators start at zero: every MMA accumulates
-    if (warp >= 4) {
-        const uint32_t lanebase = (uint32_t)((warp & 3) * 32) << 16;
-        for (int c = 0; c < kTmemCols; c += 8) tc5::tmem_st8_zero(tmem + lanebase + (uint32_t)c);
-        tc5::tmem_wait_st();
-    }
-    tc5::tc_fence_before();
-    __syncthreads();
-    tc5::tc_fence_after();
 
+    // Work items (template z, band, column tile), one CTA per SM looping over
+    // them.  Every barrier phase follows from running counters over the items
+    // this CTA has processed (steps, image boxes, read-back batches, template
+    // tiles), which all roles advance alike, so each barrier is waited for
+    // phase by phase across items.
+    const int per_t = a.tiles * a.bands;
+    const int n_items = per_t * a.T;
+    int gstep = 0, gbox = 0, gbatch = 0, gtile = 0, curz = -1;
     bool ok = true;
-    if (warp == 0) {
-        if (lane == 0) {
-            const int KS = g.Kp / 16;
-            const uint32_t idesc = tc5::idesc_bf16_f32(kBM, g.N + 16);
-            const uint32_t blbo = (uint32_t)(g.NB / 8) * 128u;
-            tc5::mbar_arrive_expect_tx(b_full, g.bbytes);
-            tc5::bulk_g2s(Bs, a.B, g.bbytes, b_full);
-            int issued = 0;   // image boxes issued
-            for (; issued < min(kNR, nbox); ++issued) {
-                tc5::mbar_arrive_expect_tx(&img_full[issued], g.boxbytes);
-                tc5::tma_load_2d(ring + issued * g.boxbytes, &tmap, x0, y0 + kBR * issued, &img_full[issued]);
+    for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
+        const int z = item / per_t, r = item - z * per_t;
+        TmplState *st = a.st + z;
+        if (st->flat || (a.dense_only && !st->dense)) continue;   // uniform
+        const int by = r / a.tiles, bx = r - by * a.tiles;
+        const int x0 = bx * kBM;
+        const int y0 = by * a.RB;
+        const int yend = min(a.Ly, y0 + a.RB);
+        const int nsteps = (yend - y0) + a.m - 1;   // image rows y0 .. yend + m - 2
+        const int nbox = (nsteps + kBR - 1) / kBR;
+        const int nbatch = (nsteps + kEB - 1) / kEB;
+        const bool new_tile = z != curz;
+        // the accumulators start at zero: every MMA accumulates
+        if (warp >= 4) {
+            const uint32_t lanebase = (uint32_t)((warp & 3) * 32) << 16;
+            for (int c = 0; c < kTmemCols; c += 8) tc5::tmem_st8_zero(tmem + lanebase + (uint32_t)c);
+            tc5::tmem_wait_st();
+        }
+        if (tid == 0) *epi_done = 0;
+        tc5::tc_fence_before();
+        __syncthreads();
+        tc5::tc_fence_after();
+
+        if (warp == 0) {
+            if (lane == 0) {
+                const int KS = g.Kp / 16;
+                const uint32_t idesc = tc5::idesc_bf16_f32(kBM, g.N + 16);
+                const uint32_t blbo = (uint32_t)(g.NB / 8) * 128u;
+                if (new_tile) {
+                    // (the previous item's MMAs were drained: the tile is free)
+                    tc5::mbar_arrive_expect_tx(b_full, g.bbytes);
+                    tc5::bulk_g2s(Bs, a.B + (size_t)z * (g.bbytes / 2), g.bbytes, b_full);
+                }
+                int issued = 0;   // image boxes issued for this item
+                for (; issued < min(kNR, nbox); ++issued) {
+                    const int gb = gbox + issued;
+                    tc5::mbar_arrive_expect_tx(&img_full[gb % kNR], g.boxbytes);
+                    tc5::tma_load_2d(ring + (gb % kNR) * g.boxbytes, &tmap, x0, y0 + kBR * issued,
+                                     &img_full[gb % kNR]);
+                }
+                if (new_tile) ok = tc5::mbar_wait(b_full, (uint32_t)(gtile & 1), kBWaitNs);
+                const uint32_t bbase = tc5::smem_u32(Bs);
+                int last = -1;
+                for (int k = 0; ok && k < nsteps; ++k) {
+                    const int G = gstep + k, s = G % kNS;
+                    if (!tc5::mbar_wait(&a_full[s], (uint32_t)((G / kNS) & 1), kBWaitNs)) {
+                        ok = false;
+                        break;
+                    }
+                    // the builders are done with image row k: after a box's last
+                    // row its slot takes the box kNR further on
+                    if ((k % kBR) == kBR - 1 && issued < nbox) {
+                        const int gb = gbox + issued;
+                        tc5::mbar_arrive_expect_tx(&img_full[gb % kNR], g.boxbytes);
+                        tc5::tma_load_2d(ring + (gb % kNR) * g.boxbytes, &tmap, x0, y0 + kBR * issued,
+                                         &img_full[gb % kNR]);
+                        ++issued;
+                    }
+                    tc5::tc_fence_after();
+                    const uint32_t abase = tc5::smem_u32(As + s * g.astride);
+                    const int dsh = k & 15;
+                    const uint32_t d = tmem + (uint32_t)(k - dsh);            // 16-column aligned
+                    const uint32_t bsh = bbase + (uint32_t)(16 - dsh) * 16u;   // tile shifted by dsh rows
+                    for (int kk = 0; kk < 2 * KS; ++kk) {
+                        const int ka = kk < KS ? kk : kk - KS;   // hi and lo halves share A
+                        const uint64_t ad = tc5::smem_desc(abase + (uint32_t)ka * 256u, 128, 128);
+                        const uint64_t bd = tc5::smem_desc(bsh + (uint32_t)kk * 2u * blbo, blbo, 128);
+                        tc5::mma_bf16(d, ad, bd, idesc, true);
+                    }
+                    tc5::mma_commit(&mma_done[s]);
+                    // the read-back's barriers: one phase per batch of kEB steps, so
+                    // that each is waited for phase by phase
+                    if (k % kEB == kEB - 1 || k == nsteps - 1)
+                        tc5::mma_commit(&acc_full[(gbatch + k / kEB) & 1]);
+                    last = G;
+                }
+                // drain (bounded): the item's last MMAs, then every image box in flight
+                if (last >= 0 && !tc5::mbar_wait(&mma_done[last % kNS], (uint32_t)((last / kNS) & 1), kBWaitNs))
+                    ok = false;
+                for (int b = max(0, issued - kNR); b < issued; ++b) {
+                    const int gb = gbox + b;
+                    if (!tc5::mbar_wait(&img_full[gb % kNR], (uint32_t)((gb / kNR) & 1), kBWaitNs)) ok = false;
+                }
             }
-            ok = tc5::mbar_wait(b_full, 0u, kBWaitNs);
-            const uint32_t bbase = tc5::smem_u32(Bs);
-            int last = -1;
-            for (int k = 0; ok && k < nsteps; ++k) {
-                const int s = k % kNS;
-                if (!tc5::mbar_wait(&a_full[s], (uint32_t)((k / kNS) & 1), kBWaitNs)) {
+        } else if (warp < 4) {
+            // operand builders: segment w of stage s holds 8 copies b of the 8
+            // pixels from column b + 8w of image row k (a Hankel operand with
+            // shift 1: element (i = 8a + b, v = 8c + d) at byte (a + c) * 128 +
+            // 16 b + 2 d)
+            const int bt = tid - 32;
+            for (int k = 0; k < nsteps; ++k) {
+                const int G = gstep + k, s = G % kNS;
+                if (G >= kNS && !wait_warp(&mma_done[s], (uint32_t)(((G / kNS) & 1) ^ 1), lane)) {
                     ok = false;
                     break;
                 }
-                // the builders are done with image row k: after a box's last
-                // row its slot takes the box kNR further on
-                if ((k % kBR) == kBR - 1 && issued < nbox) {
-                    const int sl = issued % kNR;
-                    tc5::mbar_arrive_expect_tx(&img_full[sl], g.boxbytes);
-                    tc5::tma_load_2d(ring + sl * g.boxbytes, &tmap, x0, y0 + kBR * issued, &img_full[sl]);
-                    ++issued;
+                if (k > kGate) {
+                    bool w_ok = true;
+                    if (lane == 0) {
+                        const uint64_t t0 = tc5::globaltimer();
+                        while (*epi_done < k - kGate) {
+                            if (tc5::globaltimer() - t0 > kBWaitNs) { w_ok = false; break; }
+                        }
+                    }
+                    w_ok = __shfl_sync(0xffffffffu, w_ok ? 1 : 0, 0) != 0;
+                    __syncwarp();
+                    if (!w_ok) { ok = false; break; }
                 }
+                const int gb = gbox + k / kBR;
+                if ((k % kBR) == 0 && !wait_warp(&img_full[gb % kNR], (uint32_t)((gb / kNR) & 1), lane)) {
+                    ok = false;
+                    break;
+                }
+                const uint8_t *row = ring + (gb % kNR) * g.boxbytes + (k % kBR) * g.BW;
+                uint8_t *Ab = As + s * g.astride;
+                for (int j = bt; j < g.WA * 8; j += 96) {
+                    const int c = (j & 7) + 8 * (j >> 3);
+                    const uint32_t *wp = reinterpret_cast<const uint32_t *>(row + (c & ~3));
+                    const uint32_t sh = (uint32_t)(c & 3) * 8u;
+                    const uint32_t w0 = wp[0], w1 = wp[1], w2 = wp[2];
+                    const uint32_t lo = __funnelshift_r(w0, w1, sh);
+                    const uint32_t hi = __funnelshift_r(w1, w2, sh);
+                    *reinterpret_cast<uint4 *>(Ab + (j >> 3) * 128 + (j & 7) * 16) =
+                        make_uint4(tc5::bytes_bf16x2<0>(lo), tc5::bytes_bf16x2<2>(lo),
+                                   tc5::bytes_bf16x2<0>(hi), tc5::bytes_bf16x2<2>(hi));
+                }
+                tc5::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) tc5::mbar_arrive(&a_full[s]);
+            }
+        } else {
+            // read-back: columns [k0, k0 + 16) once the MMAs of step k0 + 15 are
+            // done (later MMAs start at column k0 + 16 or beyond)
+            const int wl = warp & 3;
+            const uint32_t lanebase = (uint32_t)(wl * 32) << 16;
+            const int x = x0 + wl * 32 + lane;
+            const bool xv = x < a.Lx;
+            const float inv_t = st->inv_sigma;
+            const float c128 = 128.f * (float)(a.m * a.n), imn = 1.f / (float)(a.m * a.n);
+            float *map = a.map + (int64_t)z * a.map_stride;
+            float lo = -3.f;
+            for (int k0 = 0; k0 < nsteps; k0 += kEB) {
+                const int kb = min(k0 + kEB, nsteps) - 1;
+                const int batch = gbatch + k0 / kEB;
+                // the four warps agree (one barrier per batch) before any leaves;
+                // passing it also means all four have seen step kb complete,
+                // which is the progress the operand builders wait for
+                if (!readback_all(wait_warp(&acc_full[batch & 1], (uint32_t)((batch >> 1) & 1), lane))) {
+                    ok = false;
+                    break;
+                }
+                if (tid == 128) *epi_done = kb + 1;
                 tc5::tc_fence_after();
-                const uint32_t abase = tc5::smem_u32(As + s * g.astride);
-                const int dsh = k & 15;
-                const uint32_t d = tmem + (uint32_t)(k - dsh);            // 16-column aligned
-                const uint32_t bsh = bbase + (uint32_t)(16 - dsh) * 16u;   // tile shifted by dsh rows
-                for (int kk = 0; kk < 2 * KS; ++kk) {
-                    const int ka = kk < KS ? kk : kk - KS;   // hi and lo halves share A
-                    const uint64_t ad = tc5::smem_desc(abase + (uint32_t)ka * 256u, 128, 128);
-                    const uint64_t bd = tc5::smem_desc(bsh + (uint32_t)kk * 2u * blbo, blbo, 128);
-                    tc5::mma_bf16(d, ad, bd, idesc, true);
-                }
-                tc5::mma_commit(&mma_done[s]);
-                // the read-back's barriers: one phase per batch of kEB steps, so
-                // that each is waited for phase by phase
-                if (k % kEB == kEB - 1 || k == nsteps - 1) tc5::mma_commit(&acc_full[(k / kEB) & 1]);
-                last = k;
-            }
-            // drain (bounded): the last MMAs, then every image box in flight
-            if (last >= 0 && !tc5::mbar_wait(&mma_done[last % kNS], (uint32_t)((last / kNS) & 1), kBWaitNs))
-                ok = false;
-            for (int b = max(0, issued - kNR); b < issued; ++b)
-                if (!tc5::mbar_wait(&img_full[b % kNR], (uint32_t)((b / kNR) & 1), kBWaitNs)) ok = false;
-        }
-    } else if (warp < 4) {
-        // operand builders: segment w of stage s holds 8 copies b of the 8
-        // pixels from column b + 8w of image row k (a Hankel operand with
-        // shift 1: element (i = 8a + b, v = 8c + d) at byte (a + c) * 128 +
-        // 16 b + 2 d)
-        const int bt = tid - 32;
-        for (int k = 0; k < nsteps; ++k) {
-            const int s = k % kNS;
-            if (k >= kNS && !wait_warp(&mma_done[s], (uint32_t)(((k / kNS) & 1) ^ 1), lane)) {
-                ok = false;
-                break;
-            }
-            if (k > kGate) {
-                bool w_ok = true;
-                if (lane == 0) {
-                    const uint64_t t0 = tc5::globaltimer();
-                    while (*epi_done < k - kGate) {
-                        if (tc5::globaltimer() - t0 > kBWaitNs) { w_ok = false; break; }
+                float v[kEB];
+                tc5::tmem_ld8(tmem + lanebase + (uint32_t)k0, *reinterpret_cast<float(*)[8]>(&v[0]));
+                tc5::tmem_ld8(tmem + lanebase + (uint32_t)k0 + 8u, *reinterpret_cast<float(*)[8]>(&v[8]));
+#pragma unroll
+                for (int c = 0; c < kEB; ++c) {
+                    const int y = y0 + k0 + c - (a.m - 1);
+                    if (k0 + c > kb || y < y0 || y >= yend || !xv) continue;
+                    const int64_t idx = (int64_t)y * a.Lx + x;
+                    const float is = a.inv_sigma[idx];
+                    const float rho = (v[c] * inv_t) * is;
+                    map[idx] = rho;
+                    if (is > 0.f) {
+                        float ef;
+                        if (a.efac) {
+                            ef = a.efac[idx];
+                        } else {
+                            const float dd = ((float)a.wsum[idx] - c128) * is;
+                            ef = sqrtf(fmaf(dd * dd, imn, 1.f));
+                        }
+                        lo = fmaxf(lo, rho - fmaf(a.epsA, ef, 8.f * kU32));
                     }
                 }
-                w_ok = __shfl_sync(0xffffffffu, w_ok ? 1 : 0, 0) != 0;
-                __syncwarp();
-                if (!w_ok) { ok = false; break; }
             }
-            const int b = k / kBR;
-            if ((k % kBR) == 0 && !wait_warp(&img_full[b % kNR], (uint32_t)((b / kNR) & 1), lane)) {
-                ok = false;
-                break;
-            }
-            const uint8_t *row = ring + (b % kNR) * g.boxbytes + (k % kBR) * g.BW;
-            uint8_t *Ab = As + s * g.astride;
-            for (int j = bt; j < g.WA * 8; j += 96) {
-                const int c = (j & 7) + 8 * (j >> 3);
-                const uint32_t *wp = reinterpret_cast<const uint32_t *>(row + (c & ~3));
-                const uint32_t sh = (uint32_t)(c & 3) * 8u;
-                const uint32_t w0 = wp[0], w1 = wp[1], w2 = wp[2];
-                const uint32_t lo = __funnelshift_r(w0, w1, sh);
-                const uint32_t hi = __funnelshift_r(w1, w2, sh);
-                *reinterpret_cast<uint4 *>(Ab + (j >> 3) * 128 + (j & 7) * 16) =
-                    make_uint4(tc5::bytes_bf16x2<0>(lo), tc5::bytes_bf16x2<2>(lo),
-                               tc5::bytes_bf16x2<0>(hi), tc5::bytes_bf16x2<2>(hi));
-            }
-            tc5::fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) tc5::mbar_arrive(&a_full[s]);
+            for (int o = 16; o > 0; o >>= 1) lo = fmaxf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            if (lane == 0 && lo > -2.5f) atomicMax(&st->lo_key, float_key(lo));
         }
-    } else {
-        // read-back: columns [k0, k0 + 16) once the MMAs of step k0 + 15 are
-        // done (later MMAs start at column k0 + 16 or beyond)
-        const int wl = warp & 3;
-        const uint32_t lanebase = (uint32_t)(wl * 32) << 16;
-        const int x = x0 + wl * 32 + lane;
-        const bool xv = x < a.Lx;
-        const float inv_t = a.st->inv_sigma;
-        float lo = -3.f;
-        for (int k0 = 0; k0 < nsteps; k0 += kEB) {
-            const int kb = min(k0 + kEB, nsteps) - 1;
-            // the four warps agree (one barrier per batch) before any leaves;
-            // passing it also means all four have seen step kb complete,
-            // which is the progress the operand builders wait for
-            const int batch = k0 / kEB;
-            if (!readback_all(wait_warp(&acc_full[batch & 1], (uint32_t)((batch >> 1) & 1), lane))) {
-                ok = false;
-                break;
-            }
-            if (tid == 128) *epi_done = kb + 1;
-            tc5::tc_fence_after();
-            float v[kEB];
-            tc5::tmem_ld8(tmem + lanebase + (uint32_t)k0, *reinterpret_cast<float(*)[8]>(&v[0]));
-            tc5::tmem_ld8(tmem + lanebase + (uint32_t)k0 + 8u, *reinterpret_cast<float(*)[8]>(&v[8]));
-#pragma unroll
-            for (int c = 0; c < kEB; ++c) {
-                const int y = y0 + k0 + c - (a.m - 1);
-                if (k0 + c > kb || y < y0 || y >= yend || !xv) continue;
-                const int64_t idx = (int64_t)y * a.Lx + x;
-                const float is = a.inv_sigma[idx];
-                const float rho = (v[c] * inv_t) * is;
-                a.map[idx] = rho;
-                if (is > 0.f) lo = fmaxf(lo, rho - fmaf(a.epsA, a.efac[idx], 8.f * kU32));
-            }
-        }
-        for (int o = 16; o > 0; o >>= 1) lo = fmaxf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-        if (lane == 0 && lo > -2.5f) atomicMax(&a.st->lo_key, float_key(lo));
+        // every role is done with the item (the issuer drained its MMAs and
+        // image boxes) before the next one clears the accumulators
+        tc5::tc_fence_before();
+        ok = __syncthreads_and(ok) != 0;
+        tc5::tc_fence_after();
+        gstep += nsteps;
+        gbox += nbox;
+        gbatch += nbatch;
+        if (new_tile) ++gtile;
+        curz = z;
     }
-    tc5::tc_fence_before();
-    ok = __syncthreads_and(ok) != 0;
-    tc5::tc_fence_after();
     if (!ok && tid == 0) atomicExch(a.err, 1);
+    tc5::tc_fence_before();
+    __syncthreads();
+    tc5::tc_fence_after();
     if (warp == 0) tc5::tmem_dealloc(tmem, kTmemCols);
 }
 
 // t' (FP32, m x npad) -> the template tile of NB = N + 32 rows: row 16 + j
 // holds template row m-1-j (j < m), every other row is zero; K halves
 // hi | lo of the bf16 split, zeros past n columns.
-__global__ void brute_tmpl_kernel(const float *__restrict__ tf, int m, int n, int npad, int Kp,
-                                  int NB, __nv_bfloat16 *B) {
+__global__ void brute_tmpl_kernel(const float *__restrict__ tf, size_t tsz, int m, int n, int npad,
+                                  int Kp, int NB, const TmplState *st, __nv_bfloat16 *B) {
+    // template blockIdx.y (with st: only templates marked dense)
+    if (st && !st[blockIdx.y].dense) return;
+    tf += blockIdx.y * tsz;
     const int total = NB * 2 * Kp;
+    B += (size_t)blockIdx.y * total;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
         const int jj = idx / (2 * Kp), kk = idx - jj * 2 * Kp;
         const int v = kk < Kp ? kk : kk - Kp;
@@ -369,12 +425,14 @@ float brute_mma_epsA(int m, int n) {
     return scan1_epsA_mma(2 * m, (int)rup((uint32_t)n, 16));
 }
 
-cudaError_t launch_brute_tmpl(const float *tf, int m, int n, int npad, void *B, cudaStream_t s) {
+cudaError_t launch_brute_tmpl(const float *tf, size_t tsz, int T, int m, int n, int npad, void *B,
+                              const TmplState *dense_of, cudaStream_t s) {
     const BruteGeom g = brute_geom(m, n);
     const int total = g.NB * 2 * g.Kp;
     LaunchScope ls("brute_tmpl_kernel", s);
-    brute_tmpl_kernel<<<(total + 255) / 256, 256, 0, s>>>(tf, m, n, npad, g.Kp, g.NB,
-                                                         static_cast<__nv_bfloat16 *>(B));
+    brute_tmpl_kernel<<<dim3((total + 255) / 256, T), 256, 0, s>>>(tf, tsz, m, n, npad, g.Kp, g.NB,
+                                                                  dense_of,
+                                                                  static_cast<__nv_bfloat16 *>(B));
     return cudaGetLastError();
 }
 
@@ -387,9 +445,12 @@ cudaError_t launch_pad_rows(const uint8_t *I, int p, int q, uint8_t *out, int qs
 }
 
 cudaError_t launch_brute_mma(const uint8_t *Ipad, int qs, int p, int q, const void *B, int m, int n,
-                             const float *inv_sigma, const float *efac, TmplState *st, float *map,
+                             const float *inv_sigma, const float *efac, const int *wsum,
+                             TmplState *st, float *map, int64_t map_stride, int T, int dense_only,
                              int *err, cudaStream_t s) {
-    if (!brute_mma_supported(m, n) || qs % 16 != 0 || qs < q) return cudaErrorInvalidValue;
+    if (!brute_mma_supported(m, n) || qs % 16 != 0 || qs < q || T < 1 || T > 65535 ||
+        (!efac && !wsum))
+        return cudaErrorInvalidValue;
     const BruteGeom g = brute_geom(m, n);
     const int Ly = p - m + 1, Lx = q - n + 1;
     // a band's columns: the last MMA writes up to column (nsteps - 1) + N + 16
@@ -433,10 +494,16 @@ cudaError_t launch_brute_mma(const uint8_t *Ipad, int qs, int p, int q, const vo
     BruteArgs a;
     a.p = p; a.q = q; a.m = m; a.n = n; a.Ly = Ly; a.Lx = Lx; a.RB = RB;
     a.B = static_cast<const __nv_bfloat16 *>(B);
-    a.inv_sigma = inv_sigma; a.efac = efac; a.st = st; a.map = map; a.err = err;
+    a.inv_sigma = inv_sigma; a.efac = efac; a.wsum = wsum; a.st = st; a.map = map;
+    a.map_stride = map_stride; a.dense_only = dense_only; a.err = err;
     a.epsA = brute_mma_epsA(m, n);
+    a.tiles = tiles; a.bands = bands; a.T = T;
+    // persistent: one CTA per SM walks the (template, band, tile) items
+    const int64_t items = (int64_t)tiles * bands * T;
+    if (items > 0x7fffffff) return cudaErrorInvalidValue;
+    const int grid = (int)std::min<int64_t>(items, sms);
     LaunchScope ls("brute_mma_kernel", s);
-    brute_mma_kernel<<<dim3(tiles, bands), kBThreads, smem, s>>>(tm, a);
+    brute_mma_kernel<<<grid, kBThreads, smem, s>>>(tm, a);
     return cudaGetLastError();
 }
 

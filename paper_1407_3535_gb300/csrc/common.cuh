@@ -138,6 +138,8 @@ struct TmplState {
     int n_surv_eff;           // survivors past this index are known to be skippable
     int hat_idx;              // literal mode: maximum on the blurred image (-1 otherwise)
     int n_cand_search;        // literal mode: candidates of the search before the re-match
+    int dense;                // 1: every location's rho from the tensor-core map, no gathers
+    int n_first;              // survivors the first sweep takes (two-phase sweep)
 };
 
 // Survivors are bucketed by their upper bound (bucket 0 = highest) so that
@@ -268,6 +270,13 @@ struct Scan2Batch {
     int64_t ccap;
     int *ucnt;                           // unordered survivors found, per template
     int *bucket_cnt, *bucket_cur;        // k * kUbBuckets
+    float dense_frac;                    // > 0: a template with more survivors left than
+                                         // dense_frac * L after its first sweep takes the
+                                         // dense map; < 0: any template with a survivor
+                                         // left; 0: none (one sweep)
+    int64_t first_budget;                // survivors of the first sweep (dense_frac != 0)
+    int64_t L;                           // locations per template
+    int phase;                           // sweep: 0 all, 1 the first n_first, 2 the rest
 };
 
 // Bound of every location against each template's threshold (group test
@@ -344,11 +353,24 @@ struct ExhaustiveBufs {
 bool brute_mma_supported(int m, int n);
 size_t brute_tmpl_bytes(int m, int n);
 float brute_mma_epsA(int m, int n);
-cudaError_t launch_brute_tmpl(const float *tf, int m, int n, int npad, void *B, cudaStream_t s);
+// Template tiles of T templates (t' at tf + k * tsz) into B + k * brute_tmpl_bytes;
+// with dense_of (nullable), only templates k with dense_of[k].dense.
+cudaError_t launch_brute_tmpl(const float *tf, size_t tsz, int T, int m, int n, int npad, void *B,
+                              const TmplState *dense_of, cudaStream_t s);
 cudaError_t launch_pad_rows(const uint8_t *I, int p, int q, uint8_t *out, int qs, cudaStream_t s);
+// rho maps of T templates (tile k at B + k * brute_tmpl_bytes, state st[k],
+// map at map + k * map_stride); with dense_only, templates without
+// st[k].dense are skipped.  The error factor ||I - 128|| / Omega comes from
+// efac, or when efac is null from the window sums wsum and inv_sigma.
 cudaError_t launch_brute_mma(const uint8_t *Ipad, int qs, int p, int q, const void *B, int m, int n,
-                             const float *inv_sigma, const float *efac, TmplState *st, float *map,
+                             const float *inv_sigma, const float *efac, const int *wsum,
+                             TmplState *st, float *map, int64_t map_stride, int T, int dense_only,
                              int *err, cudaStream_t s);
+// Candidates of the templates of a scan-2 batch that took the dense map
+// (held in B.surv_rho + k * B.scap): every location whose rho + eps
+// reaches the certain lower bound on the maximum.
+cudaError_t launch_dense_candidates(const Scan2Batch &B, const int *wsum, const float *inv_sigma,
+                                    int m, int n, cudaStream_t s);
 // The exhaustive search of template tdev (m x n, row stride tld, device)
 // on the uint8 image I8 (p x q, device): window statistics, rho at every
 // location, candidates within the map's error bound of its maximum, their

@@ -106,6 +106,8 @@ tmpl_prep_kernel(const float *__restrict__ t, int64_t ld, const TmplIn *__restri
         st->n_surv_eff = 0x7fffffff;
         st->hat_idx = -1;
         st->n_cand_search = 0;
+        st->dense = 0;
+        st->n_first = 0;
     }
 }
 
@@ -1079,8 +1081,12 @@ survivors_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, int L
     float *surv_rho = B.surv_rho + blockIdx.y * B.scap;
     float *surv_eps = B.surv_eps + blockIdx.y * B.scap;
     // blocks whose first entry lies beyond the survivor list have nothing to do
-    const int ns0 = (int)min((int64_t)min(st->n_surv, st->n_surv_eff), B.scap);
-    if ((int)blockIdx.x * (int)(blockDim.x >> 5) >= ns0) return;
+    if (st->dense) return;
+    // entries [ns_lo, ns0) of the bound-ordered list in this sweep
+    const int ns_all = (int)min((int64_t)min(st->n_surv, st->n_surv_eff), B.scap);
+    const int ns_lo = B.phase == 2 ? min(st->n_first, ns_all) : 0;
+    const int ns0 = B.phase == 1 ? min(st->n_first, ns_all) : ns_all;
+    if (ns_lo + (int)blockIdx.x * (int)(blockDim.x >> 5) >= ns0) return;
     const float *tm = stage_template(tf, m, npad, tmpl_in_smem, reinterpret_cast<float *>(ssm4));
     uint8_t *wbuf = nullptr;
     if (stage) {
@@ -1103,7 +1109,7 @@ survivors_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, int L
     // lower bound is read once per round and kept current with the values
     // the warp's own atomic maxima return (a stale bound only skips less).
     float lim = -4.f;
-    for (int64_t base = warp; base < ns; base += 32 * (int64_t)nwarps) {
+    for (int64_t base = ns_lo + warp; base < ns; base += 32 * (int64_t)nwarps) {
         const int64_t sl = base + (int64_t)lane * nwarps;
         const bool have = sl < ns;
         const float ubl = have ? surv_ub[sl] : -4.f;
@@ -1154,8 +1160,12 @@ survivors_lane_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, 
     const float *surv_ub = B.surv_ub + blockIdx.y * B.scap;
     float *surv_rho = B.surv_rho + blockIdx.y * B.scap;
     float *surv_eps = B.surv_eps + blockIdx.y * B.scap;
-    const int ns = (int)min((int64_t)min(st->n_surv, st->n_surv_eff), B.scap);
-    if ((int)blockIdx.x * (int)(blockDim.x >> 5) >= ns) return;   // uniform
+    if (st->dense) return;
+    // entries [ns_lo, ns) of the bound-ordered list in this sweep
+    const int ns_all = (int)min((int64_t)min(st->n_surv, st->n_surv_eff), B.scap);
+    const int ns_lo = B.phase == 2 ? min(st->n_first, ns_all) : 0;
+    const int ns = B.phase == 1 ? min(st->n_first, ns_all) : ns_all;
+    if (ns_lo + (int)blockIdx.x * (int)(blockDim.x >> 5) >= ns) return;   // uniform
     const float *tm = stage_template(B.tf + blockIdx.y * B.tsz, m, npad, 1,
                                      reinterpret_cast<float *>(lsm4));
     const int lane = threadIdx.x & 31;
@@ -1168,7 +1178,7 @@ survivors_lane_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, 
     const uintptr_t iend = reinterpret_cast<uintptr_t>(img_end);
     float lim = -4.f;
     int evaluated = 0;
-    for (int64_t base = warp; base < ns; base += 32 * (int64_t)nwarps) {
+    for (int64_t base = ns_lo + warp; base < ns; base += 32 * (int64_t)nwarps) {
         const int64_t sl = base + (int64_t)lane * nwarps;
         lim = fmaxf(lim, __shfl_sync(0xffffffffu, key_float(*lo_key), 0));
         bool act = false;
@@ -1250,7 +1260,7 @@ survivors_lane_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, 
 // (gap/lim)^2 in [b/NB, (b+1)/NB), i.e. bounds <= cos(lim sqrt(b/NB)) + margin
 // (evaluated with a relative slack on the angle and a doubled margin).
 __global__ void __launch_bounds__(kUbBuckets)
-survivor_cut_kernel(const Scan2Batch B) {
+survivor_cut_kernel(const Scan2Batch B, int phase) {
     __shared__ int first;
     TmplState *st = B.st + blockIdx.x;
     const int *bucket_end = B.bucket_cur + blockIdx.x * kUbBuckets;
@@ -1265,7 +1275,27 @@ survivor_cut_kernel(const Scan2Batch B) {
         if (cosf(gmin) + 2.f * kCosMargin < lstar) atomicMin(&first, b);
     }
     __syncthreads();
-    if (threadIdx.x == 0) st->n_surv_eff = first < kUbBuckets ? bucket_end[first - 1] : st->n_surv;
+    if (threadIdx.x == 0) {
+        const int eff = first < kUbBuckets ? bucket_end[first - 1] : st->n_surv;
+        if (phase <= 1) {
+            st->n_surv_eff = eff;
+            st->n_first = phase == 1 ? (int)min((int64_t)eff, B.first_budget) : eff;
+        } else {
+            // after the first sweep (the highest bounds first, so the running
+            // lower bound has usually reached the maximum): with many
+            // survivors still left, the tensor-core map of every location is
+            // cheaper than their gathered evaluation
+            const int64_t left = (int64_t)eff - st->n_first;
+            if ((B.dense_frac < 0.f && left > 0) ||
+                (B.dense_frac > 0.f && (double)left > (double)B.dense_frac * (double)B.L)) {
+                st->dense = 1;
+                st->n_eval = (int)B.L;
+                st->n_surv_eff = st->n_first;
+            } else {
+                st->n_surv_eff = eff;
+            }
+        }
+    }
 }
 
 // Threshold refinement: FP32 rho at every member of the groups of the
@@ -1303,7 +1333,7 @@ group_members_kernel(const uint8_t *__restrict__ I, int q, int Ly, int Lx, int h
 
 __global__ void surv_candidates_kernel(const Scan2Batch B) {
     TmplState *st = B.st + blockIdx.y;
-    if (st->flat) return;
+    if (st->flat || st->dense) return;
     const int *surv = B.surv + blockIdx.y * B.scap;
     const float *surv_ub = B.surv_ub + blockIdx.y * B.scap;
     const float *surv_rho = B.surv_rho + blockIdx.y * B.scap;
@@ -1322,7 +1352,43 @@ __global__ void surv_candidates_kernel(const Scan2Batch B) {
     }
 }
 
+// Candidates of a template that took the dense map: every location whose
+// rho + eps reaches the certain lower bound (eps from the tensor-core map's
+// bound, ||I - 128|| / Omega from the window sum and 1/Omega).
+__global__ void dense_candidates_kernel(const Scan2Batch B, const int *__restrict__ wsum,
+                                        const float *__restrict__ inv_sigma, int mn, float epsA) {
+    TmplState *st = B.st + blockIdx.y;
+    if (st->flat || !st->dense) return;
+    const float *map = B.surv_rho + blockIdx.y * B.scap;
+    int *cand = B.cand + blockIdx.y * B.ccap;
+    const int cap = (int)B.ccap;
+    const float lstar = key_float(st->lo_key);
+    const float c128 = 128.f * (float)mn, imn = 1.f / (float)mn;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < B.L; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        bool f = false;
+        if (i < B.L) {
+            const float is = inv_sigma[i];
+            float eps = 0.f;
+            if (is > 0.f) {
+                const float d = ((float)wsum[i] - c128) * is;
+                eps = fmaf(epsA, sqrtf(fmaf(d * d, imn, 1.f)), 8.f * kU32);
+            }
+            f = map[i] + eps >= lstar;
+        }
+        warp_append(f, (int)i, &st->n_cand, cand, cap, &st->overflow);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_dense_candidates(const Scan2Batch &B, const int *wsum, const float *inv_sigma,
+                                    int m, int n, cudaStream_t s) {
+    LaunchScope ls("dense_candidates_kernel", s);
+    const int bx = std::max(1, num_sms() * 4 / std::min(B.T, 4));
+    dense_candidates_kernel<<<dim3(bx, B.T), 256, 0, s>>>(B, wsum, inv_sigma, m * n, brute_mma_epsA(m, n));
+    return cudaGetLastError();
+}
 
 static int grid_cap(int64_t n, int threads, int per_sm) {
     int64_t b = (n + threads - 1) / threads;
@@ -1544,31 +1610,10 @@ static size_t tmpl_smem(int m, int npad, int *in_smem) {
     return *in_smem ? smem : 0;
 }
 
-cudaError_t launch_survivors(const Scan2Batch &B, const uint8_t *I, int pimg, int q, int Lx,
-                             const int *wsum, int m, int n, int npad, const float *inv_sigma,
-                             cudaStream_t s) {
-    int in_smem = 0;
-    size_t smem = tmpl_smem(m, npad, &in_smem);
-    smem = (smem + 15) & ~(size_t)15;
-    // stage windows through shared memory when the template is there and the
-    // rows are narrow enough
-    const int WB = 16 * ((n + 30) / 16);
-    const int stage = in_smem && n <= 256 ? 1 : 0;
-    // (+16: a staged row's last word pair may reach 3 bytes past its row)
-    if (stage) smem += (size_t)8 * 2 * kStageRows * WB + 16;
-    {
-        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(survivors_kernel), smem);
-        if (e != cudaSuccess) return e;
-    }
-    const uint8_t *iend = I + (int64_t)q * pimg;
-    // buckets whose largest bound is below the certain lower bound already
-    // reached (threshold centres and their groups) are cut off, then one sweep
-    {
-        LaunchScope ls("survivor_cut_kernel", s);
-        survivor_cut_kernel<<<B.T, kUbBuckets, 0, s>>>(B);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+// One sweep (B.phase) over the survivor lists of a batch.
+static cudaError_t launch_sweep(const Scan2Batch &B, const uint8_t *I, int q, int Lx, const int *wsum,
+                                int m, int n, int npad, const float *inv_sigma, int in_smem, int stage,
+                                size_t smem, const uint8_t *iend, cudaStream_t s) {
     // one sweep for the whole batch: num_sms * 4 blocks for one template,
     // fewer per template (down to num_sms) when several share the launch
     const int bx = std::max(num_sms(), num_sms() * 4 / std::min(B.T, 4));
@@ -1590,6 +1635,45 @@ cudaError_t launch_survivors(const Scan2Batch &B, const uint8_t *I, int pimg, in
                                                           inv_sigma, in_smem, stage, iend);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_survivors(const Scan2Batch &B, const uint8_t *I, int pimg, int q, int Lx,
+                             const int *wsum, int m, int n, int npad, const float *inv_sigma,
+                             cudaStream_t s) {
+    int in_smem = 0;
+    size_t smem = tmpl_smem(m, npad, &in_smem);
+    smem = (smem + 15) & ~(size_t)15;
+    // stage windows through shared memory when the template is there and the
+    // rows are narrow enough
+    const int WB = 16 * ((n + 30) / 16);
+    const int stage = in_smem && n <= 256 ? 1 : 0;
+    // (+16: a staged row's last word pair may reach 3 bytes past its row)
+    if (stage) smem += (size_t)8 * 2 * kStageRows * WB + 16;
+    {
+        const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(survivors_kernel), smem);
+        if (e != cudaSuccess) return e;
+    }
+    const uint8_t *iend = I + (int64_t)q * pimg;
+    // buckets whose largest bound is below the certain lower bound already
+    // reached (threshold centres and their groups) are cut off, then one sweep
+    // -- or, with the dense path on, a first sweep over a bounded head of the
+    // list, a second cut that also decides the dense templates, and a second
+    // sweep over the rest of the others
+    const bool two = B.dense_frac != 0.f;
+    cudaError_t e;
+    for (int phase = two ? 1 : 0; phase <= (two ? 2 : 0); ++phase) {
+        Scan2Batch Bp = B;
+        Bp.phase = phase;
+        {
+            LaunchScope ls("survivor_cut_kernel", s);
+            survivor_cut_kernel<<<B.T, kUbBuckets, 0, s>>>(Bp, phase);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_sweep(Bp, I, q, Lx, wsum, m, n, npad, inv_sigma, in_smem, stage, smem, iend, s)) !=
+            cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_surv_candidates(const Scan2Batch &B, cudaStream_t s) {

@@ -121,16 +121,16 @@ ii_cols_kernel(int p, int q, T *o0, T *o1, T *o2) {
 }
 
 // Number of zero entries (flat windows: 1/Omega = 0) of the Ly x Lx map x,
-// over the rows EGS samples for group side h (every row when sample == 1).
+// over the rows EGS samples for group side h (every row when sample == 1):
+// rows over blockIdx.y (grid-strided), columns over the x threads.
 __global__ void count_zero_kernel(const float *__restrict__ x, int Ly, int Lx, int h, int sample,
                                   unsigned long long *count) {
     unsigned long long c = 0;
-    const int64_t n = (int64_t)Ly * Lx;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int row = (int)(i / Lx);
-        if (sample > 1 && ((row / h) / kEgsRun) % sample != 0) continue;
-        c += x[i] == 0.f ? 1 : 0;
+    for (int row = blockIdx.y; row < Ly; row += gridDim.y) {
+        if (sample > 1 && ((row / h) / kEgsRun) % sample != 0) continue;   // uniform
+        const float *xr = x + (int64_t)row * Lx;
+        for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < Lx; col += gridDim.x * blockDim.x)
+            c += xr[col] == 0.f ? 1 : 0;
     }
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
@@ -253,8 +253,10 @@ cudaError_t launch_integrals(const uint8_t *A, const uint8_t *B, int p, int q, l
 
 cudaError_t launch_count_zero(const float *x, int Ly, int Lx, int h, int sample,
                               unsigned long long *count, cudaStream_t s) {
+    const int bx = (Lx + 255) / 256;
+    const int by = std::max(1, std::min(Ly, (8 * num_sms() + bx - 1) / bx));
     LaunchScope ls("count_zero_kernel", s);
-    count_zero_kernel<<<grid_for((int64_t)Ly * Lx, 256), 256, 0, s>>>(x, Ly, Lx, h, sample, count);
+    count_zero_kernel<<<dim3(bx, by), 256, 0, s>>>(x, Ly, Lx, h, sample, count);
     return cudaGetLastError();
 }
 

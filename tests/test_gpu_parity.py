@@ -238,3 +238,48 @@ def test_search_is_deterministic(opta):
         for a, b in zip(first, again):
             assert (a["y"], a["x"], a["rho"], a["n_survivors"]) == (b["y"], b["x"], b["rho"], b["n_survivors"])
     h.close()
+
+
+# ---------------------------------------------------------------------------
+# Survivor-heavy templates: the dense tensor-core map instead of gathers
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("decay", [1.0, 0.5])
+def test_dense_survivor_path_matches_oracle(opta, decay):
+    """dense = 2 sends every template with a survivor left after the cut to
+    the tensor-core map of all its locations; the answers must meet the same
+    bar as the gathered survivors (dense = 0), including a flat template in
+    the batch, ragged sizes and a template wider than the map kernel's limit
+    (which keeps the gathers)."""
+    img = synth.aerial_image(400, n_octaves=7, n_prims=30, seed=71, decay=decay)[:400, :371].copy()
+    ts = synth.make_templates(img, [16, 24, (19, 29), 48, 64, 64, (40, 130)], seed=72, noise=3.0)
+    datas = [t.data for t in ts]
+    datas.insert(3, np.full((24, 24), 9.0, dtype=np.float32))
+    out = {}
+    for dense in (2, 0):
+        h = opta.optA_prepare(_cuda(img), opta.opta_params_default(dense=dense))
+        out[dense] = opta.optA_search(h, [_cuda(d) for d in datas], check=False)
+        h.close()
+    for i, d in enumerate(datas):
+        a, b = out[2][i], out[0][i]
+        if i == 3:
+            assert a.status == 2 and b.status == 2
+            continue
+        rho = ref.zncc_map(img, d)
+        _check_best(a, rho, f"dense {d.shape}")
+        _check_best(b, rho, f"gathers {d.shape}")
+        assert (a.y, a.x) == (b.y, b.x) or abs(rho[a.y, a.x] - rho[b.y, b.x]) <= TIE_TOL
+    # the dense path evaluated every location of the templates it took
+    assert any(r.n_evaluated == r.n_locations for r in out[2] if r.status == 0)
+
+
+def test_dense_path_by_the_cost_model_on_a_smooth_image(opta):
+    """On a smooth image (octave amplitudes 2^-o) the template noise keeps
+    the best rho low, few locations are eliminated and the cost model sends
+    templates to the dense map; results as the oracle's."""
+    img = synth.aerial_image(384, n_octaves=7, n_prims=20, seed=73, decay=0.5)
+    ts = synth.make_templates(img, [32, 48, 64, 96], seed=74, noise=3.0)
+    h = opta.optA_prepare(_cuda(img), opta.opta_params_default())
+    res = opta.optA_search(h, [_cuda(t.data) for t in ts])
+    h.close()
+    for t, r in zip(ts, res):
+        _check_best(r, ref.zncc_map(img, t.data), f"smooth {t.data.shape}")
