@@ -232,10 +232,17 @@ def run_case(spec: str):
         ts = [torch.from_numpy(t.data).cuda()
               for t in synth.make_templates(img, [(v, v)] * 32, seed=99, noise=3.0)]
         h = opta.optA_prepare(I, opta.opta_params_default(), sizes=[(v, v)])
-        for _ in range(2):
-            res = opta.optA_search(h, ts)
+        res = opta.optA_search(h, ts)
+        torch.cuda.synchronize()
+        opta.opta_dbg_profile_read()
+        opta.opta_dbg_profile_enable(True)
+        res = opta.optA_search(h, ts)
+        torch.cuda.synchronize()
+        opta.opta_dbg_profile_enable(False)
+        prof = opta.opta_dbg_profile_read()
         out = {"group_h": opta.optA_size_info(h, v, v)["group_h"],
-               "ok": all(r.status == 0 for r in res)}
+               "ok": all(r.status == 0 for r in res),
+               "corr_mma_ms": round(prof.get("corr_mma_kernel", (0.0, 0))[0], 4)}
         h.close()
     elif kind == "rho_co":
         R = torch.empty((p - 63) * (q - 63), dtype=torch.float32, device="cuda")

@@ -106,7 +106,7 @@ __device__ __forceinline__ ItemWords item_words(const uint8_t *row, int x, int q
     r.sh = (uint32_t)(ad & 3) * 8u;
     return r;
 }
-constexpr int kMaxRC = 8;   // centre rows per CTA (the launcher measures 1, 2, 3, 4, 6 and 8)
+constexpr int kMaxRC = 4;   // centre rows per CTA (the launcher measures 1, 2 and 4)
 
 __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaArgs a) {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -326,7 +326,7 @@ namespace {
 // Centre rows per CTA, in the order preferred before measurement: more rows
 // amortise each pivot row's operand build over more MMAs, fewer leave TMEM
 // room for more resident CTAs.
-constexpr int kRcs[] = {2, 1, 4, 3, 6, 8};
+constexpr int kRcs[] = {2, 1, 4};
 
 struct MmaTuneKey {
     int m, n, N, h, p, q;
