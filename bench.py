@@ -314,9 +314,11 @@ def main():
     prm = opta.opta_params_default()
 
     def step_device():
-        # one step: prepare the image for every size, search every template;
-        # the handle is released by the caller after the step's timing
-        h = opta.optA_prepare(dimg, prm, sizes=sizes, stream=stream)
+        # one step: prepare the image, search every template -- the search
+        # prepares the seven template sizes itself, each size's search
+        # starting as soon as that size is ready (beside the preparation of
+        # the others); the handle is released by the caller after the timing
+        h = opta.optA_prepare(dimg, prm, stream=stream)
         res = opta.optA_search(h, dts, stream=stream)
         return res, h
 
@@ -371,7 +373,8 @@ def main():
             dist.destroy_process_group()
         return 0
 
-    # search-only and prepare-only split (one extra step, not part of `value`)
+    # the same work with the sizes prepared before the search, to time the
+    # two phases apart (one extra step, not part of `value`)
     barrier()
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
     e2 = torch.cuda.Event(enable_timing=True)
@@ -457,7 +460,7 @@ def main():
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
-        hh = opta.optA_prepare(host_img, prm, sizes=sizes, stream=stream)
+        hh = opta.optA_prepare(host_img, prm, stream=stream)
         t1 = time.perf_counter()
         opta.optA_search(hh, host_ts, stream=stream)
         torch.cuda.synchronize()
@@ -533,7 +536,8 @@ def main():
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "image": f"{p}x{q} uint8", "templates": len(ts_all),
                    "template_sizes": "uniform over {16,24,32,48,64,96,128}",
-                   "step": "optA_prepare(7 sizes) + optA_search(256 templates)",
+                   "step": "optA_prepare(image) + optA_search(256 templates), the search preparing "
+                           "its 7 sizes beside the searches of the sizes already prepared",
                    "l2": "512 MiB buffer written before every timed step",
                    "parallelism": f"templates sharded over {world} GPU(s)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -652,31 +656,27 @@ def serving_report(opta, workers=4, max_batch=64, budget=64 << 30, seconds=5.0, 
 
 
 def step_report(opta, dimg, dts, sizes, prm, stream, flush, L_step, reps=2):
-    """One untimed and `reps` timed steps (prepare + search, L2 flushed before
-    each) with parameters prm: the median step, its split, and what the
-    preparation chose and the search kept."""
+    """One untimed and `reps` timed steps (prepare + search as the bench step
+    runs them, L2 flushed before each) with parameters prm: the median step,
+    and what the preparation chose and the search kept."""
     import torch
-    h = opta.optA_prepare(dimg, prm, sizes=sizes, stream=stream)
+    h = opta.optA_prepare(dimg, prm, stream=stream)
     opta.optA_search(h, dts, stream=stream)
     h.close()
-    times, split = [], []
+    times = []
     for _ in range(reps):
         flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-        e2 = torch.cuda.Event(enable_timing=True)
+        e0 = torch.cuda.Event(enable_timing=True); e2 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        h = opta.optA_prepare(dimg, prm, sizes=sizes, stream=stream)
-        e1.record(stream)
+        h = opta.optA_prepare(dimg, prm, stream=stream)
         res = opta.optA_search(h, dts, stream=stream)
         e2.record(stream)
         e2.synchronize()
         times.append(e0.elapsed_time(e2))
-        split.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
         info = {f"{m}x{n}": opta.optA_size_info(h, m, n) for (m, n) in sizes}
         h.close()
     k = int(np.argsort(times)[len(times) // 2])
     return {"ms_per_step": times[k], "value": L_step / (times[k] / 1000.0),
-            "split_ms": {"prepare": split[k][0], "search": split[k][1]},
             "group_sides": {s_: v["group_h"] for s_, v in info.items()},
             "blur_levels": {s_: v["level"] for s_, v in info.items()},
             "survivor_frac": float(np.mean([r.n_survivors / r.n_locations for r in res])),

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <algorithm>
 #include <atomic>
+#include <condition_variable>
 #include <map>
 #include <mutex>
 #include <new>
@@ -888,29 +889,47 @@ opta_status enqueue_scan2(opta_handle *H, opta_search_ctx *X, const opta_templat
     return OPTA_OK;
 }
 
-// Group templates by size (stable) and enqueue them chunk by chunk; order[i]
-// is the input index of the template whose state is states[i].
-opta_status enqueue_all(opta_handle *H, opta_search_ctx *X, const opta_template *t, int n_t, std::vector<int> &order,
-                        cudaStream_t s) {
+// Templates grouped by size (stable): order[k] is the input index of the
+// template whose state is states[k]; groups holds each size's [begin, end)
+// of states.
+void group_by_size(const opta_template *t, int n_t, std::vector<int> &order,
+                   std::vector<std::pair<int, int>> &groups) {
     order.resize(n_t);
     for (int i = 0; i < n_t; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         return std::make_pair(t[a].rows, t[a].cols) < std::make_pair(t[b].rows, t[b].cols);
     });
-    int i = 0;
-    std::vector<const opta_template *> chunk;
-    while (i < n_t) {
+    groups.clear();
+    for (int i = 0; i < n_t;) {
         int j = i;
+        while (j < n_t && t[order[j]].rows == t[order[i]].rows && t[order[j]].cols == t[order[i]].cols) ++j;
+        groups.emplace_back(i, j);
+        i = j;
+    }
+}
+
+// Scan 1 and scan 2 of the states [b, e) (templates of one size), chunk by chunk.
+opta_status enqueue_group(opta_handle *H, opta_search_ctx *X, const opta_template *t,
+                          const std::vector<int> &order, int b, int e, cudaStream_t s) {
+    std::vector<const opta_template *> chunk;
+    for (int i = b; i < e;) {
+        const int j = std::min(e, i + kChunk);
         chunk.clear();
-        while (j < n_t && (int)chunk.size() < kChunk && t[order[j]].rows == t[order[i]].rows &&
-               t[order[j]].cols == t[order[i]].cols) {
-            chunk.push_back(&t[order[j]]);
-            ++j;
-        }
+        for (int k = i; k < j; ++k) chunk.push_back(&t[order[k]]);
         TRY(enqueue_scan1(H, X, chunk.data(), (int)chunk.size(), X->states + i, s));
         TRY(enqueue_scan2(H, X, chunk.data(), (int)chunk.size(), X->states + i, nullptr, nullptr, s));
         i = j;
     }
+    return OPTA_OK;
+}
+
+// Group templates by size (stable) and enqueue them chunk by chunk; order[i]
+// is the input index of the template whose state is states[i].
+opta_status enqueue_all(opta_handle *H, opta_search_ctx *X, const opta_template *t, int n_t, std::vector<int> &order,
+                        cudaStream_t s) {
+    std::vector<std::pair<int, int>> groups;
+    group_by_size(t, n_t, order, groups);
+    for (const auto &g : groups) TRY(enqueue_group(H, X, t, order, g.first, g.second, s));
     return OPTA_OK;
 }
 
@@ -1053,6 +1072,96 @@ opta_status default_ctx(opta_handle *H) {
 // One search through context X (claimed by the caller): missing sizes are
 // prepared first (one preparation at a time per handle), then the prepared
 // sizes are read under a shared lock while the search's kernels run on s.
+// The search of templates t whose sizes `need` are not prepared yet: the
+// scratch is sized first (those sizes at their largest), the missing sizes
+// are prepared on worker threads, one stream each, while the search of every
+// size already prepared is enqueued on s, and each other size's search is
+// enqueued as soon as its preparation has finished -- so the search kernels
+// of ready sizes run beside the preparation of the others.  The caller holds
+// prep_mu; order receives the state order (see group_by_size).
+opta_status search_overlapped(opta_handle *H, opta_search_ctx *X, const opta_template *t, int n_t,
+                              const std::vector<std::pair<int, int>> &need, std::vector<int> &order,
+                              cudaStream_t s) {
+    {
+        std::shared_lock<std::shared_mutex> rl(H->sizes_rw);
+        TRY(size_scratch(H, X, t, n_t));
+    }
+    std::vector<std::pair<int, int>> groups;
+    group_by_size(t, n_t, order, groups);
+    cudaEvent_t ready = nullptr;
+    CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    CK(cudaEventRecord(ready, s));
+    std::mutex mu;
+    std::condition_variable cv;
+    size_t finished = 0;
+    std::vector<opta_status> st(need.size(), OPTA_OK);
+    std::atomic<size_t> next{0};
+    auto report = [&]() {
+        std::lock_guard<std::mutex> lk(mu);
+        ++finished;
+        cv.notify_one();
+    };
+    auto worker = [&]() {
+        cudaSetDevice(H->device);
+        cudaStream_t ws = nullptr;
+        if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamWaitEvent(ws, ready, 0) != cudaSuccess) {
+            cudaGetLastError();
+            for (size_t i = next++; i < need.size(); i = next++) {
+                st[i] = OPTA_ERR_CUDA;
+                report();
+            }
+            if (ws) cudaStreamDestroy(ws);
+            return;
+        }
+        for (size_t i = next++; i < need.size(); i = next++) {
+            st[i] = prepare_size(H, need[i].first, need[i].second, ws);
+            report();
+        }
+        cudaStreamSynchronize(ws);
+        cudaStreamDestroy(ws);
+    };
+    const size_t nth = std::min<size_t>(need.size(), 8);
+    std::vector<std::thread> threads;
+    try {
+        for (size_t k = 0; k < nth; ++k) threads.emplace_back(worker);
+    } catch (...) {
+        // no threads to be had: the sizes are prepared below, one by one
+    }
+    std::vector<char> queued(groups.size(), 0);
+    opta_status first = OPTA_OK;
+    // enqueue the search of every group whose size is prepared (once each)
+    auto enqueue_ready = [&]() {
+        std::shared_lock<std::shared_mutex> rl(H->sizes_rw);
+        for (size_t g = 0; g < groups.size(); ++g) {
+            if (queued[g]) continue;
+            const opta_template &t0 = t[order[groups[g].first]];
+            if (!size_of(H, std::make_pair(t0.rows, t0.cols))) continue;
+            queued[g] = 1;
+            if (first == OPTA_OK) first = enqueue_group(H, X, t, order, groups[g].first, groups[g].second, s);
+        }
+    };
+    enqueue_ready();
+    if (threads.empty()) {
+        worker();
+        enqueue_ready();
+    } else {
+        for (size_t seen = 0; seen < need.size();) {
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv.wait(lk, [&] { return finished > seen; });
+                seen = finished;
+            }
+            enqueue_ready();
+        }
+        for (auto &th : threads) th.join();
+    }
+    cudaEventDestroy(ready);
+    for (opta_status x : st)
+        if (x != OPTA_OK) return x;
+    return first;
+}
+
 opta_status search_in(opta_handle *H, opta_search_ctx *X, const opta_template *t, int32_t n_t,
                       opta_result *out, cudaStream_t s) {
     std::vector<std::pair<int, int>> todo;
@@ -1060,15 +1169,23 @@ opta_status search_in(opta_handle *H, opta_search_ctx *X, const opta_template *t
         if (!valid_template(&t[i], H->p, H->q)) return OPTA_ERR_INVALID_ARG;
         todo.emplace_back(t[i].rows, t[i].cols);
     }
+    std::vector<int> order;
     {
         std::lock_guard<std::mutex> pl(H->prep_mu);
-        TRY(prepare_sizes(H, todo, s));
+        if (n_t == 0) return prepare_sizes(H, todo, s);
+        std::vector<std::pair<int, int>> need;
+        for (const auto &k : todo)
+            if (!size_ready(H, k) && std::find(need.begin(), need.end(), k) == need.end()) need.push_back(k);
+        if (!need.empty()) {
+            // sizes prepared here overlap the search of the others
+            TRY(search_overlapped(H, X, t, n_t, need, order, s));
+        } else {
+            std::shared_lock<std::shared_mutex> rl0(H->sizes_rw);
+            TRY(size_scratch(H, X, t, n_t));
+            TRY(enqueue_all(H, X, t, n_t, order, s));
+        }
     }
-    if (n_t == 0) return OPTA_OK;
     std::shared_lock<std::shared_mutex> rl(H->sizes_rw);
-    TRY(size_scratch(H, X, t, n_t));
-    std::vector<int> order;
-    TRY(enqueue_all(H, X, t, n_t, order, s));
     CK(cudaMemcpyAsync(X->states_host, X->states, sizeof(TmplState) * n_t, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(X->err_host, X->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

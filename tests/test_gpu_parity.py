@@ -283,3 +283,25 @@ def test_dense_path_by_the_cost_model_on_a_smooth_image(opta):
     h.close()
     for t, r in zip(ts, res):
         _check_best(r, ref.zncc_map(img, t.data), f"smooth {t.data.shape}")
+
+
+def test_search_preparing_its_sizes_equals_prepared_search(opta):
+    """A search whose sizes are not prepared prepares them on worker threads
+    and starts each size's search as soon as it is ready; its answers equal
+    those of the same search on a handle whose sizes were prepared first,
+    and the oracle's."""
+    img = synth.aerial_image(448, n_octaves=7, n_prims=30, seed=81)
+    ts = synth.make_templates(img, [16, 24, 32, 48, 16, 24, (20, 36), 64], seed=82, noise=3.0)
+    dts = [_cuda(t.data) for t in ts]
+    sizes = sorted({t.data.shape for t in ts})
+    h1 = opta.optA_prepare(_cuda(img), opta.opta_params_default())            # image only
+    lazy = opta.optA_search(h1, dts)
+    again = opta.optA_search(h1, dts)                                       # now all prepared
+    h1.close()
+    h2 = opta.optA_prepare(_cuda(img), opta.opta_params_default(), sizes=sizes)
+    eager = opta.optA_search(h2, dts)
+    h2.close()
+    for t, a, b, c in zip(ts, lazy, again, eager):
+        assert (a.y, a.x, a.rho, a.group_h) == (c.y, c.x, c.rho, c.group_h)
+        assert (b.y, b.x, b.rho) == (c.y, c.x, c.rho)
+        _check_best(a, ref.zncc_map(img, t.data), f"lazy {t.data.shape}")
