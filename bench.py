@@ -60,7 +60,7 @@ def parse():
                     help="skip the serving report (four resident images, 4096^2 .. 16384^2)")
     ap.add_argument("--case", default=None,
                     help="one kernel for a profiler capture instead of the benchmark: "
-                         "scan1:<side>, rho_co:<h> or blur_corr:<side> (see run_case)")
+                         "scan1:<side>, rho_co:<h>, blur_corr:<side>, survforms:<n> ... (see run_case)")
     return ap.parse_args()
 
 
@@ -78,7 +78,8 @@ def workload(size: int, count: int):
     else:
         img = synth.aerial_image(size, n_octaves=max(3, int(np.log2(size)) - 3),
                                  n_prims=max(4, 800 * size * size // 4096 ** 2), seed=2004)
-        ts = synth.make_templates(img, synth.batch_sizes(count, 2104), seed=2104, noise=3.0)
+        ts = synth.make_templates(img, synth.batch_sizes(count, 2104), seed=2104, noise=3.0,
+                                  quantize=True)
     return img, ts
 
 
@@ -218,6 +219,10 @@ def run_case(spec: str):
                    (blur correlation, block flags only, as in the preparation)
     blur:<sigma>   the blur of every 64 x 64 block with one sigma (<= 3)
     brute:<s>      the exhaustive search (zncc_full) of one s x s template
+    survforms:<n>  the survivor evaluation of every template size of the batch
+                   at n locations (clusters of 5 x 5 like the group members
+                   the elimination test keeps), by each form (lane, warp) for
+                   a template of bytes and a real-valued one: kernel times
     """
     import torch
     import paper_1407_3535_gb300 as opta
@@ -230,7 +235,7 @@ def run_case(spec: str):
     out = {}
     if kind == "scan1":
         ts = [torch.from_numpy(t.data).cuda()
-              for t in synth.make_templates(img, [(v, v)] * 32, seed=99, noise=3.0)]
+              for t in synth.make_templates(img, [(v, v)] * 32, seed=99, noise=3.0, quantize=True)]
         h = opta.optA_prepare(I, opta.opta_params_default(), sizes=[(v, v)])
         res = opta.optA_search(h, ts)
         torch.cuda.synchronize()
@@ -257,7 +262,7 @@ def run_case(spec: str):
             opta.opta_dbg_blur_corr(P, I, v, v, None, lam=0.947350, block=64, fail_dev=F)
         out = {"failed_blocks": int(F.sum())}
     elif kind == "brute":
-        t = torch.from_numpy(synth.make_templates(img, [(v, v)], seed=99, noise=3.0)[0].data).cuda()
+        t = torch.from_numpy(synth.make_templates(img, [(v, v)], seed=99, noise=3.0, quantize=True)[0].data).cuda()
         r = opta.zncc_full(I, t)
         torch.cuda.synchronize()
         opta.opta_dbg_profile_read()
@@ -272,6 +277,37 @@ def run_case(spec: str):
         out = {"y": r.y, "x": r.x, "rho": r.rho, "candidates": r.n_candidates,
                "call_ms": a.elapsed_time(b),
                "kernels_ms": {k: round(v[0], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}}
+    elif kind == "survforms":
+        rng = np.random.default_rng(77)
+        count = int(v)
+        h = opta.optA_prepare(I, opta.opta_params_default(), sizes=[(b, b) for b in synth.BATCH_SIZES])
+        rows = []
+        for side in synth.BATCH_SIZES:
+            Ly, Lx = p - side + 1, q - side + 1
+            nc = (count + 24) // 25
+            cy = rng.integers(2, Ly - 2, size=nc); cx = rng.integers(2, Lx - 2, size=nc)
+            d = np.arange(-2, 3)
+            ys = (cy[:, None, None] + d[None, :, None] + 0 * d[None, None, :]).ravel()[:count]
+            xs = (cx[:, None, None] + 0 * d[None, :, None] + d[None, None, :]).ravel()[:count]
+            idx = torch.from_numpy((ys * Lx + xs).astype(np.int32)).cuda()
+            rho = torch.empty(idx.numel(), dtype=torch.float32, device="cuda")
+            eps = torch.empty_like(rho)
+            for quant in (True, False):
+                t = torch.from_numpy(synth.make_templates(img, [(side, side)], seed=99, noise=3.0,
+                                                          quantize=quant)[0].data).cuda()
+                row = {"side": side, "values": "bytes" if quant else "real"}
+                for form in (0, 1):
+                    opta.opta_dbg_survivors(h, t, idx, rho, eps, form=form)
+                    opta.opta_dbg_profile_read()
+                    opta.opta_dbg_profile_enable(True)
+                    opta.opta_dbg_survivors(h, t, idx, rho, eps, form=form)
+                    opta.opta_dbg_profile_enable(False)
+                    prof = opta.opta_dbg_profile_read()
+                    k = "survivors_lane_kernel" if form == 0 else "survivors_kernel"
+                    row["lane_ms" if form == 0 else "warp_ms"] = round(prof.get(k, (0.0, 0))[0], 4)
+                rows.append(row)
+        h.close()
+        out = {"count": count, "rows": rows}
     elif kind == "blur":
         P = torch.empty_like(I)
         for _ in range(2):
@@ -536,6 +572,7 @@ def main():
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "image": f"{p}x{q} uint8", "templates": len(ts_all),
                    "template_sizes": "uniform over {16,24,32,48,64,96,128}",
+                   "template_values": "8-bit: crop x gain + offset + N(0, 3^2), rounded, clipped to 0..255",
                    "step": "optA_prepare(image) + optA_search(256 templates), the search preparing "
                            "its 7 sizes beside the searches of the sizes already prepared",
                    "l2": "512 MiB buffer written before every timed step",
@@ -572,6 +609,10 @@ def main():
         "group_sizes": {k: v["group_h"] for k, v in size_info.items()},
         "per_size": per_size,
         "blur_levels": {k: v["level"] for k, v in size_info.items()},
+        # sweeps with at least this many survivors take the lane form (the
+        # tuner's measurement for templates of bytes / real values)
+        "survivor_lane_min": {k: [opta.opta_dbg_survivor_lane_min(*map(int, k.split("x")), u8)[0]
+                                  for u8 in (True, False)] for k in size_info},
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
@@ -605,7 +646,8 @@ def serving_report(opta, workers=4, max_batch=64, budget=64 << 30, seconds=5.0, 
     pools, locs_of = [], []
     for k, d in enumerate(dev_imgs):
         host = d.cpu().numpy()
-        ts_k = synth.make_templates(host, synth.batch_sizes(64, 2105 + k), seed=2105 + k, noise=3.0)
+        ts_k = synth.make_templates(host, synth.batch_sizes(64, 2105 + k), seed=2105 + k, noise=3.0,
+                                    quantize=True)
         pools.append([t.data for t in ts_k])
         locs_of.append({t.data.shape: (host.shape[0] - t.data.shape[0] + 1) * (host.shape[1] - t.data.shape[1] + 1)
                         for t in ts_k})
@@ -695,7 +737,8 @@ def sweep_report(opta, dimg, dts, sizes, stream, flush, L_step, n_templates):
         prm = opta.opta_params_default(rho_th=rth)
         sweep.append({"rho_th": rth, **step_report(opta, dimg, dts, sizes, prm, stream, flush, L_step)})
     img2 = synth.aerial_image(4096, n_octaves=9, n_prims=800, seed=2004, decay=0.5)
-    ts2 = synth.make_templates(img2, synth.batch_sizes(n_templates, 2104), seed=2104, noise=3.0)
+    ts2 = synth.make_templates(img2, synth.batch_sizes(n_templates, 2104), seed=2104, noise=3.0,
+                               quantize=True)
     d2 = torch.from_numpy(img2).cuda()
     dts2 = [torch.from_numpy(t.data).cuda() for t in ts2]
     smooth = step_report(opta, d2, dts2, sorted({t.data.shape for t in ts2}),

@@ -68,6 +68,29 @@ opta_status optA_debug_maps(opta_handle *h, int32_t m, int32_t n,
 opta_status optA_debug_scan1(opta_handle *h, const opta_template *t, int32_t n_t,
                              float *rho_dev, float *theta_dev, void *stream);
 
+/* The survivor evaluation of the search (Eq. rho1 at the locations that
+ * fail the elimination test of Eq. SEC) at chosen locations: rho_dev[i] and
+ * eps_dev[i] (count floats each, device) receive the FP32 rho of template t
+ * at location idx_dev[i] (linear index y * (q - n + 1) + x, device int32,
+ * each in 0 .. L - 1) and its error bound (|rho - exact| <= eps), computed
+ * by survivor form `form`: 0 one lane per location, 1 one warp per
+ * location, -1 the form the search takes for this size.  A template whose
+ * values are all integers in 0..255 takes the exact integer form of the
+ * numerator, any other the FP32 one.  Nothing is skipped.  Prepares the
+ * size if needed; synchronises `stream`.  OPTA_ERR_INVALID_ARG for a bad
+ * index range, count < 0 or count > L, or form outside -1..1. */
+opta_status opta_dbg_survivors(opta_handle *h, const opta_template *t, const int32_t *idx_dev,
+                               int64_t count, int32_t form, float *rho_dev, float *eps_dev,
+                               void *stream);
+
+/* The survivor-form threshold of an m x n size on the current device: a
+ * template (of bytes on the image itself: u8 = 1; any other: u8 = 0) whose
+ * survivor sweep has at least *lane_min entries takes the lane form, else the
+ * warp form.  *tuned = 1 when the value was measured by the tuner (the
+ * first search of the size on this device), 0 for the default rule. */
+opta_status opta_dbg_survivor_lane_min(int32_t m, int32_t n, int32_t u8, int32_t *lane_min,
+                                       int32_t *tuned);
+
 /* The kernels' int64 -> float conversion (FP32 pipe, no 64-bit conversion
  * instruction) applied to n device values: out_dev[i] = v_dev[i] rounded to
  * the nearest float (ties to even) for |v| < 2^46, within 1 ulp beyond. */

@@ -19,6 +19,7 @@ __all__ = [
     "zncc_full_noalloc",
     "optA_debug_bounds", "optA_size_info", "optA_memory_bytes", "optA_destroy",
     "optA_debug_maps", "opta_dbg_window_stats", "opta_dbg_blur", "opta_dbg_blur_corr", "opta_dbg_i64_to_f32",
+    "opta_dbg_survivors", "opta_dbg_survivor_lane_min",
     "opta_dbg_rho_co", "opta_dbg_launch_count", "opta_dbg_profile_enable", "opta_dbg_scan1_wait",
     "opta_dbg_profile_read", "optA_debug_scan1", "Handle", "lib", "OptaResult", "SearchContext", "SearchGraph", "Server",
 ]
@@ -391,6 +392,31 @@ def optA_debug_bounds(handle: Handle, template, ub_map=None, survived=None, stre
     if code not in (0, 2):
         raise OptaError(code, "optA_debug_bounds")
     return code
+
+
+def opta_dbg_survivors(handle: Handle, template, idx_dev, rho_dev, eps_dev, form: int = -1,
+                       stream=None) -> int:
+    """rho and its error bound at the locations idx_dev (int32 device tensor of
+    linear indices) by survivor form `form` (0 lane, 1 warp, -1 the search's);
+    returns the status (0, or 2 for a flat template)."""
+    t, k = _template(template)
+    n = idx_dev.numel()
+    code = lib().opta_dbg_survivors(handle.ptr, byref(t), c_void_p(idx_dev.data_ptr() if n else 0), n,
+                                    int(form), c_void_p(rho_dev.data_ptr() if n else 0),
+                                    c_void_p(eps_dev.data_ptr() if n else 0), _stream(stream))
+    del k
+    if code not in (0, 2):
+        raise OptaError(code, "opta_dbg_survivors")
+    return code
+
+
+def opta_dbg_survivor_lane_min(m: int, n: int, u8: bool) -> tuple:
+    """(lane_min, tuned) of an m x n size on the current device: sweeps with at
+    least lane_min entries take the lane form; tuned: measured by the tuner."""
+    lm, tu = c_int32(0), c_int32(0)
+    _check(lib().opta_dbg_survivor_lane_min(m, n, 1 if u8 else 0, byref(lm), byref(tu)),
+           "opta_dbg_survivor_lane_min")
+    return int(lm.value), bool(tu.value)
 
 
 def optA_size_info(handle: Handle, m: int, n: int) -> dict:

@@ -123,6 +123,9 @@ SIGNATURES = {
     "optA_debug_scan1": (c_int32, [c_void_p, POINTER(OptaTemplate), c_int32, c_void_p, c_void_p,
                                    c_void_p]),
     "opta_dbg_i64_to_f32": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p]),
+    "opta_dbg_survivors": (c_int32, [c_void_p, POINTER(OptaTemplate), c_void_p, c_int64, c_int32,
+                                     c_void_p, c_void_p, c_void_p]),
+    "opta_dbg_survivor_lane_min": (c_int32, [c_int32, c_int32, c_int32, POINTER(c_int32), POINTER(c_int32)]),
     "opta_dbg_launch_count": (ctypes.c_uint64, []),
     "opta_dbg_scan1_wait": (None, [ctypes.c_uint64, c_int32]),
     "opta_dbg_profile_enable": (None, [c_int32]),

@@ -126,6 +126,7 @@ struct opta_search_ctx {
     size_t capTS = 0, capB = 0, capRT = 0;    // template-slot, B-buffer, rho_tc capacities
     void *Bmma = nullptr;                     // bf16 hi/lo planes of a chunk (core-matrix layout)
     int *dev_err = nullptr;                   // set by a kernel whose bounded wait gave up
+    TmplState *tune_st = nullptr;             // the survivor-form tuner's template state
 };
 
 struct opta_handle {
@@ -738,7 +739,7 @@ ScratchPlan plan_scratch(opta_handle *H, const opta_template *t, int n_t) {
     for (int i = 0; i < n_t; ++i) count[std::make_pair(t[i].rows, t[i].cols)]++;
     for (auto &kv : count) {
         SizeState *S = size_of(H, kv.first);
-        const int m = kv.first.first, n = kv.first.second, npad = (n + 7) & ~7, Kp = (n + 15) & ~15;
+        const int m = kv.first.first, n = kv.first.second, Kp = (n + 15) & ~15;
         const size_t chunk = (size_t)std::min(kv.second, kChunk);
         const size_t L = (size_t)(H->p - m + 1) * (H->q - n + 1);
         const size_t G = S ? (size_t)S->Gy * S->Gx : L;
@@ -746,7 +747,7 @@ ScratchPlan plan_scratch(opta_handle *H, const opta_template *t, int n_t) {
         c.TB = std::max(c.TB, (size_t)scan2_batch(L, (int)chunk));
         c.RT = std::max(c.RT, chunk * G);
         c.T = std::max(c.T, chunk * (size_t)m * n);
-        c.TS = std::max(c.TS, chunk * (size_t)m * npad);
+        c.TS = std::max(c.TS, chunk * tmpl_slot_floats(m, n));
         const size_t N = ((2 * chunk + 15) / 16) * 16;
         if (use_mma(H)) c.B = std::max(c.B, (size_t)m * Kp * N * 2);
         // the template tiles of a scan-2 launch that may take the dense map
@@ -770,7 +771,7 @@ opta_status enqueue_scan1(opta_handle *H, opta_search_ctx *X, const opta_templat
     const int m = t[0]->rows, nn = t[0]->cols, npad = (nn + 7) & ~7, Kp = (nn + 15) & ~15;
     SizeState *S = size_of(H, std::make_pair(m, nn));
     const int64_t G = (int64_t)S->Gy * S->Gx;
-    const size_t tsz = (size_t)m * npad, dsz = (size_t)m * nn;
+    const size_t tsz = tmpl_slot_floats(m, nn), dsz = (size_t)m * nn;
     // template statistics (Eq. rho1's mu_t, sigma_t) of the whole chunk in one launch
     const ptrdiff_t slot0 = st - X->states;
     TmplIn *tin = X->tin_host + slot0;
@@ -818,6 +819,147 @@ opta_status enqueue_scan1(opta_handle *H, opta_search_ctx *X, const opta_templat
     return OPTA_OK;
 }
 
+// Scan-2 launch descriptor of templates k0 .. k0 + T of a chunk (states st)
+// of size S, over the context's scratch; no dense map (dense_frac 0).
+Scan2Batch scan2_batch_of(opta_handle *H, opta_search_ctx *X, SizeState *S, TmplState *st, int k0,
+                          int T) {
+    const int m = S->m, nn = S->n;
+    const int64_t L = (int64_t)S->Ly * S->Lx;
+    const int64_t G = (int64_t)S->Gy * S->Gx;
+    const size_t tsz = tmpl_slot_floats(m, nn);
+    Scan2Batch B;
+    B.T = T;
+    B.st = st + k0;
+    B.rho_tc = X->rho_tc + k0 * G;
+    B.tc_stride = G;
+    B.c_efac = S->c_efac;
+    B.epsA = scan1_eps_factor(H, m, nn);
+    B.tf = X->tf + k0 * tsz;
+    B.tsz = tsz;
+    B.surv = X->surv;
+    B.surv_ub = X->surv_ub;
+    B.surv_rho = X->surv_rho;
+    B.surv_eps = X->surv_eps;
+    B.scap = (int64_t)X->capL;
+    B.cand = X->cand;
+    B.ccap = (int64_t)X->capL;
+    B.ucnt = X->ucnt;
+    B.bucket_cnt = X->bucket_cnt;
+    B.bucket_cur = X->bucket_cur;
+    B.L = L;
+    B.dense_frac = 0.f;
+    // the first sweep: about a quarter of the dense map's cost (none when
+    // every template with a survivor is to take the dense map)
+    B.first_budget = H->prm.dense == 2
+                         ? 0
+                         : std::max<int64_t>(1024, (int64_t)(20.0 * (double)L / ((double)m * nn)));
+    B.phase = 0;
+    // survivors of byte templates on the image itself: exact integer sums
+    // over the 16-byte-aligned copy
+    B.Ipad = S->M == H->I8 ? H->Ipad : nullptr;
+    B.qs = H->qs;
+    B.lane_min_u8 = survivor_lane_min(m, nn, true);
+    B.lane_min_f32 = survivor_lane_min(m, nn, false);
+    return B;
+}
+
+// Survivor-form tuner.  The lane form (a lane per survivor) has a long
+// serial chain per lane and wins once there are enough survivors to fill
+// the GPU; the warp form (a warp per survivor) wins on short lists.  The
+// first search of a size on a device (outside graph capture) times both on
+// synthetic lists of c1 and c2 locations (clusters of 5 x 5, like the
+// members of the groups the elimination test keeps) with the batch's first
+// template, fits time = a + b count per form and records the count from
+// which the lane form is faster, for templates of bytes (when the template
+// is one) and for the FP32 path.
+opta_status tune_survivor_forms(opta_handle *H, opta_search_ctx *X, SizeState *S, TmplState *st, int k0,
+                                cudaStream_t s) {
+    const int m = S->m, nn = S->n, npad = (nn + 7) & ~7;
+    bool t8 = false, t32 = false;
+    survivor_lane_min(m, nn, true, &t8);
+    survivor_lane_min(m, nn, false, &t32);
+    if (t8 && t32) return OPTA_OK;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) { cudaGetLastError(); return OPTA_OK; }
+    if (cap != cudaStreamCaptureStatusNone) return OPTA_OK;
+    const int64_t L = (int64_t)S->Ly * S->Lx;
+    const int c2 = (int)std::min<int64_t>(L, 32768), c1 = std::min(c2 / 16, 2048);
+    if (c1 < 256) return OPTA_OK;   // small maps: the default rule
+    if (!X->tune_st) TRY(X->mem.alloc(&X->tune_st, 1));
+    // the synthetic list: c2 / 25 cluster centres, seeded
+    std::vector<int> idx;
+    idx.reserve((size_t)c2);
+    uint64_t r = 0x9e3779b97f4a7c15ull;
+    auto next = [&r]() { r ^= r << 13; r ^= r >> 7; r ^= r << 17; return r; };
+    while ((int)idx.size() < c2) {
+        const int cy = 2 + (int)(next() % (uint64_t)std::max(1, S->Ly - 4));
+        const int cx = 2 + (int)(next() % (uint64_t)std::max(1, S->Lx - 4));
+        for (int dy = -2; dy <= 2; ++dy)
+            for (int dx = -2; dx <= 2; ++dx) {
+                const int y = std::min(std::max(cy + dy, 0), S->Ly - 1);
+                const int x = std::min(std::max(cx + dx, 0), S->Lx - 1);
+                if ((int)idx.size() < c2) idx.push_back(y * S->Lx + x);
+            }
+    }
+    CK(cudaMemcpyAsync(X->surv, idx.data(), (size_t)c2 * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(X->tune_st, st + k0, sizeof(TmplState), cudaMemcpyDeviceToDevice, s));
+    TmplState hs;
+    CK(cudaMemcpyAsync(&hs, st + k0, sizeof(TmplState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hs.flat) return OPTA_OK;
+    Scan2Batch B = scan2_batch_of(H, X, S, st, k0, 1);
+    B.st = X->tune_st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); cudaGetLastError(); return OPTA_ERR_CUDA; }
+    auto timed = [&](int count, int form, float *ms) -> cudaError_t {
+        float best = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaError_t e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess)
+                e = launch_survivor_eval(B, S->M, H->p, H->q, S->Lx, S->wsumM, m, nn, npad, S->invM, count,
+                                         form, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float t = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (e != cudaSuccess) return e;
+            best = std::min(best, t);
+        }
+        *ms = best;
+        return cudaSuccess;
+    };
+    cudaError_t e = cudaSuccess;
+    for (int type = 1; type >= 0 && e == cudaSuccess; --type) {
+        const bool u8 = type == 1;
+        if ((u8 && (t8 || !hs.u8 || !B.Ipad)) || (!u8 && t32)) continue;
+        const int flag = u8 ? 1 : 0;   // the FP32 path: the same template as real values
+        e = cudaMemcpyAsync(&X->tune_st->u8, &flag, sizeof(int), cudaMemcpyHostToDevice, s);
+        float t[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+        for (int form = 0; form < 2 && e == cudaSuccess; ++form) {
+            float w = 0.f;
+            e = timed(c1, form, &w);   // first launches of the kernels
+            if (e == cudaSuccess) e = timed(c1, form, &t[form][0]);
+            if (e == cudaSuccess) e = timed(c2, form, &t[form][1]);
+        }
+        if (e != cudaSuccess) break;
+        const double bl = (t[0][1] - t[0][0]) / (double)(c2 - c1), al = t[0][0] - bl * c1;
+        const double bw = (t[1][1] - t[1][0]) / (double)(c2 - c1), aw = t[1][0] - bw * c1;
+        int lane_min;
+        if (bw > bl) {
+            const double c = (al - aw) / (bw - bl);
+            lane_min = c <= 0.0 ? 0 : (int)std::min<double>(std::ceil(c), (double)kLaneNever - 1);
+        } else {
+            lane_min = al <= aw ? 0 : kLaneNever;
+        }
+        set_survivor_lane_min(m, nn, u8, lane_min);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) { cudaGetLastError(); return map_err(e); }
+    return OPTA_OK;
+}
+
 // Scan 2 (Eq. SEC), survivors and FP64 argmax of the chunk whose scan 1 and
 // threshold are done, in batches of scan2_batch() templates per launch.
 opta_status enqueue_scan2(opta_handle *H, opta_search_ctx *X, const opta_template *const *t, int n, TmplState *st,
@@ -825,41 +967,16 @@ opta_status enqueue_scan2(opta_handle *H, opta_search_ctx *X, const opta_templat
     const int m = t[0]->rows, nn = t[0]->cols, npad = (nn + 7) & ~7;
     SizeState *S = size_of(H, std::make_pair(m, nn));
     const int64_t L = (int64_t)S->Ly * S->Lx;
-    const int64_t G = (int64_t)S->Gy * S->Gx;
-    const size_t tsz = (size_t)m * npad, dsz = (size_t)m * nn;
+    const size_t tsz = tmpl_slot_floats(m, nn), dsz = (size_t)m * nn;
     const int TB = std::min(scan2_batch((size_t)L, n), (int)X->capS2);
     const int64_t scap = (int64_t)X->capL;
     const bool dense = dense_usable(H, m, nn) && S->M == H->I8;
     if (TB < 1 || ((ub_map || surv_map) && n != 1)) return OPTA_ERR_INVALID_ARG;
     for (int k0 = 0; k0 < n; k0 += TB) {
         const int T = std::min(TB, n - k0);
-        Scan2Batch B;
-        B.T = T;
-        B.st = st + k0;
-        B.rho_tc = X->rho_tc + k0 * G;
-        B.tc_stride = G;
-        B.c_efac = S->c_efac;
-        B.epsA = scan1_eps_factor(H, m, nn);
-        B.tf = X->tf + k0 * tsz;
-        B.tsz = tsz;
-        B.surv = X->surv;
-        B.surv_ub = X->surv_ub;
-        B.surv_rho = X->surv_rho;
-        B.surv_eps = X->surv_eps;
-        B.scap = scap;
-        B.cand = X->cand;
-        B.ccap = scap;
-        B.ucnt = X->ucnt;
-        B.bucket_cnt = X->bucket_cnt;
-        B.bucket_cur = X->bucket_cur;
-        B.L = L;
+        if (k0 == 0 && !(ub_map || surv_map)) TRY(tune_survivor_forms(H, X, S, st, k0, s));
+        Scan2Batch B = scan2_batch_of(H, X, S, st, k0, T);
         B.dense_frac = dense ? dense_frac(H, m, nn) : 0.f;
-        // the first sweep: about a quarter of the dense map's cost (none when
-        // every template with a survivor is to take the dense map)
-        B.first_budget = H->prm.dense == 2
-                             ? 0
-                             : std::max<int64_t>(1024, (int64_t)(20.0 * (double)L / ((double)m * nn)));
-        B.phase = 0;
         CK(launch_bound_compact(B, S->theta_co, S->gco, S->Ly, S->Lx, S->h, ub_map, surv_map, s));
         // the survivor cut marks the templates with many survivors left as
         // dense; the sweep skips them
@@ -867,7 +984,7 @@ opta_status enqueue_scan2(opta_handle *H, opta_search_ctx *X, const opta_templat
         if (dense) {
             // their rho at every location on the tensor cores (templates not
             // marked are skipped on the device), into their rho slots
-            CK(launch_brute_tmpl(X->tf + k0 * tsz, tsz, T, m, nn, npad, X->Bmma, st + k0, s));
+            CK(launch_brute_tmpl(X->tf + k0 * tsz, tsz, T, m, nn, npad, X->Bmma, st + k0, 1, s));
             CK(launch_brute_mma(H->Ipad, H->qs, H->p, H->q, X->Bmma, m, nn, S->invM, nullptr, S->wsumM,
                                 st + k0, X->surv_rho, scap, T, 1, X->dev_err, s));
             CK(launch_dense_candidates(B, S->wsumM, S->invM, m, nn, s));
@@ -970,17 +1087,17 @@ opta_status exhaustive_run(const uint8_t *I8, int p, int q, const float *tdev, i
     cudaError_t e;
 #define XCK(x) do { if ((e = (x)) != cudaSuccess) return map_err(e); } while (0)
     XCK(launch_integrals(I8, nullptr, p, q, b.IIS, b.IIQ, nullptr, s));
-    XCK(launch_window_stats(b.IIS, b.IIQ, p, q, m, n, b.inv, b.ef, s));
+    XCK(launch_window_stats(b.IIS, b.IIQ, p, q, m, n, b.inv, b.ef, s, b.wsum));
     XCK(launch_tmpl_prep(tdev, tld, m, n, npad, b.tf, b.td, b.st, 0, s));
-    const bool tc = b.Ipad && b.Bt && b.err && brute_mma_supported(m, n);
+    const bool tc = b.Ipad && b.Bt && b.err && b.wsum && brute_mma_supported(m, n);
     float epsA;
     if (tc) {
         // the map on the tensor cores (bf16 hi/lo split of t', FP32 accumulation)
         const int qs = (q + 15) & ~15;
         XCK(cudaMemsetAsync(b.err, 0, sizeof(int), s));
         XCK(launch_pad_rows(I8, p, q, b.Ipad, qs, s));
-        XCK(launch_brute_tmpl(b.tf, 0, 1, m, n, npad, b.Bt, nullptr, s));
-        XCK(launch_brute_mma(b.Ipad, qs, p, q, b.Bt, m, n, b.inv, b.ef, nullptr, b.st, b.map, 0, 1, 0,
+        XCK(launch_brute_tmpl(b.tf, 0, 1, m, n, npad, b.Bt, b.st, 0, s));
+        XCK(launch_brute_mma(b.Ipad, qs, p, q, b.Bt, m, n, b.inv, b.ef, b.wsum, b.st, b.map, 0, 1, 0,
                              b.err, s));
         epsA = brute_mma_epsA(m, n);
     } else {
@@ -1024,7 +1141,7 @@ void free_ctx(opta_search_ctx *X) {
     void *ptrs[] = {X->rho_tc, X->surv, X->surv_rho, X->surv_eps, X->surv_ub, X->ucnt,
                     X->bucket_cnt, X->bucket_cur, X->Bmma, X->dev_err, X->cand_topk,
                     X->cand_rho_topk, X->tin, X->cand, X->cand_rho, X->topk_v, X->topk_i,
-                    X->tf, X->tstage, X->td, X->states};
+                    X->tf, X->tstage, X->td, X->states, X->tune_st};
     for (void *p : ptrs) if (p) cudaFree(p);
     if (X->tin_host) cudaFreeHost(X->tin_host);
     if (X->states_host) cudaFreeHost(X->states_host);
@@ -1586,6 +1703,59 @@ opta_status optA_debug_bounds(opta_handle *h, const opta_template *t, float *ub_
     return st.flat ? OPTA_ERR_FLAT_TEMPLATE : OPTA_OK;
 }
 
+opta_status opta_dbg_survivor_lane_min(int32_t m, int32_t n, int32_t u8, int32_t *lane_min,
+                                       int32_t *tuned) {
+    if (m < 1 || n < 1 || !lane_min) return OPTA_ERR_INVALID_ARG;
+    bool t = false;
+    *lane_min = survivor_lane_min(m, n, u8 != 0, &t);
+    if (tuned) *tuned = t ? 1 : 0;
+    return OPTA_OK;
+}
+
+opta_status opta_dbg_survivors(opta_handle *h, const opta_template *t, const int32_t *idx_dev,
+                               int64_t count, int32_t form, float *rho_dev, float *eps_dev,
+                               void *stream) {
+    if (!h || !t || count < 0 || form < -1 || form > 1) return OPTA_ERR_INVALID_ARG;
+    if (count > 0 && (!idx_dev || !rho_dev || !eps_dev)) return OPTA_ERR_INVALID_ARG;
+    if (!valid_template(t, h->p, h->q)) return OPTA_ERR_INVALID_ARG;
+    const int m = t->rows, nn = t->cols, npad = (nn + 7) & ~7;
+    const int64_t L = (int64_t)(h->p - m + 1) * (h->q - nn + 1);
+    if (count > L || count > INT32_MAX) return OPTA_ERR_INVALID_ARG;
+    if (h->busy) return OPTA_ERR_BUSY;
+    BusyGuard guard(h);
+    TRY(default_ctx(h));
+    opta_search_ctx *X = h->dctx;
+    bool idle = false;
+    if (!X->busy.compare_exchange_strong(idle, true)) return OPTA_ERR_BUSY;
+    CtxGuard cg(X);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    {
+        std::lock_guard<std::mutex> pl(h->prep_mu);
+        TRY(prepare_size(h, m, nn, s));
+    }
+    std::shared_lock<std::shared_mutex> rl(h->sizes_rw);
+    TRY(size_scratch(h, X, t, 1));
+    if (count == 0) return OPTA_OK;
+    // every index inside the location map before any kernel reads through it
+    std::vector<int32_t> hidx((size_t)count);
+    CK(cudaMemcpyAsync(hidx.data(), idx_dev, (size_t)count * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int32_t v : hidx)
+        if (v < 0 || (int64_t)v >= L) return OPTA_ERR_INVALID_ARG;
+    SizeState *S = size_of(h, std::make_pair(m, nn));
+    const opta_template *one = t;
+    TRY(enqueue_scan1(h, X, &one, 1, X->states, s));
+    CK(cudaMemcpyAsync(X->surv, idx_dev, (size_t)count * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    const Scan2Batch B = scan2_batch_of(h, X, S, X->states, 0, 1);
+    CK(launch_survivor_eval(B, S->M, h->p, h->q, S->Lx, S->wsumM, m, nn, npad, S->invM, (int)count, form, s));
+    CK(cudaMemcpyAsync(rho_dev, X->surv_rho, (size_t)count * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(eps_dev, X->surv_eps, (size_t)count * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    TmplState st;
+    CK(cudaMemcpyAsync(&st, X->states, sizeof(st), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return st.flat ? OPTA_ERR_FLAT_TEMPLATE : OPTA_OK;
+}
+
 opta_status optA_debug_scan1(opta_handle *h, const opta_template *t, int32_t n_t,
                              float *rho_dev, float *theta_dev, void *stream) {
     if (!h || !t || n_t < 1 || n_t > kChunk) return OPTA_ERR_INVALID_ARG;
@@ -1758,10 +1928,12 @@ opta_status zncc_full(const opta_image *img, const opta_template *t, float *rho_
     uint8_t *Ipad = nullptr;
     void *Bt = nullptr;
     int *err = nullptr;
+    int *wsum = nullptr;
     if (brute_mma_supported(m, n)) {
         ZCK(A(&Ipad, (size_t)p * ((q + 15) & ~15)));
         ZCK(A(&Bt, brute_tmpl_bytes(m, n)));
         ZCK(A(&err, sizeof(int)));
+        ZCK(A(&wsum, L * sizeof(int)));
     }
     const float *tdev = t->data;
     int64_t ld = t->stride_elems;
@@ -1773,7 +1945,7 @@ opta_status zncc_full(const opta_image *img, const opta_template *t, float *rho_
         tdev = tst;
         ld = n;
     }
-    const ExhaustiveBufs bufs{IIS, IIQ, inv, ef, map, tf, td, cand, cand_rho, st, Ipad, Bt, err};
+    const ExhaustiveBufs bufs{IIS, IIQ, inv, ef, map, tf, td, cand, cand_rho, st, Ipad, Bt, err, wsum};
     return finish(exhaustive_run(I8, p, q, tdev, ld, m, n, bufs, best, s));
 #undef ZCK
 }

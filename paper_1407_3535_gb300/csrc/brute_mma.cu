@@ -94,7 +94,8 @@ struct BruteArgs {
     const __nv_bfloat16 *B;     // template k's tile at B + k * (bbytes / 2): [2Kp/8][NB/8][8][8]
     const float *inv_sigma;     // 1/Omega per location (0: flat window)
     const float *efac;          // ||I - 128|| / Omega per location (null: from wsum)
-    const int *wsum;            // window sums (with inv_sigma, when efac is null)
+    const int *wsum;            // window sums (the integer operand's mean term; the
+                                // error factor when efac is null)
     TmplState *st;              // template k's state at st + k
     float *map;                 // template k's map at map + k * map_stride
     int64_t map_stride;
@@ -306,6 +307,7 @@ brute_mma_kernel(const __grid_constant__ CUtensorMap tmap, const BruteArgs a) {
             const int x = x0 + wl * 32 + lane;
             const bool xv = x < a.Lx;
             const float inv_t = st->inv_sigma;
+            const float c0 = st->c0;   // integer operand: t' = (t - rint(mu)) + c0
             const float c128 = 128.f * (float)(a.m * a.n), imn = 1.f / (float)(a.m * a.n);
             float *map = a.map + (int64_t)z * a.map_stride;
             float lo = -3.f;
@@ -330,7 +332,10 @@ brute_mma_kernel(const __grid_constant__ CUtensorMap tmap, const BruteArgs a) {
                     if (k0 + c > kb || y < y0 || y >= yend || !xv) continue;
                     const int64_t idx = (int64_t)y * a.Lx + x;
                     const float is = a.inv_sigma[idx];
-                    const float rho = (v[c] * inv_t) * is;
+                    // sum t'(I - 128) = sum (t - rint(mu))(I - 128) + c0 (S - 128 mn),
+                    // S - 128 mn exact (integers below 2^24)
+                    const float acc = c0 != 0.f ? fmaf(c0, (float)a.wsum[idx] - c128, v[c]) : v[c];
+                    const float rho = (acc * inv_t) * is;
                     map[idx] = rho;
                     if (is > 0.f) {
                         float ef;
@@ -368,10 +373,23 @@ brute_mma_kernel(const __grid_constant__ CUtensorMap tmap, const BruteArgs a) {
 // t' (FP32, m x npad) -> the template tile of NB = N + 32 rows: row 16 + j
 // holds template row m-1-j (j < m), every other row is zero; K halves
 // hi | lo of the bf16 split, zeros past n columns.
+// A template of integers in 0..255 with sigma_t >= sqrt(mn) / 6 (int_op)
+// takes instead hi = t - rint(mu) (an integer of at most 8 significant bits:
+// exact in bf16) and lo = 0; the epilogue adds c0 (S - 128 mn) with
+// c0 = rint(mu) - mu.  Its products are then exact and only the FP32
+// accumulation rounds: at most m Kp / 16 steps of u |partial sum|, i.e.
+// (m Kp / 16) u (||hi|| / sigma_t) ||I - 128|| / Omega with ||hi|| <=
+// sigma_t + sqrt(mn) / 2 <= 4 sigma_t, plus the correction's few roundings
+// (each below u ||I - 128|| sqrt(mn) / 2 / (sigma_t Omega) <= 3 u efac):
+// within the split's bound brute_mma_epsA, which allows (8 m Kp / 16 + 16) u
+// efac besides the split's residual term.
 __global__ void brute_tmpl_kernel(const float *__restrict__ tf, size_t tsz, int m, int n, int npad,
-                                  int Kp, int NB, const TmplState *st, __nv_bfloat16 *B) {
-    // template blockIdx.y (with st: only templates marked dense)
-    if (st && !st[blockIdx.y].dense) return;
+                                  int Kp, int NB, const TmplState *st, int dense_only,
+                                  __nv_bfloat16 *B) {
+    // template blockIdx.y (dense_only: only templates marked dense)
+    if (dense_only && !st[blockIdx.y].dense) return;
+    const bool int_op = st[blockIdx.y].int_op != 0;
+    const float c0 = st[blockIdx.y].c0;
     tf += blockIdx.y * tsz;
     const int total = NB * 2 * Kp;
     B += (size_t)blockIdx.y * total;
@@ -381,8 +399,12 @@ __global__ void brute_tmpl_kernel(const float *__restrict__ tf, size_t tsz, int 
         const int u = m - 1 - (jj - 16);
         float x = 0.f;
         if (jj >= 16 && u >= 0 && v < n) x = tf[u * npad + v];
+        // t - rint(mu) = t' - c0, recovered exactly by rounding (t' is t - mu
+        // within 255 u)
+        if (int_op) x = rintf(x - c0);
         const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-        const __nv_bfloat16 part = kk < Kp ? hi : __float2bfloat16_rn(x - __bfloat162float(hi));
+        const __nv_bfloat16 part =
+            kk < Kp ? hi : (int_op ? __float2bfloat16_rn(0.f) : __float2bfloat16_rn(x - __bfloat162float(hi)));
         B[((int64_t)(kk / 8) * (NB / 8) + jj / 8) * 64 + (jj % 8) * 8 + kk % 8] = part;
     }
 }
@@ -426,12 +448,13 @@ float brute_mma_epsA(int m, int n) {
 }
 
 cudaError_t launch_brute_tmpl(const float *tf, size_t tsz, int T, int m, int n, int npad, void *B,
-                              const TmplState *dense_of, cudaStream_t s) {
+                              const TmplState *st, int dense_only, cudaStream_t s) {
+    if (!st) return cudaErrorInvalidValue;
     const BruteGeom g = brute_geom(m, n);
     const int total = g.NB * 2 * g.Kp;
     LaunchScope ls("brute_tmpl_kernel", s);
     brute_tmpl_kernel<<<dim3((total + 255) / 256, T), 256, 0, s>>>(tf, tsz, m, n, npad, g.Kp, g.NB,
-                                                                  dense_of,
+                                                                  st, dense_only,
                                                                   static_cast<__nv_bfloat16 *>(B));
     return cudaGetLastError();
 }
@@ -448,8 +471,7 @@ cudaError_t launch_brute_mma(const uint8_t *Ipad, int qs, int p, int q, const vo
                              const float *inv_sigma, const float *efac, const int *wsum,
                              TmplState *st, float *map, int64_t map_stride, int T, int dense_only,
                              int *err, cudaStream_t s) {
-    if (!brute_mma_supported(m, n) || qs % 16 != 0 || qs < q || T < 1 || T > 65535 ||
-        (!efac && !wsum))
+    if (!brute_mma_supported(m, n) || qs % 16 != 0 || qs < q || T < 1 || T > 65535 || !wsum)
         return cudaErrorInvalidValue;
     const BruteGeom g = brute_geom(m, n);
     const int Ly = p - m + 1, Lx = q - n + 1;

@@ -140,7 +140,19 @@ struct TmplState {
     int n_cand_search;        // literal mode: candidates of the search before the re-match
     int dense;                // 1: every location's rho from the tensor-core map, no gathers
     int n_first;              // survivors the first sweep takes (two-phase sweep)
+    int u8;                   // every template value an integer in 0..255 (bytes packed)
+    int sum_t;                // sum of the template values (exact when u8)
+    int int_op;               // exhaustive map: integer operand t - rint(mu) (see brute_mma.cu)
+    float c0;                 // rint(mu) - mu when int_op, else 0
 };
+
+// Floats of one template's slot in a batch: the centred FP32 template (m rows
+// of npad = round_up(n, 8)) and then its values as bytes, four to a 32-bit
+// word, in rows of round_up(n, 16) bytes with zeros past column n (written
+// and meaningful only when TmplState::u8).
+__host__ __device__ inline size_t tmpl_slot_floats(int m, int n) {
+    return (size_t)m * ((n + 7) & ~7) + (size_t)m * ((n + 15) & ~15) / 4;
+}
 
 // Survivors are bucketed by their upper bound (bucket 0 = highest) so that
 // they are evaluated roughly in decreasing bound order.
@@ -185,7 +197,8 @@ cudaError_t launch_ingest_u8(const uint8_t *src, int64_t ld, int p, int q, uint8
 // Template statistics: tf (m x npad, FP32, zero padded) and td (m x n, FP64) hold t - mu.
 cudaError_t launch_tmpl_prep(const float *t, int64_t ld, int m, int n, int npad,
                              float *tf, double *td, TmplState *st, int topk, cudaStream_t s);
-// The same for T templates (tin: T device descriptors), outputs at k * tsz / k * dsz / st + k.
+// The same for T templates (tin: T device descriptors), outputs at k * tsz / k * dsz / st + k;
+// tsz = tmpl_slot_floats(m, n): each slot also receives the packed bytes.
 cudaError_t launch_tmpl_prep_batch(const TmplIn *tin, int T, int m, int n, int npad, float *tf,
                                    size_t tsz, double *td, size_t dsz, TmplState *st, int topk,
                                    cudaStream_t s);
@@ -277,6 +290,11 @@ struct Scan2Batch {
     int64_t first_budget;                // survivors of the first sweep (dense_frac != 0)
     int64_t L;                           // locations per template
     int phase;                           // sweep: 0 all, 1 the first n_first, 2 the rest
+    const uint8_t *Ipad;                 // the search image with rows of qs bytes (16-byte
+    int qs;                              // aligned), or null: integer survivors path off
+    int lane_min_u8, lane_min_f32;       // a template whose sweep has at least this many
+                                         // entries takes the lane form, else the warp form
+                                         // (templates of bytes on Ipad / all others)
 };
 
 // Bound of every location against each template's threshold (group test
@@ -296,6 +314,21 @@ cudaError_t launch_survivors(const Scan2Batch &B, const uint8_t *I, int pimg, in
                              const int *wsum, int m, int n, int npad, const float *inv_sigma,
                              cudaStream_t s);
 cudaError_t launch_surv_candidates(const Scan2Batch &B, cudaStream_t s);
+// rho and its error bound at the B.surv[0..count) locations of B's one
+// template (B.T == 1, st prepared) by survivor form `form` (0 one lane per
+// survivor, 1 one warp, -1 by B's thresholds), none skipped: into
+// B.surv_rho / B.surv_eps.
+cudaError_t launch_survivor_eval(const Scan2Batch &B, const uint8_t *I, int pimg, int q, int Lx,
+                                 const int *wsum, int m, int n, int npad, const float *inv_sigma,
+                                 int count, int form, cudaStream_t s);
+// Survivor forms: a template's sweep takes the lane form when it has at least
+// lane_min entries, the warp form otherwise.  survivor_lane_min gives the
+// thresholds of an m x n size on the current device (byte templates on the
+// aligned image: u8 = true), measured by the tuner (tuned = true) or from
+// the default rule; set_survivor_lane_min records measured ones.
+int survivor_lane_min(int m, int n, bool u8, bool *tuned = nullptr);
+void set_survivor_lane_min(int m, int n, bool u8, int lane_min);
+constexpr int kLaneNever = 0x7fffffff;
 
 // --- preparation ---
 // Blur with per-block sigma-level index (uint8 map; level 0 = copy) and weight table.
@@ -346,6 +379,7 @@ struct ExhaustiveBufs {
     uint8_t *Ipad = nullptr;
     void *Bt = nullptr;
     int *err = nullptr;
+    int *wsum = nullptr;   // window sums (the tensor-core map needs them)
 };
 
 // The exhaustive map on the tensor cores (brute_mma.cu): templates up to
@@ -353,10 +387,10 @@ struct ExhaustiveBufs {
 bool brute_mma_supported(int m, int n);
 size_t brute_tmpl_bytes(int m, int n);
 float brute_mma_epsA(int m, int n);
-// Template tiles of T templates (t' at tf + k * tsz) into B + k * brute_tmpl_bytes;
-// with dense_of (nullable), only templates k with dense_of[k].dense.
+// Template tiles of T templates (t' at tf + k * tsz, states st + k) into
+// B + k * brute_tmpl_bytes; with dense_only, only templates k with st[k].dense.
 cudaError_t launch_brute_tmpl(const float *tf, size_t tsz, int T, int m, int n, int npad, void *B,
-                              const TmplState *dense_of, cudaStream_t s);
+                              const TmplState *st, int dense_only, cudaStream_t s);
 cudaError_t launch_pad_rows(const uint8_t *I, int p, int q, uint8_t *out, int qs, cudaStream_t s);
 // rho maps of T templates (tile k at B + k * brute_tmpl_bytes, state st[k],
 // map at map + k * map_stride); with dense_only, templates without

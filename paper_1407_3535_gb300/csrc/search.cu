@@ -13,7 +13,9 @@
 // FP64 candidates safe.
 #include <algorithm>
 
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "common.cuh"
 
@@ -63,7 +65,7 @@ __device__ double block_sum_d(double v, double *sh) {
 __global__ void __launch_bounds__(1024)
 tmpl_prep_kernel(const float *__restrict__ t, int64_t ld, const TmplIn *__restrict__ tin, int m,
                  int n, int npad, float *tf, size_t tsz, double *td, size_t dsz, TmplState *st,
-                 int topk) {
+                 int topk, int pack) {
     __shared__ double sh[32];
     const int mn = m * n;
     // block k prepares template k of the batch
@@ -73,8 +75,26 @@ tmpl_prep_kernel(const float *__restrict__ t, int64_t ld, const TmplIn *__restri
     td += k * dsz;
     st += k;
     double s = 0.0;
-    for (int i = threadIdx.x; i < mn; i += blockDim.x) s += (double)t[(int64_t)(i / n) * ld + (i % n)];
+    int whole = 1;   // every value an integer in 0..255
+    for (int i = threadIdx.x; i < mn; i += blockDim.x) {
+        const float v = t[(int64_t)(i / n) * ld + (i % n)];
+        s += (double)v;
+        whole &= (v >= 0.f && v <= 255.f && v == rintf(v)) ? 1 : 0;
+    }
+    whole = __syncthreads_and(whole);
     s = block_sum_d(s, sh);
+    if (pack && whole) {
+        // the bytes, four to a word, rows of round_up(n, 16) bytes
+        uint32_t *tb = reinterpret_cast<uint32_t *>(tf + (size_t)m * npad);
+        const int wr = ((n + 15) & ~15) / 4;
+        for (int i = threadIdx.x; i < m * wr; i += blockDim.x) {
+            const int u = i / wr, v0 = 4 * (i % wr);
+            uint32_t w = 0u;
+            for (int b = 0; b < 4; ++b)
+                if (v0 + b < n) w |= (uint32_t)t[(int64_t)u * ld + v0 + b] << (8 * b);
+            tb[i] = w;
+        }
+    }
     const double mu = s / (double)mn;
     double ss = 0.0;
     for (int i = threadIdx.x; i < mn; i += blockDim.x) {
@@ -108,6 +128,12 @@ tmpl_prep_kernel(const float *__restrict__ t, int64_t ld, const TmplIn *__restri
         st->n_cand_search = 0;
         st->dense = 0;
         st->n_first = 0;
+        st->u8 = pack && whole;
+        st->sum_t = whole ? (int)s : 0;   // exact: integers below 2^22
+        // the exhaustive map's integer operand t - rint(mu) keeps its error
+        // bound while sigma_t >= sqrt(mn) / 6 (brute_mma.cu)
+        st->int_op = whole && sg >= sqrt((double)mn) / 6.0 ? 1 : 0;
+        st->c0 = st->int_op ? (float)(rint(mu) - mu) : 0.f;
     }
 }
 
@@ -1045,6 +1071,83 @@ __device__ inline void warp_rho32(const uint8_t *__restrict__ I, int q, int Lx,
     }
 }
 
+// Integer form of Eq. rho1's numerator for a template of bytes (TmplState::u8):
+//   sum (t - mu_t)(I - mu_I) = (mn * sum t I - sum t * sum I) / mn,
+// with sum t I accumulated exactly by 4-byte dot products (dp4a, u8 x u8 into
+// u32: at most mn * 255^2 < 2^32 for mn <= kU8MaxMN) and the difference in
+// int64.  In the lane form the window's rows come from the 16-byte-aligned
+// copy of the image (rows of qs bytes) in 16-byte loads: chunk c of 16 columns needs the
+// aligned blocks c and c + 1 of the row, from which the window's words are
+// selected by the offset o = x mod 16 (word o / 4, then a funnel shift by
+// 8 (o mod 4) bits).  Only the last rounding steps remain: the conversion of
+// the integer, the division by mn and the two products with 1/sigma_t and
+// 1/Omega (each within a few ulp), so |rho - rho_exact| <= kU8Eps.
+constexpr int kU8MaxMN = 32768;
+constexpr float kU8Eps = 16.f * kU32 * 1.01f;
+
+// warp_rho32 for a template of bytes (TmplState::u8): the staged window's
+// words against the packed template words by 4-byte dot products, summed
+// exactly in u32 and over the warp; rho from the int64 numerator as in the
+// lane form (error <= kU8Eps).  Needs the staging buffer.  Results in lane 0.
+__device__ inline void warp_rho_u8(const uint8_t *__restrict__ I, int q, int Lx,
+                                   const int *__restrict__ wsum, const uint32_t *__restrict__ tb,
+                                   int m, int n, int sum_t, const float *__restrict__ inv_sigma,
+                                   float ist, int idx, uint8_t *wbuf, const uint8_t *img_end,
+                                   float &rho, float &eps) {
+    const int lane = threadIdx.x & 31;
+    const int y = idx / Lx, x = idx % Lx;
+    const int wr = ((n + 15) & ~15) / 4;   // words per packed template row
+    const int WB = stage_width(n);
+    const int nch = (m + kStageRows - 1) / kStageRows;
+    const int n4 = n >> 2;
+    const int rpp = n4 <= 16 ? 2 : 1;
+    const int lr = rpp == 2 ? lane >> 4 : 0;
+    const int lg = rpp == 2 ? lane & 15 : lane;
+    const int gstep = rpp == 2 ? 16 : 32;
+    unsigned acc = 0u;
+    stage_rows(I, img_end, q, y, x, 0, min(kStageRows, m), n, wbuf, WB);
+    for (int c = 0; c < nch; ++c) {
+        const int u0 = c * kStageRows, rows = min(kStageRows, m - u0);
+        uint8_t *buf = wbuf + (c & 1) * kStageRows * WB;
+        if (c + 1 < nch) {
+            stage_rows(I, img_end, q, y, x, u0 + kStageRows, min(kStageRows, m - u0 - kStageRows), n,
+                       wbuf + ((c + 1) & 1) * kStageRows * WB, WB);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncwarp();
+        for (int r0 = 0; r0 < rows; r0 += rpp) {
+            const int r = r0 + lr;
+            if (r < rows) {
+                const uint8_t *row = I + (int64_t)(y + u0 + r) * q + x;
+                const int off = (int)(reinterpret_cast<uintptr_t>(row) & 15);
+                const uint8_t *sb = buf + r * WB;
+                const unsigned *sw = reinterpret_cast<const unsigned *>(sb);
+                const uint32_t *tr = tb + (u0 + r) * wr;
+                for (int g = lg; g < n4; g += gstep) {
+                    const int b0 = off + 4 * g;
+                    const unsigned w =
+                        __funnelshift_r(sw[b0 >> 2], sw[(b0 >> 2) + 1], 8u * (unsigned)(b0 & 3));
+                    acc = __dp4a(w, tr[g], acc);
+                }
+                for (int v = 4 * n4 + lg; v < n; v += gstep)
+                    acc += (unsigned)sb[off + v] * ((tr[v >> 2] >> (8 * (v & 3))) & 255u);
+            }
+        }
+        __syncwarp();   // the buffer is refilled two chunks later
+    }
+    acc = __reduce_add_sync(0xffffffffu, acc);
+    rho = 0.f;
+    eps = 0.f;
+    if (lane == 0) {
+        const float is = inv_sigma[idx];
+        const long long D = mul_sub_wide((unsigned)(m * n), acc, sum_t, wsum[idx]);
+        rho = ((i64_to_f32(D) / (float)(m * n)) * ist) * is;
+        eps = is > 0.f ? kU8Eps : 0.f;
+    }
+}
+
 // Copy the template (m x npad floats, npad a multiple of 8) into shared
 // memory with 16-byte loads, several in flight per thread.
 __device__ inline const float *stage_template(const float *tf, int m, int npad, int in_smem,
@@ -1087,7 +1190,24 @@ survivors_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, int L
     const int ns_lo = B.phase == 2 ? min(st->n_first, ns_all) : 0;
     const int ns0 = B.phase == 1 ? min(st->n_first, ns_all) : ns_all;
     if (ns_lo + (int)blockIdx.x * (int)(blockDim.x >> 5) >= ns0) return;
-    const float *tm = stage_template(tf, m, npad, tmpl_in_smem, reinterpret_cast<float *>(ssm4));
+    // as many entries as the lane form's threshold: the lane form's template
+    if (ns0 - ns_lo >= (st->u8 && B.Ipad != nullptr ? B.lane_min_u8 : B.lane_min_f32)) return;
+    // a template of bytes: exact integer sums over the staged window
+    const bool u8 = stage && st->u8 && (long long)m * n <= kU8MaxMN;
+    const float *tm = nullptr;
+    const uint32_t *tb = nullptr;
+    if (u8) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(tf + (size_t)m * npad);
+        tb = reinterpret_cast<const uint32_t *>(src);
+        if (tmpl_in_smem) {
+            const int n16 = m * ((n + 15) >> 4);
+            for (int i = threadIdx.x; i < n16; i += blockDim.x) reinterpret_cast<uint4 *>(ssm4)[i] = src[i];
+            __syncthreads();
+            tb = reinterpret_cast<const uint32_t *>(ssm4);
+        }
+    } else {
+        tm = stage_template(tf, m, npad, tmpl_in_smem, reinterpret_cast<float *>(ssm4));
+    }
     uint8_t *wbuf = nullptr;
     if (stage) {
         const size_t tb = tmpl_in_smem ? (((size_t)m * npad * sizeof(float) + 15) & ~(size_t)15) : 0;
@@ -1123,8 +1243,12 @@ survivors_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, int L
             const int idx = __shfl_sync(0xffffffffu, idxl, k);
             if (ub < lim) continue;
             float rho, eps;
-            warp_rho32(I, q, Lx, wsum, tm, m, n, npad, inv_sigma, ist, idx, wbuf, img_end, rho,
-                       eps);
+            if (u8)
+                warp_rho_u8(I, q, Lx, wsum, tb, m, n, st->sum_t, inv_sigma, ist, idx, wbuf, img_end,
+                            rho, eps);
+            else
+                warp_rho32(I, q, Lx, wsum, tm, m, n, npad, inv_sigma, ist, idx, wbuf, img_end, rho,
+                           eps);
             unsigned seen = 0u;
             if (lane == 0) {
                 const int64_t s = base + (int64_t)k * nwarps;
@@ -1149,7 +1273,182 @@ survivors_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, int L
 // depth at n + m + 2, the same error bound as the warp form.
 constexpr int kLaneMaxMN = 2304;   // above this the warp form is faster (fewer, longer dot products)
 
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ unsigned dp4a_chunk(uint4 cur, uint4 nxt, bool k1, bool k2, unsigned sh,
+                                               uint4 tv, unsigned acc) {
+    const uint32_t w[8] = {cur.x, cur.y, cur.z, cur.w, nxt.x, nxt.y, nxt.z, nxt.w};
+    uint32_t a[6], l[5];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) a[j] = k2 ? w[j + 2] : w[j];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) l[j] = k1 ? a[j + 1] : a[j];
+    acc = __dp4a(__funnelshift_r(l[0], l[1], sh), tv.x, acc);
+    acc = __dp4a(__funnelshift_r(l[1], l[2], sh), tv.y, acc);
+    acc = __dp4a(__funnelshift_r(l[2], l[3], sh), tv.z, acc);
+    acc = __dp4a(__funnelshift_r(l[3], l[4], sh), tv.w, acc);
+    return acc;
+}
+
+// window_dot_u8 for rows of NCH chunks (n <= 16 NCH): the NCH + 1 aligned
+// blocks of R rows are loaded together (R = 4, 2 or 1 as the rows widen),
+// so one load latency covers R rows (the generic form waits on every
+// chunk's block in turn).
+template <int NCH>
+__device__ __forceinline__ void load_row_u8(const uint4 *__restrict__ rp, int lb, uint4 (&b)[NCH + 1]) {
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) b[c] = __ldg(rp + c);   // 16 c < n <= lb: needed
+    b[NCH] = 16 * NCH < lb ? __ldg(rp + NCH) : make_uint4(0u, 0u, 0u, 0u);
+}
+
+template <int NCH>
+__device__ __forceinline__ unsigned window_dot_u8_rows(const uint8_t *__restrict__ Ipad, int qs, int y,
+                                                       int x, const uint4 *__restrict__ tb, int m,
+                                                       int n) {
+    constexpr int R = NCH <= 2 ? 4 : (NCH <= 4 ? 2 : 1);
+    const int o = x & 15;
+    const unsigned sh = 8u * (unsigned)(o & 3);
+    const bool k1 = (o & 4) != 0, k2 = (o & 8) != 0;
+    const int lb = o + n;
+    const int qs4 = qs >> 4;
+    const uint4 *rp = reinterpret_cast<const uint4 *>(Ipad + (int64_t)y * qs + (x - o));
+    unsigned acc0 = 0u, acc1 = 0u;
+    int u = 0;
+#pragma unroll 1
+    for (; u + R <= m; u += R, tb += R * NCH, rp += R * qs4) {
+        uint4 b[R][NCH + 1];
+#pragma unroll
+        for (int r = 0; r < R; ++r) load_row_u8<NCH>(rp + r * qs4, lb, b[r]);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                if ((r * NCH + c) & 1)
+                    acc1 = dp4a_chunk(b[r][c], b[r][c + 1], k1, k2, sh, tb[r * NCH + c], acc1);
+                else
+                    acc0 = dp4a_chunk(b[r][c], b[r][c + 1], k1, k2, sh, tb[r * NCH + c], acc0);
+            }
+    }
+#pragma unroll 1
+    for (; u < m; ++u, tb += NCH, rp += qs4) {
+        uint4 b[NCH + 1];
+        load_row_u8<NCH>(rp, lb, b);
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            if (c & 1)
+                acc1 = dp4a_chunk(b[c], b[c + 1], k1, k2, sh, tb[c], acc1);
+            else
+                acc0 = dp4a_chunk(b[c], b[c + 1], k1, k2, sh, tb[c], acc0);
+        }
+    }
+    return acc0 + acc1;
+}
+
+// sum over the m x n window at (y, x) of t * I, exactly (tb: the packed
+// template rows of nch 16-byte chunks).
+__device__ __forceinline__ unsigned window_dot_u8(const uint8_t *__restrict__ Ipad, int qs, int y,
+                                                  int x, const uint4 *__restrict__ tb, int m, int n) {
+    const int o = x & 15;
+    const unsigned sh = 8u * (unsigned)(o & 3);
+    const bool k1 = (o & 4) != 0, k2 = (o & 8) != 0;
+    const int nch = (n + 15) >> 4;
+    const int lb = o + n;   // bytes of the aligned row that the window reaches
+    const uint4 *rp = reinterpret_cast<const uint4 *>(Ipad + (int64_t)y * qs + (x - o));
+    const int qs4 = qs >> 4;
+    unsigned acc0 = 0u, acc1 = 0u;
+    for (int u = 0; u < m; ++u, rp += qs4, tb += nch) {
+        uint4 cur = __ldg(rp);
+        int c = 0;
+        for (; c + 2 <= nch; c += 2) {
+            const uint4 nx1 = __ldg(rp + c + 1);   // 16 (c + 1) < n <= lb: needed
+            const uint4 nx2 = 16 * (c + 2) < lb ? __ldg(rp + c + 2) : make_uint4(0u, 0u, 0u, 0u);
+            acc0 = dp4a_chunk(cur, nx1, k1, k2, sh, tb[c], acc0);
+            acc1 = dp4a_chunk(nx1, nx2, k1, k2, sh, tb[c + 1], acc1);
+            cur = nx2;
+        }
+        if (c < nch) {
+            const uint4 nx1 = 16 * (c + 1) < lb ? __ldg(rp + c + 1) : make_uint4(0u, 0u, 0u, 0u);
+            acc0 = dp4a_chunk(cur, nx1, k1, k2, sh, tb[c], acc0);
+        }
+    }
+    return acc0 + acc1;
+}
+
+// window_dot_u8 by the row-prefetching form where a row has at most 8
+// chunks (n <= 128); nch is uniform over a block.
+__device__ __forceinline__ unsigned window_dot_u8_any(const uint8_t *__restrict__ Ipad, int qs, int y,
+                                                      int x, const uint4 *__restrict__ tb, int m,
+                                                      int n) {
+    switch ((n + 15) >> 4) {
+    case 1: return window_dot_u8_rows<1>(Ipad, qs, y, x, tb, m, n);
+    case 2: return window_dot_u8_rows<2>(Ipad, qs, y, x, tb, m, n);
+    case 3: return window_dot_u8_rows<3>(Ipad, qs, y, x, tb, m, n);
+    case 4: return window_dot_u8_rows<4>(Ipad, qs, y, x, tb, m, n);
+    case 5: return window_dot_u8_rows<5>(Ipad, qs, y, x, tb, m, n);
+    case 6: return window_dot_u8_rows<6>(Ipad, qs, y, x, tb, m, n);
+    case 7: return window_dot_u8_rows<7>(Ipad, qs, y, x, tb, m, n);
+    case 8: return window_dot_u8_rows<8>(Ipad, qs, y, x, tb, m, n);
+    default: return window_dot_u8(Ipad, qs, y, x, tb, m, n);
+    }
+}
+
+// FP32 form of one lane's window (any template): rows read as 32-bit words
+// funnel-shifted to the window's alignment, per-row partial sums.
+__device__ __forceinline__ float lane_dot_f32(const uint8_t *__restrict__ I, int q, int y, int x,
+                                              const float *__restrict__ tm, int m, int n, int npad,
+                                              float ca, uintptr_t iend) {
+    float tot = 0.f;
+    const uint8_t *wp = I + (int64_t)y * q + x;
+    for (int u = 0; u < m; ++u) {
+        const uintptr_t ra = reinterpret_cast<uintptr_t>(wp + (int64_t)u * q);
+        const uint32_t *wr = reinterpret_cast<const uint32_t *>(ra & ~(uintptr_t)3);
+        const unsigned sh = (unsigned)(ra & 3) * 8u;
+        const float *tr = tm + u * npad;
+        uint32_t w0 = wr[0];
+        float racc = 0.f;
+        if ((n & 3) == 0 && reinterpret_cast<uintptr_t>(wr + (n >> 2) + 1) <= iend) {
+            // whole words of the row inside the image: four template values
+            // per 16-byte read (the same for every lane)
+            for (int v = 0; v < n; v += 4) {
+                const uint32_t w1 = wr[(v >> 2) + 1];
+                const uint32_t wv = __funnelshift_r(w0, w1, sh);
+                w0 = w1;
+                const float4 tv = *reinterpret_cast<const float4 *>(tr + v);
+                racc = fmaf(tv.x, __uint_as_float(__byte_perm(wv, 0x4B000000u, 0x7650)) - ca, racc);
+                racc = fmaf(tv.y, __uint_as_float(__byte_perm(wv, 0x4B000000u, 0x7651)) - ca, racc);
+                racc = fmaf(tv.z, __uint_as_float(__byte_perm(wv, 0x4B000000u, 0x7652)) - ca, racc);
+                racc = fmaf(tv.w, __uint_as_float(__byte_perm(wv, 0x4B000000u, 0x7653)) - ca, racc);
+            }
+        } else {
+            for (int v = 0; v < n; v += 4) {
+                // the next word, unless it starts past the image
+                const uint32_t *nx = wr + (v >> 2) + 1;
+                const uint32_t w1 = reinterpret_cast<uintptr_t>(nx) < iend ? *nx : 0u;
+                const uint32_t wv = __funnelshift_r(w0, w1, sh);
+                w0 = w1;
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    if (v + b < n)
+                        racc = fmaf(tr[v + b], __uint_as_float(__byte_perm(wv, 0x4B000000u, 0x7650 + b)) - ca,
+                                    racc);
+            }
+        }
+        tot += racc;
+    }
+    return tot;
+}
+
+// Per-warp queue of the entries a lane-form sweep evaluates (shared memory,
+// after the template): list position, location and bound of up to
+// 31 + 32 kLaneFetch entries, so that every evaluation round has 32 lanes
+// busy however many entries the running lower bound skips.  A warp reads
+// 32 kLaneFetch entries per round (kLaneFetch coalesced loads in flight per
+// lane), which hides the latency of the reads behind one another.
+constexpr int kLaneFetch = 4;
+constexpr int kLaneQueue = 32 * kLaneFetch + 32;
+__host__ __device__ inline size_t lane_tmpl_bytes(int m, int npad) {
+    return ((size_t)m * npad * sizeof(float) + 15) & ~(size_t)15;
+}
+
+__global__ void __launch_bounds__(256, 2)
 survivors_lane_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, int Lx,
                       const int *__restrict__ wsum, int m, int n, int npad,
                       const float *__restrict__ inv_sigma, const uint8_t *img_end) {
@@ -1165,12 +1464,32 @@ survivors_lane_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, 
     const int ns_all = (int)min((int64_t)min(st->n_surv, st->n_surv_eff), B.scap);
     const int ns_lo = B.phase == 2 ? min(st->n_first, ns_all) : 0;
     const int ns = B.phase == 1 ? min(st->n_first, ns_all) : ns_all;
-    if (ns_lo + (int)blockIdx.x * (int)(blockDim.x >> 5) >= ns) return;   // uniform
-    const float *tm = stage_template(B.tf + blockIdx.y * B.tsz, m, npad, 1,
-                                     reinterpret_cast<float *>(lsm4));
+    // entries per lane and round: kLaneFetch when every warp has that many
+    // rounds of 32 or more, else fewer (short lists keep all warps busy)
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int K = max(1, min(kLaneFetch, (ns - ns_lo) / (32 * nwarps)));
+    if (ns_lo + (int64_t)blockIdx.x * (blockDim.x >> 5) * 32 * K >= ns) return;   // uniform
+    // fewer entries than the lane form's threshold: the warp form's template
+    if (ns - ns_lo < (st->u8 && B.Ipad != nullptr ? B.lane_min_u8 : B.lane_min_f32)) return;
+    // a template of bytes with the aligned image: exact integer dot products
+    const bool u8 = B.Ipad != nullptr && st->u8 && (long long)m * n <= kU8MaxMN;
+    const float *tm = nullptr;
+    const uint4 *tb = reinterpret_cast<const uint4 *>(lsm4);
+    if (u8) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(B.tf + blockIdx.y * B.tsz + (size_t)m * npad);
+        const int n16 = m * ((n + 15) >> 4);
+        for (int i = threadIdx.x; i < n16; i += blockDim.x) reinterpret_cast<uint4 *>(lsm4)[i] = src[i];
+        __syncthreads();
+    } else {
+        tm = stage_template(B.tf + blockIdx.y * B.tsz, m, npad, 1, reinterpret_cast<float *>(lsm4));
+    }
+    int *qsl = reinterpret_cast<int *>(reinterpret_cast<uint8_t *>(lsm4) + lane_tmpl_bytes(m, npad)) +
+               (threadIdx.x >> 5) * (3 * kLaneQueue);
+    int *qix = qsl + kLaneQueue;
+    float *qub = reinterpret_cast<float *>(qix + kLaneQueue);
+    const int sum_t = st->sum_t;
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const float ist = st->inv_sigma;
     const long long mn = (long long)m * n;
     const int kacc = n + m + 2;
@@ -1178,77 +1497,100 @@ survivors_lane_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, 
     const uintptr_t iend = reinterpret_cast<uintptr_t>(img_end);
     float lim = -4.f;
     int evaluated = 0;
-    for (int64_t base = ns_lo + warp; base < ns; base += 32 * (int64_t)nwarps) {
-        const int64_t sl = base + (int64_t)lane * nwarps;
-        lim = fmaxf(lim, __shfl_sync(0xffffffffu, key_float(*lo_key), 0));
-        bool act = false;
-        int idx = 0;
-        if (sl < ns) {
-            act = surv_ub[sl] >= lim;
-            idx = surv[sl];
-        }
-        float lo = -4.f;
-        if (act) {
-            const int y = idx / Lx, x = idx - (idx / Lx) * Lx;
-            const long long S = wsum[idx];
-            const float is = inv_sigma[idx];
-            const float a = rintf((float)S / (float)mn);
-            const float ca = 8388608.f + a;   // 2^23 + a: byte b - a = float(0x4B0000bb) - ca, exactly
-            float tot = 0.f;
-            const uint8_t *wp = I + (int64_t)y * q + x;
-            for (int u = 0; u < m; ++u) {
-                const uintptr_t ra = reinterpret_cast<uintptr_t>(wp + (int64_t)u * q);
-                const uint32_t *wr = reinterpret_cast<const uint32_t *>(ra & ~(uintptr_t)3);
-                const unsigned sh = (unsigned)(ra & 3) * 8u;
-                const float *tr = tm + u * npad;
-                uint32_t w0 = wr[0];
-                float racc = 0.f;
-                if ((n & 3) == 0 && reinterpret_cast<uintptr_t>(wr + (n >> 2) + 1) <= iend) {
-                    // whole words of the row inside the image: four template
-                    // values per 16-byte read (the same for every lane)
-                    for (int v = 0; v < n; v += 4) {
-                        const uint32_t w1 = wr[(v >> 2) + 1];
-                        const uint32_t wv = __funnelshift_r(w0, w1, sh);
-                        w0 = w1;
-                        const float4 tv = *reinterpret_cast<const float4 *>(tr + v);
-                        racc = fmaf(tv.x, __uint_as_float(__byte_perm(wv, 0x4B000000u, 0x7650)) - ca, racc);
-                        racc = fmaf(tv.y, __uint_as_float(__byte_perm(wv, 0x4B000000u, 0x7651)) - ca, racc);
-                        racc = fmaf(tv.z, __uint_as_float(__byte_perm(wv, 0x4B000000u, 0x7652)) - ca, racc);
-                        racc = fmaf(tv.w, __uint_as_float(__byte_perm(wv, 0x4B000000u, 0x7653)) - ca, racc);
-                    }
-                } else {
-                    for (int v = 0; v < n; v += 4) {
-                        // the next word, unless it starts past the image
-                        const uint32_t *nx = wr + (v >> 2) + 1;
-                        const uint32_t w1 = reinterpret_cast<uintptr_t>(nx) < iend ? *nx : 0u;
-                        const uint32_t wv = __funnelshift_r(w0, w1, sh);
-                        w0 = w1;
+    // round r: warp w takes entries ns_lo + 32 K (r nwarps + w) + 32 k + lane
+    // (k < K), so all warps advance through the bound order
+    // together and the lanes of a warp hold neighbouring entries (of one
+    // bucket, mostly from one strip of groups: overlapping windows, shared
+    // cache lines); the entries the running lower bound does not skip join
+    // the warp's queue, evaluated 32 at a time (the rest once the list is done)
+    int qn = 0;
+    int64_t base = ns_lo + 32 * K * (int64_t)warp;
+    for (;;) {
+        const bool more = base < ns;   // warp-uniform
+        if (more) {
+            lim = fmaxf(lim, __shfl_sync(0xffffffffu, key_float(*lo_key), 0));
+            float ub[kLaneFetch];
+            int ix[kLaneFetch];
 #pragma unroll
-                        for (int b = 0; b < 4; ++b)
-                            if (v + b < n)
-                                racc = fmaf(tr[v + b],
-                                            __uint_as_float(__byte_perm(wv, 0x4B000000u, 0x7650 + b)) - ca, racc);
+            for (int k = 0; k < kLaneFetch; ++k) {
+                const int64_t sl = base + 32 * k + lane;
+                ub[k] = -4.f;
+                ix[k] = 0;
+                if (k < K && sl < ns) {
+                    ub[k] = surv_ub[sl];
+                    ix[k] = surv[sl];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kLaneFetch; ++k) {
+                const bool take = ub[k] >= lim;
+                const unsigned mask = __ballot_sync(0xffffffffu, take);
+                if (take) {
+                    const int pos = qn + __popc(mask & ((1u << lane) - 1u));
+                    qsl[pos] = (int)(base + 32 * k + lane);
+                    qix[pos] = ix[k];
+                    qub[pos] = ub[k];
+                }
+                qn += __popc(mask);
+            }
+            base += 32 * K * (int64_t)nwarps;
+            __syncwarp();
+        }
+        // queue entries [qh, qh + cnt), one per lane, while 32 are waiting
+        // (all of them once the list is done); after each round one atomic
+        // per warp: the largest certain lower bound of the round
+        int qh = 0;
+        while (qn - qh >= 32 || (!more && qn > qh)) {
+            const int cnt = min(qn - qh, 32);
+            const bool act = lane < cnt && qub[qh + lane] >= lim;
+            float lo = -4.f;
+            if (act) {
+                const int sl = qsl[qh + lane], idx = qix[qh + lane];
+                const int y = idx / Lx, x = idx - y * Lx;
+                const int S = wsum[idx];
+                const float is = inv_sigma[idx];
+                float rho, eps = 0.f;
+                if (u8) {
+                    const unsigned dot = window_dot_u8_any(B.Ipad, B.qs, y, x, tb, m, n);
+                    const long long D = mul_sub_wide((unsigned)mn, dot, sum_t, S);
+                    rho = ((i64_to_f32(D) / (float)mn) * ist) * is;
+                    if (is > 0.f) eps = kU8Eps;
+                } else {
+                    const float a = rintf((float)S / (float)mn);
+                    // 2^23 + a: byte b - a = float(0x4B0000bb) - ca, exactly
+                    const float tot = lane_dot_f32(I, q, y, x, tm, m, n, npad, 8388608.f + a, iend);
+                    rho = (tot * ist) * is;
+                    if (is > 0.f) {
+                        const long long dS = (long long)S - (long long)a * mn;
+                        const float r2 = (i64_to_f32(dS * dS) / i64_to_f32(mn)) * (is * is);
+                        eps = eps_bound(kacc, sqrtf(1.f + r2));
                     }
                 }
-                tot += racc;
+                surv_rho[sl] = rho;
+                surv_eps[sl] = eps;
+                lo = rho - eps;
+                ++evaluated;
             }
-            const float rho = (tot * ist) * is;
-            float eps = 0.f;
-            if (is > 0.f) {
-                const long long dS = S - (long long)a * mn;
-                const float r2 = (i64_to_f32(dS * dS) / i64_to_f32(mn)) * (is * is);
-                eps = eps_bound(kacc, sqrtf(1.f + r2));
-            }
-            surv_rho[sl] = rho;
-            surv_eps[sl] = eps;
-            lo = rho - eps;
-            ++evaluated;
+            const unsigned key = __reduce_max_sync(0xffffffffu, act ? float_key(lo) : 0u);
+            unsigned seen = 0u;
+            if (lane == 0 && key) seen = max(atomicMax(&st->lo_key, key), key);
+            lim = fmaxf(lim, key_float(__shfl_sync(0xffffffffu, seen, 0)));
+            qh += cnt;
         }
-        // one atomic per warp: the largest certain lower bound of the round
-        const unsigned key = __reduce_max_sync(0xffffffffu, act ? float_key(lo) : 0u);
-        unsigned seen = 0u;
-        if (lane == 0 && key) seen = max(atomicMax(&st->lo_key, key), key);
-        lim = fmaxf(lim, key_float(__shfl_sync(0xffffffffu, seen, 0)));
+        if (!more) break;
+        // the fewer than 32 entries left to the front of the queue (qh >= 32:
+        // no overlap)
+        if (qh > 0) {
+            const int rem = qn - qh;
+            const bool mv = lane < rem;
+            int ra = 0, rb = 0;
+            float rc = 0.f;
+            if (mv) { ra = qsl[qh + lane]; rb = qix[qh + lane]; rc = qub[qh + lane]; }
+            __syncwarp();
+            if (mv) { qsl[lane] = ra; qix[lane] = rb; qub[lane] = rc; }
+            __syncwarp();
+            qn = rem;
+        }
     }
     evaluated = __reduce_add_sync(0xffffffffu, evaluated);
     if (lane == 0 && evaluated) atomicAdd(&st->n_eval, evaluated);
@@ -1401,7 +1743,7 @@ static int grid_cap(int64_t n, int threads, int per_sm) {
 cudaError_t launch_tmpl_prep(const float *t, int64_t ld, int m, int n, int npad, float *tf,
                              double *td, TmplState *st, int topk, cudaStream_t s) {
     LaunchScope ls_tmpl_prep_kernel("tmpl_prep_kernel", s);
-    tmpl_prep_kernel<<<1, 1024, 0, s>>>(t, ld, nullptr, m, n, npad, tf, 0, td, 0, st, topk);
+    tmpl_prep_kernel<<<1, 1024, 0, s>>>(t, ld, nullptr, m, n, npad, tf, 0, td, 0, st, topk, 0);
     return cudaGetLastError();
 }
 
@@ -1409,7 +1751,8 @@ cudaError_t launch_tmpl_prep_batch(const TmplIn *tin, int T, int m, int n, int n
                                    size_t tsz, double *td, size_t dsz, TmplState *st, int topk,
                                    cudaStream_t s) {
     LaunchScope ls("tmpl_prep_kernel", s);
-    tmpl_prep_kernel<<<T, 1024, 0, s>>>(nullptr, 0, tin, m, n, npad, tf, tsz, td, dsz, st, topk);
+    tmpl_prep_kernel<<<T, 1024, 0, s>>>(nullptr, 0, tin, m, n, npad, tf, tsz, td, dsz, st, topk,
+                                        tsz >= tmpl_slot_floats(m, n) ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -1611,14 +1954,20 @@ static size_t tmpl_smem(int m, int npad, int *in_smem) {
 }
 
 // One sweep (B.phase) over the survivor lists of a batch.
+// One sweep: each template of the batch by the lane form
+// (survivors_lane_kernel) or the warp form (survivors_kernel), by its entry
+// count against B.lane_min_*; a kernel runs only when some template may
+// take its form.
 static cudaError_t launch_sweep(const Scan2Batch &B, const uint8_t *I, int q, int Lx, const int *wsum,
                                 int m, int n, int npad, const float *inv_sigma, int in_smem, int stage,
                                 size_t smem, const uint8_t *iend, cudaStream_t s) {
     // one sweep for the whole batch: num_sms * 4 blocks for one template,
     // fewer per template (down to num_sms) when several share the launch
     const int bx = std::max(num_sms(), num_sms() * 4 / std::min(B.T, 4));
-    if ((int64_t)m * n <= kLaneMaxMN) {
-        const size_t lsmem = ((size_t)m * npad * sizeof(float) + 15) & ~(size_t)15;
+    const bool lane = std::min(B.lane_min_u8, B.lane_min_f32) < kLaneNever;
+    const bool warp = std::max(B.lane_min_u8, B.lane_min_f32) > 0;
+    if (lane) {
+        const size_t lsmem = lane_tmpl_bytes(m, npad) + (size_t)8 * 3 * kLaneQueue * sizeof(int);
         {
             const cudaError_t e2 =
                 ensure_smem(reinterpret_cast<const void *>(survivors_lane_kernel), lsmem);
@@ -1627,33 +1976,89 @@ static cudaError_t launch_sweep(const Scan2Batch &B, const uint8_t *I, int q, in
         LaunchScope ls("survivors_lane_kernel", s);
         survivors_lane_kernel<<<dim3(bx, B.T), 256, lsmem, s>>>(B, I, q, Lx, wsum, m, n, npad,
                                                                 inv_sigma, iend);
-        return cudaGetLastError();
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
-    {
+    if (warp) {
         LaunchScope ls("survivors_kernel", s);
         survivors_kernel<<<dim3(bx, B.T), 256, smem, s>>>(B, I, q, Lx, wsum, m, n, npad,
                                                           inv_sigma, in_smem, stage, iend);
+        return cudaGetLastError();
     }
-    return cudaGetLastError();
+    return cudaSuccess;
+}
+
+// Lane-form thresholds per (device, m, n, bytes): measured by the tuner,
+// else the default rule -- FP32 path: the lane form up to kLaneMaxMN
+// template pixels at any count, the warp form above; integer path: the lane
+// form at any count up to 1024 pixels, above from 8192 entries on.
+static std::mutex g_form_mu;
+static std::map<std::tuple<int, int, int, int>, int> g_lane_min;
+
+static int current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); dev = 0; }
+    return dev;
+}
+
+int survivor_lane_min(int m, int n, bool u8, bool *tuned) {
+    const auto key = std::make_tuple(current_device(), m, n, u8 ? 1 : 0);
+    {
+        std::lock_guard<std::mutex> lk(g_form_mu);
+        const auto it = g_lane_min.find(key);
+        if (tuned) *tuned = it != g_lane_min.end();
+        if (it != g_lane_min.end()) return it->second;
+    }
+    const int64_t mn = (int64_t)m * n;
+    if (!u8) return mn <= kLaneMaxMN ? 0 : kLaneNever;
+    return mn <= 1024 ? 0 : 8192;
+}
+
+void set_survivor_lane_min(int m, int n, bool u8, int lane_min) {
+    const auto key = std::make_tuple(current_device(), m, n, u8 ? 1 : 0);
+    std::lock_guard<std::mutex> lk(g_form_mu);
+    if (lane_min < 0) g_lane_min.erase(key); else g_lane_min[key] = lane_min;
+}
+
+// One template's state for an evaluation of given locations: every entry
+// kept (bound above any rho), the whole list in one sweep.
+static __global__ void survivor_eval_setup_kernel(TmplState *st, float *surv_ub, int count) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        surv_ub[i] = 2.f;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->n_surv = count;
+        st->n_surv_eff = count;
+        st->n_first = 0;
+        st->dense = 0;
+    }
+}
+
+// Shared memory of the warp form (template, then each warp's double-buffered
+// staging of kStageRows window rows when the template fits and the rows are
+// narrow enough).
+static size_t warp_form_smem(int m, int n, int npad, int *in_smem, int *stage) {
+    size_t smem = tmpl_smem(m, npad, in_smem);
+    smem = (smem + 15) & ~(size_t)15;
+    const int WB = 16 * ((n + 30) / 16);
+    *stage = *in_smem && n <= 256 ? 1 : 0;
+    // (+16: a staged row's last word pair may reach 3 bytes past its row)
+    if (*stage) smem += (size_t)8 * 2 * kStageRows * WB + 16;
+    return smem;
 }
 
 cudaError_t launch_survivors(const Scan2Batch &B, const uint8_t *I, int pimg, int q, int Lx,
                              const int *wsum, int m, int n, int npad, const float *inv_sigma,
                              cudaStream_t s) {
-    int in_smem = 0;
-    size_t smem = tmpl_smem(m, npad, &in_smem);
-    smem = (smem + 15) & ~(size_t)15;
-    // stage windows through shared memory when the template is there and the
-    // rows are narrow enough
-    const int WB = 16 * ((n + 30) / 16);
-    const int stage = in_smem && n <= 256 ? 1 : 0;
-    // (+16: a staged row's last word pair may reach 3 bytes past its row)
-    if (stage) smem += (size_t)8 * 2 * kStageRows * WB + 16;
+    int in_smem = 0, stage = 0;
+    const size_t smem = warp_form_smem(m, n, npad, &in_smem, &stage);
     {
         const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(survivors_kernel), smem);
         if (e != cudaSuccess) return e;
     }
     const uint8_t *iend = I + (int64_t)q * pimg;
+    Scan2Batch Bf = B;
+    Bf.lane_min_u8 = survivor_lane_min(m, n, true);
+    Bf.lane_min_f32 = survivor_lane_min(m, n, false);
     // buckets whose largest bound is below the certain lower bound already
     // reached (threshold centres and their groups) are cut off, then one sweep
     // -- or, with the dense path on, a first sweep over a bounded head of the
@@ -1662,7 +2067,7 @@ cudaError_t launch_survivors(const Scan2Batch &B, const uint8_t *I, int pimg, in
     const bool two = B.dense_frac != 0.f;
     cudaError_t e;
     for (int phase = two ? 1 : 0; phase <= (two ? 2 : 0); ++phase) {
-        Scan2Batch Bp = B;
+        Scan2Batch Bp = Bf;
         Bp.phase = phase;
         {
             LaunchScope ls("survivor_cut_kernel", s);
@@ -1674,6 +2079,27 @@ cudaError_t launch_survivors(const Scan2Batch &B, const uint8_t *I, int pimg, in
             return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_survivor_eval(const Scan2Batch &B, const uint8_t *I, int pimg, int q, int Lx,
+                                 const int *wsum, int m, int n, int npad, const float *inv_sigma,
+                                 int count, int form, cudaStream_t s) {
+    if (B.T != 1 || count < 0 || count > B.scap || form < -1 || form > 1) return cudaErrorInvalidValue;
+    if (count == 0) return cudaSuccess;
+    int in_smem = 0, stage = 0;
+    const size_t smem = warp_form_smem(m, n, npad, &in_smem, &stage);
+    cudaError_t e = ensure_smem(reinterpret_cast<const void *>(survivors_kernel), smem);
+    if (e != cudaSuccess) return e;
+    {
+        LaunchScope ls("survivor_eval_setup_kernel", s);
+        survivor_eval_setup_kernel<<<grid_cap(count, 256, 4), 256, 0, s>>>(B.st, B.surv_ub, count);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    Scan2Batch Bp = B;
+    Bp.phase = 0;
+    if (form >= 0) Bp.lane_min_u8 = Bp.lane_min_f32 = form == 0 ? 0 : kLaneNever;
+    return launch_sweep(Bp, I, q, Lx, wsum, m, n, npad, inv_sigma, in_smem, stage, smem,
+                        I + (int64_t)q * pimg, s);
 }
 
 cudaError_t launch_surv_candidates(const Scan2Batch &B, cudaStream_t s) {

@@ -19,7 +19,10 @@ not available; the paper's experiments, Section 7, use real 962x622 and
   to [0, 255] and rounded.
 * ``make_templates``    -- square crops of the search image at seeded
   locations, transformed by an affine intensity map a*x+b and perturbed by
-  additive Gaussian noise (float32, not clipped).
+  additive Gaussian noise (float32); with ``quantize`` rounded and clipped
+  to 0..255 like an 8-bit photograph, as the named workloads are (the
+  paper's templates are images taken from another view at another time),
+  else left as real values (not clipped).
 """
 from __future__ import annotations
 
@@ -203,8 +206,12 @@ def serve_image(size: int, device="cuda"):
 
 
 def make_templates(img: np.ndarray, sizes, seed: int, noise: float,
-                   gain=(0.8, 1.2), offset=(-20.0, 20.0)) -> list:
-    """Crops at seeded top-left locations, a*x+b, plus N(0, noise^2). float32."""
+                   gain=(0.8, 1.2), offset=(-20.0, 20.0), quantize: bool = False) -> list:
+    """Crops at seeded top-left locations, a*x+b, plus N(0, noise^2). float32.
+
+    quantize: round to integers and clip to 0..255, as an 8-bit camera would
+    record the template (the paper's templates are images of the scene taken
+    from another view point at another time); the values stay float32."""
     rng = np.random.default_rng(seed)
     p, q = img.shape
     out = []
@@ -214,6 +221,8 @@ def make_templates(img: np.ndarray, sizes, seed: int, noise: float,
         a = float(rng.uniform(*gain)); b = float(rng.uniform(*offset))
         crop = np.asarray(img[y:y + m, x:x + n], dtype=np.float64)
         t = a * crop + b + rng.normal(0.0, noise, size=(m, n))
+        if quantize:
+            t = np.clip(np.rint(t), 0.0, 255.0)
         out.append(Template(np.ascontiguousarray(t.astype(np.float32)), y, x, a, b, noise))
     return out
 
@@ -224,16 +233,16 @@ def make_templates(img: np.ndarray, sizes, seed: int, noise: float,
 # ---------------------------------------------------------------------------
 WORKLOADS = {
     "white256_16": dict(image=("white_blur", dict(size=256, seed=1001)),
-            templates=dict(sizes=[16], seed=1101, noise=5.0),
+            templates=dict(sizes=[16], seed=1101, noise=5.0, quantize=True),
             group=3, blur=False),
     "aerial2048_32and64": dict(image=("aerial", dict(size=2048, n_octaves=8, n_prims=200, seed=2002)),
-            templates=dict(sizes=[32] * 8 + [64] * 8, seed=2102, noise=3.0),
+            templates=dict(sizes=[32] * 8 + [64] * 8, seed=2102, noise=3.0, quantize=True),
             group=0, blur=True),
     "aerial8192_128": dict(image=("aerial", dict(size=8192, n_octaves=12, n_prims=3200, seed=2003)),
-            templates=dict(sizes=[128] * 16, seed=2103, noise=3.0),
+            templates=dict(sizes=[128] * 16, seed=2103, noise=3.0, quantize=True),
             group=0, blur=True),
     "aerial4096_batch256": dict(image=("aerial", dict(size=4096, n_octaves=9, n_prims=800, seed=2004)),
-            templates=dict(sizes=None, seed=2104, noise=3.0, count=256),
+            templates=dict(sizes=None, seed=2104, noise=3.0, count=256, quantize=True),
             group=0, blur=True),
 }
 
@@ -258,4 +267,4 @@ def workload_templates(k: str, img: np.ndarray, count: int | None = None) -> lis
         sizes = batch_sizes(tc["count"], tc["seed"])
     if count is not None:
         sizes = sizes[:count]
-    return make_templates(img, sizes, tc["seed"], tc["noise"])
+    return make_templates(img, sizes, tc["seed"], tc["noise"], quantize=tc.get("quantize", False))
