@@ -127,6 +127,7 @@ struct opta_search_ctx {
     void *Bmma = nullptr;                     // bf16 hi/lo planes of a chunk (core-matrix layout)
     int *dev_err = nullptr;                   // set by a kernel whose bounded wait gave up
     TmplState *tune_st = nullptr;             // the survivor-form tuner's template state
+    unsigned long long *tune_span = nullptr;  // and the span of its timed sweeps
 };
 
 struct opta_handle {
@@ -860,6 +861,7 @@ Scan2Batch scan2_batch_of(opta_handle *H, opta_search_ctx *X, SizeState *S, Tmpl
     B.qs = H->qs;
     B.lane_min_u8 = survivor_lane_min(m, nn, true);
     B.lane_min_f32 = survivor_lane_min(m, nn, false);
+    B.span = nullptr;
     return B;
 }
 
@@ -886,6 +888,7 @@ opta_status tune_survivor_forms(opta_handle *H, opta_search_ctx *X, SizeState *S
     const int c2 = (int)std::min<int64_t>(L, 32768), c1 = std::min(c2 / 16, 2048);
     if (c1 < 256) return OPTA_OK;   // small maps: the default rule
     if (!X->tune_st) TRY(X->mem.alloc(&X->tune_st, 1));
+    if (!X->tune_span) TRY(X->mem.alloc(&X->tune_span, 2));
     // the synthetic list: c2 / 25 cluster centres, seeded
     std::vector<int> idx;
     idx.reserve((size_t)c2);
@@ -909,24 +912,25 @@ opta_status tune_survivor_forms(opta_handle *H, opta_search_ctx *X, SizeState *S
     if (hs.flat) return OPTA_OK;
     Scan2Batch B = scan2_batch_of(H, X, S, st, k0, 1);
     B.st = X->tune_st;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    CK(cudaEventCreate(&e0));
-    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); cudaGetLastError(); return OPTA_ERR_CUDA; }
+    B.span = X->tune_span;
+    // a sweep's time from its own blocks' clocks (first start to last end),
+    // free of launch gaps and of any profiler around the launches
     auto timed = [&](int count, int form, float *ms) -> cudaError_t {
         float best = 1e30f;
         for (int rep = 0; rep < 2; ++rep) {
-            cudaError_t e = cudaEventRecord(e0, s);
+            const unsigned long long init[2] = {~0ull, 0ull};
+            unsigned long long span[2] = {0ull, 0ull};
+            cudaError_t e = cudaMemcpyAsync(X->tune_span, init, sizeof(init), cudaMemcpyHostToDevice, s);
             if (e == cudaSuccess)
                 e = launch_survivor_eval(B, S->M, H->p, H->q, S->Lx, S->wsumM, m, nn, npad, S->invM, count,
                                          form, s);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float t = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(span, X->tune_span, sizeof(span), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) return e;
-            best = std::min(best, t);
+            if (span[1] > span[0]) best = std::min(best, (float)((double)(span[1] - span[0]) * 1e-6));
         }
-        *ms = best;
+        *ms = best < 1e30f ? best : 0.f;
         return cudaSuccess;
     };
     cudaError_t e = cudaSuccess;
@@ -954,8 +958,6 @@ opta_status tune_survivor_forms(opta_handle *H, opta_search_ctx *X, SizeState *S
         }
         set_survivor_lane_min(m, nn, u8, lane_min);
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if (e != cudaSuccess) { cudaGetLastError(); return map_err(e); }
     return OPTA_OK;
 }
@@ -1141,7 +1143,7 @@ void free_ctx(opta_search_ctx *X) {
     void *ptrs[] = {X->rho_tc, X->surv, X->surv_rho, X->surv_eps, X->surv_ub, X->ucnt,
                     X->bucket_cnt, X->bucket_cur, X->Bmma, X->dev_err, X->cand_topk,
                     X->cand_rho_topk, X->tin, X->cand, X->cand_rho, X->topk_v, X->topk_i,
-                    X->tf, X->tstage, X->td, X->states, X->tune_st};
+                    X->tf, X->tstage, X->td, X->states, X->tune_st, X->tune_span};
     for (void *p : ptrs) if (p) cudaFree(p);
     if (X->tin_host) cudaFreeHost(X->tin_host);
     if (X->states_host) cudaFreeHost(X->states_host);

@@ -295,6 +295,8 @@ struct Scan2Batch {
     int lane_min_u8, lane_min_f32;       // a template whose sweep has at least this many
                                          // entries takes the lane form, else the warp form
                                          // (templates of bytes on Ipad / all others)
+    unsigned long long *span;            // null, or [earliest block start, latest block end]
+                                         // of the sweep kernels (%globaltimer ns): the tuner
 };
 
 // Bound of every location against each template's threshold (group test

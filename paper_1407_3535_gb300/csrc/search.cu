@@ -417,10 +417,6 @@ rematch_window_kernel(TmplState *st, int Ly, int Lx, int d, int *cand, int64_t c
 // ---------------------------------------------------------------------------
 constexpr int CT_Y = 4, CT_X = 32, CT_MT = 16, CT_NT = 64;
 
-__device__ inline int centre_kacc(int m, int npad) {
-    return CT_NT + m * ((npad + CT_NT - 1) / CT_NT) + 1;
-}
-
 __global__ void __launch_bounds__(128)
 centre_rho_kernel(const uint8_t *__restrict__ P, int p, int q, const float *__restrict__ tf,
                   int m, int n, int npad, int h, int Ly, int Lx,
@@ -726,95 +722,177 @@ __global__ void group_co_kernel(const float2 *__restrict__ theta_co, int Ly, int
 // batch, then the members of the passing pairs: bucket histogram and the
 // unordered survivor list (index in surv_eps as int, gap in surv_rho) of
 // each template.
+//
+// The group test is taken in cosine space, without an arc cosine per
+// (template, group): with l = theta_lim + kAngMargin and the centre's
+// interval tv = [acos(min(1, r + e)) - kAngMargin, acos(max(-1, r - e)) +
+// kAngMargin],
+//   tv.lo - gco.hi <= theta_lim  <=>  gco.hi + l >= pi  or  r + e >= cos(gco.hi + l),
+//   gco.lo - tv.hi <= theta_lim  <=>  gco.lo <= l        or  r - e <= cos(gco.lo - l),
+// (acos decreasing on [-1, 1]; gco.hi > 0), the cosines from sincos of the
+// group's bounds (once per group) and of l (once per template).  A slack of
+// kCosSlack covers the rounding of both forms, so every pair that passes
+// the angle test passes this one (extra pairs only cost their members'
+// exact test).  A passing pair's interval tv is taken once, into shared
+// memory, for the gaps of its members.
+constexpr float kCosSlack = 8e-6f;
+constexpr float kPiF = 3.14159265358979f;
+
+// Templates per queue fill: the passing pairs of kPassTGroup templates (at
+// most kPassTGroup x kPassGroups) are queued, their members tested, then the
+// next templates'.
+constexpr int kPassTGroup = 4;
+constexpr int kPassQueue = kPassTGroup * kPassGroups;
+
+__host__ __device__ inline size_t bound_pass_smem(int T) {
+    return (size_t)T * kUbBuckets * sizeof(int) + (size_t)kPassQueue * sizeof(float2) +
+           (size_t)kPassQueue * sizeof(unsigned short);
+}
+
 __global__ void __launch_bounds__(256)
 bound_pass_kernel(const Scan2Batch B, const float2 *__restrict__ gco,
                   const float2 *__restrict__ theta_co, int Ly, int Lx, int h) {
-    __shared__ int hist[kS2MaxT][kUbBuckets];
+    extern __shared__ int bp_sm[];
     __shared__ float lims[kS2MaxT];
-    __shared__ unsigned short queue[kS2MaxT * kPassGroups];   // (t << 8) | group in tile
+    __shared__ float2 lcs[kS2MaxT];        // (cos l, sin l) of l = lim + kAngMargin
+    __shared__ int ty0[kPassGroups], tx0[kPassGroups];   // top-left member of the tile's groups
+    __shared__ unsigned short memd[81];    // member k of a group: (dy << 8) | dx
     __shared__ int qn;
     const int T = B.T;
-    for (int i = threadIdx.x; i < T * kUbBuckets; i += blockDim.x) hist[i / kUbBuckets][i % kUbBuckets] = 0;
-    if ((int)threadIdx.x < T)
-        lims[threadIdx.x] = B.st[threadIdx.x].flat ? -1.f : B.st[threadIdx.x].theta_lim;
+    int *hist = bp_sm;                                                            // T x kUbBuckets
+    float2 *qtv = reinterpret_cast<float2 *>(bp_sm + T * kUbBuckets);             // interval of entry
+    unsigned short *queue = reinterpret_cast<unsigned short *>(qtv + kPassQueue); // (t << 8) | group
+    for (int i = threadIdx.x; i < T * kUbBuckets; i += blockDim.x) hist[i] = 0;
+    if ((int)threadIdx.x < T) {
+        const float lim = B.st[threadIdx.x].flat ? -1.f : B.st[threadIdx.x].theta_lim;
+        lims[threadIdx.x] = lim;
+        lcs[threadIdx.x] = make_float2(cosf(lim + kAngMargin), sinf(lim + kAngMargin));
+    }
+    const int hh = h * h;
+    for (int k = threadIdx.x; k < hh; k += blockDim.x) memd[k] = (unsigned short)(((k / h) << 8) | (k % h));
+    // item / hh for item < 2^24 by one multiply: m = ceil(2^40 / hh) errs by
+    // less than item / 2^40 < 2^-16, below the 1 / hh gap to the next integer
+    const unsigned long long mhh = ((1ull << 40) + (unsigned long long)hh - 1) / (unsigned long long)hh;
     const int Gy = groups_along(Ly, h), Gx = groups_along(Lx, h);
     const int64_t G = (int64_t)Gy * Gx;
-    const int hh = h * h;
     const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) qn = 0;
     for (int64_t g0 = (int64_t)blockIdx.x * kPassGroups; g0 < G;
          g0 += (int64_t)gridDim.x * kPassGroups) {
-        if (threadIdx.x == 0) qn = 0;
         __syncthreads();
         const int64_t g = g0 + threadIdx.x;
         const float2 gc = g < G ? gco[g] : make_float2(4.f, -4.f);   // empty group: fails
         const float cef = g < G ? B.c_efac[g] : 0.f;
-        for (int t = 0; t < T; ++t) {
-            const float lim = lims[t];
-            bool pass = false;
-            if (lim >= 0.f && g < G) {
-                const float2 tv = centre_interval(B.rho_tc[t * B.tc_stride + g], cef, B.epsA);
-                pass = fmaxf(tv.x - gc.y, gc.x - tv.y) <= lim;
-            }
-            const unsigned msk = __ballot_sync(0xffffffffu, pass);
-            if (msk) {
-                int base = 0;
-                if (lane == 0) base = atomicAdd(&qn, __popc(msk));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (pass)
-                    queue[base + __popc(msk & ((1u << lane) - 1u))] =
-                        (unsigned short)((t << 8) | threadIdx.x);
-            }
+        const float e = fmaf(B.epsA, cef, kScan1EpsB);
+        const float shi = sinf(gc.y), chi = cosf(gc.y), slo = sinf(gc.x), clo = cosf(gc.x);
+        {
+            const int gy = (int)(g / Gx);
+            ty0[threadIdx.x] = gy * h;
+            tx0[threadIdx.x] = (int)(g - (int64_t)gy * Gx) * h;
         }
-        __syncthreads();
-        const int nitem = qn * hh;
-        for (int ib = 0; ib < nitem; ib += blockDim.x) {   // uniform trip count
-            const int item = ib + threadIdx.x;
-            bool f = false;
-            int t = 0, li = 0, b = 0;
-            float gap = 0.f;
-            if (item < nitem) {
-                const int e = item / hh, mem = item - e * hh;
-                const int code = queue[e];
-                t = code >> 8;
+        // every template's centre value of this group, loads in flight together
+        float rg[kS2MaxT];
+#pragma unroll
+        for (int t = 0; t < kS2MaxT; ++t) rg[t] = t < T && g < G ? B.rho_tc[t * B.tc_stride + g] : 0.f;
+        for (int t0 = 0; t0 < T; t0 += kPassTGroup) {
+#pragma unroll
+            for (int tt = 0; tt < kPassTGroup; ++tt) {
+                const int t = t0 + tt;
+                if (t >= T) break;
+                const float lim = lims[t];
+                bool pass = false;
+                if (lim >= 0.f && g < G) {
+                    // (constant indices keep rg in registers)
+                    static_assert(kS2MaxT == 4 * kPassTGroup, "four template groups");
+                    const float r = t0 == 0 ? rg[tt] : t0 == kPassTGroup ? rg[kPassTGroup + tt]
+                                  : t0 == 2 * kPassTGroup ? rg[2 * kPassTGroup + tt] : rg[3 * kPassTGroup + tt];
+                    const float2 cs = lcs[t];
+                    const float l = lim + kAngMargin;
+                    const bool c1 = gc.y + l >= kPiF || r + e >= fmaf(chi, cs.x, -shi * cs.y) - kCosSlack;
+                    const bool c2 = gc.x <= l || r - e <= fmaf(clo, cs.x, slo * cs.y) + kCosSlack;
+                    pass = c1 && c2;
+                }
+                const unsigned msk = __ballot_sync(0xffffffffu, pass);
+                if (msk) {
+                    int base = 0;
+                    if (lane == 0) base = atomicAdd(&qn, __popc(msk));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (pass)
+                        queue[base + __popc(msk & ((1u << lane) - 1u))] =
+                            (unsigned short)((t << 8) | threadIdx.x);
+                }
+            }
+            __syncthreads();
+            const int nq = qn;
+            // the passing pairs' centre intervals, once each
+            for (int k = threadIdx.x; k < nq; k += blockDim.x) {
+                const int code = queue[k];
                 const int64_t gg = g0 + (code & 255);
-                const int gy = (int)(gg / Gx), gx = (int)(gg - (int64_t)gy * Gx);
-                const int my = gy * h + mem / h, mx = gx * h + mem % h;
-                if (my < Ly && mx < Lx) {
-                    li = my * Lx + mx;
-                    const float2 tv = centre_interval(B.rho_tc[t * B.tc_stride + gg], B.c_efac[gg], B.epsA);
-                    gap = loc_gap(tv, theta_co[li]);
-                    f = gap <= lims[t];
-                    if (f) {
-                        b = gap_bucket(gap, lims[t]);
-                        atomicAdd(&hist[t][b], 1);
+                qtv[k] = centre_interval(B.rho_tc[(code >> 8) * B.tc_stride + gg], B.c_efac[gg], B.epsA);
+            }
+            __syncthreads();
+            const int nitem = nq * hh;
+            // two items per thread and round: both location reads in flight
+            for (int ib = 0; ib < nitem; ib += 2 * blockDim.x) {   // uniform trip count
+                int tq[2], liq[2], eqq[2];
+                float2 co[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int item = ib + u * blockDim.x + threadIdx.x;
+                    tq[u] = 0;
+                    liq[u] = -1;   // no location
+                    eqq[u] = 0;
+                    if (item < nitem) {
+                        const int eq = (int)(((unsigned long long)item * mhh) >> 40);
+                        const int mem = item - eq * hh;
+                        const int code = queue[eq];
+                        const int gi = code & 255;
+                        const int dd = memd[mem];
+                        const int my = ty0[gi] + (dd >> 8), mx = tx0[gi] + (dd & 255);
+                        tq[u] = code >> 8;
+                        eqq[u] = eq;
+                        if (my < Ly && mx < Lx) {
+                            liq[u] = my * Lx + mx;
+                            co[u] = theta_co[liq[u]];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int t = tq[u];
+                    const int li = liq[u];
+                    const float gap = li >= 0 ? loc_gap(qtv[eqq[u]], co[u]) : 0.f;
+                    const bool f = li >= 0 && gap <= lims[t];
+                    if (f) atomicAdd(&hist[t * kUbBuckets + gap_bucket(gap, lims[t])], 1);
+                    // append to template t's unordered list, aggregated over
+                    // the lanes of the warp that share t
+                    const unsigned fm = __ballot_sync(0xffffffffu, f);
+                    if (fm) {
+                        const unsigned peers = __match_any_sync(0xffffffffu, f ? t : -1);
+                        const int leader = __ffs(peers) - 1;
+                        int base = 0;
+                        if (f && lane == leader) base = atomicAdd(&B.ucnt[t], __popc(peers));
+                        base = __shfl_sync(0xffffffffu, base, leader);
+                        if (f) {
+                            const int64_t pos = base + __popc(peers & ((1u << lane) - 1u));
+                            if (pos < B.scap) {
+                                reinterpret_cast<int *>(B.surv_eps)[t * B.scap + pos] = li;
+                                B.surv_rho[t * B.scap + pos] = gap;
+                            } else {
+                                atomicOr(&B.st[t].overflow, 1);
+                            }
+                        }
                     }
                 }
             }
-            // append to template t's unordered list, aggregated over the
-            // lanes of the warp that share t
-            const unsigned fm = __ballot_sync(0xffffffffu, f);
-            if (fm) {
-                const unsigned peers = __match_any_sync(0xffffffffu, f ? t : -1);
-                const int leader = __ffs(peers) - 1;
-                int base = 0;
-                if (f && lane == leader) base = atomicAdd(&B.ucnt[t], __popc(peers));
-                base = __shfl_sync(0xffffffffu, base, leader);
-                if (f) {
-                    const int64_t pos = base + __popc(peers & ((1u << lane) - 1u));
-                    if (pos < B.scap) {
-                        reinterpret_cast<int *>(B.surv_eps)[t * B.scap + pos] = li;
-                        B.surv_rho[t * B.scap + pos] = gap;
-                    } else {
-                        atomicOr(&B.st[t].overflow, 1);
-                    }
-                }
-            }
+            __syncthreads();   // the queue is refilled
+            if (threadIdx.x == 0) qn = 0;
+            __syncthreads();
         }
-        __syncthreads();   // the queue is refilled
     }
     __syncthreads();
     for (int i = threadIdx.x; i < T * kUbBuckets; i += blockDim.x) {
-        const int v = hist[i / kUbBuckets][i % kUbBuckets];
+        const int v = hist[i];
         if (v) atomicAdd(&B.bucket_cnt[i], v);
     }
 }
@@ -1167,14 +1245,30 @@ __device__ inline const float *stage_template(const float *tf, int m, int npad, 
     return tsm;
 }
 
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// With B.span: the block's start and end into the sweep's span (every
+// thread reaches the end: the sweeps return early only block-uniformly).
+__device__ __forceinline__ void span_end(const Scan2Batch &B, unsigned long long t0) {
+    if (!B.span) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicMin(&B.span[0], t0);
+        atomicMax(&B.span[1], gtimer());
+    }
+}
+
 // Survivors of template blockIdx.y of a batch, in bucket order, skipping
 // those whose bound has fallen below the running certain lower bound of the
 // maximum.
-__global__ void __launch_bounds__(256)
-survivors_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, int Lx,
-                 const int *__restrict__ wsum, int m, int n, int npad,
-                 const float *__restrict__ inv_sigma, int tmpl_in_smem, int stage,
-                 const uint8_t *img_end) {
+__device__ __forceinline__ void warp_sweep(const Scan2Batch &B, const uint8_t *__restrict__ I, int q, int Lx,
+                                           const int *__restrict__ wsum, int m, int n, int npad,
+                                           const float *__restrict__ inv_sigma, int tmpl_in_smem,
+                                           int stage, const uint8_t *img_end) {
     extern __shared__ float4 ssm4[];
     TmplState *st = B.st + blockIdx.y;
     if (st->flat) return;
@@ -1263,6 +1357,16 @@ survivors_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, int L
         }
     }
     if (lane == 0 && evaluated) atomicAdd(&st->n_eval, evaluated);
+}
+
+__global__ void __launch_bounds__(256)
+survivors_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, int Lx,
+                 const int *__restrict__ wsum, int m, int n, int npad,
+                 const float *__restrict__ inv_sigma, int tmpl_in_smem, int stage,
+                 const uint8_t *img_end) {
+    const unsigned long long t0 = B.span ? gtimer() : 0ull;
+    warp_sweep(B, I, q, Lx, wsum, m, n, npad, inv_sigma, tmpl_in_smem, stage, img_end);
+    span_end(B, t0);
 }
 
 // Survivors of small templates (m * n <= kLaneMaxMN): one lane per survivor.
@@ -1448,10 +1552,9 @@ __host__ __device__ inline size_t lane_tmpl_bytes(int m, int npad) {
     return ((size_t)m * npad * sizeof(float) + 15) & ~(size_t)15;
 }
 
-__global__ void __launch_bounds__(256, 2)
-survivors_lane_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, int Lx,
-                      const int *__restrict__ wsum, int m, int n, int npad,
-                      const float *__restrict__ inv_sigma, const uint8_t *img_end) {
+__device__ __forceinline__ void lane_sweep(const Scan2Batch &B, const uint8_t *__restrict__ I, int q, int Lx,
+                                           const int *__restrict__ wsum, int m, int n, int npad,
+                                           const float *__restrict__ inv_sigma, const uint8_t *img_end) {
     extern __shared__ float4 lsm4[];
     TmplState *st = B.st + blockIdx.y;
     if (st->flat) return;
@@ -1594,6 +1697,15 @@ survivors_lane_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, 
     }
     evaluated = __reduce_add_sync(0xffffffffu, evaluated);
     if (lane == 0 && evaluated) atomicAdd(&st->n_eval, evaluated);
+}
+
+__global__ void __launch_bounds__(256, 2)
+survivors_lane_kernel(const Scan2Batch B, const uint8_t *__restrict__ I, int q, int Lx,
+                      const int *__restrict__ wsum, int m, int n, int npad,
+                      const float *__restrict__ inv_sigma, const uint8_t *img_end) {
+    const unsigned long long t0 = B.span ? gtimer() : 0ull;
+    lane_sweep(B, I, q, Lx, wsum, m, n, npad, inv_sigma, img_end);
+    span_end(B, t0);
 }
 
 // After the priority pass: the survivors from the first bucket whose largest
@@ -1885,7 +1997,8 @@ cudaError_t launch_threshold(TmplState *st, const double *cand_rho_topk, int T, 
 cudaError_t launch_bound_compact(const Scan2Batch &B, const float2 *theta_co, const float2 *gco,
                                  int Ly, int Lx, int h, float *ub_map, uint8_t *surv_map,
                                  cudaStream_t s) {
-    if (B.T < 1 || B.T > kS2MaxT || ((ub_map || surv_map) && B.T != 1)) return cudaErrorInvalidValue;
+    if (B.T < 1 || B.T > kS2MaxT || ((ub_map || surv_map) && B.T != 1) || h < 1 || h > 9)
+        return cudaErrorInvalidValue;
     const int64_t G = (int64_t)groups_along(Ly, h) * groups_along(Lx, h);
     const int64_t tiles = (G + kPassGroups - 1) / kPassGroups;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)num_sms() * 8));
@@ -1893,8 +2006,11 @@ cudaError_t launch_bound_compact(const Scan2Batch &B, const float2 *theta_co, co
     if (e == cudaSuccess) e = cudaMemsetAsync(B.ucnt, 0, (size_t)B.T * sizeof(int), s);
     if (e != cudaSuccess) return e;
     {
+        const size_t smem = bound_pass_smem(B.T);
+        if ((e = ensure_smem(reinterpret_cast<const void *>(bound_pass_kernel), smem)) != cudaSuccess)
+            return e;
         LaunchScope ls("bound_pass_kernel", s);
-        bound_pass_kernel<<<grid, 256, 0, s>>>(B, gco, theta_co, Ly, Lx, h);
+        bound_pass_kernel<<<grid, 256, smem, s>>>(B, gco, theta_co, Ly, Lx, h);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
@@ -1904,7 +2020,9 @@ cudaError_t launch_bound_compact(const Scan2Batch &B, const float2 *theta_co, co
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
         LaunchScope ls("bound_sort_kernel", s);
-        bound_sort_kernel<<<dim3(std::max(1, num_sms() * 4 / B.T), B.T), 256, 0, s>>>(B);
+        // every template gets the blocks a long list needs; the blocks past a
+        // short list's chunks return at once
+        bound_sort_kernel<<<dim3(num_sms() * 4, B.T), 256, 0, s>>>(B);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ub_map || surv_map) {

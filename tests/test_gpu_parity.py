@@ -140,6 +140,26 @@ def test_fixed_group_sizes_many_templates(opta, hsz):
     h.close()
 
 
+@pytest.mark.parametrize("hsz", [3, 5, 7])
+def test_group_test_keeps_every_survivor(opta, hsz):
+    """The group-first pass (a conservative group test, then each member's
+    exact test) keeps exactly the locations the full survivor map marks:
+    the search's survivor count equals the map's, for one template per
+    search (the same scan-1 launch shape as the map's)."""
+    img = synth.aerial_image(520, n_octaves=7, n_prims=30, seed=61)
+    ts = synth.make_templates(img, [16, 24, (19, 29), 40], seed=600 + hsz, noise=3.0, quantize=True)
+    h = opta.optA_prepare(_cuda(img), opta.opta_params_default(fixed_h=hsz, blur=0))
+    try:
+        for t in ts:
+            (r,) = opta.optA_search(h, [_cuda(t.data)])
+            L = (img.shape[0] - t.data.shape[0] + 1) * (img.shape[1] - t.data.shape[1] + 1)
+            sv = torch.empty(L, dtype=torch.uint8, device="cuda")
+            opta.optA_debug_bounds(h, _cuda(t.data), None, sv)
+            assert r.n_survivors == int(sv.sum()), (t.data.shape, hsz, r.n_survivors, int(sv.sum()))
+    finally:
+        h.close()
+
+
 def test_flat_regions_and_truncated_groups(opta):
     """Constant rectangles make flat windows and flat pivots; odd image sizes
     make truncated edge groups."""
