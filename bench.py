@@ -839,7 +839,11 @@ def kernel_roofline(name, tot_ms, nl, ts, results, shape, pk, src):
     elif kind == "tensor":
         achieved = flops / nl / avg_s / 1e12
         peak = pk.get("bf16_tflops", 1900.0)
-        unit, note = "TFLOP/s", f"dense bf16 cuBLAS burst ({src})"
+        # scan 1 multiplies fp16 operands, the exhaustive map bf16 ones: the
+        # tensor cores run both at one dense rate (nominal ratio 1)
+        unit = "TFLOP/s"
+        note = (f"dense bf16 cuBLAS burst ({src}) x 1: fp16 and bf16 share the dense tensor rate"
+                if name == "corr_mma_kernel" else f"dense bf16 cuBLAS burst ({src})")
     else:
         achieved = flops / nl / avg_s / 1e12
         peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12

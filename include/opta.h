@@ -113,7 +113,7 @@ typedef struct opta_params {
     int32_t fixed_h;        /* 0: EGS chooses h; odd h > 0: fixed group side */
     int32_t blur;           /* 1: run the OptA level loop; 0: unblurred pivots */
     int32_t topk;           /* 8: centres re-evaluated on I for the threshold (1..16) */
-    int32_t precision;      /* scan 1 (centre rho): 1 = bf16 hi/lo split products on the
+    int32_t precision;      /* scan 1 (centre rho): 1 = fp16 hi/lo split products on the
                                tensor cores, FP32 accumulation (default); 0 = FP32 CUDA cores */
     int32_t literal;        /* 0 (default): exact search of I with blurred pivots bounding it.
                                1: the procedure of Section 4.3 -- EGS measures the blurred

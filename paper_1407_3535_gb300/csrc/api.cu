@@ -721,7 +721,7 @@ float dense_frac(const opta_handle *H, int m, int n) {
 // kScan1EpsB): the largest over the kernels that compute its centres.
 float scan1_eps_factor(const opta_handle *H, int m, int n) {
     const int npad = (n + 7) & ~7, Kp = (n + 15) & ~15;
-    if (use_mma(H)) return std::max(scan1_epsA_mma(m, Kp), scan1_epsA_fp32(centre_column_kacc(m, n)));
+    if (use_mma(H)) return std::max(scan1_epsA_f16(m, n, Kp), scan1_epsA_fp32(centre_column_kacc(m, n)));
     return scan1_epsA_fp32(centre_rho_kacc(m, npad));
 }
 
@@ -796,7 +796,7 @@ opta_status enqueue_scan1(opta_handle *H, opta_search_ctx *X, const opta_templat
     if (use_mma(H)) {
         const int N = ((2 * n + 15) / 16) * 16;
         CK(cudaMemsetAsync(X->Bmma, 0, (size_t)m * Kp * N * 2, s));
-        CK(launch_tmpl_split(X->tf, tsz, n, m, nn, npad, Kp, N, X->Bmma, s));
+        CK(launch_tmpl_split(X->tf, tsz, n, m, nn, npad, Kp, N, st, X->Bmma, s));
         int Gx_u = S->Gx;
         CK(launch_corr_mma(S->P, H->p, H->q, X->Bmma, m, nn, Kp, N, S->h, S->Ly, S->Lx, n,
                            S->c_inv_sigma, st, X->rho_tc, G, X->dev_err, &Gx_u, s));

@@ -93,12 +93,25 @@ __device__ inline float2 angle_interval(float r, float e) {
 }
 
 // Error bounds of scan 1's rho(t, pivot block): e = A * efac + kScan1EpsB,
-// efac = ||P - 128|| / sigma_hat of the centre.  Tensor-core form: the hi/lo
-// bf16 split holds t' to 2^-16 relative and the TMEM FP32 accumulation adds
-// at most 4u per MMA step (m * Kp/16 steps); FP32 CUDA-core forms: k
-// roundings per term.
+// efac = ||P - 128|| / sigma_hat of the centre.  bf16 tensor-core form (the
+// exhaustive map's, with 2m rows): the hi/lo bf16 split holds t' to 2^-16
+// relative and the TMEM FP32 accumulation adds at most 4u per MMA step
+// (m * Kp/16 steps); FP32 CUDA-core forms: k roundings per term.
 __host__ __device__ inline float scan1_epsA_mma(int m, int Kp) {
     return ((float)(4 * m * (Kp / 16) + 16) * kU32 + 1.55e-5f) * 1.01f;
+}
+// Scan 1 on the tensor cores in fp16: the template, scaled by a power of
+// two s so that s max|t'| lies in [2^13, 2^14), is split into fp16 hi + lo.
+// |v - hi| <= 2^-11 |v| and lo rounds v - hi to 2^-11 of itself or, below
+// fp16's normal range, to 2^-25 absolute, so the residual is at most
+// 2^-22 |v| + 2^-25 per element; summed against P - 128 and divided by
+// s sigma_t Omega_hat (s sigma_t >= s max|t'| >= 2^13) that is at most
+// (2^-22 + 2^-38 sqrt(mn)) efac, plus 2^-24 for t' rounded once to FP32.
+// The FP32 accumulation in TMEM is bounded as for the bf16 form.
+__host__ __device__ inline float scan1_epsA_f16(int m, int n, int Kp) {
+    const float mn = (float)m * (float)n;
+    return ((float)(4 * m * (Kp / 16) + 16) * kU32 + 2.384185791015625e-7f +
+            5.9604644775390625e-8f + 3.637978807091713e-12f * sqrtf(mn)) * 1.01f;
 }
 __host__ __device__ inline float scan1_epsA_fp32(int k) { return (float)(k + 2) * kU32 * 1.01f; }
 constexpr float kScan1EpsB = 8.f * kU32;
@@ -144,6 +157,8 @@ struct TmplState {
     int sum_t;                // sum of the template values (exact when u8)
     int int_op;               // exhaustive map: integer operand t - rint(mu) (see brute_mma.cu)
     float c0;                 // rint(mu) - mu when int_op, else 0
+    float tscale;             // scan 1's fp16 planes hold t' * tscale (a power of two putting
+    float tscale_inv;         // max |t'| in [2^13, 2^14)); and its inverse
 };
 
 // Floats of one template's slot in a batch: the centred FP32 template (m rows
@@ -253,7 +268,7 @@ cudaError_t launch_centre_column(const uint8_t *P, int q, const float *tf, int m
 cudaError_t launch_centre_intervals(const float *rho_tc, int64_t G, int T, const float *c_efac,
                                     float epsA, float2 *out, cudaStream_t s);
 cudaError_t launch_tmpl_split(const float *tf, size_t tsz, int T, int m, int n, int npad, int Kp,
-                              int N, void *B, cudaStream_t s);
+                              int N, const TmplState *st, void *B, cudaStream_t s);
 // Threshold centres of T templates: rho_tc of template k at k * gstride;
 // tmp_val/tmp_idx: T x 256 x kTopkMax; cand_topk: T x kTopkMax.
 cudaError_t launch_topk(const float *rho_tc, int64_t gstride, int Gy, int Gx, int h, int Ly, int Lx,

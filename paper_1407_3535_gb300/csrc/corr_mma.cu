@@ -4,8 +4,8 @@
 // For a centre row cy and 128 consecutive centres along x (spacing h):
 //
 //   D[i][j] = sum_{u<m} sum_{v<Kp} A_u[i][v] * B_u[j][v]
-//   A_u[i][v] = P(cy + u, cx0 + h*i + v) - 128            (bf16, exact)
-//   B_u[j][v] = template plane j, row u                     (bf16 hi/lo split)
+//   A_u[i][v] = P(cy + u, cx0 + h*i + v) - 128            (fp16, exact)
+//   B_u[j][v] = template plane j, row u                     (fp16 hi/lo split of s t')
 //
 // with j = 2t (hi part of template t) and 2t+1 (lo part), so each template's
 // numerator is D[i][2t] + D[i][2t+1].  D lives in TMEM; the contraction over
@@ -31,11 +31,16 @@
 // hands through mbarriers (operand written, tiles landed, MMAs done), so
 // neither side waits for the other at a CTA barrier.
 //
-// Error bound of the numerator: the hi/lo split represents each template
-// value to within 2^-16 relative; FP32 accumulation in TMEM is bounded by
-// 4u per accumulation step (one step per MMA) -- scan1_epsA_mma.  The angle
-// intervals that scan 2 needs are formed there from rho and this bound.
-#include <cuda_bf16.h>
+// The operands are fp16 (kind::f16 with both operands fp16): a pixel
+// P - 128 is an integer of at most 8 bits, exact, and converts from a byte by
+// one byte permutation and one paired subtraction (tc5::bytes_f16x2); the
+// template is scaled by a power of two s (TmplState::tscale, s max|t'| in
+// [2^13, 2^14)) and split into fp16 hi + lo, which holds it to about 2^-22;
+// the epilogue multiplies by 1/s, exactly.  FP32 accumulation in TMEM is
+// bounded by 4u per accumulation step (one step per MMA) -- scan1_epsA_f16.
+// The angle intervals that scan 2 needs are formed there from rho and this
+// bound.
+#include <cuda_fp16.h>
 
 #include <atomic>
 #include <map>
@@ -64,7 +69,7 @@ __host__ __device__ inline uint32_t round_up(uint32_t x, uint32_t a) { return (x
 struct CorrMmaArgs {
     const uint8_t *V;          // pivot image, p x q
     int p, q;
-    const __nv_bfloat16 *B;    // [m][Kp/8][N/8][8][8]
+    const __half *B;           // [m][Kp/8][N/8][8][8]
     int m, n, Kp, N;
     int h, Ly, Lx, Gx, Gx_u;   // Gx_u: leading groups whose centres are uniform (cx0 + h*i)
     int Gy, RC;                // group rows; centre rows per CTA (1, 2 or 4)
@@ -151,7 +156,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaA
     __syncthreads();
     tc5::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t idesc = tc5::idesc_bf16_f32(kMmaM, a.N);
+    const uint32_t idesc = tc5::idesc_f16_f32(kMmaM, a.N);
 
     bool ok = true;
     const int r_end = group_centre_of(gy0 + nrow - 1, a.Ly, a.h) + a.m;
@@ -241,8 +246,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaA
                 const uint32_t lo = __funnelshift_r(iw.w0, iw.w1, iw.sh);
                 const uint32_t hi = __funnelshift_r(iw.w1, iw.w2, iw.sh);
                 *reinterpret_cast<uint4 *>(Ab + (j >> 3) * 128 + (j & 7) * 16) =
-                    make_uint4(tc5::bytes_bf16x2<0>(lo), tc5::bytes_bf16x2<2>(lo), tc5::bytes_bf16x2<0>(hi),
-                               tc5::bytes_bf16x2<2>(hi));
+                    make_uint4(tc5::bytes_f16x2<0>(lo), tc5::bytes_f16x2<2>(lo), tc5::bytes_f16x2<0>(hi),
+                               tc5::bytes_f16x2<2>(hi));
             }
             tc5::fence_proxy_async_smem();
             __syncwarp();
@@ -272,7 +277,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaA
                     const int t = (c0 + q2) >> 1;
                     if (valid && t < a.T) {
                         const float num = v[q2] + v[q2 + 1];
-                        a.rho_tc[t * a.gstride + g] = (num * a.st[t].inv_sigma) * cis;
+                        // num holds t' scaled by the template's power of two
+                        a.rho_tc[t * a.gstride + g] = ((num * a.st[t].tscale_inv) * a.st[t].inv_sigma) * cis;
                     }
                 }
             }
@@ -285,19 +291,20 @@ __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaA
     if (warp == 0) tc5::tmem_dealloc(tmem, ncols);
 }
 
-// Template t' (FP32, m x npad) -> hi/lo bf16 planes 2t, 2t+1 of the B buffer;
+// Template t' (FP32, m x npad) -> hi/lo fp16 planes 2t, 2t+1 of s t' in the B buffer;
 // template t = t0 + blockIdx.y, whose t' is at tf + blockIdx.y * tsz.
 __global__ void tmpl_split_kernel(const float *__restrict__ tf, size_t tsz, int m, int n, int npad,
-                                  int Kp, int N, int t0, __nv_bfloat16 *B) {
+                                  int Kp, int N, int t0, const TmplState *__restrict__ st, __half *B) {
     const int t = t0 + blockIdx.y;
     tf += blockIdx.y * tsz;
+    const float sc = st[blockIdx.y].tscale;   // a power of two: exact
     const int total = m * Kp;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += gridDim.x * blockDim.x) {
         const int u = idx / Kp, v = idx % Kp;
-        const float x = v < n ? tf[u * npad + v] : 0.f;
-        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+        const float x = v < n ? tf[u * npad + v] * sc : 0.f;
+        const __half hi = __float2half_rn(x);
+        const __half lo = __float2half_rn(x - __half2float(hi));
         const int64_t base = (((int64_t)u * (Kp / 8) + v / 8) * (N / 8)) * 64 + (v % 8);
         const int j0 = 2 * t, j1 = 2 * t + 1;
         B[base + (int64_t)(j0 / 8) * 64 + (j0 % 8) * 8] = hi;
@@ -313,11 +320,11 @@ size_t corr_mma_smem(int h, int Kp, int N, int RC) {
 }
 
 cudaError_t launch_tmpl_split(const float *tf, size_t tsz, int T, int m, int n, int npad, int Kp,
-                              int N, void *B, cudaStream_t s) {
+                              int N, const TmplState *st, void *B, cudaStream_t s) {
     LaunchScope ls("tmpl_split_kernel", s);
     const int total = m * Kp;
     tmpl_split_kernel<<<dim3((total + 255) / 256, T), 256, 0, s>>>(
-        tf, tsz, m, n, npad, Kp, N, 0, static_cast<__nv_bfloat16 *>(B));
+        tf, tsz, m, n, npad, Kp, N, 0, st, static_cast<__half *>(B));
     return cudaGetLastError();
 }
 
@@ -356,7 +363,7 @@ cudaError_t launch_corr_mma(const uint8_t *V, int p, int q, const void *B, int m
     };
     CorrMmaArgs a;
     a.V = V; a.p = p; a.q = q;
-    a.B = static_cast<const __nv_bfloat16 *>(B);
+    a.B = static_cast<const __half *>(B);
     a.m = m; a.n = n; a.Kp = Kp; a.N = N;
     a.h = h; a.Ly = Ly; a.Lx = Lx; a.Gx = Gx; a.Gx_u = Gx_u;
     a.Gy = Gy;

@@ -308,17 +308,19 @@ template <int H>
 __global__ void __launch_bounds__(RcoCfg<H>::MAXT, 1)
 rho_co_kernel(const uint8_t *__restrict__ P, const uint8_t *__restrict__ I, int p, int q,
               int m, int n, int Ly, int Lx, const int *__restrict__ wsum,
-              const float *__restrict__ inv_sigma, int GXS, int GYB, int GYS, int K, float cut,
-              float *rco, unsigned long long *count, float *c_inv_sigma, float *c_efac) {
+              const float *__restrict__ inv_sigma, int GXS, int GYB, int GYS, int SUB, int K,
+              float cut, float *rco, unsigned long long *count, float *c_inv_sigma, float *c_efac) {
     constexpr int R = RcoCfg<H>::R;
     constexpr int NS = RcoCfg<H>::NS;
     constexpr int KW = RcoCfg<H>::KW;
     constexpr int BATCH = RcoCfg<H>::BATCH;
     extern __shared__ unsigned rsm[];
     const int Gy = groups_along(Ly, H), Gx = groups_along(Lx, H);
-    // band blockIdx.y: group rows [gy0, gy0 + GYB), bands GYS apart (GYS =
-    // GYB: every group row; GYS > GYB: the sampled runs of a count)
-    const int gx0 = blockIdx.x * GXS, gy0 = blockIdx.y * GYS;
+    // band blockIdx.y: group rows [gy0, gy0 + GYB); runs of SUB bands, runs
+    // GYS apart (SUB = 1, GYS = GYB: every group row; GYS > SUB GYB: the
+    // sampled runs of a count, each split into SUB bands)
+    const int gx0 = blockIdx.x * GXS;
+    const int gy0 = (blockIdx.y / SUB) * GYS + (blockIdx.y % SUB) * GYB;
     if (gx0 >= Gx || gy0 >= Gy) return;
     const int gx1 = min(Gx, gx0 + GXS), gy1 = min(Gy, gy0 + GYB);
     const int ngx = gx1 - gx0;
@@ -858,13 +860,24 @@ cudaError_t launch_rho_co_h(const uint8_t *P, const uint8_t *I, int p, int q, in
         bps = 1;
     }
     const int Gy = groups_along(Ly, H);
-    int GYB, GYS, bands;
+    int GYB, GYS, bands, sub = 1;
     if (sample > 1) {
-        // a count over the sampled runs only: one band per run of kEgsRun
-        // group rows, every sample-th run
-        GYB = kEgsRun;
+        // a count over the sampled runs only (kEgsRun group rows, every
+        // sample-th run), each run split into sub bands: a band's time is
+        // about its rows (its group rows' H rows each, plus the m - 1 rows
+        // its windows reach below), so a run is split while the CTAs still
+        // fit in fewer waves than the rows saved
         GYS = kEgsRun * sample;
-        bands = (Gy + GYS - 1) / GYS;
+        const int runs = (Gy + GYS - 1) / GYS;
+        double best = 0.0;
+        for (int d = 1; d <= kEgsRun; d *= 2) {
+            const int64_t ctas = (int64_t)g.strips * runs * d;
+            const int64_t waves = (ctas + (int64_t)num_sms() * bps - 1) / ((int64_t)num_sms() * bps);
+            const double t = (double)waves * (double)((kEgsRun / d) * H + m - 1);
+            if (d == 1 || t < best) { best = t; sub = d; }
+        }
+        GYB = kEgsRun / sub;
+        bands = runs * sub;
     } else {
         bands = std::max(1, std::min(Gy, num_sms() * bps / g.strips));
         GYB = (Gy + bands - 1) / bands;
@@ -885,7 +898,7 @@ cudaError_t launch_rho_co_h(const uint8_t *P, const uint8_t *I, int p, int q, in
     const bool count_only = !rco && !c_inv_sigma && !c_efac;
     LaunchScope ls_rho_co_kernel(count_only ? kCountName[H] : kName[H], s);
     rho_co_kernel<H><<<grid, g.threads, smem, s>>>(P, I, p, q, m, n, Ly, Lx, wsum, inv_sigma,
-                                                   g.GXS, GYB, GYS, g.K, cut, rco, count,
+                                                   g.GXS, GYB, GYS, sub, g.K, cut, rco, count,
                                                    c_inv_sigma, c_efac);
     return cudaGetLastError();
 }

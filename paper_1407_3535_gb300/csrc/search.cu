@@ -102,11 +102,29 @@ tmpl_prep_kernel(const float *__restrict__ t, int64_t ld, const TmplIn *__restri
         td[i] = d;
         ss += d * d;
     }
+    double amax = 0.0;   // max |t'| (for scan 1's fp16 scale)
     for (int i = threadIdx.x; i < m * npad; i += blockDim.x) {
         const int u = i / npad, v = i % npad;
-        tf[i] = v < n ? (float)((double)t[(int64_t)u * ld + v] - mu) : 0.f;
+        const float x = v < n ? (float)((double)t[(int64_t)u * ld + v] - mu) : 0.f;
+        tf[i] = x;
+        amax = fmax(amax, (double)fabsf(x));
     }
     ss = block_sum_d(ss, sh);
+    // block maximum of amax (values >= 0: the maximum of the squares' order)
+    {
+        for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = amax;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double r = (int)threadIdx.x < (int)(blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+            if (threadIdx.x == 0) sh[0] = r;
+        }
+        __syncthreads();
+        amax = sh[0];
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
         const double sg = sqrt(ss);
         st->mu = mu;
@@ -134,6 +152,14 @@ tmpl_prep_kernel(const float *__restrict__ t, int64_t ld, const TmplIn *__restri
         // bound while sigma_t >= sqrt(mn) / 6 (brute_mma.cu)
         st->int_op = whole && sg >= sqrt((double)mn) / 6.0 ? 1 : 0;
         st->c0 = st->int_op ? (float)(rint(mu) - mu) : 0.f;
+        // s = 2^(14 - e) for max|t'| = f 2^e, f in [0.5, 1): s max|t'| in [2^13, 2^14)
+        int e = 0;
+        if (amax > 0.0) frexp(amax, &e);
+        // (k clamped to float's normal range: only templates whose values
+        // differ by less than 2^-112 would need more)
+        const int k = amax > 0.0 ? max(-126, min(126, 14 - e)) : 0;
+        st->tscale = ldexpf(1.f, k);
+        st->tscale_inv = ldexpf(1.f, -k);
     }
 }
 

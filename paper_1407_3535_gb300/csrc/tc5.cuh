@@ -3,6 +3,7 @@
 // copies.  Every wait is bounded by a %globaltimer deadline.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -103,13 +104,19 @@ __device__ inline uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
+// Instruction descriptor of kind::f16: F16 x F16 -> FP32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 // Instruction descriptor of kind::f16: BF16 x BF16 -> FP32, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);
 }
 
-// D(tmem) (+)= A(smem) * B(smem)^T, issued by one thread.
+// D(tmem) (+)= A(smem) * B(smem)^T, issued by one thread (kind::f16: the
+// operands' type, bf16 or fp16 for both, is in the instruction descriptor).
 __device__ inline void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                 bool accumulate) {
     asm volatile(
@@ -162,6 +169,16 @@ __device__ __forceinline__ uint32_t bytes_bf16x2(uint32_t w) {
     const float f0 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7650 + K)) - 8388736.f;
     const float f1 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7650 + K + 1)) - 8388736.f;
     return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+}
+
+// Bytes K and K + 1 of w as the fp16 pair (b - 128) (low half = byte K):
+// 0x64bb is the fp16 value 1024 + b (exponent of 2^10, b in the mantissa),
+// and 1024 + b - 1152 = b - 128 is exact.
+template <int K>
+__device__ __forceinline__ uint32_t bytes_f16x2(uint32_t w) {
+    const uint32_t h = __byte_perm(w, 0x6464u, 0x5040u + (uint32_t)K + ((uint32_t)(K + 1) << 8));
+    const __half2 v = __hsub2(*reinterpret_cast<const __half2 *>(&h), __half2half2(__ushort_as_half(0x6480u)));
+    return *reinterpret_cast<const uint32_t *>(&v);
 }
 
 // 32 lanes x 8 columns of 32-bit TMEM data: thread i of the warp gets
