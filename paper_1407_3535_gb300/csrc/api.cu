@@ -813,7 +813,7 @@ opta_status enqueue_scan1(opta_handle *H, opta_search_ctx *X, const opta_templat
     CK(launch_topk(X->rho_tc, G, S->Gy, S->Gx, S->h, S->Ly, S->Lx, H->prm.topk, n, st, X->topk_v,
                    X->topk_i, X->cand_topk, s));
     CK(launch_refine64_topk(S->M, H->q, S->Lx, X->td, dsz, m, nn, n, st, X->cand_topk,
-                            X->cand_rho_topk, s));
+                            X->cand_rho_topk, s, X->tf, tsz, npad));
     CK(launch_group_members(S->M, H->q, S->Ly, S->Lx, S->h, S->wsumM, X->tf, tsz, m, nn,
                             npad, S->invM, n, st, X->cand_topk, H->prm.topk, s));
     CK(launch_threshold(st, X->cand_rho_topk, n, s));
@@ -993,7 +993,7 @@ opta_status enqueue_scan2(opta_handle *H, opta_search_ctx *X, const opta_templat
         }
         CK(launch_surv_candidates(B, s));
         CK(launch_refine64(S->M, H->q, S->Lx, X->td + k0 * dsz, dsz, m, nn, T, st + k0, X->cand,
-                           X->cand_rho, scap, s));
+                           X->cand_rho, scap, s, X->tf + k0 * tsz, tsz, npad));
         CK(launch_final_argmax(T, st + k0, X->cand, X->cand_rho, scap, X->cand_topk + k0 * kTopkMax,
                                X->cand_rho_topk + k0 * kTopkMax, s));
         if (H->prm.literal) {
@@ -1001,7 +1001,7 @@ opta_status enqueue_scan2(opta_handle *H, opta_search_ctx *X, const opta_templat
             // neighbourhood of the maximum found on the blurred image
             CK(launch_rematch_window(T, st + k0, S->Ly, S->Lx, S->d, X->cand, scap, s));
             CK(launch_refine64(H->I8, H->q, S->Lx, X->td + k0 * dsz, dsz, m, nn, T, st + k0,
-                               X->cand, X->cand_rho, scap, s));
+                               X->cand, X->cand_rho, scap, s, X->tf + k0 * tsz, tsz, npad));
             CK(launch_final_argmax(T, st + k0, X->cand, X->cand_rho, scap, nullptr, nullptr, s));
         }
     }

@@ -159,6 +159,7 @@ struct TmplState {
     float c0;                 // rint(mu) - mu when int_op, else 0
     float tscale;             // scan 1's fp16 planes hold t' * tscale (a power of two putting
     float tscale_inv;         // max |t'| in [2^13, 2^14)); and its inverse
+    long long sumsq_t;        // sum of the squared template values (exact when u8)
 };
 
 // Floats of one template's slot in a batch: the centred FP32 template (m rows
@@ -232,9 +233,12 @@ cudaError_t launch_map_candidates(const float *map, const float *efac128, int64_
 
 // FP64 recomputation of rho at the candidate locations [0, n_cand) of T
 // templates (template k: td + k * dsz, st + k, cand / cand_rho + k * ccap).
+// With the batch's template slots (tf + k * tsz, nullable), a template of
+// bytes takes exact integer sums and an FP64 finish instead.
 cudaError_t launch_refine64(const uint8_t *I, int q, int Lx, const double *td, size_t dsz, int m,
                             int n, int T, TmplState *st, const int *cand, double *cand_rho,
-                            int64_t ccap, cudaStream_t s);
+                            int64_t ccap, cudaStream_t s, const float *tf = nullptr, size_t tsz = 0,
+                            int npad = 0);
 // Final argmax over the candidates and threshold centres (nullable; kTopkMax
 // per template) of T templates -> st->best_idx / best_rho.
 cudaError_t launch_final_argmax(int T, TmplState *st, const int *cand, const double *cand_rho,
@@ -243,10 +247,12 @@ cudaError_t launch_final_argmax(int T, TmplState *st, const int *cand, const dou
 // Literal mode: candidates := the (2d+1)^2 neighbourhood of best_idx.
 cudaError_t launch_rematch_window(int T, TmplState *st, int Ly, int Lx, int d, int *cand,
                                   int64_t ccap, cudaStream_t s);
-// FP64 rho at the threshold centres of T templates (kTopkMax slots each).
+// FP64 rho at the threshold centres of T templates (kTopkMax slots each);
+// tf / tsz / npad as for launch_refine64.
 cudaError_t launch_refine64_topk(const uint8_t *I, int q, int Lx, const double *td, size_t dsz,
                                  int m, int n, int T, TmplState *st, const int *cand_topk,
-                                 double *cand_rho_topk, cudaStream_t s);
+                                 double *cand_rho_topk, cudaStream_t s, const float *tf = nullptr,
+                                 size_t tsz = 0, int npad = 0);
 
 // --- pruned search ---
 // rho_tc per group and the angle interval of its true value (tc), for the

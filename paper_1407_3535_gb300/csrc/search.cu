@@ -74,15 +74,17 @@ tmpl_prep_kernel(const float *__restrict__ t, int64_t ld, const TmplIn *__restri
     tf += k * tsz;
     td += k * dsz;
     st += k;
-    double s = 0.0;
+    double s = 0.0, s2 = 0.0;
     int whole = 1;   // every value an integer in 0..255
     for (int i = threadIdx.x; i < mn; i += blockDim.x) {
         const float v = t[(int64_t)(i / n) * ld + (i % n)];
         s += (double)v;
+        s2 += (double)v * (double)v;   // exact for integers (below 2^53)
         whole &= (v >= 0.f && v <= 255.f && v == rintf(v)) ? 1 : 0;
     }
     whole = __syncthreads_and(whole);
     s = block_sum_d(s, sh);
+    s2 = block_sum_d(s2, sh);
     if (pack && whole) {
         // the bytes, four to a word, rows of round_up(n, 16) bytes
         uint32_t *tb = reinterpret_cast<uint32_t *>(tf + (size_t)m * npad);
@@ -148,6 +150,7 @@ tmpl_prep_kernel(const float *__restrict__ t, int64_t ld, const TmplIn *__restri
         st->n_first = 0;
         st->u8 = pack && whole;
         st->sum_t = whole ? (int)s : 0;   // exact: integers below 2^22
+        st->sumsq_t = whole ? (long long)s2 : 0;
         // the exhaustive map's integer operand t - rint(mu) keeps its error
         // bound while sigma_t >= sqrt(mn) / 6 (brute_mma.cu)
         st->int_op = whole && sg >= sqrt((double)mn) / 6.0 ? 1 : 0;
@@ -289,6 +292,45 @@ __global__ void map_candidates_kernel(const float *__restrict__ map, const float
     }
 }
 
+// Eq. rho1 at the window (y, x) for a template of bytes (tb: its rows of
+// round_up(n, 16) / 4 packed words), by the whole block: sum t I, sum I and
+// sum I^2 are integers (exact in the block's FP64 sums, all below 2^53), so
+// the numerator mn sum tI - sum t sum I and the variances mn sum t^2 -
+// (sum t)^2 and mn sum I^2 - (sum I)^2 are exact in int64 and only the FP64
+// square root and division round.  Flat window: 0.  Valid in thread 0.
+__device__ double block_rho_u8(const uint8_t *__restrict__ I, int q, int y, int x,
+                               const uint32_t *__restrict__ tb, int m, int n, const TmplState *st,
+                               double *sh) {
+    const int wr = ((n + 15) & ~15) >> 2;
+    const int mn = m * n;
+    unsigned stb = 0u, sb = 0u, sbb = 0u;   // per thread: below 2^32 for any window of 16 M pixels
+    // pixel i = r n + c, stepped by the block size without a division per pixel
+    int pr = (int)threadIdx.x / n, pc = (int)threadIdx.x - pr * n;
+    const int dr = (int)blockDim.x / n, dc = (int)blockDim.x - dr * n;
+    for (int i = threadIdx.x; i < mn; i += blockDim.x) {
+        const unsigned b = I[(int64_t)(y + pr) * q + x + pc];
+        const unsigned t = (tb[pr * wr + (pc >> 2)] >> (8 * (pc & 3))) & 255u;
+        stb += t * b;
+        sb += b;
+        sbb += b * b;
+        pr += dr;
+        pc += dc;
+        if (pc >= n) { pc -= n; ++pr; }
+    }
+    const double Stb = block_sum_d((double)stb, sh);
+    const double Sb = block_sum_d((double)sb, sh);
+    const double Sbb = block_sum_d((double)sbb, sh);
+    double r = 0.0;
+    if (threadIdx.x == 0) {
+        const long long lmn = mn;
+        const long long num = lmn * (long long)Stb - (long long)st->sum_t * (long long)Sb;
+        const long long vt = lmn * st->sumsq_t - (long long)st->sum_t * (long long)st->sum_t;
+        const long long vb = lmn * (long long)Sbb - (long long)Sb * (long long)Sb;
+        r = (vt > 0 && vb > 0) ? (double)num / sqrt((double)vt * (double)vb) : 0.0;
+    }
+    return r;
+}
+
 // ---------------------------------------------------------------------------
 // FP64 recomputation of Eq. rho1 at candidate locations (two passes, as the
 // definition reads).  One block per candidate.
@@ -297,7 +339,7 @@ __global__ void map_candidates_kernel(const float *__restrict__ map, const float
 __global__ void __launch_bounds__(256)
 refine64_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__restrict__ td,
                 size_t dsz, int m, int n, TmplState *st, const int *__restrict__ cand,
-                double *cand_rho, int64_t ccap) {
+                double *cand_rho, int64_t ccap, const float *__restrict__ tf, size_t tsz, int npad) {
     __shared__ double sh[32];
     st += blockIdx.y;
     if (st->flat) return;
@@ -308,9 +350,16 @@ refine64_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__re
     const int mn = m * n;
     const int r0 = (int)threadIdx.x / n, c0 = (int)threadIdx.x - r0 * n;   // start of this thread
     const int dr = (int)blockDim.x / n, dc = (int)blockDim.x - dr * n;    // its stride in (row, col)
+    const uint32_t *tb = tf && st->u8 ? reinterpret_cast<const uint32_t *>(tf + blockIdx.y * tsz + (size_t)m * npad)
+                                      : nullptr;
     for (int c = blockIdx.x; c < to; c += gridDim.x) {
         const int idx = cand[c];
         const int y = idx / Lx, x = idx % Lx;
+        if (tb) {
+            const double r = block_rho_u8(I, q, y, x, tb, m, n, st, sh);
+            if (threadIdx.x == 0) cand_rho[c] = r;
+            continue;
+        }
         const uint8_t *w = I + (int64_t)y * q + x;
         long long si = 0;
         for (int i = threadIdx.x, r = r0, cc = c0; i < mn; i += blockDim.x) {
@@ -340,7 +389,7 @@ refine64_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__re
 __global__ void __launch_bounds__(256)
 refine64_topk_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double *__restrict__ td,
                      size_t dsz, int m, int n, TmplState *st, const int *__restrict__ cand_topk,
-                     double *cand_rho_topk) {
+                     double *cand_rho_topk, const float *__restrict__ tf, size_t tsz, int npad) {
     __shared__ double sh[32];
     const int j = blockIdx.x, k = blockIdx.y;
     st += k;
@@ -349,6 +398,12 @@ refine64_topk_kernel(const uint8_t *__restrict__ I, int q, int Lx, const double 
     const int mn = m * n;
     const int idx = cand_topk[k * kTopkMax + j];
     const int y = idx / Lx, x = idx % Lx;
+    if (tf && st->u8) {
+        const double r = block_rho_u8(I, q, y, x, reinterpret_cast<const uint32_t *>(tf + k * tsz + (size_t)m * npad),
+                                      m, n, st, sh);
+        if (threadIdx.x == 0) cand_rho_topk[k * kTopkMax + j] = r;
+        return;
+    }
     long long si = 0;
     for (int i = threadIdx.x; i < mn; i += blockDim.x)
         si += I[(int64_t)(y + i / n) * q + x + (i % n)];
@@ -1923,10 +1978,11 @@ cudaError_t launch_map_candidates(const float *map, const float *efac128, int64_
 
 cudaError_t launch_refine64(const uint8_t *I, int q, int Lx, const double *td, size_t dsz, int m,
                             int n, int T, TmplState *st, const int *cand, double *cand_rho,
-                            int64_t ccap, cudaStream_t s) {
+                            int64_t ccap, cudaStream_t s, const float *tf, size_t tsz, int npad) {
     const int bx = std::max(1, num_sms() * 2 / std::min(T, 8));
     LaunchScope ls_refine64_kernel("refine64_kernel", s);
-    refine64_kernel<<<dim3(bx, T), 256, 0, s>>>(I, q, Lx, td, dsz, m, n, st, cand, cand_rho, ccap);
+    refine64_kernel<<<dim3(bx, T), 256, 0, s>>>(I, q, Lx, td, dsz, m, n, st, cand, cand_rho, ccap, tf,
+                                                tsz, npad);
     return cudaGetLastError();
 }
 
@@ -1948,10 +2004,11 @@ cudaError_t launch_rematch_window(int T, TmplState *st, int Ly, int Lx, int d, i
 
 cudaError_t launch_refine64_topk(const uint8_t *I, int q, int Lx, const double *td, size_t dsz,
                                  int m, int n, int T, TmplState *st, const int *cand_topk,
-                                 double *cand_rho_topk, cudaStream_t s) {
+                                 double *cand_rho_topk, cudaStream_t s, const float *tf, size_t tsz,
+                                 int npad) {
     LaunchScope ls("refine64_topk_kernel", s);
     refine64_topk_kernel<<<dim3(kTopkMax, T), 256, 0, s>>>(I, q, Lx, td, dsz, m, n, st, cand_topk,
-                                                           cand_rho_topk);
+                                                           cand_rho_topk, tf, tsz, npad);
     return cudaGetLastError();
 }
 
