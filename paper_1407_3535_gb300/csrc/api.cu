@@ -856,7 +856,7 @@ Scan2Batch scan2_batch_of(opta_handle *H, opta_search_ctx *X, SizeState *S, Tmpl
                          : std::max<int64_t>(1024, (int64_t)(20.0 * (double)L / ((double)m * nn)));
     B.phase = 0;
     // survivors of byte templates on the image itself: exact integer sums
-    // over the 16-byte-aligned copy
+    // over the 32-byte-aligned copy
     B.Ipad = S->M == H->I8 ? H->Ipad : nullptr;
     B.qs = H->qs;
     B.lane_min_u8 = survivor_lane_min(m, nn, true);
@@ -1441,8 +1441,9 @@ opta_status optA_prepare(const opta_image *img, const opta_params *prm, const in
     opta_status st;
     if ((st = H->mem.alloc(&H->I8, (size_t)p * q)) != OPTA_OK) return fail(st);
     if ((st = ingest(img, H->I8, s)) != OPTA_OK) return fail(st);
-    // the image with 16-byte rows for the tensor-core map of survivor-heavy templates
-    H->qs = (q + 15) & ~15;
+    // the image with rows padded to 32 bytes (the tensor-core map's 2-D copies
+    // and the survivors' 32-byte loads)
+    H->qs = (q + 31) & ~31;
     if ((st = H->mem.alloc(&H->Ipad, (size_t)p * H->qs)) != OPTA_OK) return fail(st);
     {
         const cudaError_t e0 = launch_pad_rows(H->I8, p, q, H->Ipad, H->qs, s);

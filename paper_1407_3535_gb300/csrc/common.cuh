@@ -164,10 +164,11 @@ struct TmplState {
 
 // Floats of one template's slot in a batch: the centred FP32 template (m rows
 // of npad = round_up(n, 8)) and then its values as bytes, four to a 32-bit
-// word, in rows of round_up(n, 16) bytes with zeros past column n (written
-// and meaningful only when TmplState::u8).
+// word, in rows of tmpl_row_bytes(n) = round_up(n, 32) bytes with zeros past
+// column n (written and meaningful only when TmplState::u8).
+__host__ __device__ inline int tmpl_row_bytes(int n) { return (n + 31) & ~31; }
 __host__ __device__ inline size_t tmpl_slot_floats(int m, int n) {
-    return (size_t)m * ((n + 7) & ~7) + (size_t)m * ((n + 15) & ~15) / 4;
+    return (size_t)m * ((n + 7) & ~7) + (size_t)m * tmpl_row_bytes(n) / 4;
 }
 
 // Survivors are bucketed by their upper bound (bucket 0 = highest) so that

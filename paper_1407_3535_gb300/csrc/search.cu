@@ -86,9 +86,9 @@ tmpl_prep_kernel(const float *__restrict__ t, int64_t ld, const TmplIn *__restri
     s = block_sum_d(s, sh);
     s2 = block_sum_d(s2, sh);
     if (pack && whole) {
-        // the bytes, four to a word, rows of round_up(n, 16) bytes
+        // the bytes, four to a word, rows of tmpl_row_bytes(n) bytes
         uint32_t *tb = reinterpret_cast<uint32_t *>(tf + (size_t)m * npad);
-        const int wr = ((n + 15) & ~15) / 4;
+        const int wr = tmpl_row_bytes(n) / 4;
         for (int i = threadIdx.x; i < m * wr; i += blockDim.x) {
             const int u = i / wr, v0 = 4 * (i % wr);
             uint32_t w = 0u;
@@ -293,7 +293,7 @@ __global__ void map_candidates_kernel(const float *__restrict__ map, const float
 }
 
 // Eq. rho1 at the window (y, x) for a template of bytes (tb: its rows of
-// round_up(n, 16) / 4 packed words), by the whole block: sum t I, sum I and
+// tmpl_row_bytes(n) / 4 packed words), by the whole block: sum t I, sum I and
 // sum I^2 are integers (exact in the block's FP64 sums, all below 2^53), so
 // the numerator mn sum tI - sum t sum I and the variances mn sum t^2 -
 // (sum t)^2 and mn sum I^2 - (sum I)^2 are exact in int64 and only the FP64
@@ -301,7 +301,7 @@ __global__ void map_candidates_kernel(const float *__restrict__ map, const float
 __device__ double block_rho_u8(const uint8_t *__restrict__ I, int q, int y, int x,
                                const uint32_t *__restrict__ tb, int m, int n, const TmplState *st,
                                double *sh) {
-    const int wr = ((n + 15) & ~15) >> 2;
+    const int wr = tmpl_row_bytes(n) >> 2;
     const int mn = m * n;
     unsigned stb = 0u, sb = 0u, sbb = 0u;   // per thread: below 2^32 for any window of 16 M pixels
     // pixel i = r n + c, stepped by the block size without a division per pixel
@@ -1234,11 +1234,12 @@ __device__ inline void warp_rho32(const uint8_t *__restrict__ I, int q, int Lx,
 //   sum (t - mu_t)(I - mu_I) = (mn * sum t I - sum t * sum I) / mn,
 // with sum t I accumulated exactly by 4-byte dot products (dp4a, u8 x u8 into
 // u32: at most mn * 255^2 < 2^32 for mn <= kU8MaxMN) and the difference in
-// int64.  In the lane form the window's rows come from the 16-byte-aligned
-// copy of the image (rows of qs bytes) in 16-byte loads: chunk c of 16 columns needs the
-// aligned blocks c and c + 1 of the row, from which the window's words are
-// selected by the offset o = x mod 16 (word o / 4, then a funnel shift by
-// 8 (o mod 4) bits).  Only the last rounding steps remain: the conversion of
+// int64.  In the lane form the window's rows come from the aligned copy of
+// the image (rows of qs bytes, a multiple of 32) in 32-byte loads: chunk c
+// of 32 columns needs the aligned blocks c and c + 1 of the row, from which
+// the window's words are selected by the offset o = x mod 32 (word o / 4,
+// then a funnel shift by 8 (o mod 4) bits); templates wider than 128 take
+// 16-byte loads.  Only the last rounding steps remain: the conversion of
 // the integer, the division by mn and the two products with 1/sigma_t and
 // 1/Omega (each within a few ulp), so |rho - rho_exact| <= kU8Eps.
 constexpr int kU8MaxMN = 32768;
@@ -1255,7 +1256,7 @@ __device__ inline void warp_rho_u8(const uint8_t *__restrict__ I, int q, int Lx,
                                    float &rho, float &eps) {
     const int lane = threadIdx.x & 31;
     const int y = idx / Lx, x = idx % Lx;
-    const int wr = ((n + 15) & ~15) / 4;   // words per packed template row
+    const int wr = tmpl_row_bytes(n) / 4;   // words per packed template row
     const int WB = stage_width(n);
     const int nch = (m + kStageRows - 1) / kStageRows;
     const int n4 = n >> 2;
@@ -1375,7 +1376,7 @@ __device__ __forceinline__ void warp_sweep(const Scan2Batch &B, const uint8_t *_
         const uint4 *src = reinterpret_cast<const uint4 *>(tf + (size_t)m * npad);
         tb = reinterpret_cast<const uint32_t *>(src);
         if (tmpl_in_smem) {
-            const int n16 = m * ((n + 15) >> 4);
+            const int n16 = m * (tmpl_row_bytes(n) >> 4);
             for (int i = threadIdx.x; i < n16; i += blockDim.x) reinterpret_cast<uint4 *>(ssm4)[i] = src[i];
             __syncthreads();
             tb = reinterpret_cast<const uint32_t *>(ssm4);
@@ -1473,73 +1474,115 @@ __device__ __forceinline__ unsigned dp4a_chunk(uint4 cur, uint4 nxt, bool k1, bo
     return acc;
 }
 
-// window_dot_u8 for rows of NCH chunks (n <= 16 NCH): the NCH + 1 aligned
-// blocks of R rows are loaded together (R = 4, 2 or 1 as the rows widen),
-// so one load latency covers R rows (the generic form waits on every
-// chunk's block in turn).
-template <int NCH>
-__device__ __forceinline__ void load_row_u8(const uint4 *__restrict__ rp, int lb, uint4 (&b)[NCH + 1]) {
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) b[c] = __ldg(rp + c);   // 16 c < n <= lb: needed
-    b[NCH] = 16 * NCH < lb ? __ldg(rp + NCH) : make_uint4(0u, 0u, 0u, 0u);
+// window_dot_u8 for rows of NC chunks of 32 pixels (n <= 32 NC): 32-byte
+// loads (ld.global.nc.v8) of the 32-byte-aligned image copy, whose rows are
+// 32-byte aligned, so that a window row costs its 32-byte sectors once each;
+// the NC + 1 blocks of R rows are loaded together (R = 4, 2 or 1 as the
+// rows widen).  Chunk c needs blocks c and c + 1; its window words are the
+// block pair's words o / 4 onward (a three-level selection by the bits of
+// o / 4), funnel-shifted by 8 (o mod 4) bits.
+__device__ __forceinline__ void ldg_v8(const uint8_t *p, uint32_t (&w)[8]) {
+    asm volatile("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]),
+                   "=r"(w[7])
+                 : "l"(p));
 }
 
-template <int NCH>
-__device__ __forceinline__ unsigned window_dot_u8_rows(const uint8_t *__restrict__ Ipad, int qs, int y,
-                                                       int x, const uint4 *__restrict__ tb, int m,
-                                                       int n) {
-    constexpr int R = NCH <= 2 ? 4 : (NCH <= 4 ? 2 : 1);
-    const int o = x & 15;
+template <int NC>
+__device__ __forceinline__ void load_row32(const uint8_t *__restrict__ rp, int lb, uint32_t (&b)[NC + 1][8]) {
+#pragma unroll
+    for (int c = 0; c <= NC; ++c) {
+        if (c == 0 || 32 * c < lb) {   // a block that holds a byte of the window
+            ldg_v8(rp + 32 * c, b[c]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) b[c][k] = 0u;
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned dp4a_chunk32(const uint32_t (&w0)[8], const uint32_t (&w1)[8], bool k1,
+                                                 bool k2, bool k4, unsigned sh, uint4 t0, uint4 t1,
+                                                 unsigned acc) {
+    uint32_t a[12], b[10], l[9];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+        const uint32_t lo = j < 8 ? w0[j] : w1[j - 8];
+        const uint32_t hi = j + 4 < 8 ? w0[j + 4] : w1[j - 4];
+        a[j] = k4 ? hi : lo;
+    }
+#pragma unroll
+    for (int j = 0; j < 10; ++j) b[j] = k2 ? a[j + 2] : a[j];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) l[j] = k1 ? b[j + 1] : b[j];
+    acc = __dp4a(__funnelshift_r(l[0], l[1], sh), t0.x, acc);
+    acc = __dp4a(__funnelshift_r(l[1], l[2], sh), t0.y, acc);
+    acc = __dp4a(__funnelshift_r(l[2], l[3], sh), t0.z, acc);
+    acc = __dp4a(__funnelshift_r(l[3], l[4], sh), t0.w, acc);
+    acc = __dp4a(__funnelshift_r(l[4], l[5], sh), t1.x, acc);
+    acc = __dp4a(__funnelshift_r(l[5], l[6], sh), t1.y, acc);
+    acc = __dp4a(__funnelshift_r(l[6], l[7], sh), t1.z, acc);
+    acc = __dp4a(__funnelshift_r(l[7], l[8], sh), t1.w, acc);
+    return acc;
+}
+
+template <int NC>
+__device__ __forceinline__ unsigned window_dot_u8_rows32(const uint8_t *__restrict__ Ipad, int qs, int y,
+                                                         int x, const uint4 *__restrict__ tb, int m,
+                                                         int n) {
+    constexpr int R = NC <= 1 ? 4 : (NC <= 2 ? 2 : 1);
+    const int o = x & 31;
     const unsigned sh = 8u * (unsigned)(o & 3);
-    const bool k1 = (o & 4) != 0, k2 = (o & 8) != 0;
+    const bool k1 = (o & 4) != 0, k2 = (o & 8) != 0, k4 = (o & 16) != 0;
     const int lb = o + n;
-    const int qs4 = qs >> 4;
-    const uint4 *rp = reinterpret_cast<const uint4 *>(Ipad + (int64_t)y * qs + (x - o));
+    const uint8_t *rp = Ipad + (int64_t)y * qs + (x - o);
     unsigned acc0 = 0u, acc1 = 0u;
     int u = 0;
 #pragma unroll 1
-    for (; u + R <= m; u += R, tb += R * NCH, rp += R * qs4) {
-        uint4 b[R][NCH + 1];
+    for (; u + R <= m; u += R, tb += R * 2 * NC, rp += (int64_t)R * qs) {
+        uint32_t b[R][NC + 1][8];
 #pragma unroll
-        for (int r = 0; r < R; ++r) load_row_u8<NCH>(rp + r * qs4, lb, b[r]);
+        for (int r = 0; r < R; ++r) load_row32<NC>(rp + (int64_t)r * qs, lb, b[r]);
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-                if ((r * NCH + c) & 1)
-                    acc1 = dp4a_chunk(b[r][c], b[r][c + 1], k1, k2, sh, tb[r * NCH + c], acc1);
+            for (int c = 0; c < NC; ++c) {
+                const uint4 t0 = tb[(r * NC + c) * 2], t1 = tb[(r * NC + c) * 2 + 1];
+                if ((r * NC + c) & 1)
+                    acc1 = dp4a_chunk32(b[r][c], b[r][c + 1], k1, k2, k4, sh, t0, t1, acc1);
                 else
-                    acc0 = dp4a_chunk(b[r][c], b[r][c + 1], k1, k2, sh, tb[r * NCH + c], acc0);
+                    acc0 = dp4a_chunk32(b[r][c], b[r][c + 1], k1, k2, k4, sh, t0, t1, acc0);
             }
     }
 #pragma unroll 1
-    for (; u < m; ++u, tb += NCH, rp += qs4) {
-        uint4 b[NCH + 1];
-        load_row_u8<NCH>(rp, lb, b);
+    for (; u < m; ++u, tb += 2 * NC, rp += qs) {
+        uint32_t b[NC + 1][8];
+        load_row32<NC>(rp, lb, b);
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) {
+        for (int c = 0; c < NC; ++c) {
             if (c & 1)
-                acc1 = dp4a_chunk(b[c], b[c + 1], k1, k2, sh, tb[c], acc1);
+                acc1 = dp4a_chunk32(b[c], b[c + 1], k1, k2, k4, sh, tb[2 * c], tb[2 * c + 1], acc1);
             else
-                acc0 = dp4a_chunk(b[c], b[c + 1], k1, k2, sh, tb[c], acc0);
+                acc0 = dp4a_chunk32(b[c], b[c + 1], k1, k2, k4, sh, tb[2 * c], tb[2 * c + 1], acc0);
         }
     }
     return acc0 + acc1;
 }
 
 // sum over the m x n window at (y, x) of t * I, exactly (tb: the packed
-// template rows of nch 16-byte chunks).
+// template rows of tmpl_row_bytes(n) bytes), in 16-byte loads (any n).
 __device__ __forceinline__ unsigned window_dot_u8(const uint8_t *__restrict__ Ipad, int qs, int y,
                                                   int x, const uint4 *__restrict__ tb, int m, int n) {
     const int o = x & 15;
     const unsigned sh = 8u * (unsigned)(o & 3);
     const bool k1 = (o & 4) != 0, k2 = (o & 8) != 0;
     const int nch = (n + 15) >> 4;
+    const int tstride = tmpl_row_bytes(n) >> 4;   // 16-byte chunks per packed template row
     const int lb = o + n;   // bytes of the aligned row that the window reaches
     const uint4 *rp = reinterpret_cast<const uint4 *>(Ipad + (int64_t)y * qs + (x - o));
     const int qs4 = qs >> 4;
     unsigned acc0 = 0u, acc1 = 0u;
-    for (int u = 0; u < m; ++u, rp += qs4, tb += nch) {
+    for (int u = 0; u < m; ++u, rp += qs4, tb += tstride) {
         uint4 cur = __ldg(rp);
         int c = 0;
         for (; c + 2 <= nch; c += 2) {
@@ -1557,20 +1600,16 @@ __device__ __forceinline__ unsigned window_dot_u8(const uint8_t *__restrict__ Ip
     return acc0 + acc1;
 }
 
-// window_dot_u8 by the row-prefetching form where a row has at most 8
-// chunks (n <= 128); nch is uniform over a block.
+// window_dot_u8 by the 32-byte row form where a row has at most 4 chunks of
+// 32 pixels (n <= 128); n is uniform over a block.
 __device__ __forceinline__ unsigned window_dot_u8_any(const uint8_t *__restrict__ Ipad, int qs, int y,
                                                       int x, const uint4 *__restrict__ tb, int m,
                                                       int n) {
-    switch ((n + 15) >> 4) {
-    case 1: return window_dot_u8_rows<1>(Ipad, qs, y, x, tb, m, n);
-    case 2: return window_dot_u8_rows<2>(Ipad, qs, y, x, tb, m, n);
-    case 3: return window_dot_u8_rows<3>(Ipad, qs, y, x, tb, m, n);
-    case 4: return window_dot_u8_rows<4>(Ipad, qs, y, x, tb, m, n);
-    case 5: return window_dot_u8_rows<5>(Ipad, qs, y, x, tb, m, n);
-    case 6: return window_dot_u8_rows<6>(Ipad, qs, y, x, tb, m, n);
-    case 7: return window_dot_u8_rows<7>(Ipad, qs, y, x, tb, m, n);
-    case 8: return window_dot_u8_rows<8>(Ipad, qs, y, x, tb, m, n);
+    switch ((n + 31) >> 5) {
+    case 1: return window_dot_u8_rows32<1>(Ipad, qs, y, x, tb, m, n);
+    case 2: return window_dot_u8_rows32<2>(Ipad, qs, y, x, tb, m, n);
+    case 3: return window_dot_u8_rows32<3>(Ipad, qs, y, x, tb, m, n);
+    case 4: return window_dot_u8_rows32<4>(Ipad, qs, y, x, tb, m, n);
     default: return window_dot_u8(Ipad, qs, y, x, tb, m, n);
     }
 }
@@ -1661,7 +1700,7 @@ __device__ __forceinline__ void lane_sweep(const Scan2Batch &B, const uint8_t *_
     const uint4 *tb = reinterpret_cast<const uint4 *>(lsm4);
     if (u8) {
         const uint4 *src = reinterpret_cast<const uint4 *>(B.tf + blockIdx.y * B.tsz + (size_t)m * npad);
-        const int n16 = m * ((n + 15) >> 4);
+        const int n16 = m * (tmpl_row_bytes(n) >> 4);
         for (int i = threadIdx.x; i < n16; i += blockDim.x) reinterpret_cast<uint4 *>(lsm4)[i] = src[i];
         __syncthreads();
     } else {
