@@ -750,7 +750,7 @@ ScratchPlan plan_scratch(opta_handle *H, const opta_template *t, int n_t) {
         c.T = std::max(c.T, chunk * (size_t)m * n);
         c.TS = std::max(c.TS, chunk * tmpl_slot_floats(m, n));
         const size_t N = ((2 * chunk + 15) / 16) * 16;
-        if (use_mma(H)) c.B = std::max(c.B, (size_t)m * Kp * N * 2);
+        if (use_mma(H)) c.B = std::max(c.B, corr_mma_bbytes(m, Kp, (int)N, S ? S->h : m));
         // the template tiles of a scan-2 launch that may take the dense map
         if (dense_usable(H, m, n))
             c.B = std::max(c.B, (size_t)scan2_batch(L, (int)chunk) * brute_tmpl_bytes(m, n));
@@ -795,7 +795,7 @@ opta_status enqueue_scan1(opta_handle *H, opta_search_ctx *X, const opta_templat
     // scan 1: rho(t, pivot) at every centre
     if (use_mma(H)) {
         const int N = ((2 * n + 15) / 16) * 16;
-        CK(cudaMemsetAsync(X->Bmma, 0, (size_t)m * Kp * N * 2, s));
+        CK(cudaMemsetAsync(X->Bmma, 0, (size_t)(m + 1) * Kp * N * 2, s));   // row m stays zero
         CK(launch_tmpl_split(X->tf, tsz, n, m, nn, npad, Kp, N, st, X->Bmma, s));
         int Gx_u = S->Gx;
         CK(launch_corr_mma(S->P, H->p, H->q, X->Bmma, m, nn, Kp, N, S->h, S->Ly, S->Lx, n,

@@ -262,7 +262,10 @@ cudaError_t launch_centre_rho(const uint8_t *P, int p, int q, const float *tf, i
                               int npad, int h, int Ly, int Lx, const float *c_inv_sigma,
                               TmplState *st, float *rho_tc, int gx_begin, cudaStream_t s);
 // Tensor-core scan 1 for T same-size templates (planes of B), see corr_mma.cu.
-cudaError_t launch_corr_mma(const uint8_t *V, int p, int q, const void *B, int m, int n, int Kp,
+// B holds corr_mma_bbytes(m, Kp, N, h) bytes: the template planes ((m + 1)
+// rows, row m zero) and the per-launch arrangement of them that follows.
+size_t corr_mma_bbytes(int m, int Kp, int N, int h);
+cudaError_t launch_corr_mma(const uint8_t *V, int p, int q, void *B, int m, int n, int Kp,
                             int N, int h, int Ly, int Lx, int T, const float *c_inv_sigma,
                             const TmplState *st, float *rho_tc, int64_t gstride, int *err,
                             int *Gx_u_out, cudaStream_t s);

@@ -22,14 +22,23 @@
 //
 // A CTA takes RC centre rows cy_k (k < RC, about h apart) of the same 128
 // centres and walks the pivot rows r: the Hankel operand of row r is built
-// once and feeds every accumulator k with u = r - cy_k in [0, m), against
-// template row u (RC tiles of B per pivot row, accumulator k at TMEM column
-// k * N).  Two stages (A and the B tiles) overlap the build of the next
-// pivot row with the MMAs of the current one, and the work is split by
-// warp: lane 0 of warp 0 queues the B tiles (bulk copies) and issues and
-// commits the MMAs, warps 1-7 build the Hankel operand; the stages change
-// hands through mbarriers (operand written, tiles landed, MMAs done), so
-// neither side waits for the other at a CTA barrier.
+// once and feeds every accumulator k with u_k = r - cy_k in [0, m), against
+// template row u_k.  The RC accumulators sit side by side in TMEM (k at
+// column k * N), so one MMA of N' = RC * N columns serves all of them: its
+// B operand holds, for each 8-wide K block, the tiles of rows u_0 .. u_RC-1
+// one after another (a zero tile, row m of the buffer, where u_k is out of
+// range).  Two stages (A and B) overlap the build of the next pivot row
+// with the MMAs of the current one, and the work is split by warp: lane 0
+// of warp 0 issues and commits the MMAs; warps 1-7 build the Hankel
+// operand, and warp 1 first queues the B operand of the step; the stages
+// change hands through mbarriers (operand and tiles ready, MMAs done), so no
+// role waits for another at a CTA barrier.  Where the CTA's centre rows are
+// exactly h apart (all but the last, clamped group row), the B operand of
+// pivot row r is one contiguous block of a buffer arranged per launch,
+// B2[u0 = r - cy_0][c][k] = tile (u0 - k h, c), and arrives by one bulk
+// copy: a bulk copy or an MMA costs its issuing thread about a hundred
+// cycles, so the step issues one copy and Kp/16 MMAs, not RC * Kp/8 copies
+// and RC * Kp/16 MMAs.
 //
 // The operands are fp16 (kind::f16 with both operands fp16): a pixel
 // P - 128 is an integer of at most 8 bits, exact, and converts from a byte by
@@ -69,7 +78,9 @@ __host__ __device__ inline uint32_t round_up(uint32_t x, uint32_t a) { return (x
 struct CorrMmaArgs {
     const uint8_t *V;          // pivot image, p x q
     int p, q;
-    const __half *B;           // [m][Kp/8][N/8][8][8]
+    const __half *B;           // [m + 1][Kp/8][N/8][8][8]; row m is zero
+    const __half *B2;          // [R2][Kp/8][RC][N/8][8][8]: B2[u0][c][k] = B[u0 - k h][c] (zero outside)
+    int R2;                    // rows of B2: m + (RC - 1) h
     int m, n, Kp, N;
     int h, Ly, Lx, Gx, Gx_u;   // Gx_u: leading groups whose centres are uniform (cx0 + h*i)
     int Gy, RC;                // group rows; centre rows per CTA (1, 2 or 4)
@@ -111,21 +122,22 @@ __device__ __forceinline__ ItemWords item_words(const uint8_t *row, int x, int q
     r.sh = (uint32_t)(ad & 3) * 8u;
     return r;
 }
-constexpr int kMaxRC = 4;   // centre rows per CTA (the launcher measures 1, 2 and 4)
+constexpr int kMaxRC = 4;   // centre rows per CTA (the launcher measures 1 to 4, RC * N <= 256)
 
-__global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaArgs a) {
+__global__ void __launch_bounds__(kMmaThreads, 4) corr_mma_kernel(const CorrMmaArgs a) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint64_t *b_full = reinterpret_cast<uint64_t *>(smem);   // [2] B tiles landed
+    uint64_t *a_full = reinterpret_cast<uint64_t *>(smem);   // [2] A written (7 builder warps) and B checked
+    uint64_t *b_full = a_full + 2;                           // [2] B tiles landed (transaction bytes)
     uint64_t *mma_done = b_full + 2;                         // [2] MMAs of the stage completed
-    uint64_t *a_full = mma_done + 2;                         // [2] A written by the 7 builder warps
-    uint64_t *stall_bar = a_full + 2;                        // never completes (verification only)
+    uint64_t *stall_bar = mma_done + 2;                      // never completes (verification only)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(stall_bar + 1);
     const int WA = 15 * a.h + a.Kp / 8;
     const uint32_t abytes = (uint32_t)WA * 128u;
-    const uint32_t bbytes = (uint32_t)a.N * a.Kp * 2u;
+    const uint32_t cbytes = (uint32_t)a.RC * a.N * 16u;      // one 8-wide K block of the RC tiles
+    const uint32_t bbytes = cbytes * (uint32_t)(a.Kp / 8);
     const uint32_t astride = round_up(abytes, 1024), bstride = round_up(bbytes, 1024);
     uint8_t *Abase = smem + 1024;
-    uint8_t *Bbase = Abase + 2 * astride;                    // [2][RC] tiles
+    uint8_t *Bbase = Abase + 2 * astride;                    // [2] stages of [Kp/8][RC][N/8] core matrices
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int gy0 = blockIdx.y * a.RC;
@@ -133,18 +145,22 @@ __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaA
     const int gx0 = blockIdx.x * kMmaM;
     const int cx0 = group_centre_of(gx0, a.Lx, a.h);
     int cyk[kMaxRC];
+    bool uniform = true;   // centre rows exactly h apart: B2 serves this CTA
 #pragma unroll
-    for (int k = 0; k < kMaxRC; ++k) cyk[k] = k < nrow ? group_centre_of(gy0 + k, a.Ly, a.h) : 0;
+    for (int k = 0; k < kMaxRC; ++k) {
+        cyk[k] = k < nrow ? group_centre_of(gy0 + k, a.Ly, a.h) : 0;
+        if (k < nrow && cyk[k] != cyk[0] + k * a.h) uniform = false;
+    }
 
     uint32_t ncols = 32;
     while ((int)ncols < a.RC * a.N) ncols <<= 1;
     if (tid == 0) {
+        tc5::mbar_init(&a_full[0], kMmaThreads / 32 - 1);
+        tc5::mbar_init(&a_full[1], kMmaThreads / 32 - 1);
         tc5::mbar_init(&b_full[0], 1);
         tc5::mbar_init(&b_full[1], 1);
         tc5::mbar_init(&mma_done[0], 1);
         tc5::mbar_init(&mma_done[1], 1);
-        tc5::mbar_init(&a_full[0], kMmaThreads / 32 - 1);
-        tc5::mbar_init(&a_full[1], kMmaThreads / 32 - 1);
         tc5::mbar_init(stall_bar, 1);
         tc5::fence_mbar_init();
     }
@@ -156,12 +172,11 @@ __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaA
     __syncthreads();
     tc5::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t idesc = tc5::idesc_f16_f32(kMmaM, a.N);
 
     bool ok = true;
     const int r_end = group_centre_of(gy0 + nrow - 1, a.Ly, a.h) + a.m;
-    // template row u_k of accumulator k at pivot row r (-1: none); both roles
-    // walk the same rows and count the same steps
+    // template row u_k of accumulator k at pivot row r (-1: none); every role
+    // walks the same rows and counts the same steps
     auto rows_of = [&](int r, int (&uk)[kMaxRC]) {
         int nvalid = 0;
 #pragma unroll
@@ -174,58 +189,50 @@ __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaA
     };
     if (warp == 0) {
         if (lane == 0) {
-            // producer of the B tiles and issuer of the MMAs: step k waits for
-            // its stage to be released by the MMAs of step k - 2, queues the B
-            // tiles, waits for the builders' A and the tiles, issues, commits
-            int step = 0, last = -1, pending = -1;   // last committed, copies not yet consumed
+            // issuer: step k waits for its stage (operand built, tiles
+            // landed), issues Kp/16 MMAs of 128 x RC*N x 16 and commits
+            const uint32_t idesc = tc5::idesc_f16_f32(kMmaM, a.RC * a.N);
+            const uint64_t ad0 = tc5::smem_desc(tc5::smem_u32(Abase), 128, 128u * a.h);
+            const uint64_t ad1 = tc5::smem_desc(tc5::smem_u32(Abase + astride), 128, 128u * a.h);
+            const uint64_t bd0 = tc5::smem_desc(tc5::smem_u32(Bbase), cbytes, 128);
+            const uint64_t bd1 = tc5::smem_desc(tc5::smem_u32(Bbase + bstride), cbytes, 128);
+            // the next 16 K columns: 256 bytes further in A, two K blocks in B
+            // (descriptor start addresses count 16-byte units)
+            const uint64_t bstep = (uint64_t)((2u * cbytes) >> 4);
+            const int nk = a.Kp / 16;
+            int step = 0, last = -1;
             // verification of the timeout path: a wait that cannot complete
             if (a.stall && !tc5::mbar_wait(stall_bar, 0u, a.wait_ns)) ok = false;
             for (int r = cyk[0]; ok && r < r_end; ++r) {
                 int uk[kMaxRC];
-                const int nvalid = rows_of(r, uk);
-                if (nvalid == 0) continue;
+                if (rows_of(r, uk) == 0) continue;
                 const int s = step & 1;
                 const uint32_t ph = (step >> 1) & 1;
-                if (step >= 2 && !tc5::mbar_wait(&mma_done[s], ph ^ 1u, a.wait_ns)) { ok = false; break; }
-                tc5::mbar_arrive_expect_tx(&b_full[s], (uint32_t)nvalid * bbytes);
-#pragma unroll
-                for (int k = 0; k < kMaxRC; ++k)
-                    if (uk[k] >= 0)
-                        tc5::bulk_g2s(Bbase + (s * a.RC + k) * bstride, a.B + (size_t)uk[k] * a.N * a.Kp,
-                                      bbytes, &b_full[s]);
-                pending = step;
-                if (!tc5::mbar_wait(&a_full[s], ph, a.wait_ns) || !tc5::mbar_wait(&b_full[s], ph, a.wait_ns)) {
-                    ok = false;
-                    break;
-                }
-                pending = -1;
+                if (!tc5::mbar_wait(&a_full[s], ph, a.wait_ns)) { ok = false; break; }
                 tc5::tc_fence_after();
-                const uint32_t abase = tc5::smem_u32(Abase + s * astride);
-                const uint32_t blbo = (uint32_t)(a.N / 8) * 128u;
-#pragma unroll
-                for (int k = 0; k < kMaxRC; ++k) {
-                    if (uk[k] < 0) continue;
-                    const uint32_t bbase = tc5::smem_u32(Bbase + (s * a.RC + k) * bstride);
-                    for (int kk = 0; kk < a.Kp / 16; ++kk) {
-                        const uint64_t ad = tc5::smem_desc(abase + kk * 256, 128, 128u * a.h);
-                        const uint64_t bd = tc5::smem_desc(bbase + kk * 2 * blbo, blbo, 128);
-                        tc5::mma_bf16(tmem + (uint32_t)(k * a.N), ad, bd, idesc, (uk[k] > 0 || kk > 0));
-                    }
-                }
+                const uint64_t ad = s ? ad1 : ad0, bd = s ? bd1 : bd0;
+                // the first step initialises every accumulator (tiles of
+                // rows out of range are zero)
+                for (int kk = 0; kk < nk; ++kk)
+                    tc5::mma_bf16(tmem, ad + (uint64_t)(16 * kk), bd + (uint64_t)kk * bstep, idesc,
+                                  step > 0 || kk > 0);
                 tc5::mma_commit(&mma_done[s]);
                 last = step;
                 ++step;
             }
-            // drain (bounded): copies still in flight, then the last MMA batch
-            if (pending >= 0) tc5::mbar_wait(&b_full[pending & 1], (pending >> 1) & 1, kWaitNs);
+            // drain (bounded): the last MMA batch
             if (last >= 0 && !tc5::mbar_wait(&mma_done[last & 1], (last >> 1) & 1, kWaitNs)) ok = false;
         }
     } else {
         // builders (warps 1..7): step k writes A of stage k & 1 once the MMAs
-        // of step k - 2 released it (lane 0 waits; the warp follows it)
+        // of step k - 2 released it (lane 0 waits; the warp follows it);
+        // warp 1 first queues the step's B tiles and, before its arrival on
+        // a_full, waits until they landed
         const int btid = tid - 32;
         constexpr int kBuilders = kMmaThreads - 32;
-        int step = 0;
+        const int ncopy = a.RC * (a.Kp / 8);
+        const uint32_t tile_bytes = (uint32_t)a.N * 16u;
+        int step = 0, last_tx = -1;
         for (int r = cyk[0]; r < r_end; ++r) {
             int uk[kMaxRC];
             if (rows_of(r, uk) == 0) continue;
@@ -238,22 +245,66 @@ __global__ void __launch_bounds__(kMmaThreads, 1) corr_mma_kernel(const CorrMmaA
                 __syncwarp();
                 if (!w_ok) { ok = false; break; }
             }
+            if (warp == 1) {
+                // slot j = c * RC + k <- K block c of template row u_k (row m: zeros)
+                if (lane == 0) tc5::mbar_arrive_expect_tx(&b_full[s], bbytes);
+                __syncwarp();
+                uint8_t *Bs = Bbase + s * bstride;
+                const int u0 = r - cyk[0];
+                if (uniform && u0 < a.R2) {
+                    if (lane == 0) tc5::bulk_g2s(Bs, a.B2 + (size_t)u0 * (bbytes / 2), bbytes, &b_full[s]);
+                } else for (int j = lane; j < ncopy; j += 32) {
+                    const int k = j % a.RC, c = j / a.RC;
+                    int u = -1;
+#pragma unroll
+                    for (int k2 = 0; k2 < kMaxRC; ++k2)
+                        if (k2 == k) u = uk[k2];
+                    if (u < 0) u = a.m;
+                    tc5::bulk_g2s(Bs + (size_t)j * tile_bytes,
+                                  a.B + ((size_t)u * (a.Kp / 8) + c) * (size_t)a.N * 8, tile_bytes,
+                                  &b_full[s]);
+                }
+                last_tx = step;
+            }
             // A_r: segment w, copy b = pixels cx0 + h*b + 8w .. +7 of row r
             const uint8_t *row = a.V + (size_t)r * a.q;
             uint8_t *Ab = Abase + s * astride;
-            for (int j = btid; j < WA * 8; j += kBuilders) {
-                const ItemWords iw = item_words(row, cx0 + a.h * (j & 7) + 8 * (j >> 3), a.q);
-                const uint32_t lo = __funnelshift_r(iw.w0, iw.w1, iw.sh);
-                const uint32_t hi = __funnelshift_r(iw.w1, iw.w2, iw.sh);
-                *reinterpret_cast<uint4 *>(Ab + (j >> 3) * 128 + (j & 7) * 16) =
-                    make_uint4(tc5::bytes_f16x2<0>(lo), tc5::bytes_f16x2<2>(lo), tc5::bytes_f16x2<0>(hi),
-                               tc5::bytes_f16x2<2>(hi));
+            // the loads of up to three items first, then their conversions and stores
+            const int nitems = WA * 8;
+            for (int j0 = btid; j0 < nitems; j0 += 3 * kBuilders) {
+                ItemWords iw[3];
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    const int j = j0 + e * kBuilders;
+                    if (j < nitems) iw[e] = item_words(row, cx0 + a.h * (j & 7) + 8 * (j >> 3), a.q);
+                }
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    const int j = j0 + e * kBuilders;
+                    if (j < nitems) {
+                        const uint32_t lo = __funnelshift_r(iw[e].w0, iw[e].w1, iw[e].sh);
+                        const uint32_t hi = __funnelshift_r(iw[e].w1, iw[e].w2, iw[e].sh);
+                        *reinterpret_cast<uint4 *>(Ab + (j >> 3) * 128 + (j & 7) * 16) =
+                            make_uint4(tc5::bytes_f16x2<0>(lo), tc5::bytes_f16x2<2>(lo),
+                                       tc5::bytes_f16x2<0>(hi), tc5::bytes_f16x2<2>(hi));
+                    }
+                }
             }
             tc5::fence_proxy_async_smem();
             __syncwarp();
+            if (warp == 1) {
+                bool w_ok = true;
+                if (lane == 0) w_ok = tc5::mbar_wait(&b_full[s], ph, a.wait_ns);
+                w_ok = __shfl_sync(0xffffffffu, w_ok ? 1 : 0, 0) != 0;
+                __syncwarp();
+                if (!w_ok) { ok = false; break; }
+            }
             if (lane == 0) tc5::mbar_arrive(&a_full[s]);
             ++step;
         }
+        // drain (bounded): the tiles of the last step queued
+        if (warp == 1 && lane == 0 && last_tx >= 0)
+            tc5::mbar_wait(&b_full[last_tx & 1], (last_tx >> 1) & 1, kWaitNs);
     }
     tc5::tc_fence_before();
     ok = __syncthreads_and(ok) != 0;
@@ -312,11 +363,37 @@ __global__ void tmpl_split_kernel(const float *__restrict__ tf, size_t tsz, int 
     }
 }
 
+// B2[u0][c][k] = B[u0 - k h][c] (a tile of N x 8 fp16, N * 16 bytes), zero
+// where u0 - k h is outside [0, m): the B operand of pivot row cy_0 + u0 for
+// a CTA whose RC centre rows are h apart, contiguous.
+__global__ void b2_arrange_kernel(const uint4 *__restrict__ B, uint4 *__restrict__ B2, int m, int KB,
+                                  int N, int RC, int h, int R2) {
+    const int64_t total = (int64_t)R2 * KB * RC * N;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int e = (int)(idx % N);
+        int64_t t = idx / N;
+        const int k = (int)(t % RC);
+        t /= RC;
+        const int c = (int)(t % KB);
+        const int u0 = (int)(t / KB);
+        const int u = u0 - k * h;
+        B2[idx] = (u >= 0 && u < m) ? B[((int64_t)u * KB + c) * N + e] : make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
 }  // namespace
+
+size_t corr_mma_bbytes(int m, int Kp, int N, int h) {
+    size_t b2 = 0;
+    for (int rc = 1; rc <= kMaxRC && rc * N <= 256; ++rc)
+        b2 = std::max(b2, (size_t)(m + (rc - 1) * h) * rc * Kp * N * 2);
+    return round_up((uint32_t)((size_t)(m + 1) * Kp * N * 2), 1024) + b2;
+}
 
 size_t corr_mma_smem(int h, int Kp, int N, int RC) {
     const uint32_t WA = 15u * h + Kp / 8;
-    return 1024 + 2 * round_up(WA * 128u, 1024) + 2 * (size_t)RC * round_up((uint32_t)N * Kp * 2u, 1024);
+    return 1024 + 2 * round_up(WA * 128u, 1024) + 2 * (size_t)round_up((uint32_t)RC * N * Kp * 2u, 1024);
 }
 
 cudaError_t launch_tmpl_split(const float *tf, size_t tsz, int T, int m, int n, int npad, int Kp,
@@ -333,7 +410,7 @@ namespace {
 // Centre rows per CTA, in the order preferred before measurement: more rows
 // amortise each pivot row's operand build over more MMAs, fewer leave TMEM
 // room for more resident CTAs.
-constexpr int kRcs[] = {2, 1, 4};
+constexpr int kRcs[] = {2, 1, 3, 4};
 
 struct MmaTuneKey {
     int m, n, N, h, p, q;
@@ -346,7 +423,7 @@ std::map<MmaTuneKey, int> g_tuned;   // chosen centre rows per CTA
 
 }  // namespace
 
-cudaError_t launch_corr_mma(const uint8_t *V, int p, int q, const void *B, int m, int n, int Kp,
+cudaError_t launch_corr_mma(const uint8_t *V, int p, int q, void *B, int m, int n, int Kp,
                             int N, int h, int Ly, int Lx, int T, const float *c_inv_sigma,
                             const TmplState *st, float *rho_tc, int64_t gstride, int *err,
                             int *Gx_u_out, cudaStream_t s) {
@@ -357,13 +434,17 @@ cudaError_t launch_corr_mma(const uint8_t *V, int p, int q, const void *B, int m
     *Gx_u_out = Gx_u;
     if (Gx_u <= 0) return cudaSuccess;
     if (N % 16 != 0 || N < 16 || N > 256 || Kp % 16 != 0) return cudaErrorInvalidValue;
-    // RC accumulators of N columns within TMEM's 512, shared memory within 227 KB
+    // RC accumulators of N columns: one MMA of RC * N <= 256 columns; shared
+    // memory within 227 KB
     auto fits = [&](int rc) {
-        return rc <= kMaxRC && rc * N <= 512 && rc <= Gy && corr_mma_smem(h, Kp, N, rc) <= 227 * 1024;
+        return rc <= kMaxRC && rc * N <= 256 && rc <= Gy && corr_mma_smem(h, Kp, N, rc) <= 227 * 1024;
     };
     CorrMmaArgs a;
     a.V = V; a.p = p; a.q = q;
     a.B = static_cast<const __half *>(B);
+    a.B2 = reinterpret_cast<const __half *>(static_cast<uint8_t *>(B) +
+                                            round_up((uint32_t)((size_t)(m + 1) * Kp * N * 2), 1024));
+    a.R2 = 0;
     a.m = m; a.n = n; a.Kp = Kp; a.N = N;
     a.h = h; a.Ly = Ly; a.Lx = Lx; a.Gx = Gx; a.Gx_u = Gx_u;
     a.Gy = Gy;
@@ -385,6 +466,16 @@ cudaError_t launch_corr_mma(const uint8_t *V, int p, int q, const void *B, int m
         const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(corr_mma_kernel), smem);
         if (e != cudaSuccess) return e;
         a.RC = rc;
+        a.R2 = m + (rc - 1) * h;
+        {
+            const int64_t total = (int64_t)a.R2 * (Kp / 8) * rc * N;
+            LaunchScope ls2("b2_arrange_kernel", s);
+            b2_arrange_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, s>>>(
+                reinterpret_cast<const uint4 *>(a.B), reinterpret_cast<uint4 *>(const_cast<__half *>(a.B2)),
+                m, Kp / 8, N, rc, h, a.R2);
+            const cudaError_t e2 = cudaGetLastError();
+            if (e2 != cudaSuccess) return e2;
+        }
         dim3 grid((Gx_u + kMmaM - 1) / kMmaM, (Gy + rc - 1) / rc);
         LaunchScope ls("corr_mma_kernel", s);
         corr_mma_kernel<<<grid, kMmaThreads, smem, s>>>(a);
