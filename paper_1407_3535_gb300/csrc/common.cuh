@@ -441,7 +441,7 @@ opta_status exhaustive_run(const uint8_t *I8, int p, int q, const float *tdev, i
                            int n, const ExhaustiveBufs &b, opta_result *best, cudaStream_t s);
 
 int num_sms();
-int topk_blocks(int G);
+int topk_blocks(int G, int T);
 // Budget of scan 1's waits for progress (0: the default 2 s) and its stall
 // switch, for the verification hook opta_dbg_scan1_wait.
 void set_scan1_wait(uint64_t wait_ns, int stall);

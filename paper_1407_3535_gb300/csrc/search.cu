@@ -558,51 +558,105 @@ centre_rho_kernel(const uint8_t *__restrict__ P, int p, int q, const float *__re
 }
 
 // rho(t_k, pivot) at the centres of one group column gx (all group rows) for a
-// chunk of templates: one warp per (template, centre).  Used for the last
-// column when its centre is off the uniform grid the tensor-core path covers.
+// chunk of templates.  Used for the last column when its centre is off the
+// uniform grid the tensor-core path covers.  A block takes one template
+// (blockIdx.y), holds it in shared memory and walks kColChunk centres, one
+// warp per centre at a time, so each template is read from global memory
+// once per chunk rather than once per centre.  A template of bytes takes
+// Eq. rho1's numerator exactly, m n sum(t P) - sum(t) sum(P), from 4-byte dot
+// products (as the survivors do); others take sum(t' (P - 128)) in FP32.
+// the largest m n whose sum of byte products fits in u32 (mn 255^2 < 2^32)
+constexpr int kU8MaxMN = 32768;
+constexpr int kColChunk = 64;
 __global__ void __launch_bounds__(256)
 centre_column_kernel(const uint8_t *__restrict__ P, int q, const float *__restrict__ tf, int m,
                      int n, int npad, size_t tsz, int h, int Ly, int Lx, int gx, int T,
                      const float *__restrict__ c_inv_sigma,
                      const TmplState *__restrict__ st, float *rho_tc, int64_t gstride) {
+    extern __shared__ float4 csm4[];   // the block's template: t' (m x npad) or its bytes (m x wr words)
     const int Gy = groups_along(Ly, h), Gx = groups_along(Lx, h);
-    const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int k = blockIdx.y;
+    const bool u8 = st[k].u8 != 0 && (long long)m * n <= kU8MaxMN;
+    const int wr = tmpl_row_bytes(n) / 4;   // words per packed template row
+    {
+        const float *src = tf + (size_t)k * tsz + (u8 ? (size_t)m * npad : 0);
+        const int n16 = u8 ? m * wr / 4 : m * npad / 4;
+        for (int i = threadIdx.x; i < n16; i += blockDim.x)
+            csm4[i] = reinterpret_cast<const float4 *>(src)[i];
+    }
+    __syncthreads();
+    const float *tsm = reinterpret_cast<const float *>(csm4);
+    const uint32_t *tsw = reinterpret_cast<const uint32_t *>(csm4);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int cx = group_centre_of(gx, Lx, h);
-    for (int w = warp; w < T * Gy; w += nwarps) {
-        const int k = w / Gy, gy = w % Gy;
+    const uint8_t *pend = P + (int64_t)(Ly + m - 1) * q;   // end of the p x q pivot
+    // four columns per lane and step; half-warps take two rows at once when
+    // n / 4 <= 16
+    const int n4 = n >> 2;
+    const int rpp = n4 <= 16 ? 2 : 1;
+    const int lr = rpp == 2 ? lane >> 4 : 0, lg = rpp == 2 ? lane & 15 : lane;
+    const int gstep = rpp == 2 ? 16 : 32;
+    constexpr float kC = 8388608.f + 128.f;
+    const int gy_end = min(Gy, (int)(blockIdx.x + 1) * kColChunk);
+    for (int gy = blockIdx.x * kColChunk + warp; gy < gy_end; gy += blockDim.x >> 5) {
         const int cy = group_centre_of(gy, Ly, h);
-        const float *tm = tf + (size_t)k * tsz;
         const uint8_t *bp = P + (int64_t)cy * q + cx;
-        // four columns per lane and step (a 16-byte template read, byte
-        // loads turned into b - 128 exactly by the 2^23 magic); half-warps
-        // take two rows at once when n / 4 <= 16 (centre_column_kacc)
-        const int n4 = n >> 2;
-        const int rpp = n4 <= 16 ? 2 : 1;
-        const int lr = rpp == 2 ? lane >> 4 : 0, lg = rpp == 2 ? lane & 15 : lane;
-        const int gstep = rpp == 2 ? 16 : 32;
-        constexpr float kC = 8388608.f + 128.f;
-        float acc = 0.f;
-        for (int u = lr; u < m; u += rpp) {
-            const uint8_t *br = bp + (int64_t)u * q;
-            const float *tr = tm + u * npad;
-            for (int g = lg; g < n4; g += gstep) {
-                const float4 tv = *reinterpret_cast<const float4 *>(tr + 4 * g);
-                const uint8_t *b4 = br + 4 * g;
-                acc = fmaf(tv.x, __uint_as_float(0x4B000000u | b4[0]) - kC, acc);
-                acc = fmaf(tv.y, __uint_as_float(0x4B000000u | b4[1]) - kC, acc);
-                acc = fmaf(tv.z, __uint_as_float(0x4B000000u | b4[2]) - kC, acc);
-                acc = fmaf(tv.w, __uint_as_float(0x4B000000u | b4[3]) - kC, acc);
+        float r = 0.f;
+        if (u8) {
+            unsigned acc = 0u, sp = 0u;   // sum t P, sum P over the window
+            for (int u = lr; u < m; u += rpp) {
+                const uint8_t *br = bp + (int64_t)u * q;
+                const uint32_t *tr = tsw + u * wr;
+                for (int g = lg; g < n4; g += gstep) {
+                    // the four pixels from the aligned words around them
+                    const uintptr_t ad = reinterpret_cast<uintptr_t>(br + 4 * g);
+                    const uint32_t *wp = reinterpret_cast<const uint32_t *>(ad & ~(uintptr_t)3);
+                    const unsigned sh = 8u * (unsigned)(ad & 3);
+                    uint32_t w;
+                    if (sh == 0u) {
+                        w = wp[0];
+                    } else if (reinterpret_cast<const uint8_t *>(wp + 2) <= pend) {
+                        w = __funnelshift_r(wp[0], wp[1], sh);
+                    } else {
+                        const uint8_t *b4 = br + 4 * g;
+                        w = (uint32_t)b4[0] | ((uint32_t)b4[1] << 8) | ((uint32_t)b4[2] << 16) |
+                            ((uint32_t)b4[3] << 24);
+                    }
+                    acc = __dp4a(w, tr[g], acc);
+                    sp = __dp4a(w, 0x01010101u, sp);
+                }
+                for (int v = 4 * n4 + lg; v < n; v += gstep) {
+                    const unsigned b = br[v];
+                    acc += b * ((tr[v >> 2] >> (8 * (v & 3))) & 255u);
+                    sp += b;
+                }
             }
-            for (int v = 4 * n4 + lg; v < n; v += gstep)
-                acc = fmaf(tr[v], __uint_as_float(0x4B000000u | br[v]) - kC, acc);
+            acc = __reduce_add_sync(0xffffffffu, acc);
+            sp = __reduce_add_sync(0xffffffffu, sp);
+            const long long D = mul_sub_wide((unsigned)(m * n), acc, st[k].sum_t, (int)sp);
+            r = i64_to_f32(D) / (float)(m * n);
+        } else {
+            float acc = 0.f;
+            for (int u = lr; u < m; u += rpp) {
+                const uint8_t *br = bp + (int64_t)u * q;
+                const float *tr = tsm + u * npad;
+                for (int g = lg; g < n4; g += gstep) {
+                    const float4 tv = *reinterpret_cast<const float4 *>(tr + 4 * g);
+                    const uint8_t *b4 = br + 4 * g;
+                    acc = fmaf(tv.x, __uint_as_float(0x4B000000u | b4[0]) - kC, acc);
+                    acc = fmaf(tv.y, __uint_as_float(0x4B000000u | b4[1]) - kC, acc);
+                    acc = fmaf(tv.z, __uint_as_float(0x4B000000u | b4[2]) - kC, acc);
+                    acc = fmaf(tv.w, __uint_as_float(0x4B000000u | b4[3]) - kC, acc);
+                }
+                for (int v = 4 * n4 + lg; v < n; v += gstep)
+                    acc = fmaf(tr[v], __uint_as_float(0x4B000000u | br[v]) - kC, acc);
+            }
+            r = warp_sum_f(acc);
         }
-        acc = warp_sum_f(acc);
         if (lane == 0) {
             const int64_t g = (int64_t)gy * Gx + gx;
             const float is = c_inv_sigma[g];
-            rho_tc[k * gstride + g] = (acc * st[k].inv_sigma) * is;
+            rho_tc[k * gstride + g] = (r * st[k].inv_sigma) * is;
         }
     }
 }
@@ -659,16 +713,18 @@ topk_stage1_kernel(const float *__restrict__ rho_tc, int G, int64_t gstride, int
     for (int j = 0; j < TOPK_PER_THREAD; ++j) { v[j] = -INFINITY; ix[j] = -1; }
     const int chunk = (G + gridDim.x - 1) / gridDim.x;
     const int g0 = blockIdx.x * chunk, g1 = min(G, g0 + chunk);
-    // four values in flight per thread, then inserted into its sorted list
-    for (int g = g0 + threadIdx.x; g < g1; g += 4 * blockDim.x) {
-        float xs[4];
+    // four values in flight per thread, then inserted into its sorted list in
+    // index order
+    constexpr int kInFlight = 4;
+    for (int g = g0 + threadIdx.x; g < g1; g += kInFlight * blockDim.x) {
+        float xs[kInFlight];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kInFlight; ++u) {
             const int gi = g + u * blockDim.x;
             xs[u] = gi < g1 ? rho_tc[gi] : -INFINITY;
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kInFlight; ++u) {
             float x = xs[u];
             int xi = g + u * blockDim.x;
             if (x > v[TOPK_PER_THREAD - 1]) {
@@ -1242,7 +1298,6 @@ __device__ inline void warp_rho32(const uint8_t *__restrict__ I, int q, int Lx,
 // 16-byte loads.  Only the last rounding steps remain: the conversion of
 // the integer, the division by mn and the two products with 1/sigma_t and
 // 1/Omega (each within a few ulp), so |rho - rho_exact| <= kU8Eps.
-constexpr int kU8MaxMN = 32768;
 constexpr float kU8Eps = 16.f * kU32 * 1.01f;
 
 // warp_rho32 for a template of bytes (TmplState::u8): the staged window's
@@ -2071,8 +2126,11 @@ cudaError_t launch_centre_rho(const uint8_t *P, int p, int q, const float *tf, i
     return cudaGetLastError();
 }
 
-int topk_blocks(int G) {
-    int nb = (G + 16383) / 16384;
+int topk_blocks(int G, int T) {
+    // one wave of the GPU over all templates (8 blocks of 256 per SM), each
+    // block a slice of at least 2048 centres
+    int nb = (num_sms() * 8 + T - 1) / max(T, 1);
+    nb = min(nb, (G + 2047) / 2048);
     if (nb > 256) nb = 256;
     if (nb < 1) nb = 1;
     return nb;
@@ -2083,8 +2141,12 @@ cudaError_t launch_centre_column(const uint8_t *P, int q, const float *tf, int m
                                  const float *c_inv_sigma, const TmplState *st, float *rho_tc,
                                  int64_t gstride, cudaStream_t s) {
     const int Gy = groups_along(Ly, h);
+    if (npad % 4 != 0 || tsz % 4 != 0) return cudaErrorInvalidValue;
+    const size_t smem = std::max((size_t)m * npad * sizeof(float), (size_t)m * tmpl_row_bytes(n));
+    const cudaError_t e = ensure_smem(reinterpret_cast<const void *>(centre_column_kernel), smem);
+    if (e != cudaSuccess) return e;
     LaunchScope ls("centre_column_kernel", s);
-    centre_column_kernel<<<grid_cap((int64_t)T * Gy * 32, 256, 8), 256, 0, s>>>(
+    centre_column_kernel<<<dim3((Gy + kColChunk - 1) / kColChunk, T), 256, smem, s>>>(
         P, q, tf, m, n, npad, tsz, h, Ly, Lx, gx, T, c_inv_sigma, st, rho_tc, gstride);
     return cudaGetLastError();
 }
@@ -2095,7 +2157,7 @@ cudaError_t launch_topk(const float *rho_tc, int64_t gstride, int Gy, int Gx, in
     const int G = Gy * Gx;
     if (k > TOPK_MAX) k = TOPK_MAX;
     if (k < 1) k = 1;
-    const int nb = topk_blocks(G);
+    const int nb = topk_blocks(G, T);
     {
         LaunchScope ls("topk_stage1_kernel", s);
         topk_stage1_kernel<<<dim3(nb, T), 256, 0, s>>>(rho_tc, G, gstride, k, tmp_val, tmp_idx, st);

@@ -30,6 +30,7 @@ def _cuda(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
+@pytest.mark.parametrize("quantize", [False, True], ids=["real", "bytes"])
 @pytest.mark.parametrize("precision", [1, 0])
 @pytest.mark.parametrize("shape,tshape,h,count", [
     ((300, 420), (16, 16), 3, 5),
@@ -38,9 +39,11 @@ def _cuda(a):
     ((333, 333), (24, 24), 9, 7),
     ((160, 1203), (12, 300), 7, 2),     # wide template: operand items past the prefetched ones
 ])
-def test_scan1_intervals_contain_exact(opta, precision, shape, tshape, h, count):
+def test_scan1_intervals_contain_exact(opta, quantize, precision, shape, tshape, h, count):
+    """Templates of bytes take the integer form in the last, off-grid group
+    column (the tensor-core path covers the others)."""
     img = synth.aerial_image(max(shape), 7, 12, seed=h + 10 * count)[:shape[0], :shape[1]].copy()
-    ts = synth.make_templates(img, [tshape] * count, seed=99 + h, noise=3.0)
+    ts = synth.make_templates(img, [tshape] * count, seed=99 + h, noise=3.0, quantize=quantize)
     hd = opta.optA_prepare(_cuda(img), opta.opta_params_default(fixed_h=h, blur=0, precision=precision))
     m, n = tshape
     Ly, Lx = shape[0] - m + 1, shape[1] - n + 1
