@@ -862,6 +862,7 @@ Scan2Batch scan2_batch_of(opta_handle *H, opta_search_ctx *X, SizeState *S, Tmpl
     B.lane_min_u8 = survivor_lane_min(m, nn, true);
     B.lane_min_f32 = survivor_lane_min(m, nn, false);
     B.span = nullptr;
+    B.group_order = (long long)m * nn >= kGroupOrderMN;
     return B;
 }
 

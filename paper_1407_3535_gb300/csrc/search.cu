@@ -1000,7 +1000,7 @@ bound_pass_kernel(const Scan2Batch B, const float2 *__restrict__ gco,
                     const int li = liq[u];
                     const float gap = li >= 0 ? loc_gap(qtv[eqq[u]], co[u]) : 0.f;
                     const bool f = li >= 0 && gap <= lims[t];
-                    if (f) atomicAdd(&hist[t * kUbBuckets + gap_bucket(gap, lims[t])], 1);
+                    if (f) atomicAdd(&hist[t * kUbBuckets + (B.group_order ? 0 : gap_bucket(gap, lims[t]))], 1);
                     // append to template t's unordered list, aggregated over
                     // the lanes of the warp that share t
                     const unsigned fm = __ballot_sync(0xffffffffu, f);
@@ -1060,7 +1060,7 @@ __global__ void bucket_scan_kernel(const Scan2Batch B) {
 
 // Pass B: the unordered survivors of template blockIdx.y into their bucket
 // ranges (bucket 0 = largest bound first) with their bound cos(gap) +
-// margin.  Each block counts a slice per bucket in shared memory and
+// margin; in group order (Scan2Batch::group_order) they keep their places.  Each block counts a slice per bucket in shared memory and
 // reserves every bucket's part with one global atomic.
 __global__ void __launch_bounds__(256)
 bound_sort_kernel(const Scan2Batch B) {
@@ -1079,6 +1079,15 @@ bound_sort_kernel(const Scan2Batch B) {
     float *surv_ub = B.surv_ub + t * B.scap;
     for (int64_t base = (int64_t)blockIdx.x * kChunkLoc; base < n;
          base += (int64_t)gridDim.x * kChunkLoc) {
+        if (B.group_order) {
+            // one bucket, in the bound pass's order: a group's members stay
+            // next to one another (block-uniform branch)
+            for (int64_t e = base + threadIdx.x; e < min(n, base + (int64_t)kChunkLoc); e += blockDim.x) {
+                surv[e] = uidx[e];
+                surv_ub[e] = cosf(ugap[e]) + kCosMargin;
+            }
+            continue;
+        }
         for (int i = threadIdx.x; i < kUbBuckets; i += blockDim.x) cnt[i] = 0;
         __syncthreads();
         float g[SC_PER];
