@@ -122,6 +122,9 @@ __device__ __forceinline__ ItemWords item_words(const uint8_t *row, int x, int q
     r.sh = (uint32_t)(ad & 3) * 8u;
     return r;
 }
+// Segments of one copy a builder thread converts per row: WA = 15 h + Kp/8
+// <= 151 (h <= 9, Kp <= 128) over 28 runs.
+constexpr int kMaxRun = 6;
 constexpr int kMaxRC = 4;   // centre rows per CTA (the launcher measures 1 to 4, RC * N <= 256)
 
 __global__ void __launch_bounds__(kMmaThreads, 4) corr_mma_kernel(const CorrMmaArgs a) {
@@ -232,6 +235,7 @@ __global__ void __launch_bounds__(kMmaThreads, 4) corr_mma_kernel(const CorrMmaA
         constexpr int kBuilders = kMmaThreads - 32;
         const int ncopy = a.RC * (a.Kp / 8);
         const uint32_t tile_bytes = (uint32_t)a.N * 16u;
+        const int runK = (WA + kBuilders / 8 - 1) / (kBuilders / 8);   // segments per thread (<= kMaxRun)
         int step = 0, last_tx = -1;
         for (int r = cyk[0]; r < r_end; ++r) {
             int uk[kMaxRC];
@@ -269,22 +273,39 @@ __global__ void __launch_bounds__(kMmaThreads, 4) corr_mma_kernel(const CorrMmaA
             // A_r: segment w, copy b = pixels cx0 + h*b + 8w .. +7 of row r
             const uint8_t *row = a.V + (size_t)r * a.q;
             uint8_t *Ab = Abase + s * astride;
-            // the loads of up to three items first, then their conversions and stores
-            const int nitems = WA * 8;
-            for (int j0 = btid; j0 < nitems; j0 += 3 * kBuilders) {
-                ItemWords iw[3];
+            // thread (b, run): copy b of the run of K consecutive segments
+            // wb .. wb + K - 1, i.e. the pixels from cx0 + h b + 8 wb on, one
+            // contiguous stretch: its words are loaded once, share one byte
+            // shift, and item k takes words 2k .. 2k + 2 (a warp stores four
+            // segment rows of 128 contiguous bytes)
+            {
+                const int b = btid & 7, wb = (btid >> 3) * runK;
+                const int nk = min(runK, WA - wb);
+                const int xr = cx0 + a.h * b + 8 * wb;
+                if (nk > 0 && xr + 8 * nk + 4 <= a.q) {
+                    const uintptr_t ad = reinterpret_cast<uintptr_t>(row + xr);
+                    const uint32_t *wp = reinterpret_cast<const uint32_t *>(ad & ~(uintptr_t)3);
+                    const uint32_t sh = (uint32_t)(ad & 3) * 8u;
+                    uint32_t wv[2 * kMaxRun + 1];
 #pragma unroll
-                for (int e = 0; e < 3; ++e) {
-                    const int j = j0 + e * kBuilders;
-                    if (j < nitems) iw[e] = item_words(row, cx0 + a.h * (j & 7) + 8 * (j >> 3), a.q);
-                }
+                    for (int i = 0; i <= 2 * kMaxRun; ++i) wv[i] = i <= 2 * nk ? wp[i] : 0u;
 #pragma unroll
-                for (int e = 0; e < 3; ++e) {
-                    const int j = j0 + e * kBuilders;
-                    if (j < nitems) {
-                        const uint32_t lo = __funnelshift_r(iw[e].w0, iw[e].w1, iw[e].sh);
-                        const uint32_t hi = __funnelshift_r(iw[e].w1, iw[e].w2, iw[e].sh);
-                        *reinterpret_cast<uint4 *>(Ab + (j >> 3) * 128 + (j & 7) * 16) =
+                    for (int k = 0; k < kMaxRun; ++k) {
+                        if (k < nk) {
+                            const uint32_t lo = __funnelshift_r(wv[2 * k], wv[2 * k + 1], sh);
+                            const uint32_t hi = __funnelshift_r(wv[2 * k + 1], wv[2 * k + 2], sh);
+                            *reinterpret_cast<uint4 *>(Ab + (wb + k) * 128 + b * 16) =
+                                make_uint4(tc5::bytes_f16x2<0>(lo), tc5::bytes_f16x2<2>(lo),
+                                           tc5::bytes_f16x2<0>(hi), tc5::bytes_f16x2<2>(hi));
+                        }
+                    }
+                } else {
+                    // the right edge of the row: item by item, clamped
+                    for (int k = 0; k < nk; ++k) {
+                        const ItemWords iw = item_words(row, xr + 8 * k, a.q);
+                        const uint32_t lo = __funnelshift_r(iw.w0, iw.w1, iw.sh);
+                        const uint32_t hi = __funnelshift_r(iw.w1, iw.w2, iw.sh);
+                        *reinterpret_cast<uint4 *>(Ab + (wb + k) * 128 + b * 16) =
                             make_uint4(tc5::bytes_f16x2<0>(lo), tc5::bytes_f16x2<2>(lo),
                                        tc5::bytes_f16x2<0>(hi), tc5::bytes_f16x2<2>(hi));
                     }
@@ -434,6 +455,7 @@ cudaError_t launch_corr_mma(const uint8_t *V, int p, int q, void *B, int m, int 
     *Gx_u_out = Gx_u;
     if (Gx_u <= 0) return cudaSuccess;
     if (N % 16 != 0 || N < 16 || N > 256 || Kp % 16 != 0) return cudaErrorInvalidValue;
+    if (15 * h + Kp / 8 > kMaxRun * ((kMmaThreads - 32) / 8)) return cudaErrorInvalidValue;
     // RC accumulators of N columns: one MMA of RC * N <= 256 columns; shared
     // memory within 227 KB
     auto fits = [&](int rc) {
