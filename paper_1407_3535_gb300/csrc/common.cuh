@@ -160,6 +160,7 @@ struct TmplState {
     float tscale;             // scan 1's fp16 planes hold t' * tscale (a power of two putting
     float tscale_inv;         // max |t'| in [2^13, 2^14)); and its inverse
     long long sumsq_t;        // sum of the squared template values (exact when u8)
+    int grouped;              // scan 2: survivors kept in the bound pass's order (group order)
 };
 
 // Floats of one template's slot in a batch: the centred FP32 template (m rows
@@ -174,12 +175,14 @@ __host__ __device__ inline size_t tmpl_slot_floats(int m, int n) {
 // Survivors are bucketed by their upper bound (bucket 0 = highest) so that
 // they are evaluated roughly in decreasing bound order.
 constexpr int kUbBuckets = 256;
-// Templates of at least kGroupOrderMN pixels keep their survivors in the
-// order the bound pass found them, in one bucket: the members of a group sit
-// next to one another, so the windows of a lane-form round overlap and share
-// cache lines (4x fewer L2 sectors at 48 x 48).  Their running lower bound
-// seldom skips a survivor (the threshold centres usually hold the maximum
-// already), so the bound order buys them little; smaller templates keep it.
+// Templates of at least kGroupOrderMN pixels whose survivors number at most
+// a quarter of the count at which their dense map would take over keep the
+// survivors in the order the bound pass found them, in one bucket: the
+// members of a group sit next to one another, so the windows of a lane-form
+// round overlap and share cache lines (4x fewer L2 sectors at 48 x 48).  With
+// so few survivors the running lower bound seldom skips one (the threshold
+// centres usually hold the maximum already) and cannot tip the template into
+// the dense map, so the bound order buys little; other templates keep it.
 constexpr long long kGroupOrderMN = 1024;
 // Templates per scan-2 launch (their histograms share one block's shared memory).
 constexpr int kScan2MaxT = 16;
@@ -328,7 +331,7 @@ struct Scan2Batch {
                                          // entries takes the lane form, else the warp form
                                          // (templates of bytes on Ipad / all others)
     unsigned long long *span;            // null, or [earliest block start, latest block end]
-    int group_order;                     // 1: survivors kept in the bound pass's order, one bucket
+    int group_order;                     // 1: the size may keep its survivors in group order
                                          // of the sweep kernels (%globaltimer ns): the tuner
 };
 

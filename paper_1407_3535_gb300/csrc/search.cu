@@ -1000,7 +1000,7 @@ bound_pass_kernel(const Scan2Batch B, const float2 *__restrict__ gco,
                     const int li = liq[u];
                     const float gap = li >= 0 ? loc_gap(qtv[eqq[u]], co[u]) : 0.f;
                     const bool f = li >= 0 && gap <= lims[t];
-                    if (f) atomicAdd(&hist[t * kUbBuckets + (B.group_order ? 0 : gap_bucket(gap, lims[t]))], 1);
+                    if (f) atomicAdd(&hist[t * kUbBuckets + gap_bucket(gap, lims[t])], 1);
                     // append to template t's unordered list, aggregated over
                     // the lanes of the warp that share t
                     const unsigned fm = __ballot_sync(0xffffffffu, f);
@@ -1052,16 +1052,27 @@ __global__ void bucket_scan_kernel(const Scan2Batch B) {
         const int v = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += v;
     }
+    // group order for a large template whose survivors are few next to the
+    // count at which the dense map would take over (so the bound order's cut
+    // has nothing to save): every cursor at the end, one bucket, and the
+    // sort keeps each entry's place
+    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+    const bool grouped = B.group_order && B.dense_frac > 0.f &&
+                         (double)tot <= 0.25 * (double)B.dense_frac * (double)B.L;
     int acc = incl - sum;
 #pragma unroll
-    for (int k = 0; k < PER; ++k) { bucket_cur[lane * PER + k] = acc; acc += loc[k]; }
-    if (lane == 31) { st->n_surv = incl; st->n_surv_eff = incl; }
+    for (int k = 0; k < PER; ++k) {
+        bucket_cur[lane * PER + k] = grouped ? tot : acc;
+        acc += loc[k];
+    }
+    if (lane == 31) { st->n_surv = incl; st->n_surv_eff = incl; st->grouped = grouped ? 1 : 0; }
 }
 
 // Pass B: the unordered survivors of template blockIdx.y into their bucket
 // ranges (bucket 0 = largest bound first) with their bound cos(gap) +
-// margin; in group order (Scan2Batch::group_order) they keep their places.  Each block counts a slice per bucket in shared memory and
-// reserves every bucket's part with one global atomic.
+// margin; in group order (TmplState::grouped) they keep their places.  Each
+// block counts a slice per bucket in shared memory and reserves every
+// bucket's part with one global atomic.
 __global__ void __launch_bounds__(256)
 bound_sort_kernel(const Scan2Batch B) {
     __shared__ int cnt[kUbBuckets];
@@ -1079,9 +1090,9 @@ bound_sort_kernel(const Scan2Batch B) {
     float *surv_ub = B.surv_ub + t * B.scap;
     for (int64_t base = (int64_t)blockIdx.x * kChunkLoc; base < n;
          base += (int64_t)gridDim.x * kChunkLoc) {
-        if (B.group_order) {
-            // one bucket, in the bound pass's order: a group's members stay
-            // next to one another (block-uniform branch)
+        if (st->grouped) {
+            // in the bound pass's order: a group's members stay next to one
+            // another (block-uniform branch)
             for (int64_t e = base + threadIdx.x; e < min(n, base + (int64_t)kChunkLoc); e += blockDim.x) {
                 surv[e] = uidx[e];
                 surv_ub[e] = cosf(ugap[e]) + kCosMargin;
