@@ -46,7 +46,8 @@
 // template is scaled by a power of two s (TmplState::tscale, s max|t'| in
 // [2^13, 2^14)) and split into fp16 hi + lo, which holds it to about 2^-22;
 // the epilogue multiplies by 1/s, exactly.  FP32 accumulation in TMEM is
-// bounded by 4u per accumulation step (one step per MMA) -- scan1_epsA_f16.
+// bounded by 4u per accumulation step (one step per MMA of a row in range;
+// the zero tiles' MMAs add exact zeros) -- scan1_epsA_f16.
 // The angle intervals that scan 2 needs are formed there from rho and this
 // bound.
 #include <cuda_fp16.h>
